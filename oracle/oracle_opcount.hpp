@@ -1,0 +1,34 @@
+// Test infrastructure only: an operation-counting scalar for the FP64 oracle. Every add, subtract,
+// multiply, divide, negate-free arithmetic op, sqrt, sin and cos performed on it increments a
+// thread-local counter; comparisons are not counted. Running the oracle's step with this scalar
+// gives the algorithmic floating-point operation count of the method on an actual trajectory.
+#pragma once
+#include <cmath>
+#include <cstdint>
+
+namespace orc {
+
+struct OpCount {
+  double v;
+  static uint64_t& counter() {
+    static thread_local uint64_t n = 0;
+    return n;
+  }
+  static void reset() { counter() = 0; }
+  static uint64_t count() { return counter(); }
+  OpCount() : v(0.0) {}
+  OpCount(double x) : v(x) {}  // NOLINT: implicit by design (constants)
+  friend OpCount operator+(const OpCount& a, const OpCount& b) { ++counter(); return OpCount(a.v + b.v); }
+  friend OpCount operator-(const OpCount& a, const OpCount& b) { ++counter(); return OpCount(a.v - b.v); }
+  friend OpCount operator*(const OpCount& a, const OpCount& b) { ++counter(); return OpCount(a.v * b.v); }
+  friend OpCount operator/(const OpCount& a, const OpCount& b) { ++counter(); return OpCount(a.v / b.v); }
+  OpCount operator-() const { return OpCount(-v); }
+  friend bool operator<(const OpCount& a, const OpCount& b) { return a.v < b.v; }
+  friend bool operator==(const OpCount& a, const OpCount& b) { return a.v == b.v; }
+};
+inline OpCount sqrt(const OpCount& a) { ++OpCount::counter(); return OpCount(std::sqrt(a.v)); }
+inline OpCount sin(const OpCount& a) { ++OpCount::counter(); return OpCount(std::sin(a.v)); }
+inline OpCount cos(const OpCount& a) { ++OpCount::counter(); return OpCount(std::cos(a.v)); }
+inline double val(const OpCount& a) { return a.v; }
+
+}  // namespace orc
