@@ -1,0 +1,302 @@
+"""Throughput of the GB300 articulated-body step (env-steps/s), one JSON line on stdout.
+
+A step is one sim_step(1/60 s, 2 substeps) over the whole batch (default: the Ant-like workload,
+4096 environments), preceded by the device-to-device copy of that step's pre-generated actions
+into the DOF actuation view. Inputs are resident in HBM before the timed region; L2 is flushed
+(256 MiB memset) between timed steps, outside each step's event pair.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload ant|humanoid|cartpole] [--envs E]
+  python bench.py --impl reference ...   # the FP64 CPU oracle timed on the host cores
+
+Under torchrun (N > 1) every rank simulates its own E environments on its own GPU (weak scaling:
+environments never interact, so there is no collective on the data path); the timed region is
+bracketed by barriers and the slowest rank's time is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SM_COUNT_NOMINAL = 152
+FP32_LANES_PER_SM = 128
+
+
+def baseline_metric():
+    try:
+        with open(os.path.join(ROOT, "BASELINE.json")) as f:
+            return json.load(f)["metric"]
+    except Exception:
+        return "env-steps/sec on 1 GB300 (Ant-like, 4096 envs)"
+
+
+def workload(name, n_envs):
+    from paper_2108_10470_gb300 import workloads as W
+    return {"ant": W.ant_workload, "humanoid": W.humanoid_workload, "cartpole": W.cartpole_workload}[name](n_envs)
+
+
+def describe(w):
+    return (f"{w.name}-like, {w.n_envs} envs, dt {w.dt:.6f} s, {w.substeps} substeps, "
+            f"{w.params.pos_iters}/{w.params.vel_iters} solver iterations, seeded synthetic inputs")
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = "clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown," \
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown," \
+             "clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(wname, n_envs, budget_s=12.0):
+    """The FP64 oracle, as it stands, on the host cores: env-steps/s on a bounded sample of the
+    same workload, plus its operation count per env-step (the algorithmic flops of the step)."""
+    import oracle
+    from paper_2108_10470_gb300 import workloads as W
+
+    w = workload(wname, n_envs)
+    threads = os.cpu_count() or 1
+    O = oracle.Oracle(w)
+    steps_max = 200
+    root, dof, acts = W.seeded_inputs(w, 0, steps_max)
+    r, d = root.astype(np.float64), dof.astype(np.float64)
+    t0 = time.perf_counter()
+    O.step(r, d, acts[0], n_threads=threads)
+    one = max(time.perf_counter() - t0, 1e-4)
+    n_steps = int(max(2, min(steps_max - 1, budget_s / one)))
+    t0 = time.perf_counter()
+    for k in range(1, 1 + n_steps):
+        O.step(r, d, acts[k], n_threads=threads)
+    el = time.perf_counter() - t0
+    value = n_envs * n_steps / el
+    # algorithmic flops per env-step, counted on a 64-env, 4-step sample of the same trajectory
+    ws = w.subset(list(range(min(64, n_envs))))
+    Oc = oracle.Oracle(ws)
+    rs, ds, acs = W.seeded_inputs(ws, 0, 4)
+    rs, ds = rs.astype(np.float64), ds.astype(np.float64)
+    flops = sum(Oc.step_flops(rs, ds, acs[k]) for k in range(4)) / (4 * ws.n_envs)
+    return {"value": value, "unit": "env-steps/s", "cores": threads, "kind": "oracle",
+            "sample": f"{n_steps} env-steps of all {n_envs} envs after 1 warm-up step ({el:.1f} s, "
+                      f"{threads} threads)"}, flops
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 oracle on the host cores, same workload / metric / unit."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_2108_10470_gb300 import workloads as W
+
+    w = workload(args.workload, args.envs)
+    threads = os.cpu_count() or 1
+    sample_envs = min(args.envs, 1024)
+    ws = w.subset(list(range(sample_envs)))
+    O = oracle.Oracle(ws)
+    root, dof, acts = W.seeded_inputs(ws, 0, args.warmup + args.steps)
+    r, d = root.astype(np.float64), dof.astype(np.float64)
+    for k in range(args.warmup):
+        O.step(r, d, acts[k], n_threads=threads)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        O.step(r, d, acts[args.warmup + k], n_threads=threads)
+    el = time.perf_counter() - t0
+    value = sample_envs * args.steps / el
+    line = {"metric": baseline_metric(), "value": value, "unit": "env-steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": describe(w), "n_envs": args.envs,
+                       "sample": f"each step advances the first {sample_envs} of the {args.envs} envs"},
+            "cpu_baseline": {"value": value, "unit": "env-steps/s", "cores": threads, "kind": "oracle",
+                             "sample": f"{sample_envs} envs x {args.steps} timed env-steps"},
+            "e2e": {"value": value, "unit": "env-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    from paper_2108_10470_gb300 import build, sim, workloads as W
+
+    build.build_library()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = workload(args.workload, args.envs)
+    K, Wm = args.steps, args.warmup
+    s = sim.Sim(w)
+    stream = torch.cuda.current_stream()
+    root, dof, acts = W.seeded_inputs(w, 1000 * rank, Wm + K)
+    s.root_state.copy_(torch.from_numpy(root))
+    s.dof_state.copy_(torch.from_numpy(dof))
+    act_dev = torch.from_numpy(acts).to(dev)  # every step's actions resident in HBM
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    for k in range(Wm):
+        s.dof_actuation.copy_(act_dev[k])
+        s.step()
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        for k in range(K):
+            flush.zero_()  # L2 flush, outside the step's events
+            e0, e1, e2 = ev[k]
+            e0.record(stream)
+            s.dof_actuation.copy_(act_dev[Wm + k])
+            e1.record(stream)
+            s.step()
+            e2.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = [ev[k][0].elapsed_time(ev[k][2]) for k in range(K)]
+    kern_ms = [ev[k][1].elapsed_time(ev[k][2]) for k in range(K)]
+    total_s = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t.item())
+    bad = s.sync_status()
+    # end-to-end through the C ABI with pinned host buffers (copies inside the timed region)
+    n_e2e = min(K, 200)
+    h_act = torch.from_numpy(acts[Wm:Wm + n_e2e]).pin_memory().numpy()
+    h_root = torch.empty((s.N_A, 13), dtype=torch.float32).pin_memory().numpy()
+    h_dof = torch.empty((max(s.N_D, 1), 2), dtype=torch.float32).pin_memory().numpy()
+    s.step_host(np.ascontiguousarray(h_act[0]), h_root, h_dof)
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for k in range(n_e2e):
+        s.step_host(h_act[k], h_root, h_dof)
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    launches = s.launches_per_step * K
+    n_d, n_a = s.N_D, s.N_A
+    s.destroy()
+    if rank != 0:
+        return
+    value = world * w.n_envs * K / total_s
+    clocks = clk.summary()
+    line = {"metric": baseline_metric(), "value": value, "unit": "env-steps/s", "n_gpus": world, "steps": K,
+            "warmup": Wm, "ms_per_step": 1e3 * total_s / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": describe(w), "n_envs_per_gpu": w.n_envs, "dt": w.dt, "substeps": w.substeps,
+                       "l2": "flushed between timed steps (256 MiB memset outside the step events)",
+                       "parallelism": f"replicas x{world} (independent envs per GPU)"},
+            "gpu_launches": launches, "nonfinite_envs": bad,
+            "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+            "e2e": {"value": world * w.n_envs * n_e2e / e2e_s, "unit": "env-steps/s",
+                    "h2d_bytes_per_step": 4 * n_d, "d2h_bytes_per_step": 4 * (13 * n_a + 2 * n_d),
+                    "api": "sim_step_host (pinned host actuation in, root + DOF state out, stream sync)"}}
+    kern_avg_s = statistics.mean(kern_ms) / 1e3
+    roof = None
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu, flops_per_env_step = cpu_baseline(args.workload, args.envs)
+        sm_mhz = clocks["sm_mhz"] or 2070.0
+        peak = SM_COUNT_NOMINAL * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6
+        achieved = flops_per_env_step * w.n_envs / kern_avg_s
+        roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": args.traffic,
+                "kernel": "step_kernel", "kernel_ms": 1e3 * kern_avg_s,
+                "flops_per_env_step": flops_per_env_step,
+                "peak_basis": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (median SM clock sampled "
+                              f"in the timed region)"}
+    line["roofline"] = roof
+    line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="ant", choices=["ant", "humanoid", "cartpole"])
+    ap.add_argument("--envs", type=int, default=4096)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="DRAM bytes per step-kernel launch from an ncu capture of the same kernel")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,199 @@
+/*
+ * sim.h - C ABI of the GB300 batched articulated-body physics step.
+ *
+ * One physics step for thousands of independent environments resident on one GPU (Isaac Gym,
+ * arXiv 2108.10470): reduced-coordinate articulations (Sec. "Physics Simulation"), ground contact
+ * generation, a fixed-iteration TGS-style Gauss-Seidel contact and joint-limit solve (same
+ * section, TGS paragraph and the simulation-parameter table), and integration. The state is
+ * exposed as flat global tensors that the caller views without copying (Sec. "Tensor API";
+ * tables "Physics state tensors" and "Physics control tensors").
+ *
+ * Conventions
+ *   - Every call returns an int status: SIM_OK (0) or a negative SIM_ERR_* code; no call throws.
+ *   - Model arrays passed to sim_create are HOST memory; they are validated and copied, and the
+ *     caller keeps ownership.
+ *   - The library owns every device buffer. Views (sim_get_view) alias them and stay valid until
+ *     sim_destroy. All device work is enqueued on the stream given to sim_create (or
+ *     sim_set_stream) and is asynchronous; reads of a view are valid in stream order.
+ *   - Units: metres, kilograms, seconds, radians. World frame is z-up; the ground is the plane
+ *     z = 0 with normal +z.
+ *   - Quaternions are (x, y, z, w). Rotational inertia is (xx, yy, zz, xy, xz, yz) about the
+ *     link's centre of mass, in link axes.
+ */
+#ifndef ARTSIM_SIM_H
+#define ARTSIM_SIM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------------------- */
+enum {
+  SIM_OK = 0,
+  SIM_ERR_INVALID_ARG = -1, /* null pointer, non-positive count, bad enum, non-finite number      */
+  SIM_ERR_TOPOLOGY = -2,    /* parent[i] >= i, parent[0] != -1, root joint not FREE/FIXED, ...     */
+  SIM_ERR_CUDA = -3,        /* a CUDA runtime call failed (message: sim_last_error_message)       */
+  SIM_ERR_CAPACITY = -4,    /* an env exceeds the kernel limits (links, DOFs, shapes, candidates) */
+  SIM_ERR_TIMEOUT = -5,     /* reserved: a bounded device wait gave up                            */
+  SIM_ERR_NONFINITE = -6,   /* sim_sync_status: some env's state became NaN/Inf                    */
+  SIM_ERR_HANDLE = -7,      /* null, destroyed or foreign handle                                   */
+  SIM_ERR_NO_DEVICE = -8    /* no CUDA device is visible                                           */
+};
+
+/* ---- model description ----------------------------------------------------------------------- */
+enum { SIM_JOINT_FREE = 0, SIM_JOINT_FIXED = 1, SIM_JOINT_REVOLUTE = 2, SIM_JOINT_PRISMATIC = 3 };
+enum { SIM_SHAPE_SPHERE = 0, SIM_SHAPE_CAPSULE = 1, SIM_SHAPE_BOX = 2 };
+
+/* One articulation (paper, Sec. "Physics Simulation": reduced-coordinate articulations; a single
+ * rigid body is a one-link articulation). Links are numbered 0..n_links-1 with parent[i] < i and
+ * parent[0] = -1; link 0 is the root and its joint_type is FREE (floating base, 6 DOF) or FIXED.
+ * Every other link's joint is REVOLUTE or PRISMATIC (1 DOF about/along joint_axis, expressed in
+ * the joint frame) or FIXED. The joint frame of link i sits at parent_pos[i] in the parent link's
+ * frame with orientation parent_quat[i]; at q = 0 the link frame coincides with it. A multi-axis
+ * joint is a chain of 1-DOF joints through massless "virtual" links (is_virtual = 1), which carry
+ * no shapes and are left out of the per-body tensors. Per-link joint data (armature = rotor
+ * inertia added to the DOF, damping = viscous joint damping, limits) belong to the link's joint.
+ * Shapes: SPHERE size[0] = radius; CAPSULE size[0] = radius, size[1] = half segment length, axis =
+ * shape-local x; BOX size = half extents. A shape sits at shape_pos / shape_quat in its link's frame.
+ * Array lengths: L = n_links, S = n_shapes; "[L*3]" means 3 floats per link, row-major. */
+typedef struct {
+  int32_t n_links;
+  const int32_t* parent;      /* [L]                                                     */
+  const int32_t* joint_type;  /* [L]   SIM_JOINT_*                                        */
+  const float* joint_axis;    /* [L*3] unit axis in the joint frame (ignored if no DOF)   */
+  const float* parent_pos;    /* [L*3]                                                     */
+  const float* parent_quat;   /* [L*4] (x, y, z, w), normalised on copy                    */
+  const float* mass;          /* [L]   >= 0; > 0 for a FREE root                           */
+  const float* com;           /* [L*3] centre of mass in the link frame                    */
+  const float* inertia;       /* [L*6] xx yy zz xy xz yz about the COM; positive semi-def. */
+  const float* armature;      /* [L]   >= 0                                                */
+  const float* damping;       /* [L]   >= 0                                                */
+  const float* limit_lo;      /* [L]   used when has_limit[i]                              */
+  const float* limit_hi;      /* [L]   >= limit_lo                                          */
+  const uint8_t* has_limit;   /* [L]   0/1                                                  */
+  const uint8_t* is_virtual;  /* [L]   0/1                                                  */
+  int32_t n_shapes;
+  const int32_t* shape_link;  /* [S]   link index, not virtual                              */
+  const int32_t* shape_type;  /* [S]   SIM_SHAPE_*                                          */
+  const float* shape_size;    /* [S*3] > 0 where used                                       */
+  const float* shape_pos;     /* [S*3]                                                      */
+  const float* shape_quat;    /* [S*4]                                                      */
+  const float* shape_friction;/* [S]   >= 0                                                 */
+} sim_model_desc;
+
+/* Solver parameters (paper's simulation-parameter table: gravity, position / velocity iteration
+ * counts, max bias, friction; contact offset and limit margin are this library's constants).
+ * flags: bit 0 (SIM_FLAG_SIGNATURE) records the per-env constraint-set signature each step. */
+enum { SIM_FLAG_SIGNATURE = 1 };
+typedef struct {
+  float gravity[3];
+  int32_t pos_iters;       /* >= 1 biased (position) iterations                  */
+  int32_t vel_iters;       /* >= 0 unbiased (velocity) iterations                */
+  float contact_offset;    /* a contact point is active iff separation < this    */
+  float limit_margin;      /* a limit row is active iff distance to limit < this */
+  float bias_coef;         /* fraction of the penetration corrected per iteration */
+  float max_depen_vel;     /* cap on the push-out velocity                       */
+  float ground_friction;   /* ground friction; a contact uses max(shape, ground) */
+  int32_t flags;
+} sim_params;
+
+/* ---- views ----------------------------------------------------------------------------------- */
+enum {
+  SIM_VIEW_ROOT_STATE = 0,        /* (N_A, 13) f32 [p 3 | quat 4 | v 3 | omega 3] world; v = root origin velocity. Get/Set */
+  SIM_VIEW_DOF_STATE = 1,         /* (N_D, 2)  f32 [q, qd]. Get/Set                                                        */
+  SIM_VIEW_DOF_ACTUATION = 2,     /* (N_D,)    f32 joint force / torque applied during the next step. Set                   */
+  SIM_VIEW_NET_CONTACT_FORCE = 3, /* (N_B, 3)  f32 net contact force on each (non-virtual) body, step average. Get          */
+  SIM_VIEW_CONTACT_PAIRS = 4,     /* (n_envs, C, 3) i32 (shape_a, shape_b or -1 = ground, slot) of the step's last substep; padding -1 */
+  SIM_VIEW_CONTACT_COUNT = 5,     /* (n_envs,) i32 number of valid rows in CONTACT_PAIRS                                     */
+  SIM_VIEW_SIGNATURE = 6,         /* (n_envs,) u32 FNV-1a of the step's constraint sets (SIM_FLAG_SIGNATURE)                */
+  SIM_VIEW_STATUS = 7,            /* (n_envs,) i32 per-env status bits: 1 non-finite state, 2 solver pivot failure           */
+  SIM_VIEW_IMPULSE_CACHE = 8      /* (n_envs, K) f32 warm-start impulses (solver state carried between substeps and steps)   */
+};
+enum { SIM_DTYPE_F32 = 0, SIM_DTYPE_I32 = 1, SIM_DTYPE_U32 = 2 };
+typedef struct {
+  void* data;          /* device pointer owned by the library */
+  int32_t ndim;
+  int64_t shape[3];
+  int64_t strides[3];  /* in elements */
+  int32_t dtype;       /* SIM_DTYPE_* */
+  int32_t device;      /* CUDA device ordinal */
+} sim_view;
+
+typedef struct sim_s* sim_handle;
+
+/* Create a simulation of n_envs environments. Env e consists of actors_per_env actors whose model
+ * indices are env_actor_model[e*actors_per_env + a] (host array). Actor roots are numbered
+ * env-major in the root tensor (N_A = n_envs * actors_per_env); joint DOFs and non-virtual bodies
+ * are numbered env-major, then actor, then link. cuda_stream is a cudaStream_t (NULL = legacy
+ * default stream). Initial state: every root at its origin with identity orientation, zero
+ * velocities and joint positions, zero actuation. Errors: INVALID_ARG, TOPOLOGY, CAPACITY, CUDA,
+ * NO_DEVICE; *out is set only on success. Environments never interact (paper: each environment
+ * is simulated without interaction with the others). */
+int sim_create(const sim_model_desc* models, int32_t n_models, const int32_t* env_actor_model,
+               int32_t actors_per_env, int32_t n_envs, const sim_params* params, void* cuda_stream,
+               sim_handle* out);
+
+/* Advance every environment by dt using `substeps` equal substeps (paper: control dt vs.
+ * simulation dt). Each substep: forward kinematics, articulated-body forward dynamics, ground
+ * contact and joint-limit rows, pos_iters + vel_iters TGS-style Gauss-Seidel iterations,
+ * integration. Reads DOF_ACTUATION, updates ROOT_STATE, DOF_STATE, NET_CONTACT_FORCE, the contact
+ * views, IMPULSE_CACHE and STATUS. Asynchronous on the handle's stream. Errors: HANDLE,
+ * INVALID_ARG (dt <= 0 or non-finite, substeps < 1), CUDA (launch failure). */
+int sim_step(sim_handle h, float dt, int32_t substeps);
+
+/* End-to-end step from host memory: copies host_actuation (N_D floats) into DOF_ACTUATION, runs
+ * sim_step, copies ROOT_STATE (N_A*13 floats) and DOF_STATE (N_D*2 floats) back into the host
+ * buffers (either output may be NULL) and synchronises the stream. Host buffers may be pageable
+ * or pinned; pinned memory is faster. Errors as sim_step. */
+int sim_step_host(sim_handle h, const float* host_actuation, float* host_root_out, float* host_dof_out,
+                  float dt, int32_t substeps);
+
+/* Describe one of the SIM_VIEW_* device tensors. Errors: HANDLE, INVALID_ARG. */
+int sim_get_view(sim_handle h, int32_t which, sim_view* out);
+
+/* Apply new root states to an indexed subset of actors (paper, Sec. "Physics State Tensors":
+ * set root or DOF states for all actors or a subset given by an index buffer). dev_src is a device
+ * array (n, 13) of root rows, dev_actor_idx a device array of n global actor indices (out-of-range
+ * indices are ignored). Teleports the roots without changing joint states, and clears the solver
+ * impulse cache of the touched environments. Errors: HANDLE, INVALID_ARG (n < 0), CUDA. */
+int sim_set_root_state_indexed(sim_handle h, const float* dev_src, const int32_t* dev_actor_idx, int32_t n);
+
+/* Apply new DOF states to an indexed subset of environments: dev_src is a device array of n rows,
+ * each holding one environment's joint DOF states (env_jdof x 2 floats, the env's own count;
+ * all envs of a batch with mixed sizes use the largest count as row stride), dev_env_idx a device
+ * array of n env indices (out-of-range ignored). Leaves root states unchanged and clears the
+ * touched environments' impulse caches. Errors: HANDLE, INVALID_ARG, CUDA. */
+int sim_set_dof_state_indexed(sim_handle h, const float* dev_src, const int32_t* dev_env_idx, int32_t n);
+
+/* Replace the stream used by later calls. Errors: HANDLE. */
+int sim_set_stream(sim_handle h, void* cuda_stream);
+
+/* Synchronise the stream and count envs whose status word is non-zero. Returns SIM_OK when all
+ * are clean, SIM_ERR_NONFINITE otherwise (*n_bad_envs receives the count). */
+int sim_sync_status(sim_handle h, int32_t* n_bad_envs);
+
+/* Sizes: out[0] = N_A, out[1] = N_D, out[2] = N_B, out[3] = contact pairs per env (C),
+ * out[4] = impulse-cache floats per env (K), out[5] = number of env types, out[6] = kernel
+ * launches per sim_step. Errors: HANDLE, INVALID_ARG. */
+int sim_get_sizes(sim_handle h, int64_t* out);
+
+/* Release every device buffer; the handle becomes invalid. Errors: HANDLE. */
+int sim_destroy(sim_handle h);
+
+/* Static string for a status code. */
+const char* sim_error_string(int code);
+
+/* Text of the last CUDA error seen by any call of this thread (empty if none). */
+const char* sim_last_error_message(void);
+
+/* FP32 FMA throughput probe (measurement of the CUDA-core roofline, which the step is bound by):
+ * runs a dependent-chain-free FMA loop on every SM for `iters` iterations and returns the achieved
+ * FP32 FLOP/s (2 per FMA) in *flops_per_s. Synchronous. Errors: INVALID_ARG, CUDA. */
+int sim_probe_fp32_peak(void* cuda_stream, int32_t iters, double* flops_per_s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ARTSIM_SIM_H */

@@ -67,6 +67,8 @@ def lib():
         L.oracle_step.restype = ctypes.c_int32
         L.oracle_step_flops.argtypes = [ctypes.c_void_p, D, D, D, D, ctypes.c_double, ctypes.c_int32]
         L.oracle_step_flops.restype = ctypes.c_double
+        L.oracle_step_f32.argtypes = [ctypes.c_void_p, D, D, D, D, ctypes.c_double, ctypes.c_int32, D]
+        L.oracle_step_f32.restype = ctypes.c_int32
         for fn in ("oracle_aba", "oracle_rnea", "oracle_momentum"):
             getattr(L, fn).argtypes = [ctypes.c_void_p, ctypes.c_int32, D, D, D, D]
             getattr(L, fn).restype = ctypes.c_int32
@@ -169,6 +171,17 @@ class Oracle:
         a = np.ascontiguousarray(act, dtype=np.float64).reshape(self.N_D)
         return float(lib().oracle_step_flops(self.h, _dp(root), _dp(dof) if self.N_D else None, _dp(self.cache),
                                              _dp(a) if self.N_D else None, float(dt), int(substeps)))
+
+    def step_f32(self, root, dof, act, dt=None, substeps=None):
+        """The identical step evaluated in single precision (conditioning probe; state and
+        self.cache updated in place like step). Returns the net contact forces."""
+        dt = self.w.dt if dt is None else dt
+        substeps = self.w.substeps if substeps is None else substeps
+        a = np.ascontiguousarray(act, dtype=np.float64).reshape(self.N_D)
+        nf = np.zeros((self.N_B, 3))
+        lib().oracle_step_f32(self.h, _dp(root), _dp(dof) if self.N_D else None, _dp(self.cache),
+                              _dp(a) if self.N_D else None, float(dt), int(substeps), _dp(nf) if self.N_B else None)
+        return nf
 
     def rk4(self, root, dof, act, dt, nsteps):
         a = np.ascontiguousarray(act, dtype=np.float64).reshape(self.N_D)

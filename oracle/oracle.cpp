@@ -946,6 +946,17 @@ double oracle_step_flops(void* h, double* root, double* dof, double* cache, cons
   return (double)OpCount::count();
 }
 
+// The same step evaluated in single precision (a conditioning probe for the parity tests: it
+// shows how far a plain FP32 evaluation of the identical algorithm lands from the FP64 result).
+int32_t oracle_step_f32(void* h, double* root, double* dof, double* cache, const double* act, double dt,
+                        int32_t substeps, double* net_force) {
+  const Oracle* O = (const Oracle*)h;
+  Outputs<float> o{cache, net_force, nullptr, nullptr, nullptr, nullptr};
+  int bad = 0;
+  for (int e = 0; e < O->n_envs; ++e) bad += env_step<float>(*O, e, root, dof, act, dt, substeps, o);
+  return bad;
+}
+
 // --- single-env helpers for the pins. root/dof point at this env's rows (actors_per_env x 13 and
 // its joint DOFs x 2); generalized vectors are env-level ([free root 6] + joints, actor by actor).
 static void env_kin(const Oracle& O, int env, const double* root, const double* dof, std::vector<ActorState<double>>& st,

@@ -27,6 +27,7 @@ using std::cos;
 using std::fabs;
 
 inline double val(double x) { return x; }
+inline double val(float x) { return (double)x; }
 template <class T> inline T tmax(const T& a, const T& b) { return (a < b) ? b : a; }
 template <class T> inline T tmin(const T& a, const T& b) { return (b < a) ? b : a; }
 

@@ -1,0 +1,673 @@
+// C ABI of the GB300 articulated-body step (declared in include/sim.h): model validation,
+// flattening of environments into env-type tables, device buffers, views, launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "../../include/sim.h"
+#include "sim_internal.h"
+#include "step_kernel.cuh"
+
+using namespace artsim;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+struct TypePlan {
+  EnvTypeTable tab;
+  SmemLayout lay;
+  std::vector<int> envs;
+  int G = 32;
+  int groups_per_block = 4;
+  size_t smem_bytes = 0;
+  int env_off = 0;  // offset into the concatenated env-id array
+};
+
+}  // namespace
+
+struct sim_s {
+  uint32_t magic = 0x5349414du;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int n_envs = 0, actors_per_env = 0;
+  int64_t N_A = 0, N_D = 0, N_B = 0;
+  int pair_stride = 0, cache_stride = 0, dof_row_stride = 0;
+  sim_params params{};
+  std::vector<TypePlan> types;
+  bool contiguous_single_type = false;
+  EnvTypeTable* d_types = nullptr;
+  int* d_env_ids = nullptr;
+  int* d_dof_base = nullptr;   // n_envs + 1
+  int* d_body_base = nullptr;  // n_envs + 1
+  float* root = nullptr;
+  float* dof = nullptr;
+  float* act = nullptr;
+  float* net_force = nullptr;
+  float* cache = nullptr;
+  int* pairs = nullptr;
+  int* n_pairs = nullptr;
+  unsigned* sig = nullptr;
+  int* status = nullptr;
+};
+
+namespace {
+
+std::mutex g_handles_mu;
+std::set<const sim_s*> g_handles;
+
+bool valid_handle(const sim_s* h) {
+  std::lock_guard<std::mutex> lk(g_handles_mu);
+  return h && g_handles.count(h) && h->magic == 0x5349414du;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  char buf[256];
+  snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
+  g_last_error = buf;
+  return SIM_ERR_CUDA;
+}
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t e__ = (call);                      \
+    if (e__ != cudaSuccess) return cuda_fail(e__, #call); \
+  } while (0)
+
+bool finite(float x) { return std::isfinite(x); }
+
+void quat_to_rot(const float* qin, float* R) {
+  double q[4] = {qin[0], qin[1], qin[2], qin[3]};
+  const double n = std::sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  for (double& x : q) x /= n;
+  const double x = q[0], y = q[1], z = q[2], w = q[3];
+  const double m[9] = {1 - 2 * (y * y + z * z), 2 * (x * y - z * w), 2 * (x * z + y * w),
+                       2 * (x * y + z * w), 1 - 2 * (x * x + z * z), 2 * (y * z - x * w),
+                       2 * (x * z - y * w), 2 * (y * z + x * w), 1 - 2 * (x * x + y * y)};
+  for (int k = 0; k < 9; ++k) R[k] = (float)m[k];
+}
+
+int validate_model(const sim_model_desc& m) {
+  if (m.n_links < 1 || m.n_links > kMaxLinks || m.n_shapes < 0 || m.n_shapes > kMaxShapes) return SIM_ERR_CAPACITY;
+  if (!m.parent || !m.joint_type || !m.joint_axis || !m.parent_pos || !m.parent_quat || !m.mass || !m.com ||
+      !m.inertia || !m.armature || !m.damping || !m.limit_lo || !m.limit_hi || !m.has_limit || !m.is_virtual)
+    return SIM_ERR_INVALID_ARG;
+  if (m.n_shapes > 0 && (!m.shape_link || !m.shape_type || !m.shape_size || !m.shape_pos || !m.shape_quat ||
+                         !m.shape_friction))
+    return SIM_ERR_INVALID_ARG;
+  if (m.parent[0] != -1) return SIM_ERR_TOPOLOGY;
+  if (m.joint_type[0] != SIM_JOINT_FREE && m.joint_type[0] != SIM_JOINT_FIXED) return SIM_ERR_TOPOLOGY;
+  for (int i = 0; i < m.n_links; ++i) {
+    if (i > 0) {
+      if (m.parent[i] < 0 || m.parent[i] >= i) return SIM_ERR_TOPOLOGY;
+      const int jt = m.joint_type[i];
+      if (jt != SIM_JOINT_FIXED && jt != SIM_JOINT_REVOLUTE && jt != SIM_JOINT_PRISMATIC) return SIM_ERR_TOPOLOGY;
+    }
+    for (int k = 0; k < 3; ++k)
+      if (!finite(m.joint_axis[3 * i + k]) || !finite(m.parent_pos[3 * i + k]) || !finite(m.com[3 * i + k]))
+        return SIM_ERR_INVALID_ARG;
+    double qn = 0;
+    for (int k = 0; k < 4; ++k) {
+      if (!finite(m.parent_quat[4 * i + k])) return SIM_ERR_INVALID_ARG;
+      qn += (double)m.parent_quat[4 * i + k] * m.parent_quat[4 * i + k];
+    }
+    if (qn < 1e-12) return SIM_ERR_INVALID_ARG;
+    if (!(m.mass[i] >= 0.f) || !finite(m.mass[i])) return SIM_ERR_INVALID_ARG;
+    if (i == 0 && m.joint_type[0] == SIM_JOINT_FREE && !(m.mass[0] > 0.f)) return SIM_ERR_INVALID_ARG;
+    const float* I = m.inertia + 6 * i;
+    for (int k = 0; k < 6; ++k)
+      if (!finite(I[k])) return SIM_ERR_INVALID_ARG;
+    // positive semi-definite: leading minors and diagonal non-negative (small tolerance)
+    const double a = I[0], b = I[1], c = I[2], xy = I[3], xz = I[4], yz = I[5];
+    const double tol = 1e-9 * (std::fabs(a) + std::fabs(b) + std::fabs(c) + 1e-12);
+    const double det = a * (b * c - yz * yz) - xy * (xy * c - yz * xz) + xz * (xy * yz - b * xz);
+    if (a < -tol || b < -tol || c < -tol || a * b - xy * xy < -tol * tol || det < -tol * tol * tol)
+      return SIM_ERR_INVALID_ARG;
+    if (i == 0 && m.joint_type[0] == SIM_JOINT_FREE && !(a > 0 && b > 0 && c > 0)) return SIM_ERR_INVALID_ARG;
+    if (!(m.armature[i] >= 0.f) || !(m.damping[i] >= 0.f) || !finite(m.armature[i]) || !finite(m.damping[i]))
+      return SIM_ERR_INVALID_ARG;
+    const int jt = m.joint_type[i];
+    if (i > 0 && (jt == SIM_JOINT_REVOLUTE || jt == SIM_JOINT_PRISMATIC)) {
+      const float* ax = m.joint_axis + 3 * i;
+      const double an = std::sqrt((double)ax[0] * ax[0] + (double)ax[1] * ax[1] + (double)ax[2] * ax[2]);
+      if (an < 1e-6) return SIM_ERR_INVALID_ARG;
+      if (m.has_limit[i] && (!finite(m.limit_lo[i]) || !finite(m.limit_hi[i]) || m.limit_lo[i] > m.limit_hi[i]))
+        return SIM_ERR_INVALID_ARG;
+    }
+    if (m.has_limit[i] > 1 || m.is_virtual[i] > 1) return SIM_ERR_INVALID_ARG;
+  }
+  for (int s = 0; s < m.n_shapes; ++s) {
+    const int li = m.shape_link[s];
+    if (li < 0 || li >= m.n_links || m.is_virtual[li]) return SIM_ERR_INVALID_ARG;
+    const int st = m.shape_type[s];
+    if (st != SIM_SHAPE_SPHERE && st != SIM_SHAPE_CAPSULE && st != SIM_SHAPE_BOX) return SIM_ERR_INVALID_ARG;
+    const float* sz = m.shape_size + 3 * s;
+    const int need = (st == SIM_SHAPE_SPHERE) ? 1 : (st == SIM_SHAPE_CAPSULE ? 2 : 3);
+    for (int k = 0; k < need; ++k)
+      if (!(sz[k] > 0.f) || !finite(sz[k])) return SIM_ERR_INVALID_ARG;
+    if (!(m.shape_friction[s] >= 0.f) || !finite(m.shape_friction[s])) return SIM_ERR_INVALID_ARG;
+    for (int k = 0; k < 3; ++k)
+      if (!finite(m.shape_pos[3 * s + k]) || !finite(sz[k])) return SIM_ERR_INVALID_ARG;
+    double qn = 0;
+    for (int k = 0; k < 4; ++k) {
+      if (!finite(m.shape_quat[4 * s + k])) return SIM_ERR_INVALID_ARG;
+      qn += (double)m.shape_quat[4 * s + k] * m.shape_quat[4 * s + k];
+    }
+    if (qn < 1e-12) return SIM_ERR_INVALID_ARG;
+  }
+  return SIM_OK;
+}
+
+int ndof_of(const sim_model_desc& m, int i) {
+  const int jt = m.joint_type[i];
+  if (i == 0) return jt == SIM_JOINT_FREE ? 6 : 0;
+  return (jt == SIM_JOINT_REVOLUTE || jt == SIM_JOINT_PRISMATIC) ? 1 : 0;
+}
+
+// Flatten the actors of one environment type into a forest of links.
+int build_type(const sim_model_desc* models, const std::vector<int>& actor_models, const sim_params& p,
+               EnvTypeTable& T) {
+  std::memset(&T, 0, sizeof(T));
+  int L = 0, n = 0, nj = 0, ns = 0, nc = 0, nb = 0;
+  for (int k = 0; k < kMaxLinks; ++k) { T.first_child[k] = -1; T.next_sibling[k] = -1; T.gdof[k] = -1; T.jdof[k] = -1; T.body[k] = -1; }
+  if ((int)actor_models.size() > kMaxActors) return SIM_ERR_CAPACITY;
+  for (size_t a = 0; a < actor_models.size(); ++a) {
+    const sim_model_desc& m = models[actor_models[a]];
+    const int base = L;
+    if (L + m.n_links > kMaxLinks || ns + m.n_shapes > kMaxShapes) return SIM_ERR_CAPACITY;
+    for (int i = 0; i < m.n_links; ++i) {
+      const int l = base + i;
+      const int nd = ndof_of(m, i);
+      if (n + nd > kMaxGen) return SIM_ERR_CAPACITY;
+      T.parent[l] = (i == 0) ? -1 : base + m.parent[i];
+      T.jtype[l] = m.joint_type[i];
+      T.depth[l] = (i == 0) ? 0 : T.depth[T.parent[l]] + 1;
+      T.actor[l] = (int)a;
+      T.aroot[l] = base;
+      T.gdof[l] = nd ? n : -1;
+      if (nd == 6) {
+        for (int k = 0; k < 6; ++k) { T.dof_link[n + k] = l; T.dof_comp[n + k] = k; }
+      } else if (nd == 1) {
+        T.dof_link[n] = l;
+        T.dof_comp[n] = -1;
+        T.jdof[l] = nj++;
+      }
+      n += nd;
+      double an = 1.0;
+      const float* ax = m.joint_axis + 3 * i;
+      if (nd == 1) an = std::sqrt((double)ax[0] * ax[0] + (double)ax[1] * ax[1] + (double)ax[2] * ax[2]);
+      for (int k = 0; k < 3; ++k) {
+        T.axis[k][l] = nd == 1 ? (float)(ax[k] / an) : 0.f;
+        T.ppos[k][l] = m.parent_pos[3 * i + k];
+        T.com[k][l] = m.com[3 * i + k];
+      }
+      float R[9];
+      quat_to_rot(m.parent_quat + 4 * i, R);
+      for (int k = 0; k < 9; ++k) T.prot[k][l] = R[k];
+      T.mass[l] = m.mass[i];
+      for (int k = 0; k < 6; ++k) T.inertia[k][l] = m.inertia[6 * i + k];
+      T.armature[l] = m.armature[i];
+      T.damping[l] = m.damping[i];
+      T.has_limit[l] = (nd == 1 && m.has_limit[i]) ? 1 : 0;
+      T.lo[l] = m.limit_lo[i];
+      T.hi[l] = m.limit_hi[i];
+      // both rows of a joint can be active only if its range is below twice the margin; the
+      // slack covers rounding of the two float comparisons near that boundary
+      T.lim_slots[l] = T.has_limit[l] ? ((T.hi[l] - T.lo[l] < 2.f * p.limit_margin + 1e-4f) ? 2 : 1) : 0;
+      T.body[l] = m.is_virtual[i] ? -1 : nb++;
+    }
+    for (int s = 0; s < m.n_shapes; ++s) {
+      const int e = ns + s;
+      T.shape_link[e] = base + m.shape_link[s];
+      T.shape_type[e] = m.shape_type[s];
+      T.cand_off[e] = nc;
+      nc += (m.shape_type[s] == SIM_SHAPE_SPHERE) ? 1 : (m.shape_type[s] == SIM_SHAPE_CAPSULE ? 2 : 8);
+      for (int k = 0; k < 3; ++k) {
+        T.shape_size[k][e] = m.shape_size[3 * s + k];
+        T.shape_pos[k][e] = m.shape_pos[3 * s + k];
+      }
+      float R[9];
+      quat_to_rot(m.shape_quat + 4 * s, R);
+      for (int k = 0; k < 9; ++k) T.shape_rot[k][e] = R[k];
+      T.shape_mu[e] = std::max(m.shape_friction[s], p.ground_friction);
+    }
+    L += m.n_links;
+    ns += m.n_shapes;
+  }
+  if (nc > kMaxCand) return SIM_ERR_CAPACITY;
+  // children lists (ascending), ancestor DOF masks, depth
+  int maxd = 0;
+  for (int l = L - 1; l >= 0; --l) {
+    const int pa = T.parent[l];
+    if (pa >= 0) { T.next_sibling[l] = T.first_child[pa]; T.first_child[pa] = l; }
+  }
+  int lim_cap = 0;
+  for (int l = 0; l < L; ++l) {
+    unsigned mask = 0u;
+    for (int a = l; a >= 0; a = T.parent[a]) {
+      const int nd = (T.parent[a] < 0) ? (T.jtype[a] == kFree ? 6 : 0)
+                                        : ((T.jtype[a] == kRevolute || T.jtype[a] == kPrismatic) ? 1 : 0);
+      for (int k = 0; k < nd; ++k) mask |= 1u << (T.gdof[a] + k);
+    }
+    T.anc[l] = mask;
+    maxd = std::max(maxd, T.depth[l]);
+    lim_cap += T.lim_slots[l];
+  }
+  T.n_links = L;
+  T.n_gen = n;
+  T.n_jdof = nj;
+  T.n_shapes = ns;
+  T.n_cand = nc;
+  T.n_body = nb;
+  T.n_actors = (int)actor_models.size();
+  T.max_depth = maxd;
+  T.lim_cap = lim_cap;
+  T.row_cap = lim_cap + 3 * nc;
+  T.cache_len = 3 * nc + 2 * nj;
+  const int need = std::max(std::max(L, n), std::max(ns, 1));
+  T.group = need <= 8 ? 8 : (need <= 16 ? 16 : 32);
+  return SIM_OK;
+}
+
+SmemLayout make_layout(const EnvTypeTable& T) {
+  SmemLayout Ly{};
+  const int n = std::max(T.n_gen, 1);
+  const int L = T.n_links;
+  Ly.rcap = std::max(T.row_cap, 1);
+  Ly.RS = Ly.rcap | 1;
+  Ly.MS = n | 1;
+  Ly.ccap = std::max(T.n_cand, 1);
+  int o = 0;
+  const int phase = std::max(L * kLinkWords, 2 * n * Ly.RS);
+  Ly.link = o;
+  Ly.J = o;
+  Ly.W = o + n * Ly.RS;
+  o += phase;
+  Ly.S = o; o += 6 * L;
+  Ly.M = o; o += n * Ly.MS;
+  Ly.vec = o; o += 6 * n;
+  Ly.con = o; o += kConWords * Ly.ccap;
+  Ly.rowh = o; o += kRowWords * Ly.rcap;
+  Ly.cache = o; o += std::max(T.cache_len, 1);
+  Ly.frc = o; o += 3 * L;
+  Ly.misc = o; o += 8;
+  Ly.total = (o + 3) & ~3;
+  return Ly;
+}
+
+template <int G> void set_smem_attr(size_t bytes) {
+  cudaFuncSetAttribute(step_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <int G> cudaError_t launch_G(const StepArgs& a, int n_envs, int gpb, size_t smem, cudaStream_t st) {
+  const int blocks = (n_envs + gpb - 1) / gpb;
+  step_kernel<G><<<blocks, gpb * G, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+void free_all(sim_s* h) {
+  void* ptrs[] = {h->d_types, h->d_env_ids, h->d_dof_base, h->d_body_base, h->root, h->dof, h->act, h->net_force,
+                  h->cache, h->pairs, h->n_pairs, h->sig, h->status};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+}
+
+__global__ void set_root_kernel(float* root, const float* src, const int* idx, int n, int64_t N_A, int A,
+                                float* cache, int cache_stride) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int a = idx[i];
+  if (a < 0 || a >= N_A) return;
+  for (int k = 0; k < 13; ++k) root[(size_t)a * 13 + k] = src[(size_t)i * 13 + k];
+  const int env = a / A;
+  for (int k = 0; k < cache_stride; ++k) cache[(size_t)env * cache_stride + k] = 0.f;
+}
+
+__global__ void set_dof_kernel(float* dof, const float* src, const int* idx, int n, int n_envs, const int* dof_base,
+                               int row_stride, float* cache, int cache_stride) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int e = idx[i];
+  if (e < 0 || e >= n_envs) return;
+  const int b0 = dof_base[e], b1 = dof_base[e + 1];
+  for (int k = 0; k < 2 * (b1 - b0); ++k) dof[(size_t)b0 * 2 + k] = src[(size_t)i * row_stride + k];
+  for (int k = 0; k < cache_stride; ++k) cache[(size_t)e * cache_stride + k] = 0.f;
+}
+
+__global__ void fma_probe_kernel(float* out, int iters, float seed) {
+  float a0 = seed + threadIdx.x, a1 = a0 + 1.f, a2 = a0 + 2.f, a3 = a0 + 3.f;
+  float a4 = a0 + 4.f, a5 = a0 + 5.f, a6 = a0 + 6.f, a7 = a0 + 7.f;
+  const float b = 0.999999f, c = 1e-7f;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      a0 = fmaf(a0, b, c); a1 = fmaf(a1, b, c); a2 = fmaf(a2, b, c); a3 = fmaf(a3, b, c);
+      a4 = fmaf(a4, b, c); a5 = fmaf(a5, b, c); a6 = fmaf(a6, b, c); a7 = fmaf(a7, b, c);
+    }
+  }
+  const float s = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
+  if (s == 123.456f) out[blockIdx.x] = s;  // keeps the loop alive
+}
+
+}  // namespace
+
+// ================================================================================================
+extern "C" {
+
+const char* sim_error_string(int code) {
+  switch (code) {
+    case SIM_OK: return "ok";
+    case SIM_ERR_INVALID_ARG: return "invalid argument";
+    case SIM_ERR_TOPOLOGY: return "invalid articulation topology";
+    case SIM_ERR_CUDA: return "CUDA error";
+    case SIM_ERR_CAPACITY: return "environment exceeds kernel capacity";
+    case SIM_ERR_TIMEOUT: return "device wait timed out";
+    case SIM_ERR_NONFINITE: return "non-finite state in some environment";
+    case SIM_ERR_HANDLE: return "invalid handle";
+    case SIM_ERR_NO_DEVICE: return "no CUDA device";
+    default: return "unknown error";
+  }
+}
+
+const char* sim_last_error_message(void) { return g_last_error.c_str(); }
+
+int sim_create(const sim_model_desc* models, int32_t n_models, const int32_t* env_actor_model, int32_t actors_per_env,
+               int32_t n_envs, const sim_params* params, void* cuda_stream, sim_handle* out) {
+  if (!models || n_models < 1 || !env_actor_model || actors_per_env < 1 || actors_per_env > kMaxActors ||
+      n_envs < 1 || !params || !out)
+    return SIM_ERR_INVALID_ARG;
+  const sim_params& p = *params;
+  for (int k = 0; k < 3; ++k)
+    if (!finite(p.gravity[k])) return SIM_ERR_INVALID_ARG;
+  if (p.pos_iters < 1 || p.vel_iters < 0 || !finite(p.contact_offset) || !finite(p.limit_margin) ||
+      !(p.bias_coef >= 0.f) || !(p.max_depen_vel >= 0.f) || !(p.ground_friction >= 0.f) ||
+      !finite(p.max_depen_vel) || !finite(p.ground_friction) || !finite(p.bias_coef))
+    return SIM_ERR_INVALID_ARG;
+  for (int m = 0; m < n_models; ++m) {
+    const int rc = validate_model(models[m]);
+    if (rc != SIM_OK) return rc;
+  }
+  for (int64_t i = 0; i < (int64_t)n_envs * actors_per_env; ++i)
+    if (env_actor_model[i] < 0 || env_actor_model[i] >= n_models) return SIM_ERR_INVALID_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+    cudaGetLastError();
+    return SIM_ERR_NO_DEVICE;
+  }
+
+  sim_s* h = new sim_s();
+  h->stream = (cudaStream_t)cuda_stream;
+  h->n_envs = n_envs;
+  h->actors_per_env = actors_per_env;
+  h->params = p;
+  cudaGetDevice(&h->device);
+  // env types
+  std::map<std::vector<int>, int> type_of;
+  std::vector<int> env_type(n_envs);
+  for (int e = 0; e < n_envs; ++e) {
+    std::vector<int> key(env_actor_model + (int64_t)e * actors_per_env, env_actor_model + (int64_t)(e + 1) * actors_per_env);
+    auto it = type_of.find(key);
+    if (it == type_of.end()) {
+      TypePlan tp;
+      const int rc = build_type(models, key, p, tp.tab);
+      if (rc != SIM_OK) { delete h; return rc; }
+      tp.lay = make_layout(tp.tab);
+      tp.G = tp.tab.group;
+      tp.groups_per_block = 128 / tp.G;
+      tp.smem_bytes = (size_t)tp.groups_per_block * tp.lay.total * 4;
+      if (tp.smem_bytes > 220 * 1024) {
+        tp.groups_per_block = std::max(1, (int)((220 * 1024) / ((size_t)tp.lay.total * 4)));
+        while (tp.groups_per_block > 1 && (tp.groups_per_block * tp.G) % 32) --tp.groups_per_block;
+        tp.smem_bytes = (size_t)tp.groups_per_block * tp.lay.total * 4;
+        if (tp.smem_bytes > 220 * 1024 || (tp.groups_per_block * tp.G) % 32) { delete h; return SIM_ERR_CAPACITY; }
+      }
+      it = type_of.emplace(key, (int)h->types.size()).first;
+      h->types.push_back(tp);
+    }
+    env_type[e] = it->second;
+    h->types[it->second].envs.push_back(e);
+  }
+  // per-env bases
+  std::vector<int> dof_base(n_envs + 1, 0), body_base(n_envs + 1, 0);
+  int max_cache = 1, max_pairs = 1, max_jdof = 0;
+  for (int e = 0; e < n_envs; ++e) {
+    const EnvTypeTable& T = h->types[env_type[e]].tab;
+    dof_base[e + 1] = dof_base[e] + T.n_jdof;
+    body_base[e + 1] = body_base[e] + T.n_body;
+    max_cache = std::max(max_cache, T.cache_len);
+    max_pairs = std::max(max_pairs, T.n_cand);
+    max_jdof = std::max(max_jdof, T.n_jdof);
+  }
+  h->N_A = (int64_t)n_envs * actors_per_env;
+  h->N_D = dof_base[n_envs];
+  h->N_B = body_base[n_envs];
+  h->cache_stride = max_cache;
+  h->pair_stride = max_pairs;
+  h->dof_row_stride = 2 * max_jdof;
+  h->contiguous_single_type = h->types.size() == 1;
+  std::vector<int> env_ids;
+  for (auto& tp : h->types) {
+    tp.env_off = (int)env_ids.size();
+    env_ids.insert(env_ids.end(), tp.envs.begin(), tp.envs.end());
+  }
+  std::vector<EnvTypeTable> tabs;
+  for (auto& tp : h->types) tabs.push_back(tp.tab);
+
+  auto fail = [&](cudaError_t e, const char* what) {
+    cuda_fail(e, what);
+    free_all(h);
+    delete h;
+    return SIM_ERR_CUDA;
+  };
+#define CKC(call)                                    \
+  do {                                               \
+    cudaError_t e__ = (call);                        \
+    if (e__ != cudaSuccess) return fail(e__, #call); \
+  } while (0)
+  CKC(cudaMalloc(&h->d_types, sizeof(EnvTypeTable) * tabs.size()));
+  CKC(cudaMalloc(&h->d_env_ids, sizeof(int) * env_ids.size()));
+  CKC(cudaMalloc(&h->d_dof_base, sizeof(int) * (n_envs + 1)));
+  CKC(cudaMalloc(&h->d_body_base, sizeof(int) * (n_envs + 1)));
+  CKC(cudaMalloc(&h->root, sizeof(float) * h->N_A * 13));
+  CKC(cudaMalloc(&h->dof, sizeof(float) * std::max<int64_t>(h->N_D * 2, 1)));
+  CKC(cudaMalloc(&h->act, sizeof(float) * std::max<int64_t>(h->N_D, 1)));
+  CKC(cudaMalloc(&h->net_force, sizeof(float) * std::max<int64_t>(h->N_B * 3, 1)));
+  CKC(cudaMalloc(&h->cache, sizeof(float) * (size_t)n_envs * h->cache_stride));
+  CKC(cudaMalloc(&h->pairs, sizeof(int) * (size_t)n_envs * h->pair_stride * 3));
+  CKC(cudaMalloc(&h->n_pairs, sizeof(int) * n_envs));
+  CKC(cudaMalloc(&h->sig, sizeof(unsigned) * n_envs));
+  CKC(cudaMalloc(&h->status, sizeof(int) * n_envs));
+  CKC(cudaMemcpy(h->d_types, tabs.data(), sizeof(EnvTypeTable) * tabs.size(), cudaMemcpyHostToDevice));
+  CKC(cudaMemcpy(h->d_env_ids, env_ids.data(), sizeof(int) * env_ids.size(), cudaMemcpyHostToDevice));
+  CKC(cudaMemcpy(h->d_dof_base, dof_base.data(), sizeof(int) * (n_envs + 1), cudaMemcpyHostToDevice));
+  CKC(cudaMemcpy(h->d_body_base, body_base.data(), sizeof(int) * (n_envs + 1), cudaMemcpyHostToDevice));
+  std::vector<float> root0((size_t)h->N_A * 13, 0.f);
+  for (int64_t a = 0; a < h->N_A; ++a) root0[a * 13 + 6] = 1.f;
+  CKC(cudaMemcpy(h->root, root0.data(), sizeof(float) * root0.size(), cudaMemcpyHostToDevice));
+  CKC(cudaMemset(h->dof, 0, sizeof(float) * std::max<int64_t>(h->N_D * 2, 1)));
+  CKC(cudaMemset(h->act, 0, sizeof(float) * std::max<int64_t>(h->N_D, 1)));
+  CKC(cudaMemset(h->net_force, 0, sizeof(float) * std::max<int64_t>(h->N_B * 3, 1)));
+  CKC(cudaMemset(h->cache, 0, sizeof(float) * (size_t)n_envs * h->cache_stride));
+  CKC(cudaMemset(h->pairs, 0xff, sizeof(int) * (size_t)n_envs * h->pair_stride * 3));
+  CKC(cudaMemset(h->n_pairs, 0, sizeof(int) * n_envs));
+  CKC(cudaMemset(h->sig, 0, sizeof(unsigned) * n_envs));
+  CKC(cudaMemset(h->status, 0, sizeof(int) * n_envs));
+  for (auto& tp : h->types) {
+    if (tp.G == 8) set_smem_attr<8>(tp.smem_bytes);
+    else if (tp.G == 16) set_smem_attr<16>(tp.smem_bytes);
+    else set_smem_attr<32>(tp.smem_bytes);
+  }
+  CKC(cudaGetLastError());
+#undef CKC
+  {
+    std::lock_guard<std::mutex> lk(g_handles_mu);
+    g_handles.insert(h);
+  }
+  *out = h;
+  return SIM_OK;
+}
+
+int sim_step(sim_handle h, float dt, int32_t substeps) {
+  if (!valid_handle(h)) return SIM_ERR_HANDLE;
+  if (!(dt > 0.f) || !finite(dt) || substeps < 1) return SIM_ERR_INVALID_ARG;
+  const sim_params& p = h->params;
+  for (size_t t = 0; t < h->types.size(); ++t) {
+    const TypePlan& tp = h->types[t];
+    StepArgs a{};
+    a.type = h->d_types + t;
+    a.env_ids = h->contiguous_single_type ? nullptr : h->d_env_ids + tp.env_off;
+    a.env_first = 0;
+    a.n_launch_envs = (int)tp.envs.size();
+    a.root = h->root; a.dof = h->dof; a.act = h->act; a.net_force = h->net_force; a.cache = h->cache;
+    a.pairs = h->pairs; a.n_pairs = h->n_pairs; a.sig = h->sig; a.status = h->status;
+    a.env_dof_base = h->d_dof_base; a.env_body_base = h->d_body_base;
+    a.actors_per_env = h->actors_per_env; a.cache_stride = h->cache_stride; a.pair_stride = h->pair_stride;
+    a.dt = dt; a.h = dt / (float)substeps; a.substeps = substeps;
+    a.gx = p.gravity[0]; a.gy = p.gravity[1]; a.gz = p.gravity[2];
+    a.pos_iters = p.pos_iters; a.vel_iters = p.vel_iters;
+    a.contact_offset = p.contact_offset; a.limit_margin = p.limit_margin;
+    a.bias_coef = p.bias_coef; a.max_depen_vel = p.max_depen_vel; a.flags = p.flags;
+    a.lay = tp.lay;
+    cudaError_t e;
+    if (tp.G == 8) e = launch_G<8>(a, a.n_launch_envs, tp.groups_per_block, tp.smem_bytes, h->stream);
+    else if (tp.G == 16) e = launch_G<16>(a, a.n_launch_envs, tp.groups_per_block, tp.smem_bytes, h->stream);
+    else e = launch_G<32>(a, a.n_launch_envs, tp.groups_per_block, tp.smem_bytes, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "step_kernel launch");
+  }
+  return SIM_OK;
+}
+
+int sim_step_host(sim_handle h, const float* host_actuation, float* host_root_out, float* host_dof_out, float dt,
+                  int32_t substeps) {
+  if (!valid_handle(h)) return SIM_ERR_HANDLE;
+  if (!host_actuation && h->N_D > 0) return SIM_ERR_INVALID_ARG;
+  if (h->N_D > 0) CK(cudaMemcpyAsync(h->act, host_actuation, sizeof(float) * h->N_D, cudaMemcpyHostToDevice, h->stream));
+  const int rc = sim_step(h, dt, substeps);
+  if (rc != SIM_OK) return rc;
+  if (host_root_out)
+    CK(cudaMemcpyAsync(host_root_out, h->root, sizeof(float) * h->N_A * 13, cudaMemcpyDeviceToHost, h->stream));
+  if (host_dof_out && h->N_D > 0)
+    CK(cudaMemcpyAsync(host_dof_out, h->dof, sizeof(float) * h->N_D * 2, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return SIM_OK;
+}
+
+int sim_get_view(sim_handle h, int32_t which, sim_view* out) {
+  if (!valid_handle(h)) return SIM_ERR_HANDLE;
+  if (!out) return SIM_ERR_INVALID_ARG;
+  sim_view v{};
+  v.device = h->device;
+  auto set = [&](void* d, int nd, int64_t s0, int64_t s1, int64_t s2, int dt) {
+    v.data = d; v.ndim = nd; v.shape[0] = s0; v.shape[1] = s1; v.shape[2] = s2; v.dtype = dt;
+    if (nd == 1) { v.strides[0] = 1; }
+    if (nd == 2) { v.strides[0] = s1; v.strides[1] = 1; }
+    if (nd == 3) { v.strides[0] = s1 * s2; v.strides[1] = s2; v.strides[2] = 1; }
+  };
+  switch (which) {
+    case SIM_VIEW_ROOT_STATE: set(h->root, 2, h->N_A, 13, 0, SIM_DTYPE_F32); break;
+    case SIM_VIEW_DOF_STATE: set(h->dof, 2, h->N_D, 2, 0, SIM_DTYPE_F32); break;
+    case SIM_VIEW_DOF_ACTUATION: set(h->act, 1, h->N_D, 0, 0, SIM_DTYPE_F32); break;
+    case SIM_VIEW_NET_CONTACT_FORCE: set(h->net_force, 2, h->N_B, 3, 0, SIM_DTYPE_F32); break;
+    case SIM_VIEW_CONTACT_PAIRS: set(h->pairs, 3, h->n_envs, h->pair_stride, 3, SIM_DTYPE_I32); break;
+    case SIM_VIEW_CONTACT_COUNT: set(h->n_pairs, 1, h->n_envs, 0, 0, SIM_DTYPE_I32); break;
+    case SIM_VIEW_SIGNATURE: set(h->sig, 1, h->n_envs, 0, 0, SIM_DTYPE_U32); break;
+    case SIM_VIEW_STATUS: set(h->status, 1, h->n_envs, 0, 0, SIM_DTYPE_I32); break;
+    case SIM_VIEW_IMPULSE_CACHE: set(h->cache, 2, h->n_envs, h->cache_stride, 0, SIM_DTYPE_F32); break;
+    default: return SIM_ERR_INVALID_ARG;
+  }
+  *out = v;
+  return SIM_OK;
+}
+
+int sim_set_root_state_indexed(sim_handle h, const float* dev_src, const int32_t* dev_actor_idx, int32_t n) {
+  if (!valid_handle(h)) return SIM_ERR_HANDLE;
+  if (n < 0 || (n > 0 && (!dev_src || !dev_actor_idx))) return SIM_ERR_INVALID_ARG;
+  if (n == 0) return SIM_OK;
+  set_root_kernel<<<(n + 127) / 128, 128, 0, h->stream>>>(h->root, dev_src, dev_actor_idx, n, h->N_A,
+                                                          h->actors_per_env, h->cache, h->cache_stride);
+  CK(cudaGetLastError());
+  return SIM_OK;
+}
+
+int sim_set_dof_state_indexed(sim_handle h, const float* dev_src, const int32_t* dev_env_idx, int32_t n) {
+  if (!valid_handle(h)) return SIM_ERR_HANDLE;
+  if (n < 0 || (n > 0 && (!dev_src || !dev_env_idx))) return SIM_ERR_INVALID_ARG;
+  if (n == 0) return SIM_OK;
+  set_dof_kernel<<<(n + 127) / 128, 128, 0, h->stream>>>(h->dof, dev_src, dev_env_idx, n, h->n_envs, h->d_dof_base,
+                                                         std::max(h->dof_row_stride, 1), h->cache, h->cache_stride);
+  CK(cudaGetLastError());
+  return SIM_OK;
+}
+
+int sim_set_stream(sim_handle h, void* cuda_stream) {
+  if (!valid_handle(h)) return SIM_ERR_HANDLE;
+  h->stream = (cudaStream_t)cuda_stream;
+  return SIM_OK;
+}
+
+int sim_sync_status(sim_handle h, int32_t* n_bad_envs) {
+  if (!valid_handle(h)) return SIM_ERR_HANDLE;
+  std::vector<int> st(h->n_envs);
+  CK(cudaMemcpyAsync(st.data(), h->status, sizeof(int) * h->n_envs, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  int bad = 0;
+  for (int s : st) bad += (s != 0);
+  if (n_bad_envs) *n_bad_envs = bad;
+  return bad ? SIM_ERR_NONFINITE : SIM_OK;
+}
+
+int sim_get_sizes(sim_handle h, int64_t* out) {
+  if (!valid_handle(h)) return SIM_ERR_HANDLE;
+  if (!out) return SIM_ERR_INVALID_ARG;
+  out[0] = h->N_A; out[1] = h->N_D; out[2] = h->N_B; out[3] = h->pair_stride; out[4] = h->cache_stride;
+  out[5] = (int64_t)h->types.size(); out[6] = (int64_t)h->types.size();
+  return SIM_OK;
+}
+
+int sim_destroy(sim_handle h) {
+  {
+    std::lock_guard<std::mutex> lk(g_handles_mu);
+    if (!h || !g_handles.count(h)) return SIM_ERR_HANDLE;
+    g_handles.erase(h);
+  }
+  cudaStreamSynchronize(h->stream);
+  free_all(h);
+  h->magic = 0;
+  delete h;
+  return SIM_OK;
+}
+
+int sim_probe_fp32_peak(void* cuda_stream, int32_t iters, double* flops_per_s) {
+  if (iters < 1 || !flops_per_s) return SIM_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  int dev = 0, sms = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  float* out = nullptr;
+  const int blocks = sms * 8, threads = 256;
+  CK(cudaMalloc(&out, sizeof(float) * blocks));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  fma_probe_kernel<<<blocks, threads, 0, st>>>(out, std::max(1, iters / 10), 1.f);  // warm-up
+  CK(cudaEventRecord(e0, st));
+  fma_probe_kernel<<<blocks, threads, 0, st>>>(out, iters, 1.f);
+  CK(cudaEventRecord(e1, st));
+  CK(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  *flops_per_s = 2.0 * 8.0 * 16.0 * (double)iters * blocks * threads / (ms * 1e-3);
+  return SIM_OK;
+}
+
+}  // extern "C"

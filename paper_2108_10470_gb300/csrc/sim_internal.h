@@ -1,0 +1,110 @@
+// Internal data layout of the GB300 articulated-body step: per-env-type model tables, the
+// per-environment shared-memory arena, and the step kernel's argument block. Shared by the
+// host-side C ABI (sim_api.cu) and the kernels (step_kernel.cuh); not part of the public ABI.
+#pragma once
+#include <cstdint>
+
+namespace artsim {
+
+// Kernel limits (one environment is handled by one group of G <= 32 lanes: a lane per link, per
+// generalized DOF, per shape).
+constexpr int kMaxLinks = 32;   // links per environment (all actors)
+constexpr int kMaxGen = 32;     // generalized DOFs per environment (6 per floating root + joints)
+constexpr int kMaxShapes = 32;  // shapes per environment
+constexpr int kMaxCand = 96;    // contact candidate points per environment
+constexpr int kMaxActors = 8;   // actors per environment
+
+enum JointType : int { kFree = 0, kFixed = 1, kRevolute = 2, kPrismatic = 3 };
+enum ShapeType : int { kSphere = 0, kCapsule = 1, kBox = 2 };
+enum RowKind : int { kRowLimit = 0, kRowNormal = 1, kRowFriction = 2 };
+
+// One environment type = one sequence of actor models, flattened into a forest of links.
+// Per-link arrays are indexed by the env-local link number (actors in order, links in order, so
+// parents precede children and generalized DOFs increase along every root-to-leaf path).
+struct EnvTypeTable {
+  int n_links, n_gen, n_jdof, n_shapes, n_cand, n_body, n_actors, max_depth;
+  int lim_cap, row_cap, cache_len, group;  // group = lanes per environment (8, 16 or 32)
+  // per link
+  int parent[kMaxLinks];        // env-local parent, -1 for an actor root
+  int jtype[kMaxLinks];
+  int depth[kMaxLinks];         // 0 for actor roots
+  int first_child[kMaxLinks];   // children in ascending order: first_child, next_sibling chain
+  int next_sibling[kMaxLinks];
+  int gdof[kMaxLinks];          // first generalized DOF of the link's joint (-1: none)
+  int jdof[kMaxLinks];          // env joint-DOF index (DOF state row within the env) or -1
+  int body[kMaxLinks];          // env body index (net-contact-force row) or -1 (virtual)
+  int actor[kMaxLinks];
+  int aroot[kMaxLinks];         // link index of the actor's root
+  unsigned anc[kMaxLinks];      // bit g set iff generalized DOF g belongs to an ancestor-or-self
+  int lim_slots[kMaxLinks];     // number of limit rows this joint can produce (0, 1 or 2)
+  float axis[3][kMaxLinks];     // joint axis in the joint frame
+  float ppos[3][kMaxLinks];     // joint frame origin in the parent frame
+  float prot[9][kMaxLinks];     // joint frame rotation (row-major, joint -> parent)
+  float mass[kMaxLinks];
+  float com[3][kMaxLinks];
+  float inertia[6][kMaxLinks];  // xx yy zz xy xz yz about the COM, link axes
+  float armature[kMaxLinks], damping[kMaxLinks], lo[kMaxLinks], hi[kMaxLinks];
+  int has_limit[kMaxLinks];
+  // per shape
+  int shape_link[kMaxShapes], shape_type[kMaxShapes], cand_off[kMaxShapes];
+  float shape_size[3][kMaxShapes], shape_pos[3][kMaxShapes], shape_rot[9][kMaxShapes];
+  float shape_mu[kMaxShapes];   // max(shape friction, ground friction)
+  // per generalized DOF
+  int dof_link[kMaxGen];
+  int dof_comp[kMaxGen];        // 0..5 for a floating root ([omega; v]), -1 for a joint DOF
+};
+
+// Per-environment shared-memory arena (offsets in 4-byte words). The link scratch of the
+// articulated-body sweeps (phase 1) and the constraint Jacobian / response (phase 2) alias.
+struct SmemLayout {
+  int link;   // kLinkWords per link: IA 21 | pA 6 | Ic 10
+  int J;      // n_gen x RS
+  int W;      // n_gen x RS
+  int RS;     // row stride of J and W (odd)
+  int S;      // 6 per link: motion subspace in world axes about the actor origin
+  int M;      // n_gen x MS (MS odd): joint-space inertia, then its Cholesky factor (lower)
+  int MS;
+  int vec;    // 6 x n_gen: qdd | v0 | vfin | dq | Linv | spare
+  int con;    // kConWords x ccap (SoA)
+  int ccap;
+  int rowh;   // kRowWords x rcap (SoA)
+  int rcap;
+  int cache;  // cache_len
+  int frc;    // 3 per link
+  int misc;   // 8 ints
+  int total;  // words per environment (multiple of 4)
+};
+constexpr int kLinkWords = 37;
+constexpr int kConWords = 9;   // x y z d mu link cand shape slot
+constexpr int kRowWords = 7;   // kind aux d invA lam mu cache
+
+struct StepArgs {
+  const EnvTypeTable* type;
+  const int* env_ids;        // env ids handled by this launch (nullptr: env_first + group index)
+  int env_first;
+  int n_launch_envs;
+  // global tensors
+  float* root;               // (N_A, 13)
+  float* dof;                // (N_D, 2)
+  const float* act;          // (N_D,)
+  float* net_force;          // (N_B, 3)
+  float* cache;              // (n_envs, cache_stride)
+  int* pairs;                // (n_envs, pair_stride, 3)
+  int* n_pairs;              // (n_envs,)
+  unsigned* sig;             // (n_envs,)
+  int* status;               // (n_envs,)
+  const int* env_dof_base;   // (n_envs,) first DOF row
+  const int* env_body_base;  // (n_envs,) first body row
+  int actors_per_env, cache_stride, pair_stride;
+  // step
+  float dt, h;
+  int substeps;
+  // parameters
+  float gx, gy, gz;
+  int pos_iters, vel_iters;
+  float contact_offset, limit_margin, bias_coef, max_depen_vel;
+  int flags;
+  SmemLayout lay;
+};
+
+}  // namespace artsim

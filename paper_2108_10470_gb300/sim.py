@@ -1,0 +1,246 @@
+"""Thin Python binding of the C ABI in include/sim.h (argument marshalling only).
+
+Every step of the physics runs in the CUDA library ``libartsim.so``; this module only converts a
+:class:`~paper_2108_10470_gb300.workloads.Workload` into ``sim_model_desc`` structs, calls the
+entry points of the same names, and wraps the library-owned device views as zero-copy torch
+tensors (paper, Sec. "Tensor API": physics buffers wrapped as framework tensors without copying).
+There is no fallback: if the library is missing or no GPU is visible, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+from .build import LIB_PATH
+
+SIM_OK = 0
+ERRORS = {-1: "SIM_ERR_INVALID_ARG", -2: "SIM_ERR_TOPOLOGY", -3: "SIM_ERR_CUDA", -4: "SIM_ERR_CAPACITY",
+          -5: "SIM_ERR_TIMEOUT", -6: "SIM_ERR_NONFINITE", -7: "SIM_ERR_HANDLE", -8: "SIM_ERR_NO_DEVICE"}
+SIM_FLAG_SIGNATURE = 1
+(SIM_VIEW_ROOT_STATE, SIM_VIEW_DOF_STATE, SIM_VIEW_DOF_ACTUATION, SIM_VIEW_NET_CONTACT_FORCE,
+ SIM_VIEW_CONTACT_PAIRS, SIM_VIEW_CONTACT_COUNT, SIM_VIEW_SIGNATURE, SIM_VIEW_STATUS,
+ SIM_VIEW_IMPULSE_CACHE) = range(9)
+EXPORTED = ("sim_create", "sim_step", "sim_step_host", "sim_get_view", "sim_set_root_state_indexed",
+            "sim_set_dof_state_indexed", "sim_set_stream", "sim_sync_status", "sim_get_sizes", "sim_destroy",
+            "sim_error_string", "sim_last_error_message", "sim_probe_fp32_peak")
+
+F = ctypes.POINTER(ctypes.c_float)
+I32 = ctypes.POINTER(ctypes.c_int32)
+U8 = ctypes.POINTER(ctypes.c_uint8)
+
+
+class sim_model_desc(ctypes.Structure):
+    _fields_ = [("n_links", ctypes.c_int32), ("parent", I32), ("joint_type", I32), ("joint_axis", F),
+                ("parent_pos", F), ("parent_quat", F), ("mass", F), ("com", F), ("inertia", F), ("armature", F),
+                ("damping", F), ("limit_lo", F), ("limit_hi", F), ("has_limit", U8), ("is_virtual", U8),
+                ("n_shapes", ctypes.c_int32), ("shape_link", I32), ("shape_type", I32), ("shape_size", F),
+                ("shape_pos", F), ("shape_quat", F), ("shape_friction", F)]
+
+
+class sim_params(ctypes.Structure):
+    _fields_ = [("gravity", ctypes.c_float * 3), ("pos_iters", ctypes.c_int32), ("vel_iters", ctypes.c_int32),
+                ("contact_offset", ctypes.c_float), ("limit_margin", ctypes.c_float), ("bias_coef", ctypes.c_float),
+                ("max_depen_vel", ctypes.c_float), ("ground_friction", ctypes.c_float), ("flags", ctypes.c_int32)]
+
+
+class sim_view(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("ndim", ctypes.c_int32), ("shape", ctypes.c_int64 * 3),
+                ("strides", ctypes.c_int64 * 3), ("dtype", ctypes.c_int32), ("device", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def load(path: Optional[str] = None) -> ctypes.CDLL:
+    """Load libartsim.so (raises if it has not been built: there is no fallback path)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is missing; build it with paper_2108_10470_gb300.build")
+    L = ctypes.CDLL(path)
+    L.sim_create.argtypes = [ctypes.POINTER(sim_model_desc), ctypes.c_int32, I32, ctypes.c_int32, ctypes.c_int32,
+                             ctypes.POINTER(sim_params), ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
+    L.sim_step.argtypes = [ctypes.c_void_p, ctypes.c_float, ctypes.c_int32]
+    L.sim_step_host.argtypes = [ctypes.c_void_p, F, F, F, ctypes.c_float, ctypes.c_int32]
+    L.sim_get_view.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(sim_view)]
+    L.sim_set_root_state_indexed.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]
+    L.sim_set_dof_state_indexed.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]
+    L.sim_set_stream.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    L.sim_sync_status.argtypes = [ctypes.c_void_p, I32]
+    L.sim_get_sizes.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]
+    L.sim_destroy.argtypes = [ctypes.c_void_p]
+    L.sim_error_string.argtypes = [ctypes.c_int]
+    L.sim_error_string.restype = ctypes.c_char_p
+    L.sim_last_error_message.argtypes = []
+    L.sim_last_error_message.restype = ctypes.c_char_p
+    L.sim_probe_fp32_peak.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]
+    _lib = L  # every other entry point returns int, ctypes' default restype
+    return L
+
+
+class SimError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        lib = load()
+        msg = lib.sim_error_string(code).decode()
+        extra = lib.sim_last_error_message().decode()
+        super().__init__(f"{where}: {ERRORS.get(code, code)} ({msg}){' - ' + extra if extra else ''}")
+        self.code = code
+
+
+def check(code: int, where: str) -> int:
+    if code != SIM_OK:
+        raise SimError(code, where)
+    return code
+
+
+def _f32(a, shape=None):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float32).reshape(-1) if shape is None else
+                             np.asarray(a, dtype=np.float32).reshape(shape))
+    return a if a.size else np.zeros(1, np.float32)
+
+
+class _DevArray:
+    """__cuda_array_interface__ wrapper around a library-owned view (kept alive by the tensor)."""
+
+    _TYPESTR = {0: "<f4", 1: "<i4", 2: "<u4"}
+
+    def __init__(self, v: sim_view, owner):
+        shape = tuple(int(v.shape[i]) for i in range(v.ndim))
+        self.__cuda_array_interface__ = {"shape": shape, "typestr": self._TYPESTR[v.dtype],
+                                         "data": (int(v.data or 0), False), "version": 2, "strides": None}
+        self.owner = owner
+
+
+def params_struct(p, flags: int = 0) -> sim_params:
+    s = sim_params()
+    for i in range(3):
+        s.gravity[i] = float(p.gravity[i])
+    s.pos_iters, s.vel_iters = int(p.pos_iters), int(p.vel_iters)
+    s.contact_offset, s.limit_margin = float(p.contact_offset), float(p.limit_margin)
+    s.bias_coef, s.max_depen_vel = float(p.bias_coef), float(p.max_depen_vel)
+    s.ground_friction = float(p.ground_friction)
+    s.flags = int(flags)
+    return s
+
+
+def model_structs(models):
+    """sim_model_desc array for a list of workloads.Model (float32 copies kept alive)."""
+    keep = []
+    arr = (sim_model_desc * len(models))()
+    for i, m in enumerate(models):
+        d = arr[i]
+        d.n_links = m.n_links
+        fields = dict(parent=np.ascontiguousarray(m.parent, np.int32), joint_type=np.ascontiguousarray(m.jtype, np.int32),
+                      joint_axis=_f32(m.axis), parent_pos=_f32(m.ppos), parent_quat=_f32(m.pquat), mass=_f32(m.mass),
+                      com=_f32(m.com), inertia=_f32(m.inertia), armature=_f32(m.armature), damping=_f32(m.damping),
+                      limit_lo=_f32(m.lo), limit_hi=_f32(m.hi),
+                      has_limit=np.ascontiguousarray(m.has_limit, np.uint8),
+                      is_virtual=np.ascontiguousarray(m.is_virtual, np.uint8))
+        d.n_shapes = m.n_shapes
+        if m.n_shapes:
+            fields.update(shape_link=np.ascontiguousarray(m.shape_link, np.int32),
+                          shape_type=np.ascontiguousarray(m.shape_type, np.int32), shape_size=_f32(m.shape_size),
+                          shape_pos=_f32(m.shape_pos), shape_quat=_f32(m.shape_quat),
+                          shape_friction=_f32(m.shape_friction))
+        for k, a in fields.items():
+            keep.append(a)
+            ctype = dict(sim_model_desc._fields_)[k]
+            setattr(d, k, a.ctypes.data_as(ctype))
+    return arr, keep
+
+
+class Sim:
+    """A simulation of one workload's environments on the current CUDA device.
+
+    Views (torch tensors aliasing library memory, valid until :meth:`destroy`):
+    ``root_state`` (N_A, 13), ``dof_state`` (N_D, 2), ``dof_actuation`` (N_D,),
+    ``net_contact_force`` (N_B, 3), ``contact_pairs`` (n_envs, C, 3), ``contact_count``,
+    ``signature``, ``status``, ``impulse_cache``.
+    """
+
+    def __init__(self, w, stream=None, flags: int = 0):
+        import torch  # device memory and streams only
+
+        L = load()
+        self.w = w
+        self._torch = torch
+        self._stream = stream if stream is not None else torch.cuda.current_stream()
+        arr, keep = model_structs(w.models)
+        self._keep = (arr, keep)
+        eam = np.ascontiguousarray(w.env_actor_model, np.int32)
+        p = params_struct(w.params, flags)
+        h = ctypes.c_void_p()
+        check(L.sim_create(arr, len(w.models), eam.ctypes.data_as(I32), w.actors_per_env, w.n_envs, ctypes.byref(p),
+                           ctypes.c_void_p(self._stream.cuda_stream), ctypes.byref(h)), "sim_create")
+        self.h = h
+        sz = (ctypes.c_int64 * 7)()
+        check(L.sim_get_sizes(h, sz), "sim_get_sizes")
+        self.N_A, self.N_D, self.N_B, self.pair_cap, self.cache_len, self.n_types, self.launches_per_step = \
+            [int(x) for x in sz]
+        names = ["root_state", "dof_state", "dof_actuation", "net_contact_force", "contact_pairs", "contact_count",
+                 "signature", "status", "impulse_cache"]
+        for which, name in enumerate(names):
+            setattr(self, name, self.view(which))
+
+    def view(self, which: int):
+        v = sim_view()
+        check(load().sim_get_view(self.h, which, ctypes.byref(v)), "sim_get_view")
+        t = self._torch.as_tensor(_DevArray(v, self), device=f"cuda:{v.device}")
+        return t
+
+    def step(self, dt: Optional[float] = None, substeps: Optional[int] = None):
+        check(load().sim_step(self.h, float(self.w.dt if dt is None else dt),
+                              int(self.w.substeps if substeps is None else substeps)), "sim_step")
+
+    def step_host(self, act: np.ndarray, root_out: Optional[np.ndarray], dof_out: Optional[np.ndarray],
+                  dt: Optional[float] = None, substeps: Optional[int] = None):
+        """End-to-end step from host buffers (float32, C-contiguous; pinned memory is faster)."""
+        fp = lambda a: None if a is None else a.ctypes.data_as(F)
+        check(load().sim_step_host(self.h, fp(act), fp(root_out), fp(dof_out),
+                                   float(self.w.dt if dt is None else dt),
+                                   int(self.w.substeps if substeps is None else substeps)), "sim_step_host")
+
+    def set_root_state_indexed(self, src, actor_idx):
+        n = int(actor_idx.numel())
+        check(load().sim_set_root_state_indexed(self.h, ctypes.c_void_p(src.data_ptr()),
+                                                ctypes.c_void_p(actor_idx.data_ptr()), n), "sim_set_root_state_indexed")
+
+    def set_dof_state_indexed(self, src, env_idx):
+        n = int(env_idx.numel())
+        check(load().sim_set_dof_state_indexed(self.h, ctypes.c_void_p(src.data_ptr()),
+                                               ctypes.c_void_p(env_idx.data_ptr()), n), "sim_set_dof_state_indexed")
+
+    def set_stream(self, stream):
+        self._stream = stream
+        check(load().sim_set_stream(self.h, ctypes.c_void_p(stream.cuda_stream)), "sim_set_stream")
+
+    def sync_status(self) -> int:
+        bad = ctypes.c_int32(0)
+        rc = load().sim_sync_status(self.h, ctypes.byref(bad))
+        if rc not in (SIM_OK, -6):
+            check(rc, "sim_sync_status")
+        return int(bad.value)
+
+    def destroy(self):
+        if getattr(self, "h", None):
+            check(load().sim_destroy(self.h), "sim_destroy")
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def probe_fp32_peak(iters: int = 20000, stream=None) -> float:
+    """Measured FP32 FMA throughput of the current GPU (FLOP/s)."""
+    out = ctypes.c_double(0.0)
+    check(load().sim_probe_fp32_peak(ctypes.c_void_p(stream.cuda_stream if stream is not None else 0), int(iters),
+                                     ctypes.byref(out)), "sim_probe_fp32_peak")
+    return float(out.value)
