@@ -284,21 +284,23 @@ SmemLayout make_layout(const EnvTypeTable& T) {
   Ly.RS = Ly.rcap | 1;
   Ly.MS = n | 1;
   Ly.ccap = std::max(T.n_cand, 1);
+  auto al4 = [](int x) { return (x + 3) & ~3; };
   int o = 0;
-  const int phase = std::max(L * kLinkWords, 2 * n * Ly.RS);
+  const int phase = std::max(L * kLinkWords, n * Ly.RS);
   Ly.link = o;
-  Ly.J = o;
-  Ly.W = o + n * Ly.RS;
+  Ly.Y = o;
   o += phase;
-  Ly.S = o; o += 6 * L;
+  Ly.SD = o; o += 6 * n;
   Ly.M = o; o += n * Ly.MS;
-  Ly.vec = o; o += 6 * n;
+  Ly.vec = o; o += 5 * n;
   Ly.con = o; o += kConWords * Ly.ccap;
-  Ly.rowh = o; o += kRowWords * Ly.rcap;
+  o = al4(o);
+  Ly.rowc = o; o += 4 * Ly.rcap;
+  Ly.lam = o; o += Ly.rcap;
+  Ly.rowa = o; o += Ly.rcap;
   Ly.cache = o; o += std::max(T.cache_len, 1);
   Ly.frc = o; o += 3 * L;
-  Ly.misc = o; o += 8;
-  Ly.total = (o + 3) & ~3;
+  Ly.total = al4(o);
   return Ly;
 }
 

@@ -54,29 +54,28 @@ struct EnvTypeTable {
   int dof_comp[kMaxGen];        // 0..5 for a floating root ([omega; v]), -1 for a joint DOF
 };
 
-// Per-environment shared-memory arena (offsets in 4-byte words). The link scratch of the
-// articulated-body sweeps (phase 1) and the constraint Jacobian / response (phase 2) alias.
+// Per-environment shared-memory arena (offsets in 4-byte words). The link hand-off slots of the
+// inward sweep (phase 1) and the constraint response Y (phase 2) alias.
 struct SmemLayout {
   int link;   // kLinkWords per link: IA 21 | pA 6 | Ic 10
-  int J;      // n_gen x RS
-  int W;      // n_gen x RS
-  int RS;     // row stride of J and W (odd)
-  int S;      // 6 per link: motion subspace in world axes about the actor origin
-  int M;      // n_gen x MS (MS odd): joint-space inertia, then its Cholesky factor (lower)
+  int Y;      // n_gen x RS: Y = L^-1 J^T, one column per constraint row
+  int RS;     // row stride of Y (odd)
+  int SD;     // 6 per generalized DOF: motion subspace in world axes about the actor origin
+  int M;      // n_gen x MS (MS odd): Cholesky factor L of the joint-space inertia (lower)
   int MS;
-  int vec;    // 6 x n_gen: qdd | v0 | vfin | dq | Linv | spare
+  int vec;    // 5 x n_gen: qdd | v0 | vf | dq | Linv
   int con;    // kConWords x ccap (SoA)
   int ccap;
-  int rowh;   // kRowWords x rcap (SoA)
+  int rowc;   // float4 x rcap: row headers (16-byte aligned)
+  int lam;    // rcap: impulses
+  int rowa;   // rcap: row aux (DOF / contact index)
   int rcap;
   int cache;  // cache_len
   int frc;    // 3 per link
-  int misc;   // 8 ints
   int total;  // words per environment (multiple of 4)
 };
 constexpr int kLinkWords = 37;
 constexpr int kConWords = 9;   // x y z d mu link cand shape slot
-constexpr int kRowWords = 7;   // kind aux d invA lam mu cache
 
 struct StepArgs {
   const EnvTypeTable* type;

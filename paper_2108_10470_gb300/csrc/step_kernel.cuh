@@ -16,14 +16,17 @@
 //     rigid-body inertias about O_a and gravity as an external force; the composite-rigid-body
 //     inertias of RBDA Table 6.2 are accumulated in the same inward sweep and give the
 //     joint-space inertia M_ij = S_i . (I^c_link(i) S_j) for DOF j on the path of DOF i.
+// Constraint response. With M = L L^T (Cholesky) and Y = L^-1 J^T, the solve runs in the
+// coordinates z = L^T v: J_r v = Y_r . z, the impulse update v += M^-1 J_r^T dl becomes
+// z += Y_r dl, and J_r M^-1 J_r^T = |Y_r|^2. Only Y (n x R) is stored; v = L^-T z at the end.
 // The TGS-style solve follows the paper's TGS paragraph: position iterations accumulate
-// h/n_pos * v into the delta buffer dq, which is projected onto each row's Jacobian and added to
-// its bias; velocity iterations are unbiased.
+// h/n_pos * v into the delta buffer dq (here dz = L^T dq), which is projected onto each row's
+// Jacobian and added to its bias; velocity iterations are unbiased.
 //
 // Lane roles: "link mode" lane l = env link l; "DOF mode" lane g = generalized DOF g; "row mode"
 // lane r = constraint row r (strided by G); "shape mode" lane s = shape s. Every loop whose body
-// shuffles has a warp-uniform trip count (maxima over the warp's groups), so the groups of one
-// warp stay converged.
+// shuffles or synchronises has a warp-uniform trip count (the groups of one launch share one env
+// type; row loops use the maximum over the warp), so the groups of one warp stay converged.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -87,7 +90,6 @@ template <int G> struct Grp {
     return x;
   }
   static __device__ __forceinline__ float get(float x, int src) { return __shfl_sync(kFull, x, src, G); }
-  static __device__ __forceinline__ int geti(int x, int src) { return __shfl_sync(kFull, x, src, G); }
   static __device__ __forceinline__ int any(int x) {
 #pragma unroll
     for (int m = G / 2; m >= 1; m >>= 1) x |= __shfl_xor_sync(kFull, x, m, G);
@@ -115,9 +117,17 @@ __device__ __forceinline__ void fnv1a(unsigned& h, int v) {
   }
 }
 
+// Row header words (float4 per row, constant during the solve):
+//   x: separation d (limit / normal rows) or friction coefficient (friction rows)
+//   y: 1 / (J M^-1 J^T), 0 for a row without response (skipped)
+//   z: int bits: kind | normal_row << 2
+//   w: int bits: impulse-cache slot
+// rowa (int per row): limit rows: g | side << 8 | jd << 16; contact rows: c | dir << 8
+// (dir 0 = normal e_z, 1 = e_x, 2 = e_y).
+
 // ---------------------------------------------------------------------------------------------
 template <int G>
-__global__ void __launch_bounds__(128) step_kernel(const StepArgs A) {
+__global__ void __launch_bounds__(128, 4) step_kernel(const StepArgs A) {
   extern __shared__ __align__(16) float smem[];
   const EnvTypeTable* __restrict__ T = A.type;
   const int lane = threadIdx.x & (G - 1);
@@ -133,20 +143,20 @@ __global__ void __launch_bounds__(128) step_kernel(const StepArgs A) {
   const int L = T->n_links, n = T->n_gen, NS = T->n_shapes;
   const int maxdepth = T->max_depth;
   const int RS = Ly.RS, MS = Ly.MS, CC = Ly.ccap, RC = Ly.rcap;
-  float* s_link = sm + Ly.link;
-  float* s_J = sm + Ly.J;
-  float* s_W = sm + Ly.W;
-  float* s_S = sm + Ly.S;
-  float* s_M = sm + Ly.M;
+  float* s_link = sm + Ly.link;  // phase 1: per-link hand-off slots of the inward sweep
+  float* s_Y = sm + Ly.Y;        // phase 2 (aliases phase 1): Y = L^-1 J^T, n x RS
+  float* s_SD = sm + Ly.SD;      // motion subspace column of every generalized DOF
+  float* s_M = sm + Ly.M;        // Cholesky factor L (lower), n x MS
   float* s_qdd = sm + Ly.vec;
   float* s_v0 = s_qdd + n;
   float* s_vf = s_v0 + n;
   float* s_dq = s_vf + n;
   float* s_Linv = s_dq + n;
   float* s_con = sm + Ly.con;
-  float* s_row = sm + Ly.rowh;
-  int* s_rowi = smi + Ly.rowh;
   int* s_coni = smi + Ly.con;
+  float4* s_rowc = reinterpret_cast<float4*>(sm + Ly.rowc);
+  float* s_lam = sm + Ly.lam;
+  int* s_rowa = smi + Ly.rowa;
   float* s_cache = sm + Ly.cache;
   float* s_frc = sm + Ly.frc;
 
@@ -162,30 +172,29 @@ __global__ void __launch_bounds__(128) step_kernel(const StepArgs A) {
   const bool is_root = isl && par < 0;
   const bool free_root = is_root && jt == kFree;
   const bool has_dof = isl && (jt == kRevolute || jt == kPrismatic);
-  const V3 jaxis = v3(T->axis[0][l], T->axis[1][l], T->axis[2][l]);
-  const float damping = T->damping[l], armature = T->armature[l];
+  const bool isg = lane < n;
 
   // ---- load state (one HBM read per env-step) ----
   const int dof_base = A.env_dof_base[env];
   float rq[4] = {0.f, 0.f, 0.f, 1.f};
   V3 rp = v3(0.f, 0.f, 0.f), rw = rp, rv = rp;  // root pose / velocity (root lanes)
-  float q = 0.f, qd = 0.f, f = 0.f;
+  float q = 0.f, qd = 0.f, tau = 0.f;
   if (is_root) {
     const float* r = A.root + (size_t)(env * A.actors_per_env + T->actor[l]) * 13;
     rp = v3(r[0], r[1], r[2]);
     rq[0] = r[3]; rq[1] = r[4]; rq[2] = r[5]; rq[3] = r[6];
-    rv = v3(r[7], r[8], r[9]);
-    rw = v3(r[10], r[11], r[12]);
-    if (!free_root) { rv = v3(0.f, 0.f, 0.f); rw = rv; }
+    if (free_root) {
+      rv = v3(r[7], r[8], r[9]);
+      rw = v3(r[10], r[11], r[12]);
+    }
   }
   if (has_dof) {
     q = A.dof[(size_t)(dof_base + jd) * 2];
     qd = A.dof[(size_t)(dof_base + jd) * 2 + 1];
-    f = A.act[dof_base + jd];
+    tau = A.act[dof_base + jd];  // joint force of the step; damping is added per substep
   }
   for (int i = lane; i < T->cache_len; i += G) s_cache[i] = A.cache[(size_t)env * A.cache_stride + i];
   for (int i = lane; i < 3 * L; i += G) s_frc[i] = 0.f;
-  const float tau = f;  // joint force; damping is applied with the substep's velocity below
 
   unsigned sig = 2166136261u;
   int status = 0;
@@ -197,9 +206,8 @@ __global__ void __launch_bounds__(128) step_kernel(const StepArgs A) {
 
   for (int sub = 0; sub < A.substeps; ++sub) {
     // ======== (a2) forward kinematics + velocities, level-synchronous (link mode) ========
-    float Rw[9];  // link -> world rotation
+    float Rw[9];               // link -> world rotation
     V3 P = v3(0.f, 0.f, 0.f);  // link origin relative to the actor origin O_a
-    V3 Ow = rp;                // actor origin in world (root lanes; others fetch below)
     float vs[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // link spatial velocity [w; v] about O_a
     float Sa[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // joint motion subspace about O_a
     float cc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // velocity-product acceleration
@@ -209,10 +217,7 @@ __global__ void __launch_bounds__(128) step_kernel(const StepArgs A) {
       const V3 pxw = cross(rv, rw);  // d/dt S_root * nu = [0; p_dot x omega]
       cc[3] = pxw.x; cc[4] = pxw.y; cc[5] = pxw.z;
     }
-    {
-      const float ox = Grp<G>::get(rp.x, ar), oy = Grp<G>::get(rp.y, ar), oz = Grp<G>::get(rp.z, ar);
-      Ow = v3(ox, oy, oz);
-    }
+    const float Oz = Grp<G>::get(rp.z, ar);  // actor origin height (world)
     for (int d = 1; d <= maxdepth; ++d) {
       float Rp[9], vp[6];
       const int src = par >= 0 ? par : lane;
@@ -223,6 +228,7 @@ __global__ void __launch_bounds__(128) step_kernel(const StepArgs A) {
       const float ppx = Grp<G>::get(P.x, src), ppy = Grp<G>::get(P.y, src), ppz = Grp<G>::get(P.z, src);
       if (dep == d) {
         const V3 Pp = v3(ppx, ppy, ppz);
+        const V3 jaxis = v3(T->axis[0][l], T->axis[1][l], T->axis[2][l]);
         float Rpj[9], RB[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) Rpj[k] = T->prot[k][l];
@@ -256,25 +262,36 @@ __global__ void __launch_bounds__(128) step_kernel(const StepArgs A) {
         cc[0] = c0.x; cc[1] = c0.y; cc[2] = c0.z; cc[3] = c1.x; cc[4] = c1.y; cc[5] = c1.z;
       }
     }
-    if (isl) {
+    // motion subspace per generalized DOF (unit columns for a floating root)
+    if (has_dof) {
 #pragma unroll
-      for (int k = 0; k < 6; ++k) s_S[6 * l + k] = Sa[k];
+      for (int k = 0; k < 6; ++k) s_SD[6 * gd + k] = Sa[k];
+    }
+    if (free_root) {
+#pragma unroll
+      for (int c = 0; c < 6; ++c)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) s_SD[6 * (gd + c) + k] = (k == c) ? 1.f : 0.f;
     }
 
-    // ======== (a3) rigid-body inertias about O_a, bias forces: p = v x* I v - f_gravity ========
-    float U[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, Dinv = 0.f, uu = 0.f;
-    if (isl) {
-      const float m = T->mass[l];
+    // ======== (a3) rigid-body inertia about O_a and bias force, in registers ========
+    // articulated inertia IA (sym 6x6), bias pA, composite inertia Ic = (m, h, I_O)
+    float IA[21], pA[6], Ic[10];
+    {
+      const float m = isl ? T->mass[l] : 0.f;
       const V3 cw = P + mv(Rw, v3(T->com[0][l], T->com[1][l], T->com[2][l]));
-      // rotational inertia about the COM in world axes: R Ic R^T
-      float Ic[9] = {T->inertia[0][l], T->inertia[3][l], T->inertia[4][l], T->inertia[3][l], T->inertia[1][l],
+      float In[9] = {T->inertia[0][l], T->inertia[3][l], T->inertia[4][l], T->inertia[3][l], T->inertia[1][l],
                      T->inertia[5][l], T->inertia[4][l], T->inertia[5][l], T->inertia[2][l]};
+      if (!isl) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) In[k] = 0.f;
+      }
       float RI[9], RIRt[9], Rt[9];
 #pragma unroll
       for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j < 3; ++j) Rt[3 * i + j] = Rw[3 * j + i];
-      mm(Rw, Ic, RI);
+      mm(Rw, In, RI);
       mm(RI, Rt, RIRt);
       // I_O = Ic_w + m (|c|^2 1 - c c^T); h = m c
       const float c2 = dot(cw, cw);
@@ -290,211 +307,40 @@ __global__ void __launch_bounds__(128) step_kernel(const StepArgs A) {
       // v x* F = [w x Fa + v x Fl; w x Fl]; gravity force I [0; g] = [h x g; m g]
       const V3 pa = cross(w, Fa) + cross(vl, Fl) - cross(hh, g);
       const V3 pl = cross(w, Fl) - g * m;
-      float* sl = s_link + kLinkWords * l;
       // articulated inertia starts as the rigid inertia: [[I_O, h~], [h~^T, m 1]]
-      sl[sidx(0, 0)] = Ixx; sl[sidx(0, 1)] = Ixy; sl[sidx(0, 2)] = Ixz;
-      sl[sidx(1, 1)] = Iyy; sl[sidx(1, 2)] = Iyz; sl[sidx(2, 2)] = Izz;
-      sl[sidx(0, 3)] = 0.f;    sl[sidx(0, 4)] = -hh.z; sl[sidx(0, 5)] = hh.y;
-      sl[sidx(1, 3)] = hh.z;   sl[sidx(1, 4)] = 0.f;   sl[sidx(1, 5)] = -hh.x;
-      sl[sidx(2, 3)] = -hh.y;  sl[sidx(2, 4)] = hh.x;  sl[sidx(2, 5)] = 0.f;
-      sl[sidx(3, 3)] = m; sl[sidx(3, 4)] = 0.f; sl[sidx(3, 5)] = 0.f;
-      sl[sidx(4, 4)] = m; sl[sidx(4, 5)] = 0.f; sl[sidx(5, 5)] = m;
-      sl[21] = pa.x; sl[22] = pa.y; sl[23] = pa.z; sl[24] = pl.x; sl[25] = pl.y; sl[26] = pl.z;
-      // composite rigid inertia (m, h, I_O)
-      sl[27] = m; sl[28] = hh.x; sl[29] = hh.y; sl[30] = hh.z;
-      sl[31] = Ixx; sl[32] = Iyy; sl[33] = Izz; sl[34] = Ixy; sl[35] = Ixz; sl[36] = Iyz;
-    }
-    __syncwarp();
-
-    // ======== inward sweep: articulated inertias (ABA pass 2) and composite inertias ========
-    const float tau_sub = tau - damping * qd;
-    for (int d = maxdepth; d >= 1; --d) {
-      if (dep == d && has_dof) {
-        float* sl = s_link + kLinkWords * l;
-#pragma unroll
-        for (int i = 0; i < 6; ++i) {
-          float s = 0.f;
-#pragma unroll
-          for (int j = 0; j < 6; ++j) s += sl[sidx(i, j)] * Sa[j];
-          U[i] = s;
-        }
-        float D = armature, sp = 0.f;
-#pragma unroll
-        for (int i = 0; i < 6; ++i) { D += Sa[i] * U[i]; sp += Sa[i] * sl[21 + i]; }
-        Dinv = 1.f / D;
-        uu = tau_sub - sp;
-        if (!(D > 0.f)) status |= 2;
-        // Ia = IA - U U^T / D ; pa = pA + Ia c + U u / D
-#pragma unroll
-        for (int i = 0; i < 6; ++i)
-#pragma unroll
-          for (int j = i; j < 6; ++j) sl[sidx(i, j)] -= U[i] * U[j] * Dinv;
-        float pa[6];
-#pragma unroll
-        for (int i = 0; i < 6; ++i) {
-          float s = sl[21 + i] + U[i] * uu * Dinv;
-#pragma unroll
-          for (int j = 0; j < 6; ++j) s += sl[sidx(i, j)] * cc[j];
-          pa[i] = s;
-        }
-#pragma unroll
-        for (int i = 0; i < 6; ++i) sl[21 + i] = pa[i];
-      }
-      __syncwarp();
-      if (dep == d - 1) {
-        float* sl = s_link + kLinkWords * l;
-        for (int ch = T->first_child[l]; ch >= 0; ch = T->next_sibling[ch]) {
-          const float* sc = s_link + kLinkWords * ch;
-#pragma unroll
-          for (int k = 0; k < kLinkWords; ++k) sl[k] += sc[k];
-        }
-      }
-      __syncwarp();
-    }
-
-    // ======== root acceleration, outward sweep (ABA pass 3) ========
-    float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    float qdd = 0.f;
-    if (free_root) {
-      // a0 = -(IA)^-1 pA by a 6x6 Cholesky solve in registers
-      const float* sl = s_link + kLinkWords * l;
-      float Lc[21], y[6];
-#pragma unroll
-      for (int k = 0; k < 21; ++k) Lc[k] = sl[k];
-#pragma unroll
-      for (int j = 0; j < 6; ++j) {
-        float s = Lc[sidx(j, j)];
-#pragma unroll
-        for (int k = 0; k < j; ++k) s -= Lc[sidx(j, k)] * Lc[sidx(j, k)];
-        if (!(s > 0.f)) { status |= 2; s = 1.f; }
-        const float ljj = sqrtf(s), inv = 1.f / ljj;
-        Lc[sidx(j, j)] = ljj;
-#pragma unroll
-        for (int i = j + 1; i < 6; ++i) {
-          float t = Lc[sidx(i, j)];
-#pragma unroll
-          for (int k = 0; k < j; ++k) t -= Lc[sidx(i, k)] * Lc[sidx(j, k)];
-          Lc[sidx(i, j)] = t * inv;
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < 6; ++i) {
-        float s = -sl[21 + i];
-#pragma unroll
-        for (int k = 0; k < i; ++k) s -= Lc[sidx(i, k)] * y[k];
-        y[i] = s / Lc[sidx(i, i)];
-      }
-#pragma unroll
-      for (int i = 5; i >= 0; --i) {
-        float s = y[i];
-#pragma unroll
-        for (int k = i + 1; k < 6; ++k) s -= Lc[sidx(k, i)] * acc[k];
-        acc[i] = s / Lc[sidx(i, i)];
-      }
-    }
-    for (int d = 1; d <= maxdepth; ++d) {
-      float ap[6];
-      const int src = par >= 0 ? par : lane;
-#pragma unroll
-      for (int k = 0; k < 6; ++k) ap[k] = Grp<G>::get(acc[k], src);
-      if (dep == d) {
-#pragma unroll
-        for (int k = 0; k < 6; ++k) acc[k] = ap[k] + cc[k];
-        if (has_dof) {
-          float ua = 0.f;
-#pragma unroll
-          for (int k = 0; k < 6; ++k) ua += U[k] * acc[k];
-          qdd = (uu - ua) * Dinv;
-#pragma unroll
-          for (int k = 0; k < 6; ++k) acc[k] += Sa[k] * qdd;
-        }
-      }
-    }
-    // generalized velocity and its rate (root: nu_dot = a0 - [0; p_dot x omega])
-    if (has_dof) { s_qdd[gd] = qdd; s_v0[gd] = qd; }
-    if (free_root) {
-#pragma unroll
-      for (int k = 0; k < 6; ++k) { s_qdd[gd + k] = acc[k] - cc[k]; s_v0[gd + k] = vs[k]; }
-    }
-    __syncwarp();
-
-    // ======== joint-space inertia M (DOF mode) ========
-    const bool isg = lane < n;
-    const int gl = isg ? T->dof_link[lane] : 0;
-    const int gcomp = isg ? T->dof_comp[lane] : -1;
-    float Sg[6];
-    if (gcomp >= 0) {
-#pragma unroll
-      for (int k = 0; k < 6; ++k) Sg[k] = (k == gcomp) ? 1.f : 0.f;
-    } else {
-#pragma unroll
-      for (int k = 0; k < 6; ++k) Sg[k] = s_S[6 * gl + k];
-    }
-    if (isg) {
-      const float* ic = s_link + kLinkWords * gl + 27;
-      const float m = ic[0];
-      const V3 hh = v3(ic[1], ic[2], ic[3]);
-      const V3 w = v3(Sg[0], Sg[1], Sg[2]), vl = v3(Sg[3], Sg[4], Sg[5]);
-      const V3 Iw = v3(ic[4] * w.x + ic[7] * w.y + ic[8] * w.z, ic[7] * w.x + ic[5] * w.y + ic[9] * w.z,
-                       ic[8] * w.x + ic[9] * w.y + ic[6] * w.z);
-      const V3 Fa = Iw + cross(hh, vl), Fl = vl * m + cross(w, hh);
-      const float F[6] = {Fa.x, Fa.y, Fa.z, Fl.x, Fl.y, Fl.z};
-      const unsigned anc = T->anc[gl];
-      for (int j = 0; j <= lane; ++j) {
-        float mij = 0.f;
-        if ((anc >> j) & 1u) {
-          const int jc = T->dof_comp[j];
-          if (jc >= 0) {
-            mij = F[jc];
-          } else {
-            const float* Sj = s_S + 6 * T->dof_link[j];
-#pragma unroll
-            for (int k = 0; k < 6; ++k) mij += Sj[k] * F[k];
-          }
-        }
-        if (j == lane && gcomp < 0) mij += T->armature[gl];
-        s_M[lane * MS + j] = mij;
-      }
-    }
-    __syncwarp();
-    // ======== dense Cholesky M = L L^T (lanes = rows; lower triangle in place) ========
-    for (int k = 0; k < n; ++k) {
-      float akk = s_M[k * MS + k];
-      if (!(akk > 0.f)) { status |= 2; akk = 1.f; }
-      const float lkk = sqrtf(akk), inv = 1.f / lkk;
-      __syncwarp();
-      if (lane > k && lane < n) s_M[lane * MS + k] *= inv;
-      if (lane == k) { s_M[k * MS + k] = lkk; s_Linv[k] = inv; }
-      __syncwarp();
-      if (lane > k && lane < n) {
-        const float lik = s_M[lane * MS + k];
-        for (int j = k + 1; j <= lane; ++j) s_M[lane * MS + j] -= lik * s_M[j * MS + k];
-      }
-      __syncwarp();
+      IA[sidx(0, 0)] = Ixx; IA[sidx(0, 1)] = Ixy; IA[sidx(0, 2)] = Ixz;
+      IA[sidx(1, 1)] = Iyy; IA[sidx(1, 2)] = Iyz; IA[sidx(2, 2)] = Izz;
+      IA[sidx(0, 3)] = 0.f;   IA[sidx(0, 4)] = -hh.z; IA[sidx(0, 5)] = hh.y;
+      IA[sidx(1, 3)] = hh.z;  IA[sidx(1, 4)] = 0.f;   IA[sidx(1, 5)] = -hh.x;
+      IA[sidx(2, 3)] = -hh.y; IA[sidx(2, 4)] = hh.x;  IA[sidx(2, 5)] = 0.f;
+      IA[sidx(3, 3)] = m; IA[sidx(3, 4)] = 0.f; IA[sidx(3, 5)] = 0.f;
+      IA[sidx(4, 4)] = m; IA[sidx(4, 5)] = 0.f; IA[sidx(5, 5)] = m;
+      pA[0] = pa.x; pA[1] = pa.y; pA[2] = pa.z; pA[3] = pl.x; pA[4] = pl.y; pA[5] = pl.z;
+      Ic[0] = m; Ic[1] = hh.x; Ic[2] = hh.y; Ic[3] = hh.z;
+      Ic[4] = Ixx; Ic[5] = Iyy; Ic[6] = Izz; Ic[7] = Ixy; Ic[8] = Ixz; Ic[9] = Iyz;
     }
 
     // ======== (a4) ground contacts (shape mode) and limit rows (link mode) ========
     {
-      // shape lanes fetch their link's pose
       const int sl_link = (lane < NS) ? T->shape_link[lane] : 0;
       float Rl[9];
 #pragma unroll
       for (int k = 0; k < 9; ++k) Rl[k] = Grp<G>::get(Rw[k], sl_link);
       const float plx = Grp<G>::get(P.x, sl_link), ply = Grp<G>::get(P.y, sl_link), plz = Grp<G>::get(P.z, sl_link);
-      const float oz = Grp<G>::get(Ow.z, sl_link);
-      int nk = 0;
+      const float oz = Grp<G>::get(Oz, sl_link);
       unsigned keep = 0u;
       float zc[8];
       V3 xs[8];
-      const int st = (lane < NS) ? T->shape_type[lane] : -1;
       const float coff = A.contact_offset;
       if (lane < NS) {
+        const int st = T->shape_type[lane];
         float Rsh[9], Rs[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) Rsh[k] = T->shape_rot[k][lane];
         mm(Rl, Rsh, Rs);
         const V3 cs = v3(plx, ply, plz) + mv(Rl, v3(T->shape_pos[0][lane], T->shape_pos[1][lane], T->shape_pos[2][lane]));
         const float s0 = T->shape_size[0][lane], s1 = T->shape_size[1][lane], s2 = T->shape_size[2][lane];
+        int nk;
         if (st == kSphere) {
           xs[0] = v3(cs.x, cs.y, cs.z - s0);
           zc[0] = (oz + cs.z) - s0;
@@ -520,8 +366,7 @@ __global__ void __launch_bounds__(128) step_kernel(const StepArgs A) {
         for (int k = 0; k < 8; ++k)
           if (k < nk && zc[k] < coff) keep |= 1u << k;
       }
-      const int cnt = __popc(keep);
-      const int base = Grp<G>::excl_scan(cnt, lane, &n_con);
+      const int base = Grp<G>::excl_scan(__popc(keep), lane, &n_con);
       if (lane < NS) {
         int o = base;
         const float mu = T->shape_mu[lane];
@@ -554,38 +399,39 @@ __global__ void __launch_bounds__(128) step_kernel(const StepArgs A) {
       const int lbase = Grp<G>::excl_scan(__popc(lf), lane, &n_lim);
       if (lf) {
         int o = lbase;
+        const int slot0 = 3 * T->n_cand + 2 * jd;
         if (lf & 1) {
-          s_rowi[0 * RC + o] = kRowLimit; s_rowi[1 * RC + o] = gd; s_row[2 * RC + o] = dlo;
-          s_row[5 * RC + o] = 1.f; s_rowi[6 * RC + o] = 3 * T->n_cand + 2 * jd; ++o;
+          s_rowc[o] = make_float4(dlo, 0.f, __int_as_float(kRowLimit), __int_as_float(slot0));
+          s_rowa[o] = gd | (jd << 16);
+          ++o;
         }
         if (lf & 2) {
-          s_rowi[0 * RC + o] = kRowLimit; s_rowi[1 * RC + o] = gd | (1 << 16); s_row[2 * RC + o] = dhi;
-          s_row[5 * RC + o] = -1.f; s_rowi[6 * RC + o] = 3 * T->n_cand + 2 * jd + 1;
+          s_rowc[o] = make_float4(dhi, 0.f, __int_as_float(kRowLimit), __int_as_float(slot0 + 1));
+          s_rowa[o] = gd | (1 << 8) | (jd << 16);
         }
       }
       R = n_lim + 3 * n_con;
       __syncwarp();
-      // contact rows: normal rows then friction pairs
+      // contact rows: every contact's normal row, then every contact's two friction rows
       for (int c = lane; c < n_con; c += G) {
         const int cand = s_coni[6 * CC + c];
         const float mu = s_con[4 * CC + c];
         const int rn = n_lim + c;
-        s_rowi[0 * RC + rn] = kRowNormal; s_rowi[1 * RC + rn] = c; s_row[2 * RC + rn] = s_con[3 * CC + c];
-        s_row[5 * RC + rn] = mu; s_rowi[6 * RC + rn] = 3 * cand;
+        s_rowc[rn] = make_float4(s_con[3 * CC + c], 0.f, __int_as_float(kRowNormal), __int_as_float(3 * cand));
+        s_rowa[rn] = c;
         for (int t = 0; t < 2; ++t) {
           const int rf = n_lim + n_con + 2 * c + t;
-          s_rowi[0 * RC + rf] = kRowFriction; s_rowi[1 * RC + rf] = c | (t << 16); s_row[2 * RC + rf] = 0.f;
-          s_row[5 * RC + rf] = mu; s_rowi[6 * RC + rf] = 3 * cand + 1 + t;
+          s_rowc[rf] = make_float4(mu, 0.f, __int_as_float(kRowFriction | (rn << 2)), __int_as_float(3 * cand + 1 + t));
+          s_rowa[rf] = c | ((1 + t) << 8);
         }
       }
+      __syncwarp();
       if ((A.flags & 1) && lane == 0) {
         fnv1a(sig, n_lim);
         for (int r = 0; r < n_lim; ++r) {
-          const int aux = s_rowi[1 * RC + r];
-          // env joint-DOF index of the limited DOF: the row's cache slot encodes it
-          const int slot = s_rowi[6 * RC + r] - 3 * T->n_cand;
-          fnv1a(sig, slot >> 1);
-          fnv1a(sig, (aux >> 16) & 1);
+          const int a = s_rowa[r];
+          fnv1a(sig, a >> 16);
+          fnv1a(sig, (a >> 8) & 1);
         }
         fnv1a(sig, n_con);
         for (int c = 0; c < n_con; ++c) {
@@ -594,113 +440,316 @@ __global__ void __launch_bounds__(128) step_kernel(const StepArgs A) {
           fnv1a(sig, s_coni[8 * CC + c]);
         }
       }
-      __syncwarp();
     }
 
-    // ======== (a5) constraint Jacobian rows (DOF mode) ========
-    const int Rw_max = __reduce_max_sync(kFull, R);
+    // ======== inward sweep: articulated inertias (ABA pass 2) and composite inertias ========
+    float U[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, Dinv = 0.f, uu = 0.f;
     {
-      const unsigned gbit = 1u << (lane & 31);
-      for (int r = 0; r < R; ++r) {
-        const int kind = s_rowi[0 * RC + r];
-        const int aux = s_rowi[1 * RC + r];
-        float jv = 0.f;
-        if (kind == kRowLimit) {
-          jv = ((aux & 0xffff) == lane) ? s_row[5 * RC + r] : 0.f;
-        } else {
-          const int c = aux & 0xffff;
-          const int la = s_coni[5 * CC + c];
-          if (isg && (T->anc[la] & gbit)) {
-            const V3 x = v3(s_con[0 * CC + c], s_con[1 * CC + c], s_con[2 * CC + c]);
-            // k = e_z (normal), e_x / e_y (friction t = 0 / 1); f = [x x k; k]
-            float fr[6];
-            if (kind == kRowNormal) { fr[0] = x.y; fr[1] = -x.x; fr[2] = 0.f; fr[3] = 0.f; fr[4] = 0.f; fr[5] = 1.f; }
-            else if ((aux >> 16) == 0) { fr[0] = 0.f; fr[1] = x.z; fr[2] = -x.y; fr[3] = 1.f; fr[4] = 0.f; fr[5] = 0.f; }
-            else { fr[0] = -x.z; fr[1] = 0.f; fr[2] = x.x; fr[3] = 0.f; fr[4] = 1.f; fr[5] = 0.f; }
+      const float tau_sub = tau - T->damping[l] * qd;
+      for (int d = maxdepth; d >= 1; --d) {
+        if (dep == d) {
+          if (has_dof) {
 #pragma unroll
-            for (int k = 0; k < 6; ++k) jv += Sg[k] * fr[k];
+            for (int i = 0; i < 6; ++i) {
+              float s = 0.f;
+#pragma unroll
+              for (int j = 0; j < 6; ++j) s += IA[sidx(i, j)] * Sa[j];
+              U[i] = s;
+            }
+            float D = T->armature[l], sp = 0.f;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) { D += Sa[i] * U[i]; sp += Sa[i] * pA[i]; }
+            if (!(D > 0.f)) { status |= 2; D = 1.f; }
+            Dinv = 1.f / D;
+            uu = tau_sub - sp;
+            // Ia = IA - U U^T / D ; pa = pA + Ia c + U u / D
+#pragma unroll
+            for (int i = 0; i < 6; ++i)
+#pragma unroll
+              for (int j = i; j < 6; ++j) IA[sidx(i, j)] -= U[i] * U[j] * Dinv;
+            float pa[6];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+              float s = pA[i] + U[i] * uu * Dinv;
+#pragma unroll
+              for (int j = 0; j < 6; ++j) s += IA[sidx(i, j)] * cc[j];
+              pa[i] = s;
+            }
+#pragma unroll
+            for (int i = 0; i < 6; ++i) pA[i] = pa[i];
+          }
+          float* sl = s_link + kLinkWords * l;
+#pragma unroll
+          for (int k = 0; k < 21; ++k) sl[k] = IA[k];
+#pragma unroll
+          for (int k = 0; k < 6; ++k) sl[21 + k] = pA[k];
+#pragma unroll
+          for (int k = 0; k < 10; ++k) sl[27 + k] = Ic[k];
+        }
+        __syncwarp();
+        if (dep == d - 1) {
+          for (int ch = T->first_child[l]; ch >= 0; ch = T->next_sibling[ch]) {
+            const float* sc = s_link + kLinkWords * ch;
+#pragma unroll
+            for (int k = 0; k < 21; ++k) IA[k] += sc[k];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) pA[k] += sc[21 + k];
+#pragma unroll
+            for (int k = 0; k < 10; ++k) Ic[k] += sc[27 + k];
           }
         }
-        if (isg) s_J[lane * RS + r] = jv;
+      }
+      // final composite inertias for the joint-space inertia (roots were never handed off)
+      if (is_root) {
+        float* sl = s_link + kLinkWords * l;
+#pragma unroll
+        for (int k = 0; k < 10; ++k) sl[27 + k] = Ic[k];
       }
     }
-    __syncwarp();
-    // ======== response W = M^-1 J^T, A = J W, warm start (row mode) ========
-    for (int r = lane; r < R; r += G) {
-      for (int i = 0; i < n; ++i) {
-        float y = s_J[i * RS + r];
-        for (int k = 0; k < i; ++k) y -= s_M[i * MS + k] * s_W[k * RS + r];
-        s_W[i * RS + r] = y * s_Linv[i];
+
+    // ======== root acceleration, outward sweep (ABA pass 3) ========
+    float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float qdd = 0.f;
+    if (free_root) {
+      // a0 = -(IA)^-1 pA by a 6x6 Cholesky solve in registers
+      float y[6];
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        float s = IA[sidx(j, j)];
+#pragma unroll
+        for (int k = 0; k < j; ++k) s -= IA[sidx(j, k)] * IA[sidx(j, k)];
+        if (!(s > 0.f)) { status |= 2; s = 1.f; }
+        const float ljj = sqrtf(s), inv = 1.f / ljj;
+        IA[sidx(j, j)] = ljj;
+#pragma unroll
+        for (int i = j + 1; i < 6; ++i) {
+          float t = IA[sidx(i, j)];
+#pragma unroll
+          for (int k = 0; k < j; ++k) t -= IA[sidx(i, k)] * IA[sidx(j, k)];
+          IA[sidx(i, j)] = t * inv;
+        }
       }
-      for (int i = n - 1; i >= 0; --i) {
-        float y = s_W[i * RS + r];
-        for (int k = i + 1; k < n; ++k) y -= s_M[k * MS + i] * s_W[k * RS + r];
-        s_W[i * RS + r] = y * s_Linv[i];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        float s = -pA[i];
+#pragma unroll
+        for (int k = 0; k < i; ++k) s -= IA[sidx(i, k)] * y[k];
+        y[i] = s / IA[sidx(i, i)];
       }
-      float a = 0.f;
-      for (int i = 0; i < n; ++i) a += s_J[i * RS + r] * s_W[i * RS + r];
-      const bool act = a > 1e-12f;
-      s_row[3 * RC + r] = act ? 1.f / a : 0.f;
-      s_row[4 * RC + r] = act ? s_cache[s_rowi[6 * RC + r]] : 0.f;
+#pragma unroll
+      for (int i = 5; i >= 0; --i) {
+        float s = y[i];
+#pragma unroll
+        for (int k = i + 1; k < 6; ++k) s -= IA[sidx(k, i)] * acc[k];
+        acc[i] = s / IA[sidx(i, i)];
+      }
+    }
+    for (int d = 1; d <= maxdepth; ++d) {
+      float ap[6];
+      const int src = par >= 0 ? par : lane;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) ap[k] = Grp<G>::get(acc[k], src);
+      if (dep == d) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) acc[k] = ap[k] + cc[k];
+        if (has_dof) {
+          float ua = 0.f;
+#pragma unroll
+          for (int k = 0; k < 6; ++k) ua += U[k] * acc[k];
+          qdd = (uu - ua) * Dinv;
+#pragma unroll
+          for (int k = 0; k < 6; ++k) acc[k] += Sa[k] * qdd;
+        }
+      }
+    }
+    // generalized velocity and its rate (root: nu_dot = a0 - [0; p_dot x omega])
+    if (has_dof) { s_qdd[gd] = qdd; s_v0[gd] = qd; }
+    if (free_root) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) { s_qdd[gd + k] = acc[k] - cc[k]; s_v0[gd + k] = vs[k]; }
     }
     __syncwarp();
 
-    // ======== (a6) TGS-style projected Gauss-Seidel (DOF mode) ========
-    float v = 0.f, dq = 0.f;
-    if (isg) {
-      v = s_v0[lane] + h * s_qdd[lane];
-      for (int r = 0; r < R; ++r) v += s_W[lane * RS + r] * s_row[4 * RC + r];
+    // ======== joint-space inertia (rows in registers) and its Cholesky factor (DOF mode) ========
+    {
+      float m[G];
+      const int gl = isg ? T->dof_link[lane] : 0;
+      const unsigned anc = isg ? T->anc[gl] : 0u;
+      float F[6];
+      {
+        const float* ic = s_link + kLinkWords * gl + 27;
+        const float mm_ = ic[0];
+        const V3 hh = v3(ic[1], ic[2], ic[3]);
+        const float* Sg = s_SD + 6 * (isg ? lane : 0);
+        const V3 w = v3(Sg[0], Sg[1], Sg[2]), vl = v3(Sg[3], Sg[4], Sg[5]);
+        const V3 Iw = v3(ic[4] * w.x + ic[7] * w.y + ic[8] * w.z, ic[7] * w.x + ic[5] * w.y + ic[9] * w.z,
+                         ic[8] * w.x + ic[9] * w.y + ic[6] * w.z);
+        const V3 Fa = Iw + cross(hh, vl), Fl = vl * mm_ + cross(w, hh);
+        F[0] = Fa.x; F[1] = Fa.y; F[2] = Fa.z; F[3] = Fl.x; F[4] = Fl.y; F[5] = Fl.z;
+      }
+      const float arm = (isg && T->dof_comp[lane] < 0) ? T->armature[gl] : 0.f;
+#pragma unroll
+      for (int j = 0; j < G; ++j) {
+        float mij = 0.f;
+        if (j < n && j <= lane && ((anc >> j) & 1u)) {
+          const float* Sj = s_SD + 6 * j;
+#pragma unroll
+          for (int k = 0; k < 6; ++k) mij += Sj[k] * F[k];
+        }
+        if (j == lane) mij += arm;
+        m[j] = mij;
+      }
+      // right-looking Cholesky, lane i owns row i: L_ik = M_ik / L_kk, M_ij -= L_ik L_jk
+      float linv = 1.f;
+#pragma unroll
+      for (int k = 0; k < G; ++k) {
+        if (k < n) {
+          float dkk = Grp<G>::get(m[k], k);
+          if (!(dkk > 0.f)) { status |= 2; dkk = 1.f; }
+          const float lkk = sqrtf(dkk), inv = 1.f / lkk;
+          const float lik = (lane > k) ? m[k] * inv : ((lane == k) ? lkk : 0.f);
+          m[k] = lik;
+          if (lane == k) linv = inv;
+#pragma unroll
+          for (int j = k + 1; j < G; ++j) {
+            const float ljk = Grp<G>::get(lik, j);
+            if (j <= lane) m[j] -= lik * ljk;
+          }
+        }
+      }
+      if (isg) {
+#pragma unroll
+        for (int j = 0; j < G; ++j)
+          if (j <= lane) s_M[lane * MS + j] = m[j];
+        s_Linv[lane] = linv;
+      }
     }
+    __syncwarp();
+
+    // ======== (a5) Jacobian rows and Y = L^-1 J^T, A = |Y_r|^2, warm start (row mode) ========
+    for (int r = lane; r < R; r += G) {
+      const float4 hc = s_rowc[r];
+      const int a = s_rowa[r];
+      const int kind = __float_as_int(hc.z) & 3;
+      float fr[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      unsigned anc = 0u;
+      int gl = -1;
+      float sgn = 0.f;
+      if (kind == kRowLimit) {
+        gl = a & 0xff;
+        sgn = ((a >> 8) & 1) ? -1.f : 1.f;
+      } else {
+        const int c = a & 0xff, dir = (a >> 8) & 3;
+        anc = T->anc[s_coni[5 * CC + c]];
+        const V3 x = v3(s_con[0 * CC + c], s_con[1 * CC + c], s_con[2 * CC + c]);
+        // k = e_z (dir 0), e_x (dir 1), e_y (dir 2); f = [x x k; k]
+        if (dir == 0) { fr[0] = x.y; fr[1] = -x.x; fr[5] = 1.f; }
+        else if (dir == 1) { fr[1] = x.z; fr[2] = -x.y; fr[3] = 1.f; }
+        else { fr[0] = -x.z; fr[2] = x.x; fr[4] = 1.f; }
+      }
+      float y[G];
+      float asum = 0.f;
+#pragma unroll
+      for (int i = 0; i < G; ++i) {
+        if (i < n) {
+          float ji = 0.f;
+          if (kind == kRowLimit) {
+            ji = (i == gl) ? sgn : 0.f;
+          } else if ((anc >> i) & 1u) {
+            const float* Si = s_SD + 6 * i;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) ji += Si[k] * fr[k];
+          }
+#pragma unroll
+          for (int k = 0; k < i; ++k) ji -= s_M[i * MS + k] * y[k];
+          y[i] = ji * s_Linv[i];
+          s_Y[i * RS + r] = y[i];
+          asum += y[i] * y[i];
+        } else {
+          y[i] = 0.f;
+        }
+      }
+      const bool act = asum > 1e-12f;
+      const float invA = act ? 1.f / asum : 0.f;
+      s_rowc[r].y = invA;
+      s_lam[r] = act ? s_cache[__float_as_int(hc.w)] : 0.f;
+    }
+    __syncwarp();
+
+    // ======== (a6) TGS-style projected Gauss-Seidel in z = L^T v (DOF mode) ========
+    float z = 0.f, dz = 0.f;
+    if (isg) s_vf[lane] = s_v0[lane] + h * s_qdd[lane];  // v_free
+    __syncwarp();
+    if (isg) {
+      for (int k = lane; k < n; ++k) z += s_M[k * MS + lane] * s_vf[k];  // z = L^T v_free
+      for (int r = 0; r < R; ++r) z += s_Y[lane * RS + r] * s_lam[r];     // warm start
+    }
+    const int Rw_max = __reduce_max_sync(kFull, R);
     {
       const float inv_hit = 1.f / hit, inv_h = 1.f / h;
       const float beta = A.bias_coef, vmax = A.max_depen_vel;
       for (int it = 0; it < npos + nvel; ++it) {
         const bool pos = it < npos;
+        float ny = (isg && 0 < R) ? s_Y[lane * RS] : 0.f;
+        float4 nc = s_rowc[0];
         for (int r = 0; r < Rw_max; ++r) {
-          const bool rv = r < R;
-          float jj = 0.f, ww = 0.f;
-          if (rv && isg) { jj = s_J[lane * RS + r]; ww = s_W[lane * RS + r]; }
-          const float jv = Grp<G>::sum(jj * v);
-          const float jdq = Grp<G>::sum(jj * dq);
-          if (rv) {
-            const float invA = s_row[3 * RC + r];
-            if (invA > 0.f) {
-              const int kind = s_rowi[0 * RC + r];
-              const float lam = s_row[4 * RC + r];
-              float lnew;
-              if (kind == kRowFriction) {
-                const int c = s_rowi[1 * RC + r] & 0xffff;
-                const float lim = s_row[5 * RC + r] * s_row[4 * RC + (n_lim + c)];
-                lnew = fminf(fmaxf(lam - jv * invA, -lim), lim);
-              } else {
-                const float sep = s_row[2 * RC + r] + jdq;
-                float target;
-                if (pos) target = (sep >= 0.f) ? -sep * inv_hit : fminf(-beta * sep * inv_hit, vmax);
-                else target = (sep > 0.f) ? -sep * inv_h : 0.f;
-                lnew = fmaxf(lam + (target - jv) * invA, 0.f);
-              }
-              v += ww * (lnew - lam);
-              s_row[4 * RC + r] = lnew;  // every lane stores the same value
+          const float y = ny;
+          const float4 hc = nc;
+          if (r + 1 < Rw_max) {  // prefetch the next row before this row's impulse is stored
+            ny = (isg && r + 1 < R) ? s_Y[lane * RS + r + 1] : 0.f;
+            nc = s_rowc[min(r + 1, RC - 1)];
+          }
+          const float yz = Grp<G>::sum(y * z);
+          const float ydz = Grp<G>::sum(y * dz);
+          if (r < R && hc.y > 0.f) {
+            const int kb = __float_as_int(hc.z);
+            const float lam = s_lam[r];
+            float lnew;
+            if ((kb & 3) == kRowFriction) {
+              const float lim = hc.x * s_lam[kb >> 2];
+              lnew = fminf(fmaxf(lam - yz * hc.y, -lim), lim);
+            } else {
+              const float sep = hc.x + ydz;
+              float target;
+              if (pos) target = (sep >= 0.f) ? -sep * inv_hit : fminf(-beta * sep * inv_hit, vmax);
+              else target = (sep > 0.f) ? -sep * inv_h : 0.f;
+              lnew = fmaxf(lam + (target - yz) * hc.y, 0.f);
             }
+            z += y * (lnew - lam);
+            s_lam[r] = lnew;  // every lane stores the same value
           }
         }
-        if (pos) dq += hit * v;
+        if (pos) dz += hit * z;
       }
     }
-    if (isg) { s_vf[lane] = v; s_dq[lane] = dq; }
+    // back to joint space: v = L^-T z, dq = L^-T dz (lane k finalises DOF k, highest first)
+    {
+      float bz = z, bd = dz, xz = 0.f, xd = 0.f;
+      for (int k = n - 1; k >= 0; --k) {
+        const float li = s_Linv[k];
+        const float xzk = Grp<G>::get(bz * li, k), xdk = Grp<G>::get(bd * li, k);
+        if (lane == k) { xz = xzk; xd = xdk; }
+        if (lane < k) {
+          const float lki = s_M[k * MS + lane];
+          bz -= lki * xzk;
+          bd -= lki * xdk;
+        }
+      }
+      if (isg) { s_vf[lane] = xz; s_dq[lane] = xd; }
+    }
     __syncwarp();
 
     // ======== impulse cache, contact impulses per link ========
     for (int i = lane; i < T->cache_len; i += G) s_cache[i] = 0.f;
     __syncwarp();
-    for (int r = lane; r < R; r += G) s_cache[s_rowi[6 * RC + r]] = s_row[4 * RC + r];
+    for (int r = lane; r < R; r += G) s_cache[__float_as_int(s_rowc[r].w)] = s_lam[r];
     if (isl) {
       float fx = 0.f, fy = 0.f, fz = 0.f;
       for (int c = 0; c < n_con; ++c) {
         if (s_coni[5 * CC + c] == l) {
-          fz += s_row[4 * RC + (n_lim + c)];
-          fx += s_row[4 * RC + (n_lim + n_con + 2 * c)];
-          fy += s_row[4 * RC + (n_lim + n_con + 2 * c + 1)];
+          fz += s_lam[n_lim + c];
+          fx += s_lam[n_lim + n_con + 2 * c];
+          fy += s_lam[n_lim + n_con + 2 * c + 1];
         }
       }
       s_frc[3 * l] += fx; s_frc[3 * l + 1] += fy; s_frc[3 * l + 2] += fz;
@@ -726,11 +775,11 @@ __global__ void __launch_bounds__(128) step_kernel(const StepArgs A) {
         e[0] = da.x * s; e[1] = da.y * s; e[2] = da.z * s; e[3] = cs;
       }
       const float x = e[3] * rq[0] + e[0] * rq[3] + e[1] * rq[2] - e[2] * rq[1];
-      const float y = e[3] * rq[1] - e[0] * rq[2] + e[1] * rq[3] + e[2] * rq[0];
-      const float z = e[3] * rq[2] + e[0] * rq[1] - e[1] * rq[0] + e[2] * rq[3];
+      const float yq = e[3] * rq[1] - e[0] * rq[2] + e[1] * rq[3] + e[2] * rq[0];
+      const float zq = e[3] * rq[2] + e[0] * rq[1] - e[1] * rq[0] + e[2] * rq[3];
       const float w = e[3] * rq[3] - e[0] * rq[0] - e[1] * rq[1] - e[2] * rq[2];
-      const float nr = sqrtf(x * x + y * y + z * z + w * w);
-      rq[0] = x / nr; rq[1] = y / nr; rq[2] = z / nr; rq[3] = w / nr;
+      const float nr = sqrtf(x * x + yq * yq + zq * zq + w * w);
+      rq[0] = x / nr; rq[1] = yq / nr; rq[2] = zq / nr; rq[3] = w / nr;
     }
     __syncwarp();
   }  // substeps

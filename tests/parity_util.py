@@ -75,7 +75,7 @@ def _ulp(a, direction):
     return np.nextafter(a.astype(np.float32), np.float32(direction * np.inf)).astype(np.float64)
 
 
-def fp32_scales(w, root, dof, acts, steps):
+def fp32_scales(w, root, dof, acts, steps, rtol=1e-4, atol=1e-5):
     """Per step, tensor and env: the largest deviation from the FP64 oracle of four single-precision
     evaluations of the same oracle algorithm (inputs as given, and nudged by one float32 ulp in
     three patterns). This is the env's FP32 conditioning scale: how far any faithful FP32
@@ -109,7 +109,7 @@ def fp32_scales(w, root, dof, acts, steps):
                     s[e] = max(np.abs(run[k][key][sl] - base[k][key][sl]).max() for run in runs)
             sk[key] = s
         sk["strict_frac"] = {key: float(np.mean(np.abs(runs[0][k][key] - base[k][key]) <=
-                                               1e-5 + 1e-4 * np.abs(base[k][key]))) if base[k][key].size else 1.0
+                                               atol + rtol * np.abs(base[k][key]))) if base[k][key].size else 1.0
                              for key in per}
         scales.append(sk)
     return base, scales
