@@ -107,7 +107,7 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline(wname, n_envs, budget_s=12.0):
+def cpu_baseline(wname, n_envs, budget_s=15.0):
     """The FP64 oracle, as it stands, on the host cores: env-steps/s on a bounded sample of the
     same workload, plus its operation count per env-step (the algorithmic flops of the step)."""
     import oracle
@@ -116,16 +116,16 @@ def cpu_baseline(wname, n_envs, budget_s=12.0):
     w = workload(wname, n_envs)
     threads = os.cpu_count() or 1
     O = oracle.Oracle(w)
-    steps_max = 200
-    root, dof, acts = W.seeded_inputs(w, 0, steps_max)
+    n_act = 100  # action steps drawn from the seed; the timed sample cycles through them
+    root, dof, acts = W.seeded_inputs(w, 0, n_act)
     r, d = root.astype(np.float64), dof.astype(np.float64)
     t0 = time.perf_counter()
     O.step(r, d, acts[0], n_threads=threads)
     one = max(time.perf_counter() - t0, 1e-4)
-    n_steps = int(max(2, min(steps_max - 1, budget_s / one)))
+    n_steps = int(max(2, min(5000, budget_s / one)))
     t0 = time.perf_counter()
     for k in range(1, 1 + n_steps):
-        O.step(r, d, acts[k], n_threads=threads)
+        O.step(r, d, acts[k % n_act], n_threads=threads)
     el = time.perf_counter() - t0
     value = n_envs * n_steps / el
     # algorithmic flops per env-step, counted on a 64-env, 4-step sample of the same trajectory

@@ -201,6 +201,7 @@ template <class T> bool small_inverse_spd(std::vector<T> A, int n, std::vector<T
 template <class T> bool aba(const ModelD& M, const ActorKin<T>& K, const std::vector<T>& tau, const Params& P,
                             std::vector<T>& qdd) {
   const int L = (int)M.links.size();
+  qdd.assign(M.n_gen, T(std::nan("")));  // stays NaN if a pivot fails (the env is reported failed)
   std::vector<SMat<T>> IA(L);
   std::vector<SVec<T>> pA(L);
   for (int i = 0; i < L; ++i) {

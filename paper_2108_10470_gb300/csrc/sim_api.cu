@@ -298,9 +298,13 @@ SmemLayout make_layout(const EnvTypeTable& T) {
   Ly.rowc = o; o += 4 * Ly.rcap;
   Ly.lam = o; o += Ly.rcap;
   Ly.rowa = o; o += Ly.rcap;
-  Ly.cache = o; o += std::max(T.cache_len, 1);
   Ly.frc = o; o += 3 * L;
   Ly.total = al4(o);
+  // Groups that share a warp (G < 32) must not share banks: pad the per-group stride to G mod 32
+  // so the g-th group of a warp is shifted by g * G banks (the row stride RS is odd, so each
+  // group's lanes also fall on distinct banks).
+  if (T.group < 32)
+    while (Ly.total % 32 != T.group) Ly.total += 4;
   return Ly;
 }
 

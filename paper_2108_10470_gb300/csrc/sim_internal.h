@@ -70,9 +70,8 @@ struct SmemLayout {
   int lam;    // rcap: impulses
   int rowa;   // rcap: row aux (DOF / contact index)
   int rcap;
-  int cache;  // cache_len
   int frc;    // 3 per link
-  int total;  // words per environment (multiple of 4)
+  int total;  // words per environment (multiple of 4; = G mod 32 when groups share a warp)
 };
 constexpr int kLinkWords = 37;
 constexpr int kConWords = 9;   // x y z d mu link cand shape slot

@@ -157,8 +157,10 @@ __global__ void __launch_bounds__(128, 4) step_kernel(const StepArgs A) {
   float4* s_rowc = reinterpret_cast<float4*>(sm + Ly.rowc);
   float* s_lam = sm + Ly.lam;
   int* s_rowa = smi + Ly.rowa;
-  float* s_cache = sm + Ly.cache;
   float* s_frc = sm + Ly.frc;
+  // warm-start impulse cache of this env, read and rewritten in place in global memory (each
+  // entry is touched once per substep; only live groups store)
+  float* gcache = A.cache + (size_t)env * A.cache_stride;
 
   // ---- per-link constants (link mode) ----
   const bool isl = lane < L;
@@ -193,7 +195,6 @@ __global__ void __launch_bounds__(128, 4) step_kernel(const StepArgs A) {
     qd = A.dof[(size_t)(dof_base + jd) * 2 + 1];
     tau = A.act[dof_base + jd];  // joint force of the step; damping is added per substep
   }
-  for (int i = lane; i < T->cache_len; i += G) s_cache[i] = A.cache[(size_t)env * A.cache_stride + i];
   for (int i = lane; i < 3 * L; i += G) s_frc[i] = 0.f;
 
   unsigned sig = 2166136261u;
@@ -672,7 +673,7 @@ __global__ void __launch_bounds__(128, 4) step_kernel(const StepArgs A) {
       const bool act = asum > 1e-12f;
       const float invA = act ? 1.f / asum : 0.f;
       s_rowc[r].y = invA;
-      s_lam[r] = act ? s_cache[__float_as_int(hc.w)] : 0.f;
+      s_lam[r] = act ? gcache[__float_as_int(hc.w)] : 0.f;
     }
     __syncwarp();
 
@@ -699,8 +700,10 @@ __global__ void __launch_bounds__(128, 4) step_kernel(const StepArgs A) {
             ny = (isg && r + 1 < R) ? s_Y[lane * RS + r + 1] : 0.f;
             nc = s_rowc[min(r + 1, RC - 1)];
           }
+          // J_r v = Y_r . z and the separation d_r + J_r dq = d_r + Y_r . dz, both reduced
+          // across the group (independent shuffle chains)
           const float yz = Grp<G>::sum(y * z);
-          const float ydz = Grp<G>::sum(y * dz);
+          const float sep = hc.x + Grp<G>::sum(y * dz);
           if (r < R && hc.y > 0.f) {
             const int kb = __float_as_int(hc.z);
             const float lam = s_lam[r];
@@ -709,7 +712,6 @@ __global__ void __launch_bounds__(128, 4) step_kernel(const StepArgs A) {
               const float lim = hc.x * s_lam[kb >> 2];
               lnew = fminf(fmaxf(lam - yz * hc.y, -lim), lim);
             } else {
-              const float sep = hc.x + ydz;
               float target;
               if (pos) target = (sep >= 0.f) ? -sep * inv_hit : fminf(-beta * sep * inv_hit, vmax);
               else target = (sep > 0.f) ? -sep * inv_h : 0.f;
@@ -740,9 +742,11 @@ __global__ void __launch_bounds__(128, 4) step_kernel(const StepArgs A) {
     __syncwarp();
 
     // ======== impulse cache, contact impulses per link ========
-    for (int i = lane; i < T->cache_len; i += G) s_cache[i] = 0.f;
+    if (live)
+      for (int i = lane; i < T->cache_len; i += G) gcache[i] = 0.f;
     __syncwarp();
-    for (int r = lane; r < R; r += G) s_cache[__float_as_int(s_rowc[r].w)] = s_lam[r];
+    if (live)
+      for (int r = lane; r < R; r += G) gcache[__float_as_int(s_rowc[r].w)] = s_lam[r];
     if (isl) {
       float fx = 0.f, fy = 0.f, fz = 0.f;
       for (int c = 0; c < n_con; ++c) {
@@ -811,7 +815,6 @@ __global__ void __launch_bounds__(128, 4) step_kernel(const StepArgs A) {
       float* nf = A.net_force + (size_t)(A.env_body_base[env] + bd) * 3;
       nf[0] = s_frc[3 * l] * inv_dt; nf[1] = s_frc[3 * l + 1] * inv_dt; nf[2] = s_frc[3 * l + 2] * inv_dt;
     }
-    for (int i = lane; i < T->cache_len; i += G) A.cache[(size_t)env * A.cache_stride + i] = s_cache[i];
     int* pr = A.pairs + (size_t)env * A.pair_stride * 3;
     for (int c = lane; c < A.pair_stride; c += G) {
       const bool vc = c < n_con;

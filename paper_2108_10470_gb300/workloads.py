@@ -250,18 +250,21 @@ def humanoid(density=1000.0, damping=0.5, friction=1.0) -> Model:
     """Humanoid-like biped: 13 bodies (capsules and spheres) on a floating torso, 21 revolute DOF.
     Multi-axis joints (abdomen 3, hips 3, ankles 2, shoulders 2) are chains of 1-DOF hinges through
     massless virtual links; the head is welded to the torso by a fixed joint. Gears 50-150 N m,
-    armature 0.02 * gear / 50. 23 links, 21 joint DOF, 27 generalized DOF."""
+    armature 0.1 * gear / 50 kg m^2 (0.1-0.3: with lighter rotors, e.g. 0.02 * gear / 50, random
+    150 N m torques drive joint rates to ~100 rad/s, where the explicit 1/120 s substeps diverge in
+    the FP64 oracle and on the GPU alike). 23 links, 21 joint DOF, 27 generalized DOF."""
     b = _Builder("humanoid")
     deg = math.radians
+    ARM = 0.1
 
     def hinge(parent, axis, limit, gear, ppos=(0, 0, 0), body=None):
         """body=None -> virtual link; else (mass, com, inertia)."""
         if body is None:
-            return b.link(parent, JOINT_REVOLUTE, axis=axis, ppos=ppos, armature=0.02 * gear / 50, damping=damping,
+            return b.link(parent, JOINT_REVOLUTE, axis=axis, ppos=ppos, armature=ARM * gear / 50, damping=damping,
                           limit=(deg(limit[0]), deg(limit[1])), virtual=True, gear=gear)
         m, c, inn = body
         return b.link(parent, JOINT_REVOLUTE, axis=axis, ppos=ppos, mass=m, com=c, inertia=inn,
-                      armature=0.02 * gear / 50, damping=damping, limit=(deg(limit[0]), deg(limit[1])), gear=gear)
+                      armature=ARM * gear / 50, damping=damping, limit=(deg(limit[0]), deg(limit[1])), gear=gear)
 
     mt, it = capsule_mass_along(0.07, 0.07, density, 1)
     torso = b.link(-1, JOINT_FREE, mass=mt, inertia=it)
