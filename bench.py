@@ -30,6 +30,14 @@ sys.path.insert(0, ROOT)
 
 SM_COUNT_NOMINAL = 152
 FP32_LANES_PER_SM = 128
+# HBM bytes one env-step must move: root (13 f32) + DOF (2 per joint) + actuation (1 per joint)
+# + impulse cache read; root + DOF + net contact force (3 per body) + impulse cache + contact
+# pairs (3 i32 per candidate) + count / status / signature written.
+ALGO_BYTES_PER_ENV_STEP = {
+    "ant": 4 * ((13 + 16 + 8 + 67) + (13 + 16 + 27 + 67 + 51 + 3)),
+    "humanoid": 4 * ((13 + 42 + 21 + 114) + (13 + 42 + 39 + 114 + 72 + 3)),
+    "cartpole": 4 * ((13 + 4 + 2) + (13 + 4 + 9 + 3)),
+}
 
 
 def baseline_metric():
@@ -38,6 +46,42 @@ def baseline_metric():
             return json.load(f)["metric"]
     except Exception:
         return "env-steps/sec on 1 GB300 (Ant-like, 4096 envs)"
+
+
+def max_over_ranks(x: float, world: int, device="cpu") -> float:
+    """Slowest rank's time (all ranks call this; a no-op on one rank)."""
+    if world <= 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_seed(rank: int) -> int:
+    """Each rank simulates its own environments from its own seed (weak scaling)."""
+    return 1000 * rank
+
+
+def weak_value(world: int, n_envs: int, steps: int, seconds: float) -> float:
+    """Whole-job env-steps/s: every rank advanced n_envs envs by `steps` steps."""
+    return world * n_envs * steps / seconds
+
+
+def profiled_traffic(wname: str, n_envs: int):
+    """DRAM bytes (read + write) per step-kernel launch from the committed ncu summary of this
+    workload, scaled to n_envs; None if there is none or the kernel source changed since."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"step_kernel_{wname}4096.md")
+    src = os.path.join(ROOT, "paper_2108_10470_gb300", "csrc", "step_kernel.cuh")
+    try:
+        fields = dict(ln.split(":", 1) for ln in open(path).read().splitlines()[:4] if ":" in ln)
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if fields.get("kernel_source_sha256_16", "").strip() != sha:
+            return None
+        return float(fields["traffic_bytes_per_launch"]) * n_envs / 4096.0
+    except Exception:
+        return None
 
 
 def workload(name, n_envs):
@@ -183,7 +227,7 @@ def run_ours(args, rank, world, local_rank):
     K, Wm = args.steps, args.warmup
     s = sim.Sim(w)
     stream = torch.cuda.current_stream()
-    root, dof, acts = W.seeded_inputs(w, 1000 * rank, Wm + K)
+    root, dof, acts = W.seeded_inputs(w, rank_seed(rank), Wm + K)
     s.root_state.copy_(torch.from_numpy(root))
     s.dof_state.copy_(torch.from_numpy(dof))
     act_dev = torch.from_numpy(acts).to(dev)  # every step's actions resident in HBM
@@ -210,11 +254,7 @@ def run_ours(args, rank, world, local_rank):
         torch.distributed.barrier()
     step_ms = [ev[k][0].elapsed_time(ev[k][2]) for k in range(K)]
     kern_ms = [ev[k][1].elapsed_time(ev[k][2]) for k in range(K)]
-    total_s = sum(step_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([total_s], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
+    total_s = max_over_ranks(sum(step_ms) / 1e3, world, dev)
     bad = s.sync_status()
     # end-to-end through the C ABI with pinned host buffers (copies inside the timed region)
     n_e2e = min(K, 200)
@@ -227,17 +267,13 @@ def run_ours(args, rank, world, local_rank):
     t0 = time.perf_counter()
     for k in range(n_e2e):
         s.step_host(h_act[k], h_root, h_dof)
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
     launches = s.launches_per_step * K
     n_d, n_a = s.N_D, s.N_A
     s.destroy()
     if rank != 0:
         return
-    value = world * w.n_envs * K / total_s
+    value = weak_value(world, w.n_envs, K, total_s)
     clocks = clk.summary()
     line = {"metric": baseline_metric(), "value": value, "unit": "env-steps/s", "n_gpus": world, "steps": K,
             "warmup": Wm, "ms_per_step": 1e3 * total_s / K, "higher_is_better": True, "scaling": "weak",
@@ -247,7 +283,7 @@ def run_ours(args, rank, world, local_rank):
                        "parallelism": f"replicas x{world} (independent envs per GPU)"},
             "gpu_launches": launches, "nonfinite_envs": bad,
             "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
-            "e2e": {"value": world * w.n_envs * n_e2e / e2e_s, "unit": "env-steps/s",
+            "e2e": {"value": weak_value(world, w.n_envs, n_e2e, e2e_s), "unit": "env-steps/s",
                     "h2d_bytes_per_step": 4 * n_d, "d2h_bytes_per_step": 4 * (13 * n_a + 2 * n_d),
                     "api": "sim_step_host (pinned host actuation in, root + DOF state out, stream sync)"}}
     kern_avg_s = statistics.mean(kern_ms) / 1e3
@@ -259,7 +295,10 @@ def run_ours(args, rank, world, local_rank):
         peak = SM_COUNT_NOMINAL * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6
         achieved = flops_per_env_step * w.n_envs / kern_avg_s
         roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": args.traffic,
+                "frac": achieved / peak,
+                "traffic": args.traffic if args.traffic is not None else profiled_traffic(args.workload, w.n_envs),
+                "algorithmic_bytes_per_launch": ALGO_BYTES_PER_ENV_STEP.get(args.workload, None) and
+                ALGO_BYTES_PER_ENV_STEP[args.workload] * w.n_envs,
                 "kernel": "step_kernel", "kernel_ms": 1e3 * kern_avg_s,
                 "flops_per_env_step": flops_per_env_step,
                 "peak_basis": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (median SM clock sampled "
