@@ -69,6 +69,8 @@ def lib():
         L.oracle_step_flops.restype = ctypes.c_double
         L.oracle_step_f32.argtypes = [ctypes.c_void_p, D, D, D, D, ctypes.c_double, ctypes.c_int32, D]
         L.oracle_step_f32.restype = ctypes.c_int32
+        L.oracle_capsule_box.argtypes = [D, D, ctypes.c_double, D, D]
+        L.oracle_capsule_box.restype = None
         for fn in ("oracle_aba", "oracle_rnea", "oracle_momentum"):
             getattr(L, fn).argtypes = [ctypes.c_void_p, ctypes.c_int32, D, D, D, D]
             getattr(L, fn).restype = ctypes.c_int32
@@ -79,10 +81,25 @@ def lib():
         L.oracle_rk4.restype = ctypes.c_int32
         L.oracle_link_pose.argtypes = [ctypes.c_void_p, ctypes.c_int32, D, D, ctypes.c_int32, D]
         L.oracle_link_pose.restype = ctypes.c_int32
-        L.oracle_rows.argtypes = [ctypes.c_void_p, ctypes.c_int32, D, D, ctypes.c_int32, D, D, I32, I32, D, D, D]
+        L.oracle_rows.argtypes = [ctypes.c_void_p, ctypes.c_int32, D, D, ctypes.c_int32, D, D, I32, I32, D, D, D,
+                                  I32]
         L.oracle_rows.restype = ctypes.c_int32
         _lib = L
     return _lib
+
+
+def capsule_box(p0, p1, r, ext):
+    """Capsule-box geometry in the box frame: t* and, for slots 0, 1, 2 (t = 0, 1, t*), the
+    normal (box -> capsule), separation and contact point."""
+    a = np.ascontiguousarray(p0, np.float64)
+    b = np.ascontiguousarray(p1, np.float64)
+    e = np.ascontiguousarray(ext, np.float64)
+    out = np.zeros(25)
+    lib().oracle_capsule_box(_dp(a), _dp(b), float(r), _dp(e), _dp(out))
+    slots = [dict(n=out[1 + 7 * s:4 + 7 * s].copy(), d=out[4 + 7 * s], x=out[5 + 7 * s:8 + 7 * s].copy())
+             for s in range(3)]
+    slots.append(dict(clip=bool(out[22]), ta=out[23], tb=out[24]))
+    return out[0], slots
 
 
 def _dp(a: np.ndarray):
@@ -238,8 +255,8 @@ class Oracle:
         n = self.ngen(env)
         J = np.zeros((cap, n)); d = np.zeros(cap); A = np.zeros(cap)
         kind = np.zeros(cap, np.int32); link = np.zeros(cap, np.int32)
-        x = np.zeros((cap, 3)); k = np.zeros((cap, 3))
+        x = np.zeros((cap, 3)); k = np.zeros((cap, 3)); info = np.zeros((cap, 3), np.int32)
         R = lib().oracle_rows(self.h, env, _dp(root), _dp(dof), cap, _dp(J), _dp(d), _ip(kind), _ip(link), _dp(x),
-                              _dp(k), _dp(A))
+                              _dp(k), _dp(A), _ip(info))
         assert R >= 0
-        return dict(J=J[:R], d=d[:R], kind=kind[:R], link=link[:R], x=x[:R], k=k[:R], A=A[:R])
+        return dict(J=J[:R], d=d[:R], kind=kind[:R], link=link[:R], x=x[:R], k=k[:R], A=A[:R], info=info[:R])

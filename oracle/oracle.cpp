@@ -64,8 +64,10 @@ struct Params {
 
 struct Oracle {
   std::vector<ModelD> models;
-  std::vector<int> env_model;  // [n_envs * actors_per_env]
-  int actors_per_env = 0, n_envs = 0;
+  std::vector<std::vector<int>> env_actors;  // per env: model index of each actor (padding dropped)
+  std::vector<int64_t> actor_off;           // per env: first row of its actors in the root tensor
+  std::vector<std::vector<std::pair<int, int>>> env_pairs;  // per env: shape-shape candidate pairs
+  int n_envs = 0;
   Params prm;
   // per env prefix offsets into the global tensors
   std::vector<int64_t> jdof_off, body_off;
@@ -73,7 +75,8 @@ struct Oracle {
   int64_t N_A = 0, N_D = 0, N_B = 0;
   int max_contact_cap = 0, max_gen = 0;
   int cache_len = 0;  // per env: 3 * contact candidates + 2 * joint DOFs (max over envs)
-  const ModelD& actor_model(int env, int a) const { return models[env_model[env * actors_per_env + a]]; }
+  const ModelD& actor_model(int env, int a) const { return models[env_actors[env][a]]; }
+  int n_act(int env) const { return (int)env_actors[env].size(); }
 };
 
 // ------------------------------------------------------------------------------------------------
@@ -321,29 +324,172 @@ template <class T> void rnea(const ModelD& M, const ActorKin<T>& K, const std::v
 // [sz>0]).
 template <class T> struct ContactPt {
   int shape_a, shape_b, slot;
-  int cand;  // env-level candidate index (shapes in order, slots within a shape)
+  int cand;  // env-level candidate index (ground candidates shape by shape, then 3 per shape pair)
   int actor_a, link_a;
-  Vec3<T> x;  // contact point (on body a)
-  T d;        // signed separation
+  int actor_b, link_b;  // -1: the ground
+  Vec3<T> x;            // contact point (world)
+  T d;                  // signed separation
   T mu;
+  Vec3<T> n, t1, t2;    // normal from b to a, friction directions
 };
 
-template <class T> void ground_contacts(const Oracle& O, int env, const std::vector<ActorKin<T>>& K,
-                                        std::vector<ContactPt<T>>& out) {
+// Friction directions for a contact normal n [reading]: anchor = e_x if |n_x| < 0.57735, else e_y if
+// |n_y| < 0.57735, else e_z; t1 = normalise(anchor - (anchor . n) n), t2 = n x t1. For the ground
+// normal e_z this gives t1 = e_x, t2 = e_y.
+template <class T> void tangent_basis(const Vec3<T>& n, Vec3<T>& t1, Vec3<T>& t2) {
+  const T lim = T(0.57735);
+  Vec3<T> an;
+  if (fabs(n[0]) < lim) an = mk3<T>(T(1.0), T(0.0), T(0.0));
+  else if (fabs(n[1]) < lim) an = mk3<T>(T(0.0), T(1.0), T(0.0));
+  else an = mk3<T>(T(0.0), T(0.0), T(1.0));
+  const Vec3<T> t = sub(an, scale(n, dot(an, n)));
+  t1 = scale(t, T(1.0) / sqrt(dot(t, t)));
+  t2 = cross(n, t1);
+}
+
+// World pose (rotation, centre) of a shape.
+template <class T> void shape_pose(const ActorKin<T>& K, const ShapeD& sh, Mat3<T>& Rs, Vec3<T>& cs) {
+  const int li = sh.link;
+  const T q[4] = {T(sh.quat[0]), T(sh.quat[1]), T(sh.quat[2]), T(sh.quat[3])};
+  Rs = mul(K.R[li], quat_to_mat<T>(q));
+  cs = add(K.p[li], mul(K.R[li], vec3_of<T>(sh.pos)));
+}
+
+// Squared distance from the point p (box frame) to the box of half extents e.
+template <class T> T box_dist2(const Vec3<T>& p, const Vec3<T>& e) {
+  T f = T(0.0);
+  for (int k = 0; k < 3; ++k) {
+    const T o = fabs(p[k]) - e[k];
+    if (T(0.0) < o) f = f + o * o;
+  }
+  return f;
+}
+
+// Exact minimiser over t in [0, 1] of the squared distance from p0 + t dv to the box (convex,
+// piecewise quadratic): split [0, 1] at the breakpoints p_k(t) = +-e_k, take each piece's
+// stationary point clamped into the piece (the piece's start if the distance is constant there),
+// and keep the smallest value, ties to the smallest t.
+template <class T> T segment_box_closest_t(const Vec3<T>& p0, const Vec3<T>& dv, const Vec3<T>& e) {
+  std::vector<T> ts = {T(0.0), T(1.0)};
+  for (int k = 0; k < 3; ++k) {
+    if (dv[k] == T(0.0)) continue;
+    for (int s = -1; s <= 1; s += 2) {
+      const T t = (T((double)s) * e[k] - p0[k]) / dv[k];
+      if (T(0.0) < t && t < T(1.0)) ts.push_back(t);
+    }
+  }
+  std::sort(ts.begin(), ts.end(), [](const T& a, const T& b) { return a < b; });
+  auto at = [&](const T& t) { return add(p0, scale(dv, t)); };
+  T best_t = T(0.0), best_f = box_dist2(at(T(0.0)), e);
+  for (size_t i = 0; i + 1 < ts.size(); ++i) {
+    const T ta = ts[i], tb = ts[i + 1];
+    const Vec3<T> pm = at((ta + tb) * T(0.5));
+    T num = T(0.0), den = T(0.0);
+    for (int k = 0; k < 3; ++k) {
+      if (!(e[k] < fabs(pm[k]))) continue;  // inside this slab on the whole piece
+      const T s = (T(0.0) < pm[k]) ? T(1.0) : T(-1.0);
+      num = num + dv[k] * (s * e[k] - p0[k]);
+      den = den + dv[k] * dv[k];
+    }
+    T t = ta;
+    if (T(0.0) < den) t = tmin(tmax(num / den, ta), tb);
+    const T f = box_dist2(at(t), e);
+    if (f < best_f) { best_f = f; best_t = t; }
+  }
+  const T f1 = box_dist2(at(T(1.0)), e);
+  if (f1 < best_f) best_t = T(1.0);
+  return best_t;
+}
+
+constexpr int kPairSlots = 5;  // capsule-box samples: t = 0, t = 1, face-clip entry / exit, closest point
+
+// The part of the segment over the box face selected by the closest point [reading]: let k be the
+// box axis along which the normal at the closest point t* is largest (ties: lowest k); clip the
+// segment to the slabs |x_j| <= e_j of the two other axes. Returns false if nothing remains,
+// else the parameter interval [ta, tb] within [0, 1]. Its ends are the extra samples that give a
+// capsule lying along a face two supporting points.
+template <class T> bool face_clip(const Vec3<T>& p0, const Vec3<T>& dv, const Vec3<T>& e, const T& r, const T& tstar,
+                                  T& ta, T& tb);
+
+// A sphere of radius r at p (box frame) against the box of half extents e: normal from the box to
+// the sphere, separation d, and the contact point halfway between the two surfaces.
+template <class T> void sphere_box(const Vec3<T>& p, const T& r, const Vec3<T>& e, Vec3<T>& n, T& d, Vec3<T>& x) {
+  bool inside = true;
+  for (int k = 0; k < 3; ++k)
+    if (e[k] < fabs(p[k])) inside = false;
+  if (!inside) {
+    Vec3<T> q;
+    for (int k = 0; k < 3; ++k) q[k] = tmin(tmax(p[k], T(0.0) - e[k]), e[k]);
+    const Vec3<T> dl = sub(p, q);
+    const T dist = sqrt(dot(dl, dl));
+    n = scale(dl, T(1.0) / dist);
+    d = dist - r;
+  } else {
+    int kb = 0;
+    T best = e[0] - fabs(p[0]);
+    for (int k = 1; k < 3; ++k)
+      if (e[k] - fabs(p[k]) < best) { best = e[k] - fabs(p[k]); kb = k; }
+    n = zero3<T>();
+    n[kb] = (p[kb] < T(0.0)) ? T(-1.0) : T(1.0);
+    d = T(0.0) - best - r;
+  }
+  x = sub(p, scale(n, r + d * T(0.5)));
+}
+
+template <class T> bool face_clip(const Vec3<T>& p0, const Vec3<T>& dv, const Vec3<T>& e, const T& r, const T& tstar,
+                                  T& ta, T& tb) {
+  Vec3<T> n, x;
+  T d;
+  sphere_box(add(p0, scale(dv, tstar)), r, e, n, d, x);
+  int kn = 0;
+  for (int k = 1; k < 3; ++k)
+    if (fabs(n[kn]) < fabs(n[k])) kn = k;
+  ta = T(0.0);
+  tb = T(1.0);
+  for (int j = 0; j < 3; ++j) {
+    if (j == kn) continue;
+    if (dv[j] == T(0.0)) {
+      if (e[j] < fabs(p0[j])) return false;
+      continue;
+    }
+    T t0 = (T(0.0) - e[j] - p0[j]) / dv[j], t1 = (e[j] - p0[j]) / dv[j];
+    if (t1 < t0) { const T s = t0; t0 = t1; t1 = s; }
+    ta = tmax(ta, t0);
+    tb = tmin(tb, t1);
+  }
+  return !(tb < ta);
+}
+
+// Contact generation at the substep-start configuration. Ground (plane z = 0, normal +z): a
+// candidate point is kept iff its separation d is strictly below the contact offset; candidates
+// are numbered shape by shape (sphere: 0; capsule: 0 = centre - h*axis, 1 = centre + h*axis; box:
+// k = 4[sx>0] + 2[sy>0] + [sz>0]). Then every capsule-box pair of shapes of different actors
+// (env-local shape indices a < b, in order): the capsule's endpoints (slots 0, 1), the ends of its
+// face clip (slots 2, 3) and the closest point of its segment to the box (slot 4), the last three
+// only if strictly inside the segment, each treated as a sphere of the capsule's radius against
+// the box.
+template <class T> void env_contacts(const Oracle& O, int env, const std::vector<ActorKin<T>>& K,
+                                     std::vector<ContactPt<T>>& out) {
   out.clear();
   const T coff = T(O.prm.contact_offset);
+  const Vec3<T> ez = mk3<T>(T(0.0), T(0.0), T(1.0)), ex = mk3<T>(T(1.0), T(0.0), T(0.0)),
+                ey = mk3<T>(T(0.0), T(1.0), T(0.0));
   int shape_base = 0, cand_base = 0;
-  for (int a = 0; a < O.actors_per_env; ++a) {
+  std::vector<std::pair<int, int>> shape_ref;  // env-local shape -> (actor, shape within actor)
+  for (int a = 0; a < O.n_act(env); ++a) {
     const ModelD& M = O.actor_model(env, a);
     for (size_t s = 0; s < M.shapes.size(); ++s) {
+      shape_ref.push_back({a, (int)s});
       const ShapeD& sh = M.shapes[s];
       const int ncand = (sh.type == SHAPE_SPHERE) ? 1 : (sh.type == SHAPE_CAPSULE ? 2 : 8);
       const int li = sh.link;
-      const Mat3<T> Rs = mul(K[a].R[li], quat_to_mat<T>(std::vector<T>{T(sh.quat[0]), T(sh.quat[1]), T(sh.quat[2]), T(sh.quat[3])}.data()));
-      const Vec3<T> cs = add(K[a].p[li], mul(K[a].R[li], vec3_of<T>(sh.pos)));
+      Mat3<T> Rs;
+      Vec3<T> cs;
+      shape_pose(K[a], sh, Rs, cs);
       const T mu = tmax(T(sh.friction), T(O.prm.ground_friction));
       auto push = [&](int slot, const Vec3<T>& x, const T& d) {
-        if (d < coff) out.push_back(ContactPt<T>{shape_base + (int)s, -1, slot, cand_base + slot, a, li, x, d, mu});
+        if (d < coff)
+          out.push_back(ContactPt<T>{shape_base + (int)s, -1, slot, cand_base + slot, a, li, -1, -1, x, d, mu, ez, ex, ey});
       };
       if (sh.type == SHAPE_SPHERE) {
         const T r = T(sh.size[0]);
@@ -366,6 +512,52 @@ template <class T> void ground_contacts(const Oracle& O, int env, const std::vec
       cand_base += ncand;
     }
     shape_base += (int)M.shapes.size();
+  }
+  // capsule-box pairs
+  for (size_t pi = 0; pi < O.env_pairs[env].size(); ++pi) {
+    const int sa = O.env_pairs[env][pi].first, sb = O.env_pairs[env][pi].second;
+    const int aa = shape_ref[sa].first, ab = shape_ref[sb].first;
+    const ShapeD& sha = O.actor_model(env, aa).shapes[shape_ref[sa].second];
+    const ShapeD& shb = O.actor_model(env, ab).shapes[shape_ref[sb].second];
+    const bool a_is_capsule = sha.type == SHAPE_CAPSULE;
+    const ShapeD& cap = a_is_capsule ? sha : shb;
+    const ShapeD& box = a_is_capsule ? shb : sha;
+    Mat3<T> Rc, Rb;
+    Vec3<T> cc, cb;
+    shape_pose(K[a_is_capsule ? aa : ab], cap, Rc, cc);
+    shape_pose(K[a_is_capsule ? ab : aa], box, Rb, cb);
+    const T r = T(cap.size[0]), hl = T(cap.size[1]);
+    const Vec3<T> ax = mk3<T>(Rc(0, 0), Rc(1, 0), Rc(2, 0));
+    const Mat3<T> RbT = transpose(Rb);
+    const Vec3<T> p0 = mul(RbT, sub(sub(cc, scale(ax, hl)), cb));
+    const Vec3<T> p1 = mul(RbT, sub(add(cc, scale(ax, hl)), cb));
+    const Vec3<T> dv = sub(p1, p0);
+    const Vec3<T> ext = vec3_of<T>(box.size);
+    const T tstar = segment_box_closest_t(p0, dv, ext);
+    T ta, tb;
+    const bool clip = face_clip(p0, dv, ext, r, tstar, ta, tb);
+    const T mu = tmax(T(sha.friction), T(shb.friction));
+    for (int slot = 0; slot < kPairSlots; ++slot) {
+      T t;
+      if (slot == 0) t = T(0.0);
+      else if (slot == 1) t = T(1.0);
+      else {
+        t = (slot == 2) ? ta : ((slot == 3) ? tb : tstar);
+        if (slot < 4 && !clip) continue;
+        if (slot == 3 && !(ta < tb)) continue;
+        if (!(T(0.0) < t && t < T(1.0))) continue;
+      }
+      Vec3<T> nb, xb;
+      T d;
+      sphere_box(add(p0, scale(dv, t)), r, ext, nb, d, xb);
+      if (!(d < coff)) continue;
+      Vec3<T> n = mul(Rb, nb);  // from the box to the capsule
+      if (!a_is_capsule) n = scale(n, T(-1.0));
+      ContactPt<T> c{sa, sb, slot, cand_base + kPairSlots * (int)pi + slot, aa, sha.link, ab, shb.link,
+                     add(cb, mul(Rb, xb)), d, mu, n, n, n};
+      tangent_basis(n, c.t1, c.t2);
+      out.push_back(c);
+    }
   }
 }
 
@@ -401,7 +593,7 @@ struct EnvLayout {
 inline EnvLayout env_layout(const Oracle& O, int env) {
   EnvLayout E;
   int g = 0, b = 0;
-  for (int a = 0; a < O.actors_per_env; ++a) {
+  for (int a = 0; a < O.n_act(env); ++a) {
     const ModelD& M = O.actor_model(env, a);
     E.gen_off.push_back(g);
     E.body_off.push_back(b);
@@ -448,7 +640,7 @@ template <class T> void build_rows(const Oracle& O, int env, const EnvLayout& E,
   const T margin = T(O.prm.limit_margin);
   std::vector<int32_t> lim_ids;
   int jbase = 0;
-  for (int a = 0; a < O.actors_per_env; ++a) {
+  for (int a = 0; a < O.n_act(env); ++a) {
     const ModelD& M = O.actor_model(env, a);
     for (size_t l = 0; l < M.links.size(); ++l) {
       const LinkD& lk = M.links[l];
@@ -480,19 +672,23 @@ template <class T> void build_rows(const Oracle& O, int env, const EnvLayout& E,
     fnv1a_int(*sig, (int32_t)C.size());
     for (const auto& c : C) { fnv1a_int(*sig, c.shape_a); fnv1a_int(*sig, c.shape_b); fnv1a_int(*sig, c.slot); }
   }
-  const Vec3<T> ez = mk3<T>(T(0.0), T(0.0), T(1.0)), ex = mk3<T>(T(1.0), T(0.0), T(0.0)), ey = mk3<T>(T(0.0), T(1.0), T(0.0));
+  // J = k . d(x_dot on body a)/d(nu) - k . d(x_dot on body b)/d(nu) at the contact point
+  auto contact_row = [&](const ContactPt<T>& c, const Vec3<T>& k, std::vector<T>& J) {
+    point_row(O, env, E, K, c.actor_a, c.link_a, c.x, k, T(1.0), J);
+    if (c.actor_b >= 0) point_row(O, env, E, K, c.actor_b, c.link_b, c.x, k, T(-1.0), J);
+  };
   const int first_normal = (int)rows.size();
   for (size_t c = 0; c < C.size(); ++c) {
-    Row<T> r{ROW_NORMAL, std::vector<T>(n, T(0.0)), C[c].d, -1, C[c].mu, (int)c, ez, {}, T(0.0), 3 * C[c].cand};
-    point_row(O, env, E, K, C[c].actor_a, C[c].link_a, C[c].x, ez, T(1.0), r.J);
+    Row<T> r{ROW_NORMAL, std::vector<T>(n, T(0.0)), C[c].d, -1, C[c].mu, (int)c, C[c].n, {}, T(0.0), 3 * C[c].cand};
+    contact_row(C[c], C[c].n, r.J);
     rows.push_back(r);
   }
   for (size_t c = 0; c < C.size(); ++c) {
     for (int t = 0; t < 2; ++t) {
-      const Vec3<T> k = (t == 0) ? ex : ey;
+      const Vec3<T> k = (t == 0) ? C[c].t1 : C[c].t2;
       Row<T> r{ROW_FRICTION, std::vector<T>(n, T(0.0)), T(0.0), first_normal + (int)c, C[c].mu, (int)c, k, {}, T(0.0),
                3 * C[c].cand + 1 + t};
-      point_row(O, env, E, K, C[c].actor_a, C[c].link_a, C[c].x, k, T(1.0), r.J);
+      contact_row(C[c], k, r.J);
       rows.push_back(r);
     }
   }
@@ -502,11 +698,11 @@ template <class T> void build_rows(const Oracle& O, int env, const EnvLayout& E,
 // [p 3 | quat xyzw 4 | v 3 | omega 3], DOF state (N_D, 2) = [q, qd]).
 template <class T> void load_env(const Oracle& O, int env, const double* root, const double* dof,
                                  std::vector<ActorState<T>>& st) {
-  st.resize(O.actors_per_env);
+  st.resize(O.n_act(env));
   int64_t jd = O.jdof_off[env];
-  for (int a = 0; a < O.actors_per_env; ++a) {
+  for (int a = 0; a < O.n_act(env); ++a) {
     const ModelD& M = O.actor_model(env, a);
-    const double* r = root + (int64_t)(env * O.actors_per_env + a) * 13;
+    const double* r = root + (int64_t)(O.actor_off[env] + a) * 13;
     ActorState<T>& s = st[a];
     s.p = vec3_of<T>(r);
     for (int k = 0; k < 4; ++k) s.quat[k] = T(r[3 + k]);
@@ -521,9 +717,9 @@ template <class T> void load_env(const Oracle& O, int env, const double* root, c
 
 template <class T> void store_env(const Oracle& O, int env, const std::vector<ActorState<T>>& st, double* root, double* dof) {
   int64_t jd = O.jdof_off[env];
-  for (int a = 0; a < O.actors_per_env; ++a) {
+  for (int a = 0; a < O.n_act(env); ++a) {
     const ModelD& M = O.actor_model(env, a);
-    double* r = root + (int64_t)(env * O.actors_per_env + a) * 13;
+    double* r = root + (int64_t)(O.actor_off[env] + a) * 13;
     const ActorState<T>& s = st[a];
     for (int k = 0; k < 3; ++k) { r[k] = val(s.p[k]); r[7 + k] = val(s.v[k]); r[10 + k] = val(s.w[k]); }
     for (int k = 0; k < 4; ++k) r[3 + k] = val(s.quat[k]);
@@ -545,7 +741,7 @@ template <class T> void env_substep(const Oracle& O, int env, std::vector<ActorS
                                     const T& h, std::vector<T>& cache, StepOut<T>& out) {
   const Params& P = O.prm;
   const EnvLayout E = env_layout(O, env);
-  const int n = E.n_gen, A = O.actors_per_env;
+  const int n = E.n_gen, A = O.n_act(env);
   // a1 + a2 + a3: controls, kinematics, ABA -> v_free = nu + h * qdd
   std::vector<ActorKin<T>> K(A);
   std::vector<T> nu(n, T(0.0)), vfree(n, T(0.0));
@@ -578,7 +774,7 @@ template <class T> void env_substep(const Oracle& O, int env, std::vector<ActorS
   }
   // a4: contacts at the substep-start configuration; a5: rows, W = M^-1 J^T, A = J W
   std::vector<ContactPt<T>> C;
-  ground_contacts(O, env, K, C);
+  env_contacts(O, env, K, C);
   std::vector<Row<T>> rows;
   build_rows(O, env, E, st, K, C, rows, &out.sig);
   if (n > 0 && !cholesky_factor(Mfull, n)) out.ok = false;
@@ -651,6 +847,10 @@ template <class T> void env_substep(const Oracle& O, int env, std::vector<ActorS
       const ContactPt<T>& c = C[rows[ri].contact];
       Vec3<T>& acc = out.impulse[link_base[c.actor_a] + c.link_a];
       acc = add(acc, scale(rows[ri].k, lam[ri]));
+      if (c.actor_b >= 0) {  // equal and opposite on body b; ground reactions are not reported
+        Vec3<T>& accb = out.impulse[link_base[c.actor_b] + c.link_b];
+        accb = sub(accb, scale(rows[ri].k, lam[ri]));
+      }
     }
   }
   out.last_contacts = C;
@@ -700,7 +900,7 @@ template <class T> int env_step(const Oracle& O, int env, double* root, double* 
   std::vector<ActorState<T>> st;
   load_env(O, env, root, dof, st);
   int nlinks = 0;
-  for (int a = 0; a < O.actors_per_env; ++a) nlinks += (int)O.actor_model(env, a).links.size();
+  for (int a = 0; a < O.n_act(env); ++a) nlinks += (int)O.actor_model(env, a).links.size();
   StepOut<T> out;
   out.impulse.assign(nlinks, zero3<T>());
   const T h = T(dt) / T((double)substeps);
@@ -714,7 +914,7 @@ template <class T> int env_step(const Oracle& O, int env, double* root, double* 
   if (o.net_force) {
     int li = 0;
     int64_t b = O.body_off[env];
-    for (int a = 0; a < O.actors_per_env; ++a) {
+    for (int a = 0; a < O.n_act(env); ++a) {
       const ModelD& M = O.actor_model(env, a);
       for (size_t l = 0; l < M.links.size(); ++l, ++li) {
         if (M.links[l].is_virtual) continue;
@@ -869,9 +1069,30 @@ void* oracle_create(const OracleModels* md, const int32_t* env_actor_model, int3
     M.n_jdof = j;
     O->models.push_back(M);
   }
-  O->actors_per_env = actors_per_env;
   O->n_envs = n_envs;
-  O->env_model.assign(env_actor_model, env_actor_model + (int64_t)n_envs * actors_per_env);
+  O->env_actors.assign(n_envs, {});
+  O->actor_off.assign(n_envs + 1, 0);
+  for (int e = 0; e < n_envs; ++e) {
+    for (int a = 0; a < actors_per_env; ++a) {
+      const int m = env_actor_model[(int64_t)e * actors_per_env + a];
+      if (m >= 0) O->env_actors[e].push_back(m);  // -1 pads envs with fewer actors
+    }
+    O->actor_off[e + 1] = O->actor_off[e] + (int64_t)O->env_actors[e].size();
+  }
+  // shape-shape candidate pairs of every env: (a < b), different actors, capsule vs box
+  O->env_pairs.assign(n_envs, {});
+  for (int e = 0; e < n_envs; ++e) {
+    std::vector<std::pair<int, int>> shp;  // (actor, type) per env-local shape
+    for (int a = 0; a < O->n_act(e); ++a)
+      for (const ShapeD& s : O->actor_model(e, a).shapes) shp.push_back({a, s.type});
+    for (int sa = 0; sa < (int)shp.size(); ++sa)
+      for (int sb = sa + 1; sb < (int)shp.size(); ++sb) {
+        if (shp[sa].first == shp[sb].first) continue;
+        const int ta = shp[sa].second, tb = shp[sb].second;
+        if ((ta == SHAPE_CAPSULE && tb == SHAPE_BOX) || (ta == SHAPE_BOX && tb == SHAPE_CAPSULE))
+          O->env_pairs[e].push_back({sa, sb});
+      }
+  }
   std::memcpy(O->prm.gravity, p->gravity, sizeof(double) * 3);
   O->prm.pos_iters = p->pos_iters;
   O->prm.vel_iters = p->vel_iters;
@@ -885,8 +1106,8 @@ void* oracle_create(const OracleModels* md, const int32_t* env_actor_model, int3
   O->n_gen.assign(n_envs, 0);
   O->contact_cap.assign(n_envs, 0);
   for (int e = 0; e < n_envs; ++e) {
-    int jd = 0, nb = 0, ng = 0, cc = 0;
-    for (int a = 0; a < actors_per_env; ++a) {
+    int jd = 0, nb = 0, ng = 0, cc = kPairSlots * (int)O->env_pairs[e].size();
+    for (int a = 0; a < O->n_act(e); ++a) {
       const ModelD& M = O->actor_model(e, a);
       jd += M.n_jdof; nb += M.n_body; ng += M.n_gen; cc += M.contact_cap;
     }
@@ -898,7 +1119,7 @@ void* oracle_create(const OracleModels* md, const int32_t* env_actor_model, int3
     O->max_gen = std::max(O->max_gen, ng);
     O->cache_len = std::max(O->cache_len, 3 * cc + 2 * jd);
   }
-  O->N_A = (int64_t)n_envs * actors_per_env;
+  O->N_A = O->actor_off[n_envs];
   O->N_D = O->jdof_off[n_envs];
   O->N_B = O->body_off[n_envs];
   return O;
@@ -958,14 +1179,37 @@ int32_t oracle_step_f32(void* h, double* root, double* dof, double* cache, const
   return bad;
 }
 
+// Capsule-box geometry for the pins, in the box frame: segment p0 -> p1, radius r, half extents e.
+// out[0] = t* (closest point of the segment); then for t = 0, 1, t*: n (3), d, x (3); out[22] = 1 if
+// the face clip is non-empty, out[23], out[24] = its ends.
+void oracle_capsule_box(const double* p0, const double* p1, double r, const double* e, double* out) {
+  const Vec3<double> a = vec3_of<double>(p0), b = vec3_of<double>(p1), ext = vec3_of<double>(e);
+  const Vec3<double> dv = sub(b, a);
+  const double ts = segment_box_closest_t(a, dv, ext);
+  out[0] = ts;
+  double ta = 0.0, tb = 0.0;
+  out[22] = face_clip(a, dv, ext, r, ts, ta, tb) ? 1.0 : 0.0;
+  out[23] = ta;
+  out[24] = tb;
+  const double tt[3] = {0.0, 1.0, ts};
+  for (int s = 0; s < 3; ++s) {
+    Vec3<double> n, x;
+    double d;
+    sphere_box(add(a, scale(dv, tt[s])), r, ext, n, d, x);
+    double* o = out + 1 + 7 * s;
+    for (int k = 0; k < 3; ++k) { o[k] = n[k]; o[4 + k] = x[k]; }
+    o[3] = d;
+  }
+}
+
 // --- single-env helpers for the pins. root/dof point at this env's rows (actors_per_env x 13 and
 // its joint DOFs x 2); generalized vectors are env-level ([free root 6] + joints, actor by actor).
 static void env_kin(const Oracle& O, int env, const double* root, const double* dof, std::vector<ActorState<double>>& st,
                     std::vector<ActorKin<double>>& K, std::vector<std::vector<double>>& gv) {
   // load from env-local pointers: build a temporary view with offset 0
-  st.resize(O.actors_per_env);
+  st.resize(O.n_act(env));
   int jd = 0;
-  for (int a = 0; a < O.actors_per_env; ++a) {
+  for (int a = 0; a < O.n_act(env); ++a) {
     const ModelD& M = O.actor_model(env, a);
     const double* r = root + a * 13;
     ActorState<double>& s = st[a];
@@ -978,9 +1222,9 @@ static void env_kin(const Oracle& O, int env, const double* root, const double* 
     for (int j = 0; j < M.n_jdof; ++j) { s.q[j] = dof[(jd + j) * 2]; s.qd[j] = dof[(jd + j) * 2 + 1]; }
     jd += M.n_jdof;
   }
-  K.resize(O.actors_per_env);
-  gv.resize(O.actors_per_env);
-  for (int a = 0; a < O.actors_per_env; ++a) {
+  K.resize(O.n_act(env));
+  gv.resize(O.n_act(env));
+  for (int a = 0; a < O.n_act(env); ++a) {
     gv[a] = gen_velocity(O.actor_model(env, a), st[a]);
     kinematics(O.actor_model(env, a), st[a], gv[a], K[a]);
   }
@@ -991,7 +1235,7 @@ int32_t oracle_aba(void* h, int32_t env, const double* root, const double* dof, 
   std::vector<ActorState<double>> st; std::vector<ActorKin<double>> K; std::vector<std::vector<double>> gv;
   env_kin(O, env, root, dof, st, K, gv);
   const EnvLayout E = env_layout(O, env);
-  for (int a = 0; a < O.actors_per_env; ++a) {
+  for (int a = 0; a < O.n_act(env); ++a) {
     const ModelD& M = O.actor_model(env, a);
     std::vector<double> t(tau + E.gen_off[a], tau + E.gen_off[a] + M.n_gen), q;
     if (!aba(M, K[a], t, O.prm, q)) return 1;
@@ -1007,7 +1251,7 @@ int32_t oracle_crba(void* h, int32_t env, const double* root, const double* dof,
   const EnvLayout E = env_layout(O, env);
   const int n = E.n_gen;
   for (int i = 0; i < n * n; ++i) Hout[i] = 0.0;
-  for (int a = 0; a < O.actors_per_env; ++a) {
+  for (int a = 0; a < O.n_act(env); ++a) {
     const ModelD& M = O.actor_model(env, a);
     std::vector<double> H;
     crba(M, K[a], H);
@@ -1022,7 +1266,7 @@ int32_t oracle_rnea(void* h, int32_t env, const double* root, const double* dof,
   std::vector<ActorState<double>> st; std::vector<ActorKin<double>> K; std::vector<std::vector<double>> gv;
   env_kin(O, env, root, dof, st, K, gv);
   const EnvLayout E = env_layout(O, env);
-  for (int a = 0; a < O.actors_per_env; ++a) {
+  for (int a = 0; a < O.n_act(env); ++a) {
     const ModelD& M = O.actor_model(env, a);
     std::vector<double> q(qdd + E.gen_off[a], qdd + E.gen_off[a] + M.n_gen), t;
     rnea(M, K[a], q, O.prm, t);
@@ -1038,7 +1282,7 @@ int32_t oracle_energy(void* h, int32_t env, const double* root, const double* do
   env_kin(O, env, root, dof, st, K, gv);
   const Vec3<double> g = mk3<double>(O.prm.gravity[0], O.prm.gravity[1], O.prm.gravity[2]);
   double T = 0.0, V = 0.0;
-  for (int a = 0; a < O.actors_per_env; ++a) {
+  for (int a = 0; a < O.n_act(env); ++a) {
     const ModelD& M = O.actor_model(env, a);
     for (size_t i = 0; i < M.links.size(); ++i) {
       T += 0.5 * sdot(K[a].v[i], smul(K[a].I[i], K[a].v[i]));
@@ -1060,7 +1304,7 @@ int32_t oracle_momentum(void* h, int32_t env, const double* root, const double* 
   env_kin(O, env, root, dof, st, K, gv);
   const EnvLayout E = env_layout(O, env);
   SVec<double> hm = szero<double>(), hd = szero<double>();
-  for (int a = 0; a < O.actors_per_env; ++a) {
+  for (int a = 0; a < O.n_act(env); ++a) {
     const ModelD& M = O.actor_model(env, a);
     const int L = (int)M.links.size();
     std::vector<SVec<double>> acc(L);
@@ -1087,7 +1331,7 @@ int32_t oracle_rk4(void* h, double* root, double* dof, const double* act, double
     std::vector<ActorState<double>> st;
     load_env(O, e, root, dof, st);
     int jb = 0;
-    for (int a = 0; a < O.actors_per_env; ++a) {
+    for (int a = 0; a < O.n_act(e); ++a) {
       const ModelD& M = O.actor_model(e, a);
       std::vector<double> tj(act + O.jdof_off[e] + jb, act + O.jdof_off[e] + jb + M.n_jdof);
       for (int s = 0; s < nsteps; ++s) {
@@ -1118,7 +1362,7 @@ int32_t oracle_link_pose(void* h, int32_t env, const double* root, const double*
   std::vector<ActorState<double>> st; std::vector<ActorKin<double>> K; std::vector<std::vector<double>> gv;
   env_kin(O, env, root, dof, st, K, gv);
   int l = link;
-  for (int a = 0; a < O.actors_per_env; ++a) {
+  for (int a = 0; a < O.n_act(env); ++a) {
     const int L = (int)O.actor_model(env, a).links.size();
     if (l < L) {
       for (int k = 0; k < 9; ++k) out[k] = K[a].R[l].e[k];
@@ -1134,19 +1378,19 @@ int32_t oracle_link_pose(void* h, int32_t env, const double* root, const double*
 // -1 if cap is too small). J is R x n_gen; kind: 0 limit, 1 normal, 2 friction; link is the env
 // link (actor-major) the row acts on (-1 for limits); x, k: contact point and direction.
 int32_t oracle_rows(void* h, int32_t env, const double* root, const double* dof, int32_t cap, double* J, double* d,
-                    int32_t* kind, int32_t* link, double* x, double* k, double* A) {
+                    int32_t* kind, int32_t* link, double* x, double* k, double* A, int32_t* info) {
   const Oracle& O = *(const Oracle*)h;
   std::vector<ActorState<double>> st; std::vector<ActorKin<double>> K; std::vector<std::vector<double>> gv;
   env_kin(O, env, root, dof, st, K, gv);
   const EnvLayout E = env_layout(O, env);
   std::vector<ContactPt<double>> C;
-  ground_contacts(O, env, K, C);
+  env_contacts(O, env, K, C);
   std::vector<Row<double>> rows;
   build_rows(O, env, E, st, K, C, rows, nullptr);
   if ((int)rows.size() > cap) return -1;
   const int n = E.n_gen;
   std::vector<double> Mfull(n * n, 0.0);
-  for (int a = 0; a < O.actors_per_env; ++a) {
+  for (int a = 0; a < O.n_act(env); ++a) {
     const ModelD& M = O.actor_model(env, a);
     std::vector<double> H;
     crba(M, K[a], H);
@@ -1154,9 +1398,9 @@ int32_t oracle_rows(void* h, int32_t env, const double* root, const double* dof,
       for (int j = 0; j < M.n_gen; ++j) Mfull[(E.gen_off[a] + i) * n + E.gen_off[a] + j] = H[i * M.n_gen + j];
   }
   if (n > 0) cholesky_factor(Mfull, n);
-  std::vector<int> link_base(O.actors_per_env, 0);
+  std::vector<int> link_base(O.n_act(env), 0);
   int lb = 0;
-  for (int a = 0; a < O.actors_per_env; ++a) { link_base[a] = lb; lb += (int)O.actor_model(env, a).links.size(); }
+  for (int a = 0; a < O.n_act(env); ++a) { link_base[a] = lb; lb += (int)O.actor_model(env, a).links.size(); }
   for (size_t r = 0; r < rows.size(); ++r) {
     for (int i = 0; i < n; ++i) J[r * n + i] = rows[r].J[i];
     std::vector<double> w = rows[r].J;
@@ -1170,9 +1414,10 @@ int32_t oracle_rows(void* h, int32_t env, const double* root, const double* dof,
       const ContactPt<double>& c = C[rows[r].contact];
       link[r] = link_base[c.actor_a] + c.link_a;
       for (int m = 0; m < 3; ++m) { x[r * 3 + m] = c.x[m]; k[r * 3 + m] = rows[r].k[m]; }
+      info[r * 3 + 0] = c.shape_a; info[r * 3 + 1] = c.shape_b; info[r * 3 + 2] = c.slot;
     } else {
       link[r] = -1;
-      for (int m = 0; m < 3; ++m) { x[r * 3 + m] = 0.0; k[r * 3 + m] = 0.0; }
+      for (int m = 0; m < 3; ++m) { x[r * 3 + m] = 0.0; k[r * 3 + m] = 0.0; info[r * 3 + m] = -1; }
     }
   }
   return (int32_t)rows.size();

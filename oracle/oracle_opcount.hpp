@@ -29,6 +29,7 @@ struct OpCount {
 inline OpCount sqrt(const OpCount& a) { ++OpCount::counter(); return OpCount(std::sqrt(a.v)); }
 inline OpCount sin(const OpCount& a) { ++OpCount::counter(); return OpCount(std::sin(a.v)); }
 inline OpCount cos(const OpCount& a) { ++OpCount::counter(); return OpCount(std::cos(a.v)); }
+inline OpCount fabs(const OpCount& a) { return OpCount(std::fabs(a.v)); }  // a sign flip, not counted
 inline double val(const OpCount& a) { return a.v; }
 
 }  // namespace orc

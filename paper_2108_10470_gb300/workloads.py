@@ -308,6 +308,68 @@ def humanoid(density=1000.0, damping=0.5, friction=1.0) -> Model:
     return b.build(root_pos=(0.0, 0.0, z0), dof_noise=0.1)
 
 
+HAND_HEIGHT = 0.5   # palm centre above the ground
+CUBE_HALF = 0.0325  # 6.5 cm cube
+
+
+def hand(density=1000.0, armature=0.01, damping=0.05, gear=0.5, friction=1.0) -> Model:
+    """Fixed-base five-finger hand, palm up, shaped like the paper's 24-DOF Shadow Hand: wrist 2 DOF,
+    index / middle / ring 4 DOF each (abduction + three flexions), little 5 (metacarpal + 4), thumb
+    5; multi-axis joints are chains through massless virtual links; every joint is limited to
+    +-90 degrees. Capsule palm and phalanges (radius 1 cm), 16 shapes. 25 links, 24 DOF."""
+    b = _Builder("hand")
+    lim = (-math.pi / 2, math.pi / 2)
+
+    def hinge(parent, axis, ppos=(0, 0, 0), body=None):
+        if body is None:
+            return b.link(parent, JOINT_REVOLUTE, axis=axis, ppos=ppos, armature=armature, damping=damping,
+                          limit=lim, virtual=True, gear=gear)
+        m, c, inn = body
+        return b.link(parent, JOINT_REVOLUTE, axis=axis, ppos=ppos, mass=m, com=c, inertia=inn, armature=armature,
+                      damping=damping, limit=lim, gear=gear)
+
+    def phalanx(parent, axis, ppos, half, r=0.01):
+        m, inn = capsule_mass_x(r, half, density)
+        link = hinge(parent, axis, ppos, body=(m, (half, 0, 0), inn))
+        b.shape(link, SHAPE_CAPSULE, (r, half), pos=(half, 0, 0), friction=friction)
+        return link
+
+    forearm = b.link(-1, JOINT_FIXED, mass=1.0, inertia=(0.01, 0.01, 0.01, 0, 0, 0))
+    v = hinge(forearm, (0, 1, 0))
+    mp, ip = capsule_mass_x(0.025, 0.035, density)
+    palm = hinge(v, (1, 0, 0), body=(mp, (0, 0, 0), ip))
+    b.shape(palm, SHAPE_CAPSULE, (0.025, 0.035), friction=friction)
+    lens = (0.0225, 0.0125, 0.01)  # half lengths of proximal, middle, distal phalanges
+
+    def finger(parent, base):
+        a = hinge(parent, (0, 0, 1), base)  # abduction (virtual)
+        p = phalanx(a, (0, 1, 0), (0, 0, 0), lens[0])
+        m = phalanx(p, (0, 1, 0), (2 * lens[0], 0, 0), lens[1])
+        phalanx(m, (0, 1, 0), (2 * lens[1], 0, 0), lens[2])
+
+    for y in (0.033, 0.011, -0.011):  # index, middle, ring
+        finger(palm, (0.06, y, 0.0))
+    mm_, im_ = capsule_mass_x(0.01, 0.015, density)
+    meta = hinge(palm, (1, 0, 0), (0.03, -0.033, 0.0), body=(mm_, (0.015, 0, 0), im_))  # little metacarpal
+    finger(meta, (0.03, 0.0, 0.0))
+    # thumb: base rotation (virtual) and metacarpal, then three flexions
+    t0 = hinge(palm, (1, 0, 0), (0.0, 0.045, 0.0))
+    tm = hinge(t0, (0, 0, 1), body=(mm_, (0.015, 0, 0), im_))
+    tp = phalanx(tm, (0, 1, 0), (0.03, 0, 0), lens[0])
+    tq = phalanx(tp, (0, 1, 0), (2 * lens[0], 0, 0), lens[1])
+    phalanx(tq, (0, 1, 0), (2 * lens[1], 0, 0), lens[2])
+    return b.build(root_pos=(0.0, 0.0, HAND_HEIGHT), dof_noise=0.1)
+
+
+def cube(mass=0.1, friction=1.0) -> Model:
+    """Free 6.5 cm, 0.1 kg cube resting 2 mm above the hand's palm."""
+    m = free_box(CUBE_HALF, CUBE_HALF, CUBE_HALF, mass=mass, friction=friction,
+                 z=HAND_HEIGHT + 0.025 + CUBE_HALF + 0.002)
+    m.name = "cube"
+    m.root_pos = np.array([0.03, 0.0, HAND_HEIGHT + 0.025 + CUBE_HALF + 0.002])
+    return m
+
+
 def free_box(hx=0.1, hy=0.1, hz=0.1, mass=1.0, friction=1.0, z=None) -> Model:
     b = _Builder("box")
     m, inn = box_mass(hx, hy, hz, mass)
@@ -395,12 +457,16 @@ class Workload:
     substeps: int = 2
 
     def actor_models(self, env: int) -> List[Model]:
+        """The env's actors in order (entries of -1 pad envs that have fewer actors)."""
         A = self.actors_per_env
-        return [self.models[int(m)] for m in self.env_actor_model[env * A:(env + 1) * A]]
+        return [self.models[int(m)] for m in self.env_actor_model[env * A:(env + 1) * A] if m >= 0]
 
     @property
     def n_actors(self) -> int:
-        return self.n_envs * self.actors_per_env
+        return int(np.sum(np.asarray(self.env_actor_model) >= 0))
+
+    def env_actor_count(self, env: int) -> int:
+        return len(self.actor_models(env))
 
     def env_jdof(self, env: int) -> int:
         return sum(m.n_jdof for m in self.actor_models(env))
@@ -430,6 +496,25 @@ def homogeneous(name: str, model: Model, n_envs: int, params: Optional[Params] =
                     n_envs=n_envs, params=params or Params(), dt=dt, substeps=substeps)
 
 
+def hand_workload(n_envs=64) -> Workload:
+    """Fixed-base 24-DOF hand holding a free cube (two actors per env: box-capsule contacts)."""
+    return Workload(name="hand", models=[hand(), cube()],
+                    env_actor_model=np.tile(np.array([0, 1], np.int32), n_envs), actors_per_env=2,
+                    n_envs=n_envs, params=Params())
+
+
+def mixed_workload(n_envs=16384, fractions=(0.4, 0.3, 0.3)) -> Workload:
+    """Heterogeneous batch: Ant-like, Humanoid-like and hand-with-cube envs in the given
+    proportions (contiguous blocks, in that order). Envs with one actor pad the second slot
+    with -1."""
+    n_ant = int(round(fractions[0] * n_envs))
+    n_hum = int(round(fractions[1] * n_envs))
+    n_hand = n_envs - n_ant - n_hum
+    eam = np.concatenate([np.tile([0, -1], n_ant), np.tile([1, -1], n_hum), np.tile([2, 3], n_hand)]).astype(np.int32)
+    return Workload(name="mixed", models=[ant(), humanoid(), hand(), cube()], env_actor_model=eam,
+                    actors_per_env=2, n_envs=n_envs, params=Params())
+
+
 def cartpole_workload(n_envs=64) -> Workload:
     """Plain step, smallest case: 64 cartpoles, no contacts, dt 1/60 s, 2 substeps."""
     return homogeneous("cartpole", cartpole(), n_envs)
@@ -454,11 +539,13 @@ def initial_state(w: Workload, rng: np.random.Generator):
     +-dof_noise, clipped into the joint limits; joint velocities are zero."""
     root = np.zeros((w.n_actors, 13), dtype=np.float32)
     dofs = []
+    row = 0
     for e in range(w.n_envs):
-        for a, m in enumerate(w.actor_models(e)):
-            r = root[e * w.actors_per_env + a]
+        for m in w.actor_models(e):
+            r = root[row]
             r[0:3] = m.root_pos
             r[6] = 1.0
+            row += 1
     for e in range(w.n_envs):
         for m in w.actor_models(e):
             nj = m.n_jdof
