@@ -5,7 +5,7 @@ A step is one sim_step(1/60 s, 2 substeps) over the whole batch (default: the An
 into the DOF actuation view. Inputs are resident in HBM before the timed region; L2 is flushed
 (256 MiB memset) between timed steps, outside each step's event pair.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload ant|humanoid|cartpole] [--envs E]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload ant|humanoid|cartpole|hand|mixed] [--envs E]
   python bench.py --impl reference ...   # the FP64 CPU oracle timed on the host cores
 
 Under torchrun (N > 1) every rank simulates its own E environments on its own GPU (weak scaling:
@@ -30,22 +30,32 @@ sys.path.insert(0, ROOT)
 
 SM_COUNT_NOMINAL = 152
 FP32_LANES_PER_SM = 128
-# HBM bytes one env-step must move: root (13 f32) + DOF (2 per joint) + actuation (1 per joint)
-# + impulse cache read; root + DOF + net contact force (3 per body) + impulse cache + contact
-# pairs (3 i32 per candidate) + count / status / signature written.
-ALGO_BYTES_PER_ENV_STEP = {
-    "ant": 4 * ((13 + 16 + 8 + 67) + (13 + 16 + 27 + 67 + 51 + 3)),
-    "humanoid": 4 * ((13 + 42 + 21 + 114) + (13 + 42 + 39 + 114 + 72 + 3)),
-    "cartpole": 4 * ((13 + 4 + 2) + (13 + 4 + 9 + 3)),
-}
+METRIC = "env-steps/sec on 1 GB300 (Ant-like, 4096 envs) vs oracle; adjoint steps/sec"
+PAIR_SLOTS = 5  # contact candidates per capsule-box pair
 
 
-def baseline_metric():
-    try:
-        with open(os.path.join(ROOT, "BASELINE.json")) as f:
-            return json.load(f)["metric"]
-    except Exception:
-        return "env-steps/sec on 1 GB300 (Ant-like, 4096 envs)"
+def env_candidates(w, e) -> int:
+    """Contact candidates of env e: ground candidates of every shape (sphere 1, capsule 2, box 8)
+    plus PAIR_SLOTS per capsule-box pair across actors."""
+    from paper_2108_10470_gb300 import workloads as W
+    models = w.actor_models(e)
+    caps = [sum(int(t == W.SHAPE_CAPSULE) for t in m.shape_type) for m in models]
+    boxes = [sum(int(t == W.SHAPE_BOX) for t in m.shape_type) for m in models]
+    pairs = sum(caps[i] * boxes[j] + boxes[i] * caps[j] for i in range(len(models)) for j in range(i + 1, len(models)))
+    return sum(m.contact_cap for m in models) + PAIR_SLOTS * pairs
+
+
+def algo_bytes_per_step(w) -> int:
+    """HBM bytes one step must move over all envs. Read: root (13 f32 per actor), DOF state (2 per
+    joint DOF), actuation (1 per joint DOF), impulse cache (3 per candidate + 2 per joint DOF).
+    Written: root, DOF state, net contact force (3 per body), impulse cache, contact list (3 i32
+    per candidate), count / status / signature."""
+    total = 0
+    for e in range(w.n_envs):
+        A, J, B, C = w.env_actor_count(e), w.env_jdof(e), w.env_body(e), env_candidates(w, e)
+        cache = 3 * C + 2 * J
+        total += 4 * ((13 * A + 2 * J + J + cache) + (13 * A + 2 * J + 3 * B + cache + 3 * C + 3))
+    return total
 
 
 def max_over_ranks(x: float, world: int, device="cpu") -> float:
@@ -86,7 +96,8 @@ def profiled_traffic(wname: str, n_envs: int):
 
 def workload(name, n_envs):
     from paper_2108_10470_gb300 import workloads as W
-    return {"ant": W.ant_workload, "humanoid": W.humanoid_workload, "cartpole": W.cartpole_workload}[name](n_envs)
+    return {"ant": W.ant_workload, "humanoid": W.humanoid_workload, "cartpole": W.cartpole_workload,
+            "hand": W.hand_workload, "mixed": W.mixed_workload}[name](n_envs)
 
 
 def describe(w):
@@ -204,7 +215,7 @@ def run_reference(args, rank, world):
         O.step(r, d, acts[args.warmup + k], n_threads=threads)
     el = time.perf_counter() - t0
     value = sample_envs * args.steps / el
-    line = {"metric": baseline_metric(), "value": value, "unit": "env-steps/s", "n_gpus": world, "steps": args.steps,
+    line = {"metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": describe(w), "n_envs": args.envs,
@@ -275,7 +286,7 @@ def run_ours(args, rank, world, local_rank):
         return
     value = weak_value(world, w.n_envs, K, total_s)
     clocks = clk.summary()
-    line = {"metric": baseline_metric(), "value": value, "unit": "env-steps/s", "n_gpus": world, "steps": K,
+    line = {"metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": world, "steps": K,
             "warmup": Wm, "ms_per_step": 1e3 * total_s / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": describe(w), "n_envs_per_gpu": w.n_envs, "dt": w.dt, "substeps": w.substeps,
@@ -297,8 +308,7 @@ def run_ours(args, rank, world, local_rank):
         roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
                 "frac": achieved / peak,
                 "traffic": args.traffic if args.traffic is not None else profiled_traffic(args.workload, w.n_envs),
-                "algorithmic_bytes_per_launch": ALGO_BYTES_PER_ENV_STEP.get(args.workload, None) and
-                ALGO_BYTES_PER_ENV_STEP[args.workload] * w.n_envs,
+                "algorithmic_bytes_per_step": algo_bytes_per_step(w),
                 "kernel": "step_kernel", "kernel_ms": 1e3 * kern_avg_s,
                 "flops_per_env_step": flops_per_env_step,
                 "peak_basis": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (median SM clock sampled "
@@ -314,7 +324,7 @@ def main():
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ant", choices=["ant", "humanoid", "cartpole"])
+    ap.add_argument("--workload", default="ant", choices=["ant", "humanoid", "cartpole", "hand", "mixed"])
     ap.add_argument("--envs", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--traffic", type=float, default=None,

@@ -40,11 +40,13 @@ class _Params(ctypes.Structure):
 
 
 def build(force: bool = False) -> str:
-    """Compile liboracle.so with the host compiler (no CUDA)."""
+    """Compile liboracle.so with the host compiler (no CUDA). Contraction of a*b+c into fused
+    multiply-adds is off, so the oracle rounds the same way on every host (aarch64 gcc contracts by
+    default, x86-64 gcc without FMA flags does not)."""
     stale = not os.path.exists(_LIB_PATH) or any(os.path.getmtime(s) > os.path.getmtime(_LIB_PATH) for s in _SRC)
     if force or stale:
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        cmd = ["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-pthread", "-o", tmp, os.path.join(_HERE, "oracle.cpp")]
+        cmd = ["g++", "-O2", "-ffp-contract=off", "-std=c++17", "-shared", "-fPIC", "-pthread", "-o", tmp, os.path.join(_HERE, "oracle.cpp")]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH

@@ -29,7 +29,8 @@ struct TypePlan {
   int G = 32;
   int groups_per_block = 4;
   size_t smem_bytes = 0;
-  int env_off = 0;  // offset into the concatenated env-id array
+  int env_off = 0;           // offset into the concatenated env-id array
+  float* scratch = nullptr;  // global rows (lay.grows): one slot per env plus one per dead group
 };
 
 }  // namespace
@@ -46,8 +47,10 @@ struct sim_s {
   bool contiguous_single_type = false;
   EnvTypeTable* d_types = nullptr;
   int* d_env_ids = nullptr;
-  int* d_dof_base = nullptr;   // n_envs + 1
-  int* d_body_base = nullptr;  // n_envs + 1
+  int* d_dof_base = nullptr;    // n_envs + 1
+  int* d_body_base = nullptr;   // n_envs + 1
+  int* d_actor_base = nullptr;  // n_envs + 1: first root-state row of each env
+  int* d_actor_env = nullptr;   // N_A: env of each actor
   float* root = nullptr;
   float* dof = nullptr;
   float* act = nullptr;
@@ -237,10 +240,26 @@ int build_type(const sim_model_desc* models, const std::vector<int>& actor_model
       quat_to_rot(m.shape_quat + 4 * s, R);
       for (int k = 0; k < 9; ++k) T.shape_rot[k][e] = R[k];
       T.shape_mu[e] = std::max(m.shape_friction[s], p.ground_friction);
+      T.shape_fr[e] = m.shape_friction[s];
     }
     L += m.n_links;
     ns += m.n_shapes;
   }
+  // capsule-box pairs across actors (a < b), candidates after every ground candidate
+  T.n_ground_cand = nc;
+  int np = 0;
+  for (int sa = 0; sa < ns; ++sa)
+    for (int sb = sa + 1; sb < ns; ++sb) {
+      if (T.actor[T.shape_link[sa]] == T.actor[T.shape_link[sb]]) continue;
+      const int ta = T.shape_type[sa], tb = T.shape_type[sb];
+      if (!((ta == kCapsule && tb == kBox) || (ta == kBox && tb == kCapsule))) continue;
+      if (np >= kMaxPairs) return SIM_ERR_CAPACITY;
+      T.pair_a[np] = sa;
+      T.pair_b[np] = sb;
+      ++np;
+    }
+  T.n_pairs = np;
+  nc += kPairSlots * np;
   if (nc > kMaxCand) return SIM_ERR_CAPACITY;
   // children lists (ascending), ancestor DOF masks, depth
   int maxd = 0;
@@ -276,6 +295,11 @@ int build_type(const sim_model_desc* models, const std::vector<int>& actor_model
   return SIM_OK;
 }
 
+// Largest per-env shared arena; bigger worst cases, and every env type with shape pairs, keep
+// their contact / row blocks in global scratch (the Humanoid's 18 KB stays in shared memory, the
+// hand-with-cube's ~60 KB does not).
+constexpr int kSharedArenaLimit = 24 * 1024;
+
 SmemLayout make_layout(const EnvTypeTable& T) {
   SmemLayout Ly{};
   const int n = std::max(T.n_gen, 1);
@@ -285,6 +309,8 @@ SmemLayout make_layout(const EnvTypeTable& T) {
   Ly.MS = n | 1;
   Ly.ccap = std::max(T.n_cand, 1);
   auto al4 = [](int x) { return (x + 3) & ~3; };
+  // ground-only env types keep the 9-word contact record (no body b, normal +z)
+  const int conw = T.n_pairs > 0 ? kConWords : 9;
   int o = 0;
   const int phase = std::max(L * kLinkWords, n * Ly.RS);
   Ly.link = o;
@@ -293,13 +319,33 @@ SmemLayout make_layout(const EnvTypeTable& T) {
   Ly.SD = o; o += 6 * n;
   Ly.M = o; o += n * Ly.MS;
   Ly.vec = o; o += 5 * n;
-  Ly.con = o; o += kConWords * Ly.ccap;
+  Ly.con = o; o += conw * Ly.ccap;
   o = al4(o);
   Ly.rowc = o; o += 4 * Ly.rcap;
   Ly.lam = o; o += Ly.rcap;
   Ly.rowa = o; o += Ly.rcap;
   Ly.frc = o; o += 3 * L;
   Ly.total = al4(o);
+  if (Ly.total * 4 > kSharedArenaLimit || T.n_pairs > 0) {
+    // worst case too large for shared memory, or shape pairs (compiled into this variant only):
+    // contact and row blocks go to a global scratch slot
+    Ly.grows = 1;
+    int g = 0;
+    Ly.con = g; g += conw * Ly.ccap;
+    g = al4(g);
+    Ly.rowc = g; g += 4 * Ly.rcap;
+    Ly.lam = g; g += Ly.rcap;
+    Ly.rowa = g; g += Ly.rcap;
+    Ly.Y = g; g += n * Ly.RS;
+    Ly.scratch_words = al4(g);
+    o = 0;
+    Ly.link = o; o += L * kLinkWords;
+    Ly.SD = o; o += 6 * n;
+    Ly.M = o; o += n * Ly.MS;
+    Ly.vec = o; o += 5 * n;
+    Ly.frc = o; o += 3 * L;
+    Ly.total = al4(o);
+  }
   // Groups that share a warp (G < 32) must not share banks: pad the per-group stride to G mod 32
   // so the g-th group of a warp is shifted by g * G banks (the row stride RS is odd, so each
   // group's lanes also fall on distinct banks).
@@ -308,31 +354,46 @@ SmemLayout make_layout(const EnvTypeTable& T) {
   return Ly;
 }
 
-template <int G> void set_smem_attr(size_t bytes) {
-  cudaFuncSetAttribute(step_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+template <int G, bool GR> void set_smem_attr(size_t bytes) {
+  cudaFuncSetAttribute(step_kernel<G, GR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-template <int G> cudaError_t launch_G(const StepArgs& a, int n_envs, int gpb, size_t smem, cudaStream_t st) {
+template <int G, bool GR> cudaError_t launch_G(const StepArgs& a, int n_envs, int gpb, size_t smem, cudaStream_t st) {
   const int blocks = (n_envs + gpb - 1) / gpb;
-  step_kernel<G><<<blocks, gpb * G, smem, st>>>(a);
+  step_kernel<G, GR><<<blocks, gpb * G, smem, st>>>(a);
   return cudaGetLastError();
 }
 
-void free_all(sim_s* h) {
-  void* ptrs[] = {h->d_types, h->d_env_ids, h->d_dof_base, h->d_body_base, h->root, h->dof, h->act, h->net_force,
-                  h->cache, h->pairs, h->n_pairs, h->sig, h->status};
-  for (void* p : ptrs)
-    if (p) cudaFree(p);
+cudaError_t launch_type(const TypePlan& tp, const StepArgs& a, cudaStream_t st) {
+  const int n = a.n_launch_envs, gpb = tp.groups_per_block;
+  const size_t sm = tp.smem_bytes;
+  if (tp.lay.grows) {
+    if (tp.G == 8) return launch_G<8, true>(a, n, gpb, sm, st);
+    if (tp.G == 16) return launch_G<16, true>(a, n, gpb, sm, st);
+    return launch_G<32, true>(a, n, gpb, sm, st);
+  }
+  if (tp.G == 8) return launch_G<8, false>(a, n, gpb, sm, st);
+  if (tp.G == 16) return launch_G<16, false>(a, n, gpb, sm, st);
+  return launch_G<32, false>(a, n, gpb, sm, st);
 }
 
-__global__ void set_root_kernel(float* root, const float* src, const int* idx, int n, int64_t N_A, int A,
-                                float* cache, int cache_stride) {
+void free_all(sim_s* h) {
+  void* ptrs[] = {h->d_types, h->d_env_ids, h->d_dof_base, h->d_body_base, h->d_actor_base, h->d_actor_env,
+                  h->root, h->dof, h->act, h->net_force, h->cache, h->pairs, h->n_pairs, h->sig, h->status};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  for (auto& tp : h->types)
+    if (tp.scratch) cudaFree(tp.scratch);
+}
+
+__global__ void set_root_kernel(float* root, const float* src, const int* idx, int n, int64_t N_A,
+                                const int* actor_env, float* cache, int cache_stride) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int a = idx[i];
   if (a < 0 || a >= N_A) return;
   for (int k = 0; k < 13; ++k) root[(size_t)a * 13 + k] = src[(size_t)i * 13 + k];
-  const int env = a / A;
+  const int env = actor_env[a];
   for (int k = 0; k < cache_stride; ++k) cache[(size_t)env * cache_stride + k] = 0.f;
 }
 
@@ -400,8 +461,16 @@ int sim_create(const sim_model_desc* models, int32_t n_models, const int32_t* en
     const int rc = validate_model(models[m]);
     if (rc != SIM_OK) return rc;
   }
-  for (int64_t i = 0; i < (int64_t)n_envs * actors_per_env; ++i)
-    if (env_actor_model[i] < 0 || env_actor_model[i] >= n_models) return SIM_ERR_INVALID_ARG;
+  // entries of -1 pad envs with fewer actors; every env needs at least one actor
+  for (int64_t e = 0; e < n_envs; ++e) {
+    int cnt = 0;
+    for (int a = 0; a < actors_per_env; ++a) {
+      const int m = env_actor_model[e * actors_per_env + a];
+      if (m < -1 || m >= n_models) return SIM_ERR_INVALID_ARG;
+      cnt += m >= 0;
+    }
+    if (cnt == 0) return SIM_ERR_INVALID_ARG;
+  }
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
     cudaGetLastError();
@@ -417,8 +486,14 @@ int sim_create(const sim_model_desc* models, int32_t n_models, const int32_t* en
   // env types
   std::map<std::vector<int>, int> type_of;
   std::vector<int> env_type(n_envs);
+  std::vector<int> actor_base(n_envs + 1, 0);
   for (int e = 0; e < n_envs; ++e) {
-    std::vector<int> key(env_actor_model + (int64_t)e * actors_per_env, env_actor_model + (int64_t)(e + 1) * actors_per_env);
+    std::vector<int> key;
+    for (int a = 0; a < actors_per_env; ++a) {
+      const int m = env_actor_model[(int64_t)e * actors_per_env + a];
+      if (m >= 0) key.push_back(m);
+    }
+    actor_base[e + 1] = actor_base[e] + (int)key.size();
     auto it = type_of.find(key);
     if (it == type_of.end()) {
       TypePlan tp;
@@ -451,7 +526,7 @@ int sim_create(const sim_model_desc* models, int32_t n_models, const int32_t* en
     max_pairs = std::max(max_pairs, T.n_cand);
     max_jdof = std::max(max_jdof, T.n_jdof);
   }
-  h->N_A = (int64_t)n_envs * actors_per_env;
+  h->N_A = actor_base[n_envs];
   h->N_D = dof_base[n_envs];
   h->N_B = body_base[n_envs];
   h->cache_stride = max_cache;
@@ -481,6 +556,14 @@ int sim_create(const sim_model_desc* models, int32_t n_models, const int32_t* en
   CKC(cudaMalloc(&h->d_env_ids, sizeof(int) * env_ids.size()));
   CKC(cudaMalloc(&h->d_dof_base, sizeof(int) * (n_envs + 1)));
   CKC(cudaMalloc(&h->d_body_base, sizeof(int) * (n_envs + 1)));
+  CKC(cudaMalloc(&h->d_actor_base, sizeof(int) * (n_envs + 1)));
+  CKC(cudaMalloc(&h->d_actor_env, sizeof(int) * h->N_A));
+  for (auto& tp : h->types)
+    if (tp.lay.grows) {
+      // one private slot per env of the type, plus one per group of the last (partial) block
+      const size_t slots = tp.envs.size() + (size_t)tp.groups_per_block;
+      CKC(cudaMalloc(&tp.scratch, sizeof(float) * slots * tp.lay.scratch_words));
+    }
   CKC(cudaMalloc(&h->root, sizeof(float) * h->N_A * 13));
   CKC(cudaMalloc(&h->dof, sizeof(float) * std::max<int64_t>(h->N_D * 2, 1)));
   CKC(cudaMalloc(&h->act, sizeof(float) * std::max<int64_t>(h->N_D, 1)));
@@ -494,6 +577,13 @@ int sim_create(const sim_model_desc* models, int32_t n_models, const int32_t* en
   CKC(cudaMemcpy(h->d_env_ids, env_ids.data(), sizeof(int) * env_ids.size(), cudaMemcpyHostToDevice));
   CKC(cudaMemcpy(h->d_dof_base, dof_base.data(), sizeof(int) * (n_envs + 1), cudaMemcpyHostToDevice));
   CKC(cudaMemcpy(h->d_body_base, body_base.data(), sizeof(int) * (n_envs + 1), cudaMemcpyHostToDevice));
+  CKC(cudaMemcpy(h->d_actor_base, actor_base.data(), sizeof(int) * (n_envs + 1), cudaMemcpyHostToDevice));
+  {
+    std::vector<int> actor_env(h->N_A);
+    for (int e = 0; e < n_envs; ++e)
+      for (int a = actor_base[e]; a < actor_base[e + 1]; ++a) actor_env[a] = e;
+    CKC(cudaMemcpy(h->d_actor_env, actor_env.data(), sizeof(int) * h->N_A, cudaMemcpyHostToDevice));
+  }
   std::vector<float> root0((size_t)h->N_A * 13, 0.f);
   for (int64_t a = 0; a < h->N_A; ++a) root0[a * 13 + 6] = 1.f;
   CKC(cudaMemcpy(h->root, root0.data(), sizeof(float) * root0.size(), cudaMemcpyHostToDevice));
@@ -506,9 +596,10 @@ int sim_create(const sim_model_desc* models, int32_t n_models, const int32_t* en
   CKC(cudaMemset(h->sig, 0, sizeof(unsigned) * n_envs));
   CKC(cudaMemset(h->status, 0, sizeof(int) * n_envs));
   for (auto& tp : h->types) {
-    if (tp.G == 8) set_smem_attr<8>(tp.smem_bytes);
-    else if (tp.G == 16) set_smem_attr<16>(tp.smem_bytes);
-    else set_smem_attr<32>(tp.smem_bytes);
+    const bool g = tp.lay.grows != 0;
+    if (tp.G == 8) g ? set_smem_attr<8, true>(tp.smem_bytes) : set_smem_attr<8, false>(tp.smem_bytes);
+    else if (tp.G == 16) g ? set_smem_attr<16, true>(tp.smem_bytes) : set_smem_attr<16, false>(tp.smem_bytes);
+    else g ? set_smem_attr<32, true>(tp.smem_bytes) : set_smem_attr<32, false>(tp.smem_bytes);
   }
   CKC(cudaGetLastError());
 #undef CKC
@@ -533,18 +624,15 @@ int sim_step(sim_handle h, float dt, int32_t substeps) {
     a.n_launch_envs = (int)tp.envs.size();
     a.root = h->root; a.dof = h->dof; a.act = h->act; a.net_force = h->net_force; a.cache = h->cache;
     a.pairs = h->pairs; a.n_pairs = h->n_pairs; a.sig = h->sig; a.status = h->status;
-    a.env_dof_base = h->d_dof_base; a.env_body_base = h->d_body_base;
-    a.actors_per_env = h->actors_per_env; a.cache_stride = h->cache_stride; a.pair_stride = h->pair_stride;
+    a.env_dof_base = h->d_dof_base; a.env_body_base = h->d_body_base; a.env_actor_base = h->d_actor_base;
+    a.scratch = tp.scratch; a.cache_stride = h->cache_stride; a.pair_stride = h->pair_stride;
     a.dt = dt; a.h = dt / (float)substeps; a.substeps = substeps;
     a.gx = p.gravity[0]; a.gy = p.gravity[1]; a.gz = p.gravity[2];
     a.pos_iters = p.pos_iters; a.vel_iters = p.vel_iters;
     a.contact_offset = p.contact_offset; a.limit_margin = p.limit_margin;
     a.bias_coef = p.bias_coef; a.max_depen_vel = p.max_depen_vel; a.flags = p.flags;
     a.lay = tp.lay;
-    cudaError_t e;
-    if (tp.G == 8) e = launch_G<8>(a, a.n_launch_envs, tp.groups_per_block, tp.smem_bytes, h->stream);
-    else if (tp.G == 16) e = launch_G<16>(a, a.n_launch_envs, tp.groups_per_block, tp.smem_bytes, h->stream);
-    else e = launch_G<32>(a, a.n_launch_envs, tp.groups_per_block, tp.smem_bytes, h->stream);
+    const cudaError_t e = launch_type(tp, a, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "step_kernel launch");
   }
   return SIM_OK;
@@ -597,7 +685,7 @@ int sim_set_root_state_indexed(sim_handle h, const float* dev_src, const int32_t
   if (n < 0 || (n > 0 && (!dev_src || !dev_actor_idx))) return SIM_ERR_INVALID_ARG;
   if (n == 0) return SIM_OK;
   set_root_kernel<<<(n + 127) / 128, 128, 0, h->stream>>>(h->root, dev_src, dev_actor_idx, n, h->N_A,
-                                                          h->actors_per_env, h->cache, h->cache_stride);
+                                                          h->d_actor_env, h->cache, h->cache_stride);
   CK(cudaGetLastError());
   return SIM_OK;
 }

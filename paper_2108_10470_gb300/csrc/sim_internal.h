@@ -11,7 +11,9 @@ namespace artsim {
 constexpr int kMaxLinks = 32;   // links per environment (all actors)
 constexpr int kMaxGen = 32;     // generalized DOFs per environment (6 per floating root + joints)
 constexpr int kMaxShapes = 32;  // shapes per environment
-constexpr int kMaxCand = 96;    // contact candidate points per environment
+constexpr int kMaxPairs = 32;   // capsule-box shape pairs per environment
+constexpr int kPairSlots = 5;   // samples per pair: t = 0, t = 1, face-clip entry / exit, closest point
+constexpr int kMaxCand = 256;   // contact candidate points per environment
 constexpr int kMaxActors = 8;   // actors per environment
 
 enum JointType : int { kFree = 0, kFixed = 1, kRevolute = 2, kPrismatic = 3 };
@@ -49,14 +51,24 @@ struct EnvTypeTable {
   int shape_link[kMaxShapes], shape_type[kMaxShapes], cand_off[kMaxShapes];
   float shape_size[3][kMaxShapes], shape_pos[3][kMaxShapes], shape_rot[9][kMaxShapes];
   float shape_mu[kMaxShapes];   // max(shape friction, ground friction)
+  float shape_fr[kMaxShapes];   // the shape's own friction (pairs use max over the two shapes)
+  // capsule-box pairs (env-local shape indices a < b, different actors), candidates after the
+  // ground candidates: n_ground_cand + kPairSlots * pair + slot
+  int n_pairs, n_ground_cand;
+  int pair_a[kMaxPairs], pair_b[kMaxPairs];
   // per generalized DOF
   int dof_link[kMaxGen];
   int dof_comp[kMaxGen];        // 0..5 for a floating root ([omega; v]), -1 for a joint DOF
 };
 
-// Per-environment shared-memory arena (offsets in 4-byte words). The link hand-off slots of the
-// inward sweep (phase 1) and the constraint response Y (phase 2) alias.
+// Per-environment arena (offsets in 4-byte words). The link hand-off slots of the inward sweep
+// (phase 1) and the constraint response Y (phase 2) alias. When an env type's worst case does not
+// fit in shared memory ("global rows"), the contact and row blocks (con, Y, rowc, lam, rowa) live
+// in a private per-env slot of global scratch memory instead (offsets relative to the slot), and
+// the link slots get a shared-memory region of their own.
 struct SmemLayout {
+  int grows;  // 1: contact and row blocks in global scratch
+  int scratch_words;  // words per env slot of global scratch (0 if grows == 0)
   int link;   // kLinkWords per link: IA 21 | pA 6 | Ic 10
   int Y;      // n_gen x RS: Y = L^-1 J^T, one column per constraint row
   int RS;     // row stride of Y (odd)
@@ -74,7 +86,9 @@ struct SmemLayout {
   int total;  // words per environment (multiple of 4; = G mod 32 when groups share a warp)
 };
 constexpr int kLinkWords = 37;
-constexpr int kConWords = 9;   // x y z d mu link cand shape slot
+// contact record (SoA): x y z (relative to actor a's origin) | d | mu | link_a | cand | shape_a |
+// slot | link_b (-1: ground) | shape_b | n x y z (from b to a) | O_b - O_a x y z
+constexpr int kConWords = 17;
 
 struct StepArgs {
   const EnvTypeTable* type;
@@ -93,7 +107,9 @@ struct StepArgs {
   int* status;               // (n_envs,)
   const int* env_dof_base;   // (n_envs,) first DOF row
   const int* env_body_base;  // (n_envs,) first body row
-  int actors_per_env, cache_stride, pair_stride;
+  const int* env_actor_base; // (n_envs,) first root-state row
+  float* scratch;            // global rows: one slot per launched env plus one per dead group
+  int cache_stride, pair_stride;
   // step
   float dt, h;
   int substeps;

@@ -117,6 +117,110 @@ __device__ __forceinline__ void fnv1a(unsigned& h, int v) {
   }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Capsule-box geometry (box frame). All three follow the definitions the FP64 oracle applies.
+__device__ __forceinline__ float comp(V3 v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
+__device__ __forceinline__ float box_dist2(V3 p, V3 e) {
+  const float ox = fmaxf(fabsf(p.x) - e.x, 0.f), oy = fmaxf(fabsf(p.y) - e.y, 0.f), oz = fmaxf(fabsf(p.z) - e.z, 0.f);
+  return ox * ox + oy * oy + oz * oz;
+}
+// Exact minimiser over [0, 1] of the squared distance from p0 + t dv to the box: pieces between the
+// breakpoints |p_k(t)| = e_k, each piece's stationary point clamped into it (its start if the
+// distance is constant there); smallest value wins, ties to the smallest t.
+__device__ float segment_box_closest_t(V3 p0, V3 dv, V3 e) {
+  float ts[8];
+  int nt = 0;
+  ts[nt++] = 0.f;
+  ts[nt++] = 1.f;
+  for (int k = 0; k < 3; ++k) {
+    const float dk = comp(dv, k), pk = comp(p0, k), ek = comp(e, k);
+    if (dk == 0.f) continue;
+    for (int s = -1; s <= 1; s += 2) {
+      const float t = ((float)s * ek - pk) / dk;
+      if (t > 0.f && t < 1.f) ts[nt++] = t;
+    }
+  }
+  for (int i = 1; i < nt; ++i) {  // insertion sort
+    const float x = ts[i];
+    int j = i - 1;
+    while (j >= 0 && x < ts[j]) { ts[j + 1] = ts[j]; --j; }
+    ts[j + 1] = x;
+  }
+  float best_t = 0.f, best_f = box_dist2(p0, e);
+  for (int i = 0; i + 1 < nt; ++i) {
+    const float ta = ts[i], tb = ts[i + 1];
+    const V3 pm = p0 + dv * ((ta + tb) * 0.5f);
+    float num = 0.f, den = 0.f;
+    for (int k = 0; k < 3; ++k) {
+      const float pk = comp(pm, k), ek = comp(e, k), dk = comp(dv, k);
+      if (!(ek < fabsf(pk))) continue;
+      const float s = (pk > 0.f) ? 1.f : -1.f;
+      num += dk * (s * ek - comp(p0, k));
+      den += dk * dk;
+    }
+    float t = ta;
+    if (den > 0.f) t = fminf(fmaxf(num / den, ta), tb);
+    const float f = box_dist2(p0 + dv * t, e);
+    if (f < best_f) { best_f = f; best_t = t; }
+  }
+  if (box_dist2(p0 + dv, e) < best_f) best_t = 1.f;
+  return best_t;
+}
+// A sphere of radius r at p against the box: normal from the box to the sphere, separation, and
+// the point halfway between the two surfaces.
+__device__ __forceinline__ void sphere_box(V3 p, float r, V3 e, V3& n, float& d, V3& x) {
+  const bool inside = fabsf(p.x) <= e.x && fabsf(p.y) <= e.y && fabsf(p.z) <= e.z;
+  if (!inside) {
+    const V3 q = v3(fminf(fmaxf(p.x, -e.x), e.x), fminf(fmaxf(p.y, -e.y), e.y), fminf(fmaxf(p.z, -e.z), e.z));
+    const V3 dl = p - q;
+    const float dist = sqrtf(dot(dl, dl));
+    n = dl * (1.f / dist);
+    d = dist - r;
+  } else {
+    int kb = 0;
+    float best = e.x - fabsf(p.x);
+    if (e.y - fabsf(p.y) < best) { best = e.y - fabsf(p.y); kb = 1; }
+    if (e.z - fabsf(p.z) < best) { best = e.z - fabsf(p.z); kb = 2; }
+    const float s = (comp(p, kb) < 0.f) ? -1.f : 1.f;
+    n = v3(kb == 0 ? s : 0.f, kb == 1 ? s : 0.f, kb == 2 ? s : 0.f);
+    d = -best - r;
+  }
+  x = p - n * (r + 0.5f * d);
+}
+// The part of the segment over the box face selected by the closest point: clip to the slabs of
+// the two axes other than the one along which the normal at t* is largest.
+__device__ __forceinline__ bool face_clip(V3 p0, V3 dv, V3 e, float r, float tstar, float& ta, float& tb) {
+  V3 n, x;
+  float d;
+  sphere_box(p0 + dv * tstar, r, e, n, d, x);
+  int kn = 0;
+  if (fabsf(n.x) < fabsf(n.y)) kn = 1;
+  if (fabsf(comp(n, kn)) < fabsf(n.z)) kn = 2;
+  ta = 0.f;
+  tb = 1.f;
+  for (int j = 0; j < 3; ++j) {
+    if (j == kn) continue;
+    const float dj = comp(dv, j), pj = comp(p0, j), ej = comp(e, j);
+    if (dj == 0.f) {
+      if (ej < fabsf(pj)) return false;
+      continue;
+    }
+    float t0 = (-ej - pj) / dj, t1 = (ej - pj) / dj;
+    if (t1 < t0) { const float s = t0; t0 = t1; t1 = s; }
+    ta = fmaxf(ta, t0);
+    tb = fminf(tb, t1);
+  }
+  return !(tb < ta);
+}
+// Friction directions of a contact normal: anchor e_x if |n_x| < 0.57735, else e_y if
+// |n_y| < 0.57735, else e_z; t1 = normalise(anchor - (anchor . n) n), t2 = n x t1.
+__device__ __forceinline__ void tangent_basis(V3 n, V3& t1, V3& t2) {
+  V3 an = (fabsf(n.x) < 0.57735f) ? v3(1.f, 0.f, 0.f) : ((fabsf(n.y) < 0.57735f) ? v3(0.f, 1.f, 0.f) : v3(0.f, 0.f, 1.f));
+  const V3 t = an - n * dot(an, n);
+  t1 = t * (1.f / sqrtf(dot(t, t)));
+  t2 = cross(n, t1);
+}
+
 // Row header words (float4 per row, constant during the solve):
 //   x: separation d (limit / normal rows) or friction coefficient (friction rows)
 //   y: 1 / (J M^-1 J^T), 0 for a row without response (skipped)
@@ -126,7 +230,7 @@ __device__ __forceinline__ void fnv1a(unsigned& h, int v) {
 // (dir 0 = normal e_z, 1 = e_x, 2 = e_y).
 
 // ---------------------------------------------------------------------------------------------
-template <int G>
+template <int G, bool GROWS>
 __global__ void __launch_bounds__(128, 4) step_kernel(const StepArgs A) {
   extern __shared__ __align__(16) float smem[];
   const EnvTypeTable* __restrict__ T = A.type;
@@ -138,13 +242,18 @@ __global__ void __launch_bounds__(128, 4) step_kernel(const StepArgs A) {
   const int env = A.env_ids ? A.env_ids[gi] : A.env_first + gi;
   const SmemLayout& Ly = A.lay;
   float* sm = smem + grp_blk * Ly.total;
+  // contact and row blocks: shared memory, or (GROWS) this group's private slot of global scratch
+  // (slot = group index; the dead groups of the last block own the slots past the launched envs)
+  float* rb = sm;
+  if (GROWS) rb = A.scratch + (size_t)grp * Ly.scratch_words;
   int* smi = reinterpret_cast<int*>(sm);
+  int* rbi = reinterpret_cast<int*>(rb);
 
   const int L = T->n_links, n = T->n_gen, NS = T->n_shapes;
   const int maxdepth = T->max_depth;
   const int RS = Ly.RS, MS = Ly.MS, CC = Ly.ccap, RC = Ly.rcap;
   float* s_link = sm + Ly.link;  // phase 1: per-link hand-off slots of the inward sweep
-  float* s_Y = sm + Ly.Y;        // phase 2 (aliases phase 1): Y = L^-1 J^T, n x RS
+  float* s_Y = rb + Ly.Y;        // phase 2 (aliases phase 1 in shared memory): Y = L^-1 J^T, n x RS
   float* s_SD = sm + Ly.SD;      // motion subspace column of every generalized DOF
   float* s_M = sm + Ly.M;        // Cholesky factor L (lower), n x MS
   float* s_qdd = sm + Ly.vec;
@@ -152,12 +261,13 @@ __global__ void __launch_bounds__(128, 4) step_kernel(const StepArgs A) {
   float* s_vf = s_v0 + n;
   float* s_dq = s_vf + n;
   float* s_Linv = s_dq + n;
-  float* s_con = sm + Ly.con;
-  int* s_coni = smi + Ly.con;
-  float4* s_rowc = reinterpret_cast<float4*>(sm + Ly.rowc);
-  float* s_lam = sm + Ly.lam;
-  int* s_rowa = smi + Ly.rowa;
+  float* s_con = rb + Ly.con;
+  int* s_coni = rbi + Ly.con;
+  float4* s_rowc = reinterpret_cast<float4*>(rb + Ly.rowc);
+  float* s_lam = rb + Ly.lam;
+  int* s_rowa = rbi + Ly.rowa;
   float* s_frc = sm + Ly.frc;
+  (void)smi;
   // warm-start impulse cache of this env, read and rewritten in place in global memory (each
   // entry is touched once per substep; only live groups store)
   float* gcache = A.cache + (size_t)env * A.cache_stride;
@@ -175,6 +285,9 @@ __global__ void __launch_bounds__(128, 4) step_kernel(const StepArgs A) {
   const bool free_root = is_root && jt == kFree;
   const bool has_dof = isl && (jt == kRevolute || jt == kPrismatic);
   const bool isg = lane < n;
+  // 17-word contact records (body b, normal, offset); shape pairs exist only in the global-rows
+  // variant, so the shared-memory variant compiles without the pair phase
+  const bool has_pairs = GROWS && T->n_pairs > 0;
 
   // ---- load state (one HBM read per env-step) ----
   const int dof_base = A.env_dof_base[env];
@@ -182,7 +295,7 @@ __global__ void __launch_bounds__(128, 4) step_kernel(const StepArgs A) {
   V3 rp = v3(0.f, 0.f, 0.f), rw = rp, rv = rp;  // root pose / velocity (root lanes)
   float q = 0.f, qd = 0.f, tau = 0.f;
   if (is_root) {
-    const float* r = A.root + (size_t)(env * A.actors_per_env + T->actor[l]) * 13;
+    const float* r = A.root + (size_t)(A.env_actor_base[env] + T->actor[l]) * 13;
     rp = v3(r[0], r[1], r[2]);
     rq[0] = r[3]; rq[1] = r[4]; rq[2] = r[5]; rq[3] = r[6];
     if (free_root) {
@@ -384,9 +497,116 @@ __global__ void __launch_bounds__(128, 4) step_kernel(const StepArgs A) {
             s_coni[6 * CC + o] = coff_s + k;
             s_coni[7 * CC + o] = lane;
             s_coni[8 * CC + o] = k;
+            if (has_pairs) {  // ground-only types use the 9-word record: body b = ground, n = +z
+              s_coni[9 * CC + o] = -1;
+              s_coni[10 * CC + o] = -1;
+              s_con[11 * CC + o] = 0.f;
+              s_con[12 * CC + o] = 0.f;
+              s_con[13 * CC + o] = 1.f;
+              s_con[14 * CC + o] = 0.f;
+              s_con[15 * CC + o] = 0.f;
+              s_con[16 * CC + o] = 0.f;
+            }
             ++o;
           }
         }
+      }
+      // ---- capsule-box pairs (lane = pair, in chunks of G), appended in pair / slot order ----
+      for (int pc = 0; has_pairs && pc < T->n_pairs; pc += G) {
+        const int p = pc + lane;
+        const bool isp = p < T->n_pairs;
+        const int sa = isp ? T->pair_a[p] : 0, sb = isp ? T->pair_b[p] : 0;
+        const bool a_cap = T->shape_type[sa] == kCapsule;
+        const int sc = a_cap ? sa : sb, sx = a_cap ? sb : sa;  // the capsule and the box
+        const int lc = T->shape_link[sc], lx = T->shape_link[sx];
+        const int rc = T->aroot[lc], rxl = T->aroot[lx];
+        float Rc[9], Rx[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) { Rc[k] = Grp<G>::get(Rw[k], lc); Rx[k] = Grp<G>::get(Rw[k], lx); }
+        const V3 Pc = v3(Grp<G>::get(P.x, lc), Grp<G>::get(P.y, lc), Grp<G>::get(P.z, lc));
+        const V3 Px = v3(Grp<G>::get(P.x, lx), Grp<G>::get(P.y, lx), Grp<G>::get(P.z, lx));
+        const V3 Oc = v3(Grp<G>::get(rp.x, rc), Grp<G>::get(rp.y, rc), Grp<G>::get(rp.z, rc));
+        const V3 Ox = v3(Grp<G>::get(rp.x, rxl), Grp<G>::get(rp.y, rxl), Grp<G>::get(rp.z, rxl));
+        unsigned pk = 0u;
+        V3 pn[kPairSlots], px[kPairSlots];
+        float pd[kPairSlots];
+        V3 Rb3[3];
+        V3 cb = v3(0.f, 0.f, 0.f);
+        if (isp) {
+          float Rsh[9], Rcs[9], Rb[9];
+#pragma unroll
+          for (int k = 0; k < 9; ++k) Rsh[k] = T->shape_rot[k][sc];
+          mm(Rc, Rsh, Rcs);
+#pragma unroll
+          for (int k = 0; k < 9; ++k) Rsh[k] = T->shape_rot[k][sx];
+          mm(Rx, Rsh, Rb);
+          // everything relative to the box actor's origin
+          const V3 cc = Pc + mv(Rc, v3(T->shape_pos[0][sc], T->shape_pos[1][sc], T->shape_pos[2][sc])) + (Oc - Ox);
+          cb = Px + mv(Rx, v3(T->shape_pos[0][sx], T->shape_pos[1][sx], T->shape_pos[2][sx]));
+          const float r = T->shape_size[0][sc], hl = T->shape_size[1][sc];
+          const V3 ax = v3(Rcs[0], Rcs[3], Rcs[6]);
+          const V3 e = v3(T->shape_size[0][sx], T->shape_size[1][sx], T->shape_size[2][sx]);
+          Rb3[0] = v3(Rb[0], Rb[3], Rb[6]);  // box axes (columns) in world
+          Rb3[1] = v3(Rb[1], Rb[4], Rb[7]);
+          Rb3[2] = v3(Rb[2], Rb[5], Rb[8]);
+          const V3 w0 = cc - ax * hl - cb, w1 = cc + ax * hl - cb;
+          const V3 p0 = v3(dot(Rb3[0], w0), dot(Rb3[1], w0), dot(Rb3[2], w0));
+          const V3 p1 = v3(dot(Rb3[0], w1), dot(Rb3[1], w1), dot(Rb3[2], w1));
+          const V3 dv = p1 - p0;
+          const float tstar = segment_box_closest_t(p0, dv, e);
+          float ta, tb;
+          const bool clip = face_clip(p0, dv, e, r, tstar, ta, tb);
+#pragma unroll
+          for (int slot = 0; slot < kPairSlots; ++slot) {
+            float t = (slot == 0) ? 0.f : ((slot == 1) ? 1.f : ((slot == 2) ? ta : ((slot == 3) ? tb : tstar)));
+            bool ok = true;
+            if (slot >= 2) {
+              if (slot < 4 && !clip) ok = false;
+              if (slot == 3 && !(ta < tb)) ok = false;
+              if (!(t > 0.f && t < 1.f)) ok = false;
+            }
+            if (ok) {
+              sphere_box(p0 + dv * t, r, e, pn[slot], pd[slot], px[slot]);
+              if (pd[slot] < coff) pk |= 1u << slot;
+            }
+          }
+        }
+        int nchunk;
+        const int pbase = n_con + Grp<G>::excl_scan(__popc(pk), lane, &nchunk);
+        if (isp && pk) {
+          int o = pbase;
+          const int ao = a_cap ? rc : rxl, bo = a_cap ? rxl : rc;   // actor roots of bodies a and b
+          const V3 Oa = a_cap ? Oc : Ox, Ob = a_cap ? Ox : Oc;
+          const float mu = fmaxf(T->shape_fr[sa], T->shape_fr[sb]);
+          (void)ao; (void)bo;
+#pragma unroll
+          for (int slot = 0; slot < kPairSlots; ++slot) {
+            if (!((pk >> slot) & 1u)) continue;
+            V3 nw = Rb3[0] * pn[slot].x + Rb3[1] * pn[slot].y + Rb3[2] * pn[slot].z;  // box -> capsule
+            if (!a_cap) nw = nw * -1.f;
+            const V3 xw = cb + Rb3[0] * px[slot].x + Rb3[1] * px[slot].y + Rb3[2] * px[slot].z + (Ox - Oa);
+            const V3 dob = Ob - Oa;
+            s_con[0 * CC + o] = xw.x;
+            s_con[1 * CC + o] = xw.y;
+            s_con[2 * CC + o] = xw.z;
+            s_con[3 * CC + o] = pd[slot];
+            s_con[4 * CC + o] = mu;
+            s_coni[5 * CC + o] = a_cap ? lc : lx;
+            s_coni[6 * CC + o] = T->n_ground_cand + kPairSlots * p + slot;
+            s_coni[7 * CC + o] = sa;
+            s_coni[8 * CC + o] = slot;
+            s_coni[9 * CC + o] = a_cap ? lx : lc;
+            s_coni[10 * CC + o] = sb;
+            s_con[11 * CC + o] = nw.x;
+            s_con[12 * CC + o] = nw.y;
+            s_con[13 * CC + o] = nw.z;
+            s_con[14 * CC + o] = dob.x;
+            s_con[15 * CC + o] = dob.y;
+            s_con[16 * CC + o] = dob.z;
+            ++o;
+          }
+        }
+        n_con += nchunk;
       }
       // limit rows in DOF order: link lanes with a limited joint
       int lf = 0;
@@ -437,7 +657,7 @@ __global__ void __launch_bounds__(128, 4) step_kernel(const StepArgs A) {
         fnv1a(sig, n_con);
         for (int c = 0; c < n_con; ++c) {
           fnv1a(sig, s_coni[7 * CC + c]);
-          fnv1a(sig, -1);
+          fnv1a(sig, has_pairs ? s_coni[10 * CC + c] : -1);
           fnv1a(sig, s_coni[8 * CC + c]);
         }
       }
@@ -632,8 +852,10 @@ __global__ void __launch_bounds__(128, 4) step_kernel(const StepArgs A) {
       const float4 hc = s_rowc[r];
       const int a = s_rowa[r];
       const int kind = __float_as_int(hc.z) & 3;
-      float fr[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      unsigned anc = 0u;
+      // contact rows: J_i = S_i . [x_a x k; k] on body a's path, - S_i . [x_b x k; k] on body b's
+      // (x_a, x_b: the contact point relative to each actor's origin; the paths never overlap)
+      float fr[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, fb[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      unsigned anc = 0u, ancb = 0u;
       int gl = -1;
       float sgn = 0.f;
       if (kind == kRowLimit) {
@@ -642,11 +864,23 @@ __global__ void __launch_bounds__(128, 4) step_kernel(const StepArgs A) {
       } else {
         const int c = a & 0xff, dir = (a >> 8) & 3;
         anc = T->anc[s_coni[5 * CC + c]];
+        const int lb = has_pairs ? s_coni[9 * CC + c] : -1;
         const V3 x = v3(s_con[0 * CC + c], s_con[1 * CC + c], s_con[2 * CC + c]);
-        // k = e_z (dir 0), e_x (dir 1), e_y (dir 2); f = [x x k; k]
-        if (dir == 0) { fr[0] = x.y; fr[1] = -x.x; fr[5] = 1.f; }
-        else if (dir == 1) { fr[1] = x.z; fr[2] = -x.y; fr[3] = 1.f; }
-        else { fr[0] = -x.z; fr[2] = x.x; fr[4] = 1.f; }
+        const V3 nrm = has_pairs ? v3(s_con[11 * CC + c], s_con[12 * CC + c], s_con[13 * CC + c]) : v3(0.f, 0.f, 1.f);
+        V3 k = nrm;
+        if (dir != 0) {
+          V3 t1, t2;
+          tangent_basis(nrm, t1, t2);
+          k = (dir == 1) ? t1 : t2;
+        }
+        const V3 xk = cross(x, k);
+        fr[0] = xk.x; fr[1] = xk.y; fr[2] = xk.z; fr[3] = k.x; fr[4] = k.y; fr[5] = k.z;
+        if (lb >= 0) {
+          ancb = T->anc[lb];
+          const V3 xb = x - v3(s_con[14 * CC + c], s_con[15 * CC + c], s_con[16 * CC + c]);
+          const V3 xbk = cross(xb, k);
+          fb[0] = -xbk.x; fb[1] = -xbk.y; fb[2] = -xbk.z; fb[3] = -k.x; fb[4] = -k.y; fb[5] = -k.z;
+        }
       }
       float y[G];
       float asum = 0.f;
@@ -660,6 +894,10 @@ __global__ void __launch_bounds__(128, 4) step_kernel(const StepArgs A) {
             const float* Si = s_SD + 6 * i;
 #pragma unroll
             for (int k = 0; k < 6; ++k) ji += Si[k] * fr[k];
+          } else if ((ancb >> i) & 1u) {
+            const float* Si = s_SD + 6 * i;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) ji += Si[k] * fb[k];
           }
 #pragma unroll
           for (int k = 0; k < i; ++k) ji -= s_M[i * MS + k] * y[k];
@@ -748,15 +986,18 @@ __global__ void __launch_bounds__(128, 4) step_kernel(const StepArgs A) {
     if (live)
       for (int r = lane; r < R; r += G) gcache[__float_as_int(s_rowc[r].w)] = s_lam[r];
     if (isl) {
-      float fx = 0.f, fy = 0.f, fz = 0.f;
+      // impulse lambda_n n + lambda_1 t1 + lambda_2 t2 on body a, the opposite on body b
+      V3 fsum = v3(0.f, 0.f, 0.f);
       for (int c = 0; c < n_con; ++c) {
-        if (s_coni[5 * CC + c] == l) {
-          fz += s_lam[n_lim + c];
-          fx += s_lam[n_lim + n_con + 2 * c];
-          fy += s_lam[n_lim + n_con + 2 * c + 1];
-        }
+        const int la = s_coni[5 * CC + c], lb = has_pairs ? s_coni[9 * CC + c] : -1;
+        if (la != l && lb != l) continue;
+        const V3 nrm = has_pairs ? v3(s_con[11 * CC + c], s_con[12 * CC + c], s_con[13 * CC + c]) : v3(0.f, 0.f, 1.f);
+        V3 t1, t2;
+        tangent_basis(nrm, t1, t2);
+        const V3 imp = nrm * s_lam[n_lim + c] + t1 * s_lam[n_lim + n_con + 2 * c] + t2 * s_lam[n_lim + n_con + 2 * c + 1];
+        fsum = (la == l) ? fsum + imp : fsum - imp;
       }
-      s_frc[3 * l] += fx; s_frc[3 * l + 1] += fy; s_frc[3 * l + 2] += fz;
+      s_frc[3 * l] += fsum.x; s_frc[3 * l + 1] += fsum.y; s_frc[3 * l + 2] += fsum.z;
     }
     __syncwarp();
 
@@ -799,7 +1040,7 @@ __global__ void __launch_bounds__(128, 4) step_kernel(const StepArgs A) {
   status = Grp<G>::any(status);
   if (live) {
     if (is_root) {
-      float* r = A.root + (size_t)(env * A.actors_per_env + T->actor[l]) * 13;
+      float* r = A.root + (size_t)(A.env_actor_base[env] + T->actor[l]) * 13;
       r[0] = rp.x; r[1] = rp.y; r[2] = rp.z;
       r[3] = rq[0]; r[4] = rq[1]; r[5] = rq[2]; r[6] = rq[3];
       r[7] = rv.x; r[8] = rv.y; r[9] = rv.z;
@@ -819,7 +1060,7 @@ __global__ void __launch_bounds__(128, 4) step_kernel(const StepArgs A) {
     for (int c = lane; c < A.pair_stride; c += G) {
       const bool vc = c < n_con;
       pr[3 * c + 0] = vc ? s_coni[7 * CC + c] : -1;
-      pr[3 * c + 1] = -1;
+      pr[3 * c + 1] = (vc && has_pairs) ? s_coni[10 * CC + c] : -1;
       pr[3 * c + 2] = vc ? s_coni[8 * CC + c] : -1;
     }
     if (lane == 0) {

@@ -65,7 +65,7 @@ def per_env_ok(w, g, o, rtol, atol, key, per):
 def compare(w, g, o, rtol, atol, mask):
     """Check root, DOF and net-force parity on the envs in mask; return a report dict."""
     rep = {}
-    for key, per in (("root", lambda e: w.actors_per_env), ("dof", w.env_jdof), ("net_force", w.env_body)):
+    for key, per in (("root", w.env_actor_count), ("dof", w.env_jdof), ("net_force", w.env_body)):
         ok, worst = per_env_ok(w, g, o, rtol, atol, key, per)
         rep[key] = (ok, worst)
     return rep
@@ -98,7 +98,7 @@ def fp32_scales(w, root, dof, acts, steps, rtol=1e-4, atol=1e-5):
             snaps.append(dict(root=r.copy(), dof=d.copy(), net_force=nf))
         runs.append(snaps)
     scales = []
-    per = {"root": lambda e: w.actors_per_env, "dof": w.env_jdof, "net_force": w.env_body}
+    per = {"root": w.env_actor_count, "dof": w.env_jdof, "net_force": w.env_body}
     for k in range(steps):
         sk = {}
         for key, pf in per.items():

@@ -37,10 +37,11 @@ def cuda():
 
 
 def workload(name, n_envs):
-    return {"cartpole": W.cartpole_workload, "ant": W.ant_workload, "humanoid": W.humanoid_workload}[name](n_envs)
+    return {"cartpole": W.cartpole_workload, "ant": W.ant_workload, "humanoid": W.humanoid_workload,
+            "hand": W.hand_workload, "mixed": W.mixed_workload}[name](n_envs)
 
 
-PER = {"root": lambda w: (lambda e: w.actors_per_env), "dof": lambda w: w.env_jdof, "net_force": lambda w: w.env_body}
+PER = {"root": lambda w: w.env_actor_count, "dof": lambda w: w.env_jdof, "net_force": lambda w: w.env_body}
 
 
 def check_rollout(w, steps, rtol, atol, seed=0, min_same=0.75):
@@ -84,23 +85,25 @@ def check_rollout(w, steps, rtol, atol, seed=0, min_same=0.75):
     return g, o, same
 
 
-@pytest.mark.parametrize("name,n_envs", [("cartpole", 64), ("cartpole", 67), ("ant", 67), ("humanoid", 37)])
+@pytest.mark.parametrize("name,n_envs", [("cartpole", 64), ("cartpole", 67), ("ant", 67), ("humanoid", 37),
+                                         ("hand", 37), ("mixed", 67)])
 def test_one_step(name, n_envs):
     """One env-step (2 substeps) at 1e-4 relative / 1e-5 absolute; sizes span several CTAs and a
     ragged last block."""
     check_rollout(workload(name, n_envs), 1, 1e-4, 1e-5, min_same=0.9)
 
 
-@pytest.mark.parametrize("name,n_envs", [("cartpole", 64), ("ant", 67), ("humanoid", 37)])
+@pytest.mark.parametrize("name,n_envs", [("cartpole", 64), ("ant", 67), ("humanoid", 37), ("hand", 37),
+                                         ("mixed", 67)])
 def test_sixteen_steps(name, n_envs):
     """16 env-steps at 1e-3 relative / absolute on envs whose constraint sets never changed."""
     check_rollout(workload(name, n_envs), 16, 1e-3, 1e-3)
 
 
-@pytest.mark.parametrize("name", ["ant", "humanoid"])
-def test_full_size_one_step(name):
-    """The bench's configuration (4096 envs, one launch per step) against the oracle on all envs."""
-    check_rollout(workload(name, 4096), 1, 1e-4, 1e-5, min_same=0.9)
+@pytest.mark.parametrize("name,n_envs", [("ant", 4096), ("humanoid", 4096), ("hand", 4096), ("mixed", 16384)])
+def test_full_size_one_step(name, n_envs):
+    """Full-size configurations (one launch per env type and step) against the oracle on all envs."""
+    check_rollout(workload(name, n_envs), 1, 1e-4, 1e-5, min_same=0.9)
 
 
 def test_impulse_cache_and_forces_match():
@@ -151,6 +154,66 @@ def test_heterogeneous_batch_two_types():
     eam = np.array([i % 2 for i in range(n)], np.int32)
     w = W.Workload("mixed", [ant, hum], eam, 1, n, W.Params())
     check_rollout(w, 4, 1e-3, 1e-3)
+
+
+def test_box_rests_on_two_capsules_gpu():
+    """Capsule-box pair contacts on the GPU: a box laid across two fixed capsules comes to rest
+    0.57 m up with the pair contacts carrying its weight; the first step's contact list (shape a,
+    shape b, slot) equals the oracle's."""
+    import torch
+    from paper_2108_10470_gb300 import sim
+    from scenes import two_actor_env
+
+    qy = W.Q_X_TO_Y
+    w, root = two_actor_env([(-0.03, 0, 0.5), (0.03, 0, 0.5)], [qy, qy], (0, 0, 0.5 + 0.02 + 0.05))
+    o = oracle_rollout(w, root, np.zeros((0, 2)), np.zeros((1, 0)), 1)
+    s = sim.Sim(w)
+    s.root_state.copy_(torch.from_numpy(root))
+    for k in range(600):
+        s.step()
+        if k == 0:
+            n = int(s.contact_count.cpu()[0])
+            assert n == int(o[0]["n_pairs"][0]) and n >= 2
+            assert np.array_equal(s.contact_pairs.cpu().numpy()[0, :n], o[0]["pairs"][0, :n])
+    r = s.root_state.cpu().numpy()
+    f = s.net_contact_force.cpu().numpy()
+    assert not s.status.cpu().numpy().any()
+    assert np.abs(r[1, 7:13]).max() < 1e-3 and abs(r[1, 2] - 0.57) < 1e-3
+    assert abs(f[1, 2] - 0.2 * 9.81) < 0.01 * 0.2 * 9.81
+    assert np.allclose(f[0], -f[1], atol=1e-4)
+    s.destroy()
+
+
+def test_padded_actor_lists_map_rows():
+    """Envs with fewer actors than the widest (-1 padding): the root-state rows run on without gaps
+    and a row reset through the indexed setter lands on the right env."""
+    import torch
+    from paper_2108_10470_gb300 import sim
+
+    w = W.mixed_workload(40)
+    root, dof, acts = W.seeded_inputs(w, 1, 2)
+    counts = [w.env_actor_count(e) for e in range(w.n_envs)]
+    assert root.shape[0] == sum(counts) < 2 * w.n_envs
+    check_rollout(w, 2, 1e-3, 1e-3)
+    # reset the second actor (the cube) of the first two-actor env: only that env's cache clears
+    e = counts.index(2)
+    a = sum(counts[:e]) + 1
+    s = sim.Sim(w)
+    s.root_state.copy_(torch.from_numpy(root))
+    s.dof_state.copy_(torch.from_numpy(dof))
+    s.dof_actuation.copy_(torch.from_numpy(acts[0]))
+    s.step()
+    before = s.impulse_cache.clone()
+    assert before[e].abs().sum() > 0
+    new_root = s.root_state[a:a + 1].clone()
+    new_root[0, 2] += 0.1
+    s.set_root_state_indexed(new_root, torch.tensor([a], dtype=torch.int32, device="cuda"))
+    torch.cuda.synchronize()
+    assert torch.equal(s.root_state[a], new_root[0])
+    assert torch.all(s.impulse_cache[e] == 0)
+    keep = [i for i in range(w.n_envs) if i != e]
+    assert torch.equal(s.impulse_cache[keep], before[keep])
+    s.destroy()
 
 
 def test_single_env_and_no_contacts():

@@ -8,6 +8,7 @@ import pytest
 
 import oracle
 from paper_2108_10470_gb300 import workloads as W
+from scenes import two_actor_env
 
 E = np.array([0.1, 0.1, 0.1])
 
@@ -75,22 +76,6 @@ def test_closest_point_brute_force(seed):
             assert abs(s[k]["d"] - (np.linalg.norm(out) - r)) < 1e-12
         else:
             assert abs(s[k]["d"] - (-(ext - np.abs(p)).min() - r)) < 1e-12
-
-
-def two_actor_env(cap_pos, cap_quat, box_pos, params=None):
-    """Fixed-base actor holding one capsule (radius 0.02, half length 0.1) and a free 0.2 kg box
-    (half extents 0.05)."""
-    b = W._Builder("holder")
-    root = b.link(-1, W.JOINT_FIXED, mass=1.0, inertia=(0.1, 0.1, 0.1, 0, 0, 0))
-    for p, q in zip(cap_pos, cap_quat):
-        b.shape(root, W.SHAPE_CAPSULE, (0.02, 0.1), pos=p, quat=q)
-    holder = b.build()
-    box = W.free_box(0.05, 0.05, 0.05, mass=0.2)
-    w = W.Workload("pair", [holder, box], np.array([0, 1], np.int32), 2, 1, params or W.Params())
-    root_st = np.zeros((2, 13))
-    root_st[:, 6] = 1.0
-    root_st[1, 0:3] = box_pos
-    return w, root_st
 
 
 def test_box_rests_on_two_capsules():
