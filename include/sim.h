@@ -100,6 +100,11 @@ typedef struct {
 } sim_params;
 
 /* ---- views ----------------------------------------------------------------------------------- */
+/* CONTACT_PAIRS rows: shape indices are env-local (actors in row order, shapes in model order);
+ * shape_a is the shape on body a (the contact normal points from body b to body a). For a ground
+ * contact slot is the sample on shape_a (sphere 0, capsule ends 0 and 1, box corners 0..7); for a
+ * capsule-box pair it is 0 / 1 (capsule segment ends), 2 / 3 (ends of the segment part over the
+ * box face or edge nearest the closest point) or 4 (closest point of segment and box). */
 enum {
   SIM_VIEW_ROOT_STATE = 0,        /* (N_A, 13) f32 [p 3 | quat 4 | v 3 | omega 3] world; v = root origin velocity. Get/Set */
   SIM_VIEW_DOF_STATE = 1,         /* (N_D, 2)  f32 [q, qd]. Get/Set                                                        */
@@ -123,12 +128,17 @@ typedef struct {
 
 typedef struct sim_s* sim_handle;
 
-/* Create a simulation of n_envs environments. Env e consists of actors_per_env actors whose model
- * indices are env_actor_model[e*actors_per_env + a] (host array). Actor roots are numbered
- * env-major in the root tensor (N_A = n_envs * actors_per_env); joint DOFs and non-virtual bodies
- * are numbered env-major, then actor, then link. cuda_stream is a cudaStream_t (NULL = legacy
- * default stream). Initial state: every root at its origin with identity orientation, zero
- * velocities and joint positions, zero actuation. Errors: INVALID_ARG, TOPOLOGY, CAPACITY, CUDA,
+/* Create a simulation of n_envs environments. Row e of env_actor_model (host array, n_envs x
+ * actors_per_env, actors_per_env <= 8) lists the model indices of env e's actors; entries of -1
+ * pad envs with fewer actors (every env needs at least one). Actor roots are numbered env-major,
+ * then in row order, in the root tensor (N_A = number of non-negative entries); joint DOFs and
+ * non-virtual bodies are numbered env-major, then actor, then link. Envs with the same actor list
+ * form one env type (one launch per type and step). Within an env, shapes of different actors
+ * collide pairwise when one is a capsule and the other a box; every shape collides with the
+ * ground plane z = 0. cuda_stream is a cudaStream_t (NULL = legacy default stream). Initial
+ * state: every root at its origin with identity orientation, zero velocities and joint
+ * positions, zero actuation. Errors: INVALID_ARG, TOPOLOGY, CAPACITY (more than 32 links, 32
+ * generalized DOFs, 32 shapes, 32 capsule-box pairs or 256 contact candidates in one env), CUDA,
  * NO_DEVICE; *out is set only on success. Environments never interact (paper: each environment
  * is simulated without interaction with the others). */
 int sim_create(const sim_model_desc* models, int32_t n_models, const int32_t* env_actor_model,
@@ -136,8 +146,8 @@ int sim_create(const sim_model_desc* models, int32_t n_models, const int32_t* en
                sim_handle* out);
 
 /* Advance every environment by dt using `substeps` equal substeps (paper: control dt vs.
- * simulation dt). Each substep: forward kinematics, articulated-body forward dynamics, ground
- * contact and joint-limit rows, pos_iters + vel_iters TGS-style Gauss-Seidel iterations,
+ * simulation dt). Each substep: forward kinematics, articulated-body forward dynamics, ground and
+ * capsule-box contact rows and joint-limit rows, pos_iters + vel_iters TGS-style Gauss-Seidel iterations,
  * integration. Reads DOF_ACTUATION, updates ROOT_STATE, DOF_STATE, NET_CONTACT_FORCE, the contact
  * views, IMPULSE_CACHE and STATUS. Asynchronous on the handle's stream. Errors: HANDLE,
  * INVALID_ARG (dt <= 0 or non-finite, substeps < 1), CUDA (launch failure). */
