@@ -160,6 +160,46 @@ int sim_step(sim_handle h, float dt, int32_t substeps);
 int sim_step_host(sim_handle h, const float* host_actuation, float* host_root_out, float* host_dof_out,
                   float dt, int32_t substeps);
 
+/* ---- step without allocation ------------------------------------------------------------------
+ * The paper has no counterpart to this call; it serves callers that cannot allocate device
+ * memory when they step: a host application that hands out all device memory from a pool it
+ * reserved up front, or a control loop that must not enter the driver's allocator while it runs.
+ * They create the handle once, at set-up, and then step on state buffers they own.
+ *
+ * Caller-owned state, one device pointer per view of the same name, with that view's shape and
+ * element layout (sizes from sim_get_sizes; C = contact pairs per env, K = impulse-cache length
+ * per env). The library never frees or keeps these pointers beyond the call. */
+typedef struct {
+  float* root_state;          /* (N_A, 13) read and written */
+  float* dof_state;           /* (N_D, 2) read and written (any 4-byte-aligned buffer when N_D = 0) */
+  const float* dof_actuation; /* (N_D,) read */
+  float* net_contact_force;   /* (N_B, 3) written */
+  float* impulse_cache;       /* (n_envs, K) read and written; zero it for a fresh start */
+  int32_t* contact_pairs;     /* (n_envs, C, 3) written */
+  int32_t* contact_count;     /* (n_envs,) written */
+  uint32_t* signature;        /* (n_envs,) written when SIM_FLAG_SIGNATURE is set */
+  int32_t* status;            /* (n_envs,) written */
+} sim_state_buffers;
+
+/* The step of sim_step on the buffers in *io, with no device allocation in the call: env types
+ * whose contact and row blocks do not fit in shared memory keep them in a scratch array built
+ * into the library (64 MiB, a file-scope device array: every device where the library's device
+ * code is loaded holds it until the process exits) instead of the handle's own scratch. The
+ * handle supplies only the model tables and its stream; its views are not touched.
+ * Limit: each such env type needs its env count, rounded up to a whole CTA (128 / G envs, G the
+ * lanes per env), times its per-env scratch within 64 MiB (a hand-with-cube env uses about 62 KB,
+ * so about 1050 of them fit); a larger type fails with CAPACITY and a message giving the sizes,
+ * before anything is launched. Env types that fit in shared memory have no limit.
+ * First call: the first call on a device looks up the array's device address (with that device
+ * made current, the caller's device restored); make that first call before any stream capture.
+ * Sharing: every call, from every handle on a device, uses the same array, which keeps the last
+ * call's contents. Nothing in it needs to start at zero (each step writes every scratch word
+ * before reading it). Calls whose kernels overlap on the GPU (different streams without ordering
+ * between them) race on the array and give wrong results: order them on one stream or with
+ * events. Asynchronous on the handle's stream. Errors: HANDLE, INVALID_ARG (a NULL buffer,
+ * dt <= 0 or non-finite, substeps < 1), CAPACITY (above), CUDA. */
+int sim_step_static_scratch(sim_handle h, const sim_state_buffers* io, float dt, int32_t substeps);
+
 /* Describe one of the SIM_VIEW_* device tensors. Errors: HANDLE, INVALID_ARG. */
 int sim_get_view(sim_handle h, int32_t which, sim_view* out);
 

@@ -426,6 +426,47 @@ __global__ void fma_probe_kernel(float* out, int iters, float seed) {
 }  // namespace
 
 // ================================================================================================
+// ---- scratch of sim_step_static_scratch ---------------------------------------------------------
+// Env types whose contact and row blocks do not fit in shared memory keep them in global scratch.
+// sim_step uses the per-type buffers that sim_create allocated; sim_step_static_scratch uses this
+// file-scope array instead, so that call allocates nothing. The array (64 MiB) exists on every
+// device where the library's device code is loaded, from that load until the process exits. In
+// host code its name is a stand-in for the device symbol, never an address: the address on each
+// device comes from cudaGetSymbolAddress.
+constexpr size_t kStaticScratchBytes = size_t(64) << 20;
+static __device__ __align__(256) float g_static_scratch[kStaticScratchBytes / sizeof(float)];
+
+namespace {
+
+constexpr int kMaxStaticDevices = 64;
+std::mutex g_static_mu;
+float* g_static_addr[kMaxStaticDevices] = {};
+
+// Device address of g_static_scratch on device `dev`, looked up on the first request for that
+// device with that device current (the caller's current device is restored afterwards).
+int static_scratch_address(int dev, float** out) {
+  if (dev < 0 || dev >= kMaxStaticDevices) {
+    g_last_error = "sim_step_static_scratch: device ordinal out of range";
+    return SIM_ERR_CAPACITY;
+  }
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_addr[dev]) {
+    int prev = 0;
+    CK(cudaGetDevice(&prev));
+    CK(cudaSetDevice(dev));
+    float* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress((void**)&p, g_static_scratch);
+    const cudaError_t e2 = cudaSetDevice(prev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_static_scratch)");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaSetDevice (restoring the caller's device)");
+    g_static_addr[dev] = p;
+  }
+  *out = g_static_addr[dev];
+  return SIM_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* sim_error_string(int code) {
@@ -634,6 +675,58 @@ int sim_step(sim_handle h, float dt, int32_t substeps) {
     a.lay = tp.lay;
     const cudaError_t e = launch_type(tp, a, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "step_kernel launch");
+  }
+  return SIM_OK;
+}
+
+int sim_step_static_scratch(sim_handle h, const sim_state_buffers* io, float dt, int32_t substeps) {
+  if (!valid_handle(h)) return SIM_ERR_HANDLE;
+  if (!io || !io->root_state || !io->dof_state || !io->dof_actuation || !io->net_contact_force ||
+      !io->impulse_cache || !io->contact_pairs || !io->contact_count || !io->signature || !io->status)
+    return SIM_ERR_INVALID_ARG;
+  if (!(dt > 0.f) || !finite(dt) || substeps < 1) return SIM_ERR_INVALID_ARG;
+  // the types launch one after another on the handle's stream, so each may use the whole array
+  for (const TypePlan& tp : h->types) {
+    if (!tp.lay.grows) continue;
+    const size_t gpb = (size_t)tp.groups_per_block;
+    const size_t slot_bytes = sizeof(float) * (size_t)tp.lay.scratch_words;
+    const size_t slots = (tp.envs.size() + gpb - 1) / gpb * gpb;
+    if (slots * slot_bytes > kStaticScratchBytes) {
+      char buf[320];
+      snprintf(buf, sizeof(buf),
+               "sim_step_static_scratch: an env type of %zu envs needs %zu bytes of scratch (%zu per env), more "
+               "than the %zu-byte static array; at most %zu envs of this type fit",
+               tp.envs.size(), slots * slot_bytes, slot_bytes, kStaticScratchBytes,
+               kStaticScratchBytes / (slot_bytes * gpb) * gpb);
+      g_last_error = buf;
+      return SIM_ERR_CAPACITY;
+    }
+  }
+  float* scratch = nullptr;
+  const int rc = static_scratch_address(h->device, &scratch);
+  if (rc != SIM_OK) return rc;
+  const sim_params& p = h->params;
+  for (size_t t = 0; t < h->types.size(); ++t) {
+    const TypePlan& tp = h->types[t];
+    StepArgs a{};
+    a.type = h->d_types + t;
+    a.env_ids = h->contiguous_single_type ? nullptr : h->d_env_ids + tp.env_off;
+    a.env_first = 0;
+    a.n_launch_envs = (int)tp.envs.size();
+    a.root = io->root_state; a.dof = io->dof_state; a.act = io->dof_actuation; a.net_force = io->net_contact_force;
+    a.cache = io->impulse_cache; a.pairs = io->contact_pairs; a.n_pairs = io->contact_count;
+    a.sig = io->signature; a.status = io->status;
+    a.env_dof_base = h->d_dof_base; a.env_body_base = h->d_body_base; a.env_actor_base = h->d_actor_base;
+    a.scratch = tp.lay.grows ? scratch : nullptr;
+    a.cache_stride = h->cache_stride; a.pair_stride = h->pair_stride;
+    a.dt = dt; a.h = dt / (float)substeps; a.substeps = substeps;
+    a.gx = p.gravity[0]; a.gy = p.gravity[1]; a.gz = p.gravity[2];
+    a.pos_iters = p.pos_iters; a.vel_iters = p.vel_iters;
+    a.contact_offset = p.contact_offset; a.limit_margin = p.limit_margin;
+    a.bias_coef = p.bias_coef; a.max_depen_vel = p.max_depen_vel; a.flags = p.flags;
+    a.lay = tp.lay;
+    const cudaError_t e = launch_type(tp, a, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "step_kernel launch (static scratch)");
   }
   return SIM_OK;
 }

@@ -25,7 +25,7 @@ SIM_FLAG_SIGNATURE = 1
  SIM_VIEW_IMPULSE_CACHE) = range(9)
 EXPORTED = ("sim_create", "sim_step", "sim_step_host", "sim_get_view", "sim_set_root_state_indexed",
             "sim_set_dof_state_indexed", "sim_set_stream", "sim_sync_status", "sim_get_sizes", "sim_destroy",
-            "sim_error_string", "sim_last_error_message", "sim_probe_fp32_peak")
+            "sim_error_string", "sim_last_error_message", "sim_probe_fp32_peak", "sim_step_static_scratch")
 
 F = ctypes.POINTER(ctypes.c_float)
 I32 = ctypes.POINTER(ctypes.c_int32)
@@ -54,6 +54,14 @@ class sim_view(ctypes.Structure):
 _lib = None
 
 
+class sim_state_buffers(ctypes.Structure):
+    """Caller-owned device state of sim_step_static_scratch (one pointer per view)."""
+    _fields_ = [("root_state", ctypes.c_void_p), ("dof_state", ctypes.c_void_p), ("dof_actuation", ctypes.c_void_p),
+                ("net_contact_force", ctypes.c_void_p), ("impulse_cache", ctypes.c_void_p),
+                ("contact_pairs", ctypes.c_void_p), ("contact_count", ctypes.c_void_p), ("signature", ctypes.c_void_p),
+                ("status", ctypes.c_void_p)]
+
+
 def load(path: Optional[str] = None) -> ctypes.CDLL:
     """Load libartsim.so (raises if it has not been built: there is no fallback path)."""
     global _lib
@@ -79,6 +87,8 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     L.sim_last_error_message.argtypes = []
     L.sim_last_error_message.restype = ctypes.c_char_p
     L.sim_probe_fp32_peak.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]
+    L.sim_step_static_scratch.argtypes = [ctypes.c_void_p, ctypes.POINTER(sim_state_buffers), ctypes.c_float,
+                                          ctypes.c_int32]
     _lib = L  # every other entry point returns int, ctypes' default restype
     return L
 
@@ -204,6 +214,18 @@ class Sim:
         check(load().sim_step_host(self.h, fp(act), fp(root_out), fp(dof_out),
                                    float(self.w.dt if dt is None else dt),
                                    int(self.w.substeps if substeps is None else substeps)), "sim_step_host")
+
+    STATE_NAMES = ("root_state", "dof_state", "dof_actuation", "net_contact_force", "impulse_cache", "contact_pairs",
+                   "contact_count", "signature", "status")
+
+    def step_static_scratch(self, bufs: dict, dt: Optional[float] = None, substeps: Optional[int] = None):
+        """The step on caller-owned device tensors (keys STATE_NAMES, each shaped and typed like the
+        view of the same name), with the library's built-in scratch array: the call allocates no
+        device memory."""
+        io = sim_state_buffers(*[ctypes.c_void_p(bufs[k].data_ptr()) for k in self.STATE_NAMES])
+        check(load().sim_step_static_scratch(self.h, ctypes.byref(io), float(self.w.dt if dt is None else dt),
+                                             int(self.w.substeps if substeps is None else substeps)),
+              "sim_step_static_scratch")
 
     def set_root_state_indexed(self, src, actor_idx):
         n = int(actor_idx.numel())
