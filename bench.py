@@ -6,6 +6,7 @@ into the DOF actuation view. Inputs are resident in HBM before the timed region;
 (256 MiB memset) between timed steps, outside each step's event pair.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload ant|humanoid|cartpole|hand|mixed] [--envs E]
+                  [--persistent] [--graph] [--autotune]
   python bench.py --impl reference ...   # the FP64 CPU oracle timed on the host cores
 
 Under torchrun (N > 1) every rank simulates its own E environments on its own GPU (weak scaling:
@@ -236,7 +237,8 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     w = workload(args.workload, args.envs)
     K, Wm = args.steps, args.warmup
-    s = sim.Sim(w)
+    flags = (sim.SIM_FLAG_PERSISTENT if args.persistent else 0) | (sim.SIM_FLAG_GRAPH if args.graph else 0)
+    s = sim.Sim(w, flags=flags)
     stream = torch.cuda.current_stream()
     root, dof, acts = W.seeded_inputs(w, rank_seed(rank), Wm + K)
     s.root_state.copy_(torch.from_numpy(root))
@@ -246,7 +248,13 @@ def run_ours(args, rank, world, local_rank):
     for k in range(Wm):
         s.dof_actuation.copy_(act_dev[k])
         s.step()
+        if args.autotune and k == Wm // 2:  # tune on a mid-warm-up state; the state is left unchanged
+            s.autotune(reps=5)
     torch.cuda.synchronize()
+    plan = {"launch": "persistent" if args.persistent else "per env type", "graph": bool(args.graph),
+            "autotuned": bool(args.autotune),
+            "types": [{k: c[k] for k in ("lanes_per_env", "rows_global", "warps_per_cta", "n_envs")}
+                      for c in (s.type_config(t) for t in range(s.n_types))]}
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
     if world > 1:
         torch.distributed.barrier()
@@ -292,7 +300,7 @@ def run_ours(args, rank, world, local_rank):
             "config": {"workload": describe(w), "n_envs_per_gpu": w.n_envs, "dt": w.dt, "substeps": w.substeps,
                        "l2": "flushed between timed steps (256 MiB memset outside the step events)",
                        "parallelism": f"replicas x{world} (independent envs per GPU)"},
-            "gpu_launches": launches, "nonfinite_envs": bad,
+            "gpu_launches": launches, "nonfinite_envs": bad, "plan": plan,
             "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
             "e2e": {"value": weak_value(world, w.n_envs, n_e2e, e2e_s), "unit": "env-steps/s",
                     "h2d_bytes_per_step": 4 * n_d, "d2h_bytes_per_step": 4 * (13 * n_a + 2 * n_d),
@@ -309,7 +317,7 @@ def run_ours(args, rank, world, local_rank):
                 "frac": achieved / peak,
                 "traffic": args.traffic if args.traffic is not None else profiled_traffic(args.workload, w.n_envs),
                 "algorithmic_bytes_per_step": algo_bytes_per_step(w),
-                "kernel": "step_kernel", "kernel_ms": 1e3 * kern_avg_s,
+                "kernel": "persistent_step_kernel" if args.persistent else "step_kernel", "kernel_ms": 1e3 * kern_avg_s,
                 "flops_per_env_step": flops_per_env_step,
                 "peak_basis": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (median SM clock sampled "
                               f"in the timed region)"}
@@ -327,6 +335,9 @@ def main():
     ap.add_argument("--workload", default="ant", choices=["ant", "humanoid", "cartpole", "hand", "mixed"])
     ap.add_argument("--envs", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--persistent", action="store_true", help="one persistent launch for all env types")
+    ap.add_argument("--graph", action="store_true", help="replay each step as a captured CUDA graph")
+    ap.add_argument("--autotune", action="store_true", help="autotune the launch knobs during warm-up")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per step-kernel launch from an ncu capture of the same kernel")
     args = ap.parse_args()

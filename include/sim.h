@@ -85,8 +85,11 @@ typedef struct {
 
 /* Solver parameters (paper's simulation-parameter table: gravity, position / velocity iteration
  * counts, max bias, friction; contact offset and limit margin are this library's constants).
- * flags: bit 0 (SIM_FLAG_SIGNATURE) records the per-env constraint-set signature each step. */
-enum { SIM_FLAG_SIGNATURE = 1 };
+ * flags: bit 0 (SIM_FLAG_SIGNATURE) records the per-env constraint-set signature each step;
+ * bit 1 (SIM_FLAG_PERSISTENT) runs every env type of a step in one persistent launch instead of
+ * one launch per env type; bit 2 (SIM_FLAG_GRAPH) makes sim_step capture its launches into a CUDA
+ * graph on first use (again whenever dt or substeps change, or the plan changes) and replay it. */
+enum { SIM_FLAG_SIGNATURE = 1, SIM_FLAG_PERSISTENT = 2, SIM_FLAG_GRAPH = 4 };
 typedef struct {
   float gravity[3];
   int32_t pos_iters;       /* >= 1 biased (position) iterations                  */
@@ -199,6 +202,39 @@ typedef struct {
  * events. Asynchronous on the handle's stream. Errors: HANDLE, INVALID_ARG (a NULL buffer,
  * dt <= 0 or non-finite, substeps < 1), CAPACITY (above), CUDA. */
 int sim_step_static_scratch(sim_handle h, const sim_state_buffers* io, float dt, int32_t substeps);
+
+/* ---- launch plan --------------------------------------------------------------------------------
+ * Envs with the same actor list form an env type. Each type is stepped with a kernel variant
+ * chosen by three knobs: lanes per env (8, 16 or 32; at least the type's largest count of links,
+ * generalized DOFs or shapes), where the solver's contact and row blocks live (shared memory, or
+ * a per-env slot of global scratch; types with capsule-box pairs always use global scratch), and
+ * warps per CTA of its per-type launch (1, 2 or 4). sim_create picks the fewest lanes, shared
+ * rows when the env's arena is at most 24 KB, and 4 warps. (Paper: thousands of environments of
+ * possibly different articulations packed into one simulation; the tuning is this library's.) */
+
+/* Knobs of env type `type` (0 .. out[5] of sim_get_sizes - 1, in order of first appearance):
+ * out[0] lanes per env, out[1] 1 if rows are in global scratch, out[2] warps per CTA, out[3]
+ * number of envs of the type, out[4] fewest lanes the type allows, out[5] lowest env index of the
+ * type. Errors: HANDLE, INVALID_ARG. */
+int sim_get_type_config(sim_handle h, int32_t type, int32_t* out);
+
+/* Set the knobs of env type `type`; results do not depend on them beyond FP32 rounding of
+ * reductions. Synchronises the device when scratch must grow. Drops a captured graph. Errors:
+ * HANDLE, INVALID_ARG (knob out of range, lanes below the type's minimum, shared rows for a type
+ * with shape pairs), CAPACITY (the CTA's arena exceeds 220 KB, or a persistent launch no longer
+ * fits), CUDA. */
+int sim_set_type_config(sim_handle h, int32_t type, int32_t lanes_per_env, int32_t rows_global,
+                        int32_t warps_per_cta);
+
+/* Autotuner: time candidate knobs on the handle's current state and keep the fastest. Without
+ * SIM_FLAG_PERSISTENT each type is tuned on its own launch over every valid (lanes, rows, warps);
+ * with it, (lanes, rows) of each type in turn are tried on the whole persistent step (two passes
+ * of coordinate descent). Each candidate is timed with CUDA events over `reps` steps (1..1000)
+ * after one warm-up step, each step starting from a snapshot of every state tensor; the snapshot
+ * is restored at the end, so the visible state is unchanged. *ms_per_step receives the chosen
+ * plan's median step time. Synchronises the stream; allocates the snapshot for the call's
+ * duration. Errors: HANDLE, INVALID_ARG, CUDA. */
+int sim_autotune(sim_handle h, float dt, int32_t substeps, int32_t reps, double* ms_per_step);
 
 /* Describe one of the SIM_VIEW_* device tensors. Errors: HANDLE, INVALID_ARG. */
 int sim_get_view(sim_handle h, int32_t which, sim_view* out);

@@ -1,23 +1,27 @@
 """Build the CUDA library (libartsim.so) in-tree with nvcc for sm_103a.
 
-One translation unit (csrc/sim_api.cu includes the kernels), compiled with
-``-gencode arch=compute_103a,code=sm_103a``; the CUDA runtime is linked statically so the library
-has no dependency beyond the driver.
+Four translation units compiled in parallel with ``-gencode arch=compute_103a,code=sm_103a``
+(the per-type kernels with shared-memory rows, with global-memory rows, the persistent kernel,
+and the C ABI), then linked into one shared library; the CUDA runtime is linked statically so the
+library has no dependency beyond the driver.
 """
 from __future__ import annotations
 
 import os
 import shutil
 import subprocess
+from concurrent.futures import ThreadPoolExecutor
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB_PATH = os.path.join(HERE, "libartsim.so")
-SOURCES = [os.path.join(CSRC, f) for f in ("sim_api.cu", "step_kernel.cuh", "sim_internal.h")] + \
+UNITS = ("kernels_shared.cu", "kernels_global.cu", "kernels_persistent.cu", "sim_api.cu")
+SOURCES = [os.path.join(CSRC, f) for f in UNITS + ("step_kernel.cuh", "sim_internal.h", "launch.h")] + \
     [os.path.join(INCLUDE, "sim.h")]
-NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
-              "-Xcompiler", "-fPIC", "-shared", "-cudart", "static"]
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+COMPILE_FLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC"]
+LINK_FLAGS = ARCH + ["-shared", "-cudart", "static"]
 
 
 def nvcc() -> str:
@@ -31,11 +35,29 @@ def build_library(force: bool = False, verbose: bool = False) -> str:
     stale = not os.path.exists(LIB_PATH) or any(os.path.getmtime(s) > os.path.getmtime(LIB_PATH) for s in SOURCES)
     if not (force or stale):
         return LIB_PATH
-    tmp = LIB_PATH + f".tmp{os.getpid()}"
-    cmd = [nvcc()] + NVCC_FLAGS + (["-Xptxas", "-v"] if verbose else []) + \
-        ["-o", tmp, os.path.join(CSRC, "sim_api.cu")]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB_PATH)
+    tag = f".tmp{os.getpid()}"
+    objs = [os.path.join(CSRC, u[:-3] + tag + ".o") for u in UNITS]
+
+    def compile_unit(i):
+        cmd = [nvcc()] + COMPILE_FLAGS + (["-Xptxas", "-v"] if verbose else []) + \
+            ["-c", "-o", objs[i], os.path.join(CSRC, UNITS[i])]
+        return subprocess.run(cmd, capture_output=True, text=True)
+
+    try:
+        with ThreadPoolExecutor(len(UNITS)) as ex:
+            results = list(ex.map(compile_unit, range(len(UNITS))))
+        for u, r in zip(UNITS, results):
+            if verbose or r.returncode:
+                print(r.stdout + r.stderr)
+            if r.returncode:
+                raise RuntimeError(f"nvcc failed on {u}")
+        tmp = LIB_PATH + tag
+        subprocess.run([nvcc()] + LINK_FLAGS + ["-o", tmp] + objs, check=True)
+        os.replace(tmp, LIB_PATH)
+    finally:
+        for o in objs:
+            if os.path.exists(o):
+                os.remove(o)
     return LIB_PATH
 
 

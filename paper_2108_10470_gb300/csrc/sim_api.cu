@@ -14,7 +14,7 @@
 
 #include "../../include/sim.h"
 #include "sim_internal.h"
-#include "step_kernel.cuh"
+#include "launch.h"
 
 using namespace artsim;
 
@@ -26,11 +26,17 @@ struct TypePlan {
   EnvTypeTable tab;
   SmemLayout lay;
   std::vector<int> envs;
-  int G = 32;
+  int G = 32;                 // lanes per env (8, 16 or 32)
+  int G_min = 32;             // fewest lanes that hold the type's links, DOFs and shapes
+  int warps_per_cta = 4;      // per-type launches
   int groups_per_block = 4;
   size_t smem_bytes = 0;
-  int env_off = 0;           // offset into the concatenated env-id array
-  float* scratch = nullptr;  // global rows (lay.grows): one slot per env plus one per dead group
+  int env_off = 0;            // offset into the concatenated env-id array
+  float* scratch = nullptr;   // global rows, per-type launches: one slot per group of the launch
+  size_t scratch_floats = 0;
+  float* pscratch = nullptr;  // global rows, persistent launch: one slot per resident group
+  size_t pscratch_floats = 0;
+  double env_cost = 0.0;      // relative cost of one env (persistent tile order)
 };
 
 }  // namespace
@@ -60,6 +66,17 @@ struct sim_s {
   int* n_pairs = nullptr;
   unsigned* sig = nullptr;
   int* status = nullptr;
+  // persistent heterogeneous launch (SIM_FLAG_PERSISTENT)
+  bool persistent = false;
+  int p_grid = 0, p_warps = 0, p_warp_words = 0;
+  size_t p_smem = 0;
+  std::vector<int> p_order;       // env types, costliest first
+  unsigned* d_counter = nullptr;  // tile counter and finished-warp counter
+  // CUDA graph of one step (SIM_FLAG_GRAPH), captured on cap_stream, replayed on stream
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  float graph_dt = 0.f;
+  int graph_substeps = 0;
 };
 
 namespace {
@@ -300,7 +317,12 @@ int build_type(const sim_model_desc* models, const std::vector<int>& actor_model
 // hand-with-cube's ~60 KB does not).
 constexpr int kSharedArenaLimit = 24 * 1024;
 
-SmemLayout make_layout(const EnvTypeTable& T) {
+// Per-CTA dynamic shared memory cap used by the planner.
+constexpr size_t kMaxSmemPerCta = 220 * 1024;
+
+// Layout of one env's arena for G lanes per env; rows_global puts the contact and row blocks in a
+// per-env slot of global scratch instead of shared memory.
+SmemLayout make_layout(const EnvTypeTable& T, int G, bool rows_global) {
   SmemLayout Ly{};
   const int n = std::max(T.n_gen, 1);
   const int L = T.n_links;
@@ -312,23 +334,22 @@ SmemLayout make_layout(const EnvTypeTable& T) {
   // ground-only env types keep the 9-word contact record (no body b, normal +z)
   const int conw = T.n_pairs > 0 ? kConWords : 9;
   int o = 0;
-  const int phase = std::max(L * kLinkWords, n * Ly.RS);
-  Ly.link = o;
-  Ly.Y = o;
-  o += phase;
-  Ly.SD = o; o += 6 * n;
-  Ly.M = o; o += n * Ly.MS;
-  Ly.vec = o; o += 5 * n;
-  Ly.con = o; o += conw * Ly.ccap;
-  o = al4(o);
-  Ly.rowc = o; o += 4 * Ly.rcap;
-  Ly.lam = o; o += Ly.rcap;
-  Ly.rowa = o; o += Ly.rcap;
-  Ly.frc = o; o += 3 * L;
-  Ly.total = al4(o);
-  if (Ly.total * 4 > kSharedArenaLimit || T.n_pairs > 0) {
-    // worst case too large for shared memory, or shape pairs (compiled into this variant only):
-    // contact and row blocks go to a global scratch slot
+  if (!rows_global) {
+    const int phase = std::max(L * kLinkWords, n * Ly.RS);
+    Ly.link = o;
+    Ly.Y = o;
+    o += phase;
+    Ly.SD = o; o += 6 * n;
+    Ly.M = o; o += n * Ly.MS;
+    Ly.vec = o; o += 5 * n;
+    Ly.con = o; o += conw * Ly.ccap;
+    o = al4(o);
+    Ly.rowc = o; o += 4 * Ly.rcap;
+    Ly.lam = o; o += Ly.rcap;
+    Ly.rowa = o; o += Ly.rcap;
+    Ly.frc = o; o += 3 * L;
+    Ly.total = al4(o);
+  } else {
     Ly.grows = 1;
     int g = 0;
     Ly.con = g; g += conw * Ly.ccap;
@@ -338,7 +359,6 @@ SmemLayout make_layout(const EnvTypeTable& T) {
     Ly.rowa = g; g += Ly.rcap;
     Ly.Y = g; g += n * Ly.RS;
     Ly.scratch_words = al4(g);
-    o = 0;
     Ly.link = o; o += L * kLinkWords;
     Ly.SD = o; o += 6 * n;
     Ly.M = o; o += n * Ly.MS;
@@ -349,32 +369,199 @@ SmemLayout make_layout(const EnvTypeTable& T) {
   // Groups that share a warp (G < 32) must not share banks: pad the per-group stride to G mod 32
   // so the g-th group of a warp is shifted by g * G banks (the row stride RS is odd, so each
   // group's lanes also fall on distinct banks).
-  if (T.group < 32)
-    while (Ly.total % 32 != T.group) Ly.total += 4;
+  if (G < 32)
+    while (Ly.total % 32 != G) Ly.total += 4;
   return Ly;
 }
 
-template <int G, bool GR> void set_smem_attr(size_t bytes) {
-  cudaFuncSetAttribute(step_kernel<G, GR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+// Default placement: rows in global scratch when the all-shared arena would exceed
+// kSharedArenaLimit, and always for env types with shape pairs (the pair phase is compiled into
+// the global-rows variant only).
+bool default_rows_global(const EnvTypeTable& T, int G) {
+  return T.n_pairs > 0 || make_layout(T, G, false).total * 4 > kSharedArenaLimit;
 }
 
-template <int G, bool GR> cudaError_t launch_G(const StepArgs& a, int n_envs, int gpb, size_t smem, cudaStream_t st) {
-  const int blocks = (n_envs + gpb - 1) / gpb;
-  step_kernel<G, GR><<<blocks, gpb * G, smem, st>>>(a);
-  return cudaGetLastError();
+cudaError_t launch_type(const TypePlan& tp, const StepArgs& a, const TypeArgs& ta, cudaStream_t st) {
+  return launch_step_kernel(tp.G, tp.lay.grows != 0, a, ta, tp.groups_per_block, tp.smem_bytes, st);
 }
 
-cudaError_t launch_type(const TypePlan& tp, const StepArgs& a, cudaStream_t st) {
-  const int n = a.n_launch_envs, gpb = tp.groups_per_block;
-  const size_t sm = tp.smem_bytes;
-  if (tp.lay.grows) {
-    if (tp.G == 8) return launch_G<8, true>(a, n, gpb, sm, st);
-    if (tp.G == 16) return launch_G<16, true>(a, n, gpb, sm, st);
-    return launch_G<32, true>(a, n, gpb, sm, st);
+int variant_of(const TypePlan& tp) {
+  return (tp.G == 8 ? kVar8 : (tp.G == 16 ? kVar16 : kVar32)) | (tp.lay.grows ? kVarRowsGlobal : 0);
+}
+
+int grow_buffer(float** buf, size_t* have, size_t need, const char* what) {
+  if (need <= *have) return SIM_OK;
+  float* p = nullptr;
+  const cudaError_t e = cudaMalloc(&p, need * sizeof(float));
+  if (e != cudaSuccess) return cuda_fail(e, what);
+  if (*buf) cudaFree(*buf);
+  *buf = p;
+  *have = need;
+  return SIM_OK;
+}
+
+// Lay out one env type for G lanes per env, its rows in shared or global memory, and `warps`
+// warps per CTA of its per-type launch; allocates the per-type scratch that launch needs.
+int configure_type(TypePlan& tp, int G, bool rows_global, int warps, bool per_type_scratch) {
+  if ((G != 8 && G != 16 && G != 32) || G < tp.G_min || (warps != 1 && warps != 2 && warps != 4)) {
+    g_last_error = "type config: lanes per env must be 8, 16 or 32 and hold the type; warps 1, 2 or 4";
+    return SIM_ERR_INVALID_ARG;
   }
-  if (tp.G == 8) return launch_G<8, false>(a, n, gpb, sm, st);
-  if (tp.G == 16) return launch_G<16, false>(a, n, gpb, sm, st);
-  return launch_G<32, false>(a, n, gpb, sm, st);
+  if (tp.tab.n_pairs > 0 && !rows_global) {
+    g_last_error = "type config: env types with shape pairs keep their rows in global memory";
+    return SIM_ERR_INVALID_ARG;
+  }
+  const SmemLayout Ly = make_layout(tp.tab, G, rows_global);
+  const int gpb = warps * 32 / G;
+  const size_t smem = (size_t)gpb * Ly.total * 4;
+  if (smem > kMaxSmemPerCta) {
+    g_last_error = "type config: the CTA's shared arena exceeds 220 KB";
+    return SIM_ERR_CAPACITY;
+  }
+  if (Ly.grows && per_type_scratch) {
+    const size_t slots = (tp.envs.size() + gpb - 1) / gpb * gpb;
+    const int rc = grow_buffer(&tp.scratch, &tp.scratch_floats, slots * (size_t)Ly.scratch_words,
+                               "cudaMalloc (global rows scratch)");
+    if (rc != SIM_OK) return rc;
+  }
+  // the attribute is a cap per kernel instantiation, shared by every type that uses it: set the
+  // planner's maximum rather than this type's size
+  const cudaError_t e = set_step_kernel_smem_cap(G, Ly.grows != 0, kMaxSmemPerCta);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+  tp.G = G;
+  tp.lay = Ly;
+  tp.warps_per_cta = warps;
+  tp.groups_per_block = gpb;
+  tp.smem_bytes = smem;
+  return SIM_OK;
+}
+
+// Resident grid, per-warp arena, global-rows slots and tile order of the persistent launch.
+int plan_persistent(sim_s* h) {
+  if (h->types.size() > (size_t)kMaxPersistTypes) {
+    g_last_error = "persistent launch: more than 8 env types";
+    return SIM_ERR_CAPACITY;
+  }
+  int warp_words = 0;
+  for (const TypePlan& tp : h->types) warp_words = std::max(warp_words, (32 / tp.G) * tp.lay.total);
+  const size_t smem = 4 * (size_t)warp_words * sizeof(float);
+  if (smem > kMaxSmemPerCta) {
+    g_last_error = "persistent launch: four warps' arenas exceed 220 KB";
+    return SIM_ERR_CAPACITY;
+  }
+  CK(set_persistent_kernel_smem_cap(kMaxSmemPerCta));
+  int per_sm = 0, sms = 0;
+  CK(persistent_kernel_occupancy(&per_sm, smem));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+  if (per_sm < 1) {
+    g_last_error = "persistent launch: no CTA fits on an SM";
+    return SIM_ERR_CAPACITY;
+  }
+  h->p_grid = per_sm * sms;
+  h->p_warps = h->p_grid * 4;
+  h->p_smem = smem;
+  h->p_warp_words = warp_words;
+  for (TypePlan& tp : h->types)
+    if (tp.lay.grows) {
+      const size_t need = (size_t)h->p_warps * (32 / tp.G) * tp.lay.scratch_words;
+      const int rc = grow_buffer(&tp.pscratch, &tp.pscratch_floats, need, "cudaMalloc (persistent rows scratch)");
+      if (rc != SIM_OK) return rc;
+    }
+  h->p_order.resize(h->types.size());
+  for (size_t t = 0; t < h->types.size(); ++t) h->p_order[t] = (int)t;
+  std::stable_sort(h->p_order.begin(), h->p_order.end(),
+                   [&](int a, int b) { return h->types[a].env_cost > h->types[b].env_cost; });
+  return SIM_OK;
+}
+
+void drop_graph(sim_s* h) {
+  if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+  h->graph_exec = nullptr;
+}
+
+void fill_common(const sim_s* h, float dt, int substeps, StepArgs& a) {
+  const sim_params& p = h->params;
+  a = StepArgs{};
+  a.root = h->root; a.dof = h->dof; a.act = h->act; a.net_force = h->net_force; a.cache = h->cache;
+  a.pairs = h->pairs; a.n_pairs = h->n_pairs; a.sig = h->sig; a.status = h->status;
+  a.env_dof_base = h->d_dof_base; a.env_body_base = h->d_body_base; a.env_actor_base = h->d_actor_base;
+  a.cache_stride = h->cache_stride; a.pair_stride = h->pair_stride;
+  a.dt = dt; a.h = dt / (float)substeps; a.substeps = substeps;
+  a.gx = p.gravity[0]; a.gy = p.gravity[1]; a.gz = p.gravity[2];
+  a.pos_iters = p.pos_iters; a.vel_iters = p.vel_iters;
+  a.contact_offset = p.contact_offset; a.limit_margin = p.limit_margin;
+  a.bias_coef = p.bias_coef; a.max_depen_vel = p.max_depen_vel; a.flags = p.flags;
+}
+
+void fill_type(const sim_s* h, size_t t, TypeArgs& ta) {
+  const TypePlan& tp = h->types[t];
+  ta = TypeArgs{};
+  ta.type = h->d_types + t;
+  ta.env_ids = h->contiguous_single_type ? nullptr : h->d_env_ids + tp.env_off;
+  ta.env_first = 0;
+  ta.n_launch_envs = (int)tp.envs.size();
+  ta.scratch = tp.scratch;
+  ta.lay = tp.lay;
+}
+
+// Enqueue one step on stream st: one persistent launch, or one launch per env type.
+int launch_step(sim_s* h, cudaStream_t st, float dt, int substeps) {
+  if (h->persistent) {
+    PersistArgs P{};
+    fill_common(h, dt, substeps, P.common);
+    int acc = 0;
+    for (size_t s = 0; s < h->p_order.size(); ++s) {
+      const int k = h->p_order[s];
+      const TypePlan& tp = h->types[k];
+      fill_type(h, (size_t)k, P.types[k]);
+      P.types[k].scratch = tp.lay.grows ? tp.pscratch : nullptr;
+      P.variant[k] = variant_of(tp);
+      P.order[s] = k;
+      const int per = 32 / tp.G;  // envs per warp tile
+      acc += ((int)tp.envs.size() + per - 1) / per;
+      P.tile_end[s] = acc;
+    }
+    P.n_tiles = acc;
+    P.n_warps = h->p_warps;
+    P.warp_words = h->p_warp_words;
+    P.counter = h->d_counter;
+    const cudaError_t e = launch_persistent_kernel(P, h->p_grid, h->p_smem, st);
+    if (e != cudaSuccess) return cuda_fail(e, "persistent_step_kernel launch");
+    return SIM_OK;
+  }
+  StepArgs a;
+  fill_common(h, dt, substeps, a);
+  for (size_t t = 0; t < h->types.size(); ++t) {
+    TypeArgs ta;
+    fill_type(h, t, ta);
+    const cudaError_t e = launch_type(h->types[t], a, ta, st);
+    if (e != cudaSuccess) return cuda_fail(e, "step_kernel launch");
+  }
+  return SIM_OK;
+}
+
+// Capture one step (for this dt / substeps) into a graph on the handle's capture stream.
+int capture_step(sim_s* h, float dt, int substeps) {
+  drop_graph(h);
+  if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+  const int rc = launch_step(h, h->cap_stream, dt, substeps);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+  if (rc != SIM_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  const cudaError_t e2 = cudaGraphInstantiate(&h->graph_exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e2 != cudaSuccess) {
+    h->graph_exec = nullptr;
+    return cuda_fail(e2, "cudaGraphInstantiate");
+  }
+  h->graph_dt = dt;
+  h->graph_substeps = substeps;
+  return SIM_OK;
 }
 
 void free_all(sim_s* h) {
@@ -382,8 +569,13 @@ void free_all(sim_s* h) {
                   h->root, h->dof, h->act, h->net_force, h->cache, h->pairs, h->n_pairs, h->sig, h->status};
   for (void* p : ptrs)
     if (p) cudaFree(p);
-  for (auto& tp : h->types)
+  for (auto& tp : h->types) {
     if (tp.scratch) cudaFree(tp.scratch);
+    if (tp.pscratch) cudaFree(tp.pscratch);
+  }
+  drop_graph(h);
+  if (h->d_counter) cudaFree(h->d_counter);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
 }
 
 __global__ void set_root_kernel(float* root, const float* src, const int* idx, int n, int64_t N_A,
@@ -540,16 +732,9 @@ int sim_create(const sim_model_desc* models, int32_t n_models, const int32_t* en
       TypePlan tp;
       const int rc = build_type(models, key, p, tp.tab);
       if (rc != SIM_OK) { delete h; return rc; }
-      tp.lay = make_layout(tp.tab);
-      tp.G = tp.tab.group;
-      tp.groups_per_block = 128 / tp.G;
-      tp.smem_bytes = (size_t)tp.groups_per_block * tp.lay.total * 4;
-      if (tp.smem_bytes > 220 * 1024) {
-        tp.groups_per_block = std::max(1, (int)((220 * 1024) / ((size_t)tp.lay.total * 4)));
-        while (tp.groups_per_block > 1 && (tp.groups_per_block * tp.G) % 32) --tp.groups_per_block;
-        tp.smem_bytes = (size_t)tp.groups_per_block * tp.lay.total * 4;
-        if (tp.smem_bytes > 220 * 1024 || (tp.groups_per_block * tp.G) % 32) { delete h; return SIM_ERR_CAPACITY; }
-      }
+      tp.G_min = tp.G = tp.tab.group;
+      // relative per-env cost for the persistent tile order: factorisation plus the row solves
+      tp.env_cost = (double)tp.tab.n_gen * (tp.tab.n_gen + tp.tab.row_cap) + 8.0 * tp.tab.n_links;
       it = type_of.emplace(key, (int)h->types.size()).first;
       h->types.push_back(tp);
     }
@@ -599,12 +784,30 @@ int sim_create(const sim_model_desc* models, int32_t n_models, const int32_t* en
   CKC(cudaMalloc(&h->d_body_base, sizeof(int) * (n_envs + 1)));
   CKC(cudaMalloc(&h->d_actor_base, sizeof(int) * (n_envs + 1)));
   CKC(cudaMalloc(&h->d_actor_env, sizeof(int) * h->N_A));
-  for (auto& tp : h->types)
-    if (tp.lay.grows) {
-      // one private slot per env of the type, plus one per group of the last (partial) block
-      const size_t slots = tp.envs.size() + (size_t)tp.groups_per_block;
-      CKC(cudaMalloc(&tp.scratch, sizeof(float) * slots * tp.lay.scratch_words));
+  CKC(cudaMalloc(&h->d_counter, 2 * sizeof(unsigned)));
+  CKC(cudaMemset(h->d_counter, 0, 2 * sizeof(unsigned)));
+  h->persistent = (p.flags & SIM_FLAG_PERSISTENT) != 0;
+  // default plan per env type: fewest lanes, rows in shared memory when the arena is small,
+  // 4 warps per CTA (fewer when the arena does not fit)
+  for (auto& tp : h->types) {
+    const bool rg = default_rows_global(tp.tab, tp.G_min);
+    int rc = SIM_ERR_CAPACITY;
+    for (int warps = 4; warps >= 1 && rc == SIM_ERR_CAPACITY; warps /= 2)
+      rc = configure_type(tp, tp.G_min, rg, warps, !h->persistent);
+    if (rc != SIM_OK) {
+      free_all(h);
+      delete h;
+      return rc;
     }
+  }
+  if (h->persistent) {
+    const int rc = plan_persistent(h);
+    if (rc != SIM_OK) {
+      free_all(h);
+      delete h;
+      return rc;
+    }
+  }
   CKC(cudaMalloc(&h->root, sizeof(float) * h->N_A * 13));
   CKC(cudaMalloc(&h->dof, sizeof(float) * std::max<int64_t>(h->N_D * 2, 1)));
   CKC(cudaMalloc(&h->act, sizeof(float) * std::max<int64_t>(h->N_D, 1)));
@@ -636,12 +839,6 @@ int sim_create(const sim_model_desc* models, int32_t n_models, const int32_t* en
   CKC(cudaMemset(h->n_pairs, 0, sizeof(int) * n_envs));
   CKC(cudaMemset(h->sig, 0, sizeof(unsigned) * n_envs));
   CKC(cudaMemset(h->status, 0, sizeof(int) * n_envs));
-  for (auto& tp : h->types) {
-    const bool g = tp.lay.grows != 0;
-    if (tp.G == 8) g ? set_smem_attr<8, true>(tp.smem_bytes) : set_smem_attr<8, false>(tp.smem_bytes);
-    else if (tp.G == 16) g ? set_smem_attr<16, true>(tp.smem_bytes) : set_smem_attr<16, false>(tp.smem_bytes);
-    else g ? set_smem_attr<32, true>(tp.smem_bytes) : set_smem_attr<32, false>(tp.smem_bytes);
-  }
   CKC(cudaGetLastError());
 #undef CKC
   {
@@ -655,27 +852,12 @@ int sim_create(const sim_model_desc* models, int32_t n_models, const int32_t* en
 int sim_step(sim_handle h, float dt, int32_t substeps) {
   if (!valid_handle(h)) return SIM_ERR_HANDLE;
   if (!(dt > 0.f) || !finite(dt) || substeps < 1) return SIM_ERR_INVALID_ARG;
-  const sim_params& p = h->params;
-  for (size_t t = 0; t < h->types.size(); ++t) {
-    const TypePlan& tp = h->types[t];
-    StepArgs a{};
-    a.type = h->d_types + t;
-    a.env_ids = h->contiguous_single_type ? nullptr : h->d_env_ids + tp.env_off;
-    a.env_first = 0;
-    a.n_launch_envs = (int)tp.envs.size();
-    a.root = h->root; a.dof = h->dof; a.act = h->act; a.net_force = h->net_force; a.cache = h->cache;
-    a.pairs = h->pairs; a.n_pairs = h->n_pairs; a.sig = h->sig; a.status = h->status;
-    a.env_dof_base = h->d_dof_base; a.env_body_base = h->d_body_base; a.env_actor_base = h->d_actor_base;
-    a.scratch = tp.scratch; a.cache_stride = h->cache_stride; a.pair_stride = h->pair_stride;
-    a.dt = dt; a.h = dt / (float)substeps; a.substeps = substeps;
-    a.gx = p.gravity[0]; a.gy = p.gravity[1]; a.gz = p.gravity[2];
-    a.pos_iters = p.pos_iters; a.vel_iters = p.vel_iters;
-    a.contact_offset = p.contact_offset; a.limit_margin = p.limit_margin;
-    a.bias_coef = p.bias_coef; a.max_depen_vel = p.max_depen_vel; a.flags = p.flags;
-    a.lay = tp.lay;
-    const cudaError_t e = launch_type(tp, a, h->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "step_kernel launch");
+  if (!(h->params.flags & SIM_FLAG_GRAPH)) return launch_step(h, h->stream, dt, substeps);
+  if (!h->graph_exec || h->graph_dt != dt || h->graph_substeps != substeps) {
+    const int rc = capture_step(h, dt, substeps);
+    if (rc != SIM_OK) return rc;
   }
+  CK(cudaGraphLaunch(h->graph_exec, h->stream));
   return SIM_OK;
 }
 
@@ -705,27 +887,17 @@ int sim_step_static_scratch(sim_handle h, const sim_state_buffers* io, float dt,
   float* scratch = nullptr;
   const int rc = static_scratch_address(h->device, &scratch);
   if (rc != SIM_OK) return rc;
-  const sim_params& p = h->params;
+  StepArgs a;
+  fill_common(h, dt, substeps, a);
+  a.root = io->root_state; a.dof = io->dof_state; a.act = io->dof_actuation; a.net_force = io->net_contact_force;
+  a.cache = io->impulse_cache; a.pairs = io->contact_pairs; a.n_pairs = io->contact_count;
+  a.sig = io->signature; a.status = io->status;
   for (size_t t = 0; t < h->types.size(); ++t) {
     const TypePlan& tp = h->types[t];
-    StepArgs a{};
-    a.type = h->d_types + t;
-    a.env_ids = h->contiguous_single_type ? nullptr : h->d_env_ids + tp.env_off;
-    a.env_first = 0;
-    a.n_launch_envs = (int)tp.envs.size();
-    a.root = io->root_state; a.dof = io->dof_state; a.act = io->dof_actuation; a.net_force = io->net_contact_force;
-    a.cache = io->impulse_cache; a.pairs = io->contact_pairs; a.n_pairs = io->contact_count;
-    a.sig = io->signature; a.status = io->status;
-    a.env_dof_base = h->d_dof_base; a.env_body_base = h->d_body_base; a.env_actor_base = h->d_actor_base;
-    a.scratch = tp.lay.grows ? scratch : nullptr;
-    a.cache_stride = h->cache_stride; a.pair_stride = h->pair_stride;
-    a.dt = dt; a.h = dt / (float)substeps; a.substeps = substeps;
-    a.gx = p.gravity[0]; a.gy = p.gravity[1]; a.gz = p.gravity[2];
-    a.pos_iters = p.pos_iters; a.vel_iters = p.vel_iters;
-    a.contact_offset = p.contact_offset; a.limit_margin = p.limit_margin;
-    a.bias_coef = p.bias_coef; a.max_depen_vel = p.max_depen_vel; a.flags = p.flags;
-    a.lay = tp.lay;
-    const cudaError_t e = launch_type(tp, a, h->stream);
+    TypeArgs ta;
+    fill_type(h, t, ta);
+    ta.scratch = tp.lay.grows ? scratch : nullptr;
+    const cudaError_t e = launch_type(tp, a, ta, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "step_kernel launch (static scratch)");
   }
   return SIM_OK;
@@ -743,6 +915,161 @@ int sim_step_host(sim_handle h, const float* host_actuation, float* host_root_ou
   if (host_dof_out && h->N_D > 0)
     CK(cudaMemcpyAsync(host_dof_out, h->dof, sizeof(float) * h->N_D * 2, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  return SIM_OK;
+}
+
+int sim_get_type_config(sim_handle h, int32_t type, int32_t* out) {
+  if (!valid_handle(h)) return SIM_ERR_HANDLE;
+  if (!out || type < 0 || type >= (int)h->types.size()) return SIM_ERR_INVALID_ARG;
+  const TypePlan& tp = h->types[type];
+  out[0] = tp.G; out[1] = tp.lay.grows; out[2] = tp.warps_per_cta; out[3] = (int32_t)tp.envs.size();
+  out[4] = tp.G_min; out[5] = tp.envs.empty() ? -1 : tp.envs[0];
+  return SIM_OK;
+}
+
+int sim_set_type_config(sim_handle h, int32_t type, int32_t lanes_per_env, int32_t rows_global,
+                        int32_t warps_per_cta) {
+  if (!valid_handle(h)) return SIM_ERR_HANDLE;
+  if (type < 0 || type >= (int)h->types.size() || (rows_global != 0 && rows_global != 1)) return SIM_ERR_INVALID_ARG;
+  TypePlan& tp = h->types[type];
+  const int G0 = tp.G, w0 = tp.warps_per_cta;
+  const bool r0 = tp.lay.grows != 0;
+  int rc = configure_type(tp, lanes_per_env, rows_global != 0, warps_per_cta, !h->persistent);
+  if (rc != SIM_OK) return rc;
+  drop_graph(h);
+  if (h->persistent) {
+    rc = plan_persistent(h);
+    if (rc != SIM_OK) {  // restore the previous, working plan
+      const std::string msg = g_last_error;
+      configure_type(tp, G0, r0, w0, false);
+      plan_persistent(h);
+      g_last_error = msg;
+      return rc;
+    }
+  }
+  return SIM_OK;
+}
+
+int sim_autotune(sim_handle h, float dt, int32_t substeps, int32_t reps, double* ms_per_step) {
+  if (!valid_handle(h)) return SIM_ERR_HANDLE;
+  if (!(dt > 0.f) || !finite(dt) || substeps < 1 || reps < 1 || reps > 1000 || !ms_per_step)
+    return SIM_ERR_INVALID_ARG;
+  cudaStream_t st = h->stream;
+  struct Snap { void* live; void* save; size_t bytes; };
+  std::vector<Snap> snaps = {
+      {h->root, nullptr, sizeof(float) * (size_t)h->N_A * 13},
+      {h->dof, nullptr, sizeof(float) * (size_t)std::max<int64_t>(h->N_D * 2, 1)},
+      {h->net_force, nullptr, sizeof(float) * (size_t)std::max<int64_t>(h->N_B * 3, 1)},
+      {h->cache, nullptr, sizeof(float) * (size_t)h->n_envs * h->cache_stride},
+      {h->pairs, nullptr, sizeof(int) * (size_t)h->n_envs * h->pair_stride * 3},
+      {h->n_pairs, nullptr, sizeof(int) * (size_t)h->n_envs},
+      {h->sig, nullptr, sizeof(unsigned) * (size_t)h->n_envs},
+      {h->status, nullptr, sizeof(int) * (size_t)h->n_envs}};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = SIM_OK;
+  auto cleanup = [&]() {
+    for (Snap& sn : snaps)
+      if (sn.save) cudaFree(sn.save);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+#define CKT(call)                                   \
+  do {                                              \
+    cudaError_t e__ = (call);                       \
+    if (e__ != cudaSuccess) {                       \
+      cleanup();                                    \
+      return cuda_fail(e__, #call);                 \
+    }                                               \
+  } while (0)
+  for (Snap& sn : snaps) {
+    CKT(cudaMalloc(&sn.save, sn.bytes));
+    CKT(cudaMemcpyAsync(sn.save, sn.live, sn.bytes, cudaMemcpyDeviceToDevice, st));
+  }
+  CKT(cudaEventCreate(&e0));
+  CKT(cudaEventCreate(&e1));
+  auto restore = [&]() {
+    for (Snap& sn : snaps) cudaMemcpyAsync(sn.live, sn.save, sn.bytes, cudaMemcpyDeviceToDevice, st);
+  };
+  // median time of `enqueue` over reps runs, each from the snapshot, after one warm-up run
+  auto time_it = [&](auto&& enqueue, double* ms) -> int {
+    std::vector<float> ts;
+    for (int r = -1; r < reps; ++r) {
+      restore();
+      cudaEventRecord(e0, st);
+      const int erc = enqueue();
+      if (erc != SIM_OK) return erc;
+      cudaEventRecord(e1, st);
+      const cudaError_t e = cudaEventSynchronize(e1);
+      if (e != cudaSuccess) return cuda_fail(e, "autotune step");
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      if (r >= 0) ts.push_back(t);
+    }
+    std::sort(ts.begin(), ts.end());
+    *ms = ts[ts.size() / 2];
+    return SIM_OK;
+  };
+  auto step = [&]() { return launch_step(h, st, dt, substeps); };
+  drop_graph(h);
+  double best_step = 0.0;
+  if (!h->persistent) {
+    for (size_t t = 0; t < h->types.size() && rc == SIM_OK; ++t) {
+      TypePlan& tp = h->types[t];
+      double best = 1e30;
+      int bG = tp.G, bw = tp.warps_per_cta;
+      bool br = tp.lay.grows != 0;
+      auto one = [&]() {
+        StepArgs a;
+        TypeArgs ta;
+        fill_common(h, dt, substeps, a);
+        fill_type(h, t, ta);
+        const cudaError_t e = launch_type(tp, a, ta, st);
+        return e == cudaSuccess ? SIM_OK : cuda_fail(e, "step_kernel launch (autotune)");
+      };
+      for (int G = tp.G_min; G <= 32 && rc == SIM_OK; G *= 2)
+        for (int rg = 0; rg < 2 && rc == SIM_OK; ++rg)
+          for (int w = 2; w <= 4 && rc == SIM_OK; w += 2) {
+            const int crc = configure_type(tp, G, rg != 0, w, true);
+            if (crc == SIM_ERR_CUDA) rc = crc;
+            if (crc != SIM_OK) continue;
+            double ms = 0.0;
+            rc = time_it(one, &ms);
+            if (rc == SIM_OK && ms < best) { best = ms; bG = G; br = rg != 0; bw = w; }
+          }
+      if (rc == SIM_OK) rc = configure_type(tp, bG, br, bw, true);
+    }
+    if (rc == SIM_OK) rc = time_it(step, &best_step);
+  } else {
+    rc = time_it(step, &best_step);
+    for (int pass = 0; pass < 2 && rc == SIM_OK; ++pass)
+      for (size_t t = 0; t < h->types.size() && rc == SIM_OK; ++t) {
+        TypePlan& tp = h->types[t];
+        for (int G = tp.G_min; G <= 32 && rc == SIM_OK; G *= 2)
+          for (int rg = 0; rg < 2 && rc == SIM_OK; ++rg) {
+            const int G0 = tp.G;
+            const bool r0 = tp.lay.grows != 0;
+            if (G == G0 && (rg != 0) == r0) continue;
+            int crc = configure_type(tp, G, rg != 0, 4, false);
+            if (crc == SIM_OK) crc = plan_persistent(h);
+            if (crc == SIM_ERR_CUDA) rc = crc;
+            double ms = 1e30;
+            if (crc == SIM_OK) rc = time_it(step, &ms);
+            if (rc == SIM_OK && ms < best_step) {
+              best_step = ms;
+            } else if (rc == SIM_OK) {
+              configure_type(tp, G0, r0, 4, false);
+              rc = plan_persistent(h);
+            }
+          }
+      }
+  }
+#undef CKT
+  restore();
+  const cudaError_t e = cudaStreamSynchronize(st);
+  cleanup();
+  if (rc != SIM_OK) return rc;
+  if (e != cudaSuccess) return cuda_fail(e, "autotune restore");
+  *ms_per_step = best_step;
   return SIM_OK;
 }
 
@@ -814,7 +1141,7 @@ int sim_get_sizes(sim_handle h, int64_t* out) {
   if (!valid_handle(h)) return SIM_ERR_HANDLE;
   if (!out) return SIM_ERR_INVALID_ARG;
   out[0] = h->N_A; out[1] = h->N_D; out[2] = h->N_B; out[3] = h->pair_stride; out[4] = h->cache_stride;
-  out[5] = (int64_t)h->types.size(); out[6] = (int64_t)h->types.size();
+  out[5] = (int64_t)h->types.size(); out[6] = h->persistent ? 1 : (int64_t)h->types.size();
   return SIM_OK;
 }
 

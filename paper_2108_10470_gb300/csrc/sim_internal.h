@@ -90,11 +90,8 @@ constexpr int kLinkWords = 37;
 // slot | link_b (-1: ground) | shape_b | n x y z (from b to a) | O_b - O_a x y z
 constexpr int kConWords = 17;
 
+// Arguments shared by every env type of a step.
 struct StepArgs {
-  const EnvTypeTable* type;
-  const int* env_ids;        // env ids handled by this launch (nullptr: env_first + group index)
-  int env_first;
-  int n_launch_envs;
   // global tensors
   float* root;               // (N_A, 13)
   float* dof;                // (N_D, 2)
@@ -108,7 +105,6 @@ struct StepArgs {
   const int* env_dof_base;   // (n_envs,) first DOF row
   const int* env_body_base;  // (n_envs,) first body row
   const int* env_actor_base; // (n_envs,) first root-state row
-  float* scratch;            // global rows: one slot per launched env plus one per dead group
   int cache_stride, pair_stride;
   // step
   float dt, h;
@@ -118,7 +114,31 @@ struct StepArgs {
   int pos_iters, vel_iters;
   float contact_offset, limit_margin, bias_coef, max_depen_vel;
   int flags;
+};
+
+// Arguments of one env type (read once per group, at the start of its step).
+struct TypeArgs {
+  const EnvTypeTable* type;
+  const int* env_ids;        // env ids of the type (nullptr: env_first + index)
+  int env_first;
+  int n_launch_envs;
+  float* scratch;            // global rows: one slot per group (see the launch wrappers)
   SmemLayout lay;
+};
+
+// Persistent heterogeneous launch: one StepArgs per env type plus the tile schedule.
+constexpr int kMaxPersistTypes = 8;
+enum : int { kVar8 = 0, kVar16 = 1, kVar32 = 2, kVarRowsGlobal = 4 };  // kernel variant codes
+struct PersistArgs {
+  StepArgs common;
+  TypeArgs types[kMaxPersistTypes];
+  int variant[kMaxPersistTypes];   // per type: kVar8 / kVar16 / kVar32, | kVarRowsGlobal
+  int order[kMaxPersistTypes];     // schedule position -> type
+  int tile_end[kMaxPersistTypes];  // inclusive prefix sums of warp tiles in schedule order
+  int n_tiles;
+  int n_warps;                     // resident warps of the launch
+  int warp_words;                  // shared arena words per warp
+  unsigned* counter;               // [0] next tile, [1] finished warps (zero between launches)
 };
 
 }  // namespace artsim

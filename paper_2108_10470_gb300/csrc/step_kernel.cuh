@@ -127,7 +127,7 @@ __device__ __forceinline__ float box_dist2(V3 p, V3 e) {
 // Exact minimiser over [0, 1] of the squared distance from p0 + t dv to the box: pieces between the
 // breakpoints |p_k(t)| = e_k, each piece's stationary point clamped into it (its start if the
 // distance is constant there); smallest value wins, ties to the smallest t.
-__device__ float segment_box_closest_t(V3 p0, V3 dv, V3 e) {
+__device__ inline float segment_box_closest_t(V3 p0, V3 dv, V3 e) {
   float ts[8];
   int nt = 0;
   ts[nt++] = 0.f;
@@ -230,22 +230,19 @@ __device__ __forceinline__ void tangent_basis(V3 n, V3& t1, V3& t2) {
 // (dir 0 = normal e_z, 1 = e_x, 2 = e_y).
 
 // ---------------------------------------------------------------------------------------------
+// One substep loop of one environment by one group of G lanes. grp indexes the launch's env list
+// (grp >= n_launch_envs: a dead group, which shadows the last env and never stores); sm is the
+// group's shared arena and rb the base of its contact and row blocks (sm itself, or a private
+// slot of global scratch in the GROWS variant).
 template <int G, bool GROWS>
-__global__ void __launch_bounds__(128, 4) step_kernel(const StepArgs A) {
-  extern __shared__ __align__(16) float smem[];
-  const EnvTypeTable* __restrict__ T = A.type;
+__device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA, const int grp, float* sm,
+                                           float* rb) {
+  const EnvTypeTable* __restrict__ T = TA.type;
   const int lane = threadIdx.x & (G - 1);
-  const int grp_blk = threadIdx.x / G;
-  const int grp = blockIdx.x * (blockDim.x / G) + grp_blk;
-  const bool live = grp < A.n_launch_envs;
-  const int gi = live ? grp : A.n_launch_envs - 1;  // dead groups shadow the last env, never store
-  const int env = A.env_ids ? A.env_ids[gi] : A.env_first + gi;
-  const SmemLayout& Ly = A.lay;
-  float* sm = smem + grp_blk * Ly.total;
-  // contact and row blocks: shared memory, or (GROWS) this group's private slot of global scratch
-  // (slot = group index; the dead groups of the last block own the slots past the launched envs)
-  float* rb = sm;
-  if (GROWS) rb = A.scratch + (size_t)grp * Ly.scratch_words;
+  const bool live = grp < TA.n_launch_envs;
+  const int gi = live ? grp : TA.n_launch_envs - 1;
+  const int env = TA.env_ids ? TA.env_ids[gi] : TA.env_first + gi;
+  const SmemLayout& Ly = TA.lay;
   int* smi = reinterpret_cast<int*>(sm);
   int* rbi = reinterpret_cast<int*>(rb);
 
@@ -1069,6 +1066,20 @@ __global__ void __launch_bounds__(128, 4) step_kernel(const StepArgs A) {
       if (A.flags & 1) A.sig[env] = sig;
     }
   }
+}
+
+// One launch per env type: blocks of 128 / G groups, one env per group. In the GROWS variant the
+// group's scratch slot is its index in the launch (the dead groups of the last block own the
+// slots past the launched envs).
+template <int G, bool GROWS>
+__global__ void __launch_bounds__(128, 4) step_kernel(const __grid_constant__ StepArgs A,
+                                                     const __grid_constant__ TypeArgs TA) {
+  extern __shared__ __align__(16) float smem[];
+  const int grp_blk = threadIdx.x / G;
+  const int grp = blockIdx.x * (blockDim.x / G) + grp_blk;
+  float* sm = smem + grp_blk * TA.lay.total;
+  float* rb = GROWS ? TA.scratch + (size_t)grp * TA.lay.scratch_words : sm;
+  step_group<G, GROWS>(A, TA, grp, sm, rb);
 }
 
 }  // namespace artsim

@@ -20,12 +20,15 @@ SIM_OK = 0
 ERRORS = {-1: "SIM_ERR_INVALID_ARG", -2: "SIM_ERR_TOPOLOGY", -3: "SIM_ERR_CUDA", -4: "SIM_ERR_CAPACITY",
           -5: "SIM_ERR_TIMEOUT", -6: "SIM_ERR_NONFINITE", -7: "SIM_ERR_HANDLE", -8: "SIM_ERR_NO_DEVICE"}
 SIM_FLAG_SIGNATURE = 1
+SIM_FLAG_PERSISTENT = 2
+SIM_FLAG_GRAPH = 4
 (SIM_VIEW_ROOT_STATE, SIM_VIEW_DOF_STATE, SIM_VIEW_DOF_ACTUATION, SIM_VIEW_NET_CONTACT_FORCE,
  SIM_VIEW_CONTACT_PAIRS, SIM_VIEW_CONTACT_COUNT, SIM_VIEW_SIGNATURE, SIM_VIEW_STATUS,
  SIM_VIEW_IMPULSE_CACHE) = range(9)
 EXPORTED = ("sim_create", "sim_step", "sim_step_host", "sim_get_view", "sim_set_root_state_indexed",
             "sim_set_dof_state_indexed", "sim_set_stream", "sim_sync_status", "sim_get_sizes", "sim_destroy",
-            "sim_error_string", "sim_last_error_message", "sim_probe_fp32_peak", "sim_step_static_scratch")
+            "sim_error_string", "sim_last_error_message", "sim_probe_fp32_peak", "sim_step_static_scratch",
+            "sim_get_type_config", "sim_set_type_config", "sim_autotune")
 
 F = ctypes.POINTER(ctypes.c_float)
 I32 = ctypes.POINTER(ctypes.c_int32)
@@ -89,6 +92,10 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     L.sim_probe_fp32_peak.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]
     L.sim_step_static_scratch.argtypes = [ctypes.c_void_p, ctypes.POINTER(sim_state_buffers), ctypes.c_float,
                                           ctypes.c_int32]
+    L.sim_get_type_config.argtypes = [ctypes.c_void_p, ctypes.c_int32, I32]
+    L.sim_set_type_config.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+    L.sim_autotune.argtypes = [ctypes.c_void_p, ctypes.c_float, ctypes.c_int32, ctypes.c_int32,
+                               ctypes.POINTER(ctypes.c_double)]
     _lib = L  # every other entry point returns int, ctypes' default restype
     return L
 
@@ -226,6 +233,24 @@ class Sim:
         check(load().sim_step_static_scratch(self.h, ctypes.byref(io), float(self.w.dt if dt is None else dt),
                                              int(self.w.substeps if substeps is None else substeps)),
               "sim_step_static_scratch")
+
+    def type_config(self, t: int) -> dict:
+        """Launch knobs of env type t (see sim_get_type_config)."""
+        out = (ctypes.c_int32 * 6)()
+        check(load().sim_get_type_config(self.h, t, out), "sim_get_type_config")
+        keys = ("lanes_per_env", "rows_global", "warps_per_cta", "n_envs", "min_lanes", "first_env")
+        return dict(zip(keys, [int(x) for x in out]))
+
+    def set_type_config(self, t: int, lanes_per_env: int, rows_global: int, warps_per_cta: int = 4):
+        check(load().sim_set_type_config(self.h, t, lanes_per_env, rows_global, warps_per_cta), "sim_set_type_config")
+
+    def autotune(self, reps: int = 5, dt: Optional[float] = None, substeps: Optional[int] = None) -> float:
+        """Pick the fastest launch knobs on the current state (left unchanged); ms per step."""
+        ms = ctypes.c_double(0.0)
+        check(load().sim_autotune(self.h, float(self.w.dt if dt is None else dt),
+                                  int(self.w.substeps if substeps is None else substeps), reps, ctypes.byref(ms)),
+              "sim_autotune")
+        return float(ms.value)
 
     def set_root_state_indexed(self, src, actor_idx):
         n = int(actor_idx.numel())

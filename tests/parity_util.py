@@ -16,11 +16,14 @@ def env_rows(w, per):
     return out
 
 
-def gpu_rollout(w, root, dof, acts, steps, flags=1):
+def gpu_rollout(w, root, dof, acts, steps, flags=1, setup=None):
+    """Run `steps` env-steps through the C ABI; setup(sim) runs once after creation (launch knobs)."""
     import torch
     from paper_2108_10470_gb300 import sim
 
     s = sim.Sim(w, flags=flags)
+    if setup is not None:
+        setup(s)
     s.root_state.copy_(torch.from_numpy(root))
     s.dof_state.copy_(torch.from_numpy(dof))
     snaps = []
@@ -108,8 +111,9 @@ def fp32_scales(w, root, dof, acts, steps, rtol=1e-4, atol=1e-5):
                 if sl.stop > sl.start:
                     s[e] = max(np.abs(run[k][key][sl] - base[k][key][sl]).max() for run in runs)
             sk[key] = s
-        sk["strict_frac"] = {key: float(np.mean(np.abs(runs[0][k][key] - base[k][key]) <=
-                                               atol + rtol * np.abs(base[k][key]))) if base[k][key].size else 1.0
-                             for key in per}
+        # fraction of components within the strict bound, lowest over the FP32 evaluations
+        sk["strict_frac"] = {key: min(float(np.mean(np.abs(run[k][key] - base[k][key]) <=
+                                                    atol + rtol * np.abs(base[k][key]))) for run in runs)
+                             if base[k][key].size else 1.0 for key in per}
         scales.append(sk)
     return base, scales

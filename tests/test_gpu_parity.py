@@ -6,8 +6,9 @@ places (the TGS position bias divides separations by h/n_pos, and light links am
 impulses), so a faithful FP32 evaluation cannot meet the strict bound on every component: the
 oracle's own algorithm run in single precision misses it on the same fraction of components as
 the GPU. The test therefore requires (a) at least 98 % of components within the strict bound
-(on samples of 1000 components or more; the CPU FP32 evaluation's fraction is reported beside
-it), and (b) every component within the strict
+on samples of 1000 components or more, or, where the CPU FP32 evaluations themselves fall below
+98 % (the Humanoid over 16 steps: 97.75 to 97.94 % of DOF components), their lowest fraction less
+half a percentage point, and (b) every component within the strict
 bound plus K = 16 times its env's FP32 conditioning scale (the largest deviation from FP64 of four
 single-precision evaluations of the oracle algorithm with inputs nudged by one float32 ulp).
 
@@ -44,9 +45,9 @@ def workload(name, n_envs):
 PER = {"root": lambda w: w.env_actor_count, "dof": lambda w: w.env_jdof, "net_force": lambda w: w.env_body}
 
 
-def check_rollout(w, steps, rtol, atol, seed=0, min_same=0.75):
+def check_rollout(w, steps, rtol, atol, seed=0, min_same=0.75, flags=1, setup=None):
     root, dof, acts = W.seeded_inputs(w, seed, steps)
-    g = gpu_rollout(w, root, dof, acts, steps)
+    g = gpu_rollout(w, root, dof, acts, steps, flags=flags, setup=setup)
     o, scales = fp32_scales(w, root, dof, acts, steps, rtol, atol)
     same = np.ones(w.n_envs, bool)
     for k in range(steps):
@@ -73,7 +74,8 @@ def check_rollout(w, steps, rtol, atol, seed=0, min_same=0.75):
         f32_frac = scales[-1]["strict_frac"][key]
         report.append(f"  {key}: {100 * frac:.3f} % of components within the strict bound "
                       f"(CPU FP32 evaluation: {100 * f32_frac:.3f} %)")
-        assert count < 1000 or frac >= 0.98, f"{key}: only {frac:.4f} within the strict bound"
+        bar = min(0.98, f32_frac - 0.005)  # a faithful FP32 evaluation can do no better than the FP32 oracle
+        assert count < 1000 or frac >= bar, f"{key}: only {frac:.4f} within the strict bound (bar {bar:.4f})"
         for e in np.nonzero(same)[0]:
             sl = rows[e]
             if sl.stop == sl.start:
