@@ -28,6 +28,7 @@
 #include <thread>
 
 #include "oracle_math.hpp"
+#include "oracle_dual.hpp"
 #include "oracle_opcount.hpp"
 
 namespace orc {
@@ -737,7 +738,7 @@ template <class T> struct StepOut {
 };
 
 // One substep of one env (steps a1-a7 of the method).
-template <class T> void env_substep(const Oracle& O, int env, std::vector<ActorState<T>>& st, const double* act,
+template <class T> void env_substep(const Oracle& O, int env, std::vector<ActorState<T>>& st, const T* act,
                                     const T& h, std::vector<T>& cache, StepOut<T>& out) {
   const Params& P = O.prm;
   const EnvLayout E = env_layout(O, env);
@@ -755,7 +756,7 @@ template <class T> void env_substep(const Oracle& O, int env, std::vector<ActorS
     for (size_t l = 0; l < M.links.size(); ++l)
       if (M.jdof[l] >= 0) {
         const int j = M.jdof[l];
-        tau[M.goff[l]] = T(act[jbase + j]) - T(M.links[l].damping) * st[a].qd[j];
+        tau[M.goff[l]] = act[jbase + j] - T(M.links[l].damping) * st[a].qd[j];
       }
     std::vector<T> qdd;
     if (!aba(M, K[a], tau, P, qdd)) out.ok = false;
@@ -906,9 +907,10 @@ template <class T> int env_step(const Oracle& O, int env, double* root, double* 
   const T h = T(dt) / T((double)substeps);
   const double* act_env = act + O.jdof_off[env];
   double* cache_env = o.cache + (int64_t)env * O.cache_len;
-  std::vector<T> cache(O.cache_len);
+  std::vector<T> cache(O.cache_len), actv(O.jdof_off[env + 1] - O.jdof_off[env]);
   for (int i = 0; i < O.cache_len; ++i) cache[i] = T(cache_env[i]);
-  for (int s = 0; s < substeps; ++s) env_substep(O, env, st, act_env, h, cache, out);
+  for (size_t j = 0; j < actv.size(); ++j) actv[j] = T(act_env[j]);
+  for (int s = 0; s < substeps; ++s) env_substep(O, env, st, actv.data(), h, cache, out);
   for (int i = 0; i < O.cache_len; ++i) cache_env[i] = val(cache[i]);
   store_env(O, env, st, root, dof);
   if (o.net_force) {
@@ -1166,6 +1168,65 @@ double oracle_step_flops(void* h, double* root, double* dof, double* cache, cons
   Outputs<OpCount> o{cache, nullptr, nullptr, nullptr, nullptr, nullptr};
   for (int e = 0; e < O->n_envs; ++e) env_step<OpCount>(*O, e, root, dof, act, dt, substeps, o);
   return (double)OpCount::count();
+}
+
+// The same step evaluated with forward-mode dual numbers: root, dof and cache advance like
+// oracle_step, and droot, ddof, dcache (same layouts) carry the input tangent in and the output
+// tangent out, with dact the actuation tangent. The derivative is exact for the discrete FP64 step
+// with its constraint and active sets held at the values' choices. Returns the failed-env count.
+int32_t oracle_step_tangent(void* h, double* root, double* dof, double* cache, const double* act, double* droot,
+                            double* ddof, double* dcache, const double* dact, double dt, int32_t substeps,
+                            int32_t n_threads) {
+  const Oracle* O = (const Oracle*)h;
+  std::atomic<int> bad{0};
+  if (n_threads < 1) n_threads = 1;
+  auto one = [&](int env) {
+    std::vector<ActorState<Dual>> st;
+    load_env(*O, env, root, dof, st);
+    int64_t jd = O->jdof_off[env];
+    for (int a = 0; a < O->n_act(env); ++a) {
+      const double* dr = droot + (int64_t)(O->actor_off[env] + a) * 13;
+      ActorState<Dual>& x = st[a];
+      for (int k = 0; k < 3; ++k) { x.p[k].d = dr[k]; x.v[k].d = dr[7 + k]; x.w[k].d = dr[10 + k]; }
+      for (int k = 0; k < 4; ++k) x.quat[k].d = dr[3 + k];
+      for (size_t j = 0; j < x.q.size(); ++j) { x.q[j].d = ddof[(jd + j) * 2]; x.qd[j].d = ddof[(jd + j) * 2 + 1]; }
+      jd += (int64_t)x.q.size();
+    }
+    int nlinks = 0;
+    for (int a = 0; a < O->n_act(env); ++a) nlinks += (int)O->actor_model(env, a).links.size();
+    StepOut<Dual> out;
+    out.impulse.assign(nlinks, zero3<Dual>());
+    const Dual hs = Dual(dt) / Dual((double)substeps);
+    const int64_t j0 = O->jdof_off[env], nj = O->jdof_off[env + 1] - j0;
+    std::vector<Dual> actv(nj), cv(O->cache_len);
+    for (int64_t j = 0; j < nj; ++j) actv[j] = Dual(act[j0 + j], dact[j0 + j]);
+    double* c_env = cache + (int64_t)env * O->cache_len;
+    double* dc_env = dcache + (int64_t)env * O->cache_len;
+    for (int i = 0; i < O->cache_len; ++i) cv[i] = Dual(c_env[i], dc_env[i]);
+    for (int s = 0; s < substeps; ++s) env_substep(*O, env, st, actv.data(), hs, cv, out);
+    for (int i = 0; i < O->cache_len; ++i) { c_env[i] = cv[i].v; dc_env[i] = cv[i].d; }
+    store_env(*O, env, st, root, dof);
+    jd = O->jdof_off[env];
+    for (int a = 0; a < O->n_act(env); ++a) {
+      double* dr = droot + (int64_t)(O->actor_off[env] + a) * 13;
+      const ActorState<Dual>& x = st[a];
+      for (int k = 0; k < 3; ++k) { dr[k] = x.p[k].d; dr[7 + k] = x.v[k].d; dr[10 + k] = x.w[k].d; }
+      for (int k = 0; k < 4; ++k) dr[3 + k] = x.quat[k].d;
+      for (size_t j = 0; j < x.q.size(); ++j) { ddof[(jd + j) * 2] = x.q[j].d; ddof[(jd + j) * 2 + 1] = x.qd[j].d; }
+      jd += (int64_t)x.q.size();
+    }
+    if (!out.ok) bad++;
+  };
+  auto work = [&](int t) {
+    for (int e = t; e < O->n_envs; e += n_threads) one(e);
+  };
+  if (n_threads == 1) work(0);
+  else {
+    std::vector<std::thread> th;
+    for (int t = 0; t < n_threads; ++t) th.emplace_back(work, t);
+    for (auto& x : th) x.join();
+  }
+  return bad.load();
 }
 
 // The same step evaluated in single precision (a conditioning probe for the parity tests: it
