@@ -236,6 +236,60 @@ int sim_set_type_config(sim_handle h, int32_t type, int32_t lanes_per_env, int32
  * duration. Errors: HANDLE, INVALID_ARG, CUDA. */
 int sim_autotune(sim_handle h, float dt, int32_t substeps, int32_t reps, double* ms_per_step);
 
+/* ---- derivative of the step ---------------------------------------------------------------------
+ * The env-step is differentiated with its constraint set and active set held fixed (contact and
+ * limit decisions, clamps and the choice of solver target follow the values, as in the forward
+ * step). The state that carries into the next step is (root state, DOF state, impulse cache); the
+ * actuation is the step's control input. Net contact forces and the contact views are not
+ * differentiated. Supported for env types without capsule-box pairs whose impulse cache has at
+ * most 384 entries; other types fail with CAPACITY. Computed by forward-mode dual arithmetic, one
+ * env per warp, each lane carrying up to 8 input directions, in passes of 256 directions per env.
+ * (The paper does not differentiate its step; this is the project's own extension.) */
+typedef struct {
+  const float* root_state;           /* (N_A, 13) state at the start of the step */
+  const float* dof_state;            /* (N_D, 2) */
+  const float* dof_actuation;        /* (N_D,) */
+  const float* impulse_cache;        /* (n_envs, K) */
+  const float* grad_root_state;      /* (N_A, 13) gradient w.r.t. the step's output root state; NULL = 0 */
+  const float* grad_dof_state;       /* (N_D, 2) w.r.t. the output DOF state; NULL = 0 */
+  const float* grad_impulse_cache;   /* (n_envs, K) w.r.t. the output impulse cache; NULL = 0 */
+  float* grad_root_state_in;         /* (N_A, 13) out: gradient w.r.t. root_state */
+  float* grad_dof_state_in;          /* (N_D, 2) out */
+  float* grad_dof_actuation;         /* (N_D,) out */
+  float* grad_impulse_cache_in;      /* (n_envs, K) out (zero past each env type's cache length) */
+  int32_t* status;                   /* (n_envs,) out, optional: 0, or 2 if the env's step failed
+                                      * (pivot, or more than 64 contacts); its gradient is then 0 */
+} sim_vjp_buffers;
+
+/* Vector-Jacobian product of one env-step (substeps of dt / substeps) at the given input state:
+ * every output gradient entry is contracted with the step's Jacobian. All pointers are device
+ * memory owned by the caller, in the layouts of the views of the same names; the handle supplies
+ * the model and its stream, its views are not touched. Asynchronous. Errors: HANDLE, INVALID_ARG
+ * (a required pointer NULL, dt or substeps invalid), CAPACITY (unsupported env type), CUDA. */
+int sim_step_vjp(sim_handle h, const sim_vjp_buffers* b, float dt, int32_t substeps);
+
+typedef struct {
+  const float* root_state;           /* (N_A, 13) state at the start of the step */
+  const float* dof_state;            /* (N_D, 2) */
+  const float* dof_actuation;        /* (N_D,) */
+  const float* impulse_cache;        /* (n_envs, K) */
+  const float* tan_root_state;       /* (N_A, 13) input tangent */
+  const float* tan_dof_state;        /* (N_D, 2) */
+  const float* tan_dof_actuation;    /* (N_D,) */
+  const float* tan_impulse_cache;    /* (n_envs, K) */
+  float* root_state_out;             /* (N_A, 13) out: the step's output, evaluated by the same serial code */
+  float* dof_state_out;              /* (N_D, 2) out */
+  float* impulse_cache_out;          /* (n_envs, K) out */
+  float* tan_root_state_out;         /* (N_A, 13) out: output tangent */
+  float* tan_dof_state_out;          /* (N_D, 2) out */
+  float* tan_impulse_cache_out;      /* (n_envs, K) out */
+  int32_t* status;                   /* (n_envs,) out, optional, as in sim_vjp_buffers */
+} sim_jvp_buffers;
+
+/* Jacobian-vector product of one env-step: the output state and its tangent along the given input
+ * tangent. Same conventions and errors as sim_step_vjp. */
+int sim_step_jvp(sim_handle h, const sim_jvp_buffers* b, float dt, int32_t substeps);
+
 /* Describe one of the SIM_VIEW_* device tensors. Errors: HANDLE, INVALID_ARG. */
 int sim_get_view(sim_handle h, int32_t which, sim_view* out);
 

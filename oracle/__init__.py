@@ -72,6 +72,8 @@ def lib():
         L.oracle_step_f32.argtypes = [ctypes.c_void_p, D, D, D, D, ctypes.c_double, ctypes.c_int32, D]
         L.oracle_step_tangent.argtypes = [ctypes.c_void_p, D, D, D, D, D, D, D, D, ctypes.c_double, ctypes.c_int32,
                                           ctypes.c_int32]
+        L.oracle_step_tangent_f32.argtypes = [ctypes.c_void_p, D, D, D, D, D, D, D, D, ctypes.c_double,
+                                              ctypes.c_int32]
         L.oracle_step_f32.restype = ctypes.c_int32
         L.oracle_capsule_box.argtypes = [D, D, ctypes.c_double, D, D]
         L.oracle_capsule_box.restype = None
@@ -204,10 +206,12 @@ class Oracle:
                               _dp(a) if self.N_D else None, float(dt), int(substeps), _dp(nf) if self.N_B else None)
         return nf
 
-    def step_tangent(self, root, dof, act, droot, ddof, dact, dcache, dt=None, substeps=None, n_threads=1):
+    def step_tangent(self, root, dof, act, droot, ddof, dact, dcache, dt=None, substeps=None, n_threads=1,
+                     single=False):
         """One env-step in forward-mode dual numbers. root, dof and self.cache advance in place like
         step; droot (N_A,13), ddof (N_D,2) and dcache (n_envs, cache_len) hold the input tangent and
-        are overwritten with the output tangent; dact (N_D,) is the actuation tangent. Returns the
+        are overwritten with the output tangent; dact (N_D,) is the actuation tangent. single=True
+        evaluates the identical derivative in single precision (conditioning probe). Returns the
         number of failed envs."""
         dt = self.w.dt if dt is None else dt
         substeps = self.w.substeps if substeps is None else substeps
@@ -217,10 +221,11 @@ class Oracle:
         a = np.ascontiguousarray(act, dtype=np.float64).reshape(self.N_D)
         da = np.ascontiguousarray(dact, dtype=np.float64).reshape(self.N_D)
         nd = self.N_D > 0
-        return int(lib().oracle_step_tangent(self.h, _dp(root), _dp(dof) if nd else None, _dp(self.cache),
-                                             _dp(a) if nd else None, _dp(droot), _dp(ddof) if nd else None,
-                                             _dp(dcache), _dp(da) if nd else None, float(dt), int(substeps),
-                                             int(n_threads)))
+        args = (self.h, _dp(root), _dp(dof) if nd else None, _dp(self.cache), _dp(a) if nd else None, _dp(droot),
+                _dp(ddof) if nd else None, _dp(dcache), _dp(da) if nd else None, float(dt), int(substeps))
+        if single:
+            return int(lib().oracle_step_tangent_f32(*args))
+        return int(lib().oracle_step_tangent(*args, int(n_threads)))
 
     def rk4(self, root, dof, act, dt, nsteps):
         a = np.ascontiguousarray(act, dtype=np.float64).reshape(self.N_D)

@@ -986,6 +986,65 @@ template <class T> ActorState<T> axpy_state(const ActorState<T>& s, const ActorS
 
 }  // namespace orc
 
+namespace orc {
+
+template <class D> int32_t step_tangent_t(void* h, double* root, double* dof, double* cache, const double* act,
+                                         double* droot, double* ddof, double* dcache, const double* dact, double dt,
+                                         int32_t substeps, int32_t n_threads) {
+  const Oracle* O = (const Oracle*)h;
+  std::atomic<int> bad{0};
+  if (n_threads < 1) n_threads = 1;
+  auto one = [&](int env) {
+    std::vector<ActorState<D>> st;
+    load_env(*O, env, root, dof, st);
+    int64_t jd = O->jdof_off[env];
+    for (int a = 0; a < O->n_act(env); ++a) {
+      const double* dr = droot + (int64_t)(O->actor_off[env] + a) * 13;
+      ActorState<D>& x = st[a];
+      for (int k = 0; k < 3; ++k) { x.p[k].d = dr[k]; x.v[k].d = dr[7 + k]; x.w[k].d = dr[10 + k]; }
+      for (int k = 0; k < 4; ++k) x.quat[k].d = dr[3 + k];
+      for (size_t j = 0; j < x.q.size(); ++j) { x.q[j].d = ddof[(jd + j) * 2]; x.qd[j].d = ddof[(jd + j) * 2 + 1]; }
+      jd += (int64_t)x.q.size();
+    }
+    int nlinks = 0;
+    for (int a = 0; a < O->n_act(env); ++a) nlinks += (int)O->actor_model(env, a).links.size();
+    StepOut<D> out;
+    out.impulse.assign(nlinks, zero3<D>());
+    const D hs = D(dt) / D((double)substeps);
+    const int64_t j0 = O->jdof_off[env], nj = O->jdof_off[env + 1] - j0;
+    std::vector<D> actv(nj), cv(O->cache_len);
+    for (int64_t j = 0; j < nj; ++j) { actv[j] = D(act[j0 + j]); actv[j].d = dact[j0 + j]; }
+    double* c_env = cache + (int64_t)env * O->cache_len;
+    double* dc_env = dcache + (int64_t)env * O->cache_len;
+    for (int i = 0; i < O->cache_len; ++i) { cv[i] = D(c_env[i]); cv[i].d = dc_env[i]; }
+    for (int s = 0; s < substeps; ++s) env_substep(*O, env, st, actv.data(), hs, cv, out);
+    for (int i = 0; i < O->cache_len; ++i) { c_env[i] = (double)cv[i].v; dc_env[i] = (double)cv[i].d; }
+    store_env(*O, env, st, root, dof);
+    jd = O->jdof_off[env];
+    for (int a = 0; a < O->n_act(env); ++a) {
+      double* dr = droot + (int64_t)(O->actor_off[env] + a) * 13;
+      const ActorState<D>& x = st[a];
+      for (int k = 0; k < 3; ++k) { dr[k] = (double)x.p[k].d; dr[7 + k] = (double)x.v[k].d; dr[10 + k] = (double)x.w[k].d; }
+      for (int k = 0; k < 4; ++k) dr[3 + k] = (double)x.quat[k].d;
+      for (size_t j = 0; j < x.q.size(); ++j) { ddof[(jd + j) * 2] = (double)x.q[j].d; ddof[(jd + j) * 2 + 1] = (double)x.qd[j].d; }
+      jd += (int64_t)x.q.size();
+    }
+    if (!out.ok) bad++;
+  };
+  auto work = [&](int t) {
+    for (int e = t; e < O->n_envs; e += n_threads) one(e);
+  };
+  if (n_threads == 1) work(0);
+  else {
+    std::vector<std::thread> th;
+    for (int t = 0; t < n_threads; ++t) th.emplace_back(work, t);
+    for (auto& x : th) x.join();
+  }
+  return bad.load();
+}
+
+}  // namespace orc
+
 // ==================================================================================================
 // C entry points (ctypes).
 using namespace orc;
@@ -1177,56 +1236,14 @@ double oracle_step_flops(void* h, double* root, double* dof, double* cache, cons
 int32_t oracle_step_tangent(void* h, double* root, double* dof, double* cache, const double* act, double* droot,
                             double* ddof, double* dcache, const double* dact, double dt, int32_t substeps,
                             int32_t n_threads) {
-  const Oracle* O = (const Oracle*)h;
-  std::atomic<int> bad{0};
-  if (n_threads < 1) n_threads = 1;
-  auto one = [&](int env) {
-    std::vector<ActorState<Dual>> st;
-    load_env(*O, env, root, dof, st);
-    int64_t jd = O->jdof_off[env];
-    for (int a = 0; a < O->n_act(env); ++a) {
-      const double* dr = droot + (int64_t)(O->actor_off[env] + a) * 13;
-      ActorState<Dual>& x = st[a];
-      for (int k = 0; k < 3; ++k) { x.p[k].d = dr[k]; x.v[k].d = dr[7 + k]; x.w[k].d = dr[10 + k]; }
-      for (int k = 0; k < 4; ++k) x.quat[k].d = dr[3 + k];
-      for (size_t j = 0; j < x.q.size(); ++j) { x.q[j].d = ddof[(jd + j) * 2]; x.qd[j].d = ddof[(jd + j) * 2 + 1]; }
-      jd += (int64_t)x.q.size();
-    }
-    int nlinks = 0;
-    for (int a = 0; a < O->n_act(env); ++a) nlinks += (int)O->actor_model(env, a).links.size();
-    StepOut<Dual> out;
-    out.impulse.assign(nlinks, zero3<Dual>());
-    const Dual hs = Dual(dt) / Dual((double)substeps);
-    const int64_t j0 = O->jdof_off[env], nj = O->jdof_off[env + 1] - j0;
-    std::vector<Dual> actv(nj), cv(O->cache_len);
-    for (int64_t j = 0; j < nj; ++j) actv[j] = Dual(act[j0 + j], dact[j0 + j]);
-    double* c_env = cache + (int64_t)env * O->cache_len;
-    double* dc_env = dcache + (int64_t)env * O->cache_len;
-    for (int i = 0; i < O->cache_len; ++i) cv[i] = Dual(c_env[i], dc_env[i]);
-    for (int s = 0; s < substeps; ++s) env_substep(*O, env, st, actv.data(), hs, cv, out);
-    for (int i = 0; i < O->cache_len; ++i) { c_env[i] = cv[i].v; dc_env[i] = cv[i].d; }
-    store_env(*O, env, st, root, dof);
-    jd = O->jdof_off[env];
-    for (int a = 0; a < O->n_act(env); ++a) {
-      double* dr = droot + (int64_t)(O->actor_off[env] + a) * 13;
-      const ActorState<Dual>& x = st[a];
-      for (int k = 0; k < 3; ++k) { dr[k] = x.p[k].d; dr[7 + k] = x.v[k].d; dr[10 + k] = x.w[k].d; }
-      for (int k = 0; k < 4; ++k) dr[3 + k] = x.quat[k].d;
-      for (size_t j = 0; j < x.q.size(); ++j) { ddof[(jd + j) * 2] = x.q[j].d; ddof[(jd + j) * 2 + 1] = x.qd[j].d; }
-      jd += (int64_t)x.q.size();
-    }
-    if (!out.ok) bad++;
-  };
-  auto work = [&](int t) {
-    for (int e = t; e < O->n_envs; e += n_threads) one(e);
-  };
-  if (n_threads == 1) work(0);
-  else {
-    std::vector<std::thread> th;
-    for (int t = 0; t < n_threads; ++t) th.emplace_back(work, t);
-    for (auto& x : th) x.join();
-  }
-  return bad.load();
+  return step_tangent_t<Dual>(h, root, dof, cache, act, droot, ddof, dcache, dact, dt, substeps, n_threads);
+}
+
+// The same derivative evaluated in single precision (conditioning probe for the GPU derivative).
+int32_t oracle_step_tangent_f32(void* h, double* root, double* dof, double* cache, const double* act,
+                                double* droot, double* ddof, double* dcache, const double* dact, double dt,
+                                int32_t substeps) {
+  return step_tangent_t<DualF>(h, root, dof, cache, act, droot, ddof, dcache, dact, dt, substeps, 1);
 }
 
 // The same step evaluated in single precision (a conditioning probe for the parity tests: it

@@ -10,29 +10,32 @@
 
 namespace orc {
 
-struct Dual {
-  double v, d;
-  Dual() : v(0.0), d(0.0) {}
-  Dual(double x) : v(x), d(0.0) {}  // NOLINT: implicit by design (constants)
-  Dual(double x, double dx) : v(x), d(dx) {}
-  friend Dual operator+(const Dual& a, const Dual& b) { return Dual(a.v + b.v, a.d + b.d); }
-  friend Dual operator-(const Dual& a, const Dual& b) { return Dual(a.v - b.v, a.d - b.d); }
-  friend Dual operator*(const Dual& a, const Dual& b) { return Dual(a.v * b.v, a.d * b.v + a.v * b.d); }
-  friend Dual operator/(const Dual& a, const Dual& b) {
-    const double q = a.v / b.v;
-    return Dual(q, (a.d - q * b.d) / b.v);
+template <class F> struct DualT {
+  F v, d;
+  DualT() : v(F(0)), d(F(0)) {}
+  DualT(double x) : v(F(x)), d(F(0)) {}  // NOLINT: implicit by design (constants)
+  DualT(F x, F dx, int) : v(x), d(dx) {}
+  friend DualT operator+(const DualT& a, const DualT& b) { return DualT(a.v + b.v, a.d + b.d, 0); }
+  friend DualT operator-(const DualT& a, const DualT& b) { return DualT(a.v - b.v, a.d - b.d, 0); }
+  friend DualT operator*(const DualT& a, const DualT& b) { return DualT(a.v * b.v, a.d * b.v + a.v * b.d, 0); }
+  friend DualT operator/(const DualT& a, const DualT& b) {
+    const F q = a.v / b.v;
+    return DualT(q, (a.d - q * b.d) / b.v, 0);
   }
-  Dual operator-() const { return Dual(-v, -d); }
-  friend bool operator<(const Dual& a, const Dual& b) { return a.v < b.v; }
-  friend bool operator==(const Dual& a, const Dual& b) { return a.v == b.v; }
+  DualT operator-() const { return DualT(-v, -d, 0); }
+  friend bool operator<(const DualT& a, const DualT& b) { return a.v < b.v; }
+  friend bool operator==(const DualT& a, const DualT& b) { return a.v == b.v; }
 };
-inline Dual sqrt(const Dual& a) {
-  const double s = std::sqrt(a.v);
-  return Dual(s, a.d / (2.0 * s));
+template <class F> inline DualT<F> sqrt(const DualT<F>& a) {
+  const F s = std::sqrt(a.v);
+  return DualT<F>(s, a.d / (F(2) * s), 0);
 }
-inline Dual sin(const Dual& a) { return Dual(std::sin(a.v), std::cos(a.v) * a.d); }
-inline Dual cos(const Dual& a) { return Dual(std::cos(a.v), -std::sin(a.v) * a.d); }
-inline Dual fabs(const Dual& a) { return a.v < 0.0 ? -a : a; }
-inline double val(const Dual& a) { return a.v; }
+template <class F> inline DualT<F> sin(const DualT<F>& a) { return DualT<F>(std::sin(a.v), std::cos(a.v) * a.d, 0); }
+template <class F> inline DualT<F> cos(const DualT<F>& a) { return DualT<F>(std::cos(a.v), -std::sin(a.v) * a.d, 0); }
+template <class F> inline DualT<F> fabs(const DualT<F>& a) { return a.v < F(0) ? -a : a; }
+template <class F> inline double val(const DualT<F>& a) { return (double)a.v; }
+
+using Dual = DualT<double>;   // the FP64 oracle derivative
+using DualF = DualT<float>;   // the same arithmetic in single precision (conditioning probe)
 
 }  // namespace orc

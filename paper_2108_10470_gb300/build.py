@@ -1,8 +1,8 @@
 """Build the CUDA library (libartsim.so) in-tree with nvcc for sm_103a.
 
-Four translation units compiled in parallel with ``-gencode arch=compute_103a,code=sm_103a``
-(the per-type kernels with shared-memory rows, with global-memory rows, the persistent kernel,
-and the C ABI), then linked into one shared library; the CUDA runtime is linked statically so the
+Five translation units compiled in parallel with ``-gencode arch=compute_103a,code=sm_103a``
+(the per-type kernels with shared-memory rows, with global-memory rows, the persistent kernel, the
+step-derivative kernel, and the C ABI), then linked into one shared library; the CUDA runtime is linked statically so the
 library has no dependency beyond the driver.
 """
 from __future__ import annotations
@@ -16,8 +16,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB_PATH = os.path.join(HERE, "libartsim.so")
-UNITS = ("kernels_shared.cu", "kernels_global.cu", "kernels_persistent.cu", "sim_api.cu")
-SOURCES = [os.path.join(CSRC, f) for f in UNITS + ("step_kernel.cuh", "sim_internal.h", "launch.h")] + \
+UNITS = ("kernels_shared.cu", "kernels_global.cu", "kernels_persistent.cu", "kernels_adjoint.cu", "sim_api.cu")
+SOURCES = [os.path.join(CSRC, f) for f in UNITS + ("step_kernel.cuh", "tangent_step.cuh", "sim_internal.h",
+                                                   "launch.h")] + \
     [os.path.join(INCLUDE, "sim.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMPILE_FLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC"]

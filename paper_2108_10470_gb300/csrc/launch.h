@@ -8,6 +8,21 @@
 
 namespace artsim {
 
+// Arguments of the derivative kernel (kernels_adjoint.cu). mode 0: adjoint (vector-Jacobian
+// product) over the directions dir_base + k * 32 + lane; mode 1: tangent (Jacobian-vector product)
+// of the caller's direction. Layouts are those of the state views.
+struct TangentArgs {
+  const float* root; const float* dof; const float* act; const float* cache;  // step input
+  const float* g_root; const float* g_dof; const float* g_cache;              // adjoint: output gradient
+  float* gi_root; float* gi_dof; float* gi_act; float* gi_cache;              // adjoint: input gradient
+  const float* t_root; const float* t_dof; const float* t_act; const float* t_cache;  // tangent: input
+  float* o_root; float* o_dof; float* o_cache;                                // step output (optional)
+  float* to_root; float* to_dof; float* to_cache;                             // tangent: output
+  int* status;                                                                // per env: 0, or 2 on failure
+  int mode, dir_base;
+};
+
+
 // One launch of step_kernel<G, rows_global> over ta.n_launch_envs envs, groups_per_block envs per
 // CTA (G lanes each), smem bytes of dynamic shared memory per CTA.
 cudaError_t launch_step_kernel(int G, bool rows_global, const StepArgs& a, const TypeArgs& ta,
@@ -18,5 +33,9 @@ cudaError_t set_step_kernel_smem_cap(int G, bool rows_global, size_t bytes);
 cudaError_t launch_persistent_kernel(const PersistArgs& P, int grid, size_t smem, cudaStream_t st);
 cudaError_t set_persistent_kernel_smem_cap(size_t bytes);
 cudaError_t persistent_kernel_occupancy(int* ctas_per_sm, size_t smem);
+
+// Derivative of the step (kernels_adjoint.cu): K tangents per lane (1, 2, 4 or 8), one env per warp.
+cudaError_t launch_tangent_kernel(int K, const StepArgs& a, const TypeArgs& ta, const TangentArgs& v, cudaStream_t st);
+int tangent_lanes_per_dir(int n_dirs);
 
 }  // namespace artsim

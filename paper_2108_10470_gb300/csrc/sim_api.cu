@@ -474,6 +474,17 @@ int plan_persistent(sim_s* h) {
   return SIM_OK;
 }
 
+// The derivative kernel covers env types with ground contacts only and a bounded impulse cache.
+int tangent_supported(const sim_s* h) {
+  for (const TypePlan& tp : h->types)
+    if (tp.tab.n_pairs > 0 || tp.tab.cache_len > 384) {
+      g_last_error = "step derivative: env types with capsule-box pairs or more than 384 impulse-cache entries "
+                     "are not supported";
+      return SIM_ERR_CAPACITY;
+    }
+  return SIM_OK;
+}
+
 void drop_graph(sim_s* h) {
   if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
   h->graph_exec = nullptr;
@@ -915,6 +926,67 @@ int sim_step_host(sim_handle h, const float* host_actuation, float* host_root_ou
   if (host_dof_out && h->N_D > 0)
     CK(cudaMemcpyAsync(host_dof_out, h->dof, sizeof(float) * h->N_D * 2, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  return SIM_OK;
+}
+
+int sim_step_vjp(sim_handle h, const sim_vjp_buffers* b, float dt, int32_t substeps) {
+  if (!valid_handle(h)) return SIM_ERR_HANDLE;
+  if (!b || !b->root_state || !b->dof_state || !b->dof_actuation || !b->impulse_cache || !b->grad_root_state_in ||
+      !b->grad_dof_state_in || !b->grad_dof_actuation || !b->grad_impulse_cache_in)
+    return SIM_ERR_INVALID_ARG;
+  if (!(dt > 0.f) || !finite(dt) || substeps < 1) return SIM_ERR_INVALID_ARG;
+  int rc = tangent_supported(h);
+  if (rc != SIM_OK) return rc;
+  StepArgs a;
+  fill_common(h, dt, substeps, a);
+  TangentArgs v{};
+  v.root = b->root_state; v.dof = b->dof_state; v.act = b->dof_actuation; v.cache = b->impulse_cache;
+  v.g_root = b->grad_root_state; v.g_dof = b->grad_dof_state; v.g_cache = b->grad_impulse_cache;
+  v.gi_root = b->grad_root_state_in; v.gi_dof = b->grad_dof_state_in; v.gi_act = b->grad_dof_actuation;
+  v.gi_cache = b->grad_impulse_cache_in;
+  v.status = b->status;
+  v.mode = 0;
+  for (size_t t = 0; t < h->types.size(); ++t) {
+    const EnvTypeTable& T = h->types[t].tab;
+    TypeArgs ta;
+    fill_type(h, t, ta);
+    const int dirs = 13 * T.n_actors + 3 * T.n_jdof + T.cache_len;
+    const int K = tangent_lanes_per_dir(dirs);
+    for (int base = 0; base < dirs; base += 32 * K) {
+      v.dir_base = base;
+      const cudaError_t e = launch_tangent_kernel(K, a, ta, v, h->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "tangent_step_kernel launch (adjoint)");
+    }
+  }
+  return SIM_OK;
+}
+
+int sim_step_jvp(sim_handle h, const sim_jvp_buffers* b, float dt, int32_t substeps) {
+  if (!valid_handle(h)) return SIM_ERR_HANDLE;
+  if (!b || !b->root_state || !b->dof_state || !b->dof_actuation || !b->impulse_cache || !b->tan_root_state ||
+      !b->tan_dof_state || !b->tan_dof_actuation || !b->tan_impulse_cache || !b->root_state_out ||
+      !b->dof_state_out || !b->impulse_cache_out || !b->tan_root_state_out || !b->tan_dof_state_out ||
+      !b->tan_impulse_cache_out)
+    return SIM_ERR_INVALID_ARG;
+  if (!(dt > 0.f) || !finite(dt) || substeps < 1) return SIM_ERR_INVALID_ARG;
+  int rc = tangent_supported(h);
+  if (rc != SIM_OK) return rc;
+  StepArgs a;
+  fill_common(h, dt, substeps, a);
+  TangentArgs v{};
+  v.root = b->root_state; v.dof = b->dof_state; v.act = b->dof_actuation; v.cache = b->impulse_cache;
+  v.t_root = b->tan_root_state; v.t_dof = b->tan_dof_state; v.t_act = b->tan_dof_actuation;
+  v.t_cache = b->tan_impulse_cache;
+  v.o_root = b->root_state_out; v.o_dof = b->dof_state_out; v.o_cache = b->impulse_cache_out;
+  v.to_root = b->tan_root_state_out; v.to_dof = b->tan_dof_state_out; v.to_cache = b->tan_impulse_cache_out;
+  v.status = b->status;
+  v.mode = 1;
+  for (size_t t = 0; t < h->types.size(); ++t) {
+    TypeArgs ta;
+    fill_type(h, t, ta);
+    const cudaError_t e = launch_tangent_kernel(1, a, ta, v, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "tangent_step_kernel launch (tangent)");
+  }
   return SIM_OK;
 }
 

@@ -1,0 +1,536 @@
+// Forward-mode derivative of the env-step on the GPU: the step of step_kernel.cuh evaluated by one
+// lane in dual arithmetic (a value and K tangents), serially over the env's links, DOFs, contacts
+// and rows. Every lane of a warp evaluates the same env with its own K input directions seeded, so
+// a warp yields 32 K columns of the env-step's Jacobian; contracting them with an output gradient
+// gives the vector-Jacobian product (the adjoint) without communication between lanes.
+//
+// The discrete step is the forward kernel's (joint forces, forward kinematics, articulated-body
+// dynamics, ground contacts and joint-limit rows, the TGS-style projected Gauss-Seidel solve in
+// z = L^T v, integration), written here in its joint-space form: M qdd = tau - b with the
+// joint-space inertia M from composite inertias and the bias b from a recursive Newton-Euler pass,
+// both in world axes about each actor's root origin. Branches (contact and limit decisions, clamps,
+// the speculative / biased target) follow the value, so the derivative is that of the step with its
+// constraint and active sets held fixed. Shape-pair contacts are not part of this path.
+#pragma once
+#include "sim_internal.h"
+
+namespace artsim {
+
+// ---- dual numbers ------------------------------------------------------------------------------
+template <int K> struct Dn {
+  float v;
+  float d[K];
+  __device__ __forceinline__ Dn() {}
+  __device__ __forceinline__ Dn(float x) : v(x) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) d[k] = 0.f;
+  }
+};
+template <int K> __device__ __forceinline__ Dn<K> operator+(const Dn<K>& a, const Dn<K>& b) {
+  Dn<K> r; r.v = a.v + b.v;
+#pragma unroll
+  for (int k = 0; k < K; ++k) r.d[k] = a.d[k] + b.d[k];
+  return r;
+}
+template <int K> __device__ __forceinline__ Dn<K> operator-(const Dn<K>& a, const Dn<K>& b) {
+  Dn<K> r; r.v = a.v - b.v;
+#pragma unroll
+  for (int k = 0; k < K; ++k) r.d[k] = a.d[k] - b.d[k];
+  return r;
+}
+template <int K> __device__ __forceinline__ Dn<K> operator-(const Dn<K>& a) {
+  Dn<K> r; r.v = -a.v;
+#pragma unroll
+  for (int k = 0; k < K; ++k) r.d[k] = -a.d[k];
+  return r;
+}
+template <int K> __device__ __forceinline__ Dn<K> operator*(const Dn<K>& a, const Dn<K>& b) {
+  Dn<K> r; r.v = a.v * b.v;
+#pragma unroll
+  for (int k = 0; k < K; ++k) r.d[k] = a.d[k] * b.v + a.v * b.d[k];
+  return r;
+}
+template <int K> __device__ __forceinline__ Dn<K> operator*(const Dn<K>& a, float s) {
+  Dn<K> r; r.v = a.v * s;
+#pragma unroll
+  for (int k = 0; k < K; ++k) r.d[k] = a.d[k] * s;
+  return r;
+}
+template <int K> __device__ __forceinline__ Dn<K> operator/(const Dn<K>& a, const Dn<K>& b) {
+  Dn<K> r; r.v = a.v / b.v;
+  const float ib = 1.f / b.v;
+#pragma unroll
+  for (int k = 0; k < K; ++k) r.d[k] = (a.d[k] - r.v * b.d[k]) * ib;
+  return r;
+}
+template <int K> __device__ __forceinline__ Dn<K> dsqrt(const Dn<K>& a) {
+  Dn<K> r; r.v = sqrtf(a.v);
+  const float h = 0.5f / r.v;
+#pragma unroll
+  for (int k = 0; k < K; ++k) r.d[k] = a.d[k] * h;
+  return r;
+}
+template <int K> __device__ __forceinline__ void dsincos(const Dn<K>& a, Dn<K>& s, Dn<K>& c) {
+  float sv, cv;
+  sincosf(a.v, &sv, &cv);
+  s.v = sv; c.v = cv;
+#pragma unroll
+  for (int k = 0; k < K; ++k) { s.d[k] = cv * a.d[k]; c.d[k] = -sv * a.d[k]; }
+}
+// a + b * c
+template <int K> __device__ __forceinline__ Dn<K> dfma(const Dn<K>& b, const Dn<K>& c, const Dn<K>& a) {
+  Dn<K> r; r.v = fmaf(b.v, c.v, a.v);
+#pragma unroll
+  for (int k = 0; k < K; ++k) r.d[k] = a.d[k] + b.d[k] * c.v + b.v * c.d[k];
+  return r;
+}
+
+template <int K> struct DV3 { Dn<K> x, y, z; };
+template <int K> __device__ __forceinline__ DV3<K> dv3(const Dn<K>& x, const Dn<K>& y, const Dn<K>& z) {
+  DV3<K> r; r.x = x; r.y = y; r.z = z; return r;
+}
+template <int K> __device__ __forceinline__ DV3<K> operator+(const DV3<K>& a, const DV3<K>& b) {
+  return dv3<K>(a.x + b.x, a.y + b.y, a.z + b.z);
+}
+template <int K> __device__ __forceinline__ DV3<K> operator-(const DV3<K>& a, const DV3<K>& b) {
+  return dv3<K>(a.x - b.x, a.y - b.y, a.z - b.z);
+}
+template <int K> __device__ __forceinline__ DV3<K> operator*(const DV3<K>& a, const Dn<K>& s) {
+  return dv3<K>(a.x * s, a.y * s, a.z * s);
+}
+template <int K> __device__ __forceinline__ Dn<K> ddot(const DV3<K>& a, const DV3<K>& b) {
+  return a.x * b.x + a.y * b.y + a.z * b.z;
+}
+template <int K> __device__ __forceinline__ DV3<K> dcross(const DV3<K>& a, const DV3<K>& b) {
+  return dv3<K>(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+// 3x3 row-major matrix times vector / matrix
+template <int K> __device__ __forceinline__ DV3<K> dmv(const Dn<K>* R, const DV3<K>& v) {
+  return dv3<K>(R[0] * v.x + R[1] * v.y + R[2] * v.z, R[3] * v.x + R[4] * v.y + R[5] * v.z,
+                R[6] * v.x + R[7] * v.y + R[8] * v.z);
+}
+template <int K> __device__ __forceinline__ void dmm(const Dn<K>* A, const Dn<K>* B, Dn<K>* C) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) C[3 * i + j] = A[3 * i] * B[j] + A[3 * i + 1] * B[3 + j] + A[3 * i + 2] * B[6 + j];
+}
+
+// ---- per-lane work space (local memory) --------------------------------------------------------
+constexpr int kTanMaxCon = 64;                       // kept ground contacts per env
+constexpr int kTanMaxRows = 2 * kMaxGen + 3 * kTanMaxCon;
+constexpr int kTanMaxCache = 384;                    // impulse-cache entries per env
+
+template <int K> struct TanWork {
+  Dn<K> R[kMaxLinks][9];     // link -> world rotation
+  Dn<K> P[kMaxLinks][3];     // link origin relative to its actor's origin
+  Dn<K> V[kMaxLinks][6];     // spatial velocity [w; v] about the actor origin
+  Dn<K> Ab[kMaxLinks][6];    // velocity-product (bias) acceleration; later the subtree bias force
+  Dn<K> Ic[kMaxLinks][10];   // rigid, then composite inertia about the actor origin: m, h (3), I (6)
+  Dn<K> S[kMaxGen][6];       // motion subspace of each generalized DOF
+  Dn<K> L[kMaxGen * (kMaxGen + 1) / 2];  // joint-space inertia, then its Cholesky factor (lower, packed)
+  Dn<K> nu[kMaxGen], rhs[kMaxGen], z[kMaxGen], dz[kMaxGen];
+  Dn<K> cx[kTanMaxCon][3], cd[kTanMaxCon];
+  int clink[kTanMaxCon], ccand[kTanMaxCon];
+  float cmu[kTanMaxCon];
+  Dn<K> lam[kTanMaxRows];
+};
+
+// packed lower-triangular index (i >= j)
+__device__ __forceinline__ int tri(int i, int j) { return i * (i + 1) / 2 + j; }
+
+template <int K> __device__ __forceinline__ void dquat_to_mat(const Dn<K>* q, Dn<K>* R) {
+  const Dn<K> x = q[0], y = q[1], z = q[2], w = q[3];
+  const Dn<K> two(2.f), one(1.f);
+  R[0] = one - two * (y * y + z * z); R[1] = two * (x * y - z * w); R[2] = two * (x * z + y * w);
+  R[3] = two * (x * y + z * w); R[4] = one - two * (x * x + z * z); R[5] = two * (y * z - x * w);
+  R[6] = two * (x * z - y * w); R[7] = two * (y * z + x * w); R[8] = one - two * (x * x + y * y);
+}
+
+// Row r's J^T solved through L: y = L^-1 J_r^T (n entries). Row kinds as in the forward kernel:
+// limit rows (unit +-1 on one DOF), contact normal / friction rows along e_z, e_x, e_y.
+template <int K> __device__ void row_response(const EnvTypeTable* T, const TanWork<K>& w, int n, int kind, int gdof,
+                                              float sgn, int c, int dir, Dn<K>* y) {
+  const unsigned anc = kind == kRowLimit ? 0u : T->anc[w.clink[c]];
+  Dn<K> fr[6];
+  if (kind != kRowLimit) {
+    // k = e_z (normal), e_x, e_y (friction); f = [x x k; k]
+    const Dn<K>& x0 = w.cx[c][0];
+    const Dn<K>& x1 = w.cx[c][1];
+    const Dn<K>& x2 = w.cx[c][2];
+    const Dn<K> zero(0.f);
+    if (dir == 0) { fr[0] = x1; fr[1] = -x0; fr[2] = zero; fr[3] = zero; fr[4] = zero; fr[5] = Dn<K>(1.f); }
+    else if (dir == 1) { fr[0] = zero; fr[1] = x2; fr[2] = -x1; fr[3] = Dn<K>(1.f); fr[4] = zero; fr[5] = zero; }
+    else { fr[0] = -x2; fr[1] = zero; fr[2] = x0; fr[3] = zero; fr[4] = Dn<K>(1.f); fr[5] = zero; }
+  }
+  for (int i = 0; i < n; ++i) {
+    Dn<K> ji(0.f);
+    if (kind == kRowLimit) {
+      if (i == gdof) ji = Dn<K>(sgn);
+    } else if ((anc >> i) & 1u) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) ji = ji + w.S[i][k] * fr[k];
+    }
+    for (int k = 0; k < i; ++k) ji = ji - w.L[tri(i, k)] * y[k];
+    y[i] = ji / w.L[tri(i, i)];
+  }
+}
+
+// Per-env state of the tangent step (per actor: root p, quat, v, w; per joint DOF: q, qd; the env's
+// actuation and impulse cache). Arrays are indexed env-locally.
+template <int K> struct TanState {
+  Dn<K> rp[kMaxActors][3], rq[kMaxActors][4], rv[kMaxActors][3], rw[kMaxActors][3];
+  Dn<K> q[kMaxGen], qd[kMaxGen], act[kMaxGen];
+  Dn<K> cache[kTanMaxCache];
+};
+
+// One substep in dual arithmetic. Returns false if a pivot or a capacity check fails.
+template <int K> __device__ bool tangent_substep(const StepArgs& A, const EnvTypeTable* T, TanState<K>& s,
+                                                 TanWork<K>& w) {
+  const int L = T->n_links, n = T->n_gen;
+  const float h = A.h;
+  const int npos = A.pos_iters, nvel = A.vel_iters;
+  const float hit = h / (float)npos;
+  const float gx = A.gx, gy = A.gy, gz = A.gz;
+  // ---- forward kinematics, velocities, bias accelerations, rigid inertias (links in order) ----
+  for (int l = 0; l < L; ++l) {
+    const int par = T->parent[l], jt = T->jtype[l], a = T->actor[l], gd = T->gdof[l], jd = T->jdof[l];
+    if (par < 0) {
+      dquat_to_mat<K>(s.rq[a], w.R[l]);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) w.P[l][k] = Dn<K>(0.f);
+      if (jt == kFree) {
+        for (int k = 0; k < 3; ++k) { w.V[l][k] = s.rw[a][k]; w.V[l][3 + k] = s.rv[a][k]; }
+        // d/dt (S_root nu) = [0; p_dot x omega]
+        const DV3<K> pxw = dcross(dv3<K>(s.rv[a][0], s.rv[a][1], s.rv[a][2]), dv3<K>(s.rw[a][0], s.rw[a][1], s.rw[a][2]));
+        w.Ab[l][0] = Dn<K>(0.f); w.Ab[l][1] = Dn<K>(0.f); w.Ab[l][2] = Dn<K>(0.f);
+        w.Ab[l][3] = pxw.x; w.Ab[l][4] = pxw.y; w.Ab[l][5] = pxw.z;
+        for (int c = 0; c < 6; ++c)
+          for (int k = 0; k < 6; ++k) w.S[gd + c][k] = Dn<K>(c == k ? 1.f : 0.f);
+        for (int k = 0; k < 3; ++k) { w.nu[gd + k] = s.rw[a][k]; w.nu[gd + 3 + k] = s.rv[a][k]; }
+      } else {
+        for (int k = 0; k < 6; ++k) { w.V[l][k] = Dn<K>(0.f); w.Ab[l][k] = Dn<K>(0.f); }
+      }
+    } else {
+      Dn<K> Rpj[9], RB[9];
+      for (int k = 0; k < 9; ++k) Rpj[k] = Dn<K>(T->prot[k][l]);
+      dmm<K>(w.R[par], Rpj, RB);
+      const DV3<K> jax = dv3<K>(Dn<K>(T->axis[0][l]), Dn<K>(T->axis[1][l]), Dn<K>(T->axis[2][l]));
+      const DV3<K> pp = dv3<K>(Dn<K>(T->ppos[0][l]), Dn<K>(T->ppos[1][l]), Dn<K>(T->ppos[2][l]));
+      const DV3<K> Pp = dv3<K>(w.P[par][0], w.P[par][1], w.P[par][2]);
+      const DV3<K> aw = dmv<K>(RB, jax);
+      DV3<K> Pl;
+      Dn<K> Sa[6];
+      for (int k = 0; k < 6; ++k) Sa[k] = Dn<K>(0.f);
+      if (jt == kRevolute) {
+        // R_J = rotation by q about the joint axis (Rodrigues)
+        Dn<K> sn, cs;
+        dsincos<K>(s.q[jd], sn, cs);
+        const Dn<K> t = Dn<K>(1.f) - cs;
+        const float ax = T->axis[0][l], ay = T->axis[1][l], az = T->axis[2][l];
+        Dn<K> RJ[9];
+        RJ[0] = t * (ax * ax) + cs;      RJ[1] = t * (ax * ay) - sn * az; RJ[2] = t * (ax * az) + sn * ay;
+        RJ[3] = t * (ax * ay) + sn * az; RJ[4] = t * (ay * ay) + cs;      RJ[5] = t * (ay * az) - sn * ax;
+        RJ[6] = t * (ax * az) - sn * ay; RJ[7] = t * (ay * az) + sn * ax; RJ[8] = t * (az * az) + cs;
+        dmm<K>(RB, RJ, w.R[l]);
+        Pl = Pp + dmv<K>(w.R[par], pp);
+        const DV3<K> pxa = dcross(Pl, aw);
+        Sa[0] = aw.x; Sa[1] = aw.y; Sa[2] = aw.z; Sa[3] = pxa.x; Sa[4] = pxa.y; Sa[5] = pxa.z;
+      } else if (jt == kPrismatic) {
+        for (int k = 0; k < 9; ++k) w.R[l][k] = RB[k];
+        Pl = Pp + dmv<K>(w.R[par], pp + dmv<K>(Rpj, jax * s.q[jd]));
+        Sa[3] = aw.x; Sa[4] = aw.y; Sa[5] = aw.z;
+      } else {
+        for (int k = 0; k < 9; ++k) w.R[l][k] = RB[k];
+        Pl = Pp + dmv<K>(w.R[par], pp);
+      }
+      w.P[l][0] = Pl.x; w.P[l][1] = Pl.y; w.P[l][2] = Pl.z;
+      Dn<K> sq[6];
+      const Dn<K> qd = (jd >= 0) ? s.qd[jd] : Dn<K>(0.f);
+      for (int k = 0; k < 6; ++k) { sq[k] = Sa[k] * qd; w.V[l][k] = w.V[par][k] + sq[k]; }
+      // c = v x (S qd); bias acceleration accumulates down the tree
+      const DV3<K> wv = dv3<K>(w.V[l][0], w.V[l][1], w.V[l][2]), vl = dv3<K>(w.V[l][3], w.V[l][4], w.V[l][5]);
+      const DV3<K> sa = dv3<K>(sq[0], sq[1], sq[2]), sl = dv3<K>(sq[3], sq[4], sq[5]);
+      const DV3<K> c0 = dcross(wv, sa), c1 = dcross(wv, sl) + dcross(vl, sa);
+      w.Ab[l][0] = w.Ab[par][0] + c0.x; w.Ab[l][1] = w.Ab[par][1] + c0.y; w.Ab[l][2] = w.Ab[par][2] + c0.z;
+      w.Ab[l][3] = w.Ab[par][3] + c1.x; w.Ab[l][4] = w.Ab[par][4] + c1.y; w.Ab[l][5] = w.Ab[par][5] + c1.z;
+      if (gd >= 0) {
+        for (int k = 0; k < 6; ++k) w.S[gd][k] = Sa[k];
+        w.nu[gd] = qd;
+      }
+    }
+    // rigid inertia about the actor origin: I_O = R I_c R^T + m (|c|^2 1 - c c^T), h = m c
+    const float m = T->mass[l];
+    const DV3<K> cw = dv3<K>(w.P[l][0], w.P[l][1], w.P[l][2]) +
+                      dmv<K>(w.R[l], dv3<K>(Dn<K>(T->com[0][l]), Dn<K>(T->com[1][l]), Dn<K>(T->com[2][l])));
+    Dn<K> In[9], RI[9], RIRt[9], Rt[9];
+    const float ii[9] = {T->inertia[0][l], T->inertia[3][l], T->inertia[4][l], T->inertia[3][l], T->inertia[1][l],
+                         T->inertia[5][l], T->inertia[4][l], T->inertia[5][l], T->inertia[2][l]};
+    for (int k = 0; k < 9; ++k) In[k] = Dn<K>(ii[k]);
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) Rt[3 * i + j] = w.R[l][3 * j + i];
+    dmm<K>(w.R[l], In, RI);
+    dmm<K>(RI, Rt, RIRt);
+    const Dn<K> c2 = ddot(cw, cw);
+    w.Ic[l][0] = Dn<K>(m);
+    w.Ic[l][1] = cw.x * m; w.Ic[l][2] = cw.y * m; w.Ic[l][3] = cw.z * m;
+    w.Ic[l][4] = RIRt[0] + (c2 - cw.x * cw.x) * m;
+    w.Ic[l][5] = RIRt[4] + (c2 - cw.y * cw.y) * m;
+    w.Ic[l][6] = RIRt[8] + (c2 - cw.z * cw.z) * m;
+    w.Ic[l][7] = RIRt[1] - cw.x * cw.y * m;
+    w.Ic[l][8] = RIRt[2] - cw.x * cw.z * m;
+    w.Ic[l][9] = RIRt[5] - cw.y * cw.z * m;
+  }
+  // ---- bias forces f = I a_bias + v x* I v - f_gravity (stored in Ab) ----
+  for (int l = 0; l < L; ++l) {
+    const Dn<K>* I = w.Ic[l];
+    const DV3<K> hh = dv3<K>(I[1], I[2], I[3]);
+    auto Imul = [&](const Dn<K>* x, DV3<K>& fa, DV3<K>& fl) {
+      const DV3<K> xw = dv3<K>(x[0], x[1], x[2]), xv = dv3<K>(x[3], x[4], x[5]);
+      const DV3<K> Iw = dv3<K>(I[4] * xw.x + I[7] * xw.y + I[8] * xw.z, I[7] * xw.x + I[5] * xw.y + I[9] * xw.z,
+                               I[8] * xw.x + I[9] * xw.y + I[6] * xw.z);
+      fa = Iw + dcross(hh, xv);
+      fl = xv * I[0] + dcross(xw, hh);
+    };
+    DV3<K> Fa, Fl, Ga, Gl;
+    Imul(w.V[l], Fa, Fl);
+    Imul(w.Ab[l], Ga, Gl);
+    const DV3<K> wv = dv3<K>(w.V[l][0], w.V[l][1], w.V[l][2]), vl = dv3<K>(w.V[l][3], w.V[l][4], w.V[l][5]);
+    const DV3<K> g = dv3<K>(Dn<K>(gx), Dn<K>(gy), Dn<K>(gz));
+    const DV3<K> pa = Ga + dcross(wv, Fa) + dcross(vl, Fl) - dcross(hh, g);
+    const DV3<K> pl = Gl + dcross(wv, Fl) - g * I[0];
+    w.Ab[l][0] = pa.x; w.Ab[l][1] = pa.y; w.Ab[l][2] = pa.z; w.Ab[l][3] = pl.x; w.Ab[l][4] = pl.y; w.Ab[l][5] = pl.z;
+  }
+  // ---- subtree sums (children after parents: sweep links backwards) ----
+  for (int l = L - 1; l >= 0; --l) {
+    const int par = T->parent[l];
+    if (par >= 0) {
+      for (int k = 0; k < 6; ++k) w.Ab[par][k] = w.Ab[par][k] + w.Ab[l][k];
+      for (int k = 0; k < 10; ++k) w.Ic[par][k] = w.Ic[par][k] + w.Ic[l][k];
+    }
+  }
+  // ---- joint-space inertia M (composite inertias) and bias b = S^T F ----
+  for (int i = 0; i < n; ++i) {
+    const int li = T->dof_link[i];
+    // f = Ic(li) S_i ... M_ij = S_j^T Ic(deeper) S_i for j an ancestor-or-self DOF of i
+    const Dn<K>* I = w.Ic[li];
+    const DV3<K> hh = dv3<K>(I[1], I[2], I[3]);
+    const DV3<K> xw = dv3<K>(w.S[i][0], w.S[i][1], w.S[i][2]), xv = dv3<K>(w.S[i][3], w.S[i][4], w.S[i][5]);
+    const DV3<K> Iw = dv3<K>(I[4] * xw.x + I[7] * xw.y + I[8] * xw.z, I[7] * xw.x + I[5] * xw.y + I[9] * xw.z,
+                             I[8] * xw.x + I[9] * xw.y + I[6] * xw.z);
+    const DV3<K> fa = Iw + dcross(hh, xv), fl = xv * I[0] + dcross(xw, hh);
+    const unsigned anc = T->anc[li];
+    for (int j = 0; j <= i; ++j) {
+      if (!((anc >> j) & 1u)) { w.L[tri(i, j)] = Dn<K>(0.f); continue; }
+      w.L[tri(i, j)] = w.S[j][0] * fa.x + w.S[j][1] * fa.y + w.S[j][2] * fa.z + w.S[j][3] * fl.x +
+                       w.S[j][4] * fl.y + w.S[j][5] * fl.z;
+    }
+    Dn<K> bi(0.f);
+    for (int k = 0; k < 6; ++k) bi = bi + w.S[i][k] * w.Ab[li][k];
+    // joint force of the substep (damping at the substep-start velocity); a floating root has none
+    const int comp = T->dof_comp[i];
+    Dn<K> tau(0.f);
+    if (comp < 0) {
+      const int jd = T->jdof[li];
+      tau = s.act[jd] - s.qd[jd] * T->damping[li];
+      w.L[tri(i, i)] = w.L[tri(i, i)] + Dn<K>(T->armature[li]);
+    }
+    w.rhs[i] = tau - bi;
+  }
+  // ---- Cholesky M = L L^T (in place, packed lower) ----
+  for (int j = 0; j < n; ++j) {
+    Dn<K> djj = w.L[tri(j, j)];
+    for (int k = 0; k < j; ++k) djj = djj - w.L[tri(j, k)] * w.L[tri(j, k)];
+    if (!(djj.v > 0.f)) return false;
+    const Dn<K> ljj = dsqrt(djj);
+    w.L[tri(j, j)] = ljj;
+    for (int i = j + 1; i < n; ++i) {
+      Dn<K> x = w.L[tri(i, j)];
+      for (int k = 0; k < j; ++k) x = x - w.L[tri(i, k)] * w.L[tri(j, k)];
+      w.L[tri(i, j)] = x / ljj;
+    }
+  }
+  // qdd = M^-1 (tau - b): y = L^-1 rhs, then v_free = nu + h L^-T y; z = L^T v_free = L^T nu + h y
+  for (int i = 0; i < n; ++i) {
+    Dn<K> x = w.rhs[i];
+    for (int k = 0; k < i; ++k) x = x - w.L[tri(i, k)] * w.rhs[k];
+    w.rhs[i] = x / w.L[tri(i, i)];
+  }
+  for (int i = 0; i < n; ++i) {
+    Dn<K> x(0.f);
+    for (int k = i; k < n; ++k) x = x + w.L[tri(k, i)] * w.nu[k];
+    w.z[i] = x + w.rhs[i] * h;
+    w.dz[i] = Dn<K>(0.f);
+  }
+  // ---- ground contacts (shape order, then slot) ----
+  const float coff = A.contact_offset;
+  int nc = 0;
+  for (int sh = 0; sh < T->n_shapes; ++sh) {
+    const int l = T->shape_link[sh], st = T->shape_type[sh], a = T->actor[l];
+    Dn<K> Rsh[9], Rs[9];
+    for (int k = 0; k < 9; ++k) Rsh[k] = Dn<K>(T->shape_rot[k][sh]);
+    dmm<K>(w.R[l], Rsh, Rs);
+    const DV3<K> cs = dv3<K>(w.P[l][0], w.P[l][1], w.P[l][2]) +
+                      dmv<K>(w.R[l], dv3<K>(Dn<K>(T->shape_pos[0][sh]), Dn<K>(T->shape_pos[1][sh]), Dn<K>(T->shape_pos[2][sh])));
+    const Dn<K> oz = s.rp[a][2];
+    const float s0 = T->shape_size[0][sh], s1 = T->shape_size[1][sh], s2 = T->shape_size[2][sh];
+    const int nk = (st == kSphere) ? 1 : (st == kCapsule ? 2 : 8);
+    for (int k = 0; k < nk; ++k) {
+      DV3<K> x;
+      Dn<K> zc;
+      if (st == kSphere) {
+        x = dv3<K>(cs.x, cs.y, cs.z - Dn<K>(s0));
+        zc = (oz + cs.z) - Dn<K>(s0);
+      } else if (st == kCapsule) {
+        const DV3<K> ax = dv3<K>(Rs[0], Rs[3], Rs[6]);
+        const DV3<K> e = (k == 0) ? cs - ax * Dn<K>(s1) : cs + ax * Dn<K>(s1);
+        x = dv3<K>(e.x, e.y, e.z - Dn<K>(s0));
+        zc = (oz + e.z) - Dn<K>(s0);
+      } else {
+        const DV3<K> loc = dv3<K>(Dn<K>((k & 4) ? s0 : -s0), Dn<K>((k & 2) ? s1 : -s1), Dn<K>((k & 1) ? s2 : -s2));
+        x = cs + dmv<K>(Rs, loc);
+        zc = oz + x.z;
+      }
+      if (zc.v < coff) {
+        if (nc >= kTanMaxCon) return false;
+        w.cx[nc][0] = x.x; w.cx[nc][1] = x.y; w.cx[nc][2] = x.z;
+        w.cd[nc] = zc;
+        w.clink[nc] = l;
+        w.ccand[nc] = T->cand_off[sh] + k;
+        w.cmu[nc] = T->shape_mu[sh];
+        ++nc;
+      }
+    }
+  }
+  // ---- rows: limits (link order, lower before upper), normals, friction pairs ----
+  // row r is described on the fly: r < nl: limit list; then contact normals; then frictions
+  int lim_g[2 * kMaxGen], lim_side[2 * kMaxGen], lim_jd[2 * kMaxGen];
+  Dn<K> lim_d[2 * kMaxGen];
+  int nl = 0;
+  for (int l = 0; l < L; ++l) {
+    const int jt = T->jtype[l];
+    if (T->parent[l] < 0 || !(jt == kRevolute || jt == kPrismatic) || !T->has_limit[l]) continue;
+    const int jd = T->jdof[l];
+    const Dn<K> dlo = s.q[jd] - Dn<K>(T->lo[l]), dhi = Dn<K>(T->hi[l]) - s.q[jd];
+    if (dlo.v < A.limit_margin) { lim_g[nl] = T->gdof[l]; lim_side[nl] = 0; lim_jd[nl] = jd; lim_d[nl] = dlo; ++nl; }
+    if (dhi.v < A.limit_margin) { lim_g[nl] = T->gdof[l]; lim_side[nl] = 1; lim_jd[nl] = jd; lim_d[nl] = dhi; ++nl; }
+  }
+  const int R = nl + 3 * nc;
+  if (R > kTanMaxRows) return false;
+  Dn<K> y[kMaxGen];
+  auto describe = [&](int r, int& kind, int& g, float& sgn, int& c, int& dir, int& slot) {
+    if (r < nl) {
+      kind = kRowLimit; g = lim_g[r]; sgn = lim_side[r] ? -1.f : 1.f; c = 0; dir = 0;
+      slot = 3 * T->n_cand + 2 * lim_jd[r] + lim_side[r];
+    } else if (r < nl + nc) {
+      kind = kRowNormal; c = r - nl; dir = 0; g = 0; sgn = 0.f; slot = 3 * w.ccand[c];
+    } else {
+      kind = kRowFriction; c = (r - nl - nc) >> 1; dir = 1 + ((r - nl - nc) & 1); g = 0; sgn = 0.f;
+      slot = 3 * w.ccand[c] + dir;
+    }
+  };
+  // warm start from the cache
+  for (int r = 0; r < R; ++r) {
+    int kind, g, c, dir, slot;
+    float sgn;
+    describe(r, kind, g, sgn, c, dir, slot);
+    row_response<K>(T, w, n, kind, g, sgn, c, dir, y);
+    Dn<K> a2(0.f);
+    for (int i = 0; i < n; ++i) a2 = a2 + y[i] * y[i];
+    w.lam[r] = (a2.v > 1e-12f) ? s.cache[slot] : Dn<K>(0.f);
+    for (int i = 0; i < n; ++i) w.z[i] = w.z[i] + y[i] * w.lam[r];
+  }
+  // ---- projected Gauss-Seidel in z = L^T v ----
+  const float beta = A.bias_coef, vmax = A.max_depen_vel;
+  for (int it = 0; it < npos + nvel; ++it) {
+    const bool pos = it < npos;
+    for (int r = 0; r < R; ++r) {
+      int kind, g, c, dir, slot;
+      float sgn;
+      describe(r, kind, g, sgn, c, dir, slot);
+      row_response<K>(T, w, n, kind, g, sgn, c, dir, y);
+      Dn<K> a2(0.f), yz(0.f), ydz(0.f);
+      for (int i = 0; i < n; ++i) { a2 = a2 + y[i] * y[i]; yz = yz + y[i] * w.z[i]; ydz = ydz + y[i] * w.dz[i]; }
+      if (!(a2.v > 1e-12f)) continue;
+      const Dn<K> dr = (kind == kRowLimit) ? lim_d[r] : w.cd[c];
+      const Dn<K> sep = dr + ydz;
+      const Dn<K> lam = w.lam[r];
+      Dn<K> lnew;
+      if (kind == kRowFriction) {
+        const Dn<K> lim = w.lam[nl + c] * w.cmu[c];
+        lnew = lam - yz / a2;
+        if (lnew.v > lim.v) lnew = lim;
+        if (lnew.v < -lim.v) lnew = -lim;
+      } else {
+        Dn<K> target(0.f);
+        if (pos) {
+          if (sep.v >= 0.f) target = -sep * (1.f / hit);
+          else {
+            target = -sep * (beta / hit);
+            if (target.v > vmax) target = Dn<K>(vmax);
+          }
+        } else if (sep.v > 0.f) {
+          target = -sep * (1.f / h);
+        }
+        lnew = lam + (target - yz) / a2;
+        if (lnew.v < 0.f) lnew = Dn<K>(0.f);
+      }
+      const Dn<K> dl = lnew - lam;
+      for (int i = 0; i < n; ++i) w.z[i] = w.z[i] + y[i] * dl;
+      w.lam[r] = lnew;
+    }
+    if (pos)
+      for (int i = 0; i < n; ++i) w.dz[i] = w.dz[i] + w.z[i] * hit;
+  }
+  // v = L^-T z, dq = L^-T dz (overwrite z, dz)
+  for (int i = n - 1; i >= 0; --i) {
+    Dn<K> a = w.z[i], b = w.dz[i];
+    for (int k = i + 1; k < n; ++k) { a = a - w.L[tri(k, i)] * w.z[k]; b = b - w.L[tri(k, i)] * w.dz[k]; }
+    w.z[i] = a / w.L[tri(i, i)];
+    w.dz[i] = b / w.L[tri(i, i)];
+  }
+  // ---- impulse cache: cleared, then every row's impulse at its slot ----
+  for (int i = 0; i < T->cache_len; ++i) s.cache[i] = Dn<K>(0.f);
+  for (int r = 0; r < R; ++r) {
+    int kind, g, c, dir, slot;
+    float sgn;
+    describe(r, kind, g, sgn, c, dir, slot);
+    s.cache[slot] = w.lam[r];
+  }
+  // ---- integrate ----
+  for (int l = 0; l < L; ++l) {
+    const int gd = T->gdof[l], jd = T->jdof[l], a = T->actor[l];
+    if (T->parent[l] >= 0) {
+      if (jd >= 0) { s.q[jd] = s.q[jd] + w.dz[gd]; s.qd[jd] = w.z[gd]; }
+    } else if (T->jtype[l] == kFree) {
+      for (int k = 0; k < 3; ++k) {
+        s.rp[a][k] = s.rp[a][k] + w.dz[gd + 3 + k];
+        s.rw[a][k] = w.z[gd + k];
+        s.rv[a][k] = w.z[gd + 3 + k];
+      }
+      // quat <- exp(da) * quat (exact exponential), normalised
+      const DV3<K> da = dv3<K>(w.dz[gd], w.dz[gd + 1], w.dz[gd + 2]);
+      const Dn<K> a2 = ddot(da, da);
+      Dn<K> e[4];
+      if (a2.v < 1e-30f) {
+        e[0] = da.x * 0.5f; e[1] = da.y * 0.5f; e[2] = da.z * 0.5f; e[3] = Dn<K>(1.f);
+      } else {
+        const Dn<K> an = dsqrt(a2);
+        Dn<K> sn, cs;
+        dsincos<K>(an * 0.5f, sn, cs);
+        const Dn<K> sc = sn / an;
+        e[0] = da.x * sc; e[1] = da.y * sc; e[2] = da.z * sc; e[3] = cs;
+      }
+      const Dn<K>* q = s.rq[a];
+      const Dn<K> x = e[3] * q[0] + e[0] * q[3] + e[1] * q[2] - e[2] * q[1];
+      const Dn<K> yq = e[3] * q[1] - e[0] * q[2] + e[1] * q[3] + e[2] * q[0];
+      const Dn<K> zq = e[3] * q[2] + e[0] * q[1] - e[1] * q[0] + e[2] * q[3];
+      const Dn<K> wq = e[3] * q[3] - e[0] * q[0] - e[1] * q[1] - e[2] * q[2];
+      const Dn<K> nr = dsqrt(x * x + yq * yq + zq * zq + wq * wq);
+      s.rq[a][0] = x / nr; s.rq[a][1] = yq / nr; s.rq[a][2] = zq / nr; s.rq[a][3] = wq / nr;
+    }
+  }
+  return true;
+}
+
+}  // namespace artsim

@@ -28,7 +28,7 @@ SIM_FLAG_GRAPH = 4
 EXPORTED = ("sim_create", "sim_step", "sim_step_host", "sim_get_view", "sim_set_root_state_indexed",
             "sim_set_dof_state_indexed", "sim_set_stream", "sim_sync_status", "sim_get_sizes", "sim_destroy",
             "sim_error_string", "sim_last_error_message", "sim_probe_fp32_peak", "sim_step_static_scratch",
-            "sim_get_type_config", "sim_set_type_config", "sim_autotune")
+            "sim_get_type_config", "sim_set_type_config", "sim_autotune", "sim_step_vjp", "sim_step_jvp")
 
 F = ctypes.POINTER(ctypes.c_float)
 I32 = ctypes.POINTER(ctypes.c_int32)
@@ -65,6 +65,22 @@ class sim_state_buffers(ctypes.Structure):
                 ("status", ctypes.c_void_p)]
 
 
+VJP_FIELDS = ("root_state", "dof_state", "dof_actuation", "impulse_cache", "grad_root_state", "grad_dof_state",
+              "grad_impulse_cache", "grad_root_state_in", "grad_dof_state_in", "grad_dof_actuation",
+              "grad_impulse_cache_in", "status")
+JVP_FIELDS = ("root_state", "dof_state", "dof_actuation", "impulse_cache", "tan_root_state", "tan_dof_state",
+              "tan_dof_actuation", "tan_impulse_cache", "root_state_out", "dof_state_out", "impulse_cache_out",
+              "tan_root_state_out", "tan_dof_state_out", "tan_impulse_cache_out", "status")
+
+
+class sim_vjp_buffers(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_void_p) for f in VJP_FIELDS]
+
+
+class sim_jvp_buffers(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_void_p) for f in JVP_FIELDS]
+
+
 def load(path: Optional[str] = None) -> ctypes.CDLL:
     """Load libartsim.so (raises if it has not been built: there is no fallback path)."""
     global _lib
@@ -96,6 +112,8 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     L.sim_set_type_config.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
     L.sim_autotune.argtypes = [ctypes.c_void_p, ctypes.c_float, ctypes.c_int32, ctypes.c_int32,
                                ctypes.POINTER(ctypes.c_double)]
+    L.sim_step_vjp.argtypes = [ctypes.c_void_p, ctypes.POINTER(sim_vjp_buffers), ctypes.c_float, ctypes.c_int32]
+    L.sim_step_jvp.argtypes = [ctypes.c_void_p, ctypes.POINTER(sim_jvp_buffers), ctypes.c_float, ctypes.c_int32]
     _lib = L  # every other entry point returns int, ctypes' default restype
     return L
 
@@ -251,6 +269,23 @@ class Sim:
                                   int(self.w.substeps if substeps is None else substeps), reps, ctypes.byref(ms)),
               "sim_autotune")
         return float(ms.value)
+
+    @staticmethod
+    def _ptrs(fields, bufs):
+        return [ctypes.c_void_p(bufs[f].data_ptr()) if bufs.get(f) is not None else None for f in fields]
+
+    def step_vjp(self, bufs: dict, dt: Optional[float] = None, substeps: Optional[int] = None):
+        """Vector-Jacobian product of one env-step at bufs' input state (keys VJP_FIELDS; device
+        tensors in the views' layouts; missing output gradients count as zero)."""
+        b = sim_vjp_buffers(*self._ptrs(VJP_FIELDS, bufs))
+        check(load().sim_step_vjp(self.h, ctypes.byref(b), float(self.w.dt if dt is None else dt),
+                                  int(self.w.substeps if substeps is None else substeps)), "sim_step_vjp")
+
+    def step_jvp(self, bufs: dict, dt: Optional[float] = None, substeps: Optional[int] = None):
+        """Jacobian-vector product of one env-step (keys JVP_FIELDS)."""
+        b = sim_jvp_buffers(*self._ptrs(JVP_FIELDS, bufs))
+        check(load().sim_step_jvp(self.h, ctypes.byref(b), float(self.w.dt if dt is None else dt),
+                                  int(self.w.substeps if substeps is None else substeps)), "sim_step_jvp")
 
     def set_root_state_indexed(self, src, actor_idx):
         n = int(actor_idx.numel())

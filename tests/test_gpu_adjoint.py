@@ -1,0 +1,249 @@
+"""The step's derivative on the GPU (sim_step_jvp / sim_step_vjp and the autograd wrappers) against
+the FP64 oracle's forward-mode derivative.
+
+Bounds. The serial step's value is checked like the forward kernel (strict bound plus 16 times the
+env's FP32 conditioning scale). A derivative is compared per env in the max norm relative to the
+env's derivative scale, with the bound 1e-3 + 16 times its FP32 conditioning scale: the largest
+deviation from the FP64 derivative of the oracle's own derivative evaluated in single precision at
+inputs nudged by one float32 ulp. Where FP32 and FP64 take different branches (a clamp or target
+switch within rounding of its threshold, which the constraint-set signature does not capture) the
+derivative jumps: such envs are counted and reported, and at most 5 % of the checked envs may be
+outside the bound.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2108_10470_gb300 import workloads as W
+from parity_util import _ulp
+
+pytestmark = pytest.mark.gpu
+K_COND = 16.0
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2108_10470_gb300 import build
+    build.build_library()
+    torch.cuda.set_device(0)
+
+
+def warm(w, seed=0, steps=3):
+    """Seeded state after a few oracle steps, with its warm impulse cache (FP64, float32-rounded)."""
+    root, dof, acts = W.seeded_inputs(w, seed, steps + 1)
+    O = oracle.Oracle(w)
+    r, d = root.astype(np.float64), dof.astype(np.float64)
+    for k in range(steps):
+        O.step(r, d, acts[k])
+    f = lambda x: x.astype(np.float32).astype(np.float64)
+    return f(r), f(d), f(O.cache), acts[steps].astype(np.float64)
+
+
+def direction(w, r, cache, rng):
+    """Random input tangent. Orientations move along the unit sphere (dq = [w; 0] q / 2): off it the
+    step's dependence on the quaternion's norm is an artefact of the formulation (the GPU works in
+    world axes, the oracle in body coordinates; they agree for unit quaternions only)."""
+    dr = rng.standard_normal(r.shape)
+    om = rng.standard_normal((r.shape[0], 3))
+    q = r[:, 3:7]
+    # [om; 0] (x) q, Hamilton product with (x, y, z, w) storage
+    dr[:, 3] = 0.5 * (om[:, 0] * q[:, 3] + om[:, 1] * q[:, 2] - om[:, 2] * q[:, 1])
+    dr[:, 4] = 0.5 * (-om[:, 0] * q[:, 2] + om[:, 1] * q[:, 3] + om[:, 2] * q[:, 0])
+    dr[:, 5] = 0.5 * (om[:, 0] * q[:, 1] - om[:, 1] * q[:, 0] + om[:, 2] * q[:, 3])
+    dr[:, 6] = 0.5 * (-om[:, 0] * q[:, 0] - om[:, 1] * q[:, 1] - om[:, 2] * q[:, 2])
+    dd = rng.standard_normal((w.n_dof, 2))
+    da = rng.standard_normal(w.n_dof)
+    dc = rng.standard_normal(cache.shape) * (cache != 0)
+    return dr, dd, da, dc
+
+
+def oracle_tangent(w, r, d, c, a, t, single=False, nudge=None):
+    O = oracle.Oracle(w)
+    r, d = r.copy(), d.copy()
+    if nudge is not None:
+        r[:, :3] = _ulp(r[:, :3], nudge)
+        d[:, 0] = _ulp(d[:, 0], -nudge)
+    O.cache[:] = c
+    tr, td, tc = t[0].copy(), t[1].copy(), t[3].copy()
+    O.step_tangent(r, d, a, tr, td, t[2], tc, single=single)
+    return r, d, O.cache.copy(), tr, td, tc
+
+
+def gpu_jvp(s, r, d, c, a, t):
+    import torch
+    f = lambda x: torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda()
+    bufs = {"root_state": f(r), "dof_state": f(d), "dof_actuation": f(a), "impulse_cache": f(c),
+            "tan_root_state": f(t[0]), "tan_dof_state": f(t[1]), "tan_dof_actuation": f(t[2]),
+            "tan_impulse_cache": f(t[3]), "status": torch.zeros(s.w.n_envs, dtype=torch.int32, device="cuda")}
+    for k, v in (("root_state_out", r), ("dof_state_out", d), ("impulse_cache_out", c), ("tan_root_state_out", r),
+                 ("tan_dof_state_out", d), ("tan_impulse_cache_out", c)):
+        bufs[k] = torch.zeros(v.shape, dtype=torch.float32, device="cuda")
+    s.step_jvp(bufs)
+    torch.cuda.synchronize()
+    g = {k: v.cpu().numpy().astype(np.float64) for k, v in bufs.items()}
+    return g
+
+
+def env_slices(w):
+    ra = np.cumsum([0] + [w.env_actor_count(e) for e in range(w.n_envs)])
+    rd = np.cumsum([0] + [w.env_jdof(e) for e in range(w.n_envs)])
+    return [(slice(ra[e], ra[e + 1]), slice(rd[e], rd[e + 1]), slice(e, e + 1)) for e in range(w.n_envs)]
+
+
+def env_max(arrs, sl):
+    return max(float(np.abs(x[s]).max()) if x[s].size else 0.0 for x, s in zip(arrs, sl))
+
+
+@pytest.mark.parametrize("name,n", [("ant", 67), ("humanoid", 37), ("cartpole", 67)])
+def test_jvp_value_and_tangent_match_oracle(name, n):
+    from paper_2108_10470_gb300 import sim
+    w = {"ant": W.ant_workload, "humanoid": W.humanoid_workload, "cartpole": W.cartpole_workload}[name](n)
+    r, d, c, a = warm(w, seed=1)
+    t = direction(w, r, c, np.random.default_rng(2))
+    s = sim.Sim(w)
+    g = gpu_jvp(s, r, d, c, a, t)
+    s.destroy()
+    assert not g["status"].any()
+    ref = oracle_tangent(w, r, d, c, a, t)
+    probes = [oracle_tangent(w, r, d, c, a, t, single=True, nudge=x) for x in (None, 1, -1)]
+    val_keys = ("root_state_out", "dof_state_out", "impulse_cache_out")
+    tan_keys = ("tan_root_state_out", "tan_dof_state_out", "tan_impulse_cache_out")
+    bad_val, bad_tan, checked = [], [], 0
+    for e, sl in enumerate(env_slices(w)):
+        checked += 1
+        # value: strict bound 1e-4 relative / 1e-5 absolute plus the FP32 scale
+        vscale = max(env_max([p[i] - ref[i] for i in range(3)], sl) for p in probes)
+        vdev = max(float(np.max(np.abs(g[k][s_] - ref[i][s_]) - (1e-5 + 1e-4 * np.abs(ref[i][s_])), initial=-1))
+                   for i, (k, s_) in enumerate(zip(val_keys, sl)))
+        if vdev > K_COND * vscale:
+            bad_val.append(e)
+        tscale = max(1.0, env_max(ref[3:], sl))
+        tcond = max(env_max([p[3 + i] - ref[3 + i] for i in range(3)], sl) for p in probes)
+        tdev = max(float(np.abs(g[k][s_] - ref[3 + i][s_]).max(initial=0.0)) for i, (k, s_) in enumerate(zip(tan_keys, sl)))
+        if tdev > 1e-3 * tscale + K_COND * tcond:
+            bad_tan.append(e)
+    print(f"{name} x{n}: value outside bound in {len(bad_val)} envs, tangent outside bound in {len(bad_tan)} envs")
+    assert len(bad_val) <= 0.05 * checked, bad_val
+    assert len(bad_tan) <= 0.05 * checked, bad_tan
+
+
+@pytest.mark.parametrize("name,n", [("ant", 40), ("humanoid", 20)])
+def test_vjp_is_the_transpose_of_the_jvp(name, n):
+    """<g, J u> (tangent mode) equals <J^T g, u> (adjoint mode) per env, for random g and u."""
+    import torch
+    from paper_2108_10470_gb300 import sim
+    w = {"ant": W.ant_workload, "humanoid": W.humanoid_workload}[name](n)
+    r, d, c, a = warm(w, seed=3)
+    rng = np.random.default_rng(4)
+    u = direction(w, r, c, rng)
+    gout = (rng.standard_normal(r.shape), rng.standard_normal(d.shape), rng.standard_normal(c.shape) * (c != 0))
+    s = sim.Sim(w)
+    jv = gpu_jvp(s, r, d, c, a, u)
+    f = lambda x: torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda()
+    bufs = {"root_state": f(r), "dof_state": f(d), "dof_actuation": f(a), "impulse_cache": f(c),
+            "grad_root_state": f(gout[0]), "grad_dof_state": f(gout[1]), "grad_impulse_cache": f(gout[2]),
+            "grad_root_state_in": torch.zeros_like(f(r)), "grad_dof_state_in": torch.zeros_like(f(d)),
+            "grad_dof_actuation": torch.zeros_like(f(a)), "grad_impulse_cache_in": torch.full_like(f(c), 7.0)}
+    s.step_vjp(bufs)
+    torch.cuda.synchronize()
+    s.destroy()
+    gi = [bufs[k].cpu().numpy().astype(np.float64) for k in ("grad_root_state_in", "grad_dof_state_in",
+                                                             "grad_dof_actuation", "grad_impulse_cache_in")]
+    u32 = [x.astype(np.float32).astype(np.float64) for x in u]
+    g32 = [x.astype(np.float32).astype(np.float64) for x in gout]
+    for e, (ra, rd, rc) in enumerate(env_slices(w)):
+        lhs = float((g32[0][ra] * jv["tan_root_state_out"][ra]).sum() + (g32[1][rd] * jv["tan_dof_state_out"][rd]).sum()
+                    + (g32[2][rc] * jv["tan_impulse_cache_out"][rc]).sum())
+        rhs = float((gi[0][ra] * u32[0][ra]).sum() + (gi[1][rd] * u32[1][rd]).sum() + (gi[2][rd] * u32[2][rd]).sum()
+                    + (gi[3][rc] * u32[3][rc]).sum())
+        scale = float(np.abs(gi[0][ra]).sum() + np.abs(gi[1][rd]).sum() + np.abs(gi[2][rd]).sum() + np.abs(gi[3][rc]).sum())
+        assert abs(lhs - rhs) <= 1e-4 * max(1.0, scale), (e, lhs, rhs, scale)
+
+
+def loss_grad_gpu(w, root, dof, acts, checkpoint):
+    import torch
+    from paper_2108_10470_gb300 import autograd as AG, sim
+    s = sim.Sim(w)
+    r0 = torch.from_numpy(root.astype(np.float32)).cuda()
+    d0 = torch.from_numpy(dof.astype(np.float32)).cuda().requires_grad_(True)
+    c0 = torch.zeros((w.n_envs, s.cache_len), device="cuda")
+    A = torch.from_numpy(acts.astype(np.float32)).cuda().requires_grad_(True)
+    rf, df, cf = AG.rollout(s, r0, d0, c0, A, checkpoint=checkpoint)
+    loss = rf[:, 7].mean()  # mean final root x-velocity
+    loss.backward()
+    out = (float(loss), d0.grad.cpu().numpy().astype(np.float64), A.grad.cpu().numpy().astype(np.float64),
+           rf.detach().cpu().numpy())
+    s.destroy()
+    return out
+
+
+def loss_grad_oracle(w, root, dof, acts):
+    """d(mean final root v_x)/d(actions) and /d(initial DOF state) by forward mode: one dual rollout
+    per input direction, seeded in every env at once (envs are independent)."""
+    steps = acts.shape[0]
+    nj = w.n_dof // w.n_envs
+    g_act = np.zeros((steps, w.n_dof))
+    g_dof = np.zeros((w.n_dof, 2))
+
+    def run(seed_step, seed_j, seed_dof_comp):
+        O = oracle.Oracle(w)
+        r, d = root.astype(np.float64), dof.astype(np.float64)
+        tr, td, tc = np.zeros_like(r), np.zeros_like(d), np.zeros_like(O.cache)
+        if seed_dof_comp is not None:
+            td[seed_j::nj, seed_dof_comp] = 1.0
+        for k in range(steps):
+            da = np.zeros(w.n_dof)
+            if seed_step == k:
+                da[seed_j::nj] = 1.0
+            O.step_tangent(r, d, acts[k].astype(np.float64), tr, td, da, tc)
+        return tr[:, 7] / w.n_envs
+
+    for k in range(steps):
+        for j in range(nj):
+            g_act[k, j::nj] = run(k, j, None)
+    for j in range(nj):
+        for comp in range(2):
+            g_dof[j::nj, comp] = run(None, j, comp)
+    return g_dof, g_act
+
+
+def test_rollout_gradient_matches_oracle_and_checkpointing_is_exact():
+    """8 Ant envs, 12 steps, loss = mean final root x-velocity: gradients w.r.t. every action and
+    the initial DOF state through the autograd rollout (checkpoints of 4 steps) against the oracle's
+    forward-mode rollout; checkpoint lengths 1, 4 and 12 give bitwise equal gradients."""
+    w = W.ant_workload(8)
+    steps = 12
+    root, dof, acts = W.seeded_inputs(w, 11, steps)
+    l4, gd4, ga4, _ = loss_grad_gpu(w, root, dof, acts, 4)
+    for ck in (1, 12):
+        l, gd, ga, _ = loss_grad_gpu(w, root, dof, acts, ck)
+        assert l == l4 and np.array_equal(gd, gd4) and np.array_equal(ga, ga4)
+    od, oa = loss_grad_oracle(w, root, dof, acts)
+    nj = w.n_dof // w.n_envs
+    bad = []
+    for e in range(w.n_envs):
+        gpu = np.concatenate([gd4[e * nj:(e + 1) * nj].ravel(), ga4[:, e * nj:(e + 1) * nj].ravel()])
+        ref = np.concatenate([od[e * nj:(e + 1) * nj].ravel(), oa[:, e * nj:(e + 1) * nj].ravel()])
+        rel = np.abs(gpu - ref).max() / max(np.abs(ref).max(), 1e-12)
+        print(f"env {e}: max |grad| {np.abs(ref).max():.3e}, relative deviation {rel:.2e}")
+        if rel > 1e-2:
+            bad.append(e)
+    assert len(bad) <= 1, bad
+
+
+def test_unsupported_types_are_refused():
+    import torch
+    from paper_2108_10470_gb300 import sim
+    w = W.hand_workload(4)
+    s = sim.Sim(w)
+    z = lambda v: torch.zeros_like(v)
+    bufs = {"root_state": s.root_state, "dof_state": s.dof_state, "dof_actuation": s.dof_actuation,
+            "impulse_cache": s.impulse_cache, "grad_root_state_in": z(s.root_state), "grad_dof_state_in": z(s.dof_state),
+            "grad_dof_actuation": z(s.dof_actuation), "grad_impulse_cache_in": z(s.impulse_cache)}
+    with pytest.raises(sim.SimError) as err:
+        s.step_vjp(bufs)
+    assert err.value.code == -4
+    s.destroy()
