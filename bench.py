@@ -342,7 +342,49 @@ def run_ours(args, rank, world, local_rank):
                               f"in the timed region)"}
     line["roofline"] = roof
     line["cpu_baseline"] = cpu
+    if world == 1 and not args.no_adjoint:
+        line["adjoint"] = adjoint_measure(dev)
     print(json.dumps(line), flush=True)
+
+
+def adjoint_measure(dev, n_envs=1024, steps=64, checkpoint=16, reps=2):
+    """Adjoint throughput on the differentiable-rollout workload: 1024 Ant-like envs, 64 env-steps,
+    loss = mean final root x-velocity, gradients w.r.t. every action and the initial DOF state
+    (autograd rollout with a checkpoint every 16 steps). value = env-steps differentiated per second
+    of the backward pass (which re-runs each segment forward, then applies the step adjoints)."""
+    import torch
+
+    from paper_2108_10470_gb300 import autograd as AG, sim, workloads as W
+
+    w = W.ant_workload(n_envs)
+    s = sim.Sim(w)
+    root, dof, acts = W.seeded_inputs(w, 0, steps)
+    r0 = torch.from_numpy(root).to(dev)
+    d0 = torch.from_numpy(dof).to(dev).requires_grad_(True)
+    c0 = torch.zeros((n_envs, s.cache_len), device=dev)
+    A = torch.from_numpy(acts).to(dev).requires_grad_(True)
+    fwd, bwd = [], []
+    for rep in range(reps + 1):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record()
+        rf, _, _ = AG.rollout(s, r0, d0, c0, A, checkpoint=checkpoint)
+        loss = rf[:, 7].mean()
+        e[1].record()
+        loss.backward()
+        e[2].record()
+        torch.cuda.synchronize()
+        if rep > 0:
+            fwd.append(e[0].elapsed_time(e[1]))
+            bwd.append(e[1].elapsed_time(e[2]))
+        d0.grad = None
+        A.grad = None
+    s.destroy()
+    f_ms, b_ms = statistics.median(fwd), statistics.median(bwd)
+    return {"value": n_envs * steps / (b_ms / 1e3), "unit": "adjoint env-steps/s",
+            "workload": f"Ant-like, {n_envs} envs, {steps} env-steps, loss = mean final root x-velocity, gradients "
+                        f"w.r.t. actions and initial DOF state, checkpoint every {checkpoint} steps",
+            "forward_ms": f_ms, "backward_ms": b_ms, "backward_over_forward": b_ms / f_ms,
+            "method": "forward-mode dual kernel (one env per warp), vector-Jacobian product per env-step"}
 
 
 def main():
@@ -357,6 +399,7 @@ def main():
     ap.add_argument("--persistent", action="store_true", help="one persistent launch for all env types")
     ap.add_argument("--graph", action="store_true", help="replay each step as a captured CUDA graph")
     ap.add_argument("--autotune", action="store_true", help="autotune the launch knobs during warm-up")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint (differentiable rollout) measurement")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per step-kernel launch from an ncu capture of the same kernel")
     args = ap.parse_args()
