@@ -29,7 +29,8 @@ class _Models(ctypes.Structure):
     _fields_ = [("n_models", ctypes.c_int32), ("link_off", I32), ("shape_off", I32), ("parent", I32), ("jtype", I32),
                 ("axis", D), ("ppos", D), ("pquat", D), ("mass", D), ("com", D), ("inertia", D), ("armature", D),
                 ("damping", D), ("lo", D), ("hi", D), ("has_limit", I32), ("is_virtual", I32), ("shape_link", I32),
-                ("shape_type", I32), ("shape_size", D), ("shape_pos", D), ("shape_quat", D), ("shape_friction", D)]
+                ("shape_type", I32), ("shape_size", D), ("shape_pos", D), ("shape_quat", D), ("shape_friction", D),
+                ("drive_kp", D), ("drive_kd", D)]
 
 
 class _Params(ctypes.Structure):
@@ -68,6 +69,11 @@ def lib():
                                   ctypes.POINTER(ctypes.c_uint32), ctypes.c_int32]
         L.oracle_step.restype = ctypes.c_int32
         L.oracle_step_flops.argtypes = [ctypes.c_void_p, D, D, D, D, ctypes.c_double, ctypes.c_int32]
+        L.oracle_step_ext.argtypes = [ctypes.c_void_p, D, D, D, D, D, D, D, ctypes.c_double, ctypes.c_int32, D, D, D,
+                                      I32, I32, ctypes.POINTER(ctypes.c_uint32), ctypes.c_int32]
+        L.oracle_step_ext.restype = ctypes.c_int32
+        L.oracle_jacobian.argtypes = [ctypes.c_void_p, ctypes.c_int32, D, D, ctypes.c_int32, D]
+        L.oracle_jacobian.restype = ctypes.c_int32
         L.oracle_step_flops.restype = ctypes.c_double
         L.oracle_step_f32.argtypes = [ctypes.c_void_p, D, D, D, D, ctypes.c_double, ctypes.c_int32, D]
         L.oracle_step_tangent.argtypes = [ctypes.c_void_p, D, D, D, D, D, D, D, D, ctypes.c_double, ctypes.c_int32,
@@ -140,6 +146,8 @@ class Oracle:
                          ("shape_type", np.int32), ("shape_size", np.float64), ("shape_pos", np.float64),
                          ("shape_quat", np.float64), ("shape_friction", np.float64)):
             keep[name] = cat(name, dt)
+        keep["drive_kp"] = np.ascontiguousarray(np.concatenate([m.drive_gains()[0] for m in ms]), np.float64)
+        keep["drive_kd"] = np.ascontiguousarray(np.concatenate([m.drive_gains()[1] for m in ms]), np.float64)
         md = _Models()
         md.n_models = len(ms)
         for k, v in keep.items():
@@ -167,11 +175,16 @@ class Oracle:
 
     # -- batch step -------------------------------------------------------------------------
     def step(self, root: np.ndarray, dof: np.ndarray, act: np.ndarray, dt: Optional[float] = None,
-             substeps: Optional[int] = None, n_threads: int = 1) -> Dict[str, np.ndarray]:
+             substeps: Optional[int] = None, n_threads: int = 1, pos_target=None, vel_target=None,
+             body_force=None) -> Dict[str, np.ndarray]:
         """One env-step of every env. root (N_A,13), dof (N_D,2) and the solver impulse cache
-        self.cache (n_envs, cache_len) are updated IN PLACE (float64 arrays); act is (N_D,). Returns net contact forces (N_B,3), the last substep's contact
-        triples (n_envs, cap, 3), their counts, the per-env constraint-set signature and the number
-        of failed envs."""
+        self.cache (n_envs, cache_len) are updated IN PLACE (float64 arrays); act is (N_D,);
+        pos_target / vel_target (N_D,) are joint drive targets (0 when omitted) and body_force
+        (N_B,6) external forces and torques (world axes, at each body's COM). Returns net contact
+        forces (N_B,3), the joint forces of the last substep (N_D,), body states after the step
+        (N_B,13: link origin, quaternion, velocity of the origin, angular velocity), the last
+        substep's contact triples (n_envs, cap, 3), their counts, the per-env constraint-set
+        signature and the number of failed envs."""
         dt = self.w.dt if dt is None else dt
         substeps = self.w.substeps if substeps is None else substeps
         assert root.dtype == np.float64 and root.flags.c_contiguous and root.shape == (self.N_A, 13)
@@ -181,11 +194,26 @@ class Oracle:
         con = np.zeros((self.w.n_envs, self.contact_cap, 3), np.int32)
         nc = np.zeros(self.w.n_envs, np.int32)
         sig = np.zeros(self.w.n_envs, np.uint32)
-        bad = lib().oracle_step(self.h, _dp(root), _dp(dof) if self.N_D else None, _dp(self.cache),
-                                _dp(a) if self.N_D else None,
-                                float(dt), int(substeps), _dp(nf) if self.N_B else None, _ip(con), _ip(nc),
-                                sig.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), int(n_threads))
-        return dict(net_force=nf, contacts=con, n_contacts=nc, signature=sig, n_failed=int(bad))
+        conv = [None if x is None else np.ascontiguousarray(x, dtype=np.float64).reshape(n)
+                for x, n in ((pos_target, self.N_D), (vel_target, self.N_D), (body_force, self.N_B * 6))]
+        pt, vt, bf = [None if x is None or x.size == 0 else _dp(x) for x in conv]  # conv keeps them alive
+        df = np.zeros(self.N_D)
+        bs = np.zeros((self.N_B, 13))
+        bad = lib().oracle_step_ext(self.h, _dp(root), _dp(dof) if self.N_D else None, _dp(self.cache),
+                                    _dp(a) if self.N_D else None, pt, vt, bf, float(dt), int(substeps),
+                                    _dp(nf) if self.N_B else None, _dp(df) if self.N_D else None,
+                                    _dp(bs) if self.N_B else None, _ip(con), _ip(nc),
+                                    sig.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), int(n_threads))
+        return dict(net_force=nf, dof_force=df, body_state=bs, contacts=con, n_contacts=nc, signature=sig,
+                    n_failed=int(bad))
+
+    def jacobian(self, env, root, dof, link):
+        """World-axis Jacobian (6, env generalized DOFs) of env-local link `link`: rows [angular
+        velocity; velocity of the link origin]."""
+        root, dof = self._c(root), self._c(dof)
+        out = np.zeros((6, self.ngen(env)))
+        assert lib().oracle_jacobian(self.h, env, _dp(root), _dp(dof), link, _dp(out)) == 0
+        return out
 
     def step_flops(self, root, dof, act, dt=None, substeps=None) -> float:
         """Floating-point operations of one env-step over all envs (state advanced in place)."""

@@ -43,6 +43,7 @@ struct LinkD {
   double mass, com[3], inertia[6];
   double armature, damping, lo, hi;
   int has_limit, is_virtual;
+  double kp = 0.0, kd = 0.0;  // joint drive stiffness and damping
 };
 struct ShapeD {
   int link, type;
@@ -202,8 +203,11 @@ template <class T> bool small_inverse_spd(std::vector<T> A, int n, std::vector<T
 
 // Articulated-body algorithm (RBDA Table 7.1) with external gravity forces; tau is the model's
 // generalized force vector. Returns the generalized acceleration.
+// diag (optional): extra joint-space inertia on each 1-DOF joint's diagonal (the implicit drive
+// term); fext (optional): external spatial force on each link, in link coordinates.
 template <class T> bool aba(const ModelD& M, const ActorKin<T>& K, const std::vector<T>& tau, const Params& P,
-                            std::vector<T>& qdd) {
+                            std::vector<T>& qdd, const std::vector<T>* diag = nullptr,
+                            const std::vector<SVec<T>>* fext = nullptr) {
   const int L = (int)M.links.size();
   qdd.assign(M.n_gen, T(std::nan("")));  // stays NaN if a pivot fails (the env is reported failed)
   std::vector<SMat<T>> IA(L);
@@ -211,6 +215,7 @@ template <class T> bool aba(const ModelD& M, const ActorKin<T>& K, const std::ve
   for (int i = 0; i < L; ++i) {
     IA[i] = K.I[i];
     pA[i] = ssub(smul(crf(K.v[i]), smul(K.I[i], K.v[i])), gravity_force(K, i, P));
+    if (fext) pA[i] = ssub(pA[i], (*fext)[i]);
   }
   std::vector<std::vector<SVec<T>>> U(L);
   std::vector<std::vector<T>> Dinv(L), u(L);
@@ -225,6 +230,7 @@ template <class T> bool aba(const ModelD& M, const ActorKin<T>& K, const std::ve
       u[i][a] = tau[M.goff[i] + a] - sdot(K.S[i][a], pA[i]);
     }
     if (nd == 1) D[0] = D[0] + T(M.links[i].armature);
+    if (nd == 1 && diag) D[0] = D[0] + (*diag)[M.goff[i]];
     if (!small_inverse_spd(D, nd, Dinv[i])) return false;
     const int par = M.links[i].parent;
     if (par < 0) continue;
@@ -266,7 +272,7 @@ template <class T> bool aba(const ModelD& M, const ActorKin<T>& K, const std::ve
 }
 
 // Composite-rigid-body algorithm (RBDA Table 6.2), armature added on the joint diagonal.
-template <class T> void crba(const ModelD& M, const ActorKin<T>& K, std::vector<T>& H) {
+template <class T> void crba(const ModelD& M, const ActorKin<T>& K, std::vector<T>& H, const std::vector<T>* diag = nullptr) {
   const int L = (int)M.links.size(), n = M.n_gen;
   H.assign(n * n, T(0.0));
   std::vector<SMat<T>> Ic(K.I);
@@ -292,6 +298,7 @@ template <class T> void crba(const ModelD& M, const ActorKin<T>& K, std::vector<
       }
     }
     if (nd == 1) H[M.goff[i] * n + M.goff[i]] = H[M.goff[i] * n + M.goff[i]] + T(M.links[i].armature);
+    if (nd == 1 && diag) H[M.goff[i] * n + M.goff[i]] = H[M.goff[i] * n + M.goff[i]] + (*diag)[M.goff[i]];
   }
 }
 
@@ -733,13 +740,22 @@ template <class T> void store_env(const Oracle& O, int env, const std::vector<Ac
 template <class T> struct StepOut {
   std::vector<Vec3<T>> impulse;  // per env link (actor-major), sum of lambda * k over substeps
   std::vector<ContactPt<T>> last_contacts;
+  std::vector<T> dof_force;      // per env joint DOF: joint force of the last substep
   uint32_t sig = 2166136261u;
   bool ok = true;
 };
 
+// Per-step controls beyond the actuation (env-local arrays, null when absent): joint drive targets
+// per joint DOF, and an external force and torque (world axes, at the body's COM) per body.
+struct Controls {
+  const double* pos_target = nullptr;
+  const double* vel_target = nullptr;
+  const double* body_force = nullptr;  // [env bodies * 6]: force (3), torque (3)
+};
+
 // One substep of one env (steps a1-a7 of the method).
 template <class T> void env_substep(const Oracle& O, int env, std::vector<ActorState<T>>& st, const T* act,
-                                    const T& h, std::vector<T>& cache, StepOut<T>& out) {
+                                    const T& h, std::vector<T>& cache, StepOut<T>& out, const Controls& ctl = {}) {
   const Params& P = O.prm;
   const EnvLayout E = env_layout(O, env);
   const int n = E.n_gen, A = O.n_act(env);
@@ -747,25 +763,53 @@ template <class T> void env_substep(const Oracle& O, int env, std::vector<ActorS
   std::vector<ActorKin<T>> K(A);
   std::vector<T> nu(n, T(0.0)), vfree(n, T(0.0));
   std::vector<T> Mfull(n * n, T(0.0));
-  int jbase = 0;
+  int jbase = 0, bbase = 0;
   for (int a = 0; a < A; ++a) {
     const ModelD& M = O.actor_model(env, a);
     const std::vector<T> gv = gen_velocity(M, st[a]);
     kinematics(M, st[a], gv, K[a]);
-    std::vector<T> tau(M.n_gen, T(0.0));
+    // joint forces of the substep: actuation, damping at the substep-start velocity, and the
+    // implicit drive kp (q* - q - h qd) + kd (qd* - qd), whose h (h kp + kd) joins the joint's
+    // diagonal of the joint-space inertia (implicit Euler of the spring-damper)
+    std::vector<T> tau(M.n_gen, T(0.0)), diag(M.n_gen, T(0.0));
     for (size_t l = 0; l < M.links.size(); ++l)
       if (M.jdof[l] >= 0) {
         const int j = M.jdof[l];
-        tau[M.goff[l]] = act[jbase + j] - T(M.links[l].damping) * st[a].qd[j];
+        const LinkD& lk = M.links[l];
+        T f = act[jbase + j] - T(lk.damping) * st[a].qd[j];
+        if (lk.kp != 0.0 || lk.kd != 0.0) {
+          const T qt = ctl.pos_target ? T(ctl.pos_target[jbase + j]) : T(0.0);
+          const T vt = ctl.vel_target ? T(ctl.vel_target[jbase + j]) : T(0.0);
+          f = f + T(lk.kp) * (qt - st[a].q[j] - h * st[a].qd[j]) + T(lk.kd) * (vt - st[a].qd[j]);
+          diag[M.goff[l]] = h * (h * T(lk.kp) + T(lk.kd));
+        }
+        tau[M.goff[l]] = f;
+        if (out.dof_force.size() > (size_t)(jbase + j)) out.dof_force[jbase + j] = f;
       }
+    // external force and torque per body (world axes, at the COM) as link-coordinate spatial forces
+    std::vector<SVec<T>> fext;
+    if (ctl.body_force) {
+      fext.assign(M.links.size(), szero<T>());
+      int b = bbase;
+      for (size_t l = 0; l < M.links.size(); ++l) {
+        if (M.links[l].is_virtual) continue;
+        const double* bf = ctl.body_force + (int64_t)b * 6;
+        ++b;
+        const Mat3<T> Rt = transpose(K[a].R[l]);
+        const Vec3<T> F = mul(Rt, mk3<T>(T(bf[0]), T(bf[1]), T(bf[2])));
+        const Vec3<T> Tq = mul(Rt, mk3<T>(T(bf[3]), T(bf[4]), T(bf[5])));
+        fext[l] = smk<T>(add(Tq, cross(vec3_of<T>(M.links[l].com), F)), F);
+      }
+    }
+    bbase += M.n_body;
     std::vector<T> qdd;
-    if (!aba(M, K[a], tau, P, qdd)) out.ok = false;
+    if (!aba(M, K[a], tau, P, qdd, &diag, ctl.body_force ? &fext : nullptr)) out.ok = false;
     if (M.free_root) {  // rate of the root-origin velocity: a_lin + omega x v
       const Vec3<T> wxv = cross(st[a].w, st[a].v);
       for (int k = 0; k < 3; ++k) qdd[3 + k] = qdd[3 + k] + wxv[k];
     }
     std::vector<T> H;
-    crba(M, K[a], H);
+    crba(M, K[a], H, &diag);
     for (int i = 0; i < M.n_gen; ++i) {
       nu[E.gen_off[a] + i] = gv[i];
       vfree[E.gen_off[a] + i] = gv[i] + h * (i < (int)qdd.size() ? qdd[i] : T(0.0));
@@ -894,7 +938,34 @@ template <class T> struct Outputs {
   int32_t* n_contacts; // [n_envs] or null
   uint32_t* sig;       // [n_envs] or null
   int32_t* status;     // [n_envs] or null
+  const double* pos_target = nullptr;  // [N_D] drive position targets or null (0)
+  const double* vel_target = nullptr;  // [N_D] drive velocity targets or null (0)
+  const double* body_force = nullptr;  // [N_B * 6] external force, torque per body or null
+  double* dof_force = nullptr;         // [N_D] out: joint force of the last substep, or null
+  double* body_state = nullptr;        // [N_B * 13] out: body poses and velocities after the step, or null
 };
+
+// Unit quaternion (x, y, z, w), w >= 0, of a rotation matrix (Shepperd's method: the largest of
+// 4w^2, 4x^2, 4y^2, 4z^2 picks the square root taken).
+inline void mat_to_quat(const Mat3<double>& R, double q[4]) {
+  const double tr = R(0, 0) + R(1, 1) + R(2, 2);
+  double x, y, z, w;
+  if (tr > 0.0) {
+    const double s = std::sqrt(tr + 1.0) * 2.0;
+    w = 0.25 * s; x = (R(2, 1) - R(1, 2)) / s; y = (R(0, 2) - R(2, 0)) / s; z = (R(1, 0) - R(0, 1)) / s;
+  } else if (R(0, 0) > R(1, 1) && R(0, 0) > R(2, 2)) {
+    const double s = std::sqrt(1.0 + R(0, 0) - R(1, 1) - R(2, 2)) * 2.0;
+    w = (R(2, 1) - R(1, 2)) / s; x = 0.25 * s; y = (R(0, 1) + R(1, 0)) / s; z = (R(0, 2) + R(2, 0)) / s;
+  } else if (R(1, 1) > R(2, 2)) {
+    const double s = std::sqrt(1.0 + R(1, 1) - R(0, 0) - R(2, 2)) * 2.0;
+    w = (R(0, 2) - R(2, 0)) / s; x = (R(0, 1) + R(1, 0)) / s; y = 0.25 * s; z = (R(1, 2) + R(2, 1)) / s;
+  } else {
+    const double s = std::sqrt(1.0 + R(2, 2) - R(0, 0) - R(1, 1)) * 2.0;
+    w = (R(1, 0) - R(0, 1)) / s; x = (R(0, 2) + R(2, 0)) / s; y = (R(1, 2) + R(2, 1)) / s; z = 0.25 * s;
+  }
+  const double sg = (w < 0.0) ? -1.0 : 1.0;
+  q[0] = sg * x; q[1] = sg * y; q[2] = sg * z; q[3] = sg * w;
+}
 
 template <class T> int env_step(const Oracle& O, int env, double* root, double* dof, const double* act, double dt,
                                 int substeps, const Outputs<T>& o) {
@@ -910,7 +981,43 @@ template <class T> int env_step(const Oracle& O, int env, double* root, double* 
   std::vector<T> cache(O.cache_len), actv(O.jdof_off[env + 1] - O.jdof_off[env]);
   for (int i = 0; i < O.cache_len; ++i) cache[i] = T(cache_env[i]);
   for (size_t j = 0; j < actv.size(); ++j) actv[j] = T(act_env[j]);
-  for (int s = 0; s < substeps; ++s) env_substep(O, env, st, actv.data(), h, cache, out);
+  Controls ctl;
+  if (o.pos_target) ctl.pos_target = o.pos_target + O.jdof_off[env];
+  if (o.vel_target) ctl.vel_target = o.vel_target + O.jdof_off[env];
+  if (o.body_force) ctl.body_force = o.body_force + O.body_off[env] * 6;
+  if (o.dof_force) out.dof_force.assign(actv.size(), T(0.0));
+  for (int s = 0; s < substeps; ++s) env_substep(O, env, st, actv.data(), h, cache, out, ctl);
+  if (o.dof_force)
+    for (size_t j = 0; j < actv.size(); ++j) o.dof_force[O.jdof_off[env] + j] = val(out.dof_force[j]);
+  if (o.body_state) {
+    // poses and velocities of the env's bodies after the step: link origin, link rotation, world
+    // angular velocity and the velocity of the link origin
+    int64_t b = O.body_off[env];
+    for (int a = 0; a < O.n_act(env); ++a) {
+      const ModelD& M = O.actor_model(env, a);
+      const std::vector<T> gv = gen_velocity(M, st[a]);
+      ActorKin<T> K;
+      kinematics(M, st[a], gv, K);
+      for (size_t l = 0; l < M.links.size(); ++l) {
+        if (M.links[l].is_virtual) continue;
+        double* bs = o.body_state + b * 13;
+        ++b;
+        Mat3<double> R;
+        for (int i = 0; i < 3; ++i)
+          for (int j = 0; j < 3; ++j) R(i, j) = val(K.R[l](i, j));
+        double q[4];
+        mat_to_quat(R, q);
+        for (int k = 0; k < 3; ++k) bs[k] = val(K.p[l][k]);
+        for (int k = 0; k < 4; ++k) bs[3 + k] = q[k];
+        for (int i = 0; i < 3; ++i) {
+          double wv = 0.0, vv = 0.0;
+          for (int j = 0; j < 3; ++j) { wv += R(i, j) * val(K.v[l][j]); vv += R(i, j) * val(K.v[l][3 + j]); }
+          bs[7 + i] = vv;
+          bs[10 + i] = wv;
+        }
+      }
+    }
+  }
   for (int i = 0; i < O.cache_len; ++i) cache_env[i] = val(cache[i]);
   store_env(O, env, st, root, dof);
   if (o.net_force) {
@@ -1075,6 +1182,8 @@ struct OracleModels {
   const double* shape_pos;
   const double* shape_quat;
   const double* shape_friction;
+  const double* drive_kp;  // [links] or null (no drives)
+  const double* drive_kd;  // [links] or null
 };
 struct OracleParams {
   double gravity[3];
@@ -1101,6 +1210,8 @@ void* oracle_create(const OracleModels* md, const int32_t* env_actor_model, int3
       L.hi = md->hi[i];
       L.has_limit = md->has_limit[i];
       L.is_virtual = md->is_virtual[i];
+      L.kp = md->drive_kp ? md->drive_kp[i] : 0.0;
+      L.kd = md->drive_kd ? md->drive_kd[i] : 0.0;
       M.links.push_back(L);
     }
     for (int s = md->shape_off[m]; s < md->shape_off[m + 1]; ++s) {
@@ -1203,6 +1314,32 @@ int32_t oracle_step(void* h, double* root, double* dof, double* cache, const dou
                     double* net_force, int32_t* contacts, int32_t* n_contacts, uint32_t* sig, int32_t n_threads) {
   const Oracle* O = (const Oracle*)h;
   Outputs<double> o{cache, net_force, contacts, n_contacts, sig, nullptr};
+  std::atomic<int> bad{0};
+  if (n_threads < 1) n_threads = 1;
+  auto work = [&](int t) {
+    for (int e = t; e < O->n_envs; e += n_threads)
+      if (env_step<double>(*O, e, root, dof, act, dt, substeps, o)) bad++;
+  };
+  if (n_threads == 1) work(0);
+  else {
+    std::vector<std::thread> th;
+    for (int t = 0; t < n_threads; ++t) th.emplace_back(work, t);
+    for (auto& x : th) x.join();
+  }
+  return bad.load();
+}
+
+// The step with the per-step controls and outputs beyond oracle_step: drive targets (N_D each, or
+// null = 0), external body forces and torques (N_B x 6, world axes at the COM, or null), the joint
+// force of the last substep (N_D, or null) and body states after the step (N_B x 13, or null).
+int32_t oracle_step_ext(void* h, double* root, double* dof, double* cache, const double* act, const double* pos_target,
+                        const double* vel_target, const double* body_force, double dt, int32_t substeps,
+                        double* net_force, double* dof_force, double* body_state, int32_t* contacts,
+                        int32_t* n_contacts, uint32_t* sig, int32_t n_threads) {
+  const Oracle* O = (const Oracle*)h;
+  Outputs<double> o{cache, net_force, contacts, n_contacts, sig, nullptr};
+  o.pos_target = pos_target; o.vel_target = vel_target; o.body_force = body_force;
+  o.dof_force = dof_force; o.body_state = body_state;
   std::atomic<int> bad{0};
   if (n_threads < 1) n_threads = 1;
   auto work = [&](int t) {
@@ -1450,6 +1587,42 @@ int32_t oracle_link_pose(void* h, int32_t env, const double* root, const double*
     l -= L;
   }
   return 1;
+}
+
+// World-axis Jacobian of env-local link `link` (6 x the env's generalized DOFs, row-major; env-local
+// root and DOF arrays as for oracle_link_pose): rows [angular velocity; velocity of the link
+// origin] as a linear map of the env's generalized velocity. Column g is the link's velocity for a
+// unit generalized velocity g, by the same outward recursion as the state's velocities.
+int32_t oracle_jacobian(void* h, int32_t env, const double* root, const double* dof, int32_t link, double* out) {
+  const Oracle& O = *(const Oracle*)h;
+  std::vector<ActorState<double>> st; std::vector<ActorKin<double>> K; std::vector<std::vector<double>> gv;
+  env_kin(O, env, root, dof, st, K, gv);
+  const EnvLayout E = env_layout(O, env);
+  const int n = E.n_gen;
+  for (int i = 0; i < 6 * n; ++i) out[i] = 0.0;
+  int l = link;
+  for (int a = 0; a < O.n_act(env); ++a) {
+    const ModelD& M = O.actor_model(env, a);
+    const int L = (int)M.links.size();
+    if (l >= L) { l -= L; continue; }
+    for (int g = 0; g < M.n_gen; ++g) {
+      std::vector<SVec<double>> v(L);
+      for (int i = 0; i < L; ++i) {
+        SVec<double> vJ = szero<double>();
+        for (size_t k = 0; k < K[a].S[i].size(); ++k)
+          if (M.goff[i] + (int)k == g) vJ = sadd(vJ, K[a].S[i][k]);
+        v[i] = (i == 0) ? vJ : sadd(smul(K[a].Xup[i], v[M.links[i].parent]), vJ);
+      }
+      for (int r = 0; r < 3; ++r) {
+        double wv = 0.0, vv = 0.0;
+        for (int c = 0; c < 3; ++c) { wv += K[a].R[l](r, c) * v[l][c]; vv += K[a].R[l](r, c) * v[l][3 + c]; }
+        out[r * n + E.gen_off[a] + g] = wv;
+        out[(3 + r) * n + E.gen_off[a] + g] = vv;
+      }
+    }
+    return 0;
+  }
+  return -1;
 }
 
 // Constraint rows of one env at the given configuration (no solve). Returns the row count R (or

@@ -58,6 +58,15 @@ class Model:
     gear: np.ndarray          # per joint DOF (action scale of the workload, not physics)
     root_pos: np.ndarray      # nominal root position of the initial state
     dof_noise: float = 0.0    # half-width of the uniform initial joint-position noise
+    drive_kp: Optional[np.ndarray] = None  # per link: joint drive stiffness (None: no drives)
+    drive_kd: Optional[np.ndarray] = None  # per link: joint drive damping
+
+    def drive_gains(self):
+        """(kp, kd) per link, zeros where no drive is set."""
+        z = np.zeros(self.n_links)
+        kp = z if self.drive_kp is None else np.asarray(self.drive_kp, np.float64)
+        kd = z if self.drive_kd is None else np.asarray(self.drive_kd, np.float64)
+        return kp, kd
 
     @property
     def n_links(self) -> int:
@@ -99,11 +108,13 @@ class _Builder:
         self.gear: List[float] = []
 
     def link(self, parent, jtype, *, axis=(0, 0, 1), ppos=(0, 0, 0), pquat=IDENT_Q, mass=0.0, com=(0, 0, 0),
-             inertia=(0, 0, 0, 0, 0, 0), armature=0.0, damping=0.0, limit=None, virtual=False, gear=1.0) -> int:
+             inertia=(0, 0, 0, 0, 0, 0), armature=0.0, damping=0.0, limit=None, virtual=False, gear=1.0,
+             drive=(0.0, 0.0)) -> int:
         lo, hi = (limit if limit is not None else (0.0, 0.0))
         self.links.append(dict(parent=parent, jtype=jtype, axis=axis, ppos=ppos, pquat=pquat, mass=mass, com=com,
                                inertia=inertia, armature=armature, damping=damping, lo=lo, hi=hi,
-                               has_limit=int(limit is not None), is_virtual=int(virtual)))
+                               has_limit=int(limit is not None), is_virtual=int(virtual), kp=float(drive[0]),
+                               kd=float(drive[1])))
         if jtype in (JOINT_REVOLUTE, JOINT_PRISMATIC):
             self.gear.append(gear)
         return len(self.links) - 1
@@ -138,7 +149,9 @@ class _Builder:
             shape_friction=sf("friction") if S else np.zeros((0,)),
             gear=np.array(self.gear, dtype=np.float64),
             root_pos=np.array(root_pos, dtype=np.float64),
-            dof_noise=float(dof_noise))
+            dof_noise=float(dof_noise),
+            drive_kp=f("kp") if any(l["kp"] for l in L) else None,
+            drive_kd=f("kd") if any(l["kd"] for l in L) else None)
 
 
 # ------------------------------------------------------------------------------------------------
