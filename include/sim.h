@@ -81,15 +81,26 @@ typedef struct {
   const float* shape_pos;     /* [S*3]                                                      */
   const float* shape_quat;    /* [S*4]                                                      */
   const float* shape_friction;/* [S]   >= 0                                                 */
+  const float* drive_stiffness; /* [L] >= 0 joint drive stiffness kp, or NULL (no drives)   */
+  const float* drive_damping;   /* [L] >= 0 joint drive damping kd, or NULL                  */
 } sim_model_desc;
+/* Joint drives (paper: DOF position / velocity targets with drive stiffness and damping): each
+ * substep a driven joint gets the force kp (q* - q - h qd) + kd (qd* - qd) with h (h kp + kd)
+ * added to its joint-space inertia diagonal, i.e. the spring-damper integrated implicitly over the
+ * substep (stable for stiff gains); q*, qd* come from the DOF_POSITION_TARGET / _VELOCITY_TARGET
+ * views. */
 
 /* Solver parameters (paper's simulation-parameter table: gravity, position / velocity iteration
  * counts, max bias, friction; contact offset and limit margin are this library's constants).
  * flags: bit 0 (SIM_FLAG_SIGNATURE) records the per-env constraint-set signature each step;
  * bit 1 (SIM_FLAG_PERSISTENT) runs every env type of a step in one persistent launch instead of
  * one launch per env type; bit 2 (SIM_FLAG_GRAPH) makes sim_step capture its launches into a CUDA
- * graph on first use (again whenever dt or substeps change, or the plan changes) and replay it. */
-enum { SIM_FLAG_SIGNATURE = 1, SIM_FLAG_PERSISTENT = 2, SIM_FLAG_GRAPH = 4 };
+ * graph on first use (again whenever dt or substeps change, or the plan changes) and replay it;
+ * bit 3 (SIM_FLAG_BODY_FORCES) applies the RIGID_BODY_FORCE view every substep; bit 4
+ * (SIM_FLAG_RIGID_BODY_STATE) writes the RIGID_BODY_STATE view after every step; bit 5
+ * (SIM_FLAG_DOF_FORCE) writes the DOF_FORCE view every step. */
+enum { SIM_FLAG_SIGNATURE = 1, SIM_FLAG_PERSISTENT = 2, SIM_FLAG_GRAPH = 4, SIM_FLAG_BODY_FORCES = 8,
+       SIM_FLAG_RIGID_BODY_STATE = 16, SIM_FLAG_DOF_FORCE = 32 };
 typedef struct {
   float gravity[3];
   int32_t pos_iters;       /* >= 1 biased (position) iterations                  */
@@ -117,7 +128,12 @@ enum {
   SIM_VIEW_CONTACT_COUNT = 5,     /* (n_envs,) i32 number of valid rows in CONTACT_PAIRS                                     */
   SIM_VIEW_SIGNATURE = 6,         /* (n_envs,) u32 FNV-1a of the step's constraint sets (SIM_FLAG_SIGNATURE)                */
   SIM_VIEW_STATUS = 7,            /* (n_envs,) i32 per-env status bits: 1 non-finite state, 2 solver pivot failure           */
-  SIM_VIEW_IMPULSE_CACHE = 8      /* (n_envs, K) f32 warm-start impulses (solver state carried between substeps and steps)   */
+  SIM_VIEW_IMPULSE_CACHE = 8,     /* (n_envs, K) f32 warm-start impulses (solver state carried between substeps and steps)   */
+  SIM_VIEW_DOF_POSITION_TARGET = 9,  /* (N_D,) f32 drive position targets q*. Set                                      */
+  SIM_VIEW_DOF_VELOCITY_TARGET = 10, /* (N_D,) f32 drive velocity targets qd*. Set                                     */
+  SIM_VIEW_DOF_FORCE = 11,        /* (N_D,) f32 joint force of the last substep: actuation - damping qd + drive (SIM_FLAG_DOF_FORCE). Get */
+  SIM_VIEW_RIGID_BODY_STATE = 12, /* (N_B, 13) f32 per body after the step: link origin 3 | quat xyzw (w >= 0) 4 | origin velocity 3 | omega 3, world (SIM_FLAG_RIGID_BODY_STATE). Get */
+  SIM_VIEW_RIGID_BODY_FORCE = 13  /* (N_B, 6) f32 per body: force 3 | torque 3, world axes, applied at the body's COM every substep (SIM_FLAG_BODY_FORCES). Set */
 };
 enum { SIM_DTYPE_F32 = 0, SIM_DTYPE_I32 = 1, SIM_DTYPE_U32 = 2 };
 typedef struct {
@@ -289,6 +305,23 @@ typedef struct {
 /* Jacobian-vector product of one env-step: the output state and its tangent along the given input
  * tangent. Same conventions and errors as sim_step_vjp. */
 int sim_step_jvp(sim_handle h, const sim_jvp_buffers* b, float dt, int32_t substeps);
+
+/* Largest generalized-DOF count (n_max) and link count (L_max) over the env types (the padded
+ * sizes of the mass-matrix and Jacobian outputs). Errors: HANDLE, INVALID_ARG. */
+int sim_get_max_dims(sim_handle h, int32_t* n_max, int32_t* l_max);
+
+/* Joint-space inertia of every env at the current state (paper: mass matrices per actor group):
+ * out (device, n_envs x n_max x n_max f32, row-major per env; entries past the env's generalized
+ * DOFs are 0) receives M, armature included, for the generalized velocity [omega; p_dot] of each
+ * floating root (world axes) followed by the joint rates, actors in order. Asynchronous on the
+ * handle's stream. Errors: HANDLE, INVALID_ARG, CUDA. */
+int sim_compute_mass_matrix(sim_handle h, float* out);
+
+/* World-axis Jacobians of every link of every env at the current state (paper: Jacobian tensors):
+ * out (device, n_envs x L_max x 6 x n_max f32) row r of link l maps the env's generalized velocity
+ * to [angular velocity; velocity of the link origin] (rows past 6, links past the env's, columns
+ * past its DOFs are 0). Asynchronous. Errors: HANDLE, INVALID_ARG, CUDA. */
+int sim_compute_jacobian(sim_handle h, float* out);
 
 /* Describe one of the SIM_VIEW_* device tensors. Errors: HANDLE, INVALID_ARG. */
 int sim_get_view(sim_handle h, int32_t which, sim_view* out);

@@ -156,6 +156,71 @@ __global__ void __launch_bounds__(64) tangent_step_kernel(const __grid_constant_
 
 }  // namespace
 
+namespace {
+
+// Mass matrices (what = 0) or link Jacobians (what = 1) at the current state, one thread per env.
+__global__ void __launch_bounds__(64) query_kernel(const __grid_constant__ StepArgs A,
+                                                   const __grid_constant__ TypeArgs TA, float* out, int what,
+                                                   int n_max, int l_max) {
+  const int grp = blockIdx.x * blockDim.x + threadIdx.x;
+  if (grp >= TA.n_launch_envs) return;
+  const int env = TA.env_ids ? TA.env_ids[grp] : TA.env_first + grp;
+  const EnvTypeTable* T = TA.type;
+  const int na = T->n_actors, nj = T->n_jdof, n = T->n_gen, L = T->n_links;
+  const int abase = A.env_actor_base[env], dbase = A.env_dof_base[env];
+  TanState<1> s;
+  TanWork<1> w;
+  unsigned free_mask = 0u;
+  for (int l = 0; l < L; ++l)
+    if (T->parent[l] < 0 && T->jtype[l] == kFree) free_mask |= 1u << T->actor[l];
+  for (int a = 0; a < na; ++a) {
+    const float* r = A.root + (size_t)(abase + a) * 13;
+    const bool fr = (free_mask >> a) & 1u;
+    for (int k = 0; k < 3; ++k) {
+      s.rp[a][k] = Dn<1>(r[k]);
+      s.rv[a][k] = Dn<1>(fr ? r[7 + k] : 0.f);
+      s.rw[a][k] = Dn<1>(fr ? r[10 + k] : 0.f);
+    }
+    for (int k = 0; k < 4; ++k) s.rq[a][k] = Dn<1>(r[3 + k]);
+  }
+  for (int j = 0; j < nj; ++j) {
+    s.q[j] = Dn<1>(A.dof[(size_t)(dbase + j) * 2]);
+    s.qd[j] = Dn<1>(A.dof[(size_t)(dbase + j) * 2 + 1]);
+    s.act[j] = Dn<1>(0.f);
+  }
+  tangent_dynamics<1>(A, T, s, w);
+  if (what == 0) {
+    float* o = out + (size_t)env * n_max * n_max;
+    for (int i = 0; i < n_max; ++i)
+      for (int j = 0; j < n_max; ++j)
+        o[i * n_max + j] = (i < n && j < n) ? (i >= j ? w.L[tri(i, j)].v : w.L[tri(j, i)].v) : 0.f;
+  } else {
+    float* o = out + (size_t)env * l_max * 6 * n_max;
+    for (int l = 0; l < l_max; ++l)
+      for (int g = 0; g < n_max; ++g) {
+        float col[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (l < L && g < n && ((T->anc[l] >> g) & 1u)) {
+          // [S_ang; S_lin + S_ang x P]: the motion subspace moved from the actor origin to the link origin
+          const float sw0 = w.S[g][0].v, sw1 = w.S[g][1].v, sw2 = w.S[g][2].v;
+          const float p0 = w.P[l][0].v, p1 = w.P[l][1].v, p2 = w.P[l][2].v;
+          col[0] = sw0; col[1] = sw1; col[2] = sw2;
+          col[3] = w.S[g][3].v + sw1 * p2 - sw2 * p1;
+          col[4] = w.S[g][4].v + sw2 * p0 - sw0 * p2;
+          col[5] = w.S[g][5].v + sw0 * p1 - sw1 * p0;
+        }
+        for (int r = 0; r < 6; ++r) o[((size_t)l * 6 + r) * n_max + g] = col[r];
+      }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_query_kernel(int what, const StepArgs& a, const TypeArgs& ta, float* out, int n_max, int l_max,
+                                cudaStream_t st) {
+  query_kernel<<<(ta.n_launch_envs + 63) / 64, 64, 0, st>>>(a, ta, out, what, n_max, l_max);
+  return cudaGetLastError();
+}
+
 int tangent_lanes_per_dir(int n_dirs) {
   if (n_dirs <= 32) return 1;
   if (n_dirs <= 64) return 2;

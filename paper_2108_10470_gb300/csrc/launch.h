@@ -37,5 +37,9 @@ cudaError_t persistent_kernel_occupancy(int* ctas_per_sm, size_t smem);
 // Derivative of the step (kernels_adjoint.cu): K tangents per lane (1, 2, 4 or 8), one env per warp.
 cudaError_t launch_tangent_kernel(int K, const StepArgs& a, const TypeArgs& ta, const TangentArgs& v, cudaStream_t st);
 int tangent_lanes_per_dir(int n_dirs);
+// Mass matrices (what = 0, n_envs x n_max x n_max) or link Jacobians (what = 1, n_envs x l_max x 6 x
+// n_max) of the envs of one type at the current state, one thread per env.
+cudaError_t launch_query_kernel(int what, const StepArgs& a, const TypeArgs& ta, float* out, int n_max, int l_max,
+                                cudaStream_t st);
 
 }  // namespace artsim

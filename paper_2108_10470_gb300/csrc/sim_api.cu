@@ -66,6 +66,11 @@ struct sim_s {
   int* n_pairs = nullptr;
   unsigned* sig = nullptr;
   int* status = nullptr;
+  float* pos_target = nullptr;   // (N_D,) drive targets
+  float* vel_target = nullptr;
+  float* dof_force = nullptr;    // (N_D,) out
+  float* body_state = nullptr;   // (N_B, 13) out
+  float* body_force = nullptr;   // (N_B, 6) external force, torque
   // persistent heterogeneous launch (SIM_FLAG_PERSISTENT)
   bool persistent = false;
   int p_grid = 0, p_warps = 0, p_warp_words = 0;
@@ -162,6 +167,8 @@ int validate_model(const sim_model_desc& m) {
         return SIM_ERR_INVALID_ARG;
     }
     if (m.has_limit[i] > 1 || m.is_virtual[i] > 1) return SIM_ERR_INVALID_ARG;
+    if (m.drive_stiffness && !(m.drive_stiffness[i] >= 0.f && finite(m.drive_stiffness[i]))) return SIM_ERR_INVALID_ARG;
+    if (m.drive_damping && !(m.drive_damping[i] >= 0.f && finite(m.drive_damping[i]))) return SIM_ERR_INVALID_ARG;
   }
   for (int s = 0; s < m.n_shapes; ++s) {
     const int li = m.shape_link[s];
@@ -236,6 +243,9 @@ int build_type(const sim_model_desc* models, const std::vector<int>& actor_model
       T.armature[l] = m.armature[i];
       T.damping[l] = m.damping[i];
       T.has_limit[l] = (nd == 1 && m.has_limit[i]) ? 1 : 0;
+      T.drive_kp[l] = (nd == 1 && i > 0 && m.drive_stiffness) ? m.drive_stiffness[i] : 0.f;
+      T.drive_kd[l] = (nd == 1 && i > 0 && m.drive_damping) ? m.drive_damping[i] : 0.f;
+      if (T.drive_kp[l] != 0.f || T.drive_kd[l] != 0.f) T.has_drives = 1;
       T.lo[l] = m.limit_lo[i];
       T.hi[l] = m.limit_hi[i];
       // both rows of a joint can be active only if its range is below twice the margin; the
@@ -476,6 +486,15 @@ int plan_persistent(sim_s* h) {
 
 // The derivative kernel covers env types with ground contacts only and a bounded impulse cache.
 int tangent_supported(const sim_s* h) {
+  if (h->params.flags & SIM_FLAG_BODY_FORCES) {
+    g_last_error = "step derivative: external body forces are not part of the differentiated step";
+    return SIM_ERR_CAPACITY;
+  }
+  for (const TypePlan& tp : h->types)
+    if (tp.tab.has_drives) {
+      g_last_error = "step derivative: joint drives are not part of the differentiated step";
+      return SIM_ERR_CAPACITY;
+    }
   for (const TypePlan& tp : h->types)
     if (tp.tab.n_pairs > 0 || tp.tab.cache_len > 384) {
       g_last_error = "step derivative: env types with capsule-box pairs or more than 384 impulse-cache entries "
@@ -496,6 +515,8 @@ void fill_common(const sim_s* h, float dt, int substeps, StepArgs& a) {
   a.root = h->root; a.dof = h->dof; a.act = h->act; a.net_force = h->net_force; a.cache = h->cache;
   a.pairs = h->pairs; a.n_pairs = h->n_pairs; a.sig = h->sig; a.status = h->status;
   a.env_dof_base = h->d_dof_base; a.env_body_base = h->d_body_base; a.env_actor_base = h->d_actor_base;
+  a.pos_target = h->pos_target; a.vel_target = h->vel_target; a.body_force = h->body_force;
+  a.dof_force = h->dof_force; a.body_state = h->body_state;
   a.cache_stride = h->cache_stride; a.pair_stride = h->pair_stride;
   a.dt = dt; a.h = dt / (float)substeps; a.substeps = substeps;
   a.gx = p.gravity[0]; a.gy = p.gravity[1]; a.gz = p.gravity[2];
@@ -577,7 +598,8 @@ int capture_step(sim_s* h, float dt, int substeps) {
 
 void free_all(sim_s* h) {
   void* ptrs[] = {h->d_types, h->d_env_ids, h->d_dof_base, h->d_body_base, h->d_actor_base, h->d_actor_env,
-                  h->root, h->dof, h->act, h->net_force, h->cache, h->pairs, h->n_pairs, h->sig, h->status};
+                  h->root, h->dof, h->act, h->net_force, h->cache, h->pairs, h->n_pairs, h->sig, h->status,
+                  h->pos_target, h->vel_target, h->dof_force, h->body_state, h->body_force};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& tp : h->types) {
@@ -828,6 +850,19 @@ int sim_create(const sim_model_desc* models, int32_t n_models, const int32_t* en
   CKC(cudaMalloc(&h->n_pairs, sizeof(int) * n_envs));
   CKC(cudaMalloc(&h->sig, sizeof(unsigned) * n_envs));
   CKC(cudaMalloc(&h->status, sizeof(int) * n_envs));
+  {
+    const size_t nd = (size_t)std::max<int64_t>(h->N_D, 1), nb = (size_t)std::max<int64_t>(h->N_B, 1);
+    CKC(cudaMalloc(&h->pos_target, sizeof(float) * nd));
+    CKC(cudaMalloc(&h->vel_target, sizeof(float) * nd));
+    CKC(cudaMalloc(&h->dof_force, sizeof(float) * nd));
+    CKC(cudaMalloc(&h->body_state, sizeof(float) * nb * 13));
+    CKC(cudaMalloc(&h->body_force, sizeof(float) * nb * 6));
+    CKC(cudaMemset(h->pos_target, 0, sizeof(float) * nd));
+    CKC(cudaMemset(h->vel_target, 0, sizeof(float) * nd));
+    CKC(cudaMemset(h->dof_force, 0, sizeof(float) * nd));
+    CKC(cudaMemset(h->body_state, 0, sizeof(float) * nb * 13));
+    CKC(cudaMemset(h->body_force, 0, sizeof(float) * nb * 6));
+  }
   CKC(cudaMemcpy(h->d_types, tabs.data(), sizeof(EnvTypeTable) * tabs.size(), cudaMemcpyHostToDevice));
   CKC(cudaMemcpy(h->d_env_ids, env_ids.data(), sizeof(int) * env_ids.size(), cudaMemcpyHostToDevice));
   CKC(cudaMemcpy(h->d_dof_base, dof_base.data(), sizeof(int) * (n_envs + 1), cudaMemcpyHostToDevice));
@@ -989,6 +1024,35 @@ int sim_step_jvp(sim_handle h, const sim_jvp_buffers* b, float dt, int32_t subst
   }
   return SIM_OK;
 }
+
+int sim_get_max_dims(sim_handle h, int32_t* n_max, int32_t* l_max) {
+  if (!valid_handle(h)) return SIM_ERR_HANDLE;
+  if (!n_max || !l_max) return SIM_ERR_INVALID_ARG;
+  int nm = 1, lm = 1;
+  for (const TypePlan& tp : h->types) { nm = std::max(nm, tp.tab.n_gen); lm = std::max(lm, tp.tab.n_links); }
+  *n_max = nm;
+  *l_max = lm;
+  return SIM_OK;
+}
+
+static int run_query(sim_handle h, float* out, int what) {
+  if (!valid_handle(h)) return SIM_ERR_HANDLE;
+  if (!out) return SIM_ERR_INVALID_ARG;
+  int nm = 1, lm = 1;
+  sim_get_max_dims(h, &nm, &lm);
+  StepArgs a;
+  fill_common(h, 1.f, 1, a);
+  for (size_t t = 0; t < h->types.size(); ++t) {
+    TypeArgs ta;
+    fill_type(h, t, ta);
+    const cudaError_t e = launch_query_kernel(what, a, ta, out, nm, lm, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "dynamics query kernel launch");
+  }
+  return SIM_OK;
+}
+
+int sim_compute_mass_matrix(sim_handle h, float* out) { return run_query(h, out, 0); }
+int sim_compute_jacobian(sim_handle h, float* out) { return run_query(h, out, 1); }
 
 int sim_get_type_config(sim_handle h, int32_t type, int32_t* out) {
   if (!valid_handle(h)) return SIM_ERR_HANDLE;
@@ -1166,6 +1230,11 @@ int sim_get_view(sim_handle h, int32_t which, sim_view* out) {
     case SIM_VIEW_SIGNATURE: set(h->sig, 1, h->n_envs, 0, 0, SIM_DTYPE_U32); break;
     case SIM_VIEW_STATUS: set(h->status, 1, h->n_envs, 0, 0, SIM_DTYPE_I32); break;
     case SIM_VIEW_IMPULSE_CACHE: set(h->cache, 2, h->n_envs, h->cache_stride, 0, SIM_DTYPE_F32); break;
+    case SIM_VIEW_DOF_POSITION_TARGET: set(h->pos_target, 1, h->N_D, 0, 0, SIM_DTYPE_F32); break;
+    case SIM_VIEW_DOF_VELOCITY_TARGET: set(h->vel_target, 1, h->N_D, 0, 0, SIM_DTYPE_F32); break;
+    case SIM_VIEW_DOF_FORCE: set(h->dof_force, 1, h->N_D, 0, 0, SIM_DTYPE_F32); break;
+    case SIM_VIEW_RIGID_BODY_STATE: set(h->body_state, 2, h->N_B, 13, 0, SIM_DTYPE_F32); break;
+    case SIM_VIEW_RIGID_BODY_FORCE: set(h->body_force, 2, h->N_B, 6, 0, SIM_DTYPE_F32); break;
     default: return SIM_ERR_INVALID_ARG;
   }
   *out = v;

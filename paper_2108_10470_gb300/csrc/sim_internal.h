@@ -47,6 +47,8 @@ struct EnvTypeTable {
   float inertia[6][kMaxLinks];  // xx yy zz xy xz yz about the COM, link axes
   float armature[kMaxLinks], damping[kMaxLinks], lo[kMaxLinks], hi[kMaxLinks];
   int has_limit[kMaxLinks];
+  float drive_kp[kMaxLinks], drive_kd[kMaxLinks];  // joint drive gains (0: no drive)
+  int has_drives;
   // per shape
   int shape_link[kMaxShapes], shape_type[kMaxShapes], cand_off[kMaxShapes];
   float shape_size[3][kMaxShapes], shape_pos[3][kMaxShapes], shape_rot[9][kMaxShapes];
@@ -105,6 +107,11 @@ struct StepArgs {
   const int* env_dof_base;   // (n_envs,) first DOF row
   const int* env_body_base;  // (n_envs,) first body row
   const int* env_actor_base; // (n_envs,) first root-state row
+  const float* pos_target;   // (N_D,) drive targets (read when the type has drives)
+  const float* vel_target;   // (N_D,)
+  const float* body_force;   // (N_B, 6) external force, torque (flag 8)
+  float* dof_force;          // (N_D,) out (flag 32)
+  float* body_state;         // (N_B, 13) out (flag 16)
   int cache_stride, pair_stride;
   // step
   float dt, h;

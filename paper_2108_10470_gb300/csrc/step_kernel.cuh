@@ -67,6 +67,27 @@ __device__ __forceinline__ void quat_to_mat(const float* q, float* R) {
   R[3] = 2.f * (x * y + z * w);       R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - x * w);
   R[6] = 2.f * (x * z - y * w);       R[7] = 2.f * (y * z + x * w);       R[8] = 1.f - 2.f * (x * x + y * y);
 }
+// Unit quaternion (x, y, z, w), w >= 0, of a row-major rotation matrix (Shepperd's method: the
+// largest of 4w^2, 4x^2, 4y^2, 4z^2 picks the square root taken).
+__device__ __forceinline__ void mat_to_quat(const float* R, float* q) {
+  const float tr = R[0] + R[4] + R[8];
+  float x, y, z, w;
+  if (tr > 0.f) {
+    const float s = sqrtf(tr + 1.f) * 2.f;
+    w = 0.25f * s; x = (R[7] - R[5]) / s; y = (R[2] - R[6]) / s; z = (R[3] - R[1]) / s;
+  } else if (R[0] > R[4] && R[0] > R[8]) {
+    const float s = sqrtf(1.f + R[0] - R[4] - R[8]) * 2.f;
+    w = (R[7] - R[5]) / s; x = 0.25f * s; y = (R[1] + R[3]) / s; z = (R[2] + R[6]) / s;
+  } else if (R[4] > R[8]) {
+    const float s = sqrtf(1.f + R[4] - R[0] - R[8]) * 2.f;
+    w = (R[2] - R[6]) / s; x = (R[1] + R[3]) / s; y = 0.25f * s; z = (R[5] + R[7]) / s;
+  } else {
+    const float s = sqrtf(1.f + R[8] - R[0] - R[4]) * 2.f;
+    w = (R[3] - R[1]) / s; x = (R[2] + R[6]) / s; y = (R[5] + R[7]) / s; z = 0.25f * s;
+  }
+  const float sg = (w < 0.f) ? -1.f : 1.f;
+  q[0] = sg * x; q[1] = sg * y; q[2] = sg * z; q[3] = sg * w;
+}
 // Rotation by angle th about unit axis a (Rodrigues), child -> joint coordinates.
 __device__ __forceinline__ void axis_angle(V3 a, float th, float* R) {
   float s, c;
@@ -305,6 +326,11 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
     qd = A.dof[(size_t)(dof_base + jd) * 2 + 1];
     tau = A.act[dof_base + jd];  // joint force of the step; damping is added per substep
   }
+  float q_t = 0.f, v_t = 0.f;  // drive targets
+  if (has_dof && T->has_drives) {
+    q_t = A.pos_target[dof_base + jd];
+    v_t = A.vel_target[dof_base + jd];
+  }
   for (int i = lane; i < 3 * L; i += G) s_frc[i] = 0.f;
 
   unsigned sig = 2166136261u;
@@ -315,20 +341,16 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
   const V3 g = v3(A.gx, A.gy, A.gz);
   int n_con = 0, n_lim = 0, R = 0;
 
-  for (int sub = 0; sub < A.substeps; ++sub) {
-    // ======== (a2) forward kinematics + velocities, level-synchronous (link mode) ========
-    float Rw[9];               // link -> world rotation
-    V3 P = v3(0.f, 0.f, 0.f);  // link origin relative to the actor origin O_a
-    float vs[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // link spatial velocity [w; v] about O_a
-    float Sa[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // joint motion subspace about O_a
-    float cc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // velocity-product acceleration
+  // (a2) forward kinematics + velocities of the current state, level-synchronous (link mode): link
+  // rotation Rw, origin P relative to the actor origin, spatial velocity vs = [w; v] about it, the
+  // joint's motion subspace Sa and velocity-product acceleration cc
+  auto kinematics = [&](float* Rw, V3& P, float* vs, float* Sa, float* cc) {
     quat_to_mat(rq, Rw);
     if (is_root) {
       vs[0] = rw.x; vs[1] = rw.y; vs[2] = rw.z; vs[3] = rv.x; vs[4] = rv.y; vs[5] = rv.z;
       const V3 pxw = cross(rv, rw);  // d/dt S_root * nu = [0; p_dot x omega]
       cc[3] = pxw.x; cc[4] = pxw.y; cc[5] = pxw.z;
     }
-    const float Oz = Grp<G>::get(rp.z, ar);  // actor origin height (world)
     for (int d = 1; d <= maxdepth; ++d) {
       float Rp[9], vp[6];
       const int src = par >= 0 ? par : lane;
@@ -373,6 +395,17 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
         cc[0] = c0.x; cc[1] = c0.y; cc[2] = c0.z; cc[3] = c1.x; cc[4] = c1.y; cc[5] = c1.z;
       }
     }
+  };
+
+  for (int sub = 0; sub < A.substeps; ++sub) {
+    // ======== (a2) forward kinematics + velocities, level-synchronous (link mode) ========
+    float Rw[9];               // link -> world rotation
+    V3 P = v3(0.f, 0.f, 0.f);  // link origin relative to the actor origin O_a
+    float vs[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // link spatial velocity [w; v] about O_a
+    float Sa[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // joint motion subspace about O_a
+    float cc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // velocity-product acceleration
+    kinematics(Rw, P, vs, Sa, cc);
+    const float Oz = Grp<G>::get(rp.z, ar);  // actor origin height (world)
     // motion subspace per generalized DOF (unit columns for a floating root)
     if (has_dof) {
 #pragma unroll
@@ -416,8 +449,17 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
                        Ixz * w.x + Iyz * w.y + Izz * w.z);
       const V3 Fa = Iw + cross(hh, vl), Fl = vl * m + cross(w, hh);
       // v x* F = [w x Fa + v x Fl; w x Fl]; gravity force I [0; g] = [h x g; m g]
-      const V3 pa = cross(w, Fa) + cross(vl, Fl) - cross(hh, g);
-      const V3 pl = cross(w, Fl) - g * m;
+      V3 pa = cross(w, Fa) + cross(vl, Fl) - cross(hh, g);
+      V3 pl = cross(w, Fl) - g * m;
+      if ((A.flags & 8) && isl) {  // external force and torque at the COM (world axes)
+        const int bd = T->body[l];
+        if (bd >= 0) {
+          const float* bf = A.body_force + (size_t)(A.env_body_base[env] + bd) * 6;
+          const V3 F = v3(bf[0], bf[1], bf[2]);
+          pa = pa - (cross(cw, F) + v3(bf[3], bf[4], bf[5]));
+          pl = pl - F;
+        }
+      }
       // articulated inertia starts as the rigid inertia: [[I_O, h~], [h~^T, m 1]]
       IA[sidx(0, 0)] = Ixx; IA[sidx(0, 1)] = Ixy; IA[sidx(0, 2)] = Ixz;
       IA[sidx(1, 1)] = Iyy; IA[sidx(1, 2)] = Iyz; IA[sidx(2, 2)] = Izz;
@@ -663,7 +705,15 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
     // ======== inward sweep: articulated inertias (ABA pass 2) and composite inertias ========
     float U[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, Dinv = 0.f, uu = 0.f;
     {
-      const float tau_sub = tau - T->damping[l] * qd;
+      // joint force of the substep: actuation, damping, and the implicit drive kp (q* - q - h qd)
+      // + kd (qd* - qd) whose h (h kp + kd) joins the pivot (and the joint-space inertia diagonal)
+      float tau_sub = tau - T->damping[l] * qd, drive_d = 0.f;
+      if (T->has_drives) {
+        const float kp = T->drive_kp[l], kd = T->drive_kd[l];
+        tau_sub += kp * (q_t - q - h * qd) + kd * (v_t - qd);
+        drive_d = h * (h * kp + kd);
+      }
+      if ((A.flags & 32) && live && has_dof && sub == A.substeps - 1) A.dof_force[dof_base + jd] = tau_sub;
       for (int d = maxdepth; d >= 1; --d) {
         if (dep == d) {
           if (has_dof) {
@@ -674,7 +724,7 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
               for (int j = 0; j < 6; ++j) s += IA[sidx(i, j)] * Sa[j];
               U[i] = s;
             }
-            float D = T->armature[l], sp = 0.f;
+            float D = T->armature[l] + drive_d, sp = 0.f;
 #pragma unroll
             for (int i = 0; i < 6; ++i) { D += Sa[i] * U[i]; sp += Sa[i] * pA[i]; }
             if (!(D > 0.f)) { status |= 2; D = 1.f; }
@@ -805,7 +855,11 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
         const V3 Fa = Iw + cross(hh, vl), Fl = vl * mm_ + cross(w, hh);
         F[0] = Fa.x; F[1] = Fa.y; F[2] = Fa.z; F[3] = Fl.x; F[4] = Fl.y; F[5] = Fl.z;
       }
-      const float arm = (isg && T->dof_comp[lane] < 0) ? T->armature[gl] : 0.f;
+      float arm = 0.f;
+      if (isg && T->dof_comp[lane] < 0) {
+        arm = T->armature[gl];
+        if (T->has_drives) arm += h * (h * T->drive_kp[gl] + T->drive_kd[gl]);
+      }
 #pragma unroll
       for (int j = 0; j < G; ++j) {
         float mij = 0.f;
@@ -1025,6 +1079,28 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
     }
     __syncwarp();
   }  // substeps
+
+  // ======== body states after the step (flag 16): one more kinematics pass ========
+  if (A.flags & 16) {
+    float Rw[9];
+    V3 P = v3(0.f, 0.f, 0.f);
+    float vs[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, Sa[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float cc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    kinematics(Rw, P, vs, Sa, cc);
+    const V3 O = v3(Grp<G>::get(rp.x, ar), Grp<G>::get(rp.y, ar), Grp<G>::get(rp.z, ar));
+    const int bd = isl ? T->body[l] : -1;
+    if (live && bd >= 0) {
+      float* bs = A.body_state + (size_t)(A.env_body_base[env] + bd) * 13;
+      float qb[4];
+      mat_to_quat(Rw, qb);
+      const V3 w = v3(vs[0], vs[1], vs[2]);
+      const V3 vp = v3(vs[3], vs[4], vs[5]) + cross(w, P);  // velocity of the link origin
+      bs[0] = O.x + P.x; bs[1] = O.y + P.y; bs[2] = O.z + P.z;
+      bs[3] = qb[0]; bs[4] = qb[1]; bs[5] = qb[2]; bs[6] = qb[3];
+      bs[7] = vp.x; bs[8] = vp.y; bs[9] = vp.z;
+      bs[10] = w.x; bs[11] = w.y; bs[12] = w.z;
+    }
+  }
 
   // ======== outputs (one HBM write per env-step) ========
   if (is_root) {

@@ -184,13 +184,11 @@ template <int K> struct TanState {
   Dn<K> cache[kTanMaxCache];
 };
 
-// One substep in dual arithmetic. Returns false if a pivot or a capacity check fails.
-template <int K> __device__ bool tangent_substep(const StepArgs& A, const EnvTypeTable* T, TanState<K>& s,
-                                                 TanWork<K>& w) {
+// Kinematics and dynamics of the substep's start state: link poses, velocities, motion subspaces,
+// the joint-space inertia M (armature included; packed lower in w.L) and tau - b in w.rhs.
+template <int K> __device__ void tangent_dynamics(const StepArgs& A, const EnvTypeTable* T, TanState<K>& s,
+                                                  TanWork<K>& w) {
   const int L = T->n_links, n = T->n_gen;
-  const float h = A.h;
-  const int npos = A.pos_iters, nvel = A.vel_iters;
-  const float hit = h / (float)npos;
   const float gx = A.gx, gy = A.gy, gz = A.gz;
   // ---- forward kinematics, velocities, bias accelerations, rigid inertias (links in order) ----
   for (int l = 0; l < L; ++l) {
@@ -337,6 +335,16 @@ template <int K> __device__ bool tangent_substep(const StepArgs& A, const EnvTyp
     }
     w.rhs[i] = tau - bi;
   }
+}
+
+// One substep in dual arithmetic. Returns false if a pivot or a capacity check fails.
+template <int K> __device__ bool tangent_substep(const StepArgs& A, const EnvTypeTable* T, TanState<K>& s,
+                                                 TanWork<K>& w) {
+  tangent_dynamics<K>(A, T, s, w);
+  const int L = T->n_links, n = T->n_gen;
+  const float h = A.h;
+  const int npos = A.pos_iters, nvel = A.vel_iters;
+  const float hit = h / (float)npos;
   // ---- Cholesky M = L L^T (in place, packed lower) ----
   for (int j = 0; j < n; ++j) {
     Dn<K> djj = w.L[tri(j, j)];

@@ -22,13 +22,18 @@ ERRORS = {-1: "SIM_ERR_INVALID_ARG", -2: "SIM_ERR_TOPOLOGY", -3: "SIM_ERR_CUDA",
 SIM_FLAG_SIGNATURE = 1
 SIM_FLAG_PERSISTENT = 2
 SIM_FLAG_GRAPH = 4
+SIM_FLAG_BODY_FORCES = 8
+SIM_FLAG_RIGID_BODY_STATE = 16
+SIM_FLAG_DOF_FORCE = 32
 (SIM_VIEW_ROOT_STATE, SIM_VIEW_DOF_STATE, SIM_VIEW_DOF_ACTUATION, SIM_VIEW_NET_CONTACT_FORCE,
  SIM_VIEW_CONTACT_PAIRS, SIM_VIEW_CONTACT_COUNT, SIM_VIEW_SIGNATURE, SIM_VIEW_STATUS,
- SIM_VIEW_IMPULSE_CACHE) = range(9)
+ SIM_VIEW_IMPULSE_CACHE, SIM_VIEW_DOF_POSITION_TARGET, SIM_VIEW_DOF_VELOCITY_TARGET, SIM_VIEW_DOF_FORCE,
+ SIM_VIEW_RIGID_BODY_STATE, SIM_VIEW_RIGID_BODY_FORCE) = range(14)
 EXPORTED = ("sim_create", "sim_step", "sim_step_host", "sim_get_view", "sim_set_root_state_indexed",
             "sim_set_dof_state_indexed", "sim_set_stream", "sim_sync_status", "sim_get_sizes", "sim_destroy",
             "sim_error_string", "sim_last_error_message", "sim_probe_fp32_peak", "sim_step_static_scratch",
-            "sim_get_type_config", "sim_set_type_config", "sim_autotune", "sim_step_vjp", "sim_step_jvp")
+            "sim_get_type_config", "sim_set_type_config", "sim_autotune", "sim_step_vjp", "sim_step_jvp",
+            "sim_get_max_dims", "sim_compute_mass_matrix", "sim_compute_jacobian")
 
 F = ctypes.POINTER(ctypes.c_float)
 I32 = ctypes.POINTER(ctypes.c_int32)
@@ -40,7 +45,8 @@ class sim_model_desc(ctypes.Structure):
                 ("parent_pos", F), ("parent_quat", F), ("mass", F), ("com", F), ("inertia", F), ("armature", F),
                 ("damping", F), ("limit_lo", F), ("limit_hi", F), ("has_limit", U8), ("is_virtual", U8),
                 ("n_shapes", ctypes.c_int32), ("shape_link", I32), ("shape_type", I32), ("shape_size", F),
-                ("shape_pos", F), ("shape_quat", F), ("shape_friction", F)]
+                ("shape_pos", F), ("shape_quat", F), ("shape_friction", F), ("drive_stiffness", F),
+                ("drive_damping", F)]
 
 
 class sim_params(ctypes.Structure):
@@ -114,6 +120,9 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
                                ctypes.POINTER(ctypes.c_double)]
     L.sim_step_vjp.argtypes = [ctypes.c_void_p, ctypes.POINTER(sim_vjp_buffers), ctypes.c_float, ctypes.c_int32]
     L.sim_step_jvp.argtypes = [ctypes.c_void_p, ctypes.POINTER(sim_jvp_buffers), ctypes.c_float, ctypes.c_int32]
+    L.sim_get_max_dims.argtypes = [ctypes.c_void_p, I32, I32]
+    L.sim_compute_mass_matrix.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    L.sim_compute_jacobian.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
     _lib = L  # every other entry point returns int, ctypes' default restype
     return L
 
@@ -182,6 +191,9 @@ def model_structs(models):
                           shape_type=np.ascontiguousarray(m.shape_type, np.int32), shape_size=_f32(m.shape_size),
                           shape_pos=_f32(m.shape_pos), shape_quat=_f32(m.shape_quat),
                           shape_friction=_f32(m.shape_friction))
+        if m.drive_kp is not None or m.drive_kd is not None:
+            kp, kd = m.drive_gains()
+            fields.update(drive_stiffness=_f32(kp), drive_damping=_f32(kd))
         for k, a in fields.items():
             keep.append(a)
             ctype = dict(sim_model_desc._fields_)[k]
@@ -195,7 +207,8 @@ class Sim:
     Views (torch tensors aliasing library memory, valid until :meth:`destroy`):
     ``root_state`` (N_A, 13), ``dof_state`` (N_D, 2), ``dof_actuation`` (N_D,),
     ``net_contact_force`` (N_B, 3), ``contact_pairs`` (n_envs, C, 3), ``contact_count``,
-    ``signature``, ``status``, ``impulse_cache``.
+    ``signature``, ``status``, ``impulse_cache``, ``dof_position_target`` / ``dof_velocity_target``
+    (N_D,), ``dof_force`` (N_D,), ``rigid_body_state`` (N_B, 13), ``rigid_body_force`` (N_B, 6).
     """
 
     def __init__(self, w, stream=None, flags: int = 0):
@@ -218,7 +231,8 @@ class Sim:
         self.N_A, self.N_D, self.N_B, self.pair_cap, self.cache_len, self.n_types, self.launches_per_step = \
             [int(x) for x in sz]
         names = ["root_state", "dof_state", "dof_actuation", "net_contact_force", "contact_pairs", "contact_count",
-                 "signature", "status", "impulse_cache"]
+                 "signature", "status", "impulse_cache", "dof_position_target", "dof_velocity_target", "dof_force",
+                 "rigid_body_state", "rigid_body_force"]
         for which, name in enumerate(names):
             setattr(self, name, self.view(which))
 
@@ -269,6 +283,25 @@ class Sim:
                                   int(self.w.substeps if substeps is None else substeps), reps, ctypes.byref(ms)),
               "sim_autotune")
         return float(ms.value)
+
+    def max_dims(self):
+        n, l = ctypes.c_int32(0), ctypes.c_int32(0)
+        check(load().sim_get_max_dims(self.h, ctypes.byref(n), ctypes.byref(l)), "sim_get_max_dims")
+        return int(n.value), int(l.value)
+
+    def compute_mass_matrix(self):
+        """(n_envs, n_max, n_max) joint-space inertia at the current state (a new tensor)."""
+        n, _ = self.max_dims()
+        out = self._torch.zeros((self.w.n_envs, n, n), device=self.root_state.device)
+        check(load().sim_compute_mass_matrix(self.h, ctypes.c_void_p(out.data_ptr())), "sim_compute_mass_matrix")
+        return out
+
+    def compute_jacobian(self):
+        """(n_envs, L_max, 6, n_max) world-axis link Jacobians at the current state (a new tensor)."""
+        n, lm = self.max_dims()
+        out = self._torch.zeros((self.w.n_envs, lm, 6, n), device=self.root_state.device)
+        check(load().sim_compute_jacobian(self.h, ctypes.c_void_p(out.data_ptr())), "sim_compute_jacobian")
+        return out
 
     @staticmethod
     def _ptrs(fields, bufs):
