@@ -30,7 +30,9 @@ class _Models(ctypes.Structure):
                 ("axis", D), ("ppos", D), ("pquat", D), ("mass", D), ("com", D), ("inertia", D), ("armature", D),
                 ("damping", D), ("lo", D), ("hi", D), ("has_limit", I32), ("is_virtual", I32), ("shape_link", I32),
                 ("shape_type", I32), ("shape_size", D), ("shape_pos", D), ("shape_quat", D), ("shape_friction", D),
-                ("drive_kp", D), ("drive_kd", D)]
+                ("drive_kp", D), ("drive_kd", D), ("tendon_off", I32), ("tendon_entry_off", I32),
+                ("tendon_link", I32), ("tendon_coef", D), ("tendon_stiffness", D), ("tendon_damping", D),
+                ("tendon_rest", D), ("tendon_lo", D), ("tendon_hi", D), ("tendon_has_limit", I32)]
 
 
 class _Params(ctypes.Structure):
@@ -148,6 +150,18 @@ class Oracle:
             keep[name] = cat(name, dt)
         keep["drive_kp"] = np.ascontiguousarray(np.concatenate([m.drive_gains()[0] for m in ms]), np.float64)
         keep["drive_kd"] = np.ascontiguousarray(np.concatenate([m.drive_gains()[1] for m in ms]), np.float64)
+        if any(m.tendons for m in ms):
+            tl = [t for m in ms for t in (m.tendons or [])]
+            keep["tendon_off"] = np.cumsum([0] + [len(m.tendons or []) for m in ms]).astype(np.int32)
+            keep["tendon_entry_off"] = np.cumsum([0] + [len(t.links) for t in tl]).astype(np.int32)
+            keep["tendon_link"] = np.array([l for t in tl for l in t.links] or [0], np.int32)
+            keep["tendon_coef"] = np.array([c for t in tl for c in t.coef] or [0.0], np.float64)
+            for name, get in (("tendon_stiffness", lambda t: t.stiffness), ("tendon_damping", lambda t: t.damping),
+                              ("tendon_rest", lambda t: t.rest),
+                              ("tendon_lo", lambda t: t.limit[0] if t.limit else 0.0),
+                              ("tendon_hi", lambda t: t.limit[1] if t.limit else 0.0)):
+                keep[name] = np.array([get(t) for t in tl] or [0.0], np.float64)
+            keep["tendon_has_limit"] = np.array([int(t.limit is not None) for t in tl] or [0], np.int32)
         md = _Models()
         md.n_models = len(ms)
         for k, v in keep.items():

@@ -49,9 +49,18 @@ struct ShapeD {
   int link, type;
   double size[3], pos[3], quat[4], friction;
 };
+// Fixed tendon: length l = sum_k coef_k q_{link_k} over 1-DOF joints of one articulation; a spring
+// -damper on the length and optional length limits.
+struct TendonD {
+  std::vector<int> links;     // model-local link of each joint
+  std::vector<double> coef;
+  double stiffness = 0.0, damping = 0.0, rest = 0.0, lo = 0.0, hi = 0.0;
+  int has_limit = 0;
+};
 struct ModelD {
   std::vector<LinkD> links;
   std::vector<ShapeD> shapes;
+  std::vector<TendonD> tendons;
   std::vector<int> ndof;   // DOFs of each link's joint (0, 1 or 6)
   std::vector<int> goff;   // offset of each link's DOFs in the model's generalized vector
   std::vector<int> jdof;   // joint-DOF index (DOF state tensor row within the model) or -1
@@ -76,7 +85,7 @@ struct Oracle {
   std::vector<int> n_gen, contact_cap;
   int64_t N_A = 0, N_D = 0, N_B = 0;
   int max_contact_cap = 0, max_gen = 0;
-  int cache_len = 0;  // per env: 3 * contact candidates + 2 * joint DOFs (max over envs)
+  int cache_len = 0;  // per env: 3 * contact candidates + 2 * joint DOFs + 2 * tendons (max over envs)
   const ModelD& actor_model(int env, int a) const { return models[env_actors[env][a]]; }
   int n_act(int env) const { return (int)env_actors[env].size(); }
 };
@@ -674,9 +683,39 @@ template <class T> void build_rows(const Oracle& O, int env, const EnvLayout& E,
     }
     jbase += M.n_jdof;
   }
+  // tendon length limits (after every joint limit): J = +-c over the tendon's joints, slots after
+  // the joint-limit slots
+  std::vector<int32_t> ten_ids;
+  int tbase = 0;
+  for (int a = 0; a < O.n_act(env); ++a) {
+    const ModelD& M = O.actor_model(env, a);
+    for (size_t t = 0; t < M.tendons.size(); ++t) {
+      const TendonD& td = M.tendons[t];
+      if (!td.has_limit) continue;
+      T len(0.0);
+      for (size_t k = 0; k < td.links.size(); ++k) len = len + T(td.coef[k]) * st[a].q[M.jdof[td.links[k]]];
+      for (int side = 0; side < 2; ++side) {
+        const T dist = side == 0 ? len - T(td.lo) : T(td.hi) - len;
+        if (!(dist < margin)) continue;
+        Row<T> r{ROW_LIMIT, std::vector<T>(n, T(0.0)), dist, -1, T(0.0), -1, zero3<T>(), {}, T(0.0),
+                 3 * O.contact_cap[env] + 2 * jbase + 2 * (tbase + (int)t) + side};
+        for (size_t k = 0; k < td.links.size(); ++k)
+          r.J[E.gen_off[a] + M.goff[td.links[k]]] = r.J[E.gen_off[a] + M.goff[td.links[k]]] +
+                                                   T(side == 0 ? td.coef[k] : -td.coef[k]);
+        rows.push_back(r);
+        ten_ids.push_back(tbase + (int)t);
+        ten_ids.push_back(side);
+      }
+    }
+    tbase += (int)M.tendons.size();
+  }
   if (sig) {
     fnv1a_int(*sig, (int32_t)(lim_ids.size() / 2));
     for (int32_t v : lim_ids) fnv1a_int(*sig, v);
+    if (tbase > 0) {  // envs with tendons also hash their tendon-limit rows
+      fnv1a_int(*sig, (int32_t)(ten_ids.size() / 2));
+      for (int32_t v : ten_ids) fnv1a_int(*sig, v);
+    }
     fnv1a_int(*sig, (int32_t)C.size());
     for (const auto& c : C) { fnv1a_int(*sig, c.shape_a); fnv1a_int(*sig, c.shape_b); fnv1a_int(*sig, c.slot); }
   }
@@ -786,6 +825,23 @@ template <class T> void env_substep(const Oracle& O, int env, std::vector<ActorS
         tau[M.goff[l]] = f;
         if (out.dof_force.size() > (size_t)(jbase + j)) out.dof_force[jbase + j] = f;
       }
+    // fixed tendons: spring-damper on the length l = sum c_k q_k, force F = -k (l - rest) - d l_dot
+    // at the substep start, applied to each joint as c_k F
+    for (const TendonD& td : M.tendons) {
+      T len(0.0), rate(0.0);
+      for (size_t k = 0; k < td.links.size(); ++k) {
+        const int j = M.jdof[td.links[k]];
+        len = len + T(td.coef[k]) * st[a].q[j];
+        rate = rate + T(td.coef[k]) * st[a].qd[j];
+      }
+      const T F = T(0.0) - T(td.stiffness) * (len - T(td.rest)) - T(td.damping) * rate;
+      for (size_t k = 0; k < td.links.size(); ++k) {
+        const int l = td.links[k];
+        tau[M.goff[l]] = tau[M.goff[l]] + T(td.coef[k]) * F;
+        if (out.dof_force.size() > (size_t)(jbase + M.jdof[l]))
+          out.dof_force[jbase + M.jdof[l]] = out.dof_force[jbase + M.jdof[l]] + T(td.coef[k]) * F;
+      }
+    }
     // external force and torque per body (world axes, at the COM) as link-coordinate spatial forces
     std::vector<SVec<T>> fext;
     if (ctl.body_force) {
@@ -1184,6 +1240,18 @@ struct OracleModels {
   const double* shape_friction;
   const double* drive_kp;  // [links] or null (no drives)
   const double* drive_kd;  // [links] or null
+  // fixed tendons (all null: none): model m owns tendons tendon_off[m] .. tendon_off[m+1]-1,
+  // tendon t owns entries entry_off[t] .. entry_off[t+1]-1 (model-local link, coefficient)
+  const int32_t* tendon_off;
+  const int32_t* tendon_entry_off;
+  const int32_t* tendon_link;
+  const double* tendon_coef;
+  const double* tendon_stiffness;
+  const double* tendon_damping;
+  const double* tendon_rest;
+  const double* tendon_lo;
+  const double* tendon_hi;
+  const int32_t* tendon_has_limit;
 };
 struct OracleParams {
   double gravity[3];
@@ -1239,6 +1307,21 @@ void* oracle_create(const OracleModels* md, const int32_t* env_actor_model, int3
     }
     M.n_gen = g;
     M.n_jdof = j;
+    if (md->tendon_off)
+      for (int t = md->tendon_off[m]; t < md->tendon_off[m + 1]; ++t) {
+        TendonD td;
+        for (int e = md->tendon_entry_off[t]; e < md->tendon_entry_off[t + 1]; ++e) {
+          td.links.push_back(md->tendon_link[e]);
+          td.coef.push_back(md->tendon_coef[e]);
+        }
+        td.stiffness = md->tendon_stiffness[t];
+        td.damping = md->tendon_damping[t];
+        td.rest = md->tendon_rest[t];
+        td.lo = md->tendon_lo[t];
+        td.hi = md->tendon_hi[t];
+        td.has_limit = md->tendon_has_limit[t];
+        M.tendons.push_back(td);
+      }
     O->models.push_back(M);
   }
   O->n_envs = n_envs;
@@ -1278,10 +1361,10 @@ void* oracle_create(const OracleModels* md, const int32_t* env_actor_model, int3
   O->n_gen.assign(n_envs, 0);
   O->contact_cap.assign(n_envs, 0);
   for (int e = 0; e < n_envs; ++e) {
-    int jd = 0, nb = 0, ng = 0, cc = kPairSlots * (int)O->env_pairs[e].size();
+    int jd = 0, nb = 0, ng = 0, nt = 0, cc = kPairSlots * (int)O->env_pairs[e].size();
     for (int a = 0; a < O->n_act(e); ++a) {
       const ModelD& M = O->actor_model(e, a);
-      jd += M.n_jdof; nb += M.n_body; ng += M.n_gen; cc += M.contact_cap;
+      jd += M.n_jdof; nb += M.n_body; ng += M.n_gen; cc += M.contact_cap; nt += (int)M.tendons.size();
     }
     O->jdof_off[e + 1] = O->jdof_off[e] + jd;
     O->body_off[e + 1] = O->body_off[e] + nb;
@@ -1289,7 +1372,7 @@ void* oracle_create(const OracleModels* md, const int32_t* env_actor_model, int3
     O->contact_cap[e] = cc;
     O->max_contact_cap = std::max(O->max_contact_cap, cc);
     O->max_gen = std::max(O->max_gen, ng);
-    O->cache_len = std::max(O->cache_len, 3 * cc + 2 * jd);
+    O->cache_len = std::max(O->cache_len, 3 * cc + 2 * jd + 2 * nt);
   }
   O->N_A = O->actor_off[n_envs];
   O->N_D = O->jdof_off[n_envs];

@@ -31,6 +31,19 @@ IDENT_Q = (0.0, 0.0, 0.0, 1.0)
 
 
 @dataclasses.dataclass
+class Tendon:
+    """Fixed tendon of one articulation: length l = sum_k coef[k] q(links[k]) over 1-DOF joints, a
+    spring-damper on the length (force -stiffness (l - rest) - damping l_dot, applied to each joint
+    as coef[k] times it) and optional length limits lo <= l <= hi."""
+    links: List[int]
+    coef: List[float]
+    stiffness: float = 0.0
+    damping: float = 0.0
+    rest: float = 0.0
+    limit: Optional[tuple] = None
+
+
+@dataclasses.dataclass
 class Model:
     """One articulation: links 0..L-1 with parent[i] < i, plus collision shapes."""
 
@@ -60,6 +73,7 @@ class Model:
     dof_noise: float = 0.0    # half-width of the uniform initial joint-position noise
     drive_kp: Optional[np.ndarray] = None  # per link: joint drive stiffness (None: no drives)
     drive_kd: Optional[np.ndarray] = None  # per link: joint drive damping
+    tendons: Optional[List[Tendon]] = None   # fixed tendons (None: none)
 
     def drive_gains(self):
         """(kp, kd) per link, zeros where no drive is set."""
@@ -106,6 +120,11 @@ class _Builder:
         self.links: List[dict] = []
         self.shapes: List[dict] = []
         self.gear: List[float] = []
+        self.tendons: List[Tendon] = []
+
+    def tendon(self, links, coef, stiffness=0.0, damping=0.0, rest=0.0, limit=None):
+        self.tendons.append(Tendon(list(links), [float(c) for c in coef], float(stiffness), float(damping),
+                                   float(rest), limit))
 
     def link(self, parent, jtype, *, axis=(0, 0, 1), ppos=(0, 0, 0), pquat=IDENT_Q, mass=0.0, com=(0, 0, 0),
              inertia=(0, 0, 0, 0, 0, 0), armature=0.0, damping=0.0, limit=None, virtual=False, gear=1.0,
@@ -151,7 +170,8 @@ class _Builder:
             root_pos=np.array(root_pos, dtype=np.float64),
             dof_noise=float(dof_noise),
             drive_kp=f("kp") if any(l["kp"] for l in L) else None,
-            drive_kd=f("kd") if any(l["kd"] for l in L) else None)
+            drive_kd=f("kd") if any(l["kd"] for l in L) else None,
+            tendons=list(self.tendons) if self.tendons else None)
 
 
 # ------------------------------------------------------------------------------------------------
