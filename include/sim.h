@@ -83,7 +83,22 @@ typedef struct {
   const float* shape_friction;/* [S]   >= 0                                                 */
   const float* drive_stiffness; /* [L] >= 0 joint drive stiffness kp, or NULL (no drives)   */
   const float* drive_damping;   /* [L] >= 0 joint drive damping kd, or NULL                  */
+  int32_t n_tendons;            /* fixed tendons, 0..8 (0: the arrays below are ignored)      */
+  const int32_t* tendon_joint_count; /* [T] 1..8 joints per tendon                             */
+  const int32_t* tendon_link;   /* [sum counts] link of each joint (a 1-DOF joint), tendon by tendon */
+  const float* tendon_coef;     /* [sum counts] length coefficient of each joint              */
+  const float* tendon_stiffness;/* [T] >= 0                                                   */
+  const float* tendon_damping;  /* [T] >= 0                                                   */
+  const float* tendon_rest_length; /* [T]                                                     */
+  const float* tendon_limit_lo; /* [T] used when tendon_has_limit                             */
+  const float* tendon_limit_hi; /* [T] >= lo                                                  */
+  const uint8_t* tendon_has_limit; /* [T] 0/1                                                 */
 } sim_model_desc;
+/* Fixed tendons (paper: fixed tendons coupling joints, with stiffness, damping and limits): the
+ * length of a tendon is l = sum_k coef_k q_k over its joints; each substep it applies the force
+ * -stiffness (l - rest) - damping l_dot (at the substep start) to each joint as coef_k times it,
+ * and a limited tendon gets constraint rows (J = +-coef over its joints, treated like joint-limit
+ * rows) when l is within the limit margin of lo or hi; lo = hi holds the length fixed. */
 /* Joint drives (paper: DOF position / velocity targets with drive stiffness and damping): each
  * substep a driven joint gets the force kp (q* - q - h qd) + kd (qd* - qd) with h (h kp + kd)
  * added to its joint-space inertia diagonal, i.e. the spring-damper integrated implicitly over the

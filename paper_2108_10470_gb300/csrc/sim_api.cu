@@ -170,6 +170,29 @@ int validate_model(const sim_model_desc& m) {
     if (m.drive_stiffness && !(m.drive_stiffness[i] >= 0.f && finite(m.drive_stiffness[i]))) return SIM_ERR_INVALID_ARG;
     if (m.drive_damping && !(m.drive_damping[i] >= 0.f && finite(m.drive_damping[i]))) return SIM_ERR_INVALID_ARG;
   }
+  if (m.n_tendons < 0 || m.n_tendons > kMaxTendons) return SIM_ERR_CAPACITY;
+  if (m.n_tendons > 0) {
+    if (!m.tendon_joint_count || !m.tendon_link || !m.tendon_coef || !m.tendon_stiffness || !m.tendon_damping ||
+        !m.tendon_rest_length || !m.tendon_limit_lo || !m.tendon_limit_hi || !m.tendon_has_limit)
+      return SIM_ERR_INVALID_ARG;
+    int e = 0;
+    for (int t = 0; t < m.n_tendons; ++t) {
+      const int cnt = m.tendon_joint_count[t];
+      if (cnt < 1 || cnt > kMaxTendonJoints) return SIM_ERR_CAPACITY;
+      for (int k = 0; k < cnt; ++k, ++e) {
+        const int li = m.tendon_link[e];
+        if (li < 1 || li >= m.n_links) return SIM_ERR_INVALID_ARG;
+        if (m.joint_type[li] != SIM_JOINT_REVOLUTE && m.joint_type[li] != SIM_JOINT_PRISMATIC) return SIM_ERR_INVALID_ARG;
+        if (!finite(m.tendon_coef[e])) return SIM_ERR_INVALID_ARG;
+      }
+      if (!(m.tendon_stiffness[t] >= 0.f) || !(m.tendon_damping[t] >= 0.f) || !finite(m.tendon_stiffness[t]) ||
+          !finite(m.tendon_damping[t]) || !finite(m.tendon_rest_length[t]) || m.tendon_has_limit[t] > 1)
+        return SIM_ERR_INVALID_ARG;
+      if (m.tendon_has_limit[t] && (!finite(m.tendon_limit_lo[t]) || !finite(m.tendon_limit_hi[t]) ||
+                                    m.tendon_limit_lo[t] > m.tendon_limit_hi[t]))
+        return SIM_ERR_INVALID_ARG;
+    }
+  }
   for (int s = 0; s < m.n_shapes; ++s) {
     const int li = m.shape_link[s];
     if (li < 0 || li >= m.n_links || m.is_virtual[li]) return SIM_ERR_INVALID_ARG;
@@ -269,6 +292,22 @@ int build_type(const sim_model_desc* models, const std::vector<int>& actor_model
       T.shape_mu[e] = std::max(m.shape_friction[s], p.ground_friction);
       T.shape_fr[e] = m.shape_friction[s];
     }
+    int e = 0;
+    for (int t = 0; t < m.n_tendons; ++t) {
+      if (T.n_tendons >= kMaxTendons) return SIM_ERR_CAPACITY;
+      const int k = T.n_tendons++;
+      T.ten_n[k] = m.tendon_joint_count[t];
+      for (int j = 0; j < T.ten_n[k]; ++j, ++e) {
+        T.ten_link[k][j] = base + m.tendon_link[e];
+        T.ten_coef[k][j] = m.tendon_coef[e];
+      }
+      T.ten_k[k] = m.tendon_stiffness[t];
+      T.ten_d[k] = m.tendon_damping[t];
+      T.ten_rest[k] = m.tendon_rest_length[t];
+      T.ten_has_limit[k] = m.tendon_has_limit[t];
+      T.ten_lo[k] = m.tendon_limit_lo[t];
+      T.ten_hi[k] = m.tendon_limit_hi[t];
+    }
     L += m.n_links;
     ns += m.n_shapes;
   }
@@ -314,9 +353,10 @@ int build_type(const sim_model_desc* models, const std::vector<int>& actor_model
   T.n_body = nb;
   T.n_actors = (int)actor_models.size();
   T.max_depth = maxd;
+  for (int t = 0; t < T.n_tendons; ++t) lim_cap += T.ten_has_limit[t] ? 2 : 0;
   T.lim_cap = lim_cap;
   T.row_cap = lim_cap + 3 * nc;
-  T.cache_len = 3 * nc + 2 * nj;
+  T.cache_len = 3 * nc + 2 * nj + 2 * T.n_tendons;
   const int need = std::max(std::max(L, n), std::max(ns, 1));
   T.group = need <= 8 ? 8 : (need <= 16 ? 16 : 32);
   return SIM_OK;
@@ -491,8 +531,8 @@ int tangent_supported(const sim_s* h) {
     return SIM_ERR_CAPACITY;
   }
   for (const TypePlan& tp : h->types)
-    if (tp.tab.has_drives) {
-      g_last_error = "step derivative: joint drives are not part of the differentiated step";
+    if (tp.tab.has_drives || tp.tab.n_tendons > 0) {
+      g_last_error = "step derivative: joint drives and tendons are not part of the differentiated step";
       return SIM_ERR_CAPACITY;
     }
   for (const TypePlan& tp : h->types)

@@ -15,10 +15,12 @@ constexpr int kMaxPairs = 32;   // capsule-box shape pairs per environment
 constexpr int kPairSlots = 5;   // samples per pair: t = 0, t = 1, face-clip entry / exit, closest point
 constexpr int kMaxCand = 256;   // contact candidate points per environment
 constexpr int kMaxActors = 8;   // actors per environment
+constexpr int kMaxTendons = 8;      // fixed tendons per environment
+constexpr int kMaxTendonJoints = 8; // joints per tendon
 
 enum JointType : int { kFree = 0, kFixed = 1, kRevolute = 2, kPrismatic = 3 };
 enum ShapeType : int { kSphere = 0, kCapsule = 1, kBox = 2 };
-enum RowKind : int { kRowLimit = 0, kRowNormal = 1, kRowFriction = 2 };
+enum RowKind : int { kRowLimit = 0, kRowNormal = 1, kRowFriction = 2, kRowTendon = 3 };
 
 // One environment type = one sequence of actor models, flattened into a forest of links.
 // Per-link arrays are indexed by the env-local link number (actors in order, links in order, so
@@ -49,6 +51,14 @@ struct EnvTypeTable {
   int has_limit[kMaxLinks];
   float drive_kp[kMaxLinks], drive_kd[kMaxLinks];  // joint drive gains (0: no drive)
   int has_drives;
+  // fixed tendons (env-local links of 1-DOF joints); limit rows follow the joint-limit rows and use
+  // impulse-cache slots 3 n_cand + 2 n_jdof + 2 t + side
+  int n_tendons;
+  int ten_n[kMaxTendons];
+  int ten_link[kMaxTendons][kMaxTendonJoints];
+  float ten_coef[kMaxTendons][kMaxTendonJoints];
+  float ten_k[kMaxTendons], ten_d[kMaxTendons], ten_rest[kMaxTendons], ten_lo[kMaxTendons], ten_hi[kMaxTendons];
+  int ten_has_limit[kMaxTendons];
   // per shape
   int shape_link[kMaxShapes], shape_type[kMaxShapes], cand_off[kMaxShapes];
   float shape_size[3][kMaxShapes], shape_pos[3][kMaxShapes], shape_rot[9][kMaxShapes];

@@ -670,6 +670,37 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
           s_rowa[o] = gd | (1 << 8) | (jd << 16);
         }
       }
+      // tendon length limits after the joint limits (lane t: tendon t); J = +-c over its joints
+      const int n_jlim = n_lim;
+      int n_tlim = 0;
+      if (T->n_tendons > 0) {
+        float tl = 0.f;
+        for (int t = 0; t < T->n_tendons; ++t)
+          for (int k = 0; k < T->ten_n[t]; ++k) {
+            const float qk = Grp<G>::get(q, T->ten_link[t][k]);
+            if (lane == t) tl += T->ten_coef[t][k] * qk;
+          }
+        int tf = 0;
+        float tdlo = 0.f, tdhi = 0.f;
+        if (lane < T->n_tendons && T->ten_has_limit[lane]) {
+          tdlo = tl - T->ten_lo[lane];
+          tdhi = T->ten_hi[lane] - tl;
+          if (tdlo < A.limit_margin) tf |= 1;
+          if (tdhi < A.limit_margin) tf |= 2;
+        }
+        int o = n_jlim + Grp<G>::excl_scan(__popc(tf), lane, &n_tlim);
+        const int slot0 = 3 * T->n_cand + 2 * T->n_jdof + 2 * lane;
+        if (tf & 1) {
+          s_rowc[o] = make_float4(tdlo, 0.f, __int_as_float(kRowTendon), __int_as_float(slot0));
+          s_rowa[o] = lane;
+          ++o;
+        }
+        if (tf & 2) {
+          s_rowc[o] = make_float4(tdhi, 0.f, __int_as_float(kRowTendon), __int_as_float(slot0 + 1));
+          s_rowa[o] = lane | (1 << 8);
+        }
+      }
+      n_lim = n_jlim + n_tlim;
       R = n_lim + 3 * n_con;
       __syncwarp();
       // contact rows: every contact's normal row, then every contact's two friction rows
@@ -687,11 +718,19 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
       }
       __syncwarp();
       if ((A.flags & 1) && lane == 0) {
-        fnv1a(sig, n_lim);
-        for (int r = 0; r < n_lim; ++r) {
+        fnv1a(sig, n_jlim);
+        for (int r = 0; r < n_jlim; ++r) {
           const int a = s_rowa[r];
           fnv1a(sig, a >> 16);
           fnv1a(sig, (a >> 8) & 1);
+        }
+        if (T->n_tendons > 0) {  // envs with tendons also hash their tendon-limit rows
+          fnv1a(sig, n_tlim);
+          for (int r = n_jlim; r < n_lim; ++r) {
+            const int a = s_rowa[r];
+            fnv1a(sig, a & 0xff);
+            fnv1a(sig, (a >> 8) & 1);
+          }
         }
         fnv1a(sig, n_con);
         for (int c = 0; c < n_con; ++c) {
@@ -712,6 +751,18 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
         const float kp = T->drive_kp[l], kd = T->drive_kd[l];
         tau_sub += kp * (q_t - q - h * qd) + kd * (v_t - qd);
         drive_d = h * (h * kp + kd);
+      }
+      // fixed tendons: force -k (l - rest) - d l_dot on the length l = sum c q, applied as c F
+      for (int t = 0; t < T->n_tendons; ++t) {
+        float len = 0.f, rate = 0.f, mine = 0.f;
+        for (int k = 0; k < T->ten_n[t]; ++k) {
+          const int lk = T->ten_link[t][k];
+          const float c = T->ten_coef[t][k];
+          len += c * Grp<G>::get(q, lk);
+          rate += c * Grp<G>::get(qd, lk);
+          if (lk == l && has_dof) mine += c;
+        }
+        tau_sub += mine * (-T->ten_k[t] * (len - T->ten_rest[t]) - T->ten_d[t] * rate);
       }
       if ((A.flags & 32) && live && has_dof && sub == A.substeps - 1) A.dof_force[dof_base + jd] = tau_sub;
       for (int d = maxdepth; d >= 1; --d) {
@@ -909,8 +960,12 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
       unsigned anc = 0u, ancb = 0u;
       int gl = -1;
       float sgn = 0.f;
+      int tt = -1;
       if (kind == kRowLimit) {
         gl = a & 0xff;
+        sgn = ((a >> 8) & 1) ? -1.f : 1.f;
+      } else if (kind == kRowTendon) {
+        tt = a & 0xff;
         sgn = ((a >> 8) & 1) ? -1.f : 1.f;
       } else {
         const int c = a & 0xff, dir = (a >> 8) & 3;
@@ -935,6 +990,19 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
       }
       float y[G];
       float asum = 0.f;
+      if (kind == kRowTendon) {
+        // (rare) tendon rows: J from the tendon's coefficients, forward substitution through the
+        // row's column of Y in shared memory (kept out of the unrolled loop below)
+        for (int i = 0; i < n; ++i) {
+          float ji = 0.f;
+          for (int k = 0; k < T->ten_n[tt]; ++k)
+            if (T->gdof[T->ten_link[tt][k]] == i) ji += sgn * T->ten_coef[tt][k];
+          for (int k = 0; k < i; ++k) ji -= s_M[i * MS + k] * s_Y[k * RS + r];
+          const float yi = ji * s_Linv[i];
+          s_Y[i * RS + r] = yi;
+          asum += yi * yi;
+        }
+      } else {
 #pragma unroll
       for (int i = 0; i < G; ++i) {
         if (i < n) {
@@ -958,6 +1026,7 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
         } else {
           y[i] = 0.f;
         }
+      }
       }
       const bool act = asum > 1e-12f;
       const float invA = act ? 1.f / asum : 0.f;

@@ -46,7 +46,9 @@ class sim_model_desc(ctypes.Structure):
                 ("damping", F), ("limit_lo", F), ("limit_hi", F), ("has_limit", U8), ("is_virtual", U8),
                 ("n_shapes", ctypes.c_int32), ("shape_link", I32), ("shape_type", I32), ("shape_size", F),
                 ("shape_pos", F), ("shape_quat", F), ("shape_friction", F), ("drive_stiffness", F),
-                ("drive_damping", F)]
+                ("drive_damping", F), ("n_tendons", ctypes.c_int32), ("tendon_joint_count", I32), ("tendon_link", I32),
+                ("tendon_coef", F), ("tendon_stiffness", F), ("tendon_damping", F), ("tendon_rest_length", F),
+                ("tendon_limit_lo", F), ("tendon_limit_hi", F), ("tendon_has_limit", U8)]
 
 
 class sim_params(ctypes.Structure):
@@ -194,6 +196,17 @@ def model_structs(models):
         if m.drive_kp is not None or m.drive_kd is not None:
             kp, kd = m.drive_gains()
             fields.update(drive_stiffness=_f32(kp), drive_damping=_f32(kd))
+        if m.tendons:
+            tl = m.tendons
+            d.n_tendons = len(tl)
+            fields.update(tendon_joint_count=np.array([len(t.links) for t in tl], np.int32),
+                          tendon_link=np.array([l for t in tl for l in t.links], np.int32),
+                          tendon_coef=_f32([c for t in tl for c in t.coef]),
+                          tendon_stiffness=_f32([t.stiffness for t in tl]), tendon_damping=_f32([t.damping for t in tl]),
+                          tendon_rest_length=_f32([t.rest for t in tl]),
+                          tendon_limit_lo=_f32([t.limit[0] if t.limit else 0.0 for t in tl]),
+                          tendon_limit_hi=_f32([t.limit[1] if t.limit else 0.0 for t in tl]),
+                          tendon_has_limit=np.array([int(t.limit is not None) for t in tl], np.uint8))
         for k, a in fields.items():
             keep.append(a)
             ctype = dict(sim_model_desc._fields_)[k]

@@ -345,11 +345,13 @@ HAND_HEIGHT = 0.5   # palm centre above the ground
 CUBE_HALF = 0.0325  # 6.5 cm cube
 
 
-def hand(density=1000.0, armature=0.01, damping=0.05, gear=0.5, friction=1.0) -> Model:
+def hand(density=1000.0, armature=0.01, damping=0.05, gear=0.5, friction=1.0, coupled=False) -> Model:
     """Fixed-base five-finger hand, palm up, shaped like the paper's 24-DOF Shadow Hand: wrist 2 DOF,
     index / middle / ring 4 DOF each (abduction + three flexions), little 5 (metacarpal + 4), thumb
     5; multi-axis joints are chains through massless virtual links; every joint is limited to
-    +-90 degrees. Capsule palm and phalanges (radius 1 cm), 16 shapes. 25 links, 24 DOF."""
+    +-90 degrees. Capsule palm and phalanges (radius 1 cm), 16 shapes. 25 links, 24 DOF.
+    coupled=True adds a fixed tendon per long finger holding its middle and distal flexions equal
+    (length q_middle - q_distal with limits [0, 0]), as the Shadow Hand couples them."""
     b = _Builder("hand")
     lim = (-math.pi / 2, math.pi / 2)
 
@@ -378,7 +380,9 @@ def hand(density=1000.0, armature=0.01, damping=0.05, gear=0.5, friction=1.0) ->
         a = hinge(parent, (0, 0, 1), base)  # abduction (virtual)
         p = phalanx(a, (0, 1, 0), (0, 0, 0), lens[0])
         m = phalanx(p, (0, 1, 0), (2 * lens[0], 0, 0), lens[1])
-        phalanx(m, (0, 1, 0), (2 * lens[1], 0, 0), lens[2])
+        d = phalanx(m, (0, 1, 0), (2 * lens[1], 0, 0), lens[2])
+        if coupled:
+            b.tendon([m, d], (1.0, -1.0), limit=(0.0, 0.0))
 
     for y in (0.033, 0.011, -0.011):  # index, middle, ring
         finger(palm, (0.06, y, 0.0))
@@ -527,6 +531,13 @@ def homogeneous(name: str, model: Model, n_envs: int, params: Optional[Params] =
                 substeps=2) -> Workload:
     return Workload(name=name, models=[model], env_actor_model=np.zeros(n_envs, dtype=np.int32), actors_per_env=1,
                     n_envs=n_envs, params=params or Params(), dt=dt, substeps=substeps)
+
+
+def hand_tendon_workload(n_envs=64) -> Workload:
+    """The hand with coupled middle / distal flexions (four equality tendons) holding a free cube."""
+    return Workload(name="hand_tendon", models=[hand(coupled=True), cube()],
+                    env_actor_model=np.tile(np.array([0, 1], np.int32), n_envs), actors_per_env=2, n_envs=n_envs,
+                    params=Params())
 
 
 def hand_workload(n_envs=64) -> Workload:
