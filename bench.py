@@ -342,9 +342,55 @@ def run_ours(args, rank, world, local_rank):
                               f"in the timed region)"}
     line["roofline"] = roof
     line["cpu_baseline"] = cpu
+    if world == 1 and not args.no_variants and args.workload == "ant" and args.envs == 4096:
+        line["variants"] = variants_measure(dev)
     if world == 1 and not args.no_adjoint:
         line["adjoint"] = adjoint_measure(dev)
     print(json.dumps(line), flush=True)
+
+
+def timed_steps(s, act_dev, warm, steps, flush):
+    """Mean device time of `steps` sim_steps (actions copied in, L2 flushed before each, outside
+    the step's events) after `warm` untimed steps."""
+    import torch
+    for k in range(warm):
+        s.dof_actuation.copy_(act_dev[k % act_dev.shape[0]])
+        s.step()
+    torch.cuda.synchronize()
+    ev = []
+    for k in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        s.dof_actuation.copy_(act_dev[(warm + k) % act_dev.shape[0]])
+        s.step()
+        e1.record()
+        ev.append((e0, e1))
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ev) / steps
+
+
+def variants_measure(dev, warm=20, steps=200):
+    """The same Ant-like step at 8192 and 16384 envs, and at 4096 envs replayed as a captured CUDA
+    graph: env-steps/s under the main line's timing protocol."""
+    import torch
+
+    from paper_2108_10470_gb300 import sim, workloads as W
+
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    out = {}
+    for n_envs, flags, key in ((8192, 0, "envs_8192"), (16384, 0, "envs_16384"),
+                               (4096, sim.SIM_FLAG_GRAPH, "cuda_graph_4096")):
+        w = W.ant_workload(n_envs)
+        root, dof, acts = W.seeded_inputs(w, 0, warm + steps)
+        s = sim.Sim(w, flags=flags)
+        s.root_state.copy_(torch.from_numpy(root))
+        s.dof_state.copy_(torch.from_numpy(dof))
+        ms = timed_steps(s, torch.from_numpy(acts).to(dev), warm, steps, flush)
+        s.destroy()
+        out[key] = {"value": n_envs / (ms / 1e3), "ms_per_step": ms}
+    out["unit"] = "env-steps/s"
+    return out
 
 
 def adjoint_measure(dev, n_envs=1024, steps=64, checkpoint=16, reps=2):
@@ -400,6 +446,7 @@ def main():
     ap.add_argument("--graph", action="store_true", help="replay each step as a captured CUDA graph")
     ap.add_argument("--autotune", action="store_true", help="autotune the launch knobs during warm-up")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint (differentiable rollout) measurement")
+    ap.add_argument("--no-variants", action="store_true", help="skip the 8192 / 16384-env and CUDA-graph lines")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per step-kernel launch from an ncu capture of the same kernel")
     args = ap.parse_args()
