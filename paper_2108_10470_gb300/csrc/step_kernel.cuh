@@ -250,6 +250,114 @@ __device__ __forceinline__ void tangent_basis(V3 n, V3& t1, V3& t2) {
 // rowa (int per row): limit rows: g | side << 8 | jd << 16; contact rows: c | dir << 8
 // (dir 0 = normal e_z, 1 = e_x, 2 = e_y).
 
+struct Mat9 { float m[9]; };
+
+// Capsule-box pair contacts of one env (lane = pair, in chunks of G), appended to the contact
+// records after the n_con ground contacts in pair / slot order; returns the new count. A separate
+// function (not inlined) so its register pressure does not spill into the rest of the step.
+template <int G>
+__device__ __noinline__ int pair_contacts(const EnvTypeTable* __restrict__ T, const int lane, const Mat9 Rw, const V3 P,
+                                          const V3 rp, float* s_con, int* s_coni, const int CC, int n_con,
+                                          const float coff) {
+  for (int pc = 0; pc < T->n_pairs; pc += G) {
+    const int p = pc + lane;
+    const bool isp = p < T->n_pairs;
+    const int sa = isp ? T->pair_a[p] : 0, sb = isp ? T->pair_b[p] : 0;
+    const bool a_cap = T->shape_type[sa] == kCapsule;
+    const int sc = a_cap ? sa : sb, sx = a_cap ? sb : sa;  // the capsule and the box
+    const int lc = T->shape_link[sc], lx = T->shape_link[sx];
+    const int rc = T->aroot[lc], rxl = T->aroot[lx];
+    float Rc[9], Rx[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) { Rc[k] = Grp<G>::get(Rw.m[k], lc); Rx[k] = Grp<G>::get(Rw.m[k], lx); }
+    const V3 Pc = v3(Grp<G>::get(P.x, lc), Grp<G>::get(P.y, lc), Grp<G>::get(P.z, lc));
+    const V3 Px = v3(Grp<G>::get(P.x, lx), Grp<G>::get(P.y, lx), Grp<G>::get(P.z, lx));
+    const V3 Oc = v3(Grp<G>::get(rp.x, rc), Grp<G>::get(rp.y, rc), Grp<G>::get(rp.z, rc));
+    const V3 Ox = v3(Grp<G>::get(rp.x, rxl), Grp<G>::get(rp.y, rxl), Grp<G>::get(rp.z, rxl));
+    unsigned pk = 0u;
+    V3 pn[kPairSlots], px[kPairSlots];
+    float pd[kPairSlots];
+    V3 Rb3[3];
+    V3 cb = v3(0.f, 0.f, 0.f);
+    if (isp) {
+      float Rsh[9], Rcs[9], Rb[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) Rsh[k] = T->shape_rot[k][sc];
+      mm(Rc, Rsh, Rcs);
+#pragma unroll
+      for (int k = 0; k < 9; ++k) Rsh[k] = T->shape_rot[k][sx];
+      mm(Rx, Rsh, Rb);
+      // everything relative to the box actor's origin
+      const V3 cc = Pc + mv(Rc, v3(T->shape_pos[0][sc], T->shape_pos[1][sc], T->shape_pos[2][sc])) + (Oc - Ox);
+      cb = Px + mv(Rx, v3(T->shape_pos[0][sx], T->shape_pos[1][sx], T->shape_pos[2][sx]));
+      const float r = T->shape_size[0][sc], hl = T->shape_size[1][sc];
+      const V3 ax = v3(Rcs[0], Rcs[3], Rcs[6]);
+      const V3 e = v3(T->shape_size[0][sx], T->shape_size[1][sx], T->shape_size[2][sx]);
+      Rb3[0] = v3(Rb[0], Rb[3], Rb[6]);  // box axes (columns) in world
+      Rb3[1] = v3(Rb[1], Rb[4], Rb[7]);
+      Rb3[2] = v3(Rb[2], Rb[5], Rb[8]);
+      const V3 w0 = cc - ax * hl - cb, w1 = cc + ax * hl - cb;
+      const V3 p0 = v3(dot(Rb3[0], w0), dot(Rb3[1], w0), dot(Rb3[2], w0));
+      const V3 p1 = v3(dot(Rb3[0], w1), dot(Rb3[1], w1), dot(Rb3[2], w1));
+      const V3 dv = p1 - p0;
+      const float tstar = segment_box_closest_t(p0, dv, e);
+      float ta, tb;
+      const bool clip = face_clip(p0, dv, e, r, tstar, ta, tb);
+#pragma unroll
+      for (int slot = 0; slot < kPairSlots; ++slot) {
+        float t = (slot == 0) ? 0.f : ((slot == 1) ? 1.f : ((slot == 2) ? ta : ((slot == 3) ? tb : tstar)));
+        bool ok = true;
+        if (slot >= 2) {
+          if (slot < 4 && !clip) ok = false;
+          if (slot == 3 && !(ta < tb)) ok = false;
+          if (!(t > 0.f && t < 1.f)) ok = false;
+        }
+        if (ok) {
+          sphere_box(p0 + dv * t, r, e, pn[slot], pd[slot], px[slot]);
+          if (pd[slot] < coff) pk |= 1u << slot;
+        }
+      }
+    }
+    int nchunk;
+    const int pbase = n_con + Grp<G>::excl_scan(__popc(pk), lane, &nchunk);
+    if (isp && pk) {
+      int o = pbase;
+      const int ao = a_cap ? rc : rxl, bo = a_cap ? rxl : rc;   // actor roots of bodies a and b
+      const V3 Oa = a_cap ? Oc : Ox, Ob = a_cap ? Ox : Oc;
+      const float mu = fmaxf(T->shape_fr[sa], T->shape_fr[sb]);
+      (void)ao; (void)bo;
+#pragma unroll
+      for (int slot = 0; slot < kPairSlots; ++slot) {
+        if (!((pk >> slot) & 1u)) continue;
+        V3 nw = Rb3[0] * pn[slot].x + Rb3[1] * pn[slot].y + Rb3[2] * pn[slot].z;  // box -> capsule
+        if (!a_cap) nw = nw * -1.f;
+        const V3 xw = cb + Rb3[0] * px[slot].x + Rb3[1] * px[slot].y + Rb3[2] * px[slot].z + (Ox - Oa);
+        const V3 dob = Ob - Oa;
+        s_con[0 * CC + o] = xw.x;
+        s_con[1 * CC + o] = xw.y;
+        s_con[2 * CC + o] = xw.z;
+        s_con[3 * CC + o] = pd[slot];
+        s_con[4 * CC + o] = mu;
+        s_coni[5 * CC + o] = a_cap ? lc : lx;
+        s_coni[6 * CC + o] = T->n_ground_cand + kPairSlots * p + slot;
+        s_coni[7 * CC + o] = sa;
+        s_coni[8 * CC + o] = slot;
+        s_coni[9 * CC + o] = a_cap ? lx : lc;
+        s_coni[10 * CC + o] = sb;
+        s_con[11 * CC + o] = nw.x;
+        s_con[12 * CC + o] = nw.y;
+        s_con[13 * CC + o] = nw.z;
+        s_con[14 * CC + o] = dob.x;
+        s_con[15 * CC + o] = dob.y;
+        s_con[16 * CC + o] = dob.z;
+        ++o;
+      }
+    }
+    n_con += nchunk;
+  }
+  return n_con;
+}
+
 // ---------------------------------------------------------------------------------------------
 // One substep loop of one environment by one group of G lanes. grp indexes the launch's env list
 // (grp >= n_launch_envs: a dead group, which shadows the last env and never stores); sm is the
@@ -550,102 +658,12 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
           }
         }
       }
-      // ---- capsule-box pairs (lane = pair, in chunks of G), appended in pair / slot order ----
-      for (int pc = 0; has_pairs && pc < T->n_pairs; pc += G) {
-        const int p = pc + lane;
-        const bool isp = p < T->n_pairs;
-        const int sa = isp ? T->pair_a[p] : 0, sb = isp ? T->pair_b[p] : 0;
-        const bool a_cap = T->shape_type[sa] == kCapsule;
-        const int sc = a_cap ? sa : sb, sx = a_cap ? sb : sa;  // the capsule and the box
-        const int lc = T->shape_link[sc], lx = T->shape_link[sx];
-        const int rc = T->aroot[lc], rxl = T->aroot[lx];
-        float Rc[9], Rx[9];
+      // ---- capsule-box pairs, appended in pair / slot order ----
+      if (has_pairs) {
+        Mat9 rw9;
 #pragma unroll
-        for (int k = 0; k < 9; ++k) { Rc[k] = Grp<G>::get(Rw[k], lc); Rx[k] = Grp<G>::get(Rw[k], lx); }
-        const V3 Pc = v3(Grp<G>::get(P.x, lc), Grp<G>::get(P.y, lc), Grp<G>::get(P.z, lc));
-        const V3 Px = v3(Grp<G>::get(P.x, lx), Grp<G>::get(P.y, lx), Grp<G>::get(P.z, lx));
-        const V3 Oc = v3(Grp<G>::get(rp.x, rc), Grp<G>::get(rp.y, rc), Grp<G>::get(rp.z, rc));
-        const V3 Ox = v3(Grp<G>::get(rp.x, rxl), Grp<G>::get(rp.y, rxl), Grp<G>::get(rp.z, rxl));
-        unsigned pk = 0u;
-        V3 pn[kPairSlots], px[kPairSlots];
-        float pd[kPairSlots];
-        V3 Rb3[3];
-        V3 cb = v3(0.f, 0.f, 0.f);
-        if (isp) {
-          float Rsh[9], Rcs[9], Rb[9];
-#pragma unroll
-          for (int k = 0; k < 9; ++k) Rsh[k] = T->shape_rot[k][sc];
-          mm(Rc, Rsh, Rcs);
-#pragma unroll
-          for (int k = 0; k < 9; ++k) Rsh[k] = T->shape_rot[k][sx];
-          mm(Rx, Rsh, Rb);
-          // everything relative to the box actor's origin
-          const V3 cc = Pc + mv(Rc, v3(T->shape_pos[0][sc], T->shape_pos[1][sc], T->shape_pos[2][sc])) + (Oc - Ox);
-          cb = Px + mv(Rx, v3(T->shape_pos[0][sx], T->shape_pos[1][sx], T->shape_pos[2][sx]));
-          const float r = T->shape_size[0][sc], hl = T->shape_size[1][sc];
-          const V3 ax = v3(Rcs[0], Rcs[3], Rcs[6]);
-          const V3 e = v3(T->shape_size[0][sx], T->shape_size[1][sx], T->shape_size[2][sx]);
-          Rb3[0] = v3(Rb[0], Rb[3], Rb[6]);  // box axes (columns) in world
-          Rb3[1] = v3(Rb[1], Rb[4], Rb[7]);
-          Rb3[2] = v3(Rb[2], Rb[5], Rb[8]);
-          const V3 w0 = cc - ax * hl - cb, w1 = cc + ax * hl - cb;
-          const V3 p0 = v3(dot(Rb3[0], w0), dot(Rb3[1], w0), dot(Rb3[2], w0));
-          const V3 p1 = v3(dot(Rb3[0], w1), dot(Rb3[1], w1), dot(Rb3[2], w1));
-          const V3 dv = p1 - p0;
-          const float tstar = segment_box_closest_t(p0, dv, e);
-          float ta, tb;
-          const bool clip = face_clip(p0, dv, e, r, tstar, ta, tb);
-#pragma unroll
-          for (int slot = 0; slot < kPairSlots; ++slot) {
-            float t = (slot == 0) ? 0.f : ((slot == 1) ? 1.f : ((slot == 2) ? ta : ((slot == 3) ? tb : tstar)));
-            bool ok = true;
-            if (slot >= 2) {
-              if (slot < 4 && !clip) ok = false;
-              if (slot == 3 && !(ta < tb)) ok = false;
-              if (!(t > 0.f && t < 1.f)) ok = false;
-            }
-            if (ok) {
-              sphere_box(p0 + dv * t, r, e, pn[slot], pd[slot], px[slot]);
-              if (pd[slot] < coff) pk |= 1u << slot;
-            }
-          }
-        }
-        int nchunk;
-        const int pbase = n_con + Grp<G>::excl_scan(__popc(pk), lane, &nchunk);
-        if (isp && pk) {
-          int o = pbase;
-          const int ao = a_cap ? rc : rxl, bo = a_cap ? rxl : rc;   // actor roots of bodies a and b
-          const V3 Oa = a_cap ? Oc : Ox, Ob = a_cap ? Ox : Oc;
-          const float mu = fmaxf(T->shape_fr[sa], T->shape_fr[sb]);
-          (void)ao; (void)bo;
-#pragma unroll
-          for (int slot = 0; slot < kPairSlots; ++slot) {
-            if (!((pk >> slot) & 1u)) continue;
-            V3 nw = Rb3[0] * pn[slot].x + Rb3[1] * pn[slot].y + Rb3[2] * pn[slot].z;  // box -> capsule
-            if (!a_cap) nw = nw * -1.f;
-            const V3 xw = cb + Rb3[0] * px[slot].x + Rb3[1] * px[slot].y + Rb3[2] * px[slot].z + (Ox - Oa);
-            const V3 dob = Ob - Oa;
-            s_con[0 * CC + o] = xw.x;
-            s_con[1 * CC + o] = xw.y;
-            s_con[2 * CC + o] = xw.z;
-            s_con[3 * CC + o] = pd[slot];
-            s_con[4 * CC + o] = mu;
-            s_coni[5 * CC + o] = a_cap ? lc : lx;
-            s_coni[6 * CC + o] = T->n_ground_cand + kPairSlots * p + slot;
-            s_coni[7 * CC + o] = sa;
-            s_coni[8 * CC + o] = slot;
-            s_coni[9 * CC + o] = a_cap ? lx : lc;
-            s_coni[10 * CC + o] = sb;
-            s_con[11 * CC + o] = nw.x;
-            s_con[12 * CC + o] = nw.y;
-            s_con[13 * CC + o] = nw.z;
-            s_con[14 * CC + o] = dob.x;
-            s_con[15 * CC + o] = dob.y;
-            s_con[16 * CC + o] = dob.z;
-            ++o;
-          }
-        }
-        n_con += nchunk;
+        for (int k = 0; k < 9; ++k) rw9.m[k] = Rw[k];
+        n_con = pair_contacts<G>(T, lane, rw9, P, rp, s_con, s_coni, CC, n_con, coff);
       }
       // limit rows in DOF order: link lanes with a limited joint
       int lf = 0;
