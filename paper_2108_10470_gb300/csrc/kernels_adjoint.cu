@@ -11,9 +11,11 @@ namespace artsim {
 
 namespace {
 
-// Input component of direction `dir` of an env with na actors, nj joint DOFs and nc cache entries.
+// Input component of direction `dir` of an env with na actors and nj joint DOFs: root state (13
+// per actor), DOF state (2 per joint DOF), actuation, then the read impulse-cache slots.
 template <int K>
-__device__ __forceinline__ Dn<K>* input_slot(TanState<K>& s, int dir, int na, int nj, int nc, int* where) {
+__device__ __forceinline__ Dn<K>* input_slot(TanState<K>& s, int dir, int na, int nj, const int* slots, int nread,
+                                             int* where) {
   if (dir < 13 * na) {
     const int a = dir / 13, c = dir % 13;
     *where = 0;
@@ -27,7 +29,7 @@ __device__ __forceinline__ Dn<K>* input_slot(TanState<K>& s, int dir, int na, in
   dir -= 2 * nj;
   if (dir < nj) { *where = 2; return &s.act[dir]; }
   dir -= nj;
-  if (dir < nc) { *where = 3; return &s.cache[dir]; }
+  if (dir < nread) { *where = 3; return &s.cache[slots[dir]]; }
   *where = -1;
   return nullptr;
 }
@@ -51,32 +53,28 @@ __global__ void __launch_bounds__(64) tangent_step_kernel(const __grid_constant_
   unsigned free_mask = 0u;
   for (int l = 0; l < T->n_links; ++l)
     if (T->parent[l] < 0 && T->jtype[l] == kFree) free_mask |= 1u << T->actor[l];
-  for (int a = 0; a < na; ++a) {
-    const float* r = V.root + (size_t)(abase + a) * 13;
-    const bool fr = (free_mask >> a) & 1u;
-    for (int k = 0; k < 3; ++k) {
-      s.rp[a][k] = Dn<K>(r[k]);
-      s.rv[a][k] = Dn<K>(fr ? r[7 + k] : 0.f);
-      s.rw[a][k] = Dn<K>(fr ? r[10 + k] : 0.f);
+  auto load = [&]() {
+    for (int a = 0; a < na; ++a) {
+      const float* r = V.root + (size_t)(abase + a) * 13;
+      const bool fr = (free_mask >> a) & 1u;
+      for (int k = 0; k < 3; ++k) {
+        s.rp[a][k] = Dn<K>(r[k]);
+        s.rv[a][k] = Dn<K>(fr ? r[7 + k] : 0.f);
+        s.rw[a][k] = Dn<K>(fr ? r[10 + k] : 0.f);
+      }
+      for (int k = 0; k < 4; ++k) s.rq[a][k] = Dn<K>(r[3 + k]);
     }
-    for (int k = 0; k < 4; ++k) s.rq[a][k] = Dn<K>(r[3 + k]);
-  }
-  for (int j = 0; j < nj; ++j) {
-    s.q[j] = Dn<K>(V.dof[(size_t)(dbase + j) * 2]);
-    s.qd[j] = Dn<K>(V.dof[(size_t)(dbase + j) * 2 + 1]);
-    s.act[j] = Dn<K>(V.act[dbase + j]);
-  }
-  for (int i = 0; i < nc; ++i) s.cache[i] = Dn<K>(V.cache[cbase + i]);
+    for (int j = 0; j < nj; ++j) {
+      s.q[j] = Dn<K>(V.dof[(size_t)(dbase + j) * 2]);
+      s.qd[j] = Dn<K>(V.dof[(size_t)(dbase + j) * 2 + 1]);
+      s.act[j] = Dn<K>(V.act[dbase + j]);
+    }
+    for (int i = 0; i < nc; ++i) s.cache[i] = Dn<K>(V.cache[cbase + i]);
+  };
+  bool ok = true;
 
-  if (V.mode == 0) {  // adjoint: seed this lane's directions
-    for (int k = 0; k < K; ++k) {
-      const int dir = V.dir_base + k * 32 + lane;
-      int where;
-      Dn<K>* x = input_slot<K>(s, dir, na, nj, nc, &where);
-      const bool fixed_vel = where == 0 && (dir % 13) >= 7 && !((free_mask >> (dir / 13)) & 1u);
-      if (x && !fixed_vel) x->d[k] = 1.f;
-    }
-  } else {  // tangent: the caller's direction in slot 0
+  if (V.mode == 1) {  // tangent: the caller's direction in slot 0
+    load();
     for (int a = 0; a < na; ++a) {
       const float* t = V.t_root + (size_t)(abase + a) * 13;
       const bool fr = (free_mask >> a) & 1u;
@@ -93,41 +91,63 @@ __global__ void __launch_bounds__(64) tangent_step_kernel(const __grid_constant_
       s.act[j].d[0] = V.t_act[dbase + j];
     }
     for (int i = 0; i < nc; ++i) s.cache[i].d[0] = V.t_cache[cbase + i];
-  }
-
-  bool ok = true;
-  for (int sub = 0; sub < A.substeps && ok; ++sub) ok = tangent_substep<K>(A, T, s, w);
-
-  if (V.mode == 0) {
-    // input gradient of each seeded direction: sum over outputs of g_out * d(output)/d(direction)
-    for (int k = 0; k < K; ++k) {
-      const int dir = V.dir_base + k * 32 + lane;
-      int where;
-      if (!input_slot<K>(s, dir, na, nj, nc, &where)) continue;
-      float g = 0.f;
-      if (V.g_root)
-        for (int a = 0; a < na; ++a) {
-          const float* gr = V.g_root + (size_t)(abase + a) * 13;
-          for (int c = 0; c < 3; ++c) g += gr[c] * s.rp[a][c].d[k] + gr[7 + c] * s.rv[a][c].d[k] + gr[10 + c] * s.rw[a][c].d[k];
-          for (int c = 0; c < 4; ++c) g += gr[3 + c] * s.rq[a][c].d[k];
-        }
-      if (V.g_dof)
-        for (int j = 0; j < nj; ++j)
-          g += V.g_dof[(size_t)(dbase + j) * 2] * s.q[j].d[k] + V.g_dof[(size_t)(dbase + j) * 2 + 1] * s.qd[j].d[k];
-      if (V.g_cache)
-        for (int i = 0; i < nc; ++i) g += V.g_cache[cbase + i] * s.cache[i].d[k];
-      if (!ok) g = 0.f;
-      int d = dir;
-      if (where == 0) V.gi_root[(size_t)(abase + d / 13) * 13 + d % 13] = g;
-      d -= 13 * na;
-      if (where == 1) V.gi_dof[(size_t)(dbase + (d >> 1)) * 2 + (d & 1)] = g;
-      d -= 2 * nj;
-      if (where == 2) V.gi_act[dbase + d] = g;
-      d -= nj;
-      if (where == 3) V.gi_cache[cbase + d] = g;
+    for (int sub = 0; sub < A.substeps && ok; ++sub) ok = tangent_substep<K>(A, T, s, w);
+  } else {
+    // adjoint. Directions: the state and actuation components, then only the impulse-cache slots
+    // the first substep reads (the others cannot affect the step); passes of 32 K directions.
+    load();
+    int slots[kTanMaxRows];
+    int nread = read_slots<K>(A, T, s, w, slots);
+    if (nread < 0) { ok = false; nread = 0; }
+    const int n_dirs = 13 * na + 3 * nj + nread;
+    for (int i = lane; i < A.cache_stride; i += 32) V.gi_cache[cbase + i] = 0.f;
+    __syncwarp();
+    for (int base = 0; base < n_dirs && ok; base += 32 * K) {
+      load();
+      for (int k = 0; k < K; ++k) {
+        const int dir = base + k * 32 + lane;
+        int where;
+        Dn<K>* x = input_slot<K>(s, dir, na, nj, slots, nread, &where);
+        const bool fixed_vel = where == 0 && (dir % 13) >= 7 && !((free_mask >> (dir / 13)) & 1u);
+        if (x && !fixed_vel) x->d[k] = 1.f;
+      }
+      for (int sub = 0; sub < A.substeps && ok; ++sub) ok = tangent_substep<K>(A, T, s, w);
+      // input gradient of each seeded direction: sum over outputs of g_out * d(output)/d(direction)
+      for (int k = 0; k < K; ++k) {
+        const int dir = base + k * 32 + lane;
+        int where;
+        if (!input_slot<K>(s, dir, na, nj, slots, nread, &where)) continue;
+        float g = 0.f;
+        if (V.g_root)
+          for (int a = 0; a < na; ++a) {
+            const float* gr = V.g_root + (size_t)(abase + a) * 13;
+            for (int c = 0; c < 3; ++c) g += gr[c] * s.rp[a][c].d[k] + gr[7 + c] * s.rv[a][c].d[k] + gr[10 + c] * s.rw[a][c].d[k];
+            for (int c = 0; c < 4; ++c) g += gr[3 + c] * s.rq[a][c].d[k];
+          }
+        if (V.g_dof)
+          for (int j = 0; j < nj; ++j)
+            g += V.g_dof[(size_t)(dbase + j) * 2] * s.q[j].d[k] + V.g_dof[(size_t)(dbase + j) * 2 + 1] * s.qd[j].d[k];
+        if (V.g_cache)
+          for (int i = 0; i < nc; ++i) g += V.g_cache[cbase + i] * s.cache[i].d[k];
+        if (!ok) g = 0.f;
+        int d = dir;
+        if (where == 0) V.gi_root[(size_t)(abase + d / 13) * 13 + d % 13] = g;
+        d -= 13 * na;
+        if (where == 1) V.gi_dof[(size_t)(dbase + (d >> 1)) * 2 + (d & 1)] = g;
+        d -= 2 * nj;
+        if (where == 2) V.gi_act[dbase + d] = g;
+        d -= nj;
+        if (where == 3) V.gi_cache[cbase + slots[d]] = g;
+      }
     }
-    if (V.dir_base == 0)
-      for (int i = nc + lane; i < A.cache_stride; i += 32) V.gi_cache[cbase + i] = 0.f;
+    if (!ok) {  // a failed step has no derivative: every input gradient of the env is zero
+      __syncwarp();
+      for (int i = lane; i < 13 * na; i += 32) V.gi_root[(size_t)abase * 13 + i] = 0.f;
+      for (int i = lane; i < 2 * nj; i += 32) V.gi_dof[(size_t)dbase * 2 + i] = 0.f;
+      for (int i = lane; i < nj; i += 32) V.gi_act[dbase + i] = 0.f;
+      __syncwarp();
+      for (int i = lane; i < A.cache_stride; i += 32) V.gi_cache[cbase + i] = 0.f;
+    }
   }
   if (lane == 0) {
     for (int a = 0; a < na; ++a) {

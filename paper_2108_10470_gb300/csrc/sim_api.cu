@@ -1025,13 +1025,12 @@ int sim_step_vjp(sim_handle h, const sim_vjp_buffers* b, float dt, int32_t subst
     const EnvTypeTable& T = h->types[t].tab;
     TypeArgs ta;
     fill_type(h, t, ta);
-    const int dirs = 13 * T.n_actors + 3 * T.n_jdof + T.cache_len;
-    const int K = tangent_lanes_per_dir(dirs);
-    for (int base = 0; base < dirs; base += 32 * K) {
-      v.dir_base = base;
-      const cudaError_t e = launch_tangent_kernel(K, a, ta, v, h->stream);
-      if (e != cudaSuccess) return cuda_fail(e, "tangent_step_kernel launch (adjoint)");
-    }
+    // directions: state and actuation, plus the impulse-cache slots the env's first substep reads
+    // (known only in the kernel; budgeted here at 24, more run as further passes in the kernel)
+    const int K = tangent_lanes_per_dir(13 * T.n_actors + 3 * T.n_jdof + 24);
+    v.dir_base = 0;
+    const cudaError_t e = launch_tangent_kernel(K, a, ta, v, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "tangent_step_kernel launch (adjoint)");
   }
   return SIM_OK;
 }

@@ -337,6 +337,111 @@ template <int K> __device__ void tangent_dynamics(const StepArgs& A, const EnvTy
   }
 }
 
+// Ground contacts of the current poses (w.R, w.P) in shape / slot order into w.cx, w.cd, w.clink,
+// w.ccand, w.cmu; returns their count, or -1 past kTanMaxCon.
+template <int K> __device__ int tangent_contacts(const StepArgs& A, const EnvTypeTable* T, const TanState<K>& s,
+                                                 TanWork<K>& w) {
+  const float coff = A.contact_offset;
+  int nc = 0;
+  for (int sh = 0; sh < T->n_shapes; ++sh) {
+    const int l = T->shape_link[sh], st = T->shape_type[sh], a = T->actor[l];
+    Dn<K> Rsh[9], Rs[9];
+    for (int k = 0; k < 9; ++k) Rsh[k] = Dn<K>(T->shape_rot[k][sh]);
+    dmm<K>(w.R[l], Rsh, Rs);
+    const DV3<K> cs = dv3<K>(w.P[l][0], w.P[l][1], w.P[l][2]) +
+                      dmv<K>(w.R[l], dv3<K>(Dn<K>(T->shape_pos[0][sh]), Dn<K>(T->shape_pos[1][sh]), Dn<K>(T->shape_pos[2][sh])));
+    const Dn<K> oz = s.rp[a][2];
+    const float s0 = T->shape_size[0][sh], s1 = T->shape_size[1][sh], s2 = T->shape_size[2][sh];
+    const int nk = (st == kSphere) ? 1 : (st == kCapsule ? 2 : 8);
+    for (int k = 0; k < nk; ++k) {
+      DV3<K> x;
+      Dn<K> zc;
+      if (st == kSphere) {
+        x = dv3<K>(cs.x, cs.y, cs.z - Dn<K>(s0));
+        zc = (oz + cs.z) - Dn<K>(s0);
+      } else if (st == kCapsule) {
+        const DV3<K> ax = dv3<K>(Rs[0], Rs[3], Rs[6]);
+        const DV3<K> e = (k == 0) ? cs - ax * Dn<K>(s1) : cs + ax * Dn<K>(s1);
+        x = dv3<K>(e.x, e.y, e.z - Dn<K>(s0));
+        zc = (oz + e.z) - Dn<K>(s0);
+      } else {
+        const DV3<K> loc = dv3<K>(Dn<K>((k & 4) ? s0 : -s0), Dn<K>((k & 2) ? s1 : -s1), Dn<K>((k & 1) ? s2 : -s2));
+        x = cs + dmv<K>(Rs, loc);
+        zc = oz + x.z;
+      }
+      if (zc.v < coff) {
+        if (nc >= kTanMaxCon) return -1;
+        w.cx[nc][0] = x.x; w.cx[nc][1] = x.y; w.cx[nc][2] = x.z;
+        w.cd[nc] = zc;
+        w.clink[nc] = l;
+        w.ccand[nc] = T->cand_off[sh] + k;
+        w.cmu[nc] = T->shape_mu[sh];
+        ++nc;
+      }
+    }
+  }
+  return nc;
+}
+
+// Link poses only (w.R, w.P), as in tangent_dynamics.
+template <int K> __device__ void tangent_poses(const EnvTypeTable* T, const TanState<K>& s, TanWork<K>& w) {
+  for (int l = 0; l < T->n_links; ++l) {
+    const int par = T->parent[l], jt = T->jtype[l], jd = T->jdof[l];
+    if (par < 0) {
+      dquat_to_mat<K>(s.rq[T->actor[l]], w.R[l]);
+      for (int k = 0; k < 3; ++k) w.P[l][k] = Dn<K>(0.f);
+      continue;
+    }
+    Dn<K> Rpj[9], RB[9];
+    for (int k = 0; k < 9; ++k) Rpj[k] = Dn<K>(T->prot[k][l]);
+    dmm<K>(w.R[par], Rpj, RB);
+    const DV3<K> jax = dv3<K>(Dn<K>(T->axis[0][l]), Dn<K>(T->axis[1][l]), Dn<K>(T->axis[2][l]));
+    const DV3<K> pp = dv3<K>(Dn<K>(T->ppos[0][l]), Dn<K>(T->ppos[1][l]), Dn<K>(T->ppos[2][l]));
+    const DV3<K> Pp = dv3<K>(w.P[par][0], w.P[par][1], w.P[par][2]);
+    DV3<K> Pl;
+    if (jt == kRevolute) {
+      Dn<K> sn, cs;
+      dsincos<K>(s.q[jd], sn, cs);
+      const Dn<K> t = Dn<K>(1.f) - cs;
+      const float ax = T->axis[0][l], ay = T->axis[1][l], az = T->axis[2][l];
+      Dn<K> RJ[9];
+      RJ[0] = t * (ax * ax) + cs;      RJ[1] = t * (ax * ay) - sn * az; RJ[2] = t * (ax * az) + sn * ay;
+      RJ[3] = t * (ax * ay) + sn * az; RJ[4] = t * (ay * ay) + cs;      RJ[5] = t * (ay * az) - sn * ax;
+      RJ[6] = t * (ax * az) - sn * ay; RJ[7] = t * (ay * az) + sn * ax; RJ[8] = t * (az * az) + cs;
+      dmm<K>(RB, RJ, w.R[l]);
+      Pl = Pp + dmv<K>(w.R[par], pp);
+    } else if (jt == kPrismatic) {
+      for (int k = 0; k < 9; ++k) w.R[l][k] = RB[k];
+      Pl = Pp + dmv<K>(w.R[par], pp + dmv<K>(Rpj, jax * s.q[jd]));
+    } else {
+      for (int k = 0; k < 9; ++k) w.R[l][k] = RB[k];
+      Pl = Pp + dmv<K>(w.R[par], pp);
+    }
+    w.P[l][0] = Pl.x; w.P[l][1] = Pl.y; w.P[l][2] = Pl.z;
+  }
+}
+
+// Impulse-cache slots the step's first substep reads (the warm start of each of its constraint
+// rows: joint limits, then contacts' normal and friction rows), into slots[]; returns their count,
+// or -1 past the capacities.
+template <int K> __device__ int read_slots(const StepArgs& A, const EnvTypeTable* T, const TanState<K>& s,
+                                           TanWork<K>& w, int* slots) {
+  tangent_poses<K>(T, s, w);
+  const int nc = tangent_contacts<K>(A, T, s, w);
+  if (nc < 0) return -1;
+  int m = 0;
+  for (int l = 0; l < T->n_links; ++l) {
+    const int jt = T->jtype[l];
+    if (T->parent[l] < 0 || !(jt == kRevolute || jt == kPrismatic) || !T->has_limit[l]) continue;
+    const int jd = T->jdof[l];
+    if (s.q[jd].v - T->lo[l] < A.limit_margin) slots[m++] = 3 * T->n_cand + 2 * jd;
+    if (T->hi[l] - s.q[jd].v < A.limit_margin) slots[m++] = 3 * T->n_cand + 2 * jd + 1;
+  }
+  for (int c = 0; c < nc; ++c)
+    for (int d = 0; d < 3; ++d) slots[m++] = 3 * w.ccand[c] + d;
+  return m;
+}
+
 // One substep in dual arithmetic. Returns false if a pivot or a capacity check fails.
 template <int K> __device__ bool tangent_substep(const StepArgs& A, const EnvTypeTable* T, TanState<K>& s,
                                                  TanWork<K>& w) {
@@ -370,46 +475,8 @@ template <int K> __device__ bool tangent_substep(const StepArgs& A, const EnvTyp
     w.z[i] = x + w.rhs[i] * h;
     w.dz[i] = Dn<K>(0.f);
   }
-  // ---- ground contacts (shape order, then slot) ----
-  const float coff = A.contact_offset;
-  int nc = 0;
-  for (int sh = 0; sh < T->n_shapes; ++sh) {
-    const int l = T->shape_link[sh], st = T->shape_type[sh], a = T->actor[l];
-    Dn<K> Rsh[9], Rs[9];
-    for (int k = 0; k < 9; ++k) Rsh[k] = Dn<K>(T->shape_rot[k][sh]);
-    dmm<K>(w.R[l], Rsh, Rs);
-    const DV3<K> cs = dv3<K>(w.P[l][0], w.P[l][1], w.P[l][2]) +
-                      dmv<K>(w.R[l], dv3<K>(Dn<K>(T->shape_pos[0][sh]), Dn<K>(T->shape_pos[1][sh]), Dn<K>(T->shape_pos[2][sh])));
-    const Dn<K> oz = s.rp[a][2];
-    const float s0 = T->shape_size[0][sh], s1 = T->shape_size[1][sh], s2 = T->shape_size[2][sh];
-    const int nk = (st == kSphere) ? 1 : (st == kCapsule ? 2 : 8);
-    for (int k = 0; k < nk; ++k) {
-      DV3<K> x;
-      Dn<K> zc;
-      if (st == kSphere) {
-        x = dv3<K>(cs.x, cs.y, cs.z - Dn<K>(s0));
-        zc = (oz + cs.z) - Dn<K>(s0);
-      } else if (st == kCapsule) {
-        const DV3<K> ax = dv3<K>(Rs[0], Rs[3], Rs[6]);
-        const DV3<K> e = (k == 0) ? cs - ax * Dn<K>(s1) : cs + ax * Dn<K>(s1);
-        x = dv3<K>(e.x, e.y, e.z - Dn<K>(s0));
-        zc = (oz + e.z) - Dn<K>(s0);
-      } else {
-        const DV3<K> loc = dv3<K>(Dn<K>((k & 4) ? s0 : -s0), Dn<K>((k & 2) ? s1 : -s1), Dn<K>((k & 1) ? s2 : -s2));
-        x = cs + dmv<K>(Rs, loc);
-        zc = oz + x.z;
-      }
-      if (zc.v < coff) {
-        if (nc >= kTanMaxCon) return false;
-        w.cx[nc][0] = x.x; w.cx[nc][1] = x.y; w.cx[nc][2] = x.z;
-        w.cd[nc] = zc;
-        w.clink[nc] = l;
-        w.ccand[nc] = T->cand_off[sh] + k;
-        w.cmu[nc] = T->shape_mu[sh];
-        ++nc;
-      }
-    }
-  }
+  const int nc = tangent_contacts<K>(A, T, s, w);
+  if (nc < 0) return false;
   // ---- rows: limits (link order, lower before upper), normals, friction pairs ----
   // row r is described on the fly: r < nl: limit list; then contact normals; then frictions
   int lim_g[2 * kMaxGen], lim_side[2 * kMaxGen], lim_jd[2 * kMaxGen];
