@@ -113,9 +113,14 @@ typedef struct {
  * graph on first use (again whenever dt or substeps change, or the plan changes) and replay it;
  * bit 3 (SIM_FLAG_BODY_FORCES) applies the RIGID_BODY_FORCE view every substep; bit 4
  * (SIM_FLAG_RIGID_BODY_STATE) writes the RIGID_BODY_STATE view after every step; bit 5
- * (SIM_FLAG_DOF_FORCE) writes the DOF_FORCE view every step. */
+ * (SIM_FLAG_DOF_FORCE) writes the DOF_FORCE view every step; bit 6 (SIM_FLAG_ROW_SOLVER) runs
+ * every substep's Gauss-Seidel solve in the row form (each row's J v and separation as group
+ * reductions over Y = L^-1 J^T) instead of the Delassus form (W = J M^-1 J^T per substep, one
+ * row value per lane), which is used otherwise whenever W fits beside Y; the two agree to FP32
+ * rounding (paper, Sec. "Physics Simulation": the TGS solve; both forms keep its row order and
+ * projections). */
 enum { SIM_FLAG_SIGNATURE = 1, SIM_FLAG_PERSISTENT = 2, SIM_FLAG_GRAPH = 4, SIM_FLAG_BODY_FORCES = 8,
-       SIM_FLAG_RIGID_BODY_STATE = 16, SIM_FLAG_DOF_FORCE = 32 };
+       SIM_FLAG_RIGID_BODY_STATE = 16, SIM_FLAG_DOF_FORCE = 32, SIM_FLAG_ROW_SOLVER = 64 };
 typedef struct {
   float gravity[3];
   int32_t pos_iters;       /* >= 1 biased (position) iterations                  */

@@ -19,9 +19,16 @@ LIB_PATH = os.path.join(HERE, "libartsim.so")
 UNITS = ("kernels_shared.cu", "kernels_global.cu", "kernels_persistent.cu", "kernels_adjoint.cu", "sim_api.cu")
 SOURCES = [os.path.join(CSRC, f) for f in UNITS + ("step_kernel.cuh", "tangent_step.cuh", "sim_internal.h",
                                                    "launch.h")] + \
-    [os.path.join(INCLUDE, "sim.h")]
+    [os.path.join(INCLUDE, "sim.h"), os.path.abspath(__file__)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMPILE_FLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC"]
+# The step kernels divide and take square roots with the approximate forms (a few ulp) instead
+# of the IEEE-rounded sequences, which sit on the Cholesky pivot chain and in the articulated-body
+# sweeps (humanoid and hand steps 4-5 % faster); the FP32 results move by far less than the
+# tolerance the parity tests derive from the FP32 conditioning of each step. The derivative
+# kernel and the host code keep IEEE division and square root.
+STEP_UNITS = ("kernels_shared.cu", "kernels_global.cu", "kernels_persistent.cu")
+STEP_FLAGS = ["-prec-div=false", "-prec-sqrt=false"]
 LINK_FLAGS = ARCH + ["-shared", "-cudart", "static"]
 
 
@@ -40,8 +47,8 @@ def build_library(force: bool = False, verbose: bool = False) -> str:
     objs = [os.path.join(CSRC, u[:-3] + tag + ".o") for u in UNITS]
 
     def compile_unit(i):
-        cmd = [nvcc()] + COMPILE_FLAGS + (["-Xptxas", "-v"] if verbose else []) + \
-            ["-c", "-o", objs[i], os.path.join(CSRC, UNITS[i])]
+        cmd = [nvcc()] + COMPILE_FLAGS + (STEP_FLAGS if UNITS[i] in STEP_UNITS else []) + \
+            (["-Xptxas", "-v"] if verbose else []) + ["-c", "-o", objs[i], os.path.join(CSRC, UNITS[i])]
         return subprocess.run(cmd, capture_output=True, text=True)
 
     try:

@@ -388,6 +388,7 @@ SmemLayout make_layout(const EnvTypeTable& T, int G, bool rows_global) {
     const int phase = std::max(L * kLinkWords, n * Ly.RS);
     Ly.link = o;
     Ly.Y = o;
+    Ly.ywords = phase;
     o += phase;
     Ly.SD = o; o += 6 * n;
     Ly.M = o; o += n * Ly.MS;
@@ -409,6 +410,7 @@ SmemLayout make_layout(const EnvTypeTable& T, int G, bool rows_global) {
     Ly.rowa = g; g += Ly.rcap;
     Ly.Y = g; g += n * Ly.RS;
     Ly.scratch_words = al4(g);
+    Ly.ywords = Ly.scratch_words - Ly.Y;
     Ly.link = o; o += L * kLinkWords;
     Ly.SD = o; o += 6 * n;
     Ly.M = o; o += n * Ly.MS;

@@ -95,6 +95,8 @@ struct SmemLayout {
   int rowa;   // rcap: row aux (DOF / contact index)
   int rcap;
   int frc;    // 3 per link
+  int ywords; // words from Y to the end of its region: Y (n_gen x (R | 1) for R rows), then the
+              // solver's Delassus block R x R and R accumulated impulses when they fit
   int total;  // words per environment (multiple of 4; = G mod 32 when groups share a warp)
 };
 constexpr int kLinkWords = 37;

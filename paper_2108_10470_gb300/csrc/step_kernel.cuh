@@ -359,6 +359,48 @@ __device__ __noinline__ int pair_contacts(const EnvTypeTable* __restrict__ T, co
 }
 
 // ---------------------------------------------------------------------------------------------
+// Row form of the projected Gauss-Seidel solve in z = L^T v, for substeps whose Delassus block
+// does not fit beside Y (many rows): per row, J_r v = Y_r . z and the separation d_r + Y_r . dz
+// come from two group reductions, and z moves by Y_r dl. Starts from z_free (z0 of the DOF lane)
+// plus the warm start; returns (z, dz) of the lane. The impulses are updated in s_lam.
+template <int G>
+__device__ __noinline__ float2 pgs_row_form(const float* s_Y, const int YS, const float4* s_rowc, float* s_lam,
+                                            const int R, const int Rw_max, const bool isg, const int lane,
+                                            const int npos, const int nvel, const float h, const float hit,
+                                            const float beta, const float vmax, const float z0) {
+  float z = z0, dz = 0.f;
+  if (isg)
+    for (int r = 0; r < R; ++r) z += s_Y[lane * YS + r] * s_lam[r];  // warm start
+  const float inv_hit = 1.f / hit, inv_h = 1.f / h;
+  for (int it = 0; it < npos + nvel; ++it) {
+    const bool pos = it < npos;
+    // two independent group reductions per row, then a branch-free update (selects: measured 7 %
+    // faster on the Ant step than a branch around it)
+    for (int r = 0; r < Rw_max; ++r) {
+      const float y = (isg && r < R) ? s_Y[lane * YS + r] : 0.f;
+      const float4 hc = s_rowc[r];
+      const float yz = Grp<G>::sum(y * z), ydz = Grp<G>::sum(y * dz);
+      const float sep = hc.x + ydz;
+      const int kb = __float_as_int(hc.z);
+      const bool valid = (r < R) && (hc.y > 0.f);
+      const bool fric = (kb & 3) == kRowFriction;
+      const float lam = s_lam[r];
+      const float lim = hc.x * s_lam[(valid && fric) ? (kb >> 2) : 0];
+      const float lf = fminf(fmaxf(lam - yz * hc.y, -lim), lim);
+      const float tp = (sep >= 0.f) ? -sep * inv_hit : fminf(-beta * sep * inv_hit, vmax);
+      const float tv = (sep > 0.f) ? -sep * inv_h : 0.f;
+      const float ln = fmaxf(lam + ((pos ? tp : tv) - yz) * hc.y, 0.f);
+      const float lnew = fric ? lf : ln;
+      const float dl = valid ? lnew - lam : 0.f;
+      z += y * dl;
+      if (valid) s_lam[r] = lnew;  // every lane stores the same value
+    }
+    if (pos) dz += hit * z;
+  }
+  return make_float2(z, dz);
+}
+
+// ---------------------------------------------------------------------------------------------
 // One substep loop of one environment by one group of G lanes. grp indexes the launch's env list
 // (grp >= n_launch_envs: a dead group, which shadows the last env and never stores); sm is the
 // group's shared arena and rb the base of its contact and row blocks (sm itself, or a private
@@ -377,9 +419,9 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
 
   const int L = T->n_links, n = T->n_gen, NS = T->n_shapes;
   const int maxdepth = T->max_depth;
-  const int RS = Ly.RS, MS = Ly.MS, CC = Ly.ccap, RC = Ly.rcap;
+  const int MS = Ly.MS, CC = Ly.ccap;
   float* s_link = sm + Ly.link;  // phase 1: per-link hand-off slots of the inward sweep
-  float* s_Y = rb + Ly.Y;        // phase 2 (aliases phase 1 in shared memory): Y = L^-1 J^T, n x RS
+  float* s_Y = rb + Ly.Y;        // phase 2 (aliases phase 1 in shared memory): Y = L^-1 J^T, n x (R | 1)
   float* s_SD = sm + Ly.SD;      // motion subspace column of every generalized DOF
   float* s_M = sm + Ly.M;        // Cholesky factor L (lower), n x MS
   float* s_qdd = sm + Ly.vec;
@@ -940,34 +982,33 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
         if (j == lane) mij += arm;
         m[j] = mij;
       }
-      // right-looking Cholesky, lane i owns row i: L_ik = M_ik / L_kk, M_ij -= L_ik L_jk
+      // right-looking Cholesky, lane i owns row i: L_ik = M_ik / L_kk, M_ij -= L_ik L_jk. The
+      // column loop is not unrolled: the row shifts down one register per column (m[0] holds
+      // M_ik at step k), which keeps the code a few hundred bytes at any G (the unrolled
+      // triangle was 60 KB at G = 32 and the instruction fetch stalled); same operations, same order
       float linv = 1.f;
+      for (int k = 0; k < n; ++k) {
+        float dkk = Grp<G>::get(m[0], k);
+        if (!(dkk > 0.f)) { status |= 2; dkk = 1.f; }
+        const float lkk = sqrtf(dkk), inv = 1.f / lkk;
+        const float lik = (lane > k) ? m[0] * inv : ((lane == k) ? lkk : 0.f);
+        if (lane == k) linv = inv;
+        if (isg && lane >= k) s_M[lane * MS + k] = lik;
 #pragma unroll
-      for (int k = 0; k < G; ++k) {
-        if (k < n) {
-          float dkk = Grp<G>::get(m[k], k);
-          if (!(dkk > 0.f)) { status |= 2; dkk = 1.f; }
-          const float lkk = sqrtf(dkk), inv = 1.f / lkk;
-          const float lik = (lane > k) ? m[k] * inv : ((lane == k) ? lkk : 0.f);
-          m[k] = lik;
-          if (lane == k) linv = inv;
-#pragma unroll
-          for (int j = k + 1; j < G; ++j) {
-            const float ljk = Grp<G>::get(lik, j);
-            if (j <= lane) m[j] -= lik * ljk;
-          }
+        for (int j = 1; j < G; ++j) {
+          if (j >= n - k) break;
+          const float ljk = Grp<G>::get(lik, k + j);
+          m[j - 1] = (k + j <= lane) ? m[j] - lik * ljk : m[j];
         }
       }
-      if (isg) {
-#pragma unroll
-        for (int j = 0; j < G; ++j)
-          if (j <= lane) s_M[lane * MS + j] = m[j];
-        s_Linv[lane] = linv;
-      }
+      if (isg) s_Linv[lane] = linv;
     }
     __syncwarp();
 
     // ======== (a5) Jacobian rows and Y = L^-1 J^T, A = |Y_r|^2, warm start (row mode) ========
+    // Y is n x YS with the odd stride YS = R | 1 of this substep's rows, so that the rest of the
+    // region can hold the Delassus block of the solve below
+    const int YS = R | 1;
     for (int r = lane; r < R; r += G) {
       const float4 hc = s_rowc[r];
       const int a = s_rowa[r];
@@ -1015,36 +1056,44 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
           float ji = 0.f;
           for (int k = 0; k < T->ten_n[tt]; ++k)
             if (T->gdof[T->ten_link[tt][k]] == i) ji += sgn * T->ten_coef[tt][k];
-          for (int k = 0; k < i; ++k) ji -= s_M[i * MS + k] * s_Y[k * RS + r];
+          for (int k = 0; k < i; ++k) ji -= s_M[i * MS + k] * s_Y[k * YS + r];
           const float yi = ji * s_Linv[i];
-          s_Y[i * RS + r] = yi;
+          s_Y[i * YS + r] = yi;
           asum += yi * yi;
         }
       } else {
+        // J_r in registers, then a right-looking forward substitution: y_k = b_k / L_kk and
+        // b_i -= L_ik y_k for i > k (the subtractions of the row-by-row form, in the same order).
+        // The vector shifts down one register per step (y[0] holds b_k), so the loop over k is
+        // not unrolled (the unrolled triangle was 25 KB of code at G = 32)
 #pragma unroll
-      for (int i = 0; i < G; ++i) {
-        if (i < n) {
+        for (int i = 0; i < G; ++i) {
           float ji = 0.f;
-          if (kind == kRowLimit) {
-            ji = (i == gl) ? sgn : 0.f;
-          } else if ((anc >> i) & 1u) {
-            const float* Si = s_SD + 6 * i;
+          if (i < n) {
+            if (kind == kRowLimit) {
+              ji = (i == gl) ? sgn : 0.f;
+            } else if ((anc >> i) & 1u) {
+              const float* Si = s_SD + 6 * i;
 #pragma unroll
-            for (int k = 0; k < 6; ++k) ji += Si[k] * fr[k];
-          } else if ((ancb >> i) & 1u) {
-            const float* Si = s_SD + 6 * i;
+              for (int k = 0; k < 6; ++k) ji += Si[k] * fr[k];
+            } else if ((ancb >> i) & 1u) {
+              const float* Si = s_SD + 6 * i;
 #pragma unroll
-            for (int k = 0; k < 6; ++k) ji += Si[k] * fb[k];
+              for (int k = 0; k < 6; ++k) ji += Si[k] * fb[k];
+            }
           }
-#pragma unroll
-          for (int k = 0; k < i; ++k) ji -= s_M[i * MS + k] * y[k];
-          y[i] = ji * s_Linv[i];
-          s_Y[i * RS + r] = y[i];
-          asum += y[i] * y[i];
-        } else {
-          y[i] = 0.f;
+          y[i] = ji;
         }
-      }
+        for (int k = 0; k < n; ++k) {
+          const float yk = y[0] * s_Linv[k];
+          s_Y[k * YS + r] = yk;
+          asum += yk * yk;
+#pragma unroll
+          for (int j = 1; j < G; ++j) {
+            if (j >= n - k) break;
+            y[j - 1] = y[j] - s_M[(k + j) * MS + k] * yk;
+          }
+        }
       }
       const bool act = asum > 1e-12f;
       const float invA = act ? 1.f / asum : 0.f;
@@ -1053,44 +1102,99 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
     }
     __syncwarp();
 
-    // ======== (a6) TGS-style projected Gauss-Seidel in z = L^T v (DOF mode) ========
-    float z = 0.f, dz = 0.f;
+    // ======== (a6) TGS-style projected Gauss-Seidel in z = L^T v ========
+    // With v = L^-T z, row r's velocity is J_r v = Y_r . z and its separation d_r + J_r dq =
+    // d_r + Y_r . dz; an impulse change dl on row r moves z by Y_r dl.
+    float z0 = 0.f;  // z of the free velocity (DOF lanes)
     if (isg) s_vf[lane] = s_v0[lane] + h * s_qdd[lane];  // v_free
     __syncwarp();
-    if (isg) {
-      for (int k = lane; k < n; ++k) z += s_M[k * MS + lane] * s_vf[k];  // z = L^T v_free
-      for (int r = 0; r < R; ++r) z += s_Y[lane * RS + r] * s_lam[r];     // warm start
-    }
+    if (isg)
+      for (int k = lane; k < n; ++k) z0 += s_M[k * MS + lane] * s_vf[k];  // z = L^T v_free
     const int Rw_max = __reduce_max_sync(kFull, R);
-    {
+    float z = 0.f, dz = 0.f;
+    // The Delassus form serves one env per warp (G = 32: five-level reductions, nothing to share
+    // the warp's issue slots with); at G <= 16 forming W costs more than it saves (measured on the
+    // Ant: +5 %). W and the impulse sums go after Y in its region, or, with the rows in global
+    // scratch, into the shared link slots (free from the inertia pass to the next substep's
+    // inward sweep); flag 64 keeps every substep in the row form.
+    float* s_W = GROWS ? s_link : s_Y + n * YS;
+    const int wcap = GROWS ? L * kLinkWords : Ly.ywords - n * YS;
+    const bool delassus = G == 32 && !(A.flags & 64) && __all_sync(kFull, R <= G && R * R + R <= wcap);
+    if (delassus) {
+      // Delassus form (at most one row per lane): lane s holds w_s = Y_s . z, d_s = Y_s . dz, the
+      // impulse lambda_s and its sum over the position iterations. A row reads w_r, d_r and
+      // lambda_r from lane r (one shuffle each, no reduction) and every lane adds W_sr dl to w_s,
+      // with W = Y^T Y = J M^-1 J^T; z and dz are rebuilt from the impulses at the end.
+      float* s_acc = s_W + R * R;  // W: row r at r * R; then the impulses summed over the position iterations
+      float zw = z0;               // z after the warm start
+      if (isg)
+        for (int r = 0; r < R; ++r) zw += s_Y[lane * YS + r] * s_lam[r];
+      if (isg) s_dq[lane] = zw;    // s_dq is free until the back-substitution below
+      // W is symmetric: lane s forms W_sm for m = s + d (mod R), d = 0 .. R/2, and stores both
+      // triangles (for even R the pair d = R/2 is formed by two lanes, with identical values)
+      if (lane < R) {
+        for (int d = 0; d <= R / 2; ++d) {
+          const int m = (lane + d < R) ? lane + d : lane + d - R;
+          float acc = 0.f;
+          for (int i = 0; i < n; ++i) acc += s_Y[i * YS + lane] * s_Y[i * YS + m];
+          s_W[m * R + lane] = acc;
+          s_W[lane * R + m] = acc;
+        }
+      }
+      __syncwarp();
+      float wv = 0.f, dv = 0.f, lv = 0.f, av = 0.f;
+      if (lane < R) {
+        for (int i = 0; i < n; ++i) wv += s_Y[i * YS + lane] * s_dq[i];
+        lv = s_lam[lane];
+      }
       const float inv_hit = 1.f / hit, inv_h = 1.f / h;
       const float beta = A.bias_coef, vmax = A.max_depen_vel;
       for (int it = 0; it < npos + nvel; ++it) {
         const bool pos = it < npos;
-        // per row: J_r v = Y_r . z and the separation d_r + J_r dq = d_r + Y_r . dz (two
-        // independent group reductions), then a branch-free update (selects: measured 7 % faster
-        // on the Ant step than a branch around it)
         for (int r = 0; r < Rw_max; ++r) {
-          const float y = (isg && r < R) ? s_Y[lane * RS + r] : 0.f;
+          const bool inr = r < R;
           const float4 hc = s_rowc[r];
-          const float yz = Grp<G>::sum(y * z), ydz = Grp<G>::sum(y * dz);
-          const float sep = hc.x + ydz;
+          const float wc = (inr && lane < R) ? s_W[r * R + lane] : 0.f;  // W_sr of this lane's row
           const int kb = __float_as_int(hc.z);
-          const bool valid = (r < R) && (hc.y > 0.f);
+          const float yz = Grp<G>::get(wv, r), ydz = Grp<G>::get(dv, r);
+          // friction rows: the normal impulse of their contact, from its row's lane
+          const float lam = Grp<G>::get(lv, r), lam_n = Grp<G>::get(lv, (kb >> 2) & (G - 1));
+          const float sep = hc.x + ydz;
+          const bool valid = inr && (hc.y > 0.f);
           const bool fric = (kb & 3) == kRowFriction;
-          const float lam = s_lam[r];
-          const float lim = hc.x * s_lam[(valid && fric) ? (kb >> 2) : 0];
+          const float lim = hc.x * lam_n;
           const float lf = fminf(fmaxf(lam - yz * hc.y, -lim), lim);
           const float tp = (sep >= 0.f) ? -sep * inv_hit : fminf(-beta * sep * inv_hit, vmax);
           const float tv = (sep > 0.f) ? -sep * inv_h : 0.f;
           const float ln = fmaxf(lam + ((pos ? tp : tv) - yz) * hc.y, 0.f);
           const float lnew = fric ? lf : ln;
           const float dl = valid ? lnew - lam : 0.f;
-          z += y * dl;
-          if (valid) s_lam[r] = lnew;  // every lane stores the same value
+          wv += wc * dl;
+          if (valid && lane == r) lv = lnew;
         }
-        if (pos) dz += hit * z;
+        if (pos) {
+          dv += hit * wv;
+          av += lv;
+        }
       }
+      if (lane < R) { s_lam[lane] = lv; s_acc[lane] = av; }
+      __syncwarp();
+      // z = z_free + Y lambda; dz = sum over the position iterations of h_it z
+      if (isg) {
+        float zs = 0.f, as = 0.f;
+        for (int r = 0; r < R; ++r) {
+          const float y = s_Y[lane * YS + r];
+          zs += y * s_lam[r];
+          as += y * s_acc[r];
+        }
+        z = z0 + zs;
+        dz = hit * ((float)npos * z0 + as);
+      }
+    } else {
+      const float2 zd = pgs_row_form<G>(s_Y, YS, s_rowc, s_lam, R, Rw_max, isg, lane, npos, nvel, h, hit,
+                                        A.bias_coef, A.max_depen_vel, z0);
+      z = zd.x;
+      dz = zd.y;
     }
     // back to joint space: v = L^-T z, dq = L^-T dz (lane k finalises DOF k, highest first)
     {

@@ -25,6 +25,7 @@ SIM_FLAG_GRAPH = 4
 SIM_FLAG_BODY_FORCES = 8
 SIM_FLAG_RIGID_BODY_STATE = 16
 SIM_FLAG_DOF_FORCE = 32
+SIM_FLAG_ROW_SOLVER = 64
 (SIM_VIEW_ROOT_STATE, SIM_VIEW_DOF_STATE, SIM_VIEW_DOF_ACTUATION, SIM_VIEW_NET_CONTACT_FORCE,
  SIM_VIEW_CONTACT_PAIRS, SIM_VIEW_CONTACT_COUNT, SIM_VIEW_SIGNATURE, SIM_VIEW_STATUS,
  SIM_VIEW_IMPULSE_CACHE, SIM_VIEW_DOF_POSITION_TARGET, SIM_VIEW_DOF_VELOCITY_TARGET, SIM_VIEW_DOF_FORCE,

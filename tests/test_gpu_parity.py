@@ -102,6 +102,15 @@ def test_sixteen_steps(name, n_envs):
     check_rollout(workload(name, n_envs), 16, 1e-3, 1e-3)
 
 
+@pytest.mark.parametrize("name,n_envs", [("ant", 67), ("humanoid", 37), ("hand", 37), ("mixed", 67)])
+@pytest.mark.parametrize("steps,rtol,atol,min_same", [(1, 1e-4, 1e-5, 0.9), (16, 1e-3, 1e-3, 0.75)])
+def test_row_solver_form(name, n_envs, steps, rtol, atol, min_same):
+    """The row form of the Gauss-Seidel solve (SIM_FLAG_ROW_SOLVER: each row's J v and separation
+    as group reductions over Y), the form a substep falls back to when its Delassus block does not
+    fit beside Y, against the oracle at the same bars as the default form."""
+    check_rollout(workload(name, n_envs), steps, rtol, atol, min_same=min_same, flags=1 | 64)
+
+
 @pytest.mark.parametrize("name,n_envs", [("ant", 4096), ("humanoid", 4096), ("hand", 4096), ("mixed", 16384)])
 def test_full_size_one_step(name, n_envs):
     """Full-size configurations (one launch per env type and step) against the oracle on all envs."""
