@@ -971,17 +971,22 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
         arm = T->armature[gl];
         if (T->has_drives) arm += h * (h * T->drive_kp[gl] + T->drive_kd[gl]);
       }
+      // row i of M through its shared row (a loop, not unrolled: less code), then into registers
+      if (isg) {
+        for (int j = 0; j <= lane; ++j) {
+          float mij = 0.f;
+          if ((anc >> j) & 1u) {
+            const float* Sj = s_SD + 6 * j;
 #pragma unroll
-      for (int j = 0; j < G; ++j) {
-        float mij = 0.f;
-        if (j < n && j <= lane && ((anc >> j) & 1u)) {
-          const float* Sj = s_SD + 6 * j;
-#pragma unroll
-          for (int k = 0; k < 6; ++k) mij += Sj[k] * F[k];
+            for (int k = 0; k < 6; ++k) mij += Sj[k] * F[k];
+          }
+          if (j == lane) mij += arm;
+          s_M[lane * MS + j] = mij;
         }
-        if (j == lane) mij += arm;
-        m[j] = mij;
       }
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < G; ++j) m[j] = (isg && j <= lane) ? s_M[lane * MS + j] : 0.f;
       // right-looking Cholesky, lane i owns row i: L_ik = M_ik / L_kk, M_ij -= L_ik L_jk. The
       // column loop is not unrolled: the row shifts down one register per column (m[0] holds
       // M_ik at step k), which keeps the code a few hundred bytes at any G (the unrolled
@@ -1066,24 +1071,24 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
         // b_i -= L_ik y_k for i > k (the subtractions of the row-by-row form, in the same order).
         // The vector shifts down one register per step (y[0] holds b_k), so the loop over k is
         // not unrolled (the unrolled triangle was 25 KB of code at G = 32)
-#pragma unroll
-        for (int i = 0; i < G; ++i) {
+        // J_r through the row's column of Y (a loop, not unrolled: less code), then into registers
+        for (int i = 0; i < n; ++i) {
           float ji = 0.f;
-          if (i < n) {
-            if (kind == kRowLimit) {
-              ji = (i == gl) ? sgn : 0.f;
-            } else if ((anc >> i) & 1u) {
-              const float* Si = s_SD + 6 * i;
+          if (kind == kRowLimit) {
+            ji = (i == gl) ? sgn : 0.f;
+          } else if ((anc >> i) & 1u) {
+            const float* Si = s_SD + 6 * i;
 #pragma unroll
-              for (int k = 0; k < 6; ++k) ji += Si[k] * fr[k];
-            } else if ((ancb >> i) & 1u) {
-              const float* Si = s_SD + 6 * i;
+            for (int k = 0; k < 6; ++k) ji += Si[k] * fr[k];
+          } else if ((ancb >> i) & 1u) {
+            const float* Si = s_SD + 6 * i;
 #pragma unroll
-              for (int k = 0; k < 6; ++k) ji += Si[k] * fb[k];
-            }
+            for (int k = 0; k < 6; ++k) ji += Si[k] * fb[k];
           }
-          y[i] = ji;
+          s_Y[i * YS + r] = ji;
         }
+#pragma unroll
+        for (int i = 0; i < G; ++i) y[i] = (i < n) ? s_Y[i * YS + r] : 0.f;
         for (int k = 0; k < n; ++k) {
           const float yk = y[0] * s_Linv[k];
           s_Y[k * YS + r] = yk;
