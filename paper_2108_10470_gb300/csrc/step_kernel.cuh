@@ -401,6 +401,88 @@ __device__ __noinline__ float2 pgs_row_form(const float* s_Y, const int YS, cons
 }
 
 // ---------------------------------------------------------------------------------------------
+// Delassus form of the same solve, for substeps with at most one row per lane whose W fits in
+// s_W (R * R + R words): lane s holds w_s = Y_s . z, d_s = Y_s . dz, the impulse lambda_s and its
+// sum over the position iterations. A row reads w_r, d_r and lambda_r from lane r (one shuffle
+// each, no reduction) and every lane adds W_sr dl to w_s, with W = Y^T Y = J M^-1 J^T formed once
+// per substep; z and dz are rebuilt from the impulses at the end. Returns (z, dz) of the lane and
+// leaves the impulses in s_lam; s_dq is used as scratch. Out of line, like the row form, so the
+// loop gets its own register allocation.
+template <int G>
+__device__ __noinline__ float2 pgs_delassus_form(const float* s_Y, const int YS, float* s_W, const float4* s_rowc,
+                                                 float* s_lam, float* s_dq, const int R, const int Rw_max,
+                                                 const int n, const bool isg, const int lane, const int npos,
+                                                 const int nvel, const float h, const float hit, const float beta,
+                                                 const float vmax, const float z0) {
+  float* s_acc = s_W + R * R;  // W: row r at r * R; then the impulses summed over the position iterations
+  float zw = z0;               // z after the warm start
+  if (isg)
+    for (int r = 0; r < R; ++r) zw += s_Y[lane * YS + r] * s_lam[r];
+  if (isg) s_dq[lane] = zw;
+  // W is symmetric: lane s forms W_sm for m = s + d (mod R), d = 0 .. R/2, and stores both
+  // triangles (for even R the pair d = R/2 is formed by two lanes, with identical values)
+  if (lane < R) {
+    for (int d = 0; d <= R / 2; ++d) {
+      const int m = (lane + d < R) ? lane + d : lane + d - R;
+      float acc = 0.f;
+      for (int i = 0; i < n; ++i) acc += s_Y[i * YS + lane] * s_Y[i * YS + m];
+      s_W[m * R + lane] = acc;
+      s_W[lane * R + m] = acc;
+    }
+  }
+  __syncwarp();
+  float wv = 0.f, dv = 0.f, lv = 0.f, av = 0.f;
+  if (lane < R) {
+    for (int i = 0; i < n; ++i) wv += s_Y[i * YS + lane] * s_dq[i];
+    lv = s_lam[lane];
+  }
+  const float inv_hit = 1.f / hit, inv_h = 1.f / h;
+  for (int it = 0; it < npos + nvel; ++it) {
+    const bool pos = it < npos;
+    for (int r = 0; r < Rw_max; ++r) {
+      const bool inr = r < R;
+      const float4 hc = s_rowc[r];
+      const float wc = (inr && lane < R) ? s_W[r * R + lane] : 0.f;  // W_sr of this lane's row
+      const int kb = __float_as_int(hc.z);
+      const float yz = Grp<G>::get(wv, r), ydz = Grp<G>::get(dv, r);
+      // friction rows: the normal impulse of their contact, from its row's lane
+      const float lam = Grp<G>::get(lv, r), lam_n = Grp<G>::get(lv, (kb >> 2) & (G - 1));
+      const float sep = hc.x + ydz;
+      const bool valid = inr && (hc.y > 0.f);
+      const bool fric = (kb & 3) == kRowFriction;
+      const float lim = hc.x * lam_n;
+      const float lf = fminf(fmaxf(lam - yz * hc.y, -lim), lim);
+      const float tp = (sep >= 0.f) ? -sep * inv_hit : fminf(-beta * sep * inv_hit, vmax);
+      const float tv = (sep > 0.f) ? -sep * inv_h : 0.f;
+      const float ln = fmaxf(lam + ((pos ? tp : tv) - yz) * hc.y, 0.f);
+      const float lnew = fric ? lf : ln;
+      const float dl = valid ? lnew - lam : 0.f;
+      wv += wc * dl;
+      if (valid && lane == r) lv = lnew;
+    }
+    if (pos) {
+      dv += hit * wv;
+      av += lv;
+    }
+  }
+  if (lane < R) { s_lam[lane] = lv; s_acc[lane] = av; }
+  __syncwarp();
+  // z = z_free + Y lambda; dz = sum over the position iterations of h_it z
+  float z = 0.f, dz = 0.f;
+  if (isg) {
+    float zs = 0.f, as = 0.f;
+    for (int r = 0; r < R; ++r) {
+      const float y = s_Y[lane * YS + r];
+      zs += y * s_lam[r];
+      as += y * s_acc[r];
+    }
+    z = z0 + zs;
+    dz = hit * ((float)npos * z0 + as);
+  }
+  return make_float2(z, dz);
+}
+
+// ---------------------------------------------------------------------------------------------
 // One substep loop of one environment by one group of G lanes. grp indexes the launch's env list
 // (grp >= n_launch_envs: a dead group, which shadows the last env and never stores); sm is the
 // group's shared arena and rb the base of its contact and row blocks (sm itself, or a private
@@ -1119,82 +1201,18 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
     float z = 0.f, dz = 0.f;
     // The Delassus form serves one env per warp (G = 32: five-level reductions, nothing to share
     // the warp's issue slots with); at G <= 16 forming W costs more than it saves (measured on the
-    // Ant: +5 %). W and the impulse sums go after Y in its region, or, with the rows in global
+    // Ant: 3 % slower, 8 % with two rows per lane so that every Ant substep fits). W and the
+    // impulse sums go after Y in its region, or, with the rows in global
     // scratch, into the shared link slots (free from the inertia pass to the next substep's
     // inward sweep); flag 64 keeps every substep in the row form.
     float* s_W = GROWS ? s_link : s_Y + n * YS;
     const int wcap = GROWS ? L * kLinkWords : Ly.ywords - n * YS;
     const bool delassus = G == 32 && !(A.flags & 64) && __all_sync(kFull, R <= G && R * R + R <= wcap);
     if (delassus) {
-      // Delassus form (at most one row per lane): lane s holds w_s = Y_s . z, d_s = Y_s . dz, the
-      // impulse lambda_s and its sum over the position iterations. A row reads w_r, d_r and
-      // lambda_r from lane r (one shuffle each, no reduction) and every lane adds W_sr dl to w_s,
-      // with W = Y^T Y = J M^-1 J^T; z and dz are rebuilt from the impulses at the end.
-      float* s_acc = s_W + R * R;  // W: row r at r * R; then the impulses summed over the position iterations
-      float zw = z0;               // z after the warm start
-      if (isg)
-        for (int r = 0; r < R; ++r) zw += s_Y[lane * YS + r] * s_lam[r];
-      if (isg) s_dq[lane] = zw;    // s_dq is free until the back-substitution below
-      // W is symmetric: lane s forms W_sm for m = s + d (mod R), d = 0 .. R/2, and stores both
-      // triangles (for even R the pair d = R/2 is formed by two lanes, with identical values)
-      if (lane < R) {
-        for (int d = 0; d <= R / 2; ++d) {
-          const int m = (lane + d < R) ? lane + d : lane + d - R;
-          float acc = 0.f;
-          for (int i = 0; i < n; ++i) acc += s_Y[i * YS + lane] * s_Y[i * YS + m];
-          s_W[m * R + lane] = acc;
-          s_W[lane * R + m] = acc;
-        }
-      }
-      __syncwarp();
-      float wv = 0.f, dv = 0.f, lv = 0.f, av = 0.f;
-      if (lane < R) {
-        for (int i = 0; i < n; ++i) wv += s_Y[i * YS + lane] * s_dq[i];
-        lv = s_lam[lane];
-      }
-      const float inv_hit = 1.f / hit, inv_h = 1.f / h;
-      const float beta = A.bias_coef, vmax = A.max_depen_vel;
-      for (int it = 0; it < npos + nvel; ++it) {
-        const bool pos = it < npos;
-        for (int r = 0; r < Rw_max; ++r) {
-          const bool inr = r < R;
-          const float4 hc = s_rowc[r];
-          const float wc = (inr && lane < R) ? s_W[r * R + lane] : 0.f;  // W_sr of this lane's row
-          const int kb = __float_as_int(hc.z);
-          const float yz = Grp<G>::get(wv, r), ydz = Grp<G>::get(dv, r);
-          // friction rows: the normal impulse of their contact, from its row's lane
-          const float lam = Grp<G>::get(lv, r), lam_n = Grp<G>::get(lv, (kb >> 2) & (G - 1));
-          const float sep = hc.x + ydz;
-          const bool valid = inr && (hc.y > 0.f);
-          const bool fric = (kb & 3) == kRowFriction;
-          const float lim = hc.x * lam_n;
-          const float lf = fminf(fmaxf(lam - yz * hc.y, -lim), lim);
-          const float tp = (sep >= 0.f) ? -sep * inv_hit : fminf(-beta * sep * inv_hit, vmax);
-          const float tv = (sep > 0.f) ? -sep * inv_h : 0.f;
-          const float ln = fmaxf(lam + ((pos ? tp : tv) - yz) * hc.y, 0.f);
-          const float lnew = fric ? lf : ln;
-          const float dl = valid ? lnew - lam : 0.f;
-          wv += wc * dl;
-          if (valid && lane == r) lv = lnew;
-        }
-        if (pos) {
-          dv += hit * wv;
-          av += lv;
-        }
-      }
-      if (lane < R) { s_lam[lane] = lv; s_acc[lane] = av; }
-      __syncwarp();
-      // z = z_free + Y lambda; dz = sum over the position iterations of h_it z
-      if (isg) {
-        float zs = 0.f, as = 0.f;
-        for (int r = 0; r < R; ++r) {
-          const float y = s_Y[lane * YS + r];
-          zs += y * s_lam[r];
-          as += y * s_acc[r];
-        }
-        z = z0 + zs;
-        dz = hit * ((float)npos * z0 + as);
-      }
+      const float2 zd = pgs_delassus_form<G>(s_Y, YS, s_W, s_rowc, s_lam, s_dq, R, Rw_max, n, isg, lane, npos, nvel, h,
+                                             hit, A.bias_coef, A.max_depen_vel, z0);
+      z = zd.x;
+      dz = zd.y;
     } else {
       const float2 zd = pgs_row_form<G>(s_Y, YS, s_rowc, s_lam, R, Rw_max, isg, lane, npos, nvel, h, hit,
                                         A.bias_coef, A.max_depen_vel, z0);
