@@ -371,15 +371,17 @@ def timed_steps(s, act_dev, warm, steps, flush):
 
 
 def variants_measure(dev, warm=20, steps=200):
-    """The same Ant-like step at 8192 and 16384 envs, and at 4096 envs replayed as a captured CUDA
-    graph: env-steps/s under the main line's timing protocol."""
+    """The same Ant-like step at 8192 and 16384 envs, and at 4096 envs launched directly and replayed
+    as a captured CUDA graph: env-steps/s under the main line's timing protocol, over 200 timed
+    steps after 20 warm-up steps (fewer than the main line's, so fewer ground contacts: compare
+    these lines with each other)."""
     import torch
 
     from paper_2108_10470_gb300 import sim, workloads as W
 
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     out = {}
-    for n_envs, flags, key in ((8192, 0, "envs_8192"), (16384, 0, "envs_16384"),
+    for n_envs, flags, key in ((8192, 0, "envs_8192"), (16384, 0, "envs_16384"), (4096, 0, "envs_4096"),
                                (4096, sim.SIM_FLAG_GRAPH, "cuda_graph_4096")):
         w = W.ant_workload(n_envs)
         root, dof, acts = W.seeded_inputs(w, 0, warm + steps)
