@@ -269,10 +269,12 @@ class Oracle:
             return int(lib().oracle_step_tangent_f32(*args))
         return int(lib().oracle_step_tangent(*args, int(n_threads)))
 
-    def rk4(self, root, dof, act, dt, nsteps):
+    def rk4(self, root, dof, act, dt, nsteps) -> int:
+        """Contact-free RK4 reference integration in place; returns 0, or -2 (nothing done) for
+        models with ball joints."""
         a = np.ascontiguousarray(act, dtype=np.float64).reshape(self.N_D)
-        lib().oracle_rk4(self.h, _dp(root), _dp(dof) if self.N_D else None, _dp(a) if self.N_D else None,
-                         float(dt), int(nsteps))
+        return int(lib().oracle_rk4(self.h, _dp(root), _dp(dof) if self.N_D else None, _dp(a) if self.N_D else None,
+                                    float(dt), int(nsteps)))
 
     # -- single-env helpers (root: (actors_per_env,13), dof: (env joint DOFs,2), float64) ---------
     def ngen(self, env=0) -> int:

@@ -33,7 +33,7 @@
 
 namespace orc {
 
-enum { JOINT_FREE = 0, JOINT_FIXED = 1, JOINT_REVOLUTE = 2, JOINT_PRISMATIC = 3 };
+enum { JOINT_FREE = 0, JOINT_FIXED = 1, JOINT_REVOLUTE = 2, JOINT_PRISMATIC = 3, JOINT_SPHERICAL = 4 };
 enum { SHAPE_SPHERE = 0, SHAPE_CAPSULE = 1, SHAPE_BOX = 2 };
 enum { ROW_LIMIT = 0, ROW_NORMAL = 1, ROW_FRICTION = 2 };
 
@@ -61,9 +61,9 @@ struct ModelD {
   std::vector<LinkD> links;
   std::vector<ShapeD> shapes;
   std::vector<TendonD> tendons;
-  std::vector<int> ndof;   // DOFs of each link's joint (0, 1 or 6)
+  std::vector<int> ndof;   // DOFs of each link's joint (0, 1, 3 for a ball joint, or 6)
   std::vector<int> goff;   // offset of each link's DOFs in the model's generalized vector
-  std::vector<int> jdof;   // joint-DOF index (DOF state tensor row within the model) or -1
+  std::vector<int> jdof;   // first joint-DOF index (DOF state tensor row within the model) or -1
   int n_gen = 0, n_jdof = 0, n_body = 0, contact_cap = 0;
   bool free_root = false;
 };
@@ -125,7 +125,8 @@ template <class T> std::vector<T> gen_velocity(const ModelD& M, const ActorState
   if (M.free_root)
     for (int k = 0; k < 3; ++k) { g[k] = s.w[k]; g[3 + k] = s.v[k]; }
   for (size_t i = 0; i < M.links.size(); ++i)
-    if (M.jdof[i] >= 0) g[M.goff[i]] = s.qd[M.jdof[i]];
+    if (M.jdof[i] >= 0)
+      for (int k = 0; k < M.ndof[i]; ++k) g[M.goff[i] + k] = s.qd[M.jdof[i] + k];
   return g;
 }
 
@@ -166,6 +167,20 @@ template <class T> void kinematics(const ModelD& M, const ActorState<T>& s, cons
       Rj = axis_angle<T>(a, qi);
       XJ = plux<T>(transpose(Rj), zero3<T>());
       K.S[i].push_back(smk<T>(a, zero3<T>()));
+    } else if (lk.jtype == JOINT_SPHERICAL) {
+      // ball joint (RBDA Table 4.1): position = rotation vector r, R_J = exp([r]x); velocity =
+      // the child's angular velocity relative to the parent in child coordinates, S = [I; 0]
+      const int j0 = M.jdof[i];
+      const Vec3<T> rv = mk3<T>(s.q[j0], s.q[j0 + 1], s.q[j0 + 2]);
+      T qj[4];
+      quat_exp(rv, qj);
+      Rj = quat_to_mat<T>(qj);
+      XJ = plux<T>(transpose(Rj), zero3<T>());
+      for (int k = 0; k < 3; ++k) {
+        Vec3<T> e = zero3<T>();
+        e[k] = T(1.0);
+        K.S[i].push_back(smk<T>(e, zero3<T>()));
+      }
     } else if (lk.jtype == JOINT_PRISMATIC) {
       tj = scale(a, qi);
       XJ = plux<T>(ident3<T>(), tj);
@@ -238,7 +253,8 @@ template <class T> bool aba(const ModelD& M, const ActorKin<T>& K, const std::ve
       for (int b = 0; b < nd; ++b) D[a * nd + b] = sdot(K.S[i][a], U[i][b]);
       u[i][a] = tau[M.goff[i] + a] - sdot(K.S[i][a], pA[i]);
     }
-    if (nd == 1) D[0] = D[0] + T(M.links[i].armature);
+    if (nd == 1 || nd == 3)  // armature on every joint DOF (not on a free root)
+      for (int k = 0; k < nd; ++k) D[k * nd + k] = D[k * nd + k] + T(M.links[i].armature);
     if (nd == 1 && diag) D[0] = D[0] + (*diag)[M.goff[i]];
     if (!small_inverse_spd(D, nd, Dinv[i])) return false;
     const int par = M.links[i].parent;
@@ -306,7 +322,11 @@ template <class T> void crba(const ModelD& M, const ActorKin<T>& K, std::vector<
         }
       }
     }
-    if (nd == 1) H[M.goff[i] * n + M.goff[i]] = H[M.goff[i] * n + M.goff[i]] + T(M.links[i].armature);
+    if (nd == 1 || nd == 3)
+      for (int k = 0; k < nd; ++k) {
+        const int g = M.goff[i] + k;
+        H[g * n + g] = H[g * n + g] + T(M.links[i].armature);
+      }
     if (nd == 1 && diag) H[M.goff[i] * n + M.goff[i]] = H[M.goff[i] * n + M.goff[i]] + (*diag)[M.goff[i]];
   }
 }
@@ -328,7 +348,9 @@ template <class T> void rnea(const ModelD& M, const ActorKin<T>& K, const std::v
   tau.assign(M.n_gen, T(0.0));
   for (int i = L - 1; i >= 0; --i) {
     for (size_t k = 0; k < K.S[i].size(); ++k) tau[M.goff[i] + k] = sdot(K.S[i][k], f[i]);
-    if (K.S[i].size() == 1) tau[M.goff[i]] = tau[M.goff[i]] + T(M.links[i].armature) * qdd[M.goff[i]];
+    if (K.S[i].size() == 1 || K.S[i].size() == 3)
+      for (size_t k = 0; k < K.S[i].size(); ++k)
+        tau[M.goff[i] + k] = tau[M.goff[i] + k] + T(M.links[i].armature) * qdd[M.goff[i] + k];
     const int par = M.links[i].parent;
     if (par >= 0) f[par] = sadd(f[par], smul(stranspose(K.Xup[i]), f[i]));
   }
@@ -661,7 +683,7 @@ template <class T> void build_rows(const Oracle& O, int env, const EnvLayout& E,
     const ModelD& M = O.actor_model(env, a);
     for (size_t l = 0; l < M.links.size(); ++l) {
       const LinkD& lk = M.links[l];
-      if (M.jdof[l] < 0 || !lk.has_limit) continue;
+      if (M.jdof[l] < 0 || M.ndof[l] != 1 || !lk.has_limit) continue;
       const T q = st[a].q[M.jdof[l]];
       const int g = E.gen_off[a] + M.goff[l];
       if (q - T(lk.lo) < margin) {
@@ -811,6 +833,13 @@ template <class T> void env_substep(const Oracle& O, int env, std::vector<ActorS
     // implicit drive kp (q* - q - h qd) + kd (qd* - qd), whose h (h kp + kd) joins the joint's
     // diagonal of the joint-space inertia (implicit Euler of the spring-damper)
     std::vector<T> tau(M.n_gen, T(0.0)), diag(M.n_gen, T(0.0));
+    for (size_t l = 0; l < M.links.size(); ++l)
+      for (int k = 1; k < M.ndof[l] && M.jdof[l] >= 0; ++k) {  // ball-joint DOFs 1, 2 (no drives)
+        const int j = M.jdof[l] + k;
+        const T f = act[jbase + j] - T(M.links[l].damping) * st[a].qd[j];
+        tau[M.goff[l] + k] = f;
+        if (out.dof_force.size() > (size_t)(jbase + j)) out.dof_force[jbase + j] = f;
+      }
     for (size_t l = 0; l < M.links.size(); ++l)
       if (M.jdof[l] >= 0) {
         const int j = M.jdof[l];
@@ -979,7 +1008,19 @@ template <class T> void env_substep(const Oracle& O, int env, std::vector<ActorS
       s.v = zero3<T>();
     }
     for (size_t l = 0; l < M.links.size(); ++l)
-      if (M.jdof[l] >= 0) {
+      if (M.ndof[l] == 3) {
+        // ball joint: R_J <- R_J exp([dq]x) (dq in child coordinates), back to a rotation vector
+        const int j = M.jdof[l], g = g0 + M.goff[l];
+        T qj[4], e[4], qn[4];
+        quat_exp(mk3<T>(s.q[j], s.q[j + 1], s.q[j + 2]), qj);
+        quat_exp(mk3<T>(dq[g], dq[g + 1], dq[g + 2]), e);
+        quat_mul(qj, e, qn);
+        const Vec3<T> r = quat_log(qn);
+        for (int k = 0; k < 3; ++k) {
+          s.q[j + k] = r[k];
+          s.qd[j + k] = v[g + k];
+        }
+      } else if (M.jdof[l] >= 0) {
         const int j = M.jdof[l], g = g0 + M.goff[l];
         s.q[j] = s.q[j] + dq[g];
         s.qd[j] = v[g];
@@ -1302,6 +1343,7 @@ void* oracle_create(const OracleModels* md, const int32_t* env_actor_model, int3
       M.goff[i] = g;
       if (i == 0 && jt == JOINT_FREE) { M.ndof[i] = 6; M.free_root = true; }
       else if (jt == JOINT_REVOLUTE || jt == JOINT_PRISMATIC) { M.ndof[i] = 1; M.jdof[i] = j++; }
+      else if (jt == JOINT_SPHERICAL && i > 0) { M.ndof[i] = 3; M.jdof[i] = j; j += 3; }
       g += M.ndof[i];
       if (!M.links[i].is_virtual) M.n_body++;
     }
@@ -1584,7 +1626,8 @@ int32_t oracle_energy(void* h, int32_t env, const double* root, const double* do
     const ModelD& M = O.actor_model(env, a);
     for (size_t i = 0; i < M.links.size(); ++i) {
       T += 0.5 * sdot(K[a].v[i], smul(K[a].I[i], K[a].v[i]));
-      if (M.jdof[i] >= 0) T += 0.5 * M.links[i].armature * st[a].qd[M.jdof[i]] * st[a].qd[M.jdof[i]];
+      for (int k = 0; k < M.ndof[i] && M.jdof[i] >= 0; ++k)
+        T += 0.5 * M.links[i].armature * st[a].qd[M.jdof[i] + k] * st[a].qd[M.jdof[i] + k];
       const Vec3<double> c = add(K[a].p[i], mul(K[a].R[i], vec3_of<double>(M.links[i].com)));
       V -= M.links[i].mass * dot(g, c);
     }
@@ -1625,6 +1668,10 @@ int32_t oracle_momentum(void* h, int32_t env, const double* root, const double* 
 // Contact-free RK4 steps of every env (tau = act - damping * qd), in place.
 int32_t oracle_rk4(void* h, double* root, double* dof, const double* act, double dt, int32_t nsteps) {
   const Oracle& O = *(const Oracle*)h;
+  // the reference integrator advances joint positions by q_dot = qd: hinges and sliders only
+  for (const ModelD& M : O.models)
+    for (int nd : M.ndof)
+      if (nd == 3) return -2;
   for (int e = 0; e < O.n_envs; ++e) {
     std::vector<ActorState<double>> st;
     load_env(O, e, root, dof, st);

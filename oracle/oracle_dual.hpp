@@ -33,6 +33,10 @@ template <class F> inline DualT<F> sqrt(const DualT<F>& a) {
 template <class F> inline DualT<F> sin(const DualT<F>& a) { return DualT<F>(std::sin(a.v), std::cos(a.v) * a.d, 0); }
 template <class F> inline DualT<F> cos(const DualT<F>& a) { return DualT<F>(std::cos(a.v), -std::sin(a.v) * a.d, 0); }
 template <class F> inline DualT<F> fabs(const DualT<F>& a) { return a.v < F(0) ? -a : a; }
+template <class F> inline DualT<F> atan2(const DualT<F>& y, const DualT<F>& x) {
+  const F r2 = x.v * x.v + y.v * y.v;
+  return DualT<F>(std::atan2(y.v, x.v), (x.v * y.d - y.v * x.d) / r2, 0);
+}
 template <class F> inline double val(const DualT<F>& a) { return (double)a.v; }
 
 using Dual = DualT<double>;   // the FP64 oracle derivative

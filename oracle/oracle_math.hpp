@@ -25,6 +25,7 @@ using std::sqrt;
 using std::sin;
 using std::cos;
 using std::fabs;
+using std::atan2;
 
 inline double val(double x) { return x; }
 inline double val(float x) { return (double)x; }
@@ -122,6 +123,24 @@ template <class T> void quat_exp(const Vec3<T>& th, T out[4]) {
   const T ang = sqrt(ang2);
   const T s = sin(ang * T(0.5)) / ang;
   out[0] = th[0] * s; out[1] = th[1] * s; out[2] = th[2] * s; out[3] = cos(ang * T(0.5));
+}
+// Rotation vector of the quaternion q = (x, y, z, w) (need not be exactly unit): the shorter
+// rotation (w >= 0), angle 2 atan2(|v|, w) about v / |v|; r = 2 v / w in the limit |v| -> 0.
+template <class T> Vec3<T> quat_log(const T qin[4]) {
+  T q[4] = {qin[0], qin[1], qin[2], qin[3]};
+  if (q[3] < T(0.0))
+    for (int k = 0; k < 4; ++k) q[k] = T(0.0) - q[k];
+  const T s2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
+  T f;
+  if (s2 < T(1e-30)) {
+    f = T(2.0) / q[3];
+  } else {
+    const T sn = sqrt(s2);
+    f = T(2.0) * atan2(sn, q[3]) / sn;
+  }
+  Vec3<T> r = zero3<T>();
+  r[0] = q[0] * f; r[1] = q[1] * f; r[2] = q[2] * f;
+  return r;
 }
 // Rotation by angle th about the unit axis a (Rodrigues' formula): maps rotated-frame coords to
 // original-frame coords.

@@ -30,6 +30,7 @@ inline OpCount sqrt(const OpCount& a) { ++OpCount::counter(); return OpCount(std
 inline OpCount sin(const OpCount& a) { ++OpCount::counter(); return OpCount(std::sin(a.v)); }
 inline OpCount cos(const OpCount& a) { ++OpCount::counter(); return OpCount(std::cos(a.v)); }
 inline OpCount fabs(const OpCount& a) { return OpCount(std::fabs(a.v)); }  // a sign flip, not counted
+inline OpCount atan2(const OpCount& y, const OpCount& x) { ++OpCount::counter(); return OpCount(std::atan2(y.v, x.v)); }
 inline double val(const OpCount& a) { return a.v; }
 
 }  // namespace orc

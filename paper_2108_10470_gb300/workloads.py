@@ -25,7 +25,9 @@ from typing import List, Optional, Sequence
 
 import numpy as np
 
-JOINT_FREE, JOINT_FIXED, JOINT_REVOLUTE, JOINT_PRISMATIC = 0, 1, 2, 3
+JOINT_FREE, JOINT_FIXED, JOINT_REVOLUTE, JOINT_PRISMATIC, JOINT_SPHERICAL = 0, 1, 2, 3, 4
+# DOFs of each joint type (a ball joint: rotation vector and angular velocity, 3 each)
+JOINT_NDOF = {JOINT_FREE: 0, JOINT_FIXED: 0, JOINT_REVOLUTE: 1, JOINT_PRISMATIC: 1, JOINT_SPHERICAL: 3}
 SHAPE_SPHERE, SHAPE_CAPSULE, SHAPE_BOX = 0, 1, 2
 IDENT_Q = (0.0, 0.0, 0.0, 1.0)
 
@@ -96,7 +98,11 @@ class Model:
 
     @property
     def n_jdof(self) -> int:
-        return int(np.sum((self.jtype == JOINT_REVOLUTE) | (self.jtype == JOINT_PRISMATIC)))
+        return int(sum(JOINT_NDOF[int(t)] for t in self.jtype))
+
+    def dof_links(self) -> List[int]:
+        """The link of every joint DOF, in DOF order (a ball joint's link three times)."""
+        return [i for i in range(self.n_links) for _ in range(JOINT_NDOF[int(self.jtype[i])])]
 
     @property
     def n_gen(self) -> int:
@@ -134,8 +140,7 @@ class _Builder:
                                inertia=inertia, armature=armature, damping=damping, lo=lo, hi=hi,
                                has_limit=int(limit is not None), is_virtual=int(virtual), kp=float(drive[0]),
                                kd=float(drive[1])))
-        if jtype in (JOINT_REVOLUTE, JOINT_PRISMATIC):
-            self.gear.append(gear)
+        self.gear.extend([gear] * JOINT_NDOF[jtype])
         return len(self.links) - 1
 
     def shape(self, link, stype, size, pos=(0, 0, 0), quat=IDENT_Q, friction=1.0):
@@ -225,6 +230,17 @@ def pendulum(mass=0.5, length=1.0) -> Model:
     i_perp = mass * length * length / 12.0
     b.link(0, JOINT_REVOLUTE, axis=(0, 1, 0), mass=mass, com=(0, 0, -length / 2.0),
            inertia=(i_perp, i_perp, 1e-6, 0, 0, 0))
+    return b.build()
+
+
+def ball_pendulum(mass=0.5, length=1.0, inertia=None, com=None, name="ball_pendulum") -> Model:
+    """Fixed pivot + a body on a ball joint (3 DOF: rotation vector, angular velocity in the body
+    frame); by default the uniform thin rod of `pendulum` hanging along -z (no shapes)."""
+    b = _Builder(name)
+    b.link(-1, JOINT_FIXED, mass=1.0, inertia=(1, 1, 1, 0, 0, 0))
+    i_perp = mass * length * length / 12.0
+    b.link(0, JOINT_SPHERICAL, mass=mass, com=(0, 0, -length / 2.0) if com is None else com,
+           inertia=(i_perp, i_perp, 1e-6, 0, 0, 0) if inertia is None else inertia)
     return b.build()
 
 
@@ -425,9 +441,10 @@ def free_sphere(r=0.1, mass=1.0, friction=1.0, z=None) -> Model:
 
 
 def random_tree(rng: np.random.Generator, n_links: int, floating: bool, name="random_tree",
-                allow_fixed=True) -> Model:
-    """Random tree (parent[i] < i) with mixed revolute / prismatic / fixed joints, random offsets,
-    orientations, axes and SPD inertias; no shapes."""
+                allow_fixed=True, ball_joints=False) -> Model:
+    """Random tree (parent[i] < i) with mixed revolute / prismatic / fixed joints (and ball joints
+    when ball_joints), random offsets, orientations, axes and SPD inertias; no shapes. The draws of
+    a tree without ball joints do not change with the option."""
     b = _Builder(name)
 
     def rand_inertia():
@@ -455,7 +472,8 @@ def random_tree(rng: np.random.Generator, n_links: int, floating: bool, name="ra
            com=tuple(rng.uniform(-0.1, 0.1, 3)), inertia=rand_inertia())
     for i in range(1, n_links):
         par = int(rng.integers(0, i))
-        choices = [JOINT_REVOLUTE, JOINT_REVOLUTE, JOINT_PRISMATIC] + ([JOINT_FIXED] if allow_fixed else [])
+        choices = [JOINT_REVOLUTE, JOINT_REVOLUTE, JOINT_PRISMATIC] + ([JOINT_FIXED] if allow_fixed else []) + \
+            ([JOINT_SPHERICAL, JOINT_SPHERICAL] if ball_joints else [])
         jt = int(rng.choice(choices))
         b.link(par, jt, axis=rand_axis(), ppos=tuple(rng.uniform(-0.4, 0.4, 3)), pquat=rand_quat(),
                mass=float(rng.uniform(0.2, 2.0)), com=tuple(rng.uniform(-0.2, 0.2, 3)), inertia=rand_inertia(),
@@ -594,9 +612,8 @@ def initial_state(w: Workload, rng: np.random.Generator):
         for m in w.actor_models(e):
             nj = m.n_jdof
             q = rng.uniform(-m.dof_noise, m.dof_noise, size=nj) if nj else np.zeros(0)
-            jl = [i for i in range(m.n_links) if m.jtype[i] in (JOINT_REVOLUTE, JOINT_PRISMATIC)]
-            for j, li in enumerate(jl):
-                if m.has_limit[li]:
+            for j, li in enumerate(m.dof_links()):
+                if m.has_limit[li]:  # 1-DOF joints only
                     q[j] = min(max(q[j], m.lo[li]), m.hi[li])
             d = np.zeros((nj, 2))
             d[:, 0] = q
