@@ -43,17 +43,23 @@ enum {
 };
 
 /* ---- model description ----------------------------------------------------------------------- */
-enum { SIM_JOINT_FREE = 0, SIM_JOINT_FIXED = 1, SIM_JOINT_REVOLUTE = 2, SIM_JOINT_PRISMATIC = 3 };
+enum { SIM_JOINT_FREE = 0, SIM_JOINT_FIXED = 1, SIM_JOINT_REVOLUTE = 2, SIM_JOINT_PRISMATIC = 3,
+       SIM_JOINT_SPHERICAL = 4 };
 enum { SIM_SHAPE_SPHERE = 0, SIM_SHAPE_CAPSULE = 1, SIM_SHAPE_BOX = 2 };
 
 /* One articulation (paper, Sec. "Physics Simulation": reduced-coordinate articulations; a single
  * rigid body is a one-link articulation). Links are numbered 0..n_links-1 with parent[i] < i and
  * parent[0] = -1; link 0 is the root and its joint_type is FREE (floating base, 6 DOF) or FIXED.
  * Every other link's joint is REVOLUTE or PRISMATIC (1 DOF about/along joint_axis, expressed in
- * the joint frame) or FIXED. The joint frame of link i sits at parent_pos[i] in the parent link's
- * frame with orientation parent_quat[i]; at q = 0 the link frame coincides with it. A multi-axis
- * joint is a chain of 1-DOF joints through massless "virtual" links (is_virtual = 1), which carry
- * no shapes and are left out of the per-body tensors. Per-link joint data (armature = rotor
+ * the joint frame), SPHERICAL (a ball joint, 3 DOF: positions = the rotation vector r of the link
+ * frame in the joint frame, R = exp([r]x), kept as the shorter rotation, |r| <= pi; velocities =
+ * the link's angular velocity relative to its parent in link coordinates; RBDA Table 4.1; no
+ * limits, drives or tendons; its env type runs the global-rows kernel variant and has no step
+ * derivative or mass-matrix / Jacobian query) or FIXED. The joint frame of link i sits at
+ * parent_pos[i] in the parent link's frame with orientation parent_quat[i]; at q = 0 the link
+ * frame coincides with it. A multi-axis joint can also be a chain of 1-DOF joints through massless
+ * "virtual" links (is_virtual = 1), which carry no shapes and are left out of the per-body tensors.
+ * The DOF state rows of a joint follow link order, a ball joint's three in a row. Per-link joint data (armature = rotor
  * inertia added to the DOF, damping = viscous joint damping, limits) belong to the link's joint.
  * Shapes: SPHERE size[0] = radius; CAPSULE size[0] = radius, size[1] = half segment length, axis =
  * shape-local x; BOX size = half extents. A shape sits at shape_pos / shape_quat in its link's frame.

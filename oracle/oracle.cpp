@@ -663,6 +663,11 @@ template <class T> void point_row(const Oracle& O, int env, const EnvLayout& E, 
     } else if (lk.jtype == JOINT_PRISMATIC) {
       const Vec3<T> ax = mul(K[a].R[l], vec3_of<T>(lk.axis));
       J[g] = J[g] + sign * dot(k, ax);
+    } else if (lk.jtype == JOINT_SPHERICAL) {  // rotation about each child axis through the joint
+      for (int c = 0; c < 3; ++c) {
+        const Vec3<T> ax = mk3<T>(K[a].R[l](0, c), K[a].R[l](1, c), K[a].R[l](2, c));
+        J[g + c] = J[g + c] + sign * dot(k, cross(ax, sub(x, K[a].p[l])));
+      }
     }
     l = lk.parent;
   }

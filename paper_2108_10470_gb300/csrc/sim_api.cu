@@ -133,7 +133,8 @@ int validate_model(const sim_model_desc& m) {
     if (i > 0) {
       if (m.parent[i] < 0 || m.parent[i] >= i) return SIM_ERR_TOPOLOGY;
       const int jt = m.joint_type[i];
-      if (jt != SIM_JOINT_FIXED && jt != SIM_JOINT_REVOLUTE && jt != SIM_JOINT_PRISMATIC) return SIM_ERR_TOPOLOGY;
+      if (jt != SIM_JOINT_FIXED && jt != SIM_JOINT_REVOLUTE && jt != SIM_JOINT_PRISMATIC && jt != SIM_JOINT_SPHERICAL)
+        return SIM_ERR_TOPOLOGY;
     }
     for (int k = 0; k < 3; ++k)
       if (!finite(m.joint_axis[3 * i + k]) || !finite(m.parent_pos[3 * i + k]) || !finite(m.com[3 * i + k]))
@@ -167,6 +168,9 @@ int validate_model(const sim_model_desc& m) {
         return SIM_ERR_INVALID_ARG;
     }
     if (m.has_limit[i] > 1 || m.is_virtual[i] > 1) return SIM_ERR_INVALID_ARG;
+    if (jt == SIM_JOINT_SPHERICAL &&  // ball joints take no limits and no drives
+        (m.has_limit[i] || (m.drive_stiffness && m.drive_stiffness[i] != 0.f) || (m.drive_damping && m.drive_damping[i] != 0.f)))
+      return SIM_ERR_INVALID_ARG;
     if (m.drive_stiffness && !(m.drive_stiffness[i] >= 0.f && finite(m.drive_stiffness[i]))) return SIM_ERR_INVALID_ARG;
     if (m.drive_damping && !(m.drive_damping[i] >= 0.f && finite(m.drive_damping[i]))) return SIM_ERR_INVALID_ARG;
   }
@@ -218,6 +222,7 @@ int validate_model(const sim_model_desc& m) {
 int ndof_of(const sim_model_desc& m, int i) {
   const int jt = m.joint_type[i];
   if (i == 0) return jt == SIM_JOINT_FREE ? 6 : 0;
+  if (jt == SIM_JOINT_SPHERICAL) return 3;
   return (jt == SIM_JOINT_REVOLUTE || jt == SIM_JOINT_PRISMATIC) ? 1 : 0;
 }
 
@@ -244,10 +249,11 @@ int build_type(const sim_model_desc* models, const std::vector<int>& actor_model
       T.gdof[l] = nd ? n : -1;
       if (nd == 6) {
         for (int k = 0; k < 6; ++k) { T.dof_link[n + k] = l; T.dof_comp[n + k] = k; }
-      } else if (nd == 1) {
-        T.dof_link[n] = l;
-        T.dof_comp[n] = -1;
-        T.jdof[l] = nj++;
+      } else if (nd == 1 || nd == 3) {  // a joint's DOFs (armature on each)
+        for (int k = 0; k < nd; ++k) { T.dof_link[n + k] = l; T.dof_comp[n + k] = -1; }
+        T.jdof[l] = nj;
+        nj += nd;
+        if (nd == 3) T.has_ball = 1;
       }
       n += nd;
       double an = 1.0;
@@ -338,7 +344,8 @@ int build_type(const sim_model_desc* models, const std::vector<int>& actor_model
     unsigned mask = 0u;
     for (int a = l; a >= 0; a = T.parent[a]) {
       const int nd = (T.parent[a] < 0) ? (T.jtype[a] == kFree ? 6 : 0)
-                                        : ((T.jtype[a] == kRevolute || T.jtype[a] == kPrismatic) ? 1 : 0);
+                                        : (T.jtype[a] == kSpherical ? 3
+                                                                    : ((T.jtype[a] == kRevolute || T.jtype[a] == kPrismatic) ? 1 : 0));
       for (int k = 0; k < nd; ++k) mask |= 1u << (T.gdof[a] + k);
     }
     T.anc[l] = mask;
@@ -416,6 +423,7 @@ SmemLayout make_layout(const EnvTypeTable& T, int G, bool rows_global) {
     Ly.M = o; o += n * Ly.MS;
     Ly.vec = o; o += 5 * n;
     Ly.frc = o; o += 3 * L;
+    Ly.ball = o; o += T.has_ball ? kBallWords * L : 0;
     Ly.total = al4(o);
   }
   // Groups that share a warp (G < 32) must not share banks: pad the per-group stride to G mod 32
@@ -427,10 +435,10 @@ SmemLayout make_layout(const EnvTypeTable& T, int G, bool rows_global) {
 }
 
 // Default placement: rows in global scratch when the all-shared arena would exceed
-// kSharedArenaLimit, and always for env types with shape pairs (the pair phase is compiled into
-// the global-rows variant only).
+// kSharedArenaLimit, and always for env types with shape pairs or ball joints (the pair phase and
+// the 3-DOF joint blocks are compiled into the global-rows variant only).
 bool default_rows_global(const EnvTypeTable& T, int G) {
-  return T.n_pairs > 0 || make_layout(T, G, false).total * 4 > kSharedArenaLimit;
+  return T.n_pairs > 0 || T.has_ball || make_layout(T, G, false).total * 4 > kSharedArenaLimit;
 }
 
 cudaError_t launch_type(const TypePlan& tp, const StepArgs& a, const TypeArgs& ta, cudaStream_t st) {
@@ -459,8 +467,8 @@ int configure_type(TypePlan& tp, int G, bool rows_global, int warps, bool per_ty
     g_last_error = "type config: lanes per env must be 8, 16 or 32 and hold the type; warps 1, 2 or 4";
     return SIM_ERR_INVALID_ARG;
   }
-  if (tp.tab.n_pairs > 0 && !rows_global) {
-    g_last_error = "type config: env types with shape pairs keep their rows in global memory";
+  if ((tp.tab.n_pairs > 0 || tp.tab.has_ball) && !rows_global) {
+    g_last_error = "type config: env types with shape pairs or ball joints keep their rows in global memory";
     return SIM_ERR_INVALID_ARG;
   }
   const SmemLayout Ly = make_layout(tp.tab, G, rows_global);
@@ -533,8 +541,8 @@ int tangent_supported(const sim_s* h) {
     return SIM_ERR_CAPACITY;
   }
   for (const TypePlan& tp : h->types)
-    if (tp.tab.has_drives || tp.tab.n_tendons > 0) {
-      g_last_error = "step derivative: joint drives and tendons are not part of the differentiated step";
+    if (tp.tab.has_drives || tp.tab.n_tendons > 0 || tp.tab.has_ball) {
+      g_last_error = "step derivative: joint drives, tendons and ball joints are not part of the differentiated step";
       return SIM_ERR_CAPACITY;
     }
   for (const TypePlan& tp : h->types)
@@ -1079,6 +1087,11 @@ int sim_get_max_dims(sim_handle h, int32_t* n_max, int32_t* l_max) {
 static int run_query(sim_handle h, float* out, int what) {
   if (!valid_handle(h)) return SIM_ERR_HANDLE;
   if (!out) return SIM_ERR_INVALID_ARG;
+  for (const TypePlan& tp : h->types)
+    if (tp.tab.has_ball) {
+      g_last_error = "mass-matrix and Jacobian queries: env types with ball joints are not supported";
+      return SIM_ERR_CAPACITY;
+    }
   int nm = 1, lm = 1;
   sim_get_max_dims(h, &nm, &lm);
   StepArgs a;

@@ -18,7 +18,7 @@ constexpr int kMaxActors = 8;   // actors per environment
 constexpr int kMaxTendons = 8;      // fixed tendons per environment
 constexpr int kMaxTendonJoints = 8; // joints per tendon
 
-enum JointType : int { kFree = 0, kFixed = 1, kRevolute = 2, kPrismatic = 3 };
+enum JointType : int { kFree = 0, kFixed = 1, kRevolute = 2, kPrismatic = 3, kSpherical = 4 };
 enum ShapeType : int { kSphere = 0, kCapsule = 1, kBox = 2 };
 enum RowKind : int { kRowLimit = 0, kRowNormal = 1, kRowFriction = 2, kRowTendon = 3 };
 
@@ -35,7 +35,7 @@ struct EnvTypeTable {
   int first_child[kMaxLinks];   // children in ascending order: first_child, next_sibling chain
   int next_sibling[kMaxLinks];
   int gdof[kMaxLinks];          // first generalized DOF of the link's joint (-1: none)
-  int jdof[kMaxLinks];          // env joint-DOF index (DOF state row within the env) or -1
+  int jdof[kMaxLinks];          // first env joint-DOF index (DOF state row within the env) or -1
   int body[kMaxLinks];          // env body index (net-contact-force row) or -1 (virtual)
   int actor[kMaxLinks];
   int aroot[kMaxLinks];         // link index of the actor's root
@@ -51,6 +51,7 @@ struct EnvTypeTable {
   int has_limit[kMaxLinks];
   float drive_kp[kMaxLinks], drive_kd[kMaxLinks];  // joint drive gains (0: no drive)
   int has_drives;
+  int has_ball;  // the type has ball joints (3 DOF; global-rows variant only)
   // fixed tendons (env-local links of 1-DOF joints); limit rows follow the joint-limit rows and use
   // impulse-cache slots 3 n_cand + 2 n_jdof + 2 t + side
   int n_tendons;
@@ -95,11 +96,13 @@ struct SmemLayout {
   int rowa;   // rcap: row aux (DOF / contact index)
   int rcap;
   int frc;    // 3 per link
+  int ball;   // kBallWords per link: ball-joint state and sweep blocks, global rows only
   int ywords; // words from Y to the end of its region: Y (n_gen x (R | 1) for R rows), then the
               // solver's Delassus block R x R and R accumulated impulses when they fit
   int total;  // words per environment (multiple of 4; = G mod 32 when groups share a warp)
 };
 constexpr int kLinkWords = 37;
+constexpr int kBallWords = 36;  // per ball-joint link: U 18 | D^-1 6 | u 3 | q 3 | qd 3 | tau 3
 // contact record (SoA): x y z (relative to actor a's origin) | d | mu | link_a | cand | shape_a |
 // slot | link_b (-1: ground) | shape_b | n x y z (from b to a) | O_b - O_a x y z
 constexpr int kConWords = 17;

@@ -98,6 +98,35 @@ __device__ __forceinline__ void axis_angle(V3 a, float th, float* R) {
   R[6] = t * a.x * a.z - s * a.y; R[7] = t * a.y * a.z + s * a.x; R[8] = t * a.z * a.z + c;
 }
 
+// Unit quaternion (x, y, z, w) of the rotation vector r: rotation by |r| about r / |r|.
+__device__ __forceinline__ void rotvec_quat(float rx, float ry, float rz, float* e) {
+  const float a2 = rx * rx + ry * ry + rz * rz;
+  if (a2 < 1e-30f) {  // sin(a/2)/a -> 1/2
+    e[0] = 0.5f * rx; e[1] = 0.5f * ry; e[2] = 0.5f * rz; e[3] = 1.f;
+    return;
+  }
+  const float an = sqrtf(a2);
+  float sn, cs;
+  sincosf(0.5f * an, &sn, &cs);
+  const float sc = sn / an;
+  e[0] = rx * sc; e[1] = ry * sc; e[2] = rz * sc; e[3] = cs;
+}
+// Rotation vector of the quaternion q (need not be exactly unit): the shorter rotation (w >= 0),
+// angle 2 atan2(|v|, w) about v / |v|.
+__device__ __forceinline__ void quat_rotvec(const float* q, float* r) {
+  const float sg = q[3] < 0.f ? -1.f : 1.f;
+  const float x = sg * q[0], y = sg * q[1], z = sg * q[2], w = sg * q[3];
+  const float s2 = x * x + y * y + z * z;
+  float f;
+  if (s2 < 1e-30f) {
+    f = 2.f / w;
+  } else {
+    const float sn = sqrtf(s2);
+    f = 2.f * atan2f(sn, w) / sn;
+  }
+  r[0] = x * f; r[1] = y * f; r[2] = z * f;
+}
+
 // Symmetric 6x6 stored as its upper triangle, row-major (21 words).
 __host__ __device__ constexpr int sidx(int i, int j) {
   return (i <= j) ? (i * 6 - (i * (i - 1)) / 2 + (j - i)) : (j * 6 - (j * (j - 1)) / 2 + (i - j));
@@ -359,6 +388,96 @@ __device__ __noinline__ int pair_contacts(const EnvTypeTable* __restrict__ T, co
 }
 
 // ---------------------------------------------------------------------------------------------
+// Ball-joint block of the articulated-body inward sweep (RBDA Table 7.1, a 3-DOF joint): with IA,
+// pA the link's articulated inertia (packed symmetric, 21) and bias (6) in its hand-off slot sl and
+// S the joint's three motion-subspace columns (world axes about the actor origin), U = IA S,
+// D = S^T U + armature I, u = tau - S^T pA with tau = actuation - damping qd (bl's state words);
+// the slot becomes Ia = IA - U D^-1 U^T and pa = pA + Ia c + U D^-1 u, and U, D^-1 (00 11 22 01
+// 02 12) and u go to bl for the outward sweep.
+// Returns the status bit 2 if D is not positive definite (D^-1 = I is used then).
+static __device__ __noinline__ int ball_joint_block(float* sl, float* bl, const float* S, const float c0, const float c1,
+                                             const float c2, const float c3, const float c4, const float c5,
+                                             const float damping, const float arm) {
+  const float cc[6] = {c0, c1, c2, c3, c4, c5};
+  float tau3[3];  // actuation - damping qd (from the joint's state words of bl)
+#pragma unroll
+  for (int k = 0; k < 3; ++k) tau3[k] = bl[33 + k] - damping * bl[30 + k];
+  int st = 0;
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      float t = 0.f;
+#pragma unroll
+      for (int j = 0; j < 6; ++j) t += sl[sidx(i, j)] * S[6 * c + j];
+      bl[6 * c + i] = t;
+    }
+  float Dm[9], u3[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    float sp = 0.f;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) sp += S[6 * c + i] * sl[21 + i];
+    u3[c] = tau3[c] - sp;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      float t = 0.f;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) t += S[6 * c + i] * bl[6 * m + i];
+      Dm[3 * c + m] = t;
+    }
+    Dm[4 * c] += arm;
+  }
+  // symmetric inverse by cofactors
+  const float a = Dm[0], b = Dm[4], cz = Dm[8];
+  const float dxy = 0.5f * (Dm[1] + Dm[3]), dxz = 0.5f * (Dm[2] + Dm[6]), dyz = 0.5f * (Dm[5] + Dm[7]);
+  const float k00 = b * cz - dyz * dyz, k01 = dxz * dyz - dxy * cz, k02 = dxy * dyz - b * dxz;
+  const float k11 = a * cz - dxz * dxz, k12 = dxy * dxz - a * dyz, k22 = a * b - dxy * dxy;
+  const float det = a * k00 + dxy * k01 + dxz * k02;
+  float Di[6];
+  if (!(a > 0.f && k22 > 0.f && det > 0.f)) {
+    st = 2;
+    Di[0] = 1.f; Di[1] = 1.f; Di[2] = 1.f; Di[3] = 0.f; Di[4] = 0.f; Di[5] = 0.f;
+  } else {
+    const float id = 1.f / det;
+    Di[0] = k00 * id; Di[1] = k11 * id; Di[2] = k22 * id; Di[3] = k01 * id; Di[4] = k02 * id; Di[5] = k12 * id;
+  }
+  const float D9[9] = {Di[0], Di[3], Di[4], Di[3], Di[1], Di[5], Di[4], Di[5], Di[2]};
+#pragma unroll
+  for (int k = 0; k < 6; ++k) bl[18 + k] = Di[k];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) bl[24 + k] = u3[k];
+  float w3[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) w3[c] = D9[3 * c] * u3[0] + D9[3 * c + 1] * u3[1] + D9[3 * c + 2] * u3[2];
+  // Ia = IA - sum_c U_c V_c^T, V_c = sum_m D^-1_cm U_m
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    float Uc[6], Vc[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      Uc[i] = bl[6 * c + i];
+      Vc[i] = D9[3 * c] * bl[i] + D9[3 * c + 1] * bl[6 + i] + D9[3 * c + 2] * bl[12 + i];
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = i; j < 6; ++j) sl[sidx(i, j)] -= Uc[i] * Vc[j];
+  }
+  float pa[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    float t = sl[21 + i] + bl[i] * w3[0] + bl[6 + i] * w3[1] + bl[12 + i] * w3[2];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) t += sl[sidx(i, j)] * cc[j];
+    pa[i] = t;
+  }
+#pragma unroll
+  for (int i = 0; i < 6; ++i) sl[21 + i] = pa[i];
+  return st;
+}
+
+// ---------------------------------------------------------------------------------------------
 // Row form of the projected Gauss-Seidel solve in z = L^T v: per row, J_r v = Y_r . z comes from
 // a group reduction, and z moves by Y_r dl; the separations d_r + Y_r . dz are formed once per
 // iteration into s_sep (R words; s_dz, n words, is scratch). Starts from z_free (z0 of the DOF
@@ -548,6 +667,9 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
   const bool is_root = isl && par < 0;
   const bool free_root = is_root && jt == kFree;
   const bool has_dof = isl && (jt == kRevolute || jt == kPrismatic);
+  // ball joint (3 DOF from joint-DOF row jd: rotation vector, angular velocity in the child
+  // frame; compiled into the global-rows variant only)
+  const bool is_ball = GROWS && isl && jt == kSpherical;
   const bool isg = lane < n;
   // 17-word contact records (body b, normal, offset); shape pairs exist only in the global-rows
   // variant, so the shared-memory variant compiles without the pair phase
@@ -571,6 +693,18 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
     q = A.dof[(size_t)(dof_base + jd) * 2];
     qd = A.dof[(size_t)(dof_base + jd) * 2 + 1];
     tau = A.act[dof_base + jd];  // joint force of the step; damping is added per substep
+  }
+  // ball-joint links keep their state in a shared slot of kBallWords (not in registers, which the
+  // rest of the global-rows variant needs): U (3 x 6) | D^-1 (sym 3 x 3) | u (3) | q (3) | qd (3) | tau (3)
+  float* s_ball = sm + Ly.ball;
+  float* bst = s_ball + kBallWords * l + 27;  // q | qd | tau of this lane's ball joint
+  if (is_ball) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      bst[k] = A.dof[(size_t)(dof_base + jd + k) * 2];
+      bst[3 + k] = A.dof[(size_t)(dof_base + jd + k) * 2 + 1];
+      bst[6 + k] = A.act[dof_base + jd + k];
+    }
   }
   float q_t = 0.f, v_t = 0.f;  // drive targets
   if (has_dof && T->has_drives) {
@@ -626,6 +760,12 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
           for (int k = 0; k < 9; ++k) Rw[k] = RB[k];
           P = Pp + mv(Rp, pp + mv(Rpj, jaxis * q));
           Sa[3] = aw.x; Sa[4] = aw.y; Sa[5] = aw.z;
+        } else if (GROWS && jt == kSpherical) {
+          float qj[4], RJ[9];
+          rotvec_quat(bst[0], bst[1], bst[2], qj);
+          quat_to_mat(qj, RJ);
+          mm(RB, RJ, Rw);
+          P = Pp + mv(Rp, pp);
         } else {
 #pragma unroll
           for (int k = 0; k < 9; ++k) Rw[k] = RB[k];
@@ -633,7 +773,22 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
         }
         float sq[6];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) { sq[k] = Sa[k] * qd; vs[k] = vp[k] + sq[k]; }
+        for (int k = 0; k < 6; ++k) sq[k] = Sa[k] * qd;
+        if (GROWS && jt == kSpherical) {
+          // motion subspace: the child's axes in world coordinates about O_a, one column per DOF
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const V3 ax = v3(Rw[c], Rw[3 + c], Rw[6 + c]);
+            const V3 px = cross(P, ax);
+            float* Sc = s_SD + 6 * (gd + c);
+            Sc[0] = ax.x; Sc[1] = ax.y; Sc[2] = ax.z; Sc[3] = px.x; Sc[4] = px.y; Sc[5] = px.z;
+            const float w = bst[3 + c];
+            sq[0] += ax.x * w; sq[1] += ax.y * w; sq[2] += ax.z * w;
+            sq[3] += px.x * w; sq[4] += px.y * w; sq[5] += px.z * w;
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) vs[k] = vp[k] + sq[k];
         // c = v x (S qd) (motion cross product)
         const V3 w = v3(vs[0], vs[1], vs[2]), vl = v3(vs[3], vs[4], vs[5]);
         const V3 sa = v3(sq[0], sq[1], sq[2]), sl = v3(sq[3], sq[4], sq[5]);
@@ -921,6 +1076,10 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
         tau_sub += mine * (-T->ten_k[t] * (len - T->ten_rest[t]) - T->ten_d[t] * rate);
       }
       if ((A.flags & 32) && live && has_dof && sub == A.substeps - 1) A.dof_force[dof_base + jd] = tau_sub;
+      if ((A.flags & 32) && live && is_ball && sub == A.substeps - 1) {  // ball joint: actuation - damping qd
+#pragma unroll
+        for (int k = 0; k < 3; ++k) A.dof_force[dof_base + jd + k] = bst[6 + k] - T->damping[l] * bst[3 + k];
+      }
       for (int d = maxdepth; d >= 1; --d) {
         if (dep == d) {
           if (has_dof) {
@@ -954,10 +1113,21 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
             for (int i = 0; i < 6; ++i) pA[i] = pa[i];
           }
           float* sl = s_link + kLinkWords * l;
+          if (is_ball) {
+            // the 3-DOF block works on the link's hand-off slot (out of line: its temporaries
+            // stay out of the register allocation of the whole step)
 #pragma unroll
-          for (int k = 0; k < 21; ++k) sl[k] = IA[k];
+            for (int k = 0; k < 21; ++k) sl[k] = IA[k];
 #pragma unroll
-          for (int k = 0; k < 6; ++k) sl[21 + k] = pA[k];
+            for (int k = 0; k < 6; ++k) sl[21 + k] = pA[k];
+            status |= ball_joint_block(sl, s_ball + kBallWords * l, s_SD + 6 * gd, cc[0], cc[1], cc[2], cc[3], cc[4],
+                                       cc[5], T->damping[l], T->armature[l]);
+          } else {
+#pragma unroll
+            for (int k = 0; k < 21; ++k) sl[k] = IA[k];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) sl[21 + k] = pA[k];
+          }
 #pragma unroll
           for (int k = 0; k < 10; ++k) sl[27 + k] = Ic[k];
         }
@@ -984,7 +1154,7 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
 
     // ======== root acceleration, outward sweep (ABA pass 3) ========
     float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    float qdd = 0.f;
+    float qdd = 0.f, qdd3[3] = {0.f, 0.f, 0.f};
     if (free_root) {
       // a0 = -(IA)^-1 pA by a 6x6 Cholesky solve in registers
       float y[6];
@@ -1035,10 +1205,35 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
 #pragma unroll
           for (int k = 0; k < 6; ++k) acc[k] += Sa[k] * qdd;
         }
+        if (is_ball) {  // qdd = D^-1 (u - U^T a), a += S qdd
+          const float* bl = s_ball + kBallWords * l;
+          float r3[3];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            float ua = 0.f;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) ua += bl[6 * c + k] * acc[k];
+            r3[c] = bl[24 + c] - ua;
+          }
+          const float* Di = bl + 18;  // 00 11 22 01 02 12
+          qdd3[0] = Di[0] * r3[0] + Di[3] * r3[1] + Di[4] * r3[2];
+          qdd3[1] = Di[3] * r3[0] + Di[1] * r3[1] + Di[5] * r3[2];
+          qdd3[2] = Di[4] * r3[0] + Di[5] * r3[1] + Di[2] * r3[2];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const float* Sc = s_SD + 6 * (gd + c);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) acc[k] += Sc[k] * qdd3[c];
+          }
+        }
       }
     }
     // generalized velocity and its rate (root: nu_dot = a0 - [0; p_dot x omega])
     if (has_dof) { s_qdd[gd] = qdd; s_v0[gd] = qd; }
+    if (is_ball) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) { s_qdd[gd + c] = qdd3[c]; s_v0[gd + c] = bst[3 + c]; }
+    }
     if (free_root) {
 #pragma unroll
       for (int k = 0; k < 6; ++k) { s_qdd[gd + k] = acc[k] - cc[k]; s_v0[gd + k] = vs[k]; }
@@ -1275,6 +1470,18 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
 
     // ======== (a7) integrate (link mode) ========
     if (has_dof) { q += s_dq[gd]; qd = s_vf[gd]; }
+    if (is_ball) {  // R_J <- R_J exp([dq]x), dq in child coordinates; stored as the shorter rotation
+      float e1[4], e2[4], qn[4];
+      rotvec_quat(bst[0], bst[1], bst[2], e1);
+      rotvec_quat(s_dq[gd], s_dq[gd + 1], s_dq[gd + 2], e2);
+      qn[0] = e1[3] * e2[0] + e1[0] * e2[3] + e1[1] * e2[2] - e1[2] * e2[1];
+      qn[1] = e1[3] * e2[1] - e1[0] * e2[2] + e1[1] * e2[3] + e1[2] * e2[0];
+      qn[2] = e1[3] * e2[2] + e1[0] * e2[1] - e1[1] * e2[0] + e1[2] * e2[3];
+      qn[3] = e1[3] * e2[3] - e1[0] * e2[0] - e1[1] * e2[1] - e1[2] * e2[2];
+      quat_rotvec(qn, bst);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) bst[3 + c] = s_vf[gd + c];
+    }
     if (free_root) {
       const V3 da = v3(s_dq[gd], s_dq[gd + 1], s_dq[gd + 2]);
       rp = rp + v3(s_dq[gd + 3], s_dq[gd + 4], s_dq[gd + 5]);
@@ -1331,6 +1538,9 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
       status |= 1;
   }
   if (has_dof && !(isfinite(q) && isfinite(qd))) status |= 1;
+  if (is_ball && !(isfinite(bst[0]) && isfinite(bst[1]) && isfinite(bst[2]) && isfinite(bst[3]) && isfinite(bst[4]) &&
+                   isfinite(bst[5])))
+    status |= 1;
   status = Grp<G>::any(status);
   if (live) {
     if (is_root) {
@@ -1343,6 +1553,13 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
     if (has_dof) {
       A.dof[(size_t)(dof_base + jd) * 2] = q;
       A.dof[(size_t)(dof_base + jd) * 2 + 1] = qd;
+    }
+    if (is_ball) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        A.dof[(size_t)(dof_base + jd + c) * 2] = bst[c];
+        A.dof[(size_t)(dof_base + jd + c) * 2 + 1] = bst[3 + c];
+      }
     }
     const int bd = isl ? T->body[l] : -1;
     if (bd >= 0) {

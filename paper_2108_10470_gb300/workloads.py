@@ -268,22 +268,24 @@ ANT_SHIN = 0.40
 ANT_KNEE_TILT = math.pi / 4  # shin points outward and 45 degrees down at q = 0
 
 
-def ant(density=5.0, armature=1.0, damping=1.0, gear=15.0, friction=1.0) -> Model:
+def ant(density=5.0, armature=1.0, damping=1.0, gear=15.0, friction=1.0, ball_hips=False) -> Model:
     """Ant-like quadruped: floating sphere torso (r 0.25, 0.33 kg), four legs at azimuths
     45/135/225/315 degrees, each a hip hinge about z (+-30 deg) carrying a 0.28 m thigh capsule and a
     knee hinge about the horizontal axis perpendicular to the leg (+-70 deg) carrying a 0.40 m shin
-    capsule (radius 0.08). 9 links, 8 joint DOF, 14 generalized DOF."""
-    b = _Builder("ant")
+    capsule (radius 0.08). 9 links, 8 joint DOF, 14 generalized DOF. With ball_hips, each hip is a
+    ball joint (3 DOF, no limits): 16 joint DOF, 22 generalized DOF."""
+    b = _Builder("ball_ant" if ball_hips else "ant")
     mt, it = sphere_mass(ANT_TORSO_R, density)
     torso = b.link(-1, JOINT_FREE, mass=mt, inertia=it)
     b.shape(torso, SHAPE_SPHERE, (ANT_TORSO_R,), friction=friction)
     for k in range(4):
         phi = math.radians(45 + 90 * k)
         m1, i1 = capsule_mass_x(ANT_LEG_R, ANT_THIGH / 2, density)
-        thigh = b.link(torso, JOINT_REVOLUTE, axis=(0, 0, 1),
+        thigh = b.link(torso, JOINT_SPHERICAL if ball_hips else JOINT_REVOLUTE, axis=(0, 0, 1),
                        ppos=(ANT_TORSO_R * math.cos(phi), ANT_TORSO_R * math.sin(phi), 0.0),
                        pquat=quat_axis_angle((0, 0, 1), phi), mass=m1, com=(ANT_THIGH / 2, 0, 0), inertia=i1,
-                       armature=armature, damping=damping, limit=(-math.radians(30), math.radians(30)), gear=gear)
+                       armature=armature, damping=damping,
+                       limit=None if ball_hips else (-math.radians(30), math.radians(30)), gear=gear)
         b.shape(thigh, SHAPE_CAPSULE, (ANT_LEG_R, ANT_THIGH / 2), pos=(ANT_THIGH / 2, 0, 0), friction=friction)
         m2, i2 = capsule_mass_x(ANT_LEG_R, ANT_SHIN / 2, density)
         shin = b.link(thigh, JOINT_REVOLUTE, axis=(0, 1, 0), ppos=(ANT_THIGH, 0, 0),

@@ -65,7 +65,8 @@ def bad(model, **kw):
     ("root_parent", -2), ("forward_parent", -2), ("root_joint", -2), ("joint_type", -2),
     ("neg_mass", -1), ("free_root_massless", -1), ("inertia_not_psd", -1), ("nan_axis", -1),
     ("zero_axis", -1), ("limits_swapped", -1), ("shape_type", -1), ("shape_on_virtual", -1),
-    ("shape_size", -1), ("too_many_links", -4),
+    ("shape_size", -1), ("too_many_links", -4), ("ball_root", -2), ("ball_limit", -1), ("ball_drive", -1),
+    ("ball_tendon", -1),
 ])
 def test_malformed_models_rejected(lib, case, code):
     m = W.ant()
@@ -98,6 +99,19 @@ def test_malformed_models_rejected(lib, case, code):
     elif case == "too_many_links":
         rng = np.random.default_rng(0)
         m = W.random_tree(rng, 33, True)
+    elif case == "ball_root":  # a ball joint attaches a child, never the root
+        j = m.jtype.copy(); j[0] = W.JOINT_SPHERICAL; m = bad(m, jtype=j)
+    elif case in ("ball_limit", "ball_drive", "ball_tendon"):  # ball joints take no limits, drives or tendons
+        j = m.jtype.copy(); j[1] = W.JOINT_SPHERICAL
+        m = bad(m, jtype=j, gear=np.concatenate([m.gear[:1], [1.0, 1.0], m.gear[1:]]))
+        if case == "ball_limit":
+            assert m.has_limit[1]
+        else:
+            h = m.has_limit.copy(); h[1] = 0; m = bad(m, has_limit=h)
+            if case == "ball_drive":
+                kp = np.zeros(m.n_links); kp[1] = 10.0; m = bad(m, drive_kp=kp, drive_kd=np.zeros(m.n_links))
+            else:
+                m = bad(m, tendons=[W.Tendon([1, 2], [1.0, 1.0], 1.0, 0.0, 0.0, None)])
     rc, _ = create(lib, [m])
     assert rc == code
 

@@ -1,0 +1,53 @@
+"""GPU parity of ball joints (3 DOF: rotation vector, angular velocity in the child frame) against
+the FP64 oracle: random trees mixing ball joints with hinges and sliders on fixed and floating
+bases, an Ant whose hips are ball joints walking on the ground (contact rows through the ball
+DOFs), and a batch mixing it with the plain Ant. Env types with ball joints run the global-rows
+kernel variant."""
+import numpy as np
+import pytest
+
+from paper_2108_10470_gb300 import workloads as W
+from test_gpu_parity import check_rollout
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2108_10470_gb300 import build
+    build.build_library()
+    torch.cuda.set_device(0)
+
+
+def tree(seed, n_links, floating):
+    rng = np.random.default_rng(seed)
+    while True:
+        m = W.random_tree(rng, n_links, floating, allow_fixed=False, ball_joints=True)
+        if (m.jtype == W.JOINT_SPHERICAL).any() and m.n_gen <= 32:
+            break
+    m.armature = np.full(m.n_links, 0.05)  # keep the joint-space inertia well conditioned
+    m.dof_noise = 0.3
+    return m
+
+
+@pytest.mark.parametrize("seed,n_links,floating", [(3, 6, False), (5, 9, True), (8, 12, False)])
+@pytest.mark.parametrize("steps,rtol,atol", [(1, 1e-4, 1e-5), (16, 1e-3, 1e-3)])
+def test_random_trees_with_ball_joints(seed, n_links, floating, steps, rtol, atol):
+    w = W.homogeneous("balltree", tree(seed, n_links, floating), 37)
+    check_rollout(w, steps, rtol, atol, min_same=1.0)
+
+
+@pytest.mark.parametrize("steps,rtol,atol,min_same", [(1, 1e-4, 1e-5, 0.9), (16, 1e-3, 1e-3, 0.75)])
+def test_ball_hip_ant_on_the_ground(steps, rtol, atol, min_same):
+    w = W.homogeneous("ball_ant", W.ant(ball_hips=True), 67)
+    check_rollout(w, steps, rtol, atol, min_same=min_same)
+
+
+def test_ball_hip_ant_beside_the_ant():
+    models = [W.ant(), W.ant(ball_hips=True)]
+    eam = np.array([i % 2 for i in range(64)], np.int32)
+    w = W.Workload("ants", models, eam, 1, 64, W.Params())
+    check_rollout(w, 4, 1e-3, 1e-3, min_same=0.75)

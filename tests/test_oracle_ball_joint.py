@@ -104,3 +104,29 @@ def test_rk4_reference_refuses_ball_joints():
     root = np.zeros((1, 13)); root[0, 6] = 1.0
     dof = np.zeros((3, 2))
     assert O.rk4(root, dof, np.zeros(3), 1e-3, 1) == -2
+
+
+def test_contact_rows_match_the_link_jacobian():
+    """Each contact row J_r = k . d(x_dot)/d(nu) of a ball-hip Ant on the ground (built joint by
+    joint along the contact link's path) against the same direction through the link's spatial
+    Jacobian (velocity propagation with the motion subspaces): k . v_O + (r x k) . w, with
+    r = x - O the contact point from the link origin, to 1e-12."""
+    w = W.homogeneous("ball_ant", W.ant(ball_hips=True), 1)
+    O = oracle.Oracle(w)
+    root, dof, acts = W.seeded_inputs(w, 0, 40)
+    root = root.astype(np.float64); dof = dof.astype(np.float64)
+    n_checked = 0
+    for k in range(40):
+        O.step(root, dof, acts[k])
+        rows = O.rows(0, root, dof)
+        for r in range(len(rows["d"])):
+            if rows["kind"][r] == 0:
+                continue
+            li = int(rows["link"][r])
+            Jl = O.jacobian(0, root, dof, li)
+            _, p = O.link_pose(0, root, dof, li)
+            kk, x = rows["k"][r], rows["x"][r]
+            ref = kk @ Jl[3:] + np.cross(x - p, kk) @ Jl[:3]
+            assert np.allclose(rows["J"][r], ref, rtol=0, atol=1e-12), (k, r)
+            n_checked += 1
+    assert n_checked > 20
