@@ -51,3 +51,42 @@ def test_ball_hip_ant_beside_the_ant():
     eam = np.array([i % 2 for i in range(64)], np.int32)
     w = W.Workload("ants", models, eam, 1, 64, W.Params())
     check_rollout(w, 4, 1e-3, 1e-3, min_same=0.75)
+
+
+def test_ball_hip_ant_persistent_launch():
+    """The persistent launch (one tile body per variant) steps ball-joint envs like the per-type
+    launch: against the oracle at 4 steps."""
+    from paper_2108_10470_gb300 import sim
+    w = W.homogeneous("ball_ant", W.ant(ball_hips=True), 64)
+    check_rollout(w, 4, 1e-3, 1e-3, min_same=0.75, flags=sim.SIM_FLAG_SIGNATURE | sim.SIM_FLAG_PERSISTENT)
+
+
+def test_ball_hip_ant_dof_forces_and_body_states():
+    """The DOF-force view (actuation - damping qd per ball DOF) and the rigid-body states after the
+    step (one more kinematics pass through the ball joints) against the oracle."""
+    from paper_2108_10470_gb300 import sim
+    from test_gpu_control import rollout_both, within
+    w = W.homogeneous("ball_ant", W.ant(ball_hips=True), 37)
+    flags = sim.SIM_FLAG_SIGNATURE | sim.SIM_FLAG_DOF_FORCE | sim.SIM_FLAG_RIGID_BODY_STATE
+    g, o = rollout_both(w, 2, flags, lambda k: {})
+    same = (g[0]["sig"] == o[0]["sig"]) & (g[1]["sig"] == o[1]["sig"])
+    assert same.mean() >= 0.9
+    m = w.models[0]
+    dmask = np.repeat(same, m.n_jdof)
+    bmask = np.repeat(same, m.n_body)
+    ok, f = within(g[0]["dof_force"][dmask], o[0]["dof_force"][dmask], 1e-4, 1e-4)
+    assert ok, f
+    ok, f = within(g[0]["body"][bmask][:, :3], o[0]["body"][bmask][:, :3], 1e-4, 1e-5)
+    assert ok, f
+    qg, qo = g[1]["body"][bmask][:, 3:7], o[1]["body"][bmask][:, 3:7]
+    assert (np.abs((qg * qo).sum(1)) > 1 - 1e-4).mean() >= 0.98
+
+
+def test_ball_joint_types_refuse_the_derivative_and_queries():
+    import torch
+    from paper_2108_10470_gb300 import sim
+    w = W.homogeneous("ball_ant", W.ant(ball_hips=True), 4)
+    s = sim.Sim(w)
+    with pytest.raises(sim.SimError):
+        s.compute_mass_matrix()
+    s.destroy()
