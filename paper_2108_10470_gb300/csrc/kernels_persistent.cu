@@ -11,16 +11,17 @@ namespace artsim {
 // finish resets the counters, so back-to-back launches (and graph replays) need no memset. Each
 // variant's tile body is a separate (not inlined) function, so it gets its own register
 // allocation: inlining all six into the one kernel measured 10 % slower on Humanoid-like envs.
-template <int G, bool GROWS>
+template <int G, bool GROWS, bool BALL>
 __device__ __noinline__ void persistent_tile(const StepArgs& A, const TypeArgs& TA, int tile, float* wsm,
                                                 int gwarp) {
   const int gw = (threadIdx.x & 31) / G;  // group within the warp
   const int grp = tile * (32 / G) + gw;
   float* sm = wsm + gw * TA.lay.total;
   float* rb = GROWS ? TA.scratch + (size_t)(gwarp * (32 / G) + gw) * TA.lay.scratch_words : sm;
-  step_group<G, GROWS>(A, TA, grp, sm, rb);
+  step_group<G, GROWS, BALL>(A, TA, grp, sm, rb);
 }
 
+template <bool BALL>
 __global__ void __launch_bounds__(128, 4) persistent_step_kernel(const __grid_constant__ PersistArgs P) {
   extern __shared__ __align__(16) float smem[];
   const int lane = threadIdx.x & 31;
@@ -38,12 +39,12 @@ __global__ void __launch_bounds__(128, 4) persistent_step_kernel(const __grid_co
     const int tile = t - (s ? P.tile_end[s - 1] : 0);
     const TypeArgs& TA = P.types[k];
     switch (P.variant[k]) {
-      case kVar8: persistent_tile<8, false>(P.common, TA, tile, wsm, gwarp); break;
-      case kVar16: persistent_tile<16, false>(P.common, TA, tile, wsm, gwarp); break;
-      case kVar32: persistent_tile<32, false>(P.common, TA, tile, wsm, gwarp); break;
-      case kVar8 | kVarRowsGlobal: persistent_tile<8, true>(P.common, TA, tile, wsm, gwarp); break;
-      case kVar16 | kVarRowsGlobal: persistent_tile<16, true>(P.common, TA, tile, wsm, gwarp); break;
-      default: persistent_tile<32, true>(P.common, TA, tile, wsm, gwarp); break;
+      case kVar8: persistent_tile<8, false, false>(P.common, TA, tile, wsm, gwarp); break;
+      case kVar16: persistent_tile<16, false, false>(P.common, TA, tile, wsm, gwarp); break;
+      case kVar32: persistent_tile<32, false, false>(P.common, TA, tile, wsm, gwarp); break;
+      case kVar8 | kVarRowsGlobal: persistent_tile<8, true, BALL>(P.common, TA, tile, wsm, gwarp); break;
+      case kVar16 | kVarRowsGlobal: persistent_tile<16, true, BALL>(P.common, TA, tile, wsm, gwarp); break;
+      default: persistent_tile<32, true, BALL>(P.common, TA, tile, wsm, gwarp); break;
     }
     __syncwarp();
   }
@@ -56,17 +57,23 @@ __global__ void __launch_bounds__(128, 4) persistent_step_kernel(const __grid_co
   }
 }
 
-cudaError_t launch_persistent_kernel(const PersistArgs& P, int grid, size_t smem, cudaStream_t st) {
-  persistent_step_kernel<<<grid, 128, smem, st>>>(P);
+cudaError_t launch_persistent_kernel(const PersistArgs& P, bool ball, int grid, size_t smem, cudaStream_t st) {
+  if (ball)
+    persistent_step_kernel<true><<<grid, 128, smem, st>>>(P);
+  else
+    persistent_step_kernel<false><<<grid, 128, smem, st>>>(P);
   return cudaGetLastError();
 }
 
-cudaError_t set_persistent_kernel_smem_cap(size_t bytes) {
-  return cudaFuncSetAttribute(persistent_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+cudaError_t set_persistent_kernel_smem_cap(bool ball, size_t bytes) {
+  const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  return ball ? cudaFuncSetAttribute(persistent_step_kernel<true>, at, (int)bytes)
+              : cudaFuncSetAttribute(persistent_step_kernel<false>, at, (int)bytes);
 }
 
-cudaError_t persistent_kernel_occupancy(int* ctas_per_sm, size_t smem) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, persistent_step_kernel, 128, smem);
+cudaError_t persistent_kernel_occupancy(bool ball, int* ctas_per_sm, size_t smem) {
+  return ball ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, persistent_step_kernel<true>, 128, smem)
+              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, persistent_step_kernel<false>, 128, smem);
 }
 
 }  // namespace artsim

@@ -26,17 +26,18 @@ cudaError_t launch_shared_smem_cap(int G, size_t bytes) {
   return cudaFuncSetAttribute(step_kernel<32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-cudaError_t launch_global(int G, const StepArgs& a, const TypeArgs& ta, int gpb, size_t smem, cudaStream_t st);
-cudaError_t launch_global_smem_cap(int G, size_t bytes);
+cudaError_t launch_global(int G, bool ball, const StepArgs& a, const TypeArgs& ta, int gpb, size_t smem,
+                          cudaStream_t st);
+cudaError_t launch_global_smem_cap(int G, bool ball, size_t bytes);
 
-cudaError_t launch_step_kernel(int G, bool rows_global, const StepArgs& a, const TypeArgs& ta,
+cudaError_t launch_step_kernel(int G, bool rows_global, bool ball, const StepArgs& a, const TypeArgs& ta,
                                int groups_per_block, size_t smem, cudaStream_t st) {
-  return rows_global ? launch_global(G, a, ta, groups_per_block, smem, st)
+  return rows_global ? launch_global(G, ball, a, ta, groups_per_block, smem, st)
                      : launch_shared(G, a, ta, groups_per_block, smem, st);
 }
 
-cudaError_t set_step_kernel_smem_cap(int G, bool rows_global, size_t bytes) {
-  return rows_global ? launch_global_smem_cap(G, bytes) : launch_shared_smem_cap(G, bytes);
+cudaError_t set_step_kernel_smem_cap(int G, bool rows_global, bool ball, size_t bytes) {
+  return rows_global ? launch_global_smem_cap(G, ball, bytes) : launch_shared_smem_cap(G, bytes);
 }
 
 }  // namespace artsim

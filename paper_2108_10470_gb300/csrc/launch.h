@@ -23,16 +23,19 @@ struct TangentArgs {
 };
 
 
-// One launch of step_kernel<G, rows_global> over ta.n_launch_envs envs, groups_per_block envs per
-// CTA (G lanes each), smem bytes of dynamic shared memory per CTA.
-cudaError_t launch_step_kernel(int G, bool rows_global, const StepArgs& a, const TypeArgs& ta,
+// One launch of step_kernel<G, rows_global, ball> over ta.n_launch_envs envs, groups_per_block envs
+// per CTA (G lanes each), smem bytes of dynamic shared memory per CTA. ball selects the global-rows
+// instantiation with the ball-joint code (ignored for shared rows).
+cudaError_t launch_step_kernel(int G, bool rows_global, bool ball, const StepArgs& a, const TypeArgs& ta,
                                int groups_per_block, size_t smem, cudaStream_t st);
-// Cap of dynamic shared memory per CTA for step_kernel<G, rows_global>.
-cudaError_t set_step_kernel_smem_cap(int G, bool rows_global, size_t bytes);
+// Cap of dynamic shared memory per CTA for step_kernel<G, rows_global, ball>.
+cudaError_t set_step_kernel_smem_cap(int G, bool rows_global, bool ball, size_t bytes);
 
-cudaError_t launch_persistent_kernel(const PersistArgs& P, int grid, size_t smem, cudaStream_t st);
-cudaError_t set_persistent_kernel_smem_cap(size_t bytes);
-cudaError_t persistent_kernel_occupancy(int* ctas_per_sm, size_t smem);
+// The persistent kernel; ball selects the instantiation whose global-rows tile bodies carry the
+// ball-joint code (a step with any ball-joint env type).
+cudaError_t launch_persistent_kernel(const PersistArgs& P, bool ball, int grid, size_t smem, cudaStream_t st);
+cudaError_t set_persistent_kernel_smem_cap(bool ball, size_t bytes);
+cudaError_t persistent_kernel_occupancy(bool ball, int* ctas_per_sm, size_t smem);
 
 // Derivative of the step (kernels_adjoint.cu): K tangents per lane (1, 2, 4 or 8), one env per warp.
 cudaError_t launch_tangent_kernel(int K, const StepArgs& a, const TypeArgs& ta, const TangentArgs& v, cudaStream_t st);

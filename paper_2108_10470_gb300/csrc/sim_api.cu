@@ -74,6 +74,7 @@ struct sim_s {
   // persistent heterogeneous launch (SIM_FLAG_PERSISTENT)
   bool persistent = false;
   int p_grid = 0, p_warps = 0, p_warp_words = 0;
+  bool p_ball = false;  // the persistent instantiation with the ball-joint code
   size_t p_smem = 0;
   std::vector<int> p_order;       // env types, costliest first
   unsigned* d_counter = nullptr;  // tile counter and finished-warp counter
@@ -442,7 +443,7 @@ bool default_rows_global(const EnvTypeTable& T, int G) {
 }
 
 cudaError_t launch_type(const TypePlan& tp, const StepArgs& a, const TypeArgs& ta, cudaStream_t st) {
-  return launch_step_kernel(tp.G, tp.lay.grows != 0, a, ta, tp.groups_per_block, tp.smem_bytes, st);
+  return launch_step_kernel(tp.G, tp.lay.grows != 0, tp.tab.has_ball != 0, a, ta, tp.groups_per_block, tp.smem_bytes, st);
 }
 
 int variant_of(const TypePlan& tp) {
@@ -486,7 +487,7 @@ int configure_type(TypePlan& tp, int G, bool rows_global, int warps, bool per_ty
   }
   // the attribute is a cap per kernel instantiation, shared by every type that uses it: set the
   // planner's maximum rather than this type's size
-  const cudaError_t e = set_step_kernel_smem_cap(G, Ly.grows != 0, kMaxSmemPerCta);
+  const cudaError_t e = set_step_kernel_smem_cap(G, Ly.grows != 0, tp.tab.has_ball != 0, kMaxSmemPerCta);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
   tp.G = G;
   tp.lay = Ly;
@@ -509,9 +510,12 @@ int plan_persistent(sim_s* h) {
     g_last_error = "persistent launch: four warps' arenas exceed 220 KB";
     return SIM_ERR_CAPACITY;
   }
-  CK(set_persistent_kernel_smem_cap(kMaxSmemPerCta));
+  bool ball = false;
+  for (const TypePlan& tp : h->types) ball = ball || tp.tab.has_ball;
+  h->p_ball = ball;
+  CK(set_persistent_kernel_smem_cap(ball, kMaxSmemPerCta));
   int per_sm = 0, sms = 0;
-  CK(persistent_kernel_occupancy(&per_sm, smem));
+  CK(persistent_kernel_occupancy(ball, &per_sm, smem));
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
   if (per_sm < 1) {
     g_last_error = "persistent launch: no CTA fits on an SM";
@@ -607,7 +611,7 @@ int launch_step(sim_s* h, cudaStream_t st, float dt, int substeps) {
     P.n_warps = h->p_warps;
     P.warp_words = h->p_warp_words;
     P.counter = h->d_counter;
-    const cudaError_t e = launch_persistent_kernel(P, h->p_grid, h->p_smem, st);
+    const cudaError_t e = launch_persistent_kernel(P, h->p_ball, h->p_grid, h->p_smem, st);
     if (e != cudaSuccess) return cuda_fail(e, "persistent_step_kernel launch");
     return SIM_OK;
   }

@@ -620,7 +620,7 @@ __device__ __noinline__ float2 pgs_delassus_form(const float* s_Y, const int YS,
 // (grp >= n_launch_envs: a dead group, which shadows the last env and never stores); sm is the
 // group's shared arena and rb the base of its contact and row blocks (sm itself, or a private
 // slot of global scratch in the GROWS variant).
-template <int G, bool GROWS>
+template <int G, bool GROWS, bool BALL = false>
 __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA, const int grp, float* sm,
                                            float* rb) {
   const EnvTypeTable* __restrict__ T = TA.type;
@@ -668,8 +668,9 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
   const bool free_root = is_root && jt == kFree;
   const bool has_dof = isl && (jt == kRevolute || jt == kPrismatic);
   // ball joint (3 DOF from joint-DOF row jd: rotation vector, angular velocity in the child
-  // frame; compiled into the global-rows variant only)
-  const bool is_ball = GROWS && isl && jt == kSpherical;
+  // frame; compiled into the global-rows variant with BALL only, which env types with ball
+  // joints use: the other kernels carry none of its code)
+  const bool is_ball = BALL && GROWS && isl && jt == kSpherical;
   const bool isg = lane < n;
   // 17-word contact records (body b, normal, offset); shape pairs exist only in the global-rows
   // variant, so the shared-memory variant compiles without the pair phase
@@ -760,7 +761,7 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
           for (int k = 0; k < 9; ++k) Rw[k] = RB[k];
           P = Pp + mv(Rp, pp + mv(Rpj, jaxis * q));
           Sa[3] = aw.x; Sa[4] = aw.y; Sa[5] = aw.z;
-        } else if (GROWS && jt == kSpherical) {
+        } else if (BALL && jt == kSpherical) {
           float qj[4], RJ[9];
           rotvec_quat(bst[0], bst[1], bst[2], qj);
           quat_to_mat(qj, RJ);
@@ -774,7 +775,7 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
         float sq[6];
 #pragma unroll
         for (int k = 0; k < 6; ++k) sq[k] = Sa[k] * qd;
-        if (GROWS && jt == kSpherical) {
+        if (BALL && jt == kSpherical) {
           // motion subspace: the child's axes in world coordinates about O_a, one column per DOF
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
@@ -1585,7 +1586,7 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
 // One launch per env type: blocks of 128 / G groups, one env per group. In the GROWS variant the
 // group's scratch slot is its index in the launch (the dead groups of the last block own the
 // slots past the launched envs).
-template <int G, bool GROWS>
+template <int G, bool GROWS, bool BALL = false>
 __global__ void __launch_bounds__(128, 4) step_kernel(const __grid_constant__ StepArgs A,
                                                      const __grid_constant__ TypeArgs TA) {
   extern __shared__ __align__(16) float smem[];
@@ -1593,7 +1594,7 @@ __global__ void __launch_bounds__(128, 4) step_kernel(const __grid_constant__ St
   const int grp = blockIdx.x * (blockDim.x / G) + grp_blk;
   float* sm = smem + grp_blk * TA.lay.total;
   float* rb = GROWS ? TA.scratch + (size_t)grp * TA.lay.scratch_words : sm;
-  step_group<G, GROWS>(A, TA, grp, sm, rb);
+  step_group<G, GROWS, BALL>(A, TA, grp, sm, rb);
 }
 
 }  // namespace artsim
