@@ -297,14 +297,16 @@ def ant(density=5.0, armature=1.0, damping=1.0, gear=15.0, friction=1.0, ball_hi
     return b.build(root_pos=(0.0, 0.0, z0), dof_noise=0.1)
 
 
-def humanoid(density=1000.0, damping=0.5, friction=1.0) -> Model:
+def humanoid(density=1000.0, damping=0.5, friction=1.0, ball_joints=False) -> Model:
     """Humanoid-like biped: 13 bodies (capsules and spheres) on a floating torso, 21 revolute DOF.
     Multi-axis joints (abdomen 3, hips 3, ankles 2, shoulders 2) are chains of 1-DOF hinges through
     massless virtual links; the head is welded to the torso by a fixed joint. Gears 50-150 N m,
     armature 0.1 * gear / 50 kg m^2 (0.1-0.3: with lighter rotors, e.g. 0.02 * gear / 50, random
     150 N m torques drive joint rates to ~100 rad/s, where the explicit 1/120 s substeps diverge in
-    the FP64 oracle and on the GPU alike). 23 links, 21 joint DOF, 27 generalized DOF."""
-    b = _Builder("humanoid")
+    the FP64 oracle and on the GPU alike). 23 links, 21 joint DOF, 27 generalized DOF. With
+    ball_joints, the abdomen and the hips are ball joints (3 DOF each, no limits) instead of hinge
+    chains: 17 links, 21 joint DOF."""
+    b = _Builder("ball_humanoid" if ball_joints else "humanoid")
     deg = math.radians
     ARM = 0.1
 
@@ -323,18 +325,29 @@ def humanoid(density=1000.0, damping=0.5, friction=1.0) -> Model:
     mh, ih = sphere_mass(0.09, density)
     head = b.link(torso, JOINT_FIXED, ppos=(0, 0, 0.19), mass=mh, inertia=ih)
     b.shape(head, SHAPE_SPHERE, (0.09,), friction=friction)
+    def ball(parent, gear, ppos, body):
+        m, c, inn = body
+        return b.link(parent, JOINT_SPHERICAL, ppos=ppos, mass=m, com=c, inertia=inn, armature=ARM * gear / 50,
+                      damping=damping, gear=gear)
+
     # abdomen z, y, x -> pelvis
-    v = hinge(torso, (0, 0, 1), (-45, 45), 100, ppos=(0, 0, -0.26))
-    v = hinge(v, (0, 1, 0), (-75, 30), 100)
     mp, ip = capsule_mass_along(0.09, 0.07, density, 1)
-    pelvis = hinge(v, (1, 0, 0), (-35, 35), 100, body=(mp, (0, 0, 0), ip))
+    if ball_joints:
+        pelvis = ball(torso, 100, (0, 0, -0.26), (mp, (0, 0, 0), ip))
+    else:
+        v = hinge(torso, (0, 0, 1), (-45, 45), 100, ppos=(0, 0, -0.26))
+        v = hinge(v, (0, 1, 0), (-75, 30), 100)
+        pelvis = hinge(v, (1, 0, 0), (-35, 35), 100, body=(mp, (0, 0, 0), ip))
     b.shape(pelvis, SHAPE_CAPSULE, (0.09, 0.07), quat=Q_X_TO_Y, friction=friction)
     for side in (-1.0, 1.0):
         # hip x, z, y -> thigh
-        v = hinge(pelvis, (1, 0, 0), (-25, 5) if side < 0 else (-5, 25), 125, ppos=(0, 0.1 * side, -0.04))
-        v = hinge(v, (0, 0, 1), (-60, 35) if side < 0 else (-35, 60), 125)
         m, inn = capsule_mass_along(0.06, 0.17, density, 2)
-        thigh = hinge(v, (0, 1, 0), (-110, 20), 150, body=(m, (0, 0, -0.17), inn))
+        if ball_joints:
+            thigh = ball(pelvis, 125, (0, 0.1 * side, -0.04), (m, (0, 0, -0.17), inn))
+        else:
+            v = hinge(pelvis, (1, 0, 0), (-25, 5) if side < 0 else (-5, 25), 125, ppos=(0, 0.1 * side, -0.04))
+            v = hinge(v, (0, 0, 1), (-60, 35) if side < 0 else (-35, 60), 125)
+            thigh = hinge(v, (0, 1, 0), (-110, 20), 150, body=(m, (0, 0, -0.17), inn))
         b.shape(thigh, SHAPE_CAPSULE, (0.06, 0.17), pos=(0, 0, -0.17), quat=Q_X_TO_NEG_Z, friction=friction)
         # knee -> shin
         m, inn = capsule_mass_along(0.049, 0.15, density, 2)

@@ -90,3 +90,11 @@ def test_ball_joint_types_refuse_the_derivative_and_queries():
     with pytest.raises(sim.SimError):
         s.compute_mass_matrix()
     s.destroy()
+
+
+@pytest.mark.parametrize("steps,rtol,atol,min_same", [(1, 1e-4, 1e-5, 0.9), (16, 1e-3, 1e-3, 0.75)])
+def test_ball_joint_humanoid(steps, rtol, atol, min_same):
+    """The Humanoid with ball joints at the abdomen and hips (instead of hinge chains through
+    virtual links; 17 links, 21 joint DOF) on the ground."""
+    w = W.homogeneous("ball_humanoid", W.humanoid(ball_joints=True), 37)
+    check_rollout(w, steps, rtol, atol, min_same=min_same)
