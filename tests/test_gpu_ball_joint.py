@@ -98,3 +98,14 @@ def test_ball_joint_humanoid(steps, rtol, atol, min_same):
     virtual links; 17 links, 21 joint DOF) on the ground."""
     w = W.homogeneous("ball_humanoid", W.humanoid(ball_joints=True), 37)
     check_rollout(w, steps, rtol, atol, min_same=min_same)
+
+
+def test_spinning_body_on_a_ball_joint_eight_lanes():
+    """A single body on a ball joint at its centre of mass (3 generalized DOFs: the 8-lane kernel),
+    spinning about all three axes of an asymmetric inertia without gravity, with random initial
+    rotations: against the oracle over 16 steps."""
+    prm = W.Params(gravity=(0.0, 0.0, 0.0))
+    m = W.ball_pendulum(mass=1.0, com=(0, 0, 0), inertia=(0.3, 0.5, 0.8, 0, 0, 0), name="spinner")
+    m.dof_noise = 1.0
+    w = W.homogeneous("spinner", m, 40, params=prm)
+    check_rollout(w, 16, 1e-3, 1e-3, min_same=1.0)
