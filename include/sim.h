@@ -54,8 +54,7 @@ enum { SIM_SHAPE_SPHERE = 0, SIM_SHAPE_CAPSULE = 1, SIM_SHAPE_BOX = 2 };
  * the joint frame), SPHERICAL (a ball joint, 3 DOF: positions = the rotation vector r of the link
  * frame in the joint frame, R = exp([r]x), kept as the shorter rotation, |r| <= pi; velocities =
  * the link's angular velocity relative to its parent in link coordinates; RBDA Table 4.1; no
- * limits, drives or tendons; its env type runs the global-rows kernel variant and has no step
- * derivative or mass-matrix / Jacobian query) or FIXED. The joint frame of link i sits at
+ * limits, drives or tendons; its env type runs a global-rows kernel variant) or FIXED. The joint frame of link i sits at
  * parent_pos[i] in the parent link's frame with orientation parent_quat[i]; at q = 0 the link
  * frame coincides with it. A multi-axis joint can also be a chain of 1-DOF joints through massless
  * "virtual" links (is_virtual = 1), which carry no shapes and are left out of the per-body tensors.
@@ -283,9 +282,9 @@ int sim_autotune(sim_handle h, float dt, int32_t substeps, int32_t reps, double*
  * limit decisions, clamps and the choice of solver target follow the values, as in the forward
  * step). The state that carries into the next step is (root state, DOF state, impulse cache); the
  * actuation is the step's control input. Net contact forces and the contact views are not
- * differentiated. Supported for env types without capsule-box pairs, drives, tendons or ball joints
- * whose impulse cache has at most 384 entries, and not under SIM_FLAG_BODY_FORCES; other handles
- * fail with CAPACITY. Computed by forward-mode dual arithmetic, one
+ * differentiated. Supported for env types without capsule-box pairs, drives or tendons whose
+ * impulse cache has at most 384 entries, and not under SIM_FLAG_BODY_FORCES; other handles fail
+ * with CAPACITY. Computed by forward-mode dual arithmetic, one
  * env per warp, each lane carrying up to 8 input directions, in passes of 256 directions per env.
  * (The paper does not differentiate its step; this is the project's own extension.) */
 typedef struct {
@@ -341,14 +340,13 @@ int sim_get_max_dims(sim_handle h, int32_t* n_max, int32_t* l_max);
  * out (device, n_envs x n_max x n_max f32, row-major per env; entries past the env's generalized
  * DOFs are 0) receives M, armature included, for the generalized velocity [omega; p_dot] of each
  * floating root (world axes) followed by the joint rates, actors in order. Asynchronous on the
- * handle's stream. Errors: HANDLE, INVALID_ARG, CAPACITY (an env type with ball joints), CUDA. */
+ * handle's stream. Errors: HANDLE, INVALID_ARG, CUDA. */
 int sim_compute_mass_matrix(sim_handle h, float* out);
 
 /* World-axis Jacobians of every link of every env at the current state (paper: Jacobian tensors):
  * out (device, n_envs x L_max x 6 x n_max f32) row r of link l maps the env's generalized velocity
  * to [angular velocity; velocity of the link origin] (rows past 6, links past the env's, columns
- * past its DOFs are 0). Asynchronous. Errors: HANDLE, INVALID_ARG, CAPACITY (an env type with ball
- * joints), CUDA. */
+ * past its DOFs are 0). Asynchronous. Errors: HANDLE, INVALID_ARG, CUDA. */
 int sim_compute_jacobian(sim_handle h, float* out);
 
 /* Describe one of the SIM_VIEW_* device tensors. Errors: HANDLE, INVALID_ARG. */

@@ -549,8 +549,8 @@ int tangent_supported(const sim_s* h) {
     return SIM_ERR_CAPACITY;
   }
   for (const TypePlan& tp : h->types)
-    if (tp.tab.has_drives || tp.tab.n_tendons > 0 || tp.tab.has_ball) {
-      g_last_error = "step derivative: joint drives, tendons and ball joints are not part of the differentiated step";
+    if (tp.tab.has_drives || tp.tab.n_tendons > 0) {
+      g_last_error = "step derivative: joint drives and tendons are not part of the differentiated step";
       return SIM_ERR_CAPACITY;
     }
   for (const TypePlan& tp : h->types)
@@ -1128,11 +1128,6 @@ int sim_get_max_dims(sim_handle h, int32_t* n_max, int32_t* l_max) {
 static int run_query(sim_handle h, float* out, int what) {
   if (!valid_handle(h)) return SIM_ERR_HANDLE;
   if (!out) return SIM_ERR_INVALID_ARG;
-  for (const TypePlan& tp : h->types)
-    if (tp.tab.has_ball) {
-      g_last_error = "mass-matrix and Jacobian queries: env types with ball joints are not supported";
-      return SIM_ERR_CAPACITY;
-    }
   int nm = 1, lm = 1;
   sim_get_max_dims(h, &nm, &lm);
   StepArgs a;

@@ -147,6 +147,42 @@ template <int K> __device__ __forceinline__ void dquat_to_mat(const Dn<K>* q, Dn
   R[6] = two * (x * z - y * w); R[7] = two * (y * z + x * w); R[8] = one - two * (x * x + y * y);
 }
 
+// Quaternion (x, y, z, w) of the rotation vector r (exact exponential).
+template <int K> __device__ __forceinline__ void drotvec_quat(const Dn<K>& rx, const Dn<K>& ry, const Dn<K>& rz, Dn<K>* e) {
+  const Dn<K> a2 = rx * rx + ry * ry + rz * rz;
+  if (a2.v < 1e-30f) {
+    e[0] = rx * 0.5f; e[1] = ry * 0.5f; e[2] = rz * 0.5f; e[3] = Dn<K>(1.f);
+    return;
+  }
+  const Dn<K> an = dsqrt(a2);
+  Dn<K> sn, cs;
+  dsincos<K>(an * 0.5f, sn, cs);
+  const Dn<K> sc = sn / an;
+  e[0] = rx * sc; e[1] = ry * sc; e[2] = rz * sc; e[3] = cs;
+}
+// atan2 with its derivative (x dy - y dx) / (x^2 + y^2).
+template <int K> __device__ __forceinline__ Dn<K> datan2(const Dn<K>& y, const Dn<K>& x) {
+  Dn<K> r(atan2f(y.v, x.v));
+  const float id = 1.f / (x.v * x.v + y.v * y.v);
+#pragma unroll
+  for (int k = 0; k < K; ++k) r.d[k] = (x.v * y.d[k] - y.v * x.d[k]) * id;
+  return r;
+}
+// Rotation vector of the quaternion q (need not be exactly unit): the shorter rotation.
+template <int K> __device__ __forceinline__ void dquat_rotvec(const Dn<K>* q, Dn<K>* r) {
+  const float sg = q[3].v < 0.f ? -1.f : 1.f;
+  const Dn<K> x = q[0] * sg, y = q[1] * sg, z = q[2] * sg, w = q[3] * sg;
+  const Dn<K> s2 = x * x + y * y + z * z;
+  Dn<K> f;
+  if (s2.v < 1e-30f) {
+    f = Dn<K>(2.f) / w;
+  } else {
+    const Dn<K> sn = dsqrt(s2);
+    f = datan2<K>(sn, w) * 2.f / sn;
+  }
+  r[0] = x * f; r[1] = y * f; r[2] = z * f;
+}
+
 // Row r's J^T solved through L: y = L^-1 J_r^T (n entries). Row kinds as in the forward kernel:
 // limit rows (unit +-1 on one DOF), contact normal / friction rows along e_z, e_x, e_y.
 template <int K> __device__ void row_response(const EnvTypeTable* T, const TanWork<K>& w, int n, int kind, int gdof,
@@ -238,21 +274,39 @@ template <int K> __device__ void tangent_dynamics(const StepArgs& A, const EnvTy
         for (int k = 0; k < 9; ++k) w.R[l][k] = RB[k];
         Pl = Pp + dmv<K>(w.R[par], pp + dmv<K>(Rpj, jax * s.q[jd]));
         Sa[3] = aw.x; Sa[4] = aw.y; Sa[5] = aw.z;
+      } else if (jt == kSpherical) {  // ball joint: R_J = exp([r]x), r = (q[jd], q[jd+1], q[jd+2])
+        Dn<K> e[4], RJ[9];
+        drotvec_quat<K>(s.q[jd], s.q[jd + 1], s.q[jd + 2], e);
+        dquat_to_mat<K>(e, RJ);
+        dmm<K>(RB, RJ, w.R[l]);
+        Pl = Pp + dmv<K>(w.R[par], pp);
       } else {
         for (int k = 0; k < 9; ++k) w.R[l][k] = RB[k];
         Pl = Pp + dmv<K>(w.R[par], pp);
       }
       w.P[l][0] = Pl.x; w.P[l][1] = Pl.y; w.P[l][2] = Pl.z;
       Dn<K> sq[6];
-      const Dn<K> qd = (jd >= 0) ? s.qd[jd] : Dn<K>(0.f);
-      for (int k = 0; k < 6; ++k) { sq[k] = Sa[k] * qd; w.V[l][k] = w.V[par][k] + sq[k]; }
+      const Dn<K> qd = (jd >= 0 && jt != kSpherical) ? s.qd[jd] : Dn<K>(0.f);
+      for (int k = 0; k < 6; ++k) sq[k] = Sa[k] * qd;
+      if (jt == kSpherical) {
+        // the child's axes in world coordinates about the actor origin, one column per DOF
+        for (int c = 0; c < 3; ++c) {
+          const DV3<K> ax = dv3<K>(w.R[l][c], w.R[l][3 + c], w.R[l][6 + c]);
+          const DV3<K> px = dcross(Pl, ax);
+          w.S[gd + c][0] = ax.x; w.S[gd + c][1] = ax.y; w.S[gd + c][2] = ax.z;
+          w.S[gd + c][3] = px.x; w.S[gd + c][4] = px.y; w.S[gd + c][5] = px.z;
+          w.nu[gd + c] = s.qd[jd + c];
+          for (int k = 0; k < 6; ++k) sq[k] = sq[k] + w.S[gd + c][k] * s.qd[jd + c];
+        }
+      }
+      for (int k = 0; k < 6; ++k) w.V[l][k] = w.V[par][k] + sq[k];
       // c = v x (S qd); bias acceleration accumulates down the tree
       const DV3<K> wv = dv3<K>(w.V[l][0], w.V[l][1], w.V[l][2]), vl = dv3<K>(w.V[l][3], w.V[l][4], w.V[l][5]);
       const DV3<K> sa = dv3<K>(sq[0], sq[1], sq[2]), sl = dv3<K>(sq[3], sq[4], sq[5]);
       const DV3<K> c0 = dcross(wv, sa), c1 = dcross(wv, sl) + dcross(vl, sa);
       w.Ab[l][0] = w.Ab[par][0] + c0.x; w.Ab[l][1] = w.Ab[par][1] + c0.y; w.Ab[l][2] = w.Ab[par][2] + c0.z;
       w.Ab[l][3] = w.Ab[par][3] + c1.x; w.Ab[l][4] = w.Ab[par][4] + c1.y; w.Ab[l][5] = w.Ab[par][5] + c1.z;
-      if (gd >= 0) {
+      if (gd >= 0 && jt != kSpherical) {
         for (int k = 0; k < 6; ++k) w.S[gd][k] = Sa[k];
         w.nu[gd] = qd;
       }
@@ -329,7 +383,7 @@ template <int K> __device__ void tangent_dynamics(const StepArgs& A, const EnvTy
     const int comp = T->dof_comp[i];
     Dn<K> tau(0.f);
     if (comp < 0) {
-      const int jd = T->jdof[li];
+      const int jd = T->jdof[li] + (i - T->gdof[li]);  // the DOF's row (a ball joint has three)
       tau = s.act[jd] - s.qd[jd] * T->damping[li];
       w.L[tri(i, i)] = w.L[tri(i, i)] + Dn<K>(T->armature[li]);
     }
@@ -413,6 +467,12 @@ template <int K> __device__ void tangent_poses(const EnvTypeTable* T, const TanS
     } else if (jt == kPrismatic) {
       for (int k = 0; k < 9; ++k) w.R[l][k] = RB[k];
       Pl = Pp + dmv<K>(w.R[par], pp + dmv<K>(Rpj, jax * s.q[jd]));
+    } else if (jt == kSpherical) {
+      Dn<K> e[4], RJ[9];
+      drotvec_quat<K>(s.q[jd], s.q[jd + 1], s.q[jd + 2], e);
+      dquat_to_mat<K>(e, RJ);
+      dmm<K>(RB, RJ, w.R[l]);
+      Pl = Pp + dmv<K>(w.R[par], pp);
     } else {
       for (int k = 0; k < 9; ++k) w.R[l][k] = RB[k];
       Pl = Pp + dmv<K>(w.R[par], pp);
@@ -575,7 +635,19 @@ template <int K> __device__ bool tangent_substep(const StepArgs& A, const EnvTyp
   // ---- integrate ----
   for (int l = 0; l < L; ++l) {
     const int gd = T->gdof[l], jd = T->jdof[l], a = T->actor[l];
-    if (T->parent[l] >= 0) {
+    if (T->parent[l] >= 0 && T->jtype[l] == kSpherical) {
+      // R_J <- R_J exp([dq]x), back to the shorter rotation vector
+      Dn<K> e1[4], e2[4], qn[4];
+      drotvec_quat<K>(s.q[jd], s.q[jd + 1], s.q[jd + 2], e1);
+      drotvec_quat<K>(w.dz[gd], w.dz[gd + 1], w.dz[gd + 2], e2);
+      qn[0] = e1[3] * e2[0] + e1[0] * e2[3] + e1[1] * e2[2] - e1[2] * e2[1];
+      qn[1] = e1[3] * e2[1] - e1[0] * e2[2] + e1[1] * e2[3] + e1[2] * e2[0];
+      qn[2] = e1[3] * e2[2] + e1[0] * e2[1] - e1[1] * e2[0] + e1[2] * e2[3];
+      qn[3] = e1[3] * e2[3] - e1[0] * e2[0] - e1[1] * e2[1] - e1[2] * e2[2];
+      Dn<K> r[3];
+      dquat_rotvec<K>(qn, r);
+      for (int c = 0; c < 3; ++c) { s.q[jd + c] = r[c]; s.qd[jd + c] = w.z[gd + c]; }
+    } else if (T->parent[l] >= 0) {
       if (jd >= 0) { s.q[jd] = s.q[jd] + w.dz[gd]; s.qd[jd] = w.z[gd]; }
     } else if (T->jtype[l] == kFree) {
       for (int k = 0; k < 3; ++k) {

@@ -97,10 +97,14 @@ def env_max(arrs, sl):
     return max(float(np.abs(x[s]).max()) if x[s].size else 0.0 for x, s in zip(arrs, sl))
 
 
-@pytest.mark.parametrize("name,n", [("ant", 67), ("humanoid", 37), ("cartpole", 67)])
+WORKLOADS = {"ant": W.ant_workload, "humanoid": W.humanoid_workload, "cartpole": W.cartpole_workload,
+             "ball_ant": lambda n: W.homogeneous("ball_ant", W.ant(ball_hips=True), n)}
+
+
+@pytest.mark.parametrize("name,n", [("ant", 67), ("humanoid", 37), ("cartpole", 67), ("ball_ant", 40)])
 def test_jvp_value_and_tangent_match_oracle(name, n):
     from paper_2108_10470_gb300 import sim
-    w = {"ant": W.ant_workload, "humanoid": W.humanoid_workload, "cartpole": W.cartpole_workload}[name](n)
+    w = WORKLOADS[name](n)
     r, d, c, a = warm(w, seed=1)
     t = direction(w, r, c, np.random.default_rng(2))
     s = sim.Sim(w)
@@ -130,12 +134,12 @@ def test_jvp_value_and_tangent_match_oracle(name, n):
     assert len(bad_tan) <= 0.05 * checked, bad_tan
 
 
-@pytest.mark.parametrize("name,n", [("ant", 40), ("humanoid", 20)])
+@pytest.mark.parametrize("name,n", [("ant", 40), ("humanoid", 20), ("ball_ant", 20)])
 def test_vjp_is_the_transpose_of_the_jvp(name, n):
     """<g, J u> (tangent mode) equals <J^T g, u> (adjoint mode) per env, for random g and u."""
     import torch
     from paper_2108_10470_gb300 import sim
-    w = {"ant": W.ant_workload, "humanoid": W.humanoid_workload}[name](n)
+    w = WORKLOADS[name](n)
     r, d, c, a = warm(w, seed=3)
     rng = np.random.default_rng(4)
     u = direction(w, r, c, rng)

@@ -2,7 +2,8 @@
 the FP64 oracle: random trees mixing ball joints with hinges and sliders on fixed and floating
 bases, an Ant whose hips are ball joints walking on the ground (contact rows through the ball
 DOFs), and a batch mixing it with the plain Ant. Env types with ball joints run the global-rows
-kernel variant."""
+kernel variant. (The step derivative and the dynamics queries of ball-joint types are checked in
+test_gpu_adjoint.py and test_gpu_control.py.)"""
 import numpy as np
 import pytest
 
@@ -80,16 +81,6 @@ def test_ball_hip_ant_dof_forces_and_body_states():
     assert ok, f
     qg, qo = g[1]["body"][bmask][:, 3:7], o[1]["body"][bmask][:, 3:7]
     assert (np.abs((qg * qo).sum(1)) > 1 - 1e-4).mean() >= 0.98
-
-
-def test_ball_joint_types_refuse_the_derivative_and_queries():
-    import torch
-    from paper_2108_10470_gb300 import sim
-    w = W.homogeneous("ball_ant", W.ant(ball_hips=True), 4)
-    s = sim.Sim(w)
-    with pytest.raises(sim.SimError):
-        s.compute_mass_matrix()
-    s.destroy()
 
 
 @pytest.mark.parametrize("steps,rtol,atol,min_same", [(1, 1e-4, 1e-5, 0.9), (16, 1e-3, 1e-3, 0.75)])

@@ -137,11 +137,12 @@ def test_free_body_pushed_in_zero_gravity():
     s.destroy()
 
 
-@pytest.mark.parametrize("name", ["ant", "humanoid"])
+@pytest.mark.parametrize("name", ["ant", "humanoid", "ball_ant"])
 def test_mass_matrix_and_jacobian_match_oracle(name):
     import torch
     from paper_2108_10470_gb300 import sim
-    w = {"ant": W.ant_workload, "humanoid": W.humanoid_workload}[name](5)
+    w = {"ant": W.ant_workload, "humanoid": W.humanoid_workload,
+         "ball_ant": lambda n: W.homogeneous("ball_ant", W.ant(ball_hips=True), n)}[name](5)
     root, dof, _ = W.seeded_inputs(w, 2, 1)
     rng = np.random.default_rng(7)
     root[:, 7:13] = rng.uniform(-1, 1, (w.n_envs, 6))
