@@ -1199,11 +1199,15 @@ namespace orc {
 
 template <class D> int32_t step_tangent_t(void* h, double* root, double* dof, double* cache, const double* act,
                                          double* droot, double* ddof, double* dcache, const double* dact, double dt,
-                                         int32_t substeps, int32_t n_threads) {
+                                         int32_t substeps, int32_t n_threads, const double* pos_target = nullptr,
+                                         const double* vel_target = nullptr) {
   const Oracle* O = (const Oracle*)h;
   std::atomic<int> bad{0};
   if (n_threads < 1) n_threads = 1;
   auto one = [&](int env) {
+    Controls ctl;  // the env's drive targets (constants of the derivative; zero when absent)
+    if (pos_target) ctl.pos_target = pos_target + O->jdof_off[env];
+    if (vel_target) ctl.vel_target = vel_target + O->jdof_off[env];
     std::vector<ActorState<D>> st;
     load_env(*O, env, root, dof, st);
     int64_t jd = O->jdof_off[env];
@@ -1226,7 +1230,7 @@ template <class D> int32_t step_tangent_t(void* h, double* root, double* dof, do
     double* c_env = cache + (int64_t)env * O->cache_len;
     double* dc_env = dcache + (int64_t)env * O->cache_len;
     for (int i = 0; i < O->cache_len; ++i) { cv[i] = D(c_env[i]); cv[i].d = dc_env[i]; }
-    for (int s = 0; s < substeps; ++s) env_substep(*O, env, st, actv.data(), hs, cv, out);
+    for (int s = 0; s < substeps; ++s) env_substep(*O, env, st, actv.data(), hs, cv, out, ctl);
     for (int i = 0; i < O->cache_len; ++i) { c_env[i] = (double)cv[i].v; dc_env[i] = (double)cv[i].d; }
     store_env(*O, env, st, root, dof);
     jd = O->jdof_off[env];
@@ -1502,15 +1506,17 @@ double oracle_step_flops(void* h, double* root, double* dof, double* cache, cons
 // with its constraint and active sets held at the values' choices. Returns the failed-env count.
 int32_t oracle_step_tangent(void* h, double* root, double* dof, double* cache, const double* act, double* droot,
                             double* ddof, double* dcache, const double* dact, double dt, int32_t substeps,
-                            int32_t n_threads) {
-  return step_tangent_t<Dual>(h, root, dof, cache, act, droot, ddof, dcache, dact, dt, substeps, n_threads);
+                            int32_t n_threads, const double* pos_target, const double* vel_target) {
+  return step_tangent_t<Dual>(h, root, dof, cache, act, droot, ddof, dcache, dact, dt, substeps, n_threads, pos_target,
+                              vel_target);
 }
 
 // The same derivative evaluated in single precision (conditioning probe for the GPU derivative).
 int32_t oracle_step_tangent_f32(void* h, double* root, double* dof, double* cache, const double* act,
                                 double* droot, double* ddof, double* dcache, const double* dact, double dt,
-                                int32_t substeps) {
-  return step_tangent_t<DualF>(h, root, dof, cache, act, droot, ddof, dcache, dact, dt, substeps, 1);
+                                int32_t substeps, const double* pos_target, const double* vel_target) {
+  return step_tangent_t<DualF>(h, root, dof, cache, act, droot, ddof, dcache, dact, dt, substeps, 1, pos_target,
+                               vel_target);
 }
 
 // The same step evaluated in single precision (a conditioning probe for the parity tests: it

@@ -68,6 +68,9 @@ __global__ void __launch_bounds__(64) tangent_step_kernel(const __grid_constant_
       s.q[j] = Dn<K>(V.dof[(size_t)(dbase + j) * 2]);
       s.qd[j] = Dn<K>(V.dof[(size_t)(dbase + j) * 2 + 1]);
       s.act[j] = Dn<K>(V.act[dbase + j]);
+      // drive targets: the handle's target views, as in the forward step
+      s.qt[j] = T->has_drives ? A.pos_target[dbase + j] : 0.f;
+      s.vt[j] = T->has_drives ? A.vel_target[dbase + j] : 0.f;
     }
     for (int i = 0; i < nc; ++i) s.cache[i] = Dn<K>(V.cache[cbase + i]);
   };
@@ -208,7 +211,7 @@ __global__ void __launch_bounds__(64) query_kernel(const __grid_constant__ StepA
     s.qd[j] = Dn<1>(A.dof[(size_t)(dbase + j) * 2 + 1]);
     s.act[j] = Dn<1>(0.f);
   }
-  tangent_dynamics<1>(A, T, s, w);
+  tangent_dynamics<1>(A, T, s, w, false);  // the physical M: no implicit drive term
   if (what == 0) {
     float* o = out + (size_t)env * n_max * n_max;
     for (int i = 0; i < n_max; ++i)

@@ -549,8 +549,8 @@ int tangent_supported(const sim_s* h) {
     return SIM_ERR_CAPACITY;
   }
   for (const TypePlan& tp : h->types)
-    if (tp.tab.has_drives || tp.tab.n_tendons > 0) {
-      g_last_error = "step derivative: joint drives and tendons are not part of the differentiated step";
+    if (tp.tab.n_tendons > 0) {
+      g_last_error = "step derivative: tendons are not part of the differentiated step";
       return SIM_ERR_CAPACITY;
     }
   for (const TypePlan& tp : h->types)

@@ -218,12 +218,15 @@ template <int K> struct TanState {
   Dn<K> rp[kMaxActors][3], rq[kMaxActors][4], rv[kMaxActors][3], rw[kMaxActors][3];
   Dn<K> q[kMaxGen], qd[kMaxGen], act[kMaxGen];
   Dn<K> cache[kTanMaxCache];
+  float qt[kMaxGen], vt[kMaxGen];  // drive position / velocity targets (constants of the derivative)
 };
 
 // Kinematics and dynamics of the substep's start state: link poses, velocities, motion subspaces,
-// the joint-space inertia M (armature included; packed lower in w.L) and tau - b in w.rhs.
+// the joint-space inertia M (armature included; packed lower in w.L) and tau - b in w.rhs. With
+// drives (a step, not a query: `drives`), each driven DOF adds kp (q* - q - h qd) + kd (v* - qd) to
+// tau and h (h kp + kd) to its diagonal of M (the implicit drive of the forward step).
 template <int K> __device__ void tangent_dynamics(const StepArgs& A, const EnvTypeTable* T, TanState<K>& s,
-                                                  TanWork<K>& w) {
+                                                  TanWork<K>& w, const bool drives = true) {
   const int L = T->n_links, n = T->n_gen;
   const float gx = A.gx, gy = A.gy, gz = A.gz;
   // ---- forward kinematics, velocities, bias accelerations, rigid inertias (links in order) ----
@@ -386,6 +389,11 @@ template <int K> __device__ void tangent_dynamics(const StepArgs& A, const EnvTy
       const int jd = T->jdof[li] + (i - T->gdof[li]);  // the DOF's row (a ball joint has three)
       tau = s.act[jd] - s.qd[jd] * T->damping[li];
       w.L[tri(i, i)] = w.L[tri(i, i)] + Dn<K>(T->armature[li]);
+      if (drives && T->has_drives) {
+        const float kp = T->drive_kp[li], kd = T->drive_kd[li], h = A.h;
+        tau = tau + (Dn<K>(s.qt[jd]) - s.q[jd] - s.qd[jd] * h) * kp + (Dn<K>(s.vt[jd]) - s.qd[jd]) * kd;
+        w.L[tri(i, i)] = w.L[tri(i, i)] + Dn<K>(h * (h * kp + kd));
+      }
     }
     w.rhs[i] = tau - bi;
   }

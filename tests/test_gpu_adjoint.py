@@ -60,7 +60,7 @@ def direction(w, r, cache, rng):
     return dr, dd, da, dc
 
 
-def oracle_tangent(w, r, d, c, a, t, single=False, nudge=None):
+def oracle_tangent(w, r, d, c, a, t, single=False, nudge=None, targets=None):
     O = oracle.Oracle(w)
     r, d = r.copy(), d.copy()
     if nudge is not None:
@@ -68,7 +68,8 @@ def oracle_tangent(w, r, d, c, a, t, single=False, nudge=None):
         d[:, 0] = _ulp(d[:, 0], -nudge)
     O.cache[:] = c
     tr, td, tc = t[0].copy(), t[1].copy(), t[3].copy()
-    O.step_tangent(r, d, a, tr, td, t[2], tc, single=single)
+    pt, vt = targets if targets is not None else (None, None)
+    O.step_tangent(r, d, a, tr, td, t[2], tc, single=single, pos_target=pt, vel_target=vt)
     return r, d, O.cache.copy(), tr, td, tc
 
 
@@ -97,22 +98,38 @@ def env_max(arrs, sl):
     return max(float(np.abs(x[s]).max()) if x[s].size else 0.0 for x, s in zip(arrs, sl))
 
 
+def _driven_ant(n):
+    from test_gpu_control import driven_ant
+    return W.homogeneous("ant_driven", driven_ant(), n)
+
+
 WORKLOADS = {"ant": W.ant_workload, "humanoid": W.humanoid_workload, "cartpole": W.cartpole_workload,
-             "ball_ant": lambda n: W.homogeneous("ball_ant", W.ant(ball_hips=True), n)}
+             "ball_ant": lambda n: W.homogeneous("ball_ant", W.ant(ball_hips=True), n), "driven_ant": _driven_ant}
 
 
-@pytest.mark.parametrize("name,n", [("ant", 67), ("humanoid", 37), ("cartpole", 67), ("ball_ant", 40)])
+@pytest.mark.parametrize("name,n", [("ant", 67), ("humanoid", 37), ("cartpole", 67), ("ball_ant", 40),
+                                    ("driven_ant", 40)])
 def test_jvp_value_and_tangent_match_oracle(name, n):
+    """(driven_ant: joint drives with random position / velocity targets in the handle's target
+    views, constants of the derivative)"""
+    import torch
     from paper_2108_10470_gb300 import sim
     w = WORKLOADS[name](n)
     r, d, c, a = warm(w, seed=1)
     t = direction(w, r, c, np.random.default_rng(2))
     s = sim.Sim(w)
+    targets = None
+    if name == "driven_ant":
+        rng = np.random.default_rng(9)
+        targets = (rng.uniform(-0.3, 0.3, w.n_dof).astype(np.float32).astype(np.float64),
+                   rng.uniform(-0.5, 0.5, w.n_dof).astype(np.float32).astype(np.float64))
+        s.dof_position_target.copy_(torch.from_numpy(targets[0].astype(np.float32)))
+        s.dof_velocity_target.copy_(torch.from_numpy(targets[1].astype(np.float32)))
     g = gpu_jvp(s, r, d, c, a, t)
     s.destroy()
     assert not g["status"].any()
-    ref = oracle_tangent(w, r, d, c, a, t)
-    probes = [oracle_tangent(w, r, d, c, a, t, single=True, nudge=x) for x in (None, 1, -1)]
+    ref = oracle_tangent(w, r, d, c, a, t, targets=targets)
+    probes = [oracle_tangent(w, r, d, c, a, t, single=True, nudge=x, targets=targets) for x in (None, 1, -1)]
     val_keys = ("root_state_out", "dof_state_out", "impulse_cache_out")
     tan_keys = ("tan_root_state_out", "tan_dof_state_out", "tan_impulse_cache_out")
     bad_val, bad_tan, checked = [], [], 0
@@ -134,7 +151,7 @@ def test_jvp_value_and_tangent_match_oracle(name, n):
     assert len(bad_tan) <= 0.05 * checked, bad_tan
 
 
-@pytest.mark.parametrize("name,n", [("ant", 40), ("humanoid", 20), ("ball_ant", 20)])
+@pytest.mark.parametrize("name,n", [("ant", 40), ("humanoid", 20), ("ball_ant", 20), ("driven_ant", 20)])
 def test_vjp_is_the_transpose_of_the_jvp(name, n):
     """<g, J u> (tangent mode) equals <J^T g, u> (adjoint mode) per env, for random g and u."""
     import torch

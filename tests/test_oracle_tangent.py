@@ -128,3 +128,53 @@ def test_free_flight_closed_form():
         assert abs(dr[0, k] - w.dt) < 1e-15
         assert abs(dr[0, 7 + k] - 1.0) < 1e-15
         assert np.abs(np.delete(dr[0], [k, 7 + k])).max() < 1e-15
+
+
+def _driven_ant_workload(n, kp=60.0, kd=4.0):
+    m = W.ant()
+    kps = np.where(np.isin(m.jtype, [W.JOINT_REVOLUTE, W.JOINT_PRISMATIC]), kp, 0.0)
+    kps[0] = 0.0
+    m.drive_kp = kps
+    m.drive_kd = np.where(kps > 0, kd, 0.0)
+    return W.homogeneous("ant_driven", m, n)
+
+
+def test_drives_with_per_env_targets():
+    """Joint drives with targets that differ per env (constants of the derivative): the tangent
+    step's values equal the plain step's with the same targets, bit for bit, in every env, and its
+    directional derivative equals central differences of that step."""
+    w = _driven_ant_workload(5)
+    O, r, d, a = warm_state(w, seed=6)
+    rng = np.random.default_rng(7)
+    pt = rng.uniform(-0.3, 0.3, O.N_D)
+    vt = rng.uniform(-0.5, 0.5, O.N_D)
+
+    def plain(cache, r0, d0, a0):
+        P = oracle.Oracle(w)
+        P.cache[:] = cache
+        r1, d1 = r0.copy(), d0.copy()
+        out = P.step(r1, d1, a0, pos_target=pt, vel_target=vt)
+        return r1, d1, P.cache.copy(), out["signature"]
+
+    dr, dd, da, dc = random_direction(w, O, r, rng)
+    c0 = O.cache.copy()
+    r1, d1 = r.copy(), d.copy()
+    tr, td, tc = dr.copy(), dd.copy(), dc.copy()
+    O.step_tangent(r1, d1, a, tr, td, da, tc, pos_target=pt, vel_target=vt)
+    z = plain(c0, r, d, a)
+    assert np.array_equal(r1, z[0]) and np.array_equal(d1, z[1]) and np.array_equal(O.cache, z[2])
+    # the targets matter: without them the step differs
+    assert not np.array_equal(d1, plain_step(w, c0, r, d, a)[1])
+    eps = 1e-7
+    p = plain(c0 + eps * dc, r + eps * dr, d + eps * dd, a + eps * da)
+    m = plain(c0 - eps * dc, r - eps * dr, d - eps * dd, a - eps * da)
+    checked = 0
+    for e in np.nonzero(p[3] == m[3])[0]:
+        sl = [slice(e, e + 1), slice(e * O.N_D // w.n_envs, (e + 1) * O.N_D // w.n_envs), slice(e, e + 1)]
+        tang = (tr, td, tc)
+        for k in range(3):
+            scale = max(1.0, np.abs(tang[k][sl[k]]).max())
+            fd = (p[k][sl[k]] - m[k][sl[k]]) / (2 * eps)
+            assert np.abs(fd - tang[k][sl[k]]).max() <= 1e-6 * scale, (e, k)
+        checked += 1
+    assert checked >= 3
