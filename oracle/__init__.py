@@ -79,9 +79,9 @@ def lib():
         L.oracle_step_flops.restype = ctypes.c_double
         L.oracle_step_f32.argtypes = [ctypes.c_void_p, D, D, D, D, ctypes.c_double, ctypes.c_int32, D]
         L.oracle_step_tangent.argtypes = [ctypes.c_void_p, D, D, D, D, D, D, D, D, ctypes.c_double, ctypes.c_int32,
-                                          ctypes.c_int32, D, D]
+                                          ctypes.c_int32, D, D, D]
         L.oracle_step_tangent_f32.argtypes = [ctypes.c_void_p, D, D, D, D, D, D, D, D, ctypes.c_double,
-                                              ctypes.c_int32, D, D]
+                                              ctypes.c_int32, D, D, D]
         L.oracle_step_f32.restype = ctypes.c_int32
         L.oracle_capsule_box.argtypes = [D, D, ctypes.c_double, D, D]
         L.oracle_capsule_box.restype = None
@@ -249,11 +249,12 @@ class Oracle:
         return nf
 
     def step_tangent(self, root, dof, act, droot, ddof, dact, dcache, dt=None, substeps=None, n_threads=1,
-                     single=False, pos_target=None, vel_target=None):
+                     single=False, pos_target=None, vel_target=None, body_force=None):
         """One env-step in forward-mode dual numbers. root, dof and self.cache advance in place like
         step; droot (N_A,13), ddof (N_D,2) and dcache (n_envs, cache_len) hold the input tangent and
         are overwritten with the output tangent; dact (N_D,) is the actuation tangent; pos_target /
-        vel_target (N_D,) are drive targets (constants; 0 when omitted). single=True evaluates the
+        vel_target (N_D,) are drive targets and body_force (N_B,6) external forces and torques
+        (constants; 0 when omitted). single=True evaluates the
         identical derivative in single precision (conditioning probe). Returns the number of failed
         envs."""
         dt = self.w.dt if dt is None else dt
@@ -266,8 +267,9 @@ class Oracle:
         nd = self.N_D > 0
         args = (self.h, _dp(root), _dp(dof) if nd else None, _dp(self.cache), _dp(a) if nd else None, _dp(droot),
                 _dp(ddof) if nd else None, _dp(dcache), _dp(da) if nd else None, float(dt), int(substeps))
-        tg = [None if x is None else np.ascontiguousarray(x, dtype=np.float64).reshape(self.N_D)
-              for x in (pos_target, vel_target)]  # kept alive through the call
+        tg = [None if x is None else np.ascontiguousarray(x, dtype=np.float64).reshape(-1)
+              for x in (pos_target, vel_target, body_force)]  # kept alive through the call
+        assert all(x is None or x.size == n for x, n in zip(tg, (self.N_D, self.N_D, self.N_B * 6)))
         tp = [None if x is None or x.size == 0 else _dp(x) for x in tg]
         if single:
             return int(lib().oracle_step_tangent_f32(*args, *tp))

@@ -1200,14 +1200,15 @@ namespace orc {
 template <class D> int32_t step_tangent_t(void* h, double* root, double* dof, double* cache, const double* act,
                                          double* droot, double* ddof, double* dcache, const double* dact, double dt,
                                          int32_t substeps, int32_t n_threads, const double* pos_target = nullptr,
-                                         const double* vel_target = nullptr) {
+                                         const double* vel_target = nullptr, const double* body_force = nullptr) {
   const Oracle* O = (const Oracle*)h;
   std::atomic<int> bad{0};
   if (n_threads < 1) n_threads = 1;
   auto one = [&](int env) {
-    Controls ctl;  // the env's drive targets (constants of the derivative; zero when absent)
+    Controls ctl;  // the env's drive targets and body forces (constants of the derivative; zero when absent)
     if (pos_target) ctl.pos_target = pos_target + O->jdof_off[env];
     if (vel_target) ctl.vel_target = vel_target + O->jdof_off[env];
+    if (body_force) ctl.body_force = body_force + O->body_off[env] * 6;
     std::vector<ActorState<D>> st;
     load_env(*O, env, root, dof, st);
     int64_t jd = O->jdof_off[env];
@@ -1506,17 +1507,19 @@ double oracle_step_flops(void* h, double* root, double* dof, double* cache, cons
 // with its constraint and active sets held at the values' choices. Returns the failed-env count.
 int32_t oracle_step_tangent(void* h, double* root, double* dof, double* cache, const double* act, double* droot,
                             double* ddof, double* dcache, const double* dact, double dt, int32_t substeps,
-                            int32_t n_threads, const double* pos_target, const double* vel_target) {
+                            int32_t n_threads, const double* pos_target, const double* vel_target,
+                            const double* body_force) {
   return step_tangent_t<Dual>(h, root, dof, cache, act, droot, ddof, dcache, dact, dt, substeps, n_threads, pos_target,
-                              vel_target);
+                              vel_target, body_force);
 }
 
 // The same derivative evaluated in single precision (conditioning probe for the GPU derivative).
 int32_t oracle_step_tangent_f32(void* h, double* root, double* dof, double* cache, const double* act,
                                 double* droot, double* ddof, double* dcache, const double* dact, double dt,
-                                int32_t substeps, const double* pos_target, const double* vel_target) {
+                                int32_t substeps, const double* pos_target, const double* vel_target,
+                                const double* body_force) {
   return step_tangent_t<DualF>(h, root, dof, cache, act, droot, ddof, dcache, dact, dt, substeps, 1, pos_target,
-                               vel_target);
+                               vel_target, body_force);
 }
 
 // The same step evaluated in single precision (a conditioning probe for the parity tests: it

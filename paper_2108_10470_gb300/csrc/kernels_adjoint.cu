@@ -73,6 +73,7 @@ __global__ void __launch_bounds__(64) tangent_step_kernel(const __grid_constant_
       s.vt[j] = T->has_drives ? A.vel_target[dbase + j] : 0.f;
     }
     for (int i = 0; i < nc; ++i) s.cache[i] = Dn<K>(V.cache[cbase + i]);
+    s.bf = (A.flags & 8) ? A.body_force + (size_t)A.env_body_base[env] * 6 : nullptr;
   };
   bool ok = true;
 

@@ -544,10 +544,6 @@ int plan_persistent(sim_s* h) {
 
 // The derivative kernel covers env types with ground contacts only and a bounded impulse cache.
 int tangent_supported(const sim_s* h) {
-  if (h->params.flags & SIM_FLAG_BODY_FORCES) {
-    g_last_error = "step derivative: external body forces are not part of the differentiated step";
-    return SIM_ERR_CAPACITY;
-  }
   for (const TypePlan& tp : h->types)
     if (tp.tab.n_tendons > 0) {
       g_last_error = "step derivative: tendons are not part of the differentiated step";

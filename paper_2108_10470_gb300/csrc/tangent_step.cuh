@@ -219,6 +219,7 @@ template <int K> struct TanState {
   Dn<K> q[kMaxGen], qd[kMaxGen], act[kMaxGen];
   Dn<K> cache[kTanMaxCache];
   float qt[kMaxGen], vt[kMaxGen];  // drive position / velocity targets (constants of the derivative)
+  const float* bf = nullptr;       // the env's external body forces (N_B rows of 6) or null (constants)
 };
 
 // Kinematics and dynamics of the substep's start state: link poses, velocities, motion subspaces,
@@ -352,8 +353,17 @@ template <int K> __device__ void tangent_dynamics(const StepArgs& A, const EnvTy
     Imul(w.Ab[l], Ga, Gl);
     const DV3<K> wv = dv3<K>(w.V[l][0], w.V[l][1], w.V[l][2]), vl = dv3<K>(w.V[l][3], w.V[l][4], w.V[l][5]);
     const DV3<K> g = dv3<K>(Dn<K>(gx), Dn<K>(gy), Dn<K>(gz));
-    const DV3<K> pa = Ga + dcross(wv, Fa) + dcross(vl, Fl) - dcross(hh, g);
-    const DV3<K> pl = Gl + dcross(wv, Fl) - g * I[0];
+    DV3<K> pa = Ga + dcross(wv, Fa) + dcross(vl, Fl) - dcross(hh, g);
+    DV3<K> pl = Gl + dcross(wv, Fl) - g * I[0];
+    if (s.bf && T->body[l] >= 0) {
+      // external force F and torque at the COM c (world axes): c x F + torque about the origin
+      const float* f = s.bf + (size_t)T->body[l] * 6;
+      const DV3<K> cw = dv3<K>(w.P[l][0], w.P[l][1], w.P[l][2]) +
+                        dmv<K>(w.R[l], dv3<K>(Dn<K>(T->com[0][l]), Dn<K>(T->com[1][l]), Dn<K>(T->com[2][l])));
+      const DV3<K> F = dv3<K>(Dn<K>(f[0]), Dn<K>(f[1]), Dn<K>(f[2]));
+      pa = pa - (dcross(cw, F) + dv3<K>(Dn<K>(f[3]), Dn<K>(f[4]), Dn<K>(f[5])));
+      pl = pl - F;
+    }
     w.Ab[l][0] = pa.x; w.Ab[l][1] = pa.y; w.Ab[l][2] = pa.z; w.Ab[l][3] = pl.x; w.Ab[l][4] = pl.y; w.Ab[l][5] = pl.z;
   }
   // ---- subtree sums (children after parents: sweep links backwards) ----

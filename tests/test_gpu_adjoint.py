@@ -60,7 +60,7 @@ def direction(w, r, cache, rng):
     return dr, dd, da, dc
 
 
-def oracle_tangent(w, r, d, c, a, t, single=False, nudge=None, targets=None):
+def oracle_tangent(w, r, d, c, a, t, single=False, nudge=None, ctl=None):
     O = oracle.Oracle(w)
     r, d = r.copy(), d.copy()
     if nudge is not None:
@@ -68,8 +68,7 @@ def oracle_tangent(w, r, d, c, a, t, single=False, nudge=None, targets=None):
         d[:, 0] = _ulp(d[:, 0], -nudge)
     O.cache[:] = c
     tr, td, tc = t[0].copy(), t[1].copy(), t[3].copy()
-    pt, vt = targets if targets is not None else (None, None)
-    O.step_tangent(r, d, a, tr, td, t[2], tc, single=single, pos_target=pt, vel_target=vt)
+    O.step_tangent(r, d, a, tr, td, t[2], tc, single=single, **(ctl or {}))
     return r, d, O.cache.copy(), tr, td, tc
 
 
@@ -104,32 +103,47 @@ def _driven_ant(n):
 
 
 WORKLOADS = {"ant": W.ant_workload, "humanoid": W.humanoid_workload, "cartpole": W.cartpole_workload,
-             "ball_ant": lambda n: W.homogeneous("ball_ant", W.ant(ball_hips=True), n), "driven_ant": _driven_ant}
+             "ball_ant": lambda n: W.homogeneous("ball_ant", W.ant(ball_hips=True), n), "driven_ant": _driven_ant,
+             "pushed_ant": W.ant_workload}
+
+
+def make_sim(name, w, seed=9):
+    """The handle for a workload and the controls it carries (random per-env drive targets for
+    driven_ant, random external body forces for pushed_ant: constants of the derivative), as the
+    oracle's keyword arguments (values rounded to FP32 like the views)."""
+    import torch
+    from paper_2108_10470_gb300 import sim
+    rng = np.random.default_rng(seed)
+    r32 = lambda x: x.astype(np.float32).astype(np.float64)
+    t32 = lambda x: torch.from_numpy(x.astype(np.float32))
+    if name == "driven_ant":
+        s = sim.Sim(w)
+        ctl = dict(pos_target=r32(rng.uniform(-0.3, 0.3, w.n_dof)), vel_target=r32(rng.uniform(-0.5, 0.5, w.n_dof)))
+        s.dof_position_target.copy_(t32(ctl["pos_target"]))
+        s.dof_velocity_target.copy_(t32(ctl["vel_target"]))
+        return s, ctl
+    if name == "pushed_ant":
+        s = sim.Sim(w, flags=sim.SIM_FLAG_BODY_FORCES)
+        ctl = dict(body_force=r32(rng.uniform(-3.0, 3.0, (w.n_body, 6))))
+        s.rigid_body_force.copy_(t32(ctl["body_force"]))
+        return s, ctl
+    return sim.Sim(w), None
 
 
 @pytest.mark.parametrize("name,n", [("ant", 67), ("humanoid", 37), ("cartpole", 67), ("ball_ant", 40),
-                                    ("driven_ant", 40)])
+                                    ("driven_ant", 40), ("pushed_ant", 40)])
 def test_jvp_value_and_tangent_match_oracle(name, n):
-    """(driven_ant: joint drives with random position / velocity targets in the handle's target
-    views, constants of the derivative)"""
-    import torch
-    from paper_2108_10470_gb300 import sim
+    """(driven_ant / pushed_ant: drive targets / body forces from the handle's views, constants of
+    the derivative)"""
     w = WORKLOADS[name](n)
     r, d, c, a = warm(w, seed=1)
     t = direction(w, r, c, np.random.default_rng(2))
-    s = sim.Sim(w)
-    targets = None
-    if name == "driven_ant":
-        rng = np.random.default_rng(9)
-        targets = (rng.uniform(-0.3, 0.3, w.n_dof).astype(np.float32).astype(np.float64),
-                   rng.uniform(-0.5, 0.5, w.n_dof).astype(np.float32).astype(np.float64))
-        s.dof_position_target.copy_(torch.from_numpy(targets[0].astype(np.float32)))
-        s.dof_velocity_target.copy_(torch.from_numpy(targets[1].astype(np.float32)))
+    s, ctl = make_sim(name, w)
     g = gpu_jvp(s, r, d, c, a, t)
     s.destroy()
     assert not g["status"].any()
-    ref = oracle_tangent(w, r, d, c, a, t, targets=targets)
-    probes = [oracle_tangent(w, r, d, c, a, t, single=True, nudge=x, targets=targets) for x in (None, 1, -1)]
+    ref = oracle_tangent(w, r, d, c, a, t, ctl=ctl)
+    probes = [oracle_tangent(w, r, d, c, a, t, single=True, nudge=x, ctl=ctl) for x in (None, 1, -1)]
     val_keys = ("root_state_out", "dof_state_out", "impulse_cache_out")
     tan_keys = ("tan_root_state_out", "tan_dof_state_out", "tan_impulse_cache_out")
     bad_val, bad_tan, checked = [], [], 0
@@ -151,7 +165,8 @@ def test_jvp_value_and_tangent_match_oracle(name, n):
     assert len(bad_tan) <= 0.05 * checked, bad_tan
 
 
-@pytest.mark.parametrize("name,n", [("ant", 40), ("humanoid", 20), ("ball_ant", 20), ("driven_ant", 20)])
+@pytest.mark.parametrize("name,n", [("ant", 40), ("humanoid", 20), ("ball_ant", 20), ("driven_ant", 20),
+                                    ("pushed_ant", 20)])
 def test_vjp_is_the_transpose_of_the_jvp(name, n):
     """<g, J u> (tangent mode) equals <J^T g, u> (adjoint mode) per env, for random g and u."""
     import torch
@@ -161,7 +176,7 @@ def test_vjp_is_the_transpose_of_the_jvp(name, n):
     rng = np.random.default_rng(4)
     u = direction(w, r, c, rng)
     gout = (rng.standard_normal(r.shape), rng.standard_normal(d.shape), rng.standard_normal(c.shape) * (c != 0))
-    s = sim.Sim(w)
+    s, _ = make_sim(name, w)
     jv = gpu_jvp(s, r, d, c, a, u)
     f = lambda x: torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda()
     bufs = {"root_state": f(r), "dof_state": f(d), "dof_actuation": f(a), "impulse_cache": f(c),

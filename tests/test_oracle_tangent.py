@@ -139,31 +139,34 @@ def _driven_ant_workload(n, kp=60.0, kd=4.0):
     return W.homogeneous("ant_driven", m, n)
 
 
-def test_drives_with_per_env_targets():
-    """Joint drives with targets that differ per env (constants of the derivative): the tangent
-    step's values equal the plain step's with the same targets, bit for bit, in every env, and its
-    directional derivative equals central differences of that step."""
-    w = _driven_ant_workload(5)
+@pytest.mark.parametrize("control", ["drives", "body_forces"])
+def test_controls_with_per_env_values(control):
+    """Joint drives with targets, or external body forces, that differ per env (constants of the
+    derivative): the tangent step's values equal the plain step's with the same controls, bit for
+    bit, in every env, and its directional derivative equals central differences of that step."""
+    w = _driven_ant_workload(5) if control == "drives" else W.ant_workload(5)
     O, r, d, a = warm_state(w, seed=6)
     rng = np.random.default_rng(7)
-    pt = rng.uniform(-0.3, 0.3, O.N_D)
-    vt = rng.uniform(-0.5, 0.5, O.N_D)
+    if control == "drives":
+        ctl = dict(pos_target=rng.uniform(-0.3, 0.3, O.N_D), vel_target=rng.uniform(-0.5, 0.5, O.N_D))
+    else:
+        ctl = dict(body_force=rng.uniform(-3.0, 3.0, (O.N_B, 6)))
 
     def plain(cache, r0, d0, a0):
         P = oracle.Oracle(w)
         P.cache[:] = cache
         r1, d1 = r0.copy(), d0.copy()
-        out = P.step(r1, d1, a0, pos_target=pt, vel_target=vt)
+        out = P.step(r1, d1, a0, **ctl)
         return r1, d1, P.cache.copy(), out["signature"]
 
     dr, dd, da, dc = random_direction(w, O, r, rng)
     c0 = O.cache.copy()
     r1, d1 = r.copy(), d.copy()
     tr, td, tc = dr.copy(), dd.copy(), dc.copy()
-    O.step_tangent(r1, d1, a, tr, td, da, tc, pos_target=pt, vel_target=vt)
+    O.step_tangent(r1, d1, a, tr, td, da, tc, **ctl)
     z = plain(c0, r, d, a)
     assert np.array_equal(r1, z[0]) and np.array_equal(d1, z[1]) and np.array_equal(O.cache, z[2])
-    # the targets matter: without them the step differs
+    # the controls matter: without them the step differs
     assert not np.array_equal(d1, plain_step(w, c0, r, d, a)[1])
     eps = 1e-7
     p = plain(c0 + eps * dc, r + eps * dr, d + eps * dd, a + eps * da)
