@@ -284,9 +284,9 @@ int sim_autotune(sim_handle h, float dt, int32_t substeps, int32_t reps, double*
  * actuation is the step's control input. Net contact forces and the contact views are not
  * differentiated. Joint drives act as in the step, with the handle's DOF_POSITION_TARGET /
  * DOF_VELOCITY_TARGET views as constants (no gradient with respect to the targets), and so do the
- * RIGID_BODY_FORCE view's forces under SIM_FLAG_BODY_FORCES. Supported for env types without
- * capsule-box pairs or tendons whose impulse cache has at most 384 entries; other handles fail
- * with CAPACITY. Computed by forward-mode dual arithmetic, one
+ * RIGID_BODY_FORCE view's forces under SIM_FLAG_BODY_FORCES; tendon springs and tendon-limit rows
+ * are differentiated. Supported for env types without capsule-box pairs whose impulse cache has at
+ * most 384 entries; other handles fail with CAPACITY. Computed by forward-mode dual arithmetic, one
  * env per warp, each lane carrying up to 8 input directions, in passes of 256 directions per env.
  * (The paper does not differentiate its step; this is the project's own extension.) */
 typedef struct {

@@ -545,11 +545,6 @@ int plan_persistent(sim_s* h) {
 // The derivative kernel covers env types with ground contacts only and a bounded impulse cache.
 int tangent_supported(const sim_s* h) {
   for (const TypePlan& tp : h->types)
-    if (tp.tab.n_tendons > 0) {
-      g_last_error = "step derivative: tendons are not part of the differentiated step";
-      return SIM_ERR_CAPACITY;
-    }
-  for (const TypePlan& tp : h->types)
     if (tp.tab.n_pairs > 0 || tp.tab.cache_len > 384) {
       g_last_error = "step derivative: env types with capsule-box pairs or more than 384 impulse-cache entries "
                      "are not supported";

@@ -118,7 +118,7 @@ template <int K> __device__ __forceinline__ void dmm(const Dn<K>* A, const Dn<K>
 
 // ---- per-lane work space (local memory) --------------------------------------------------------
 constexpr int kTanMaxCon = 64;                       // kept ground contacts per env
-constexpr int kTanMaxRows = 2 * kMaxGen + 3 * kTanMaxCon;
+constexpr int kTanMaxRows = 2 * (kMaxGen + kMaxTendons) + 3 * kTanMaxCon;
 constexpr int kTanMaxCache = 384;                    // impulse-cache entries per env
 
 template <int K> struct TanWork {
@@ -187,9 +187,10 @@ template <int K> __device__ __forceinline__ void dquat_rotvec(const Dn<K>* q, Dn
 // limit rows (unit +-1 on one DOF), contact normal / friction rows along e_z, e_x, e_y.
 template <int K> __device__ void row_response(const EnvTypeTable* T, const TanWork<K>& w, int n, int kind, int gdof,
                                               float sgn, int c, int dir, Dn<K>* y) {
-  const unsigned anc = kind == kRowLimit ? 0u : T->anc[w.clink[c]];
+  const bool jrow = kind == kRowLimit || kind == kRowTendon;  // rows on joint coordinates
+  const unsigned anc = jrow ? 0u : T->anc[w.clink[c]];
   Dn<K> fr[6];
-  if (kind != kRowLimit) {
+  if (!jrow) {
     // k = e_z (normal), e_x, e_y (friction); f = [x x k; k]
     const Dn<K>& x0 = w.cx[c][0];
     const Dn<K>& x1 = w.cx[c][1];
@@ -203,6 +204,11 @@ template <int K> __device__ void row_response(const EnvTypeTable* T, const TanWo
     Dn<K> ji(0.f);
     if (kind == kRowLimit) {
       if (i == gdof) ji = Dn<K>(sgn);
+    } else if (kind == kRowTendon) {  // gdof holds the tendon: J = +-c over its joints
+      float jt = 0.f;
+      for (int k = 0; k < T->ten_n[gdof]; ++k)
+        if (T->gdof[T->ten_link[gdof][k]] == i) jt += sgn * T->ten_coef[gdof][k];
+      ji = Dn<K>(jt);
     } else if ((anc >> i) & 1u) {
 #pragma unroll
       for (int k = 0; k < 6; ++k) ji = ji + w.S[i][k] * fr[k];
@@ -404,6 +410,21 @@ template <int K> __device__ void tangent_dynamics(const StepArgs& A, const EnvTy
         tau = tau + (Dn<K>(s.qt[jd]) - s.q[jd] - s.qd[jd] * h) * kp + (Dn<K>(s.vt[jd]) - s.qd[jd]) * kd;
         w.L[tri(i, i)] = w.L[tri(i, i)] + Dn<K>(h * (h * kp + kd));
       }
+      // fixed tendons: F = -k (l - rest) - d l_dot on the length l = sum c q (substep start),
+      // applied to each of the tendon's joints as c F
+      for (int t = 0; t < T->n_tendons; ++t) {
+        Dn<K> len(0.f), rate(0.f);
+        float mine = 0.f;
+        for (int k = 0; k < T->ten_n[t]; ++k) {
+          const int lk = T->ten_link[t][k], jk = T->jdof[lk];
+          const float c = T->ten_coef[t][k];
+          len = len + s.q[jk] * c;
+          rate = rate + s.qd[jk] * c;
+          if (lk == li) mine += c;
+        }
+        if (mine != 0.f)
+          tau = tau + ((len - Dn<K>(T->ten_rest[t])) * (-T->ten_k[t]) - rate * T->ten_d[t]) * mine;
+      }
     }
     w.rhs[i] = tau - bi;
   }
@@ -515,6 +536,14 @@ template <int K> __device__ int read_slots(const StepArgs& A, const EnvTypeTable
     if (s.q[jd].v - T->lo[l] < A.limit_margin) slots[m++] = 3 * T->n_cand + 2 * jd;
     if (T->hi[l] - s.q[jd].v < A.limit_margin) slots[m++] = 3 * T->n_cand + 2 * jd + 1;
   }
+  for (int t = 0; t < T->n_tendons; ++t) {
+    if (!T->ten_has_limit[t]) continue;
+    float tl = 0.f;
+    for (int k = 0; k < T->ten_n[t]; ++k) tl += T->ten_coef[t][k] * s.q[T->jdof[T->ten_link[t][k]]].v;
+    const int slot0 = 3 * T->n_cand + 2 * T->n_jdof + 2 * t;
+    if (tl - T->ten_lo[t] < A.limit_margin) slots[m++] = slot0;
+    if (T->ten_hi[t] - tl < A.limit_margin) slots[m++] = slot0 + 1;
+  }
   for (int c = 0; c < nc; ++c)
     for (int d = 0; d < 3; ++d) slots[m++] = 3 * w.ccand[c] + d;
   return m;
@@ -555,10 +584,11 @@ template <int K> __device__ bool tangent_substep(const StepArgs& A, const EnvTyp
   }
   const int nc = tangent_contacts<K>(A, T, s, w);
   if (nc < 0) return false;
-  // ---- rows: limits (link order, lower before upper), normals, friction pairs ----
-  // row r is described on the fly: r < nl: limit list; then contact normals; then frictions
-  int lim_g[2 * kMaxGen], lim_side[2 * kMaxGen], lim_jd[2 * kMaxGen];
-  Dn<K> lim_d[2 * kMaxGen];
+  // ---- rows: joint limits (link order, lower before upper), tendon limits (tendon order), normals,
+  // friction pairs. Row r is described on the fly: r < nl: limit list; then contact normals; then
+  // frictions. A tendon row keeps its tendon in lim_g and -1 - slot offset in lim_jd.
+  int lim_g[2 * (kMaxGen + kMaxTendons)], lim_side[2 * (kMaxGen + kMaxTendons)], lim_jd[2 * (kMaxGen + kMaxTendons)];
+  Dn<K> lim_d[2 * (kMaxGen + kMaxTendons)];
   int nl = 0;
   for (int l = 0; l < L; ++l) {
     const int jt = T->jtype[l];
@@ -568,13 +598,21 @@ template <int K> __device__ bool tangent_substep(const StepArgs& A, const EnvTyp
     if (dlo.v < A.limit_margin) { lim_g[nl] = T->gdof[l]; lim_side[nl] = 0; lim_jd[nl] = jd; lim_d[nl] = dlo; ++nl; }
     if (dhi.v < A.limit_margin) { lim_g[nl] = T->gdof[l]; lim_side[nl] = 1; lim_jd[nl] = jd; lim_d[nl] = dhi; ++nl; }
   }
+  for (int t = 0; t < T->n_tendons; ++t) {
+    if (!T->ten_has_limit[t]) continue;
+    Dn<K> tl(0.f);
+    for (int k = 0; k < T->ten_n[t]; ++k) tl = tl + s.q[T->jdof[T->ten_link[t][k]]] * T->ten_coef[t][k];
+    const Dn<K> dlo = tl - Dn<K>(T->ten_lo[t]), dhi = Dn<K>(T->ten_hi[t]) - tl;
+    if (dlo.v < A.limit_margin) { lim_g[nl] = t; lim_side[nl] = 0; lim_jd[nl] = -1; lim_d[nl] = dlo; ++nl; }
+    if (dhi.v < A.limit_margin) { lim_g[nl] = t; lim_side[nl] = 1; lim_jd[nl] = -1; lim_d[nl] = dhi; ++nl; }
+  }
   const int R = nl + 3 * nc;
   if (R > kTanMaxRows) return false;
   Dn<K> y[kMaxGen];
   auto describe = [&](int r, int& kind, int& g, float& sgn, int& c, int& dir, int& slot) {
     if (r < nl) {
-      kind = kRowLimit; g = lim_g[r]; sgn = lim_side[r] ? -1.f : 1.f; c = 0; dir = 0;
-      slot = 3 * T->n_cand + 2 * lim_jd[r] + lim_side[r];
+      kind = lim_jd[r] >= 0 ? kRowLimit : kRowTendon; g = lim_g[r]; sgn = lim_side[r] ? -1.f : 1.f; c = 0; dir = 0;
+      slot = 3 * T->n_cand + 2 * (lim_jd[r] >= 0 ? lim_jd[r] : T->n_jdof + lim_g[r]) + lim_side[r];
     } else if (r < nl + nc) {
       kind = kRowNormal; c = r - nl; dir = 0; g = 0; sgn = 0.f; slot = 3 * w.ccand[c];
     } else {
@@ -605,7 +643,7 @@ template <int K> __device__ bool tangent_substep(const StepArgs& A, const EnvTyp
       Dn<K> a2(0.f), yz(0.f), ydz(0.f);
       for (int i = 0; i < n; ++i) { a2 = a2 + y[i] * y[i]; yz = yz + y[i] * w.z[i]; ydz = ydz + y[i] * w.dz[i]; }
       if (!(a2.v > 1e-12f)) continue;
-      const Dn<K> dr = (kind == kRowLimit) ? lim_d[r] : w.cd[c];
+      const Dn<K> dr = (kind == kRowLimit || kind == kRowTendon) ? lim_d[r] : w.cd[c];
       const Dn<K> sep = dr + ydz;
       const Dn<K> lam = w.lam[r];
       Dn<K> lnew;

@@ -268,13 +268,15 @@ ANT_SHIN = 0.40
 ANT_KNEE_TILT = math.pi / 4  # shin points outward and 45 degrees down at q = 0
 
 
-def ant(density=5.0, armature=1.0, damping=1.0, gear=15.0, friction=1.0, ball_hips=False) -> Model:
+def ant(density=5.0, armature=1.0, damping=1.0, gear=15.0, friction=1.0, ball_hips=False, tendons=False) -> Model:
     """Ant-like quadruped: floating sphere torso (r 0.25, 0.33 kg), four legs at azimuths
     45/135/225/315 degrees, each a hip hinge about z (+-30 deg) carrying a 0.28 m thigh capsule and a
     knee hinge about the horizontal axis perpendicular to the leg (+-70 deg) carrying a 0.40 m shin
     capsule (radius 0.08). 9 links, 8 joint DOF, 14 generalized DOF. With ball_hips, each hip is a
-    ball joint (3 DOF, no limits): 16 joint DOF, 22 generalized DOF."""
-    b = _Builder("ball_ant" if ball_hips else "ant")
+    ball joint (3 DOF, no limits): 16 joint DOF, 22 generalized DOF. With tendons (hinge hips only):
+    a spring-damper tendon on leg 0's hip and knee, a length-limited tendon on the knees of legs 1
+    and 2, and an equality tendon on the hips of legs 2 and 3."""
+    b = _Builder("ball_ant" if ball_hips else ("tendon_ant" if tendons else "ant"))
     mt, it = sphere_mass(ANT_TORSO_R, density)
     torso = b.link(-1, JOINT_FREE, mass=mt, inertia=it)
     b.shape(torso, SHAPE_SPHERE, (ANT_TORSO_R,), friction=friction)
@@ -292,6 +294,10 @@ def ant(density=5.0, armature=1.0, damping=1.0, gear=15.0, friction=1.0, ball_hi
                       pquat=quat_axis_angle((0, 1, 0), ANT_KNEE_TILT), mass=m2, com=(ANT_SHIN / 2, 0, 0), inertia=i2,
                       armature=armature, damping=damping, limit=(-math.radians(70), math.radians(70)), gear=gear)
         b.shape(shin, SHAPE_CAPSULE, (ANT_LEG_R, ANT_SHIN / 2), pos=(ANT_SHIN / 2, 0, 0), friction=friction)
+    if tendons and not ball_hips:  # leg k: thigh link 1 + 2k, shin link 2 + 2k
+        b.tendon([1, 2], (1.0, -0.5), stiffness=30.0, damping=2.0, rest=0.1)
+        b.tendon([4, 6], (1.0, 1.0), limit=(-0.1, 0.1))
+        b.tendon([5, 7], (1.0, -1.0), limit=(0.0, 0.0))
     # lowest point at q = 0: shin tip minus its radius; start it 5 mm above the ground
     z0 = ANT_SHIN * math.sin(ANT_KNEE_TILT) + ANT_LEG_R + 0.005
     return b.build(root_pos=(0.0, 0.0, z0), dof_noise=0.1)

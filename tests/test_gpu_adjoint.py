@@ -104,7 +104,8 @@ def _driven_ant(n):
 
 WORKLOADS = {"ant": W.ant_workload, "humanoid": W.humanoid_workload, "cartpole": W.cartpole_workload,
              "ball_ant": lambda n: W.homogeneous("ball_ant", W.ant(ball_hips=True), n), "driven_ant": _driven_ant,
-             "pushed_ant": W.ant_workload}
+             "pushed_ant": W.ant_workload,
+             "tendon_ant": lambda n: W.homogeneous("tendon_ant", W.ant(tendons=True), n)}
 
 
 def make_sim(name, w, seed=9):
@@ -131,7 +132,7 @@ def make_sim(name, w, seed=9):
 
 
 @pytest.mark.parametrize("name,n", [("ant", 67), ("humanoid", 37), ("cartpole", 67), ("ball_ant", 40),
-                                    ("driven_ant", 40), ("pushed_ant", 40)])
+                                    ("driven_ant", 40), ("pushed_ant", 40), ("tendon_ant", 40)])
 def test_jvp_value_and_tangent_match_oracle(name, n):
     """(driven_ant / pushed_ant: drive targets / body forces from the handle's views, constants of
     the derivative)"""
@@ -166,7 +167,7 @@ def test_jvp_value_and_tangent_match_oracle(name, n):
 
 
 @pytest.mark.parametrize("name,n", [("ant", 40), ("humanoid", 20), ("ball_ant", 20), ("driven_ant", 20),
-                                    ("pushed_ant", 20)])
+                                    ("pushed_ant", 20), ("tendon_ant", 20)])
 def test_vjp_is_the_transpose_of_the_jvp(name, n):
     """<g, J u> (tangent mode) equals <J^T g, u> (adjoint mode) per env, for random g and u."""
     import torch
