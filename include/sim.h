@@ -285,8 +285,8 @@ int sim_autotune(sim_handle h, float dt, int32_t substeps, int32_t reps, double*
  * differentiated. Joint drives act as in the step, with the handle's DOF_POSITION_TARGET /
  * DOF_VELOCITY_TARGET views as constants (no gradient with respect to the targets), and so do the
  * RIGID_BODY_FORCE view's forces under SIM_FLAG_BODY_FORCES; tendon springs and tendon-limit rows
- * are differentiated. Supported for env types without capsule-box pairs whose impulse cache has at
- * most 384 entries; other handles fail with CAPACITY. Computed by forward-mode dual arithmetic, one
+ * are differentiated, and so are capsule-box pair contacts. Supported for env types whose impulse
+ * cache has at most 448 entries; other handles fail with CAPACITY. Computed by forward-mode dual arithmetic, one
  * env per warp, each lane carrying up to 8 input directions, in passes of 256 directions per env.
  * (The paper does not differentiate its step; this is the project's own extension.) */
 typedef struct {

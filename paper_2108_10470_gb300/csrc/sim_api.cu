@@ -542,12 +542,11 @@ int plan_persistent(sim_s* h) {
   return SIM_OK;
 }
 
-// The derivative kernel covers env types with ground contacts only and a bounded impulse cache.
+// The derivative kernel covers env types with a bounded impulse cache.
 int tangent_supported(const sim_s* h) {
   for (const TypePlan& tp : h->types)
-    if (tp.tab.n_pairs > 0 || tp.tab.cache_len > 384) {
-      g_last_error = "step derivative: env types with capsule-box pairs or more than 384 impulse-cache entries "
-                     "are not supported";
+    if (tp.tab.cache_len > 448) {
+      g_last_error = "step derivative: env types with more than 448 impulse-cache entries are not supported";
       return SIM_ERR_CAPACITY;
     }
   return SIM_OK;

@@ -117,9 +117,9 @@ template <int K> __device__ __forceinline__ void dmm(const Dn<K>* A, const Dn<K>
 }
 
 // ---- per-lane work space (local memory) --------------------------------------------------------
-constexpr int kTanMaxCon = 64;                       // kept ground contacts per env
+constexpr int kTanMaxCon = 64;                       // kept contacts per env (ground and pairs)
 constexpr int kTanMaxRows = 2 * (kMaxGen + kMaxTendons) + 3 * kTanMaxCon;
-constexpr int kTanMaxCache = 384;                    // impulse-cache entries per env
+constexpr int kTanMaxCache = 448;                    // impulse-cache entries per env
 
 template <int K> struct TanWork {
   Dn<K> R[kMaxLinks][9];     // link -> world rotation
@@ -133,6 +133,8 @@ template <int K> struct TanWork {
   Dn<K> cx[kTanMaxCon][3], cd[kTanMaxCon];
   int clink[kTanMaxCon], ccand[kTanMaxCon];
   float cmu[kTanMaxCon];
+  int clb[kTanMaxCon];          // body b of a pair contact (its link), -1 for the ground
+  Dn<K> cn[kTanMaxCon][3];      // pair contact normal (world, from b to a); the ground's is +z
   Dn<K> lam[kTanMaxRows];
 };
 
@@ -181,41 +183,6 @@ template <int K> __device__ __forceinline__ void dquat_rotvec(const Dn<K>* q, Dn
     f = datan2<K>(sn, w) * 2.f / sn;
   }
   r[0] = x * f; r[1] = y * f; r[2] = z * f;
-}
-
-// Row r's J^T solved through L: y = L^-1 J_r^T (n entries). Row kinds as in the forward kernel:
-// limit rows (unit +-1 on one DOF), contact normal / friction rows along e_z, e_x, e_y.
-template <int K> __device__ void row_response(const EnvTypeTable* T, const TanWork<K>& w, int n, int kind, int gdof,
-                                              float sgn, int c, int dir, Dn<K>* y) {
-  const bool jrow = kind == kRowLimit || kind == kRowTendon;  // rows on joint coordinates
-  const unsigned anc = jrow ? 0u : T->anc[w.clink[c]];
-  Dn<K> fr[6];
-  if (!jrow) {
-    // k = e_z (normal), e_x, e_y (friction); f = [x x k; k]
-    const Dn<K>& x0 = w.cx[c][0];
-    const Dn<K>& x1 = w.cx[c][1];
-    const Dn<K>& x2 = w.cx[c][2];
-    const Dn<K> zero(0.f);
-    if (dir == 0) { fr[0] = x1; fr[1] = -x0; fr[2] = zero; fr[3] = zero; fr[4] = zero; fr[5] = Dn<K>(1.f); }
-    else if (dir == 1) { fr[0] = zero; fr[1] = x2; fr[2] = -x1; fr[3] = Dn<K>(1.f); fr[4] = zero; fr[5] = zero; }
-    else { fr[0] = -x2; fr[1] = zero; fr[2] = x0; fr[3] = zero; fr[4] = Dn<K>(1.f); fr[5] = zero; }
-  }
-  for (int i = 0; i < n; ++i) {
-    Dn<K> ji(0.f);
-    if (kind == kRowLimit) {
-      if (i == gdof) ji = Dn<K>(sgn);
-    } else if (kind == kRowTendon) {  // gdof holds the tendon: J = +-c over its joints
-      float jt = 0.f;
-      for (int k = 0; k < T->ten_n[gdof]; ++k)
-        if (T->gdof[T->ten_link[gdof][k]] == i) jt += sgn * T->ten_coef[gdof][k];
-      ji = Dn<K>(jt);
-    } else if ((anc >> i) & 1u) {
-#pragma unroll
-      for (int k = 0; k < 6; ++k) ji = ji + w.S[i][k] * fr[k];
-    }
-    for (int k = 0; k < i; ++k) ji = ji - w.L[tri(i, k)] * y[k];
-    y[i] = ji / w.L[tri(i, i)];
-  }
 }
 
 // Per-env state of the tangent step (per actor: root p, quat, v, w; per joint DOF: q, qd; the env's
@@ -430,6 +397,193 @@ template <int K> __device__ void tangent_dynamics(const StepArgs& A, const EnvTy
   }
 }
 
+// ---- capsule-box geometry in dual arithmetic (box frame): the forward step's definitions, every
+// branch (inside / outside, breakpoint order, clamps, the face and the friction anchor) taken on the
+// value ----
+template <int K> __device__ __forceinline__ const Dn<K>& dcomp(const DV3<K>& v, int k) {
+  return k == 0 ? v.x : (k == 1 ? v.y : v.z);
+}
+template <int K> __device__ __forceinline__ Dn<K> dabs(const Dn<K>& a) { return a.v < 0.f ? -a : a; }
+template <int K> __device__ Dn<K> dbox_dist2(const DV3<K>& p, const float* e) {
+  Dn<K> f(0.f);
+  for (int k = 0; k < 3; ++k) {
+    const Dn<K> o = dabs(dcomp(p, k)) - Dn<K>(e[k]);
+    if (o.v > 0.f) f = f + o * o;
+  }
+  return f;
+}
+// minimiser over [0, 1] of the squared distance from p0 + t dv to the box (pieces between the
+// breakpoints |p_k(t)| = e_k, each piece's stationary point clamped into it; ties to the smaller t)
+template <int K> __device__ Dn<K> dsegment_box_closest_t(const DV3<K>& p0, const DV3<K>& dv, const float* e) {
+  Dn<K> ts[8];
+  int nt = 0;
+  ts[nt++] = Dn<K>(0.f);
+  ts[nt++] = Dn<K>(1.f);
+  for (int k = 0; k < 3; ++k) {
+    const Dn<K>& dk = dcomp(dv, k);
+    if (dk.v == 0.f) continue;
+    for (int sg = -1; sg <= 1; sg += 2) {
+      const Dn<K> t = (Dn<K>((float)sg * e[k]) - dcomp(p0, k)) / dk;
+      if (t.v > 0.f && t.v < 1.f) ts[nt++] = t;
+    }
+  }
+  for (int i = 1; i < nt; ++i) {  // insertion sort on the values
+    const Dn<K> x = ts[i];
+    int j = i - 1;
+    while (j >= 0 && x.v < ts[j].v) { ts[j + 1] = ts[j]; --j; }
+    ts[j + 1] = x;
+  }
+  Dn<K> best_t(0.f);
+  float best_f = dbox_dist2<K>(p0, e).v;
+  for (int i = 0; i + 1 < nt; ++i) {
+    const Dn<K> ta = ts[i], tb = ts[i + 1];
+    const DV3<K> pm = p0 + dv * ((ta + tb) * 0.5f);
+    Dn<K> num(0.f), den(0.f);
+    for (int k = 0; k < 3; ++k) {
+      const Dn<K>& pk = dcomp(pm, k);
+      if (!(e[k] < fabsf(pk.v))) continue;
+      const float sg = (pk.v > 0.f) ? 1.f : -1.f;
+      const Dn<K>& dk = dcomp(dv, k);
+      num = num + dk * (Dn<K>(sg * e[k]) - dcomp(p0, k));
+      den = den + dk * dk;
+    }
+    Dn<K> t = ta;
+    if (den.v > 0.f) {
+      t = num / den;
+      if (t.v < ta.v) t = ta;
+      if (t.v > tb.v) t = tb;
+    }
+    const float f = dbox_dist2<K>(p0 + dv * t, e).v;
+    if (f < best_f) { best_f = f; best_t = t; }
+  }
+  if (dbox_dist2<K>(p0 + dv, e).v < best_f) best_t = Dn<K>(1.f);
+  return best_t;
+}
+// a sphere of radius r at p against the box: normal (box -> sphere), separation, and the point
+// halfway between the two surfaces
+template <int K> __device__ void dsphere_box(const DV3<K>& p, float r, const float* e, DV3<K>& n, Dn<K>& d,
+                                             DV3<K>& x) {
+  const bool inside = fabsf(p.x.v) <= e[0] && fabsf(p.y.v) <= e[1] && fabsf(p.z.v) <= e[2];
+  if (!inside) {
+    Dn<K> q[3];
+    for (int k = 0; k < 3; ++k) {
+      const Dn<K>& pk = dcomp(p, k);
+      q[k] = pk.v > e[k] ? Dn<K>(e[k]) : (pk.v < -e[k] ? Dn<K>(-e[k]) : pk);
+    }
+    const DV3<K> dl = p - dv3<K>(q[0], q[1], q[2]);
+    const Dn<K> dist = dsqrt(ddot(dl, dl));
+    n = dv3<K>(dl.x / dist, dl.y / dist, dl.z / dist);
+    d = dist - Dn<K>(r);
+  } else {
+    int kb = 0;
+    float best = e[0] - fabsf(p.x.v);
+    if (e[1] - fabsf(p.y.v) < best) { best = e[1] - fabsf(p.y.v); kb = 1; }
+    if (e[2] - fabsf(p.z.v) < best) { best = e[2] - fabsf(p.z.v); kb = 2; }
+    const float sg = (dcomp(p, kb).v < 0.f) ? -1.f : 1.f;
+    n = dv3<K>(Dn<K>(kb == 0 ? sg : 0.f), Dn<K>(kb == 1 ? sg : 0.f), Dn<K>(kb == 2 ? sg : 0.f));
+    d = -(Dn<K>(e[kb]) - dabs(dcomp(p, kb))) - Dn<K>(r);
+  }
+  x = p - n * (Dn<K>(r) + d * 0.5f);
+}
+// the part of the segment over the box face selected by the closest point t*
+template <int K> __device__ bool dface_clip(const DV3<K>& p0, const DV3<K>& dv, const float* e, float r,
+                                           const Dn<K>& tstar, Dn<K>& ta, Dn<K>& tb) {
+  DV3<K> n, x;
+  Dn<K> d;
+  dsphere_box<K>(p0 + dv * tstar, r, e, n, d, x);
+  int kn = 0;
+  if (fabsf(n.x.v) < fabsf(n.y.v)) kn = 1;
+  if (fabsf(dcomp(n, kn).v) < fabsf(n.z.v)) kn = 2;
+  ta = Dn<K>(0.f);
+  tb = Dn<K>(1.f);
+  for (int j = 0; j < 3; ++j) {
+    if (j == kn) continue;
+    const Dn<K>& dj = dcomp(dv, j);
+    const Dn<K>& pj = dcomp(p0, j);
+    if (dj.v == 0.f) {
+      if (e[j] < fabsf(pj.v)) return false;
+      continue;
+    }
+    Dn<K> t0 = (Dn<K>(-e[j]) - pj) / dj, t1 = (Dn<K>(e[j]) - pj) / dj;
+    if (t1.v < t0.v) { const Dn<K> sw = t0; t0 = t1; t1 = sw; }
+    if (t0.v > ta.v) ta = t0;
+    if (t1.v < tb.v) tb = t1;
+  }
+  return !(tb.v < ta.v);
+}
+// friction directions of a contact normal (anchor e_x, e_y or e_z chosen on the value)
+template <int K> __device__ void dtangent_basis(const DV3<K>& n, DV3<K>& t1, DV3<K>& t2) {
+  const float ax = fabsf(n.x.v) < 0.57735f ? 1.f : 0.f;
+  const float ay = ax == 0.f && fabsf(n.y.v) < 0.57735f ? 1.f : 0.f;
+  const float az = (ax == 0.f && ay == 0.f) ? 1.f : 0.f;
+  const DV3<K> an = dv3<K>(Dn<K>(ax), Dn<K>(ay), Dn<K>(az));
+  const DV3<K> t = an - n * ddot(an, n);
+  const Dn<K> tn = dsqrt(ddot(t, t));
+  t1 = dv3<K>(t.x / tn, t.y / tn, t.z / tn);
+  t2 = dcross(n, t1);
+}
+
+// Row r's J^T solved through L: y = L^-1 J_r^T (n entries). Row kinds as in the forward kernel:
+// limit rows (unit +-1 on one DOF), tendon rows (+-c on the tendon's DOFs), ground contact normal /
+// friction rows along e_z, e_x, e_y, and pair contact rows on two bodies along the pair normal and
+// its friction directions.
+template <int K> __device__ void row_response(const EnvTypeTable* T, const TanState<K>& s, const TanWork<K>& w, int n,
+                                              int kind, int gdof, float sgn, int c, int dir, Dn<K>* y) {
+  const bool jrow = kind == kRowLimit || kind == kRowTendon;  // rows on joint coordinates
+  const bool pair = !jrow && w.clb[c] >= 0;                   // a contact between two bodies
+  const unsigned anc = jrow ? 0u : T->anc[w.clink[c]];
+  const unsigned ancb = pair ? T->anc[w.clb[c]] : 0u;
+  Dn<K> fr[6], fb[6];
+  if (pair) {
+    // direction k: the normal (from b to a) or a friction direction of it; body a sees f = [x x k; k]
+    // about its actor origin, body b -[x_b x k; k] with x_b the point about b's actor origin
+    const DV3<K> nrm = dv3<K>(w.cn[c][0], w.cn[c][1], w.cn[c][2]);
+    DV3<K> k = nrm;
+    if (dir != 0) {
+      DV3<K> t1, t2;
+      dtangent_basis<K>(nrm, t1, t2);
+      k = (dir == 1) ? t1 : t2;
+    }
+    const DV3<K> x = dv3<K>(w.cx[c][0], w.cx[c][1], w.cx[c][2]);
+    const int aa = T->actor[w.clink[c]], ab = T->actor[w.clb[c]];
+    const DV3<K> dob = dv3<K>(s.rp[ab][0] - s.rp[aa][0], s.rp[ab][1] - s.rp[aa][1], s.rp[ab][2] - s.rp[aa][2]);
+    const DV3<K> xk = dcross(x, k), xbk = dcross(x - dob, k);
+    fr[0] = xk.x; fr[1] = xk.y; fr[2] = xk.z; fr[3] = k.x; fr[4] = k.y; fr[5] = k.z;
+    fb[0] = -xbk.x; fb[1] = -xbk.y; fb[2] = -xbk.z; fb[3] = -k.x; fb[4] = -k.y; fb[5] = -k.z;
+  } else if (!jrow) {
+    // ground: k = e_z (normal), e_x, e_y (friction); f = [x x k; k]
+    const Dn<K>& x0 = w.cx[c][0];
+    const Dn<K>& x1 = w.cx[c][1];
+    const Dn<K>& x2 = w.cx[c][2];
+    const Dn<K> zero(0.f);
+    if (dir == 0) { fr[0] = x1; fr[1] = -x0; fr[2] = zero; fr[3] = zero; fr[4] = zero; fr[5] = Dn<K>(1.f); }
+    else if (dir == 1) { fr[0] = zero; fr[1] = x2; fr[2] = -x1; fr[3] = Dn<K>(1.f); fr[4] = zero; fr[5] = zero; }
+    else { fr[0] = -x2; fr[1] = zero; fr[2] = x0; fr[3] = zero; fr[4] = Dn<K>(1.f); fr[5] = zero; }
+  }
+  for (int i = 0; i < n; ++i) {
+    Dn<K> ji(0.f);
+    if (kind == kRowLimit) {
+      if (i == gdof) ji = Dn<K>(sgn);
+    } else if (kind == kRowTendon) {  // gdof holds the tendon: J = +-c over its joints
+      float jt = 0.f;
+      for (int k = 0; k < T->ten_n[gdof]; ++k)
+        if (T->gdof[T->ten_link[gdof][k]] == i) jt += sgn * T->ten_coef[gdof][k];
+      ji = Dn<K>(jt);
+    } else {
+      if ((anc >> i) & 1u) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) ji = ji + w.S[i][k] * fr[k];
+      }
+      if ((ancb >> i) & 1u) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) ji = ji + w.S[i][k] * fb[k];
+      }
+    }
+    for (int k = 0; k < i; ++k) ji = ji - w.L[tri(i, k)] * y[k];
+    y[i] = ji / w.L[tri(i, i)];
+  }
+}
+
 // Ground contacts of the current poses (w.R, w.P) in shape / slot order into w.cx, w.cd, w.clink,
 // w.ccand, w.cmu; returns their count, or -1 past kTanMaxCon.
 template <int K> __device__ int tangent_contacts(const StepArgs& A, const EnvTypeTable* T, const TanState<K>& s,
@@ -469,8 +623,66 @@ template <int K> __device__ int tangent_contacts(const StepArgs& A, const EnvTyp
         w.clink[nc] = l;
         w.ccand[nc] = T->cand_off[sh] + k;
         w.cmu[nc] = T->shape_mu[sh];
+        w.clb[nc] = -1;
         ++nc;
       }
+    }
+  }
+  // capsule-box pairs, appended in pair / slot order (everything relative to the box actor's
+  // origin; the stored point relative to body a's actor origin)
+  for (int p = 0; p < T->n_pairs; ++p) {
+    const int sa = T->pair_a[p], sb = T->pair_b[p];
+    const bool a_cap = T->shape_type[sa] == kCapsule;
+    const int sc = a_cap ? sa : sb, sx = a_cap ? sb : sa;
+    const int lc = T->shape_link[sc], lx = T->shape_link[sx];
+    const int ac = T->actor[lc], axr = T->actor[lx];
+    const DV3<K> Oc = dv3<K>(s.rp[ac][0], s.rp[ac][1], s.rp[ac][2]);
+    const DV3<K> Ox = dv3<K>(s.rp[axr][0], s.rp[axr][1], s.rp[axr][2]);
+    Dn<K> Rsh[9], Rcs[9], Rb[9];
+    for (int k = 0; k < 9; ++k) Rsh[k] = Dn<K>(T->shape_rot[k][sc]);
+    dmm<K>(w.R[lc], Rsh, Rcs);
+    for (int k = 0; k < 9; ++k) Rsh[k] = Dn<K>(T->shape_rot[k][sx]);
+    dmm<K>(w.R[lx], Rsh, Rb);
+    const DV3<K> cc = dv3<K>(w.P[lc][0], w.P[lc][1], w.P[lc][2]) +
+                      dmv<K>(w.R[lc], dv3<K>(Dn<K>(T->shape_pos[0][sc]), Dn<K>(T->shape_pos[1][sc]),
+                                             Dn<K>(T->shape_pos[2][sc]))) + (Oc - Ox);
+    const DV3<K> cb = dv3<K>(w.P[lx][0], w.P[lx][1], w.P[lx][2]) +
+                      dmv<K>(w.R[lx], dv3<K>(Dn<K>(T->shape_pos[0][sx]), Dn<K>(T->shape_pos[1][sx]),
+                                             Dn<K>(T->shape_pos[2][sx])));
+    const float r = T->shape_size[0][sc], hl = T->shape_size[1][sc];
+    const float e[3] = {T->shape_size[0][sx], T->shape_size[1][sx], T->shape_size[2][sx]};
+    const DV3<K> ax = dv3<K>(Rcs[0], Rcs[3], Rcs[6]);
+    const DV3<K> b0 = dv3<K>(Rb[0], Rb[3], Rb[6]), b1 = dv3<K>(Rb[1], Rb[4], Rb[7]), b2 = dv3<K>(Rb[2], Rb[5], Rb[8]);
+    const DV3<K> w0 = cc - ax * Dn<K>(hl) - cb, w1 = cc + ax * Dn<K>(hl) - cb;
+    const DV3<K> p0 = dv3<K>(ddot(b0, w0), ddot(b1, w0), ddot(b2, w0));
+    const DV3<K> dv = dv3<K>(ddot(b0, w1), ddot(b1, w1), ddot(b2, w1)) - p0;
+    const Dn<K> tstar = dsegment_box_closest_t<K>(p0, dv, e);
+    Dn<K> ta, tb;
+    const bool clip = dface_clip<K>(p0, dv, e, r, tstar, ta, tb);
+    const DV3<K> Oa = a_cap ? Oc : Ox;
+    for (int slot = 0; slot < kPairSlots; ++slot) {
+      const Dn<K> t = slot == 0 ? Dn<K>(0.f) : (slot == 1 ? Dn<K>(1.f) : (slot == 2 ? ta : (slot == 3 ? tb : tstar)));
+      if (slot >= 2) {
+        if (slot < 4 && !clip) continue;
+        if (slot == 3 && !(ta.v < tb.v)) continue;
+        if (!(t.v > 0.f && t.v < 1.f)) continue;
+      }
+      DV3<K> pn, px;
+      Dn<K> pd;
+      dsphere_box<K>(p0 + dv * t, r, e, pn, pd, px);
+      if (!(pd.v < coff)) continue;
+      if (nc >= kTanMaxCon) return -1;
+      DV3<K> nw = b0 * pn.x + b1 * pn.y + b2 * pn.z;  // box -> capsule
+      if (!a_cap) nw = dv3<K>(-nw.x, -nw.y, -nw.z);
+      const DV3<K> xw = cb + b0 * px.x + b1 * px.y + b2 * px.z + (Ox - Oa);
+      w.cx[nc][0] = xw.x; w.cx[nc][1] = xw.y; w.cx[nc][2] = xw.z;
+      w.cn[nc][0] = nw.x; w.cn[nc][1] = nw.y; w.cn[nc][2] = nw.z;
+      w.cd[nc] = pd;
+      w.clink[nc] = a_cap ? lc : lx;
+      w.clb[nc] = a_cap ? lx : lc;
+      w.ccand[nc] = T->n_ground_cand + kPairSlots * p + slot;
+      w.cmu[nc] = fmaxf(T->shape_fr[sa], T->shape_fr[sb]);
+      ++nc;
     }
   }
   return nc;
@@ -625,7 +837,7 @@ template <int K> __device__ bool tangent_substep(const StepArgs& A, const EnvTyp
     int kind, g, c, dir, slot;
     float sgn;
     describe(r, kind, g, sgn, c, dir, slot);
-    row_response<K>(T, w, n, kind, g, sgn, c, dir, y);
+    row_response<K>(T, s, w, n, kind, g, sgn, c, dir, y);
     Dn<K> a2(0.f);
     for (int i = 0; i < n; ++i) a2 = a2 + y[i] * y[i];
     w.lam[r] = (a2.v > 1e-12f) ? s.cache[slot] : Dn<K>(0.f);
@@ -639,7 +851,7 @@ template <int K> __device__ bool tangent_substep(const StepArgs& A, const EnvTyp
       int kind, g, c, dir, slot;
       float sgn;
       describe(r, kind, g, sgn, c, dir, slot);
-      row_response<K>(T, w, n, kind, g, sgn, c, dir, y);
+      row_response<K>(T, s, w, n, kind, g, sgn, c, dir, y);
       Dn<K> a2(0.f), yz(0.f), ydz(0.f);
       for (int i = 0; i < n; ++i) { a2 = a2 + y[i] * y[i]; yz = yz + y[i] * w.z[i]; ydz = ydz + y[i] * w.dz[i]; }
       if (!(a2.v > 1e-12f)) continue;

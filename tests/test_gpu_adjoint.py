@@ -105,7 +105,8 @@ def _driven_ant(n):
 WORKLOADS = {"ant": W.ant_workload, "humanoid": W.humanoid_workload, "cartpole": W.cartpole_workload,
              "ball_ant": lambda n: W.homogeneous("ball_ant", W.ant(ball_hips=True), n), "driven_ant": _driven_ant,
              "pushed_ant": W.ant_workload,
-             "tendon_ant": lambda n: W.homogeneous("tendon_ant", W.ant(tendons=True), n)}
+             "tendon_ant": lambda n: W.homogeneous("tendon_ant", W.ant(tendons=True), n),
+             "hand": W.hand_workload, "hand_tendon": W.hand_tendon_workload}
 
 
 def make_sim(name, w, seed=9):
@@ -132,7 +133,8 @@ def make_sim(name, w, seed=9):
 
 
 @pytest.mark.parametrize("name,n", [("ant", 67), ("humanoid", 37), ("cartpole", 67), ("ball_ant", 40),
-                                    ("driven_ant", 40), ("pushed_ant", 40), ("tendon_ant", 40)])
+                                    ("driven_ant", 40), ("pushed_ant", 40), ("tendon_ant", 40), ("hand", 24),
+                                    ("hand_tendon", 16)])
 def test_jvp_value_and_tangent_match_oracle(name, n):
     """(driven_ant / pushed_ant: drive targets / body forces from the handle's views, constants of
     the derivative)"""
@@ -167,7 +169,7 @@ def test_jvp_value_and_tangent_match_oracle(name, n):
 
 
 @pytest.mark.parametrize("name,n", [("ant", 40), ("humanoid", 20), ("ball_ant", 20), ("driven_ant", 20),
-                                    ("pushed_ant", 20), ("tendon_ant", 20)])
+                                    ("pushed_ant", 20), ("tendon_ant", 20), ("hand", 12)])
 def test_vjp_is_the_transpose_of_the_jvp(name, n):
     """<g, J u> (tangent mode) equals <J^T g, u> (adjoint mode) per env, for random g and u."""
     import torch
@@ -271,11 +273,23 @@ def test_rollout_gradient_matches_oracle_and_checkpointing_is_exact():
     assert len(bad) <= 1, bad
 
 
+def many_boxes(n_boxes=19):
+    """A free body carrying n_boxes box shapes (8 ground candidates each) and a hinged child: 19
+    boxes give an impulse cache of 3 * 152 + 2 = 458 entries, past the derivative's 448."""
+    b = W._Builder("boxes")
+    root = b.link(-1, W.JOINT_FREE, mass=1.0, inertia=(0.1, 0.1, 0.1, 0, 0, 0))
+    b.link(root, W.JOINT_REVOLUTE, axis=(0, 0, 1), ppos=(0.0, 0.2, 0.0), mass=0.1, inertia=(0.01, 0.01, 0.01, 0, 0, 0))
+    for i in range(n_boxes):
+        b.shape(root, W.SHAPE_BOX, (0.05, 0.05, 0.05), pos=(0.1 * i, 0.0, 0.0))
+    return b.build(root_pos=(0.0, 0.0, 1.0))
+
+
 def test_unsupported_types_are_refused():
     import torch
     from paper_2108_10470_gb300 import sim
-    w = W.hand_workload(4)
+    w = W.homogeneous("boxes", many_boxes(), 4)
     s = sim.Sim(w)
+    assert s.cache_len > 448
     z = lambda v: torch.zeros_like(v)
     bufs = {"root_state": s.root_state, "dof_state": s.dof_state, "dof_actuation": s.dof_actuation,
             "impulse_cache": s.impulse_cache, "grad_root_state_in": z(s.root_state), "grad_dof_state_in": z(s.dof_state),
