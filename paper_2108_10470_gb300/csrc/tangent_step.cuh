@@ -523,6 +523,27 @@ template <int K> __device__ void dtangent_basis(const DV3<K>& n, DV3<K>& t1, DV3
   t2 = dcross(n, t1);
 }
 
+// Spatial forces of a pair contact row (direction k: the normal from b to a, or one of its friction
+// directions): body a sees f = [x x k; k] about its actor origin, body b -[x_b x k; k] with x_b the
+// point about b's actor origin. Out of line: it keeps the pair geometry out of the solver loop.
+template <int K> __device__ __noinline__ void pair_row_forces(const EnvTypeTable* T, const TanState<K>& s,
+                                                              const TanWork<K>& w, int c, int dir, Dn<K>* fr,
+                                                              Dn<K>* fb) {
+  const DV3<K> nrm = dv3<K>(w.cn[c][0], w.cn[c][1], w.cn[c][2]);
+  DV3<K> k = nrm;
+  if (dir != 0) {
+    DV3<K> t1, t2;
+    dtangent_basis<K>(nrm, t1, t2);
+    k = (dir == 1) ? t1 : t2;
+  }
+  const DV3<K> x = dv3<K>(w.cx[c][0], w.cx[c][1], w.cx[c][2]);
+  const int aa = T->actor[w.clink[c]], ab = T->actor[w.clb[c]];
+  const DV3<K> dob = dv3<K>(s.rp[ab][0] - s.rp[aa][0], s.rp[ab][1] - s.rp[aa][1], s.rp[ab][2] - s.rp[aa][2]);
+  const DV3<K> xk = dcross(x, k), xbk = dcross(x - dob, k);
+  fr[0] = xk.x; fr[1] = xk.y; fr[2] = xk.z; fr[3] = k.x; fr[4] = k.y; fr[5] = k.z;
+  fb[0] = -xbk.x; fb[1] = -xbk.y; fb[2] = -xbk.z; fb[3] = -k.x; fb[4] = -k.y; fb[5] = -k.z;
+}
+
 // Row r's J^T solved through L: y = L^-1 J_r^T (n entries). Row kinds as in the forward kernel:
 // limit rows (unit +-1 on one DOF), tendon rows (+-c on the tendon's DOFs), ground contact normal /
 // friction rows along e_z, e_x, e_y, and pair contact rows on two bodies along the pair normal and
@@ -535,21 +556,7 @@ template <int K> __device__ void row_response(const EnvTypeTable* T, const TanSt
   const unsigned ancb = pair ? T->anc[w.clb[c]] : 0u;
   Dn<K> fr[6], fb[6];
   if (pair) {
-    // direction k: the normal (from b to a) or a friction direction of it; body a sees f = [x x k; k]
-    // about its actor origin, body b -[x_b x k; k] with x_b the point about b's actor origin
-    const DV3<K> nrm = dv3<K>(w.cn[c][0], w.cn[c][1], w.cn[c][2]);
-    DV3<K> k = nrm;
-    if (dir != 0) {
-      DV3<K> t1, t2;
-      dtangent_basis<K>(nrm, t1, t2);
-      k = (dir == 1) ? t1 : t2;
-    }
-    const DV3<K> x = dv3<K>(w.cx[c][0], w.cx[c][1], w.cx[c][2]);
-    const int aa = T->actor[w.clink[c]], ab = T->actor[w.clb[c]];
-    const DV3<K> dob = dv3<K>(s.rp[ab][0] - s.rp[aa][0], s.rp[ab][1] - s.rp[aa][1], s.rp[ab][2] - s.rp[aa][2]);
-    const DV3<K> xk = dcross(x, k), xbk = dcross(x - dob, k);
-    fr[0] = xk.x; fr[1] = xk.y; fr[2] = xk.z; fr[3] = k.x; fr[4] = k.y; fr[5] = k.z;
-    fb[0] = -xbk.x; fb[1] = -xbk.y; fb[2] = -xbk.z; fb[3] = -k.x; fb[4] = -k.y; fb[5] = -k.z;
+    pair_row_forces<K>(T, s, w, c, dir, fr, fb);
   } else if (!jrow) {
     // ground: k = e_z (normal), e_x, e_y (friction); f = [x x k; k]
     const Dn<K>& x0 = w.cx[c][0];
@@ -584,52 +591,12 @@ template <int K> __device__ void row_response(const EnvTypeTable* T, const TanSt
   }
 }
 
-// Ground contacts of the current poses (w.R, w.P) in shape / slot order into w.cx, w.cd, w.clink,
-// w.ccand, w.cmu; returns their count, or -1 past kTanMaxCon.
-template <int K> __device__ int tangent_contacts(const StepArgs& A, const EnvTypeTable* T, const TanState<K>& s,
-                                                 TanWork<K>& w) {
+// Capsule-box pair contacts appended after the nc ground contacts in pair / slot order (everything
+// relative to the box actor's origin; the stored point relative to body a's actor origin); returns
+// the new count, or -1 past kTanMaxCon. Out of line: it runs once per substep.
+template <int K> __device__ __noinline__ int tangent_pair_contacts(const StepArgs& A, const EnvTypeTable* T,
+                                                                   const TanState<K>& s, TanWork<K>& w, int nc) {
   const float coff = A.contact_offset;
-  int nc = 0;
-  for (int sh = 0; sh < T->n_shapes; ++sh) {
-    const int l = T->shape_link[sh], st = T->shape_type[sh], a = T->actor[l];
-    Dn<K> Rsh[9], Rs[9];
-    for (int k = 0; k < 9; ++k) Rsh[k] = Dn<K>(T->shape_rot[k][sh]);
-    dmm<K>(w.R[l], Rsh, Rs);
-    const DV3<K> cs = dv3<K>(w.P[l][0], w.P[l][1], w.P[l][2]) +
-                      dmv<K>(w.R[l], dv3<K>(Dn<K>(T->shape_pos[0][sh]), Dn<K>(T->shape_pos[1][sh]), Dn<K>(T->shape_pos[2][sh])));
-    const Dn<K> oz = s.rp[a][2];
-    const float s0 = T->shape_size[0][sh], s1 = T->shape_size[1][sh], s2 = T->shape_size[2][sh];
-    const int nk = (st == kSphere) ? 1 : (st == kCapsule ? 2 : 8);
-    for (int k = 0; k < nk; ++k) {
-      DV3<K> x;
-      Dn<K> zc;
-      if (st == kSphere) {
-        x = dv3<K>(cs.x, cs.y, cs.z - Dn<K>(s0));
-        zc = (oz + cs.z) - Dn<K>(s0);
-      } else if (st == kCapsule) {
-        const DV3<K> ax = dv3<K>(Rs[0], Rs[3], Rs[6]);
-        const DV3<K> e = (k == 0) ? cs - ax * Dn<K>(s1) : cs + ax * Dn<K>(s1);
-        x = dv3<K>(e.x, e.y, e.z - Dn<K>(s0));
-        zc = (oz + e.z) - Dn<K>(s0);
-      } else {
-        const DV3<K> loc = dv3<K>(Dn<K>((k & 4) ? s0 : -s0), Dn<K>((k & 2) ? s1 : -s1), Dn<K>((k & 1) ? s2 : -s2));
-        x = cs + dmv<K>(Rs, loc);
-        zc = oz + x.z;
-      }
-      if (zc.v < coff) {
-        if (nc >= kTanMaxCon) return -1;
-        w.cx[nc][0] = x.x; w.cx[nc][1] = x.y; w.cx[nc][2] = x.z;
-        w.cd[nc] = zc;
-        w.clink[nc] = l;
-        w.ccand[nc] = T->cand_off[sh] + k;
-        w.cmu[nc] = T->shape_mu[sh];
-        w.clb[nc] = -1;
-        ++nc;
-      }
-    }
-  }
-  // capsule-box pairs, appended in pair / slot order (everything relative to the box actor's
-  // origin; the stored point relative to body a's actor origin)
   for (int p = 0; p < T->n_pairs; ++p) {
     const int sa = T->pair_a[p], sb = T->pair_b[p];
     const bool a_cap = T->shape_type[sa] == kCapsule;
@@ -686,6 +653,54 @@ template <int K> __device__ int tangent_contacts(const StepArgs& A, const EnvTyp
     }
   }
   return nc;
+}
+
+// Contacts of the current poses (w.R, w.P): ground contacts in shape / slot order, then capsule-box
+// pair contacts, into w.cx, w.cd, w.clink, w.ccand, w.cmu, w.clb (and w.cn for pairs); returns their
+// count, or -1 past kTanMaxCon.
+template <int K> __device__ int tangent_contacts(const StepArgs& A, const EnvTypeTable* T, const TanState<K>& s,
+                                                 TanWork<K>& w) {
+  const float coff = A.contact_offset;
+  int nc = 0;
+  for (int sh = 0; sh < T->n_shapes; ++sh) {
+    const int l = T->shape_link[sh], st = T->shape_type[sh], a = T->actor[l];
+    Dn<K> Rsh[9], Rs[9];
+    for (int k = 0; k < 9; ++k) Rsh[k] = Dn<K>(T->shape_rot[k][sh]);
+    dmm<K>(w.R[l], Rsh, Rs);
+    const DV3<K> cs = dv3<K>(w.P[l][0], w.P[l][1], w.P[l][2]) +
+                      dmv<K>(w.R[l], dv3<K>(Dn<K>(T->shape_pos[0][sh]), Dn<K>(T->shape_pos[1][sh]), Dn<K>(T->shape_pos[2][sh])));
+    const Dn<K> oz = s.rp[a][2];
+    const float s0 = T->shape_size[0][sh], s1 = T->shape_size[1][sh], s2 = T->shape_size[2][sh];
+    const int nk = (st == kSphere) ? 1 : (st == kCapsule ? 2 : 8);
+    for (int k = 0; k < nk; ++k) {
+      DV3<K> x;
+      Dn<K> zc;
+      if (st == kSphere) {
+        x = dv3<K>(cs.x, cs.y, cs.z - Dn<K>(s0));
+        zc = (oz + cs.z) - Dn<K>(s0);
+      } else if (st == kCapsule) {
+        const DV3<K> ax = dv3<K>(Rs[0], Rs[3], Rs[6]);
+        const DV3<K> e = (k == 0) ? cs - ax * Dn<K>(s1) : cs + ax * Dn<K>(s1);
+        x = dv3<K>(e.x, e.y, e.z - Dn<K>(s0));
+        zc = (oz + e.z) - Dn<K>(s0);
+      } else {
+        const DV3<K> loc = dv3<K>(Dn<K>((k & 4) ? s0 : -s0), Dn<K>((k & 2) ? s1 : -s1), Dn<K>((k & 1) ? s2 : -s2));
+        x = cs + dmv<K>(Rs, loc);
+        zc = oz + x.z;
+      }
+      if (zc.v < coff) {
+        if (nc >= kTanMaxCon) return -1;
+        w.cx[nc][0] = x.x; w.cx[nc][1] = x.y; w.cx[nc][2] = x.z;
+        w.cd[nc] = zc;
+        w.clink[nc] = l;
+        w.ccand[nc] = T->cand_off[sh] + k;
+        w.cmu[nc] = T->shape_mu[sh];
+        w.clb[nc] = -1;
+        ++nc;
+      }
+    }
+  }
+  return T->n_pairs > 0 ? tangent_pair_contacts<K>(A, T, s, w, nc) : nc;
 }
 
 // Link poses only (w.R, w.P), as in tangent_dynamics.
