@@ -58,8 +58,9 @@ def test_values_equal_plain_step():
 @pytest.mark.parametrize("make", [lambda: W.ant_workload(6), lambda: W.humanoid_workload(4), lambda: W.cartpole_workload(4),
                                   lambda: W.hand_workload(3),
                                   lambda: W.homogeneous("ball_ant", W.ant(ball_hips=True), 6),
-                                  lambda: W.homogeneous("tendon_ant", W.ant(tendons=True), 6)],
-                         ids=["ant", "humanoid", "cartpole", "hand", "ball_ant", "tendon_ant"])
+                                  lambda: W.homogeneous("tendon_ant", W.ant(tendons=True), 6),
+                                  lambda: W.hand_tendon_workload(3)],
+                         ids=["ant", "humanoid", "cartpole", "hand", "ball_ant", "tendon_ant", "hand_tendon"])
 def test_directional_derivative_equals_central_differences(make):
     """JVP against (f(x + eps u) - f(x - eps u)) / 2 eps with eps = 1e-7, on envs whose constraint
     set is the same at both ends and whose one-sided differences agree (no clamp or target switch
