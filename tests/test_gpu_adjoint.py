@@ -220,8 +220,8 @@ def loss_grad_gpu(w, root, dof, acts, checkpoint):
 
 
 def loss_grad_oracle(w, root, dof, acts):
-    """d(mean final root v_x)/d(actions) and /d(initial DOF state) by forward mode: one dual rollout
-    per input direction, seeded in every env at once (envs are independent)."""
+    """d(mean final root v_x over all actors)/d(actions) and /d(initial DOF state) by forward mode:
+    one dual rollout per input direction, seeded in every env at once (envs are independent)."""
     steps = acts.shape[0]
     nj = w.n_dof // w.n_envs
     g_act = np.zeros((steps, w.n_dof))
@@ -238,7 +238,7 @@ def loss_grad_oracle(w, root, dof, acts):
             if seed_step == k:
                 da[seed_j::nj] = 1.0
             O.step_tangent(r, d, acts[k].astype(np.float64), tr, td, da, tc)
-        return tr[:, 7] / w.n_envs
+        return (tr[:, 7] / tr.shape[0]).reshape(w.n_envs, -1).sum(1)  # mean over actors, per env
 
     for k in range(steps):
         for j in range(nj):
@@ -249,15 +249,18 @@ def loss_grad_oracle(w, root, dof, acts):
     return g_dof, g_act
 
 
-def test_rollout_gradient_matches_oracle_and_checkpointing_is_exact():
-    """8 Ant envs, 12 steps, loss = mean final root x-velocity: gradients w.r.t. every action and
-    the initial DOF state through the autograd rollout (checkpoints of 4 steps) against the oracle's
-    forward-mode rollout; checkpoint lengths 1, 4 and 12 give bitwise equal gradients."""
-    w = W.ant_workload(8)
-    steps = 12
+@pytest.mark.parametrize("name,steps,max_bad", [("ant", 12, 1), ("hand", 6, 2)])
+def test_rollout_gradient_matches_oracle_and_checkpointing_is_exact(name, steps, max_bad):
+    """8 envs (Ant over 12 steps; the hand holding its cube over 6), loss = mean final root
+    x-velocity: gradients w.r.t. every action and the initial DOF state through the autograd rollout
+    (checkpoints of 4 steps) against the oracle's forward-mode rollout; checkpoint lengths 1, 4 and
+    the whole rollout give bitwise equal gradients. max_bad envs may deviate by more than 1e-2: the
+    hand's contact-rich rollouts include an env whose derivative evaluated in single precision by the
+    oracle itself lands 8e-2 from its FP64 value (a clamp within rounding of its threshold)."""
+    w = W.ant_workload(8) if name == "ant" else W.hand_workload(8)
     root, dof, acts = W.seeded_inputs(w, 11, steps)
     l4, gd4, ga4, _ = loss_grad_gpu(w, root, dof, acts, 4)
-    for ck in (1, 12):
+    for ck in (1, steps):
         l, gd, ga, _ = loss_grad_gpu(w, root, dof, acts, ck)
         assert l == l4 and np.array_equal(gd, gd4) and np.array_equal(ga, ga4)
     od, oa = loss_grad_oracle(w, root, dof, acts)
@@ -270,7 +273,7 @@ def test_rollout_gradient_matches_oracle_and_checkpointing_is_exact():
         print(f"env {e}: max |grad| {np.abs(ref).max():.3e}, relative deviation {rel:.2e}")
         if rel > 1e-2:
             bad.append(e)
-    assert len(bad) <= 1, bad
+    assert len(bad) <= max_bad, bad
 
 
 def many_boxes(n_boxes=19):
