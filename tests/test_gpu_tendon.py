@@ -1,5 +1,6 @@
 """Fixed tendons on the GPU against the FP64 oracle: spring-damper tendons, equality and limited
-tendons on two-joint models, and the hand with coupled middle / distal flexions holding a cube."""
+tendons on two-joint models, the Ant with three tendons, and the hand with coupled middle / distal
+flexions holding a cube."""
 import numpy as np
 import pytest
 
@@ -37,6 +38,14 @@ def test_two_joint_tendons_match_oracle(kind, steps, rtol, atol):
 @pytest.mark.parametrize("steps,rtol,atol", [(1, 1e-4, 1e-5), (16, 1e-3, 1e-3)])
 def test_coupled_hand_matches_oracle(steps, rtol, atol):
     check_rollout(W.hand_tendon_workload(37), steps, rtol, atol, min_same=0.9 if steps == 1 else 0.75)
+
+
+@pytest.mark.parametrize("steps,rtol,atol", [(1, 1e-4, 1e-5), (16, 1e-3, 1e-3)])
+def test_tendon_ant_matches_oracle(steps, rtol, atol):
+    """The Ant with a spring, a length-limited and an equality tendon (floating base, ground
+    contacts and joint limits with tendon rows in the same solve)."""
+    check_rollout(W.homogeneous("tendon_ant", W.ant(tendons=True), 67), steps, rtol, atol,
+                  min_same=0.9 if steps == 1 else 0.75)
 
 
 def test_equality_tendon_moves_joints_together_on_gpu():
