@@ -229,19 +229,28 @@ typedef struct {
  * whose contact and row blocks do not fit in shared memory keep them in a scratch array built
  * into the library (64 MiB, a file-scope device array: every device where the library's device
  * code is loaded holds it until the process exits) instead of the handle's own scratch. The
- * handle supplies only the model tables and its stream; its views are not touched.
+ * handle supplies only the model tables, its launch plan and its stream; its views are neither
+ * read nor written. Steps that would use them are refused with INVALID_ARG: handles created with
+ * SIM_FLAG_BODY_FORCES (reads the RIGID_BODY_FORCE view), SIM_FLAG_RIGID_BODY_STATE or
+ * SIM_FLAG_DOF_FORCE (write those views), and env types with joint drives (read the target views).
+ * Handles with SIM_FLAG_PERSISTENT or SIM_FLAG_GRAPH step here with one launch per env type on
+ * the handle's stream, without a graph.
  * Limit: each such env type needs its env count, rounded up to a whole CTA (128 / G envs, G the
  * lanes per env), times its per-env scratch within 64 MiB (a hand-with-cube env uses about 62 KB,
  * so about 1050 of them fit); a larger type fails with CAPACITY and a message giving the sizes,
  * before anything is launched. Env types that fit in shared memory have no limit.
- * First call: the first call on a device looks up the array's device address (with that device
- * made current, the caller's device restored); make that first call before any stream capture.
+ * Address: each call outside a stream capture looks up the array's device address on the
+ * handle's device (with that device made current, the caller's device restored), so a device
+ * reset between calls is followed; a call during a capture reuses the address of the last call on
+ * that device, so make a first call before any stream capture (one made during a capture fails
+ * with INVALID_ARG).
  * Sharing: every call, from every handle on a device, uses the same array, which keeps the last
  * call's contents. Nothing in it needs to start at zero (each step writes every scratch word
  * before reading it). Calls whose kernels overlap on the GPU (different streams without ordering
  * between them) race on the array and give wrong results: order them on one stream or with
  * events. Asynchronous on the handle's stream. Errors: HANDLE, INVALID_ARG (a NULL buffer,
- * dt <= 0 or non-finite, substeps < 1), CAPACITY (above), CUDA. */
+ * dt <= 0 or non-finite, substeps < 1, the refused flags and drives above, a first call during a
+ * capture), CAPACITY (above), CUDA. */
 int sim_step_static_scratch(sim_handle h, const sim_state_buffers* io, float dt, int32_t substeps);
 
 /* ---- launch plan --------------------------------------------------------------------------------

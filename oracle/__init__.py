@@ -98,6 +98,8 @@ def lib():
         L.oracle_rows.argtypes = [ctypes.c_void_p, ctypes.c_int32, D, D, ctypes.c_int32, D, D, I32, I32, D, D, D,
                                   I32]
         L.oracle_rows.restype = ctypes.c_int32
+        L.oracle_opcount_probe.argtypes = [ctypes.c_int32, ctypes.c_int32]
+        L.oracle_opcount_probe.restype = ctypes.c_double
         _lib = L
     return _lib
 
@@ -114,6 +116,11 @@ def capsule_box(p0, p1, r, ext):
              for s in range(3)]
     slots.append(dict(clip=bool(out[22]), ta=out[23], tb=out[24]))
     return out[0], slots
+
+
+def opcount_probe(which: int, n: int = 0) -> float:
+    """Operations the counting scalar records for one primitive (see oracle_opcount_probe)."""
+    return float(lib().oracle_opcount_probe(int(which), int(n)))
 
 
 def _dp(a: np.ndarray):

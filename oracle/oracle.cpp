@@ -1818,4 +1818,62 @@ int32_t oracle_rows(void* h, int32_t env, const double* root, const double* dof,
   return (int32_t)rows.size();
 }
 
+// Operation count of one primitive evaluated on the counting scalar (the pins of the counter
+// itself): which = 0..7 one add, sub, mul, div, sqrt, sin, cos, atan2; 8 a negation; 9 fabs; 10 a
+// comparison; 20 dot; 21 cross; 22 3x3 matrix times vector; 23 3x3 matrix product; 24 quaternion
+// product; 25 quaternion exponential of a rotation vector of length 0.3; 26 6x6 matrix times
+// spatial vector; 27 6x6 matrix product; 28 spatial dot product; 29 Cholesky factor of an n x n SPD
+// matrix; 30 the two triangular solves with that factor. Returns -1 for an unknown `which`.
+double oracle_opcount_probe(int32_t which, int32_t n) {
+  using C = OpCount;
+  const C a(0.7), b(1.3);
+  Vec3<C> u = mk3<C>(C(0.1), C(0.2), C(0.3)), w = mk3<C>(C(-0.4), C(0.5), C(0.6));
+  Mat3<C> R, S;
+  SMat<C> X, Y;
+  SVec<C> sv;
+  for (int i = 0; i < 9; ++i) { R.e[i] = C(0.1 * i + 0.05); S.e[i] = C(0.3 - 0.02 * i); }
+  for (int i = 0; i < 36; ++i) { X.e[i] = C(0.01 * i); Y.e[i] = C(0.5 - 0.01 * i); }
+  for (int i = 0; i < 6; ++i) sv[i] = C(0.2 * i - 0.4);
+  const C q1[4] = {C(0.1), C(0.2), C(0.3), C(0.9)}, q2[4] = {C(-0.2), C(0.1), C(0.4), C(0.8)};
+  C qo[4];
+  // SPD matrix for the Cholesky probes: n I + (all ones)
+  std::vector<C> A((size_t)std::max(n, 1) * std::max(n, 1));
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) A[i * n + j] = C((i == j ? (double)n : 0.0) + 1.0);
+  if (which == 29 || which == 30) {
+    if (n < 1) return -1.0;
+    if (which == 30) cholesky_factor(A, n);
+  }
+  std::vector<C> rhs((size_t)std::max(n, 1), C(1.0));
+  volatile double sink = 0.0;
+  OpCount::reset();
+  switch (which) {
+    case 0: sink = val(a + b); break;
+    case 1: sink = val(a - b); break;
+    case 2: sink = val(a * b); break;
+    case 3: sink = val(a / b); break;
+    case 4: sink = val(sqrt(a)); break;
+    case 5: sink = val(sin(a)); break;
+    case 6: sink = val(cos(a)); break;
+    case 7: sink = val(atan2(a, b)); break;
+    case 8: sink = val(-a); break;
+    case 9: sink = val(fabs(a)); break;
+    case 10: sink = (a < b) ? 1.0 : 0.0; break;
+    case 20: sink = val(dot(u, w)); break;
+    case 21: sink = val(cross(u, w)[0]); break;
+    case 22: sink = val(mul(R, u)[1]); break;
+    case 23: sink = val(mul(R, S).e[4]); break;
+    case 24: quat_mul(q1, q2, qo); sink = val(qo[3]); break;
+    case 25: quat_exp(mk3<C>(C(0.1), C(0.2), C(std::sqrt(0.09 - 0.05))), qo); sink = val(qo[3]); break;
+    case 26: sink = val(smul(X, sv)[2]); break;
+    case 27: sink = val(smul(X, Y).e[7]); break;
+    case 28: sink = val(sdot(sv, sv)); break;
+    case 29: cholesky_factor(A, n); sink = val(A[0]); break;
+    case 30: cholesky_solve(A, n, rhs.data()); sink = val(rhs[0]); break;
+    default: return -1.0;
+  }
+  (void)sink;
+  return (double)OpCount::count();
+}
+
 }  // extern "C"

@@ -2,6 +2,9 @@
 // multiply, divide, negate-free arithmetic op, sqrt, sin and cos performed on it increments a
 // thread-local counter; comparisons are not counted. Running the oracle's step with this scalar
 // gives the algorithmic floating-point operation count of the method on an actual trajectory.
+// Pinned (tests/test_oracle_opcount.py): each counted operation type counts once and the free ones
+// not at all, helper routines and the Cholesky factor / solve match hand-derived closed forms, and
+// the solve's cost per position and velocity iteration matches its hand count on the whole step.
 #pragma once
 #include <cmath>
 #include <cstdint>

@@ -6,7 +6,9 @@ vector-Jacobian product (sim_step_vjp), with the step's constraint and active se
 
 `rollout` chains env-steps with checkpointing: each segment of `checkpoint` steps keeps only its
 input state during the forward pass and, in the backward pass, re-runs its steps (bitwise the same
-values) to recover every step's input before applying the adjoints in reverse order.
+values) to recover every step's input before applying the adjoints in reverse order. The forward
+pass leaves the handle's views at the rollout's final state; the backward pass restores them after
+its recomputation.
 """
 from __future__ import annotations
 
@@ -60,6 +62,10 @@ class Segment(torch.autograd.Function):
         s = ctx.s
         root, dof, cache, acts = ctx.saved_tensors
         with torch.no_grad():
+            # the recomputation steps the handle's own views; they are put back afterwards, so a
+            # caller that keeps stepping the handle after backward() continues from where the
+            # forward pass (or its own later steps) left it
+            kept = (s.root_state.clone(), s.dof_state.clone(), s.impulse_cache.clone(), s.dof_actuation.clone())
             _, inputs = _forward_steps(s, root, dof, cache, acts, keep_inputs=True)
             g_acts = torch.zeros_like(acts)
             g = (g_root if g_root is not None else torch.zeros_like(root),
@@ -70,6 +76,8 @@ class Segment(torch.autograd.Function):
                 gr, gd, gc, ga = _vjp(s, r, d, c, acts[k], *g)
                 g_acts[k] = ga
                 g = (gr, gd, gc)
+            for view, value in zip((s.root_state, s.dof_state, s.impulse_cache, s.dof_actuation), kept):
+                view.copy_(value)
         return None, g[0], g[1], g[2], g_acts
 
 

@@ -10,7 +10,8 @@ namespace artsim {
 // costliest types first, so the cheap tiles fill the tail) until none is left. The last warp to
 // finish resets the counters, so back-to-back launches (and graph replays) need no memset. Each
 // variant's tile body is a separate (not inlined) function, so it gets its own register
-// allocation: inlining all six into the one kernel measured 10 % slower on Humanoid-like envs.
+// allocation: inlining all six into the one kernel measured slower on Humanoid-like envs (by 10
+// and by 20 % in two builds of the kernel).
 template <int G, bool GROWS, bool BALL>
 __device__ __noinline__ void persistent_tile(const StepArgs& A, const TypeArgs& TA, int tile, float* wsm,
                                                 int gwarp) {

@@ -748,26 +748,37 @@ constexpr int kMaxStaticDevices = 64;
 std::mutex g_static_mu;
 float* g_static_addr[kMaxStaticDevices] = {};
 
-// Device address of g_static_scratch on device `dev`, looked up on the first request for that
-// device with that device current (the caller's current device is restored afterwards).
-int static_scratch_address(int dev, float** out) {
+// Device address of g_static_scratch on device `dev`, looked up with that device current (the
+// caller's current device is restored afterwards). Outside a stream capture every call looks the
+// address up again, so a context the caller destroyed and re-created between calls (the module
+// reloaded, possibly elsewhere) is followed; during a capture the address of the last call on the
+// device is reused (a lookup could load the module, which a capture does not allow).
+int static_scratch_address(int dev, cudaStream_t st, float** out) {
   if (dev < 0 || dev >= kMaxStaticDevices) {
     g_last_error = "sim_step_static_scratch: device ordinal out of range";
     return SIM_ERR_CAPACITY;
   }
   std::lock_guard<std::mutex> lk(g_static_mu);
-  if (!g_static_addr[dev]) {
-    int prev = 0;
-    CK(cudaGetDevice(&prev));
-    CK(cudaSetDevice(dev));
-    float* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress((void**)&p, g_static_scratch);
-    const cudaError_t e2 = cudaSetDevice(prev);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_static_scratch)");
-    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaSetDevice (restoring the caller's device)");
-    g_static_addr[dev] = p;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  CK(cudaStreamIsCapturing(st, &cs));
+  if (cs != cudaStreamCaptureStatusNone) {
+    if (!g_static_addr[dev]) {
+      g_last_error = "sim_step_static_scratch: the first call on a device must come before any stream capture";
+      return SIM_ERR_INVALID_ARG;
+    }
+    *out = g_static_addr[dev];
+    return SIM_OK;
   }
-  *out = g_static_addr[dev];
+  int prev = 0;
+  CK(cudaGetDevice(&prev));
+  CK(cudaSetDevice(dev));
+  float* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress((void**)&p, g_static_scratch);
+  const cudaError_t e2 = cudaSetDevice(prev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_static_scratch)");
+  if (e2 != cudaSuccess) return cuda_fail(e2, "cudaSetDevice (restoring the caller's device)");
+  g_static_addr[dev] = p;
+  *out = p;
   return SIM_OK;
 }
 
@@ -994,6 +1005,19 @@ int sim_step_static_scratch(sim_handle h, const sim_state_buffers* io, float dt,
       !io->impulse_cache || !io->contact_pairs || !io->contact_count || !io->signature || !io->status)
     return SIM_ERR_INVALID_ARG;
   if (!(dt > 0.f) || !finite(dt) || substeps < 1) return SIM_ERR_INVALID_ARG;
+  // the call reads and writes only *io: steps that would read the handle's control views (drive
+  // targets, body forces) or write its output views (DOF forces, rigid-body states) are refused
+  if (h->params.flags & (SIM_FLAG_BODY_FORCES | SIM_FLAG_RIGID_BODY_STATE | SIM_FLAG_DOF_FORCE)) {
+    g_last_error = "sim_step_static_scratch: handles created with SIM_FLAG_BODY_FORCES, SIM_FLAG_RIGID_BODY_STATE "
+                   "or SIM_FLAG_DOF_FORCE are refused (those steps use the handle's views)";
+    return SIM_ERR_INVALID_ARG;
+  }
+  for (const TypePlan& tp : h->types)
+    if (tp.tab.has_drives) {
+      g_last_error = "sim_step_static_scratch: env types with joint drives are refused (their targets are the "
+                     "handle's views)";
+      return SIM_ERR_INVALID_ARG;
+    }
   // the types launch one after another on the handle's stream, so each may use the whole array
   for (const TypePlan& tp : h->types) {
     if (!tp.lay.grows) continue;
@@ -1012,13 +1036,15 @@ int sim_step_static_scratch(sim_handle h, const sim_state_buffers* io, float dt,
     }
   }
   float* scratch = nullptr;
-  const int rc = static_scratch_address(h->device, &scratch);
+  const int rc = static_scratch_address(h->device, h->stream, &scratch);
   if (rc != SIM_OK) return rc;
   StepArgs a;
   fill_common(h, dt, substeps, a);
   a.root = io->root_state; a.dof = io->dof_state; a.act = io->dof_actuation; a.net_force = io->net_contact_force;
   a.cache = io->impulse_cache; a.pairs = io->contact_pairs; a.n_pairs = io->contact_count;
   a.sig = io->signature; a.status = io->status;
+  a.pos_target = nullptr; a.vel_target = nullptr; a.body_force = nullptr;  // refused above: never read
+  a.dof_force = nullptr; a.body_state = nullptr;                          // nor written
   for (size_t t = 0; t < h->types.size(); ++t) {
     const TypePlan& tp = h->types[t];
     TypeArgs ta;

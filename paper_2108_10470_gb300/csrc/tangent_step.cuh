@@ -10,7 +10,8 @@
 // joint-space inertia M from composite inertias and the bias b from a recursive Newton-Euler pass,
 // both in world axes about each actor's root origin. Branches (contact and limit decisions, clamps,
 // the speculative / biased target) follow the value, so the derivative is that of the step with its
-// constraint and active sets held fixed. Shape-pair contacts are not part of this path.
+// constraint and active sets held fixed. Capsule-box pair contacts go through a dual version of the
+// forward step's pair geometry (segment-box closest point, face clip, sphere-box) with two-body rows.
 #pragma once
 #include "sim_internal.h"
 

@@ -286,11 +286,41 @@ class Sim:
     STATE_NAMES = ("root_state", "dof_state", "dof_actuation", "net_contact_force", "impulse_cache", "contact_pairs",
                    "contact_count", "signature", "status")
 
+    # view whose dtype and size each caller-owned buffer of the VJP / JVP / static-scratch calls mirrors
+    MIRRORS = {"root_state": "root_state", "dof_state": "dof_state", "dof_actuation": "dof_actuation",
+               "impulse_cache": "impulse_cache", "net_contact_force": "net_contact_force",
+               "contact_pairs": "contact_pairs", "contact_count": "contact_count", "signature": "signature",
+               "status": "status"}
+
+    def _dev_ptr(self, t, name: str, dtypes, need: int) -> int:
+        """Address of a caller-owned device tensor after checking what the C ABI assumes of it: a
+        torch tensor of one of `dtypes`, contiguous, on the handle's device, with at least `need`
+        elements. Raises ValueError (before anything is launched) otherwise."""
+        torch = self._torch
+        if not isinstance(t, torch.Tensor):
+            raise ValueError(f"{name}: expected a torch tensor, got {type(t).__name__}")
+        if t.dtype not in dtypes:
+            raise ValueError(f"{name}: dtype {t.dtype}, expected {' or '.join(str(d) for d in dtypes)}")
+        if t.device != self.root_state.device:
+            raise ValueError(f"{name}: on {t.device}, the simulation is on {self.root_state.device}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name}: must be contiguous")
+        if t.numel() < need:
+            raise ValueError(f"{name}: {t.numel()} elements, at least {need} needed")
+        return t.data_ptr()
+
+    def _mirror_ptr(self, t, name: str, view: str) -> int:
+        """_dev_ptr for a buffer laid out like the view `view` (same dtype family and size)."""
+        torch = self._torch
+        v = getattr(self, view)
+        dtypes = (torch.float32,) if v.dtype == torch.float32 else (torch.int32, getattr(torch, "uint32", torch.int32))
+        return self._dev_ptr(t, name, dtypes, v.numel())
+
     def step_static_scratch(self, bufs: dict, dt: Optional[float] = None, substeps: Optional[int] = None):
         """The step on caller-owned device tensors (keys STATE_NAMES, each shaped and typed like the
         view of the same name), with the library's built-in scratch array: the call allocates no
         device memory."""
-        io = sim_state_buffers(*[ctypes.c_void_p(bufs[k].data_ptr()) for k in self.STATE_NAMES])
+        io = sim_state_buffers(*[ctypes.c_void_p(self._mirror_ptr(bufs[k], k, k)) for k in self.STATE_NAMES])
         check(load().sim_step_static_scratch(self.h, ctypes.byref(io), float(self.w.dt if dt is None else dt),
                                              int(self.w.substeps if substeps is None else substeps)),
               "sim_step_static_scratch")
@@ -332,9 +362,18 @@ class Sim:
         check(load().sim_compute_jacobian(self.h, ctypes.c_void_p(out.data_ptr())), "sim_compute_jacobian")
         return out
 
-    @staticmethod
-    def _ptrs(fields, bufs):
-        return [ctypes.c_void_p(bufs[f].data_ptr()) if bufs.get(f) is not None else None for f in fields]
+    def _ptrs(self, fields, bufs):
+        """Checked addresses of the VJP / JVP buffers (each laid out like the view its name ends in;
+        missing or None entries pass as NULL)."""
+        out = []
+        for f in fields:
+            t = bufs.get(f)
+            if t is None:
+                out.append(None)
+                continue
+            view = next(v for v in ("root_state", "dof_state", "dof_actuation", "impulse_cache", "status") if v in f)
+            out.append(ctypes.c_void_p(self._mirror_ptr(t, f, view)))
+        return out
 
     def step_vjp(self, bufs: dict, dt: Optional[float] = None, substeps: Optional[int] = None):
         """Vector-Jacobian product of one env-step at bufs' input state (keys VJP_FIELDS; device
@@ -350,14 +389,22 @@ class Sim:
                                   int(self.w.substeps if substeps is None else substeps)), "sim_step_jvp")
 
     def set_root_state_indexed(self, src, actor_idx):
+        """src: (n, 13) float32 root states; actor_idx: n int32 actor indices (device tensors)."""
         n = int(actor_idx.numel())
-        check(load().sim_set_root_state_indexed(self.h, ctypes.c_void_p(src.data_ptr()),
-                                                ctypes.c_void_p(actor_idx.data_ptr()), n), "sim_set_root_state_indexed")
+        pi = self._dev_ptr(actor_idx, "actor_idx", (self._torch.int32,), n)
+        ps = self._dev_ptr(src, "src", (self._torch.float32,), 13 * n)
+        check(load().sim_set_root_state_indexed(self.h, ctypes.c_void_p(ps), ctypes.c_void_p(pi), n),
+              "sim_set_root_state_indexed")
 
     def set_dof_state_indexed(self, src, env_idx):
+        """src: n rows of (largest env DOF count) x 2 float32; env_idx: n int32 env indices."""
         n = int(env_idx.numel())
-        check(load().sim_set_dof_state_indexed(self.h, ctypes.c_void_p(src.data_ptr()),
-                                               ctypes.c_void_p(env_idx.data_ptr()), n), "sim_set_dof_state_indexed")
+        if not hasattr(self, "_max_jdof"):
+            self._max_jdof = max((self.w.env_jdof(e) for e in range(self.w.n_envs)), default=0)
+        pi = self._dev_ptr(env_idx, "env_idx", (self._torch.int32,), n)
+        ps = self._dev_ptr(src, "src", (self._torch.float32,), 2 * self._max_jdof * n)
+        check(load().sim_set_dof_state_indexed(self.h, ctypes.c_void_p(ps), ctypes.c_void_p(pi), n),
+              "sim_set_dof_state_indexed")
 
     def set_stream(self, stream):
         self._stream = stream

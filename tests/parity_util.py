@@ -115,5 +115,8 @@ def fp32_scales(w, root, dof, acts, steps, rtol=1e-4, atol=1e-5):
         sk["strict_frac"] = {key: min(float(np.mean(np.abs(run[k][key] - base[k][key]) <=
                                                     atol + rtol * np.abs(base[k][key]))) for run in runs)
                              if base[k][key].size else 1.0 for key in per}
+        # per component: the largest deviation of the four FP32 evaluations from FP64
+        sk["component"] = {key: np.max([np.abs(run[k][key] - base[k][key]) for run in runs], axis=0)
+                           for key in per}
         scales.append(sk)
     return base, scales

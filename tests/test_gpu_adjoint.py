@@ -213,6 +213,9 @@ def loss_grad_gpu(w, root, dof, acts, checkpoint):
     rf, df, cf = AG.rollout(s, r0, d0, c0, A, checkpoint=checkpoint)
     loss = rf[:, 7].mean()  # mean final root x-velocity
     loss.backward()
+    # the backward pass re-ran the segments on the handle: its views are back at the final state
+    assert torch.equal(s.root_state, rf.detach()) and torch.equal(s.dof_state, df.detach())
+    assert torch.equal(s.impulse_cache, cf.detach())
     out = (float(loss), d0.grad.cpu().numpy().astype(np.float64), A.grad.cpu().numpy().astype(np.float64),
            rf.detach().cpu().numpy())
     s.destroy()

@@ -4,18 +4,22 @@ Tolerance. The strict bound per component is |gpu - oracle| <= atol + rtol |orac
 1e-4 / 1e-5 after one env-step and 1e-3 / 1e-3 after 16. The method is ill-conditioned in
 places (the TGS position bias divides separations by h/n_pos, and light links amplify contact
 impulses), so a faithful FP32 evaluation cannot meet the strict bound on every component: the
-oracle's own algorithm run in single precision misses it on the same fraction of components as
-the GPU. The test therefore requires (a) at least 98 % of components within the strict bound
-on samples of 1000 components or more, or, where the CPU FP32 evaluations themselves fall below
-98 % (the Humanoid over 16 steps: 97.75 to 97.94 % of DOF components), their lowest fraction less
-half a percentage point, and (b) every component within the strict
-bound plus K = 16 times its env's FP32 conditioning scale (the largest deviation from FP64 of four
-single-precision evaluations of the oracle algorithm with inputs nudged by one float32 ulp).
+oracle's own algorithm run in single precision misses it on a small fraction of components. With
+f32 = the lowest fraction of components within the strict bound over four single-precision
+evaluations of the oracle (inputs as given and nudged by one float32 ulp), every sample, however
+small, must have
+  (a) a fraction within the strict bound of at least max(0.98, f32 - 0.005), or f32 - 0.005 where
+      the FP32 evaluations themselves stay below 98 % (the Humanoid over 16 steps);
+  (b) every component within the strict bound plus K = 16 times its env's FP32 conditioning scale
+      (the largest deviation from FP64 of those four evaluations over the env's components);
+  (c) on samples of fewer than 1000 components, where the fraction is coarse, every component
+      within the strict bound or within 4 times that component's own FP32 deviation.
 
 Integer work (contact pairs, counts, the constraint-set signature) must match bit-exactly; an
 environment whose constraint set differs at some step (a contact or limit decision within
 rounding of its threshold) is counted as a contact-set change, reported, and excluded from the
-state comparison from then on.
+state comparison from then on. At most 5 % of the envs of a small one-step batch may change
+(1 % at full size), and 10 % over 16 steps.
 """
 import numpy as np
 import pytest
@@ -45,7 +49,19 @@ def workload(name, n_envs):
 PER = {"root": lambda w: w.env_actor_count, "dof": lambda w: w.env_jdof, "net_force": lambda w: w.env_body}
 
 
-def check_rollout(w, steps, rtol, atol, seed=0, min_same=0.75, flags=1, setup=None):
+K_COMPONENT = 4.0
+SMALL_SAMPLE = 1000
+
+
+def strict_fraction_bar(f32_frac):
+    """Lowest admissible fraction of components within the strict bound: 98 %, or half a
+    percentage point under the FP32 evaluations of the oracle where those do better or worse."""
+    return max(0.98, f32_frac - 0.005) if f32_frac >= 0.98 else f32_frac - 0.005
+
+
+def check_rollout(w, steps, rtol, atol, seed=0, min_same=None, flags=1, setup=None):
+    if min_same is None:
+        min_same = (0.99 if w.n_envs >= 1024 else 0.95) if steps == 1 else 0.9
     root, dof, acts = W.seeded_inputs(w, seed, steps)
     g = gpu_rollout(w, root, dof, acts, steps, flags=flags, setup=setup)
     o, scales = fp32_scales(w, root, dof, acts, steps, rtol, atol)
@@ -59,7 +75,8 @@ def check_rollout(w, steps, rtol, atol, seed=0, min_same=0.75, flags=1, setup=No
             c = int(o[k]["n_pairs"][e])
             assert np.array_equal(g[k]["pairs"][e, :c], o[k]["pairs"][e, :c])
     changed = int((~same).sum())
-    assert same.mean() >= min_same, f"{changed} of {w.n_envs} envs changed constraint sets"
+    assert same.mean() >= min_same, \
+        f"{changed} of {w.n_envs} envs changed constraint sets (at most {(1 - min_same) * 100:.0f} % may)"
     report = [f"{w.name} x{w.n_envs}, {steps} steps: contact-set changes in {changed} envs"]
     for key in ("root", "dof", "net_force"):
         a, b = g[-1][key], o[-1][key]
@@ -72,10 +89,16 @@ def check_rollout(w, steps, rtol, atol, seed=0, min_same=0.75, flags=1, setup=No
         count = int(comp_mask.sum()) * (a.shape[1] if a.ndim > 1 else 1)
         frac = float(within[comp_mask].mean()) if comp_mask.any() else 1.0
         f32_frac = scales[-1]["strict_frac"][key]
-        report.append(f"  {key}: {100 * frac:.3f} % of components within the strict bound "
-                      f"(CPU FP32 evaluation: {100 * f32_frac:.3f} %)")
-        bar = min(0.98, f32_frac - 0.005)  # a faithful FP32 evaluation can do no better than the FP32 oracle
-        assert count < 1000 or frac >= bar, f"{key}: only {frac:.4f} within the strict bound (bar {bar:.4f})"
+        bar = strict_fraction_bar(f32_frac)
+        report.append(f"  {key}: {100 * frac:.3f} % of {count} components within the strict bound "
+                      f"(CPU FP32 evaluation: {100 * f32_frac:.3f} %, bar {100 * bar:.3f} %)")
+        assert frac >= bar, f"{key}: only {frac:.4f} of {count} components within the strict bound (bar {bar:.4f})"
+        if count < SMALL_SAMPLE and comp_mask.any():
+            own = scales[-1]["component"][key]
+            ok = within | (np.abs(a - b) <= K_COMPONENT * own)
+            bad = int((~ok[comp_mask]).sum())
+            assert bad == 0, f"{key}: {bad} of {count} components outside both the strict bound and " \
+                             f"{K_COMPONENT:g} x their own FP32 deviation"
         for e in np.nonzero(same)[0]:
             sl = rows[e]
             if sl.stop == sl.start:
@@ -92,7 +115,7 @@ def check_rollout(w, steps, rtol, atol, seed=0, min_same=0.75, flags=1, setup=No
 def test_one_step(name, n_envs):
     """One env-step (2 substeps) at 1e-4 relative / 1e-5 absolute; sizes span several CTAs and a
     ragged last block."""
-    check_rollout(workload(name, n_envs), 1, 1e-4, 1e-5, min_same=0.9)
+    check_rollout(workload(name, n_envs), 1, 1e-4, 1e-5)
 
 
 @pytest.mark.parametrize("name,n_envs", [("cartpole", 64), ("ant", 67), ("humanoid", 37), ("hand", 37),
@@ -103,18 +126,18 @@ def test_sixteen_steps(name, n_envs):
 
 
 @pytest.mark.parametrize("name,n_envs", [("ant", 67), ("humanoid", 37), ("hand", 37), ("mixed", 67)])
-@pytest.mark.parametrize("steps,rtol,atol,min_same", [(1, 1e-4, 1e-5, 0.9), (16, 1e-3, 1e-3, 0.75)])
-def test_row_solver_form(name, n_envs, steps, rtol, atol, min_same):
+@pytest.mark.parametrize("steps,rtol,atol", [(1, 1e-4, 1e-5), (16, 1e-3, 1e-3)])
+def test_row_solver_form(name, n_envs, steps, rtol, atol):
     """The row form of the Gauss-Seidel solve (SIM_FLAG_ROW_SOLVER: each row's J v and separation
     as group reductions over Y), the form a substep falls back to when its Delassus block does not
     fit beside Y, against the oracle at the same bars as the default form."""
-    check_rollout(workload(name, n_envs), steps, rtol, atol, min_same=min_same, flags=1 | 64)
+    check_rollout(workload(name, n_envs), steps, rtol, atol, flags=1 | 64)
 
 
 @pytest.mark.parametrize("name,n_envs", [("ant", 4096), ("humanoid", 4096), ("hand", 4096), ("mixed", 16384)])
 def test_full_size_one_step(name, n_envs):
     """Full-size configurations (one launch per env type and step) against the oracle on all envs."""
-    check_rollout(workload(name, n_envs), 1, 1e-4, 1e-5, min_same=0.9)
+    check_rollout(workload(name, n_envs), 1, 1e-4, 1e-5)
 
 
 def test_impulse_cache_and_forces_match():

@@ -32,20 +32,19 @@ TENDONS = {
 @pytest.mark.parametrize("steps,rtol,atol", [(1, 1e-4, 1e-5), (16, 1e-3, 1e-3)])
 def test_two_joint_tendons_match_oracle(kind, steps, rtol, atol):
     w = W.homogeneous("pair", two_joints(tendon=TENDONS[kind]), 67, params=NOGRAV)
-    check_rollout(w, steps, rtol, atol, min_same=0.9)
+    check_rollout(w, steps, rtol, atol)
 
 
 @pytest.mark.parametrize("steps,rtol,atol", [(1, 1e-4, 1e-5), (16, 1e-3, 1e-3)])
 def test_coupled_hand_matches_oracle(steps, rtol, atol):
-    check_rollout(W.hand_tendon_workload(37), steps, rtol, atol, min_same=0.9 if steps == 1 else 0.75)
+    check_rollout(W.hand_tendon_workload(37), steps, rtol, atol)
 
 
 @pytest.mark.parametrize("steps,rtol,atol", [(1, 1e-4, 1e-5), (16, 1e-3, 1e-3)])
 def test_tendon_ant_matches_oracle(steps, rtol, atol):
     """The Ant with a spring, a length-limited and an equality tendon (floating base, ground
     contacts and joint limits with tendon rows in the same solve)."""
-    check_rollout(W.homogeneous("tendon_ant", W.ant(tendons=True), 67), steps, rtol, atol,
-                  min_same=0.9 if steps == 1 else 0.75)
+    check_rollout(W.homogeneous("tendon_ant", W.ant(tendons=True), 67), steps, rtol, atol)
 
 
 def test_equality_tendon_moves_joints_together_on_gpu():
