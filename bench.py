@@ -93,6 +93,63 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def profile_fields(kernel: str, wname: str):
+    """(fields, table rows, captured env count) of the committed ncu summary of this kernel and
+    workload whose kernel sources match the current ones; (None, None, None) if there is none."""
+    import glob
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", f"{kernel}_{wname}[0-9]*.md"))):
+        try:
+            text = open(path).read().splitlines()
+            fields = dict(ln.split(":", 1) for ln in text[:6] if ":" in ln)
+            if fields.get("kernel_source_sha256_16", "").strip() != kernel_source_hash():
+                continue
+            rows = {}
+            for ln in text:
+                cells = [c.strip() for c in ln.split("|")]
+                if len(cells) > 4 and cells[2].startswith("`"):
+                    rows[cells[2].strip("`")] = cells[3]
+            return fields, rows, int(os.path.basename(path)[len(kernel) + 1 + len(wname):-3])
+        except (OSError, ValueError):
+            continue
+    return None, None, None
+
+
+def profiled_fma_pipe_pct(kernel: str, wname: str):
+    """FMA-pipe utilisation (% of peak, active cycles) from the committed ncu summary, or None."""
+    _, rows, _ = profile_fields(kernel, wname)
+    try:
+        return float(rows["sm__pipe_fma_cycles_active.avg.pct_of_peak_sustained_active"].split()[0])
+    except (TypeError, KeyError, ValueError, IndexError):
+        return None
+
+
+def sample_inputs(w, idx, root, dof, acts):
+    """The seeded inputs of a subset of envs, taken from the whole batch's arrays (so the subset sees
+    exactly the inputs the GPU run gives those envs)."""
+    ra = np.cumsum([0] + [w.env_actor_count(e) for e in range(w.n_envs)])
+    rd = np.cumsum([0] + [w.env_jdof(e) for e in range(w.n_envs)])
+    r = np.concatenate([root[ra[e]:ra[e + 1]] for e in idx])
+    d = np.concatenate([dof[rd[e]:rd[e + 1]] for e in idx])
+    a = np.concatenate([acts[:, rd[e]:rd[e + 1]] for e in idx], axis=1)
+    return r, d, a
+
+
+def window_flops(w, root, dof, acts, warm, steps, sample=64):
+    """Algorithmic flops per env-step over the steps warm .. warm + steps - 1 of the seeded
+    trajectory (the bench's timed window), counted by the oracle's operation-counting scalar on a
+    strided sample of the batch's envs (the step's cost grows with the ground contacts made)."""
+    import oracle
+    idx = list(range(0, w.n_envs, max(1, w.n_envs // sample)))[:sample]
+    ws = w.subset(idx)
+    r, d, a = sample_inputs(w, idx, root, dof, acts)
+    O = oracle.Oracle(ws)
+    r, d = r.astype(np.float64), d.astype(np.float64)
+    for k in range(warm):
+        O.step(r, d, a[k])
+    total = sum(O.step_flops(r, d, a[warm + k]) for k in range(steps))
+    return total / (steps * len(idx)), f"steps {warm}..{warm + steps - 1}, {len(idx)} envs (every {w.n_envs // len(idx)}th)"
+
+
 def profiled_traffic(kernel: str, wname: str, n_envs: int):
     """DRAM bytes (read + write) per launch of `kernel` from the committed ncu summary of this
     workload (profiles/<kernel>_<workload><envs>.md), scaled to n_envs; None if there is none or
@@ -199,15 +256,9 @@ def cpu_baseline(wname, n_envs, budget_s=15.0):
         O.step(r, d, acts[k % n_act], n_threads=threads)
     el = time.perf_counter() - t0
     value = n_envs * n_steps / el
-    # algorithmic flops per env-step, counted on a 64-env, 4-step sample of the same trajectory
-    ws = w.subset(list(range(min(64, n_envs))))
-    Oc = oracle.Oracle(ws)
-    rs, ds, acs = W.seeded_inputs(ws, 0, 4)
-    rs, ds = rs.astype(np.float64), ds.astype(np.float64)
-    flops = sum(Oc.step_flops(rs, ds, acs[k]) for k in range(4)) / (4 * ws.n_envs)
     return {"value": value, "unit": "env-steps/s", "cores": threads, "kind": "oracle",
             "sample": f"{n_steps} env-steps of all {n_envs} envs after 1 warm-up step ({el:.1f} s, "
-                      f"{threads} threads)"}, flops
+                      f"{threads} threads)"}
 
 
 def run_reference(args, rank, world):
@@ -325,28 +376,41 @@ def run_ours(args, rank, world, local_rank):
     kern_avg_s = statistics.mean(kern_ms) / 1e3
     roof = None
     cpu = None
-    if world == 1 and not args.no_cpu_baseline:
-        cpu, flops_per_env_step = cpu_baseline(args.workload, args.envs)
+    if world == 1:
+        kname = "persistent_step_kernel" if args.persistent else "step_kernel"
+        flops_per_env_step, window = window_flops(w, root, dof, acts, Wm, K)
+        peak = probe_peak_flops()
         sm_mhz = clocks["sm_mhz"] or 2070.0
-        peak = SM_COUNT_NOMINAL * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6
+        nominal = SM_COUNT_NOMINAL * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6
         achieved = flops_per_env_step * w.n_envs / kern_avg_s
         roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
                 "frac": achieved / peak,
-                "traffic": args.traffic if args.traffic is not None else
-                profiled_traffic("persistent_step_kernel" if args.persistent else "step_kernel", args.workload,
-                                 w.n_envs),
+                "traffic": args.traffic if args.traffic is not None else profiled_traffic(kname, args.workload, w.n_envs),
                 "algorithmic_bytes_per_step": algo_bytes_per_step(w),
-                "kernel": "persistent_step_kernel" if args.persistent else "step_kernel", "kernel_ms": 1e3 * kern_avg_s,
-                "flops_per_env_step": flops_per_env_step,
-                "peak_basis": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (median SM clock sampled "
-                              f"in the timed region)"}
+                "kernel": kname, "kernel_ms": 1e3 * kern_avg_s,
+                "flops_per_env_step": flops_per_env_step, "flops_window": window,
+                "peak_basis": "measured: FP32 FMA throughput of sim_probe_fp32_peak on this GPU (all SMs, 8 "
+                              "independent FMA chains per thread, 64 warps per SM), of measured",
+                "peak_nominal": nominal / 1e12, "frac_of_nominal": achieved / nominal,
+                "peak_nominal_basis": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (median SM clock "
+                                      f"sampled in the timed region)",
+                "ncu_fma_pipe_pct": profiled_fma_pipe_pct(kname, args.workload)}
+        if not args.no_cpu_baseline:
+            cpu = cpu_baseline(args.workload, args.envs)
     line["roofline"] = roof
     line["cpu_baseline"] = cpu
     if world == 1 and not args.no_variants and args.workload == "ant" and args.envs == 4096:
         line["variants"] = variants_measure(dev)
+        line["configs"] = configs_measure(dev, peak / 1e12 if roof else None)
     if world == 1 and not args.no_adjoint:
         line["adjoint"] = adjoint_measure(dev)
     print(json.dumps(line), flush=True)
+
+
+def probe_peak_flops() -> float:
+    """The GPU's FP32 FMA throughput measured by the library's probe (median of three runs)."""
+    from paper_2108_10470_gb300 import sim
+    return statistics.median(sim.probe_fp32_peak(20000) for _ in range(3))
 
 
 def timed_steps(s, act_dev, warm, steps, flush):
@@ -395,6 +459,80 @@ def variants_measure(dev, warm=20, steps=200):
     return out
 
 
+def config_line(w, dev, flush, warm, steps, flags=0, autotune=False, peak_tflops=None, flops_sample=32, seed=0):
+    """One config's env-steps/s under the main line's protocol (L2 flushed between timed steps, CUDA
+    events around the action copy and the step), with its FP32 roofline fraction when a peak is
+    given (flops counted by the oracle over the same window on a strided sample of envs)."""
+    import torch
+
+    from paper_2108_10470_gb300 import sim, workloads as W
+
+    root, dof, acts = W.seeded_inputs(w, seed, warm + steps)
+    s = sim.Sim(w, flags=flags)
+    s.root_state.copy_(torch.from_numpy(root))
+    s.dof_state.copy_(torch.from_numpy(dof))
+    act_dev = torch.from_numpy(acts).to(dev)
+    if autotune:
+        for k in range(warm // 2):
+            s.dof_actuation.copy_(act_dev[k])
+            s.step()
+        s.autotune(reps=5)
+        s.root_state.copy_(torch.from_numpy(root))
+        s.dof_state.copy_(torch.from_numpy(dof))
+        s.impulse_cache.zero_()
+    ms = timed_steps(s, act_dev, warm, steps, flush)
+    plan = [{k: c[k] for k in ("lanes_per_env", "rows_global", "warps_per_cta")} for c in
+            (s.type_config(t) for t in range(s.n_types))]
+    s.destroy()
+    out = {"value": w.n_envs / (ms / 1e3), "ms_per_step": ms, "timed_steps": steps, "warmup": warm, "plan": plan}
+    if peak_tflops:
+        f, window = window_flops(w, root, dof, acts, warm, steps, flops_sample)
+        out["roofline"] = {"bound": "alu", "flops_per_env_step": f, "flops_window": window,
+                           "achieved": f * w.n_envs / (ms / 1e3) / 1e12, "peak": peak_tflops, "unit": "TFLOP/s",
+                           "frac": f * w.n_envs / (ms / 1e3) / 1e12 / peak_tflops,
+                           "note": "step time includes the action copy (one launch per env type)"}
+    return out
+
+
+def configs_measure(dev, peak_tflops, warm=20, steps=100):
+    """The other configurations of the workload set, each under the main line's timing protocol:
+    Humanoid-like 4096 envs, hand with cube 4096 envs, cartpole 64 envs over 1000 steps, and the
+    heterogeneous 16384-env batch (40 % Ant-like, 30 % Humanoid-like, 30 % hand with cube) as one
+    launch per env type (concurrent on forked streams, the default), one persistent launch (default
+    and autotuned knobs, and autotuned replayed as a CUDA graph), against the sum of each type's
+    envs stepped alone."""
+    import torch
+
+    from paper_2108_10470_gb300 import sim, workloads as W
+
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    out = {"unit": "env-steps/s"}
+    out["humanoid_4096"] = config_line(W.humanoid_workload(4096), dev, flush, warm, steps, peak_tflops=peak_tflops)
+    out["hand_4096"] = config_line(W.hand_workload(4096), dev, flush, warm, steps, peak_tflops=peak_tflops)
+    out["cartpole_64_1000_steps"] = config_line(W.cartpole_workload(64), dev, flush, warm, 1000,
+                                                peak_tflops=peak_tflops)
+    out["cartpole_64_1000_steps_graph"] = config_line(W.cartpole_workload(64), dev, flush, warm, 1000,
+                                                      flags=sim.SIM_FLAG_GRAPH)
+    mixed = W.mixed_workload(16384)
+    out["mixed_16384_per_type"] = config_line(mixed, dev, flush, warm, steps, peak_tflops=peak_tflops)
+    out["mixed_16384_persistent"] = config_line(mixed, dev, flush, warm, steps, flags=sim.SIM_FLAG_PERSISTENT)
+    out["mixed_16384_persistent_autotuned"] = config_line(mixed, dev, flush, warm, steps, flags=sim.SIM_FLAG_PERSISTENT,
+                                                          autotune=True)
+    out["mixed_16384_persistent_autotuned_graph"] = config_line(
+        mixed, dev, flush, warm, steps, flags=sim.SIM_FLAG_PERSISTENT | sim.SIM_FLAG_GRAPH, autotune=True)
+    # each type's envs of the mixed batch stepped alone (seeded inputs of the same distributions)
+    alone = 0.0
+    for t, name in enumerate(("ant", "humanoid", "hand")):
+        idx = [e for e in range(mixed.n_envs) if int(mixed.env_actor_model[2 * e]) == t]
+        ms = config_line(mixed.subset(idx), dev, flush, warm, steps)["ms_per_step"]
+        out[f"mixed_16384_{name}_alone_ms"] = ms
+        alone += ms
+    out["mixed_16384_sum_of_types_alone_ms"] = alone
+    for k in ("per_type", "persistent", "persistent_autotuned", "persistent_autotuned_graph"):
+        out[f"mixed_16384_{k}_over_sum_of_types_alone"] = out[f"mixed_16384_{k}"]["ms_per_step"] / alone
+    return out
+
+
 def adjoint_measure(dev, n_envs=1024, steps=64, checkpoint=16, reps=2):
     """Adjoint throughput on the differentiable-rollout workload: 1024 Ant-like envs, 64 env-steps,
     loss = mean final root x-velocity, gradients w.r.t. every action and the initial DOF state
@@ -406,6 +544,7 @@ def adjoint_measure(dev, n_envs=1024, steps=64, checkpoint=16, reps=2):
 
     w = W.ant_workload(n_envs)
     s = sim.Sim(w)
+    s_reverse = s.tape_floats() is not None
     root, dof, acts = W.seeded_inputs(w, 0, steps)
     r0 = torch.from_numpy(root).to(dev)
     d0 = torch.from_numpy(dof).to(dev).requires_grad_(True)
@@ -432,7 +571,9 @@ def adjoint_measure(dev, n_envs=1024, steps=64, checkpoint=16, reps=2):
             "workload": f"Ant-like, {n_envs} envs, {steps} env-steps, loss = mean final root x-velocity, gradients "
                         f"w.r.t. actions and initial DOF state, checkpoint every {checkpoint} steps",
             "forward_ms": f_ms, "backward_ms": b_ms, "backward_over_forward": b_ms / f_ms,
-            "method": "forward-mode dual kernel (one env per warp), vector-Jacobian product per env-step"}
+            "method": ("reverse pass: each segment re-run with its tapes recorded (sim_step_taped), then the "
+                       "steps' adjoints (sim_step_adjoint) in reverse order" if s_reverse else
+                       "forward-mode dual kernel (one env per warp), vector-Jacobian product per env-step")}
 
 
 def main():

@@ -123,9 +123,11 @@ typedef struct {
  * reductions over Y = L^-1 J^T) instead of the Delassus form (W = J M^-1 J^T per substep, one
  * row value per lane), which is used otherwise whenever W fits beside Y; the two agree to FP32
  * rounding (paper, Sec. "Physics Simulation": the TGS solve; both forms keep its row order and
- * projections). */
+ * projections); bit 7 (SIM_FLAG_TANGENT_VJP) makes sim_step_vjp use the forward-mode derivative
+ * kernel even where the reverse pass covers the step (a second, independent evaluation). */
 enum { SIM_FLAG_SIGNATURE = 1, SIM_FLAG_PERSISTENT = 2, SIM_FLAG_GRAPH = 4, SIM_FLAG_BODY_FORCES = 8,
-       SIM_FLAG_RIGID_BODY_STATE = 16, SIM_FLAG_DOF_FORCE = 32, SIM_FLAG_ROW_SOLVER = 64 };
+       SIM_FLAG_RIGID_BODY_STATE = 16, SIM_FLAG_DOF_FORCE = 32, SIM_FLAG_ROW_SOLVER = 64,
+       SIM_FLAG_TANGENT_VJP = 128 };
 typedef struct {
   float gravity[3];
   int32_t pos_iters;       /* >= 1 biased (position) iterations                  */
@@ -294,10 +296,17 @@ int sim_autotune(sim_handle h, float dt, int32_t substeps, int32_t reps, double*
  * differentiated. Joint drives act as in the step, with the handle's DOF_POSITION_TARGET /
  * DOF_VELOCITY_TARGET views as constants (no gradient with respect to the targets), and so do the
  * RIGID_BODY_FORCE view's forces under SIM_FLAG_BODY_FORCES; tendon springs and tendon-limit rows
- * are differentiated, and so are capsule-box pair contacts. Supported for env types whose impulse
- * cache has at most 448 entries; other handles fail with CAPACITY. Computed by forward-mode dual arithmetic, one
- * env per warp, each lane carrying up to 8 input directions, in passes of 256 directions per env.
- * (The paper does not differentiate its step; this is the project's own extension.) */
+ * are differentiated, and so are capsule-box pair contacts.
+ * Two evaluations. The reverse pass (sim_step_taped + sim_step_adjoint below) covers env types
+ * without tendons, ball joints and shape pairs, in steps without SIM_FLAG_BODY_FORCES; there the
+ * gradient w.r.t. a root quaternion is its component tangent to the unit sphere (the step's
+ * dependence on |q| is an artefact of the formulation: the output quaternion is normalised).
+ * Otherwise (and under SIM_FLAG_TANGENT_VJP) forward-mode dual arithmetic, one env per warp, each
+ * lane carrying up to 8 input directions, in passes of 256 directions per env, for env types whose
+ * impulse cache has at most 448 entries (other handles fail with CAPACITY).
+ * (The paper does not differentiate its step; this is the project's own extension, following the
+ * paper's remark that its operational-space controller is differentiable, Sec. "Franka cube
+ * stacking".) */
 typedef struct {
   const float* root_state;           /* (N_A, 13) state at the start of the step */
   const float* dof_state;            /* (N_D, 2) */
@@ -317,9 +326,50 @@ typedef struct {
 /* Vector-Jacobian product of one env-step (substeps of dt / substeps) at the given input state:
  * every output gradient entry is contracted with the step's Jacobian. All pointers are device
  * memory owned by the caller, in the layouts of the views of the same names; the handle supplies
- * the model and its stream, its views are not touched. Asynchronous. Errors: HANDLE, INVALID_ARG
- * (a required pointer NULL, dt or substeps invalid), CAPACITY (unsupported env type), CUDA. */
+ * the model and its stream, its views are not touched (the reverse pass steps a library-owned copy
+ * of the input state, allocated on first use). Asynchronous. Errors: HANDLE, INVALID_ARG (a
+ * required pointer NULL, dt or substeps invalid), CAPACITY (unsupported env type), CUDA. */
 int sim_step_vjp(sim_handle h, const sim_vjp_buffers* b, float dt, int32_t substeps);
+
+/* ---- reverse pass of a recorded step ------------------------------------------------------------
+ * The rollout pattern of a differentiable simulation: step forward recording each step's tape,
+ * then apply the steps' adjoints in reverse order. The tape of one step holds, per env and
+ * substep, the substep's input state, its contact and constraint-row lists, the joint-space
+ * factor L and Y = L^-1 J^T, the generalized acceleration, the solve's vectors and each row
+ * update's impulse and separation; everything else is recomputed by the adjoint. Covered: env
+ * types without tendons, ball joints and shape pairs, steps without SIM_FLAG_BODY_FORCES (other
+ * handles are refused with INVALID_ARG, or CAPACITY when an env type's adjoint arena does not fit
+ * a CTA, and differentiate through sim_step_vjp's forward mode). */
+
+/* Floats of one step's tape (caller-owned device memory: allocate this many floats per recorded
+ * step; the size depends on the handle's env types, solver iterations and substeps). Errors:
+ * HANDLE, INVALID_ARG (substeps < 1, or the handle is not covered), CAPACITY. */
+int sim_tape_size(sim_handle h, int32_t substeps, int64_t* floats);
+
+/* One step of the handle's own state, exactly as sim_step computes it (the same kernel code and
+ * arithmetic, one launch per env type whatever the handle's launch plan), that also writes the
+ * step's tape to `tape` (device, sim_tape_size floats). The tape stays valid until it is
+ * overwritten; it does not refer to the handle's views. Asynchronous. Errors: HANDLE, INVALID_ARG,
+ * CAPACITY, CUDA. */
+int sim_step_taped(sim_handle h, float* tape, float dt, int32_t substeps);
+
+typedef struct {
+  const float* grad_root_state;      /* (N_A, 13) gradient w.r.t. the step's output root state; NULL = 0 */
+  const float* grad_dof_state;       /* (N_D, 2) w.r.t. the output DOF state; NULL = 0 */
+  const float* grad_impulse_cache;   /* (n_envs, K) w.r.t. the output impulse cache; NULL = 0 */
+  float* grad_root_state_in;         /* (N_A, 13) out: gradient w.r.t. the step's input root state */
+  float* grad_dof_state_in;          /* (N_D, 2) out */
+  float* grad_dof_actuation;         /* (N_D,) out */
+  float* grad_impulse_cache_in;      /* (n_envs, K) out (zero past each env's read slots) */
+  int32_t* status;                   /* (n_envs,) out, optional: 0, or 2 if a gradient is not finite */
+} sim_adjoint_buffers;
+
+/* Vector-Jacobian product of the step recorded in `tape` by sim_step_taped (same dt and substeps):
+ * the output gradients in, the input gradients out (device memory owned by the caller, in the
+ * layouts of the views of the same names; outputs may alias nothing else). One launch per env
+ * type, one env per group of lanes, substeps in reverse order; the step's constraint and active
+ * sets are those recorded. Asynchronous. Errors: HANDLE, INVALID_ARG, CAPACITY, CUDA. */
+int sim_step_adjoint(sim_handle h, const float* tape, const sim_adjoint_buffers* b, float dt, int32_t substeps);
 
 typedef struct {
   const float* root_state;           /* (N_A, 13) state at the start of the step */

@@ -2,7 +2,9 @@
 
 The carried state is (root state, DOF state, impulse cache); the actuation is the per-step
 control. The forward value is the CUDA step kernel; the backward pass is the step's
-vector-Jacobian product (sim_step_vjp), with the step's constraint and active sets held fixed.
+vector-Jacobian product with the step's constraint and active sets held fixed: the reverse pass
+(sim_step_taped records each re-run step's tape, sim_step_adjoint applies the adjoints in reverse
+order) where it covers the handle, else sim_step_vjp in forward mode.
 
 `rollout` chains env-steps with checkpointing: each segment of `checkpoint` steps keeps only its
 input state during the forward pass and, in the backward pass, re-runs its steps (bitwise the same
@@ -66,16 +68,39 @@ class Segment(torch.autograd.Function):
             # caller that keeps stepping the handle after backward() continues from where the
             # forward pass (or its own later steps) left it
             kept = (s.root_state.clone(), s.dof_state.clone(), s.impulse_cache.clone(), s.dof_actuation.clone())
-            _, inputs = _forward_steps(s, root, dof, cache, acts, keep_inputs=True)
             g_acts = torch.zeros_like(acts)
-            g = (g_root if g_root is not None else torch.zeros_like(root),
-                 g_dof if g_dof is not None else torch.zeros_like(dof),
-                 g_cache if g_cache is not None else torch.zeros_like(cache))
-            for k in range(acts.shape[0] - 1, -1, -1):
-                r, d, c = inputs[k]
-                gr, gd, gc, ga = _vjp(s, r, d, c, acts[k], *g)
-                g_acts[k] = ga
-                g = (gr, gd, gc)
+            g = (g_root.contiguous() if g_root is not None else torch.zeros_like(root),
+                 g_dof.contiguous() if g_dof is not None else torch.zeros_like(dof),
+                 g_cache.contiguous() if g_cache is not None else torch.zeros_like(cache))
+            tf = s.tape_floats()
+            if tf is not None:
+                # reverse pass: the segment re-run with each step's tape recorded, then the steps'
+                # adjoints in reverse order (two gradient sets, used alternately)
+                tapes = torch.empty((acts.shape[0], max(tf, 1)), dtype=torch.float32, device=root.device)
+                s.root_state.copy_(root)
+                s.dof_state.copy_(dof)
+                s.impulse_cache.copy_(cache)
+                for k in range(acts.shape[0]):
+                    s.dof_actuation.copy_(acts[k])
+                    s.step_taped(tapes[k])
+                sets = [tuple(torch.empty_like(x) for x in (root, dof, cache)) for _ in range(2)]
+                ga = torch.empty_like(s.dof_actuation)
+                for k in range(acts.shape[0] - 1, -1, -1):
+                    out = sets[k % 2]
+                    s.step_adjoint(tapes[k], {"grad_root_state": g[0], "grad_dof_state": g[1],
+                                              "grad_impulse_cache": g[2], "grad_root_state_in": out[0],
+                                              "grad_dof_state_in": out[1], "grad_dof_actuation": ga,
+                                              "grad_impulse_cache_in": out[2]})
+                    g_acts[k] = ga
+                    g = out
+                g = tuple(x.clone() for x in g)
+            else:
+                _, inputs = _forward_steps(s, root, dof, cache, acts, keep_inputs=True)
+                for k in range(acts.shape[0] - 1, -1, -1):
+                    r, d, c = inputs[k]
+                    gr, gd, gc, ga = _vjp(s, r, d, c, acts[k], *g)
+                    g_acts[k] = ga
+                    g = (gr, gd, gc)
             for view, value in zip((s.root_state, s.dof_state, s.impulse_cache, s.dof_actuation), kept):
                 view.copy_(value)
         return None, g[0], g[1], g[2], g_acts

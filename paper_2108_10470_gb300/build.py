@@ -16,8 +16,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB_PATH = os.path.join(HERE, "libartsim.so")
-UNITS = ("kernels_shared.cu", "kernels_global.cu", "kernels_persistent.cu", "kernels_adjoint.cu", "sim_api.cu")
-SOURCES = [os.path.join(CSRC, f) for f in UNITS + ("step_kernel.cuh", "tangent_step.cuh", "sim_internal.h",
+UNITS = ("kernels_shared.cu", "kernels_global.cu", "kernels_persistent.cu", "kernels_adjoint.cu", "kernels_tape.cu",
+         "sim_api.cu")
+SOURCES = [os.path.join(CSRC, f) for f in UNITS + ("step_kernel.cuh", "tangent_step.cuh", "adjoint_kernel.cuh", "sim_internal.h",
                                                    "launch.h")] + \
     [os.path.join(INCLUDE, "sim.h"), os.path.abspath(__file__)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -27,7 +28,7 @@ COMPILE_FLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC"]
 # sweeps (humanoid and hand steps 4-5 % faster); the FP32 results move by far less than the
 # tolerance the parity tests derive from the FP32 conditioning of each step. The derivative
 # kernel and the host code keep IEEE division and square root.
-STEP_UNITS = ("kernels_shared.cu", "kernels_global.cu", "kernels_persistent.cu")
+STEP_UNITS = ("kernels_shared.cu", "kernels_global.cu", "kernels_persistent.cu", "kernels_tape.cu")
 STEP_FLAGS = ["-prec-div=false", "-prec-sqrt=false"]
 LINK_FLAGS = ARCH + ["-shared", "-cudart", "static"]
 

@@ -1,0 +1,925 @@
+// Reverse (adjoint) pass of the env-step for sm_103a: the vector-Jacobian product of one recorded
+// step, one environment per group of G lanes, substeps in reverse order. The forward step's
+// discrete choices (contact set, limit rows, every projection and target branch of the solve) are
+// held fixed, as in the forward-mode derivative; the step's taped instantiation records what the
+// reverse needs (TapeLayout in sim_internal.h), and everything else is recomputed.
+//
+// Formulation. The forward step computes qdd = M^-1 (tau - b) (articulated-body algorithm), a
+// Gauss-Seidel solve in z = L^T v with Y = L^-1 J^T, and integration. Its adjoint is taken in the
+// same coordinates:
+//  * integration: joints are additive; the root quaternion's adjoint is carried as the adjoint of
+//    a world-axis rotation th (q_bar = 2 [th_bar; 0] (x) q, the component along q is dropped: the
+//    step's output quaternion is normalised), through the exact exponential by the left Jacobian
+//    of SO(3);
+//  * v = L^-T z, dq = L^-T dz: z_bar = L^-1 v_bar, dz_bar = L^-1 dq_bar;
+//  * the solve: row updates in reverse order, z reconstructed from its final value by subtracting
+//    each update (z_before = z_after - Y_r dlambda), the taped impulses giving dlambda and the
+//    branches (a normal impulse at 0, a friction impulse at +-mu lambda_n, the biased target's cap);
+//  * M through its factor: with L_bar the adjoint of L, M_bar = sym(L^-T Phi(L^T L_bar) L^-1)
+//    (Phi: lower triangle, halved diagonal); L^T L_bar is formed in z coordinates,
+//    -Y_bar Y^T - z z_bar^T - dz dz_bar^T + z0 z0_bar^T, without L^-T Y_bar;
+//  * qdd: c_bar = M^-1 qdd_bar, tau_bar = c_bar, and the pose and velocity adjoints of
+//    -c_bar . (M qdd + b) come from the reverse of the recursive Newton-Euler algorithm (RBDA Table
+//    5.1) at the recorded qdd; those of M_bar . M from the reverse of the composite-rigid-body
+//    algorithm (RBDA Table 6.2);
+//  * configuration: every pose-dependent quantity (motion subspaces, spatial inertias about the
+//    actor origin, contact points) is attached to a link; its adjoint becomes a wrench on that link
+//    (a motion subspace S: S x* S_bar; a point x: [x x x_bar; x_bar]; an inertia: from its COM
+//    position and rotational inertia), and a joint's position adjoint is S . (wrenches summed over
+//    its subtree), the root rotation's the angular part over the whole actor.
+// Supported: floating and fixed roots, revolute, prismatic and fixed joints, ground contacts of
+// spheres, capsules and boxes, joint limits, damping, armature, joint drives. (Tendons, ball joints,
+// shape pairs and external body forces use the forward-mode derivative kernel.)
+#pragma once
+#include "step_kernel.cuh"
+
+namespace artsim {
+
+// Hamilton product and conjugate of quaternions stored (x, y, z, w).
+__device__ __forceinline__ void qmul4(const float* a, const float* b, float* o) {
+  o[0] = a[3] * b[0] + a[0] * b[3] + a[1] * b[2] - a[2] * b[1];
+  o[1] = a[3] * b[1] - a[0] * b[2] + a[1] * b[3] + a[2] * b[0];
+  o[2] = a[3] * b[2] + a[0] * b[1] - a[1] * b[0] + a[2] * b[3];
+  o[3] = a[3] * b[3] - a[0] * b[0] - a[1] * b[1] - a[2] * b[2];
+}
+// spatial inertia (m, h, I_O about the actor origin, I_O as xx yy zz xy xz yz) times a motion vector:
+// [I_O w + h x v; m v + w x h]
+__device__ __forceinline__ void inertia_mul(const float m, const V3 h, const float* IO, const float* x, float* o) {
+  const V3 w = v3(x[0], x[1], x[2]), vl = v3(x[3], x[4], x[5]);
+  const V3 Iw = v3(IO[0] * w.x + IO[3] * w.y + IO[4] * w.z, IO[3] * w.x + IO[1] * w.y + IO[5] * w.z,
+                   IO[4] * w.x + IO[5] * w.y + IO[2] * w.z);
+  const V3 a = Iw + cross(h, vl), l = vl * m + cross(w, h);
+  o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = l.x; o[4] = l.y; o[5] = l.z;
+}
+// motion cross product v x m = [w x m_a; w x m_l + v_l x m_a]
+__device__ __forceinline__ void crm6(const float* v, const float* m, float* o) {
+  const V3 w = v3(v[0], v[1], v[2]), vl = v3(v[3], v[4], v[5]);
+  const V3 ma = v3(m[0], m[1], m[2]), ml = v3(m[3], m[4], m[5]);
+  const V3 a = cross(w, ma), l = cross(w, ml) + cross(vl, ma);
+  o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = l.x; o[4] = l.y; o[5] = l.z;
+}
+// force cross product v x* f = [w x f_a + v_l x f_l; w x f_l]
+__device__ __forceinline__ void crf6(const float* v, const float* f, float* o) {
+  const V3 w = v3(v[0], v[1], v[2]), vl = v3(v[3], v[4], v[5]);
+  const V3 fa = v3(f[0], f[1], f[2]), fl = v3(f[3], f[4], f[5]);
+  const V3 a = cross(w, fa) + cross(vl, fl), l = cross(w, fl);
+  o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = l.x; o[4] = l.y; o[5] = l.z;
+}
+// adjoint of an inertia (I_O sym as xx yy zz xy xz yz, h) from an outer product a b^T of 6-vectors:
+// the symmetric part of the angular block, and h_bar = b_l x a_a - b_a x a_l
+__device__ __forceinline__ void inertia_outer(const float* a, const float* b, float* IOb, float* hb) {
+  IOb[0] += a[0] * b[0];
+  IOb[1] += a[1] * b[1];
+  IOb[2] += a[2] * b[2];
+  IOb[3] += 0.5f * (a[0] * b[1] + a[1] * b[0]);
+  IOb[4] += 0.5f * (a[0] * b[2] + a[2] * b[0]);
+  IOb[5] += 0.5f * (a[1] * b[2] + a[2] * b[1]);
+  const V3 aa = v3(a[0], a[1], a[2]), al = v3(a[3], a[4], a[5]);
+  const V3 ba = v3(b[0], b[1], b[2]), bl = v3(b[3], b[4], b[5]);
+  const V3 t = cross(bl, aa) - cross(ba, al);
+  hb[0] += t.x; hb[1] += t.y; hb[2] += t.z;
+}
+// 3x3 symmetric (xx yy zz xy xz yz) times vector
+__device__ __forceinline__ V3 sym_mv(const float* S, V3 x) {
+  return v3(S[0] * x.x + S[3] * x.y + S[4] * x.z, S[3] * x.x + S[1] * x.y + S[5] * x.z,
+            S[4] * x.x + S[5] * x.y + S[2] * x.z);
+}
+
+// Per-link record of the reverse arena (kAdjLinkWords words).
+enum : int {
+  kRecVs = 0, kRecCc = 6, kRecIO = 12, kRecH = 18, kRecCw = 21, kRecIcw = 24, kRecM = 30, kRecS = 31,
+  kRecIc = 37,   // composite inertia m | h 3 | I_O 6 (10 words)
+  kRecSlot = 47  // 6-word hand-off slot of the inward sweeps
+};
+// Vectors of the reverse arena (n words each, kAdjVecs of them).
+enum : int {
+  kVQdd = 0, kVFree = 1, kVZ0 = 2, kVZf = 3, kVDzf = 4, kVV = 5, kVDq = 6, kVLinv = 7,
+  kVVb = 8, kVDqb = 9, kVZb6 = 10, kVDzb6 = 11, kVZb0 = 12, kVCb = 13
+};
+
+// Group-parallel forward substitution L x = b (lane k holds b_k in, x_k out); two right-hand sides.
+template <int G>
+__device__ __forceinline__ void fwd_subst2(const float* sL, const int LS, const float* linv, const int n,
+                                           const int lane, float& b0, float& b1) {
+  float x0 = 0.f, x1 = 0.f;
+  for (int k = 0; k < n; ++k) {
+    const float li = linv[k];
+    const float y0 = Grp<G>::get(b0 * li, k), y1 = Grp<G>::get(b1 * li, k);
+    if (lane == k) { x0 = y0; x1 = y1; }
+    if (lane > k && lane < n) {
+      const float lik = sL[lane * LS + k];
+      b0 -= lik * y0;
+      b1 -= lik * y1;
+    }
+  }
+  b0 = x0;
+  b1 = x1;
+}
+// Group-parallel back substitution L^T x = b (lane k holds b_k in, x_k out).
+template <int G>
+__device__ __forceinline__ float back_subst(const float* sL, const int LS, const float* linv, const int n,
+                                            const int lane, float b) {
+  float x = 0.f;
+  for (int k = n - 1; k >= 0; --k) {
+    const float xk = Grp<G>::get(b * linv[k], k);
+    if (lane == k) x = xk;
+    if (lane < k) b -= sL[k * LS + lane] * xk;
+  }
+  return x;
+}
+
+// ---------------------------------------------------------------------------------------------
+// The reverse pass of one env (group of G lanes): sm is the group's arena (AdjLayout), gi its index
+// in the launch (the tape block), live false for the dead groups of the last CTA (they shadow the
+// last env and store nothing).
+template <int G>
+__device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs& TA, const AdjArgs& J, const int grp,
+                                              float* sm) {
+  const EnvTypeTable* __restrict__ T = TA.type;
+  const int lane = threadIdx.x & (G - 1);
+  const bool live = grp < TA.n_launch_envs;
+  const int gi = live ? grp : TA.n_launch_envs - 1;
+  const int env = TA.env_ids ? TA.env_ids[gi] : TA.env_first + gi;
+  const AdjLayout& al = J.al;
+  const TapeLayout& TL = TA.tl;
+  const int L = T->n_links, n = T->n_gen;
+  const int maxdepth = T->max_depth;
+  const int YS = al.YS, LS = al.LS, RC = TL.rcap;
+  float* s_Y = sm + al.Y;
+  float* s_Yb = sm + al.Yb;
+  float* s_L = sm + al.L;
+  float* s_Mb = sm + al.Mb;
+  float4* s_rowc = reinterpret_cast<float4*>(sm + al.rowc);
+  int* s_rowa = reinterpret_cast<int*>(sm + al.rowa);
+  float* s_lam = sm + al.lam;
+  float* s_lamb = sm + al.lamb;
+  float* s_db = sm + al.db;
+  float* s_invAb = sm + al.invAb;
+  float* s_lam0 = sm + al.lam0;
+  float* s_xb = sm + al.xb;
+  float* s_lambef = sm + al.lambef;
+  float* s_seps = sm + al.seps;
+  float* s_con = sm + al.con;
+  int* s_coni = reinterpret_cast<int*>(s_con);
+  float* s_vec = sm + al.vec;
+  float* s_SD = sm + al.SD;
+  float* s_FM = sm + al.FM;
+  float* s_FMb = sm + al.FMb;
+  float* s_Sb = sm + al.Sb;
+  float* s_link = sm + al.link;
+  auto V = [&](int k) { return s_vec + k * n; };
+  const float* s_linv = s_vec + kVLinv * n;
+
+  // ---- per-link constants (link mode) ----
+  const bool isl = lane < L;
+  const int l = isl ? lane : 0;
+  const int par = isl ? T->parent[l] : -1;
+  const int jt = T->jtype[l];
+  const int dep = isl ? T->depth[l] : -1;
+  const int gd = T->gdof[l];
+  const int jd = T->jdof[l];
+  const bool is_root = isl && par < 0;
+  const bool free_root = is_root && jt == kFree;
+  const bool has_dof = isl && (jt == kRevolute || jt == kPrismatic);
+  const bool isg = lane < n;
+  float* rec = s_link + kAdjLinkWords * l;
+  float* slot = rec + kRecSlot;
+  const int dof_base = A.env_dof_base[env];
+  const int actor_row = isl ? A.env_actor_base[env] + T->actor[l] : 0;
+  const float h = A.h;
+  const int npos = A.pos_iters, nvel = A.vel_iters;
+  const float hit = h / (float)npos;
+  const float inv_hit = 1.f / hit, inv_h = 1.f / h;
+  const float beta = A.bias_coef, vmax = A.max_depen_vel;
+  const V3 g = v3(A.gx, A.gy, A.gz);
+  float* cacheb = J.gi_cache + (size_t)env * A.cache_stride;
+
+  // inward sum of a 6-vector over each link's subtree (children in the fixed sibling order)
+  auto inward6 = [&](float* x) {
+    for (int d = maxdepth; d >= 1; --d) {
+      if (dep == d) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) slot[k] = x[k];
+      }
+      __syncwarp();
+      if (dep == d - 1)
+        for (int ch = T->first_child[l]; ch >= 0; ch = T->next_sibling[ch]) {
+          const float* sc = s_link + kAdjLinkWords * ch + kRecSlot;
+#pragma unroll
+          for (int k = 0; k < 6; ++k) x[k] += sc[k];
+        }
+      __syncwarp();
+    }
+  };
+  // outward prefix sum of a K-vector over each link's ancestors (root first)
+  auto outward = [&](float* x, const int K) {
+    for (int d = 1; d <= maxdepth; ++d) {
+      const int src = par >= 0 ? par : lane;
+      for (int k = 0; k < K; ++k) {
+        const float pv = Grp<G>::get(x[k], src);
+        if (dep == d) x[k] += pv;
+      }
+    }
+  };
+
+  // ---- carried adjoints: the output gradient of the step ----
+  float qb = 0.f, qdb = 0.f, actb = 0.f;
+  float rpb[3] = {0.f, 0.f, 0.f}, rqb[4] = {0.f, 0.f, 0.f, 0.f}, rwb[3] = {0.f, 0.f, 0.f}, rvb[3] = {0.f, 0.f, 0.f};
+  if (has_dof && J.g_dof) {
+    qb = J.g_dof[(size_t)(dof_base + jd) * 2];
+    qdb = J.g_dof[(size_t)(dof_base + jd) * 2 + 1];
+  }
+  if (is_root && J.g_root) {
+    const float* gr = J.g_root + (size_t)actor_row * 13;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) { rpb[k] = gr[k]; rvb[k] = free_root ? gr[7 + k] : 0.f; rwb[k] = free_root ? gr[10 + k] : 0.f; }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) rqb[k] = gr[3 + k];
+  }
+  if (live)
+    for (int i = lane; i < A.cache_stride; i += G) cacheb[i] = J.g_cache ? J.g_cache[(size_t)env * A.cache_stride + i] : 0.f;
+  __syncwarp();
+
+  for (int sub = A.substeps - 1; sub >= 0; --sub) {
+    const float* tp = J.tape + ((size_t)gi * A.substeps + sub) * TL.words;
+    const int* th = reinterpret_cast<const int*>(tp + TL.hdr);
+    const int n_con = th[0], n_lim = th[1], R = th[2];
+    // ---- stage the tape into the arena ----
+    for (int i = 0; i < n; ++i)
+      for (int r = lane; r < R; r += G) {
+        s_Y[i * YS + r] = tp[TL.Y + i * RC + r];
+        s_Yb[i * YS + r] = 0.f;
+      }
+    for (int i = 0; i < n; ++i)
+      for (int k = lane; k < n; k += G) s_L[i * LS + k] = (k <= i) ? tp[TL.L + i * n + k] : 0.f;
+    for (int r = lane; r < R; r += G) {
+      const float4 hc = reinterpret_cast<const float4*>(tp + TL.rowc)[r];
+      s_rowc[r] = hc;
+      s_rowa[r] = __float_as_int(tp[TL.rowa + r]);
+      s_lam[r] = tp[TL.lamf + r];
+      s_lam0[r] = tp[TL.lam0 + r];
+      s_lamb[r] = (hc.y > 0.f) ? cacheb[__float_as_int(hc.w)] : 0.f;
+      s_db[r] = 0.f;
+      s_invAb[r] = 0.f;
+    }
+    for (int it = 0; it < npos + nvel; ++it)
+      for (int r = lane; r < R; r += G) s_lambef[it * RC + r] = tp[TL.lamb + it * RC + r];
+    for (int it = 0; it <= npos; ++it)
+      for (int r = lane; r < R; r += G) s_seps[it * RC + r] = tp[TL.seps + it * RC + r];
+    for (int c = lane; c < n_con; c += G)
+#pragma unroll
+      for (int k = 0; k < 5; ++k) s_con[k * TL.ccap + c] = tp[TL.con + k * TL.ccap + c];
+    for (int i = lane; i < 7 * n; i += G) s_vec[i] = tp[TL.vec + i];
+    if (isg) s_vec[kVLinv * n + lane] = tp[TL.Linv + lane];
+    // the substep's input state
+    float q = 0.f, qd = 0.f, rq[4] = {0.f, 0.f, 0.f, 1.f};
+    V3 rp = v3(0.f, 0.f, 0.f), rw = rp, rv = rp;
+    if (has_dof) { q = tp[TL.st + 2 * l]; qd = tp[TL.st + 2 * l + 1]; }
+    if (is_root) {
+      const float* r = tp + TL.st + 2 * L + 13 * T->actor[l];
+      rp = v3(r[0], r[1], r[2]);
+      rq[0] = r[3]; rq[1] = r[4]; rq[2] = r[5]; rq[3] = r[6];
+      rv = v3(r[7], r[8], r[9]);
+      rw = v3(r[10], r[11], r[12]);
+    }
+    __syncwarp();
+
+    // ---- kinematics and inertias of the substep's input state (as in the forward step) ----
+    float S[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    {
+      float Rw[9];
+      V3 P = v3(0.f, 0.f, 0.f);
+      float vs[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, cc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      quat_to_mat(rq, Rw);
+      if (is_root) {
+        vs[0] = rw.x; vs[1] = rw.y; vs[2] = rw.z; vs[3] = rv.x; vs[4] = rv.y; vs[5] = rv.z;
+        const V3 pxw = cross(rv, rw);
+        cc[3] = pxw.x; cc[4] = pxw.y; cc[5] = pxw.z;
+      }
+      for (int d = 1; d <= maxdepth; ++d) {
+        float Rp[9], vp[6];
+        const int src = par >= 0 ? par : lane;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Rp[k] = Grp<G>::get(Rw[k], src);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) vp[k] = Grp<G>::get(vs[k], src);
+        const float ppx = Grp<G>::get(P.x, src), ppy = Grp<G>::get(P.y, src), ppz = Grp<G>::get(P.z, src);
+        if (dep == d) {
+          const V3 Pp = v3(ppx, ppy, ppz);
+          const V3 jaxis = v3(T->axis[0][l], T->axis[1][l], T->axis[2][l]);
+          float Rpj[9], RB[9];
+#pragma unroll
+          for (int k = 0; k < 9; ++k) Rpj[k] = T->prot[k][l];
+          mm(Rp, Rpj, RB);
+          const V3 pp = v3(T->ppos[0][l], T->ppos[1][l], T->ppos[2][l]);
+          const V3 aw = mv(RB, jaxis);
+          if (jt == kRevolute) {
+            float RJ[9];
+            axis_angle(jaxis, q, RJ);
+            mm(RB, RJ, Rw);
+            P = Pp + mv(Rp, pp);
+            const V3 pxa = cross(P, aw);
+            S[0] = aw.x; S[1] = aw.y; S[2] = aw.z; S[3] = pxa.x; S[4] = pxa.y; S[5] = pxa.z;
+          } else if (jt == kPrismatic) {
+#pragma unroll
+            for (int k = 0; k < 9; ++k) Rw[k] = RB[k];
+            P = Pp + mv(Rp, pp + mv(Rpj, jaxis * q));
+            S[3] = aw.x; S[4] = aw.y; S[5] = aw.z;
+          } else {
+#pragma unroll
+            for (int k = 0; k < 9; ++k) Rw[k] = RB[k];
+            P = Pp + mv(Rp, pp);
+          }
+          float sq[6];
+#pragma unroll
+          for (int k = 0; k < 6; ++k) { sq[k] = S[k] * qd; vs[k] = vp[k] + sq[k]; }
+          crm6(vs, sq, cc);
+        }
+      }
+      if (isl) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) { rec[kRecVs + k] = vs[k]; rec[kRecCc + k] = cc[k]; rec[kRecS + k] = S[k]; }
+        // rigid inertia about the actor origin: m, h = m c, I_O = R I_c R^T + m (|c|^2 1 - c c^T)
+        const float m = T->mass[l];
+        const V3 cw = P + mv(Rw, v3(T->com[0][l], T->com[1][l], T->com[2][l]));
+        const float In[9] = {T->inertia[0][l], T->inertia[3][l], T->inertia[4][l], T->inertia[3][l], T->inertia[1][l],
+                             T->inertia[5][l], T->inertia[4][l], T->inertia[5][l], T->inertia[2][l]};
+        float RI[9], Rt[9], Ic9[9];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j) Rt[3 * i + j] = Rw[3 * j + i];
+        mm(Rw, In, RI);
+        mm(RI, Rt, Ic9);
+        const float c2 = dot(cw, cw);
+        const float icw[6] = {Ic9[0], Ic9[4], Ic9[8], Ic9[1], Ic9[2], Ic9[5]};
+        const float io[6] = {icw[0] + m * (c2 - cw.x * cw.x), icw[1] + m * (c2 - cw.y * cw.y),
+                             icw[2] + m * (c2 - cw.z * cw.z), icw[3] - m * cw.x * cw.y, icw[4] - m * cw.x * cw.z,
+                             icw[5] - m * cw.y * cw.z};
+#pragma unroll
+        for (int k = 0; k < 6; ++k) { rec[kRecIcw + k] = icw[k]; rec[kRecIO + k] = io[k]; }
+        rec[kRecH] = m * cw.x; rec[kRecH + 1] = m * cw.y; rec[kRecH + 2] = m * cw.z;
+        rec[kRecCw] = cw.x; rec[kRecCw + 1] = cw.y; rec[kRecCw + 2] = cw.z;
+        rec[kRecM] = m;
+      }
+      // motion subspace per generalized DOF (unit columns for a floating root)
+      if (has_dof) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) s_SD[6 * gd + k] = S[k];
+      }
+      if (free_root) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c)
+#pragma unroll
+          for (int k = 0; k < 6; ++k) s_SD[6 * (gd + c) + k] = (k == c) ? 1.f : 0.f;
+      }
+    }
+
+    // ---- integration reverse: v_bar, dq_bar from the output adjoints ----
+    float thb[3] = {0.f, 0.f, 0.f};  // adjoint of the input root rotation (world axes)
+    if (has_dof) {
+      V(kVDqb)[gd] = qb;   // q' = q + dq (qb stays: the identity path)
+      V(kVVb)[gd] = qdb;   // qd' = v
+      qdb = 0.f;
+    }
+    if (is_root) {
+      // rotation adjoint of the output quaternion q' (its component along q' is dropped)
+      float qo[4] = {rq[0], rq[1], rq[2], rq[3]};
+      float E[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
+      V3 phi = v3(0.f, 0.f, 0.f);
+      if (free_root) {
+        phi = v3(V(kVDq)[gd], V(kVDq)[gd + 1], V(kVDq)[gd + 2]);
+        float e[4];
+        rotvec_quat(phi.x, phi.y, phi.z, e);
+        quat_to_mat(e, E);
+        float qn[4];
+        qmul4(e, rq, qn);
+        const float nr = sqrtf(qn[0] * qn[0] + qn[1] * qn[1] + qn[2] * qn[2] + qn[3] * qn[3]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) qo[k] = qn[k] / nr;
+      }
+      const float qc[4] = {-qo[0], -qo[1], -qo[2], qo[3]};
+      float t4[4];
+      qmul4(rqb, qc, t4);
+      const V3 tho = v3(0.5f * t4[0], 0.5f * t4[1], 0.5f * t4[2]);
+      // th_in = E^T th_out (q' = e (x) q: a world rotation of q is rotated by e)
+      const V3 ti = v3(E[0] * tho.x + E[3] * tho.y + E[6] * tho.z, E[1] * tho.x + E[4] * tho.y + E[7] * tho.z,
+                       E[2] * tho.x + E[5] * tho.y + E[8] * tho.z);
+      thb[0] = ti.x; thb[1] = ti.y; thb[2] = ti.z;
+      if (free_root) {
+        // dq_ang_bar = J_l(phi)^T th_out, J_l^T x = x - a phi x x + b phi x (phi x x)
+        const float a2 = dot(phi, phi);
+        float ca, cb;
+        if (a2 < 1e-8f) {
+          ca = 0.5f - a2 / 24.f;
+          cb = 1.f / 6.f - a2 / 120.f;
+        } else {
+          const float an = sqrtf(a2);
+          float sn, cs;
+          sincosf(an, &sn, &cs);
+          ca = (1.f - cs) / a2;
+          cb = (an - sn) / (a2 * an);
+        }
+        const V3 px = cross(phi, tho);
+        const V3 jt3 = tho - px * ca + cross(phi, px) * cb;
+        V(kVDqb)[gd] = jt3.x; V(kVDqb)[gd + 1] = jt3.y; V(kVDqb)[gd + 2] = jt3.z;
+        // p' = p + dq_lin (rpb stays), omega' = v_ang, p_dot' = v_lin
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          V(kVDqb)[gd + 3 + k] = rpb[k];
+          V(kVVb)[gd + k] = rwb[k];
+          V(kVVb)[gd + 3 + k] = rvb[k];
+          rwb[k] = 0.f;
+          rvb[k] = 0.f;
+        }
+      }
+    }
+    __syncwarp();
+
+    // ---- v = L^-T z, dq = L^-T dz: z_bar = L^-1 v_bar, dz_bar = L^-1 dq_bar (DOF mode) ----
+    float zb = isg ? V(kVVb)[lane] : 0.f, dzb = isg ? V(kVDqb)[lane] : 0.f;
+    fwd_subst2<G>(s_L, LS, s_linv, n, lane, zb, dzb);
+    if (isg) { V(kVZb6)[lane] = zb; V(kVDzb6)[lane] = dzb; }
+
+    // ---- the Gauss-Seidel solve in reverse (DOF mode: lane g holds z_g, z_bar_g, dz_g, dz_bar_g) ----
+    {
+      float z = isg ? V(kVZf)[lane] : 0.f, dz = isg ? V(kVDzf)[lane] : 0.f;
+      const float dzf = dz;
+      const int Rw_max = __reduce_max_sync(kFull, R);
+      for (int it = npos + nvel - 1; it >= 0; --it) {
+        const bool pos = it < npos;
+        if (pos) {  // forward: dz(it + 1) = dz(it) + h_it z after the iteration's rows
+          zb += hit * dzb;
+          dz -= hit * z;
+        }
+        const float dzs = pos ? dz : dzf;  // the dz this iteration's separations used
+        const float* sp = s_seps + (pos ? it : npos) * RC;
+        const float* lb = s_lambef + it * RC;
+        for (int r = Rw_max - 1; r >= 0; --r) {
+          const bool inr = r < R;
+          const float4 hc = inr ? s_rowc[r] : make_float4(0.f, 0.f, 0.f, 0.f);
+          const bool valid = inr && hc.y > 0.f;
+          const int kb = __float_as_int(hc.z);
+          const bool fric = (kb & 3) == kRowFriction;
+          const int nrow = valid && fric ? (kb >> 2) : 0;
+          const float la = valid ? s_lam[r] : 0.f, lbf = valid ? lb[r] : 0.f;
+          const float ln_cur = s_lam[nrow];
+          const float lbar = valid ? s_lamb[r] : 0.f;
+          const float sep = valid ? sp[r] : 0.f;
+          const float D = la - lbf;
+          const float y = (isg && inr) ? s_Y[lane * YS + r] : 0.f;
+          const float zbef = z - y * D;
+          // two group reductions in one pass: Y_r . z_bar and Y_r . z (before the update)
+          float Db = y * zb, yz = y * zbef;
+#pragma unroll
+          for (int m = G / 2; m >= 1; m >>= 1) {
+            Db += __shfl_xor_sync(kFull, Db, m, G);
+            yz += __shfl_xor_sync(kFull, yz, m, G);
+          }
+          const float invA = hc.y;
+          const float ap = lbar + Db;  // adjoint of the impulse after the update
+          float argb = 0.f, nbar = 0.f, tgt = 0.f, sepb = 0.f;
+          if (fric) {
+            const float lim = hc.x * ln_cur;
+            bool hi = la == lim, lo = la == -lim;
+            if (hi && lo) {  // lim = 0: the side of the clamp is the sign of its argument
+              const float arg = lbf - yz * invA;
+              hi = arg > 0.f;
+              lo = arg < 0.f;
+            }
+            if (hi) nbar = hc.x * ap;
+            else if (lo) nbar = -hc.x * ap;
+            else argb = ap;
+          } else {
+            argb = (la == 0.f) ? 0.f : ap;  // max(arg, 0) at 0: the clamped side
+            if (pos) {
+              if (sep >= 0.f) {
+                tgt = -sep * inv_hit;
+                sepb = -inv_hit;
+              } else {
+                const float t1 = -beta * sep * inv_hit;
+                if (t1 < vmax) { tgt = t1; sepb = -beta * inv_hit; }
+                else { tgt = vmax; sepb = 0.f; }
+              }
+            } else if (sep > 0.f) {
+              tgt = -sep * inv_h;
+              sepb = -inv_h;
+            }
+          }
+          const float yzb = -argb * invA;
+          const float invAb_add = argb * ((fric ? 0.f : tgt) - yz);
+          sepb *= argb * invA;  // d(arg)/d(sep) = invA d(tgt)/d(sep)
+          if (valid && isg) {
+            s_Yb[lane * YS + r] += D * zb + yzb * zbef + sepb * dzs;
+            zb += yzb * y;
+            dzb += sepb * y;
+          }
+          if (valid) z = zbef;
+          __syncwarp();
+          if (valid && lane == 0) {  // one lane owns the row scalars (read-modify-write)
+            s_lam[r] = lbf;
+            s_lamb[r] = argb - Db;
+            if (fric) s_lamb[nrow] += nbar;
+            s_db[r] += sepb;
+            s_invAb[r] += invAb_add;
+          }
+          __syncwarp();
+        }
+      }
+      if (isg) V(kVZb0)[lane] = zb;  // adjoint of z0 = L^T v_free (after the warm start)
+    }
+    __syncwarp();
+
+    // ---- warm start z = z0 + sum Y_r lambda0_r and A_r = |Y_r|^2 (row mode) ----
+    for (int r = lane; r < R; r += G) {
+      const float4 hc = s_rowc[r];
+      if (!(hc.y > 0.f)) { s_lamb[r] = 0.f; continue; }
+      const float l0 = s_lam0[r], ia = hc.y, ca = -2.f * s_invAb[r] * ia * ia;
+      float acc = 0.f;
+      for (int i = 0; i < n; ++i) {
+        const float yi = s_Y[i * YS + r], zbi = V(kVZb0)[i];
+        acc += yi * zbi;
+        s_Yb[i * YS + r] += l0 * zbi + ca * yi;
+      }
+      s_lamb[r] += acc;  // adjoint of the warm-start impulse: the input impulse cache
+    }
+    __syncwarp();
+
+    // ---- v_free_bar = L z0_bar; c_bar = M^-1 (h v_free_bar) (DOF mode) ----
+    float vfb = 0.f;
+    if (isg)
+      for (int j = 0; j <= lane; ++j) vfb += s_L[lane * LS + j] * V(kVZb0)[j];
+    {
+      float b = h * vfb, dummy = 0.f;
+      fwd_subst2<G>(s_L, LS, s_linv, n, lane, b, dummy);
+      const float cb = back_subst<G>(s_L, LS, s_linv, n, lane, b);
+      if (isg) V(kVCb)[lane] = cb;
+    }
+    // ---- P = Phi(L^T L_bar) = Phi(-Y_bar Y^T - z z_bar^T - dz dz_bar^T + z0 z0_bar^T) (lane = row) ----
+    if (isg) {
+      const float zf = V(kVZf)[lane], dzf = V(kVDzf)[lane], z0 = V(kVZ0)[lane];
+      for (int j = 0; j < n; ++j) {
+        float p = 0.f;
+        if (j <= lane) {
+          for (int r = 0; r < R; ++r) p -= s_Yb[lane * YS + r] * s_Y[j * YS + r];
+          p += -zf * V(kVZb6)[j] - dzf * V(kVDzb6)[j] + z0 * V(kVZb0)[j];
+          if (j == lane) p *= 0.5f;
+        }
+        s_Mb[lane * LS + j] = p;
+      }
+    }
+    __syncwarp();
+    // ---- Jacobian-row adjoints J_bar_r = L^-T Y_bar_r, in place (row mode, contact rows) ----
+    for (int r = lane; r < R; r += G) {
+      if (!(s_rowc[r].y > 0.f) || (__float_as_int(s_rowc[r].z) & 3) == kRowLimit) continue;
+      for (int k = n - 1; k >= 0; --k) {
+        float t = s_Yb[k * YS + r];
+        for (int i = k + 1; i < n; ++i) t -= s_L[i * LS + k] * s_Yb[i * YS + r];
+        s_Yb[k * YS + r] = t * s_linv[k];
+      }
+    }
+    // ---- M_bar' = L^-T P L^-1 (its symmetric part is the joint-space inertia's adjoint) ----
+    if (isg) {  // X = L^-T P, lane = column
+      const int j = lane;
+      for (int i = n - 1; i >= 0; --i) {
+        float t = s_Mb[i * LS + j];
+        for (int k = i + 1; k < n; ++k) t -= s_L[k * LS + i] * s_Mb[k * LS + j];
+        s_Mb[i * LS + j] = t * s_linv[i];
+      }
+    }
+    __syncwarp();
+    if (isg) {  // M_bar' = X L^-1, lane = row
+      const int i = lane;
+      for (int j = n - 1; j >= 0; --j) {
+        float t = s_Mb[i * LS + j];
+        for (int k = j + 1; k < n; ++k) t -= s_Mb[i * LS + k] * s_L[k * LS + j];
+        s_Mb[i * LS + j] = t * s_linv[j];
+      }
+    }
+    __syncwarp();
+
+    // ---- composite inertias (inward sweep of m, h, I_O) and F_i = Ic S_i (DOF mode) ----
+    {
+      float ic[10];
+      if (isl) {
+        ic[0] = rec[kRecM];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) ic[1 + k] = rec[kRecH + k];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) ic[4 + k] = rec[kRecIO + k];
+      }
+      for (int d = maxdepth; d >= 1; --d) {
+        if (dep == d) {
+#pragma unroll
+          for (int k = 0; k < 10; ++k) rec[kRecIc + k] = ic[k];
+        }
+        __syncwarp();
+        if (dep == d - 1)
+          for (int ch = T->first_child[l]; ch >= 0; ch = T->next_sibling[ch]) {
+            const float* sc = s_link + kAdjLinkWords * ch + kRecIc;
+#pragma unroll
+            for (int k = 0; k < 10; ++k) ic[k] += sc[k];
+          }
+        __syncwarp();
+      }
+      if (is_root) {
+#pragma unroll
+        for (int k = 0; k < 10; ++k) rec[kRecIc + k] = ic[k];
+      }
+    }
+    __syncwarp();
+    if (isg) {
+      const float* ic = s_link + kAdjLinkWords * T->dof_link[lane] + kRecIc;
+      inertia_mul(ic[0], v3(ic[1], ic[2], ic[3]), ic + 4, s_SD + 6 * lane, s_FM + 6 * lane);
+    }
+    __syncwarp();
+    // ---- reverse of the composite-rigid-body algorithm and of the contact rows (DOF mode) ----
+    if (isg) {
+      const int i = lane;
+      const unsigned anc_i = T->anc[T->dof_link[i]];
+      float Fb[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, Sb[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      for (int j = 0; j <= i; ++j) {
+        if (!((anc_i >> j) & 1u)) continue;
+        const float w = (j == i) ? s_Mb[i * LS + i] : s_Mb[i * LS + j] + s_Mb[j * LS + i];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) Fb[k] += w * s_SD[6 * j + k];
+      }
+      for (int kk = i; kk < n; ++kk) {
+        if (!((T->anc[T->dof_link[kk]] >> i) & 1u)) continue;
+        const float w = (kk == i) ? s_Mb[i * LS + i] : s_Mb[kk * LS + i] + s_Mb[i * LS + kk];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) Sb[k] += w * s_FM[6 * kk + k];
+      }
+      {
+        const float* ic = s_link + kAdjLinkWords * T->dof_link[i] + kRecIc;
+        float t[6];
+        inertia_mul(ic[0], v3(ic[1], ic[2], ic[3]), ic + 4, Fb, t);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) Sb[k] += t[k];
+      }
+      // contact rows: J_ri = S_i . [x x k; k] on the contact link's path
+      for (int r = n_lim; r < R; ++r) {
+        const float4 hc = s_rowc[r];
+        if (!(hc.y > 0.f)) continue;
+        const int a = s_rowa[r];
+        const int c = a & 0xff, dir = (a >> 8) & 3;
+        if (!((T->anc[s_coni[3 * TL.ccap + c]] >> i) & 1u)) continue;
+        const float jb = s_Yb[i * YS + r];
+        const V3 x = v3(s_con[c], s_con[TL.ccap + c], s_con[2 * TL.ccap + c]);
+        const V3 k = dir == 0 ? v3(0.f, 0.f, 1.f) : (dir == 1 ? v3(1.f, 0.f, 0.f) : v3(0.f, 1.f, 0.f));
+        const V3 xk = cross(x, k);
+        Sb[0] += jb * xk.x; Sb[1] += jb * xk.y; Sb[2] += jb * xk.z;
+        Sb[3] += jb * k.x; Sb[4] += jb * k.y; Sb[5] += jb * k.z;
+      }
+#pragma unroll
+      for (int k = 0; k < 6; ++k) { s_Sb[6 * i + k] = Sb[k]; s_FMb[6 * i + k] = Fb[k]; }
+    }
+    // contact-point adjoints per row (row mode): x_bar = sum_g J_bar_rg (k x a_g), + d_bar e_z
+    for (int r = n_lim + lane; r < R; r += G) {
+      const float4 hc = s_rowc[r];
+      V3 xb = v3(0.f, 0.f, 0.f);
+      if (hc.y > 0.f) {
+        const int a = s_rowa[r];
+        const int c = a & 0xff, dir = (a >> 8) & 3;
+        const unsigned anc = T->anc[s_coni[3 * TL.ccap + c]];
+        const V3 k = dir == 0 ? v3(0.f, 0.f, 1.f) : (dir == 1 ? v3(1.f, 0.f, 0.f) : v3(0.f, 1.f, 0.f));
+        V3 sa = v3(0.f, 0.f, 0.f);
+        for (int gg = 0; gg < n; ++gg)
+          if ((anc >> gg) & 1u) sa = sa + v3(s_SD[6 * gg], s_SD[6 * gg + 1], s_SD[6 * gg + 2]) * s_Yb[gg * YS + r];
+        xb = cross(k, sa);
+        if (dir == 0) xb.z += s_db[r];
+      }
+      s_xb[3 * r] = xb.x; s_xb[3 * r + 1] = xb.y; s_xb[3 * r + 2] = xb.z;
+    }
+    __syncwarp();
+
+    // ---- link mode: gathers of the DOF- and row-level adjoints ----
+    float IOb[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, hbar[3] = {0.f, 0.f, 0.f};  // composite inertia adjoint
+    float wr[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // pose wrench of the link's attached quantities
+    if (isl) {
+      for (int gg = 0; gg < n; ++gg)
+        if (T->dof_link[gg] == l) inertia_outer(s_FMb + 6 * gg, s_SD + 6 * gg, IOb, hbar);
+      for (int c = 0; c < n_con; ++c) {
+        if (s_coni[3 * TL.ccap + c] != l) continue;
+        const int rn = n_lim + c, rf = n_lim + n_con + 2 * c;
+        const V3 xb = v3(s_xb[3 * rn] + s_xb[3 * rf] + s_xb[3 * rf + 3], s_xb[3 * rn + 1] + s_xb[3 * rf + 1] + s_xb[3 * rf + 4],
+                         s_xb[3 * rn + 2] + s_xb[3 * rf + 2] + s_xb[3 * rf + 5]);
+        const int sh = s_coni[4 * TL.ccap + c];
+        const float rad = (T->shape_type[sh] == kBox) ? 0.f : T->shape_size[0][sh];
+        // the body-fixed point: the contact point lies one radius straight below it
+        const V3 xf = v3(s_con[c], s_con[TL.ccap + c], s_con[2 * TL.ccap + c] + rad);
+        const V3 m = cross(xf, xb);
+        wr[0] += m.x; wr[1] += m.y; wr[2] += m.z; wr[3] += xb.x; wr[4] += xb.y; wr[5] += xb.z;
+      }
+      if (has_dof)
+        for (int r = 0; r < n_lim; ++r) {
+          const int a = s_rowa[r];
+          if ((a & 0xff) == gd && s_rowc[r].y > 0.f) qb += ((a >> 8) & 1) ? -s_db[r] : s_db[r];
+        }
+      if (is_root)
+        for (int c = 0; c < n_con; ++c)
+          if (T->actor[s_coni[3 * TL.ccap + c]] == T->actor[l]) rpb[2] += s_db[n_lim + c];
+    }
+    {  // composite-inertia adjoints reach every link of the subtree: outward prefix over ancestors
+      float t9[9] = {IOb[0], IOb[1], IOb[2], IOb[3], IOb[4], IOb[5], hbar[0], hbar[1], hbar[2]};
+      outward(t9, 9);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) IOb[k] = t9[k];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) hbar[k] = t9[6 + k];
+    }
+
+    // ---- reverse of the recursive Newton-Euler algorithm at the recorded qdd, seeded -c_bar ----
+    float Sbar[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (has_dof) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) Sbar[k] = s_Sb[6 * gd + k];
+    }
+    float vs[6], cc[6], io[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) { vs[k] = rec[kRecVs + k]; cc[k] = rec[kRecCc + k]; io[k] = rec[kRecIO + k]; }
+    const float m_l = isl ? rec[kRecM] : 0.f;
+    const V3 h_l = isl ? v3(rec[kRecH], rec[kRecH + 1], rec[kRecH + 2]) : v3(0.f, 0.f, 0.f);
+    const float qdd_l = has_dof ? V(kVQdd)[gd] : 0.f;
+    float acc[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) acc[k] = isl ? cc[k] + S[k] * qdd_l : 0.f;
+    if (free_root) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) acc[k] += V(kVQdd)[gd + k];
+    }
+    outward(acc, 6);
+    float ag[6] = {acc[0], acc[1], acc[2], acc[3] - g.x, acc[4] - g.y, acc[5] - g.z};
+    float u[6], Fc[6];
+    inertia_mul(m_l, h_l, io, vs, u);
+    {
+      float ia[6], vu[6];
+      inertia_mul(m_l, h_l, io, ag, ia);
+      crf6(vs, u, vu);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) Fc[k] = isl ? ia[k] + vu[k] : 0.f;
+    }
+    inward6(Fc);
+    float fb[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (has_dof) {
+      const float cb = V(kVCb)[gd];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) { fb[k] = -cb * S[k]; Sbar[k] -= cb * Fc[k]; }
+    }
+    if (free_root) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) fb[k] = -V(kVCb)[gd + k];
+    }
+    outward(fb, 6);
+    float accb[6], vsb[6];
+    {
+      float ub[6], t[6];
+      crm6(vs, fb, ub);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) ub[k] = -ub[k];
+      inertia_outer(fb, ag, IOb, hbar);
+      inertia_outer(ub, vs, IOb, hbar);
+      inertia_mul(m_l, h_l, io, fb, accb);
+      inertia_mul(m_l, h_l, io, ub, t);
+      const V3 ua = v3(u[0], u[1], u[2]), ul = v3(u[3], u[4], u[5]);
+      const V3 fa = v3(fb[0], fb[1], fb[2]), fl = v3(fb[3], fb[4], fb[5]);
+      const V3 b0 = cross(ua, fa) + cross(ul, fl), b1 = cross(ul, fa);
+      vsb[0] = b0.x + t[0]; vsb[1] = b0.y + t[1]; vsb[2] = b0.z + t[2];
+      vsb[3] = b1.x + t[3]; vsb[4] = b1.y + t[4]; vsb[5] = b1.z + t[5];
+      if (!isl) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) { accb[k] = 0.f; vsb[k] = 0.f; }
+      }
+    }
+    inward6(accb);  // acc_bar summed over the subtree: the adjoint of c and of S qdd
+    if (has_dof) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) Sbar[k] += accb[k] * qdd_l;
+      // c = v x (S qd): v_bar += (S qd) x* c_bar, (S qd)_bar = -v x* c_bar
+      float sq[6], t[6], sqb[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) sq[k] = S[k] * qd;
+      crf6(sq, accb, t);
+      crf6(vs, accb, sqb);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) { vsb[k] += t[k]; Sbar[k] -= sqb[k] * qd; qdb -= S[k] * sqb[k]; }
+    }
+    if (free_root) {  // c_root = [0; p_dot x omega]
+      const V3 cb = v3(accb[3], accb[4], accb[5]);
+      const V3 a = cross(rw, cb), b = cross(cb, rv);
+      rvb[0] += a.x; rvb[1] += a.y; rvb[2] += a.z;
+      rwb[0] += b.x; rwb[1] += b.y; rwb[2] += b.z;
+    }
+    inward6(vsb);  // v = v_parent + S qd
+    if (has_dof) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) { Sbar[k] += vsb[k] * qd; qdb += S[k] * vsb[k]; }
+    }
+    if (free_root) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) { rwb[k] += vsb[k]; rvb[k] += vsb[3 + k]; }
+    }
+
+    // ---- configuration: wrenches of S, the inertia and the contact points, summed over subtrees ----
+    if (isl) {
+      if (has_dof) {
+        float t[6];
+        crf6(S, Sbar, t);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) wr[k] += t[k];
+      }
+      const V3 cw = v3(rec[kRecCw], rec[kRecCw + 1], rec[kRecCw + 2]);
+      const float* icw = rec + kRecIcw;
+      const float tr = IOb[0] + IOb[1] + IOb[2];
+      const V3 gc = (cw * (2.f * tr) - sym_mv(IOb, cw) * 2.f) * m_l + v3(hbar[0], hbar[1], hbar[2]) * m_l;
+      // B = IOb Icw; vee(B - B^T) = 2 (B21 - B12, B02 - B20, B10 - B01)
+      const float B01 = IOb[0] * icw[3] + IOb[3] * icw[1] + IOb[4] * icw[5];
+      const float B02 = IOb[0] * icw[4] + IOb[3] * icw[5] + IOb[4] * icw[2];
+      const float B10 = IOb[3] * icw[0] + IOb[1] * icw[3] + IOb[5] * icw[4];
+      const float B12 = IOb[3] * icw[4] + IOb[1] * icw[5] + IOb[5] * icw[2];
+      const float B20 = IOb[4] * icw[0] + IOb[5] * icw[3] + IOb[2] * icw[4];
+      const float B21 = IOb[4] * icw[3] + IOb[5] * icw[1] + IOb[2] * icw[5];
+      const V3 nrot = v3(2.f * (B21 - B12), 2.f * (B02 - B20), 2.f * (B10 - B01)) + cross(cw, gc);
+      wr[0] += nrot.x; wr[1] += nrot.y; wr[2] += nrot.z; wr[3] += gc.x; wr[4] += gc.y; wr[5] += gc.z;
+    }
+    inward6(wr);
+    if (has_dof) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) qb += S[k] * wr[k];
+    }
+    if (is_root) { thb[0] += wr[0]; thb[1] += wr[1]; thb[2] += wr[2]; }
+
+    // ---- joint forces (actuation, damping, drives) and v_free = nu + h qdd ----
+    if (isg) V(kVVb)[lane] = vfb;
+    __syncwarp();
+    if (has_dof) {
+      const float cb = V(kVCb)[gd];
+      actb += cb;
+      float dq_damp = T->damping[l];
+      if (T->has_drives) {
+        const float kp = T->drive_kp[l], kd = T->drive_kd[l];
+        dq_damp += kd + h * kp;
+        qb -= kp * cb;
+      }
+      qdb -= dq_damp * cb;
+      qdb += V(kVVb)[gd];
+    }
+    if (free_root) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) { rwb[k] += V(kVVb)[gd + k]; rvb[k] += V(kVVb)[gd + 3 + k]; }
+    }
+    // ---- input impulse cache adjoint: the warm-start impulses' adjoints at their slots ----
+    if (live)
+      for (int i = lane; i < A.cache_stride; i += G) cacheb[i] = 0.f;
+    __syncwarp();
+    if (live)
+      for (int r = lane; r < R; r += G)
+        if (s_rowc[r].y > 0.f) cacheb[__float_as_int(s_rowc[r].w)] = s_lamb[r];
+    __syncwarp();
+    // ---- the input quaternion's adjoint from the rotation adjoint: q_bar = 2 [th_bar; 0] (x) q ----
+    if (is_root) {
+      const float t4[4] = {thb[0], thb[1], thb[2], 0.f};
+      float o4[4];
+      qmul4(t4, rq, o4);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) rqb[k] = 2.f * o4[k];
+    }
+    __syncwarp();
+  }  // substeps
+
+  // ---- outputs ----
+  int status = 0;
+  if (has_dof && !(isfinite(qb) && isfinite(qdb) && isfinite(actb))) status = 2;
+  if (is_root && !(isfinite(rpb[0] + rpb[1] + rpb[2]) && isfinite(rqb[0] + rqb[1] + rqb[2] + rqb[3]) &&
+                   isfinite(rwb[0] + rwb[1] + rwb[2]) && isfinite(rvb[0] + rvb[1] + rvb[2])))
+    status = 2;
+  status = Grp<G>::any(status);
+  if (live) {
+    if (has_dof) {
+      J.gi_dof[(size_t)(dof_base + jd) * 2] = qb;
+      J.gi_dof[(size_t)(dof_base + jd) * 2 + 1] = qdb;
+      J.gi_act[dof_base + jd] = actb;
+    }
+    if (is_root) {
+      float* o = J.gi_root + (size_t)actor_row * 13;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) { o[k] = rpb[k]; o[7 + k] = free_root ? rvb[k] : 0.f; o[10 + k] = free_root ? rwb[k] : 0.f; }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) o[3 + k] = rqb[k];
+    }
+    if (lane == 0 && J.status) J.status[env] = status;
+  }
+}
+
+// One launch per env type: blocks of blockDim / G groups, one env per group.
+template <int G>
+__global__ void __launch_bounds__(64) adjoint_kernel(const __grid_constant__ StepArgs A,
+                                                    const __grid_constant__ TypeArgs TA,
+                                                    const __grid_constant__ AdjArgs J) {
+  extern __shared__ __align__(16) float smem[];
+  const int grp_blk = threadIdx.x / G;
+  const int grp = blockIdx.x * (blockDim.x / G) + grp_blk;
+  adjoint_group<G>(A, TA, J, grp, smem + grp_blk * J.al.total);
+}
+
+}  // namespace artsim

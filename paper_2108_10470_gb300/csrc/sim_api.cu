@@ -87,6 +87,12 @@ struct sim_s {
   cudaGraphExec_t graph_exec = nullptr;
   float graph_dt = 0.f;
   int graph_substeps = 0;
+  // sim_step_vjp by the reverse pass: a copy of the step's input state stepped by the taped step,
+  // and the tape (allocated on first use)
+  float* rv_state = nullptr;
+  size_t rv_state_floats = 0;
+  float* rv_tape = nullptr;
+  size_t rv_tape_floats = 0;
 };
 
 namespace {
@@ -685,6 +691,8 @@ void free_all(sim_s* h) {
     if (tp.scratch) cudaFree(tp.scratch);
     if (tp.pscratch) cudaFree(tp.pscratch);
   }
+  if (h->rv_state) cudaFree(h->rv_state);
+  if (h->rv_tape) cudaFree(h->rv_tape);
   drop_graph(h);
   if (h->d_counter) cudaFree(h->d_counter);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -1071,12 +1079,234 @@ int sim_step_host(sim_handle h, const float* host_actuation, float* host_root_ou
   return SIM_OK;
 }
 
+// ---- reverse pass ---------------------------------------------------------------------------------
+namespace {
+
+int al4i(int x) { return (x + 3) & ~3; }
+
+// Tape of one env-substep of type tp (offsets in words; see TapeLayout).
+TapeLayout tape_layout(const TypePlan& tp, int npos, int nvel) {
+  const EnvTypeTable& T = tp.tab;
+  TapeLayout t{};
+  t.n = std::max(T.n_gen, 1);
+  t.rcap = tp.lay.rcap;
+  t.ccap = tp.lay.ccap;
+  t.npos = npos;
+  t.iters = npos + nvel;
+  const int n = t.n;
+  int o = 0;
+  t.hdr = o; o += 4;
+  t.st = o; o += 2 * T.n_links + 13 * T.n_actors;
+  o = al4i(o);
+  t.vec = o; o += 7 * n;
+  t.L = o; o += n * n;
+  t.Linv = o; o += n;
+  t.con = o; o += 5 * t.ccap;
+  o = al4i(o);
+  t.rowc = o; o += 4 * t.rcap;
+  t.rowa = o; o += t.rcap;
+  t.lam0 = o; o += t.rcap;
+  t.lamf = o; o += t.rcap;
+  t.Y = o; o += n * t.rcap;
+  t.lamb = o; o += t.iters * t.rcap;
+  t.seps = o; o += (npos + 1) * t.rcap;
+  t.words = al4i(o);
+  return t;
+}
+
+// Arena of one env in the adjoint kernel (offsets in words; see AdjLayout).
+AdjLayout adj_layout(const TypePlan& tp, int npos, int nvel) {
+  const EnvTypeTable& T = tp.tab;
+  AdjLayout a{};
+  const int n = std::max(T.n_gen, 1), rc = tp.lay.rcap, cc = tp.lay.ccap, it = npos + nvel;
+  a.YS = rc | 1;
+  a.LS = n | 1;
+  int o = 0;
+  a.Y = o; o += n * a.YS;
+  a.Yb = o; o += n * a.YS;
+  a.L = o; o += n * a.LS;
+  a.Mb = o; o += n * a.LS;
+  o = al4i(o);
+  a.rowc = o; o += 4 * rc;
+  a.rowa = o; o += rc;
+  a.lam = o; o += rc;
+  a.lamb = o; o += rc;
+  a.db = o; o += rc;
+  a.invAb = o; o += rc;
+  a.lam0 = o; o += rc;
+  a.xb = o; o += 3 * rc;
+  a.lambef = o; o += it * rc;
+  a.seps = o; o += (npos + 1) * rc;
+  a.con = o; o += 5 * cc;
+  a.vec = o; o += kAdjVecs * n;
+  a.SD = o; o += 6 * n;
+  a.FM = o; o += 6 * n;
+  a.FMb = o; o += 6 * n;
+  a.Sb = o; o += 6 * n;
+  a.link = o; o += kAdjLinkWords * T.n_links;
+  a.total = al4i(o);
+  return a;
+}
+
+constexpr int kAdjThreads = 64;
+
+// The reverse pass covers env types without tendons, ball joints and shape pairs, in steps
+// without external body forces, whose adjoint arena fits a CTA.
+int reverse_supported(const sim_s* h) {
+  if (h->params.flags & SIM_FLAG_BODY_FORCES) {
+    g_last_error = "reverse pass: steps with external body forces use the forward-mode derivative";
+    return SIM_ERR_INVALID_ARG;
+  }
+  for (const TypePlan& tp : h->types) {
+    if (tp.tab.n_tendons > 0 || tp.tab.has_ball || tp.tab.n_pairs > 0) {
+      g_last_error = "reverse pass: env types with tendons, ball joints or shape pairs use the forward-mode derivative";
+      return SIM_ERR_INVALID_ARG;
+    }
+    const AdjLayout al = adj_layout(tp, h->params.pos_iters, h->params.vel_iters);
+    if ((size_t)(kAdjThreads / tp.G) * al.total * sizeof(float) > kMaxSmemPerCta) {
+      g_last_error = "reverse pass: the env type's adjoint arena exceeds a CTA's shared memory";
+      return SIM_ERR_CAPACITY;
+    }
+  }
+  return SIM_OK;
+}
+
+// Floats of one step's tape over all env types, and each type's offset.
+int64_t tape_floats(const sim_s* h, int substeps, std::vector<int64_t>* offs) {
+  int64_t total = 0;
+  for (const TypePlan& tp : h->types) {
+    if (offs) offs->push_back(total);
+    total += (int64_t)tp.envs.size() * substeps * tape_layout(tp, h->params.pos_iters, h->params.vel_iters).words;
+  }
+  return total;
+}
+
+// One taped step: the state buffers of `a` advance exactly as sim_step advances them (same kernel
+// code and arithmetic), and each env-substep's tape is written to `tape`.
+int launch_taped(sim_s* h, StepArgs a, float* tape, cudaStream_t st) {
+  std::vector<int64_t> offs;
+  tape_floats(h, a.substeps, &offs);
+  for (size_t t = 0; t < h->types.size(); ++t) {
+    TypePlan& tp = h->types[t];
+    if (tp.lay.grows && !tp.scratch) {  // a persistent handle steps without per-type scratch
+      const size_t gpb = (size_t)tp.groups_per_block;
+      const int rc = grow_buffer(&tp.scratch, &tp.scratch_floats,
+                                 (tp.envs.size() + gpb - 1) / gpb * gpb * (size_t)tp.lay.scratch_words,
+                                 "cudaMalloc (global rows scratch)");
+      if (rc != SIM_OK) return rc;
+    }
+    TypeArgs ta;
+    fill_type(h, t, ta);
+    ta.tape = tape + offs[t];
+    ta.tl = tape_layout(tp, a.pos_iters, a.vel_iters);
+    CK(set_taped_step_kernel_smem_cap(tp.G, tp.lay.grows != 0, kMaxSmemPerCta));
+    const cudaError_t e = launch_taped_step_kernel(tp.G, tp.lay.grows != 0, a, ta, tp.groups_per_block,
+                                                   tp.smem_bytes, st);
+    if (e != cudaSuccess) return cuda_fail(e, "taped step_kernel launch");
+  }
+  return SIM_OK;
+}
+
+// The adjoint of a taped step: one launch per env type.
+int launch_adjoint(sim_s* h, const StepArgs& a, const float* tape, AdjArgs j, cudaStream_t st) {
+  std::vector<int64_t> offs;
+  tape_floats(h, a.substeps, &offs);
+  for (size_t t = 0; t < h->types.size(); ++t) {
+    const TypePlan& tp = h->types[t];
+    TypeArgs ta;
+    fill_type(h, t, ta);
+    ta.tl = tape_layout(tp, a.pos_iters, a.vel_iters);
+    j.tape = tape + offs[t];
+    j.al = adj_layout(tp, a.pos_iters, a.vel_iters);
+    CK(set_adjoint_kernel_smem_cap(tp.G, kMaxSmemPerCta));
+    const cudaError_t e = launch_adjoint_kernel(tp.G, a, ta, j, st);
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint_kernel launch");
+  }
+  return SIM_OK;
+}
+
+}  // namespace
+
+int sim_tape_size(sim_handle h, int32_t substeps, int64_t* floats) {
+  if (!valid_handle(h)) return SIM_ERR_HANDLE;
+  if (!floats || substeps < 1) return SIM_ERR_INVALID_ARG;
+  const int rc = reverse_supported(h);
+  if (rc != SIM_OK) return rc;
+  *floats = tape_floats(h, substeps, nullptr);
+  return SIM_OK;
+}
+
+int sim_step_taped(sim_handle h, float* tape, float dt, int32_t substeps) {
+  if (!valid_handle(h)) return SIM_ERR_HANDLE;
+  if (!tape || !(dt > 0.f) || !finite(dt) || substeps < 1) return SIM_ERR_INVALID_ARG;
+  const int rc = reverse_supported(h);
+  if (rc != SIM_OK) return rc;
+  StepArgs a;
+  fill_common(h, dt, substeps, a);
+  return launch_taped(h, a, tape, h->stream);
+}
+
+int sim_step_adjoint(sim_handle h, const float* tape, const sim_adjoint_buffers* b, float dt, int32_t substeps) {
+  if (!valid_handle(h)) return SIM_ERR_HANDLE;
+  if (!tape || !b || !b->grad_root_state_in || !b->grad_dof_state_in || !b->grad_dof_actuation ||
+      !b->grad_impulse_cache_in)
+    return SIM_ERR_INVALID_ARG;
+  if (!(dt > 0.f) || !finite(dt) || substeps < 1) return SIM_ERR_INVALID_ARG;
+  const int rc = reverse_supported(h);
+  if (rc != SIM_OK) return rc;
+  StepArgs a;
+  fill_common(h, dt, substeps, a);
+  AdjArgs j{};
+  j.g_root = b->grad_root_state; j.g_dof = b->grad_dof_state; j.g_cache = b->grad_impulse_cache;
+  j.gi_root = b->grad_root_state_in; j.gi_dof = b->grad_dof_state_in; j.gi_act = b->grad_dof_actuation;
+  j.gi_cache = b->grad_impulse_cache_in;
+  j.status = b->status;
+  return launch_adjoint(h, a, tape, j, h->stream);
+}
+
 int sim_step_vjp(sim_handle h, const sim_vjp_buffers* b, float dt, int32_t substeps) {
   if (!valid_handle(h)) return SIM_ERR_HANDLE;
   if (!b || !b->root_state || !b->dof_state || !b->dof_actuation || !b->impulse_cache || !b->grad_root_state_in ||
       !b->grad_dof_state_in || !b->grad_dof_actuation || !b->grad_impulse_cache_in)
     return SIM_ERR_INVALID_ARG;
   if (!(dt > 0.f) || !finite(dt) || substeps < 1) return SIM_ERR_INVALID_ARG;
+  if (!(h->params.flags & SIM_FLAG_TANGENT_VJP) && reverse_supported(h) == SIM_OK) {
+    // the reverse pass: the taped step on a copy of the input state, then its adjoint
+    g_last_error.clear();
+    const size_t nr = 13 * (size_t)h->N_A, nd = 2 * (size_t)h->N_D, nc = (size_t)h->n_envs * h->cache_stride;
+    const size_t nn = 3 * (size_t)h->N_B, np = (size_t)h->n_envs * h->pair_stride * 3, ne = (size_t)h->n_envs;
+    int rc = grow_buffer(&h->rv_state, &h->rv_state_floats, nr + nd + nc + nn + np + 3 * ne + 4,
+                         "cudaMalloc (reverse-pass state)");
+    if (rc != SIM_OK) return rc;
+    const int64_t tf = tape_floats(h, substeps, nullptr);
+    rc = grow_buffer(&h->rv_tape, &h->rv_tape_floats, (size_t)std::max<int64_t>(tf, 4), "cudaMalloc (reverse-pass tape)");
+    if (rc != SIM_OK) return rc;
+    float* st_root = h->rv_state;
+    float* st_dof = st_root + nr;
+    float* st_cache = st_dof + nd;
+    float* st_net = st_cache + nc;
+    int* st_pairs = reinterpret_cast<int*>(st_net + nn);
+    int* st_np = st_pairs + np;
+    unsigned* st_sig = reinterpret_cast<unsigned*>(st_np + ne);
+    int* st_status = reinterpret_cast<int*>(st_sig + ne);
+    CK(cudaMemcpyAsync(st_root, b->root_state, sizeof(float) * nr, cudaMemcpyDeviceToDevice, h->stream));
+    if (nd) CK(cudaMemcpyAsync(st_dof, b->dof_state, sizeof(float) * nd, cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaMemcpyAsync(st_cache, b->impulse_cache, sizeof(float) * nc, cudaMemcpyDeviceToDevice, h->stream));
+    StepArgs a;
+    fill_common(h, dt, substeps, a);
+    a.root = st_root; a.dof = st_dof; a.act = b->dof_actuation; a.cache = st_cache; a.net_force = st_net;
+    a.pairs = st_pairs; a.n_pairs = st_np; a.sig = st_sig; a.status = st_status;
+    a.flags &= ~(SIM_FLAG_RIGID_BODY_STATE | SIM_FLAG_DOF_FORCE);  // no writes to the handle's views
+    a.dof_force = nullptr; a.body_state = nullptr;
+    rc = launch_taped(h, a, h->rv_tape, h->stream);
+    if (rc != SIM_OK) return rc;
+    AdjArgs j{};
+    j.g_root = b->grad_root_state; j.g_dof = b->grad_dof_state; j.g_cache = b->grad_impulse_cache;
+    j.gi_root = b->grad_root_state_in; j.gi_dof = b->grad_dof_state_in; j.gi_act = b->grad_dof_actuation;
+    j.gi_cache = b->grad_impulse_cache_in;
+    j.status = b->status;
+    return launch_adjoint(h, a, h->rv_tape, j, h->stream);
+  }
   int rc = tangent_supported(h);
   if (rc != SIM_OK) return rc;
   StepArgs a;

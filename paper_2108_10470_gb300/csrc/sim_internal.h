@@ -138,6 +138,30 @@ struct StepArgs {
   int flags;
 };
 
+// Tape of one env-substep, written by the taped instantiation of the step kernel for the reverse
+// pass (offsets in 4-byte words within the env's block of `words` per substep). What the reverse
+// cannot cheaply recompute: the substep's input state, the contact and row lists, the joint-space
+// factor L, Y = L^-1 J^T, the generalized acceleration and the solve's vectors, and every row
+// update's impulse before it and separation used.
+struct TapeLayout {
+  int words;  // per env and substep (multiple of 4)
+  int hdr;    // 4: n_con | n_lim | R | 0 (int bits)
+  int st;     // 2 per link (q, qd), then 13 per actor root (p 3 | quat 4 | v 3 | w 3)
+  int vec;    // 7 x n: qdd | v_free | z0 = L^T v_free | z final | dz final | v | dq
+  int L;      // n x n, row-major, lower triangle
+  int Linv;   // n: 1 / L_kk
+  int con;    // 5 x ccap (SoA): x y z (relative to the actor origin) | link | shape
+  int rowc;   // 4 x rcap: the row headers (16-byte aligned)
+  int rowa;   // rcap
+  int lam0;   // rcap: warm-start impulses
+  int lamf;   // rcap: final impulses
+  int Y;      // n x rcap: Y = L^-1 J^T, column r = row r
+  int lamb;   // (npos + nvel) x rcap: impulse of row r before its update in iteration it
+  int seps;   // (npos + 1) x rcap: separation d_r + Y_r . dz used in iteration it (the last for
+              // every velocity iteration)
+  int rcap, ccap, n, npos, iters;
+};
+
 // Arguments of one env type (read once per group, at the start of its step).
 struct TypeArgs {
   const EnvTypeTable* type;
@@ -146,6 +170,39 @@ struct TypeArgs {
   int n_launch_envs;
   float* scratch;            // global rows: one slot per group (see the launch wrappers)
   SmemLayout lay;
+  float* tape;               // taped instantiation only: the type's tape, env-major then substep
+  TapeLayout tl;
+};
+
+// Shared-memory arena of one env in the reverse (adjoint) kernel, offsets in words.
+struct AdjLayout {
+  int Y, Yb, YS;    // n x YS each (YS odd): Y, then its adjoint (the Jacobian-row adjoint later)
+  int L, Mb, LS;    // n x LS each (LS odd): the factor L; P, then L^-T P, then the inertia adjoint
+  int rowc;         // float4 x rcap (16-byte aligned)
+  int rowa, lam, lamb, db, invAb, lam0;  // rcap each
+  int xb;           // 3 x rcap: adjoint of each row's contact point
+  int lambef, seps; // iters x rcap, (npos + 1) x rcap
+  int con;          // 5 x ccap
+  int vec;          // kAdjVecs x n (see adjoint_kernel.cuh)
+  int SD, FM, FMb, Sb;  // 6 x n each: motion subspace, composite-inertia force, its adjoint, S adjoint
+  int link;         // kAdjLinkWords x L
+  int total;        // words per env (multiple of 4)
+};
+constexpr int kAdjVecs = 14;
+constexpr int kAdjLinkWords = 56;
+
+// Arguments of the reverse pass of one recorded step.
+struct AdjArgs {
+  const float* tape;         // the type's tape (as written by the taped step)
+  const float* g_root;       // (N_A, 13) gradient w.r.t. the step's output root state, or null
+  const float* g_dof;        // (N_D, 2) or null
+  const float* g_cache;      // (n_envs, cache_stride) or null
+  float* gi_root;            // (N_A, 13) out
+  float* gi_dof;             // (N_D, 2) out
+  float* gi_act;             // (N_D,) out
+  float* gi_cache;           // (n_envs, cache_stride) out (also the working storage between substeps)
+  int* status;               // (n_envs,) out or null
+  AdjLayout al;
 };
 
 // Persistent heterogeneous launch: one StepArgs per env type plus the tile schedule.

@@ -26,6 +26,7 @@ SIM_FLAG_BODY_FORCES = 8
 SIM_FLAG_RIGID_BODY_STATE = 16
 SIM_FLAG_DOF_FORCE = 32
 SIM_FLAG_ROW_SOLVER = 64
+SIM_FLAG_TANGENT_VJP = 128
 (SIM_VIEW_ROOT_STATE, SIM_VIEW_DOF_STATE, SIM_VIEW_DOF_ACTUATION, SIM_VIEW_NET_CONTACT_FORCE,
  SIM_VIEW_CONTACT_PAIRS, SIM_VIEW_CONTACT_COUNT, SIM_VIEW_SIGNATURE, SIM_VIEW_STATUS,
  SIM_VIEW_IMPULSE_CACHE, SIM_VIEW_DOF_POSITION_TARGET, SIM_VIEW_DOF_VELOCITY_TARGET, SIM_VIEW_DOF_FORCE,
@@ -34,7 +35,8 @@ EXPORTED = ("sim_create", "sim_step", "sim_step_host", "sim_get_view", "sim_set_
             "sim_set_dof_state_indexed", "sim_set_stream", "sim_sync_status", "sim_get_sizes", "sim_destroy",
             "sim_error_string", "sim_last_error_message", "sim_probe_fp32_peak", "sim_step_static_scratch",
             "sim_get_type_config", "sim_set_type_config", "sim_autotune", "sim_step_vjp", "sim_step_jvp",
-            "sim_get_max_dims", "sim_compute_mass_matrix", "sim_compute_jacobian")
+            "sim_get_max_dims", "sim_compute_mass_matrix", "sim_compute_jacobian", "sim_tape_size",
+            "sim_step_taped", "sim_step_adjoint")
 
 F = ctypes.POINTER(ctypes.c_float)
 
@@ -103,6 +105,14 @@ class sim_jvp_buffers(ctypes.Structure):
     _fields_ = [(f, ctypes.c_void_p) for f in JVP_FIELDS]
 
 
+ADJ_FIELDS = ("grad_root_state", "grad_dof_state", "grad_impulse_cache", "grad_root_state_in", "grad_dof_state_in",
+              "grad_dof_actuation", "grad_impulse_cache_in", "status")
+
+
+class sim_adjoint_buffers(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_void_p) for f in ADJ_FIELDS]
+
+
 def load(path: Optional[str] = None) -> ctypes.CDLL:
     """Load libartsim.so (raises if it has not been built: there is no fallback path)."""
     global _lib
@@ -140,6 +150,10 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     L.sim_get_max_dims.argtypes = [ctypes.c_void_p, I32, I32]
     L.sim_compute_mass_matrix.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
     L.sim_compute_jacobian.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    L.sim_tape_size.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)]
+    L.sim_step_taped.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float, ctypes.c_int32]
+    L.sim_step_adjoint.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(sim_adjoint_buffers),
+                                   ctypes.c_float, ctypes.c_int32]
     _lib = L  # every other entry point returns int, ctypes' default restype
     return L
 
@@ -387,6 +401,39 @@ class Sim:
         b = sim_jvp_buffers(*self._ptrs(JVP_FIELDS, bufs))
         check(load().sim_step_jvp(self.h, ctypes.byref(b), float(self.w.dt if dt is None else dt),
                                   int(self.w.substeps if substeps is None else substeps)), "sim_step_jvp")
+
+    def tape_floats(self, substeps: Optional[int] = None) -> Optional[int]:
+        """Floats of one recorded step's tape, or None if the reverse pass does not cover this
+        handle (its env types or flags): the derivative then runs in forward mode (step_vjp)."""
+        out = ctypes.c_int64(0)
+        rc = load().sim_tape_size(self.h, int(self.w.substeps if substeps is None else substeps), ctypes.byref(out))
+        if rc in (-1, -4):
+            return None
+        check(rc, "sim_tape_size")
+        return int(out.value)
+
+    def step_taped(self, tape, dt: Optional[float] = None, substeps: Optional[int] = None):
+        """sim_step on the handle's views that also records the step's tape (a float32 device
+        tensor of at least tape_floats() elements)."""
+        sub = int(self.w.substeps if substeps is None else substeps)
+        need = self.tape_floats(sub)
+        if need is None:
+            raise ValueError("the reverse pass does not cover this handle")
+        p = self._dev_ptr(tape, "tape", (self._torch.float32,), need)
+        check(load().sim_step_taped(self.h, ctypes.c_void_p(p), float(self.w.dt if dt is None else dt), sub),
+              "sim_step_taped")
+
+    def step_adjoint(self, tape, bufs: dict, dt: Optional[float] = None, substeps: Optional[int] = None):
+        """Vector-Jacobian product of the step recorded in `tape` (keys ADJ_FIELDS; output
+        gradients may be missing or None: zero)."""
+        sub = int(self.w.substeps if substeps is None else substeps)
+        need = self.tape_floats(sub)
+        if need is None:
+            raise ValueError("the reverse pass does not cover this handle")
+        p = self._dev_ptr(tape, "tape", (self._torch.float32,), need)
+        b = sim_adjoint_buffers(*self._ptrs(ADJ_FIELDS, bufs))
+        check(load().sim_step_adjoint(self.h, ctypes.c_void_p(p), ctypes.byref(b), float(self.w.dt if dt is None else dt),
+                                      sub), "sim_step_adjoint")
 
     def set_root_state_indexed(self, src, actor_idx):
         """src: (n, 13) float32 root states; actor_idx: n int32 actor indices (device tensors)."""

@@ -290,17 +290,28 @@ def many_boxes(n_boxes=19):
     return b.build(root_pos=(0.0, 0.0, 1.0))
 
 
-def test_unsupported_types_are_refused():
+def test_forward_mode_refuses_large_caches_the_reverse_pass_does_not():
+    """An impulse cache past 448 entries: the forward-mode kernel (SIM_FLAG_TANGENT_VJP) refuses the
+    handle with CAPACITY; the reverse pass, which keeps no per-lane copy of the cache, differentiates it."""
     import torch
     from paper_2108_10470_gb300 import sim
     w = W.homogeneous("boxes", many_boxes(), 4)
-    s = sim.Sim(w)
-    assert s.cache_len > 448
-    z = lambda v: torch.zeros_like(v)
-    bufs = {"root_state": s.root_state, "dof_state": s.dof_state, "dof_actuation": s.dof_actuation,
-            "impulse_cache": s.impulse_cache, "grad_root_state_in": z(s.root_state), "grad_dof_state_in": z(s.dof_state),
-            "grad_dof_actuation": z(s.dof_actuation), "grad_impulse_cache_in": z(s.impulse_cache)}
-    with pytest.raises(sim.SimError) as err:
-        s.step_vjp(bufs)
-    assert err.value.code == -4
-    s.destroy()
+    for flags in (sim.SIM_FLAG_TANGENT_VJP, 0):
+        s = sim.Sim(w, flags=flags)
+        assert s.cache_len > 448
+        z = lambda v: torch.zeros_like(v)
+        bufs = {"root_state": s.root_state, "dof_state": s.dof_state, "dof_actuation": s.dof_actuation,
+                "impulse_cache": s.impulse_cache, "grad_root_state": torch.ones_like(s.root_state),
+                "grad_root_state_in": z(s.root_state), "grad_dof_state_in": z(s.dof_state),
+                "grad_dof_actuation": z(s.dof_actuation), "grad_impulse_cache_in": z(s.impulse_cache),
+                "status": torch.full((w.n_envs,), 9, dtype=torch.int32, device="cuda")}
+        if flags:
+            with pytest.raises(sim.SimError) as err:
+                s.step_vjp(bufs)
+            assert err.value.code == -4
+        else:
+            s.step_vjp(bufs)
+            torch.cuda.synchronize()
+            assert not bufs["status"].any() and torch.isfinite(bufs["grad_root_state_in"]).all()
+            assert bufs["grad_root_state_in"][:, 2].abs().sum() > 0  # the height reaches the output
+        s.destroy()

@@ -1,0 +1,236 @@
+"""The reverse pass of the env-step on the GPU (sim_step_taped + sim_step_adjoint, and sim_step_vjp,
+which uses them where they cover the handle) against the FP64 oracle's forward-mode derivative.
+
+* The taped step is the step: the same states, contacts and impulses bit for bit as sim_step.
+* The vector-Jacobian product of one step: for every input direction of every env (root position,
+  root rotation along the unit sphere, root velocities of floating roots, joint positions and
+  velocities, actuation, every impulse-cache slot) the GPU's J^T g against the oracle's J u . g,
+  per env in the max norm relative to the env's gradient scale: within 1e-3 of the scale plus
+  16 times the env's FP32 conditioning spread (the largest deviation from FP64 of the oracle's own
+  derivative evaluated in single precision, at the input and at inputs nudged by one float32 ulp).
+  An env whose FP32 evaluation takes a different branch (a clamp or target within rounding of its
+  threshold) may deviate: at most one env per test.
+* The reverse and the forward-mode GPU evaluations agree (the second, independent kernel).
+* Handles the reverse pass does not cover report no tape size.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2108_10470_gb300 import workloads as W
+from test_gpu_adjoint import K_COND, WORKLOADS, make_sim, warm
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2108_10470_gb300 import build
+    build.build_library()
+    torch.cuda.set_device(0)
+
+
+STATE = ("root_state", "dof_state", "impulse_cache", "net_contact_force", "contact_pairs", "contact_count", "signature")
+
+
+@pytest.mark.parametrize("name,n,plan", [("ant", 67, "per_type"), ("humanoid", 37, "per_type"), ("cartpole", 64, "per_type"),
+                                         ("driven_ant", 40, "per_type"), ("ant", 67, "persistent"),
+                                         ("humanoid", 37, "row_solver"), ("mixed_no_hand", 48, "per_type")])
+def test_taped_step_is_the_step(name, n, plan):
+    """Six steps of sim_step and of sim_step_taped from the same seeded state: every view equal bit
+    for bit (the taped instantiation only adds stores)."""
+    import torch
+    from paper_2108_10470_gb300 import sim
+    if name == "mixed_no_hand":
+        ant, hum = W.ant(), W.humanoid()
+        w = W.Workload("two_types", [ant, hum], np.array([i % 2 for i in range(n)], np.int32), 1, n, W.Params())
+    else:
+        w = WORKLOADS[name](n)
+    flags = sim.SIM_FLAG_SIGNATURE | {"per_type": 0, "persistent": sim.SIM_FLAG_PERSISTENT,
+                                      "row_solver": sim.SIM_FLAG_ROW_SOLVER}[plan]
+    root, dof, acts = W.seeded_inputs(w, 4, 6)
+    handles = []
+    for _ in range(2):
+        if name == "driven_ant":
+            s, _ = make_sim(name, w)
+            s.destroy()
+            s, _ = make_sim(name, w)
+        else:
+            s = sim.Sim(w, flags=flags)
+        s.root_state.copy_(torch.from_numpy(root))
+        s.dof_state.copy_(torch.from_numpy(dof))
+        handles.append(s)
+    ref, tap = handles
+    tape = torch.empty(tap.tape_floats(), device="cuda")
+    for k in range(6):
+        for s in handles:
+            s.dof_actuation.copy_(torch.from_numpy(acts[k]))
+        ref.step()
+        tap.step_taped(tape)
+        torch.cuda.synchronize()
+        for v in STATE:
+            assert torch.equal(getattr(ref, v), getattr(tap, v)), (v, k)
+    for s in handles:
+        s.destroy()
+
+
+def gpu_vjp(s, r, d, c, a, gout):
+    import torch
+    f = lambda x: torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda()
+    bufs = {"root_state": f(r), "dof_state": f(d), "dof_actuation": f(a), "impulse_cache": f(c),
+            "grad_root_state": f(gout[0]), "grad_dof_state": f(gout[1]), "grad_impulse_cache": f(gout[2]),
+            "grad_root_state_in": torch.full_like(f(r), 5.0), "grad_dof_state_in": torch.full_like(f(d), 5.0),
+            "grad_dof_actuation": torch.full_like(f(a), 5.0), "grad_impulse_cache_in": torch.full_like(f(c), 7.0),
+            "status": torch.full((s.w.n_envs,), 9, dtype=torch.int32, device="cuda")}
+    s.step_vjp(bufs)
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy().astype(np.float64) for k, v in bufs.items()}
+
+
+def qtangent(q, k):
+    """(1/2) [e_k; 0] (x) q: the quaternion's tangent of a world-axis rotation about axis k."""
+    om = np.zeros((q.shape[0], 3))
+    om[:, k] = 1.0
+    t = np.zeros_like(q)
+    t[:, 0] = 0.5 * (om[:, 0] * q[:, 3] + om[:, 1] * q[:, 2] - om[:, 2] * q[:, 1])
+    t[:, 1] = 0.5 * (-om[:, 0] * q[:, 2] + om[:, 1] * q[:, 3] + om[:, 2] * q[:, 0])
+    t[:, 2] = 0.5 * (om[:, 0] * q[:, 1] - om[:, 1] * q[:, 0] + om[:, 2] * q[:, 3])
+    t[:, 3] = 0.5 * (-om[:, 0] * q[:, 0] - om[:, 1] * q[:, 1] - om[:, 2] * q[:, 2])
+    return t
+
+
+def directions(w, r, c):
+    """Input directions seeded in every env at once: (label, root, dof, act, cache) tangents."""
+    nj = w.n_dof // w.n_envs
+    free = w.models[0].free_root
+    out = []
+    for k in range(3):
+        t = np.zeros_like(r); t[:, k] = 1.0
+        out.append((f"p{k}", t, None, None, None))
+        t = np.zeros_like(r); t[:, 3:7] = qtangent(r[:, 3:7], k)
+        out.append((f"th{k}", t, None, None, None))
+        if free:
+            for base, nm in ((7, "v"), (10, "w")):
+                t = np.zeros_like(r); t[:, base + k] = 1.0
+                out.append((f"{nm}{k}", t, None, None, None))
+    for j in range(nj):
+        for comp, nm in ((0, "q"), (1, "qd")):
+            t = np.zeros((w.n_dof, 2)); t[j::nj, comp] = 1.0
+            out.append((f"{nm}{j}", None, t, None, None))
+        t = np.zeros(w.n_dof); t[j::nj] = 1.0
+        out.append((f"a{j}", None, None, t, None))
+    for k in range(c.shape[1]):
+        t = np.zeros_like(c); t[:, k] = 1.0
+        out.append((f"c{k}", None, None, None, t))
+    return out
+
+
+def oracle_grad(w, r, d, c, a, gout, dirs, ctl, single=False, nudge=None):
+    """Per env and direction: the oracle's directional derivative of <gout, step output>."""
+    from test_gpu_adjoint import oracle_tangent
+    ra = np.cumsum([0] + [w.env_actor_count(e) for e in range(w.n_envs)])
+    rd = np.cumsum([0] + [w.env_jdof(e) for e in range(w.n_envs)])
+    G = np.zeros((w.n_envs, len(dirs)))
+    for i, (_, tr, td, ta, tc) in enumerate(dirs):
+        t = (np.zeros_like(r) if tr is None else tr, np.zeros((w.n_dof, 2)) if td is None else td,
+             np.zeros(w.n_dof) if ta is None else ta, np.zeros_like(c) if tc is None else tc)
+        _, _, _, orr, odd, occ = oracle_tangent(w, r, d, c, a, t, single=single, nudge=nudge, ctl=ctl)
+        for e in range(w.n_envs):
+            G[e, i] = ((gout[0][ra[e]:ra[e + 1]] * orr[ra[e]:ra[e + 1]]).sum()
+                       + (gout[1][rd[e]:rd[e + 1]] * odd[rd[e]:rd[e + 1]]).sum() + (gout[2][e] * occ[e]).sum())
+    return G
+
+
+def gpu_grad(w, g, r, dirs):
+    ra = np.cumsum([0] + [w.env_actor_count(e) for e in range(w.n_envs)])
+    rd = np.cumsum([0] + [w.env_jdof(e) for e in range(w.n_envs)])
+    G = np.zeros((w.n_envs, len(dirs)))
+    for i, (_, tr, td, ta, tc) in enumerate(dirs):
+        for e in range(w.n_envs):
+            v = 0.0
+            if tr is not None:
+                v += (g["grad_root_state_in"][ra[e]:ra[e + 1]] * tr[ra[e]:ra[e + 1]]).sum()
+            if td is not None:
+                v += (g["grad_dof_state_in"][rd[e]:rd[e + 1]] * td[rd[e]:rd[e + 1]]).sum()
+            if ta is not None:
+                v += (g["grad_dof_actuation"][rd[e]:rd[e + 1]] * ta[rd[e]:rd[e + 1]]).sum()
+            if tc is not None:
+                v += (g["grad_impulse_cache_in"][e] * tc[e]).sum()
+            G[e, i] = v
+    return G
+
+
+def output_gradient(w, r, d, c, rng):
+    gout = (rng.standard_normal(r.shape), rng.standard_normal(d.shape), rng.standard_normal(c.shape))
+    if not w.models[0].free_root:
+        gout[0][:, 7:] = 0.0  # a fixed root's velocity is not state
+    return gout
+
+
+@pytest.mark.parametrize("name,n", [("ant", 40), ("humanoid", 16), ("cartpole", 32), ("driven_ant", 24)])
+def test_reverse_vjp_matches_oracle_derivative(name, n):
+    w = WORKLOADS[name](n)
+    r, d, c, a = warm(w, seed=5)
+    rng = np.random.default_rng(6)
+    gout = output_gradient(w, r, d, c, rng)
+    s, ctl = make_sim(name, w)
+    assert s.tape_floats() is not None
+    g = gpu_vjp(s, r, d, c, a, gout)
+    s.destroy()
+    assert not g["status"].any()
+    g32 = tuple(x.astype(np.float32).astype(np.float64) for x in gout)
+    dirs = directions(w, r, c)
+    ref = oracle_grad(w, r, d, c, a, g32, dirs, ctl)
+    probes = [oracle_grad(w, r, d, c, a, g32, dirs, ctl, single=True, nudge=x) for x in (None, 1)]
+    got = gpu_grad(w, g, r, dirs)
+    bad = []
+    worst = 0.0
+    for e in range(w.n_envs):
+        scale = max(1.0, np.abs(ref[e]).max())
+        spread = max(np.abs(p[e] - ref[e]).max() for p in probes)
+        dev = np.abs(got[e] - ref[e]).max()
+        worst = max(worst, dev / scale)
+        if dev > 1e-3 * scale + K_COND * spread:
+            bad.append((e, dev / scale, dirs[int(np.argmax(np.abs(got[e] - ref[e])))][0]))
+    print(f"{name} x{n}: {len(dirs)} directions per env, largest relative deviation {worst:.2e}, "
+          f"{len(bad)} envs outside the bound {bad}")
+    assert len(bad) <= 1, bad
+
+
+@pytest.mark.parametrize("name,n", [("ant", 40), ("humanoid", 16), ("driven_ant", 24)])
+def test_reverse_and_forward_mode_agree(name, n):
+    """The reverse pass against the forward-mode kernel (SIM_FLAG_TANGENT_VJP) on the same inputs:
+    two FP32 evaluations of the same derivative; the quaternion gradient compared along the sphere."""
+    from paper_2108_10470_gb300 import sim
+    w = WORKLOADS[name](n)
+    r, d, c, a = warm(w, seed=7)
+    rng = np.random.default_rng(8)
+    gout = output_gradient(w, r, d, c, rng)
+    s, ctl = make_sim(name, w)
+    g_rev = gpu_vjp(s, r, d, c, a, gout)
+    s.destroy()
+    w_f = WORKLOADS[name](n)
+    s = sim.Sim(w_f, flags=sim.SIM_FLAG_TANGENT_VJP)
+    if ctl:
+        import torch
+        s.dof_position_target.copy_(torch.from_numpy(ctl["pos_target"].astype(np.float32)))
+        s.dof_velocity_target.copy_(torch.from_numpy(ctl["vel_target"].astype(np.float32)))
+    g_fwd = gpu_vjp(s, r, d, c, a, gout)
+    s.destroy()
+    dirs = directions(w, r, c)
+    A, B = gpu_grad(w, g_rev, r, dirs), gpu_grad(w, g_fwd, r, dirs)
+    rel = np.abs(A - B).max(1) / np.maximum(1.0, np.abs(B).max(1))
+    print(f"{name} x{n}: reverse vs forward mode, relative deviation median {np.median(rel):.2e}, max {rel.max():.2e}")
+    assert (rel <= 1e-2).mean() >= 0.95 and np.median(rel) <= 1e-3
+
+
+@pytest.mark.parametrize("name", ["hand", "tendon_ant", "ball_ant", "pushed_ant"])
+def test_uncovered_handles_report_no_tape(name):
+    """Shape pairs, tendons, ball joints and external body forces are differentiated in forward mode."""
+    w = WORKLOADS[name](4)
+    s, _ = make_sim(name, w)
+    assert s.tape_floats() is None
+    s.destroy()
