@@ -75,25 +75,12 @@ class Segment(torch.autograd.Function):
             tf = s.tape_floats()
             if tf is not None:
                 # reverse pass: the segment re-run with each step's tape recorded, then the steps'
-                # adjoints in reverse order (two gradient sets, used alternately)
+                # adjoints in reverse order
                 tapes = torch.empty((acts.shape[0], max(tf, 1)), dtype=torch.float32, device=root.device)
                 s.root_state.copy_(root)
                 s.dof_state.copy_(dof)
                 s.impulse_cache.copy_(cache)
-                for k in range(acts.shape[0]):
-                    s.dof_actuation.copy_(acts[k])
-                    s.step_taped(tapes[k])
-                sets = [tuple(torch.empty_like(x) for x in (root, dof, cache)) for _ in range(2)]
-                ga = torch.empty_like(s.dof_actuation)
-                for k in range(acts.shape[0] - 1, -1, -1):
-                    out = sets[k % 2]
-                    s.step_adjoint(tapes[k], {"grad_root_state": g[0], "grad_dof_state": g[1],
-                                              "grad_impulse_cache": g[2], "grad_root_state_in": out[0],
-                                              "grad_dof_state_in": out[1], "grad_dof_actuation": ga,
-                                              "grad_impulse_cache_in": out[2]})
-                    g_acts[k] = ga
-                    g = out
-                g = tuple(x.clone() for x in g)
+                g = s.reverse_rollout(tapes, acts.contiguous(), g, g_acts)
             else:
                 _, inputs = _forward_steps(s, root, dof, cache, acts, keep_inputs=True)
                 for k in range(acts.shape[0] - 1, -1, -1):

@@ -28,7 +28,7 @@ COMPILE_FLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC"]
 # sweeps (humanoid and hand steps 4-5 % faster); the FP32 results move by far less than the
 # tolerance the parity tests derive from the FP32 conditioning of each step. The derivative
 # kernel and the host code keep IEEE division and square root.
-STEP_UNITS = ("kernels_shared.cu", "kernels_global.cu", "kernels_persistent.cu", "kernels_tape.cu")
+STEP_UNITS = ("kernels_shared.cu", "kernels_global.cu", "kernels_persistent.cu")
 STEP_FLAGS = ["-prec-div=false", "-prec-sqrt=false"]
 LINK_FLAGS = ARCH + ["-shared", "-cudart", "static"]
 

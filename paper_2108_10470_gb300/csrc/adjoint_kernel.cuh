@@ -91,11 +91,62 @@ enum : int {
   kRecIc = 37,   // composite inertia m | h 3 | I_O 6 (10 words)
   kRecSlot = 47  // 6-word hand-off slot of the inward sweeps
 };
-// Vectors of the reverse arena (n words each, kAdjVecs of them).
+// Vectors (n words each): the tape's (in the image) and the reverse's own (kAdjVecs in the arena).
 enum : int {
   kVQdd = 0, kVFree = 1, kVZ0 = 2, kVZf = 3, kVDzf = 4, kVV = 5, kVDq = 6, kVLinv = 7,
   kVVb = 8, kVDqb = 9, kVZb6 = 10, kVDzb6 = 11, kVZb0 = 12, kVCb = 13
 };
+
+// Bulk asynchronous copy (the TMA engine) of `bytes` (a multiple of 16, both addresses 16-byte
+// aligned) from global memory into shared memory, completing on the mbarrier at `bar`.
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes, void* bar) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst), b = (unsigned)__cvta_generic_to_shared(bar);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier writes to dst come first
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(d),
+               "l"(src), "r"(bytes), "r"(b)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_init(void* bar) {
+  const unsigned b = (unsigned)__cvta_generic_to_shared(bar);
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// Wait for the phase `parity` of the mbarrier, giving up after a bounded number of tries (each
+// try suspends for at most a hardware time limit): false means the copy did not complete.
+__device__ __forceinline__ bool mbar_wait(void* bar, unsigned parity) {
+  const unsigned b = (unsigned)__cvta_generic_to_shared(bar);
+  for (int i = 0; i < (1 << 20); ++i) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(b), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+// Back substitution L^T x = b by one lane for one right-hand side: b_i at base[i * stride] in,
+// x_k written there (right-looking, the remaining right-hand side in registers: y[0] holds b_k).
+template <int G>
+__device__ __forceinline__ void lt_solve_lane(const float* L, const int LS, const float* linv, const int n, float* base,
+                                              const int stride) {
+  float y[G];
+#pragma unroll
+  for (int m = 0; m < G; ++m) y[m] = (m < n) ? base[(n - 1 - m) * stride] : 0.f;
+  for (int k = n - 1; k >= 0; --k) {
+    const float xk = y[0] * linv[k];
+    base[k * stride] = xk;
+    const float* Lk = L + k * LS;
+#pragma unroll
+    for (int m = 1; m < G; ++m) {
+      if (m > k) break;
+      y[m - 1] = y[m] - Lk[k - m] * xk;
+    }
+  }
+}
 
 // Group-parallel forward substitution L x = b (lane k holds b_k in, x_k out); two right-hand sides.
 template <int G>
@@ -145,30 +196,35 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
   const int L = T->n_links, n = T->n_gen;
   const int maxdepth = T->max_depth;
   const int YS = al.YS, LS = al.LS, RC = TL.rcap;
-  float* s_Y = sm + al.Y;
+  // the substep's tape image (read in place; its final impulses are rewound during the solve)
+  float* img = sm + al.img;
+  void* bar = sm + al.bar;
+  float* s_Y = img + TL.Y;
+  float* s_L = img + TL.L;
+  float4* s_rowc = reinterpret_cast<float4*>(img + TL.rowc);
+  int* s_rowa = reinterpret_cast<int*>(img + TL.rowa);
+  float* s_lam = img + TL.lamf;
+  float* s_lam0 = img + TL.lam0;
+  float* s_lambef = img + TL.lamb;
+  float* s_seps = img + TL.seps;
+  float* s_con = img + TL.con;
+  int* s_coni = reinterpret_cast<int*>(s_con);
+  const float* s_linv = img + TL.Linv;
   float* s_Yb = sm + al.Yb;
-  float* s_L = sm + al.L;
   float* s_Mb = sm + al.Mb;
-  float4* s_rowc = reinterpret_cast<float4*>(sm + al.rowc);
-  int* s_rowa = reinterpret_cast<int*>(sm + al.rowa);
-  float* s_lam = sm + al.lam;
   float* s_lamb = sm + al.lamb;
   float* s_db = sm + al.db;
   float* s_invAb = sm + al.invAb;
-  float* s_lam0 = sm + al.lam0;
   float* s_xb = sm + al.xb;
-  float* s_lambef = sm + al.lambef;
-  float* s_seps = sm + al.seps;
-  float* s_con = sm + al.con;
-  int* s_coni = reinterpret_cast<int*>(s_con);
   float* s_vec = sm + al.vec;
   float* s_SD = sm + al.SD;
   float* s_FM = sm + al.FM;
   float* s_FMb = sm + al.FMb;
   float* s_Sb = sm + al.Sb;
   float* s_link = sm + al.link;
-  auto V = [&](int k) { return s_vec + k * n; };
-  const float* s_linv = s_vec + kVLinv * n;
+  auto V = [&](int k) -> float* {
+    return k < 7 ? img + TL.vec + k * n : (k == kVLinv ? img + TL.Linv : s_vec + (k - kVVb) * n);
+  };
 
   // ---- per-link constants (link mode) ----
   const bool isl = lane < L;
@@ -238,45 +294,40 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
   }
   if (live)
     for (int i = lane; i < A.cache_stride; i += G) cacheb[i] = J.g_cache ? J.g_cache[(size_t)env * A.cache_stride + i] : 0.f;
+  if (lane == 0) mbar_init(bar);
   __syncwarp();
+  unsigned parity = 0;
+  bool failed = false;  // a tape copy that did not complete: the env's gradient is not computed
 
   for (int sub = A.substeps - 1; sub >= 0; --sub) {
     const float* tp = J.tape + ((size_t)gi * A.substeps + sub) * TL.words;
-    const int* th = reinterpret_cast<const int*>(tp + TL.hdr);
+    // ---- the tape block into the arena: one bulk copy by the TMA engine ----
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // this lane's writes to the image first
+    __syncwarp();
+    if (lane == 0) bulk_copy_g2s(img, tp, 4u * (unsigned)TL.words, bar);
+    const bool arrived = mbar_wait(bar, parity);
+    parity ^= 1u;
+    if (__any_sync(kFull, !arrived)) {  // warp-uniform: both groups of the warp stop here
+      failed = true;
+      mbar_wait(bar, parity ^ 1u);  // once more for the copy in flight, then no further use
+      break;
+    }
+    const int* th = reinterpret_cast<const int*>(img + TL.hdr);
     const int n_con = th[0], n_lim = th[1], R = th[2];
-    // ---- stage the tape into the arena ----
     for (int i = 0; i < n; ++i)
-      for (int r = lane; r < R; r += G) {
-        s_Y[i * YS + r] = tp[TL.Y + i * RC + r];
-        s_Yb[i * YS + r] = 0.f;
-      }
-    for (int i = 0; i < n; ++i)
-      for (int k = lane; k < n; k += G) s_L[i * LS + k] = (k <= i) ? tp[TL.L + i * n + k] : 0.f;
+      for (int r = lane; r < R; r += G) s_Yb[i * YS + r] = 0.f;
     for (int r = lane; r < R; r += G) {
-      const float4 hc = reinterpret_cast<const float4*>(tp + TL.rowc)[r];
-      s_rowc[r] = hc;
-      s_rowa[r] = __float_as_int(tp[TL.rowa + r]);
-      s_lam[r] = tp[TL.lamf + r];
-      s_lam0[r] = tp[TL.lam0 + r];
+      const float4 hc = s_rowc[r];
       s_lamb[r] = (hc.y > 0.f) ? cacheb[__float_as_int(hc.w)] : 0.f;
       s_db[r] = 0.f;
       s_invAb[r] = 0.f;
     }
-    for (int it = 0; it < npos + nvel; ++it)
-      for (int r = lane; r < R; r += G) s_lambef[it * RC + r] = tp[TL.lamb + it * RC + r];
-    for (int it = 0; it <= npos; ++it)
-      for (int r = lane; r < R; r += G) s_seps[it * RC + r] = tp[TL.seps + it * RC + r];
-    for (int c = lane; c < n_con; c += G)
-#pragma unroll
-      for (int k = 0; k < 5; ++k) s_con[k * TL.ccap + c] = tp[TL.con + k * TL.ccap + c];
-    for (int i = lane; i < 7 * n; i += G) s_vec[i] = tp[TL.vec + i];
-    if (isg) s_vec[kVLinv * n + lane] = tp[TL.Linv + lane];
     // the substep's input state
     float q = 0.f, qd = 0.f, rq[4] = {0.f, 0.f, 0.f, 1.f};
     V3 rp = v3(0.f, 0.f, 0.f), rw = rp, rv = rp;
-    if (has_dof) { q = tp[TL.st + 2 * l]; qd = tp[TL.st + 2 * l + 1]; }
+    if (has_dof) { q = img[TL.st + 2 * l]; qd = img[TL.st + 2 * l + 1]; }
     if (is_root) {
-      const float* r = tp + TL.st + 2 * L + 13 * T->actor[l];
+      const float* r = img + TL.st + 2 * L + 13 * T->actor[l];
       rp = v3(r[0], r[1], r[2]);
       rq[0] = r[3]; rq[1] = r[4]; rq[2] = r[5]; rq[3] = r[6];
       rv = v3(r[7], r[8], r[9]);
@@ -457,17 +508,20 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
         const float* lb = s_lambef + it * RC;
         for (int r = Rw_max - 1; r >= 0; --r) {
           const bool inr = r < R;
-          const float4 hc = inr ? s_rowc[r] : make_float4(0.f, 0.f, 0.f, 0.f);
-          const bool valid = inr && hc.y > 0.f;
+          const int rr = inr ? r : 0;
+          const float4 hc = s_rowc[rr];
+          const float invA = inr ? hc.y : 0.f;
+          const bool valid = invA > 0.f;
           const int kb = __float_as_int(hc.z);
           const bool fric = (kb & 3) == kRowFriction;
-          const int nrow = valid && fric ? (kb >> 2) : 0;
-          const float la = valid ? s_lam[r] : 0.f, lbf = valid ? lb[r] : 0.f;
-          const float ln_cur = s_lam[nrow];
-          const float lbar = valid ? s_lamb[r] : 0.f;
-          const float sep = valid ? sp[r] : 0.f;
-          const float D = la - lbf;
-          const float y = (isg && inr) ? s_Y[lane * YS + r] : 0.f;
+          const int nrow = (valid && fric) ? (kb >> 2) : 0;
+          // every value this row's update reads, before any lane stores (the stores below write
+          // the same value from every lane of the group)
+          const float la = s_lam[rr], lbf = lb[rr], lbar = s_lamb[rr], sep = sp[rr];
+          const float dbr = s_db[rr], iab = s_invAb[rr], ln_cur = s_lam[nrow], lbn = s_lamb[nrow];
+          const float D = valid ? la - lbf : 0.f;
+          const float y = (isg && inr) ? s_Y[lane * YS + rr] : 0.f;
+          const float ybar = (isg && inr) ? s_Yb[lane * YS + rr] : 0.f;
           const float zbef = z - y * D;
           // two group reductions in one pass: Y_r . z_bar and Y_r . z (before the update)
           float Db = y * zb, yz = y * zbef;
@@ -476,52 +530,37 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
             Db += __shfl_xor_sync(kFull, Db, m, G);
             yz += __shfl_xor_sync(kFull, yz, m, G);
           }
-          const float invA = hc.y;
           const float ap = lbar + Db;  // adjoint of the impulse after the update
-          float argb = 0.f, nbar = 0.f, tgt = 0.f, sepb = 0.f;
-          if (fric) {
-            const float lim = hc.x * ln_cur;
-            bool hi = la == lim, lo = la == -lim;
-            if (hi && lo) {  // lim = 0: the side of the clamp is the sign of its argument
-              const float arg = lbf - yz * invA;
-              hi = arg > 0.f;
-              lo = arg < 0.f;
-            }
-            if (hi) nbar = hc.x * ap;
-            else if (lo) nbar = -hc.x * ap;
-            else argb = ap;
-          } else {
-            argb = (la == 0.f) ? 0.f : ap;  // max(arg, 0) at 0: the clamped side
-            if (pos) {
-              if (sep >= 0.f) {
-                tgt = -sep * inv_hit;
-                sepb = -inv_hit;
-              } else {
-                const float t1 = -beta * sep * inv_hit;
-                if (t1 < vmax) { tgt = t1; sepb = -beta * inv_hit; }
-                else { tgt = vmax; sepb = 0.f; }
-              }
-            } else if (sep > 0.f) {
-              tgt = -sep * inv_h;
-              sepb = -inv_h;
-            }
-          }
+          // friction: clamped at +lim or -lim (lim = mu lambda_n; at lim = 0 the argument's sign)
+          const float lim = hc.x * ln_cur;
+          const float arg_f = lbf - yz * invA;
+          const bool zl = (lim == 0.f);
+          const bool hi = fric && (la == lim) && (!zl || arg_f > 0.f);
+          const bool lo = fric && !hi && (la == -lim) && (!zl || arg_f < 0.f);
+          // normal and limit rows: max(arg, 0) at 0 is the clamped side; the target and its slope
+          const bool clamped = fric ? (hi || lo) : (la == 0.f);
+          const float t1 = -beta * sep * inv_hit;
+          const bool cap = !(t1 < vmax);
+          const float tgt = pos ? ((sep >= 0.f) ? -sep * inv_hit : (cap ? vmax : t1)) : ((sep > 0.f) ? -sep * inv_h : 0.f);
+          const float dts = pos ? ((sep >= 0.f) ? -inv_hit : (cap ? 0.f : -beta * inv_hit)) : ((sep > 0.f) ? -inv_h : 0.f);
+          const float argb = clamped ? 0.f : ap;
+          const float nbar = hi ? hc.x * ap : (lo ? -hc.x * ap : 0.f);
           const float yzb = -argb * invA;
-          const float invAb_add = argb * ((fric ? 0.f : tgt) - yz);
-          sepb *= argb * invA;  // d(arg)/d(sep) = invA d(tgt)/d(sep)
+          const float iadd = argb * ((fric ? 0.f : tgt) - yz);
+          const float sepb = fric ? 0.f : argb * invA * dts;
           if (valid && isg) {
-            s_Yb[lane * YS + r] += D * zb + yzb * zbef + sepb * dzs;
+            s_Yb[lane * YS + rr] = ybar + D * zb + yzb * zbef + sepb * dzs;
             zb += yzb * y;
             dzb += sepb * y;
           }
           if (valid) z = zbef;
-          __syncwarp();
-          if (valid && lane == 0) {  // one lane owns the row scalars (read-modify-write)
+          __syncwarp();  // every lane has read what the stores below overwrite
+          if (valid) {
             s_lam[r] = lbf;
             s_lamb[r] = argb - Db;
-            if (fric) s_lamb[nrow] += nbar;
-            s_db[r] += sepb;
-            s_invAb[r] += invAb_add;
+            s_db[r] = dbr + sepb;
+            s_invAb[r] = iab + iadd;
+            if (fric) s_lamb[nrow] = lbn + nbar;
           }
           __syncwarp();
         }
@@ -557,45 +596,37 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
     }
     // ---- P = Phi(L^T L_bar) = Phi(-Y_bar Y^T - z z_bar^T - dz dz_bar^T + z0 z0_bar^T) (lane = row) ----
     if (isg) {
+      float p[G];
+#pragma unroll
+      for (int j = 0; j < G; ++j) p[j] = 0.f;
+      for (int r = 0; r < R; ++r) {
+        const float yb = s_Yb[lane * YS + r];
+#pragma unroll
+        for (int j = 0; j < G; ++j)
+          if (j < n) p[j] -= yb * s_Y[j * YS + r];
+      }
       const float zf = V(kVZf)[lane], dzf = V(kVDzf)[lane], z0 = V(kVZ0)[lane];
-      for (int j = 0; j < n; ++j) {
-        float p = 0.f;
+#pragma unroll
+      for (int j = 0; j < G; ++j) {
+        if (j >= n) break;
+        float v = 0.f;
         if (j <= lane) {
-          for (int r = 0; r < R; ++r) p -= s_Yb[lane * YS + r] * s_Y[j * YS + r];
-          p += -zf * V(kVZb6)[j] - dzf * V(kVDzb6)[j] + z0 * V(kVZb0)[j];
-          if (j == lane) p *= 0.5f;
+          v = p[j] - zf * V(kVZb6)[j] - dzf * V(kVDzb6)[j] + z0 * V(kVZb0)[j];
+          if (j == lane) v *= 0.5f;
         }
-        s_Mb[lane * LS + j] = p;
+        s_Mb[lane * LS + j] = v;
       }
     }
     __syncwarp();
     // ---- Jacobian-row adjoints J_bar_r = L^-T Y_bar_r, in place (row mode, contact rows) ----
     for (int r = lane; r < R; r += G) {
       if (!(s_rowc[r].y > 0.f) || (__float_as_int(s_rowc[r].z) & 3) == kRowLimit) continue;
-      for (int k = n - 1; k >= 0; --k) {
-        float t = s_Yb[k * YS + r];
-        for (int i = k + 1; i < n; ++i) t -= s_L[i * LS + k] * s_Yb[i * YS + r];
-        s_Yb[k * YS + r] = t * s_linv[k];
-      }
+      lt_solve_lane<G>(s_L, LS, s_linv, n, s_Yb + r, YS);
     }
     // ---- M_bar' = L^-T P L^-1 (its symmetric part is the joint-space inertia's adjoint) ----
-    if (isg) {  // X = L^-T P, lane = column
-      const int j = lane;
-      for (int i = n - 1; i >= 0; --i) {
-        float t = s_Mb[i * LS + j];
-        for (int k = i + 1; k < n; ++k) t -= s_L[k * LS + i] * s_Mb[k * LS + j];
-        s_Mb[i * LS + j] = t * s_linv[i];
-      }
-    }
+    if (isg) lt_solve_lane<G>(s_L, LS, s_linv, n, s_Mb + lane, LS);  // X = L^-T P, lane = column
     __syncwarp();
-    if (isg) {  // M_bar' = X L^-1, lane = row
-      const int i = lane;
-      for (int j = n - 1; j >= 0; --j) {
-        float t = s_Mb[i * LS + j];
-        for (int k = j + 1; k < n; ++k) t -= s_Mb[i * LS + k] * s_L[k * LS + j];
-        s_Mb[i * LS + j] = t * s_linv[j];
-      }
-    }
+    if (isg) lt_solve_lane<G>(s_L, LS, s_linv, n, s_Mb + lane * LS, 1);  // M_bar'^T solves L^T: lane = row
     __syncwarp();
 
     // ---- composite inertias (inward sweep of m, h, I_O) and F_i = Ic S_i (DOF mode) ----
@@ -888,7 +919,14 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
   }  // substeps
 
   // ---- outputs ----
-  int status = 0;
+  int status = failed ? 4 : 0;
+  if (failed) {  // no gradient for an env whose tape did not arrive
+    qb = qdb = actb = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) { rpb[k] = 0.f; rwb[k] = 0.f; rvb[k] = 0.f; }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) rqb[k] = 0.f;
+  }
   if (has_dof && !(isfinite(qb) && isfinite(qdb) && isfinite(actb))) status = 2;
   if (is_root && !(isfinite(rpb[0] + rpb[1] + rpb[2]) && isfinite(rqb[0] + rqb[1] + rqb[2] + rqb[3]) &&
                    isfinite(rwb[0] + rwb[1] + rwb[2]) && isfinite(rvb[0] + rvb[1] + rvb[2])))

@@ -40,12 +40,9 @@ cudaError_t persistent_kernel_occupancy(bool ball, int* ctas_per_sm, size_t smem
 // Derivative of the step (kernels_adjoint.cu): K tangents per lane (1, 2, 4 or 8), one env per warp.
 cudaError_t launch_tangent_kernel(int K, const StepArgs& a, const TypeArgs& ta, const TangentArgs& v, cudaStream_t st);
 int tangent_lanes_per_dir(int n_dirs);
-// Reverse pass (kernels_tape.cu): the taped step (step_kernel<G, rows_global, false, true>, the same
-// launch shape as the per-type step) and the adjoint kernel (64-thread CTAs, 64 / G envs each, the
-// AdjLayout arena per env).
-cudaError_t launch_taped_step_kernel(int G, bool rows_global, const StepArgs& a, const TypeArgs& ta,
-                                     int groups_per_block, size_t smem, cudaStream_t st);
-cudaError_t set_taped_step_kernel_smem_cap(int G, bool rows_global, size_t bytes);
+// Reverse pass (kernels_tape.cu): the adjoint kernel (64-thread CTAs, 64 / G envs each, the
+// AdjLayout arena per env). The tape is written by the per-type step kernels when TypeArgs::tape
+// is set.
 cudaError_t launch_adjoint_kernel(int G, const StepArgs& a, const TypeArgs& ta, const AdjArgs& j, cudaStream_t st);
 cudaError_t set_adjoint_kernel_smem_cap(int G, size_t bytes);
 // Mass matrices (what = 0, n_envs x n_max x n_max) or link Jacobians (what = 1, n_envs x l_max x 6 x

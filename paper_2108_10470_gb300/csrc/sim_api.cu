@@ -1098,8 +1098,10 @@ TapeLayout tape_layout(const TypePlan& tp, int npos, int nvel) {
   t.hdr = o; o += 4;
   t.st = o; o += 2 * T.n_links + 13 * T.n_actors;
   o = al4i(o);
+  t.LT = n | 1;
+  t.YT = t.rcap | 1;
   t.vec = o; o += 7 * n;
-  t.L = o; o += n * n;
+  t.L = o; o += n * t.LT;
   t.Linv = o; o += n;
   t.con = o; o += 5 * t.ccap;
   o = al4i(o);
@@ -1107,7 +1109,7 @@ TapeLayout tape_layout(const TypePlan& tp, int npos, int nvel) {
   t.rowa = o; o += t.rcap;
   t.lam0 = o; o += t.rcap;
   t.lamf = o; o += t.rcap;
-  t.Y = o; o += n * t.rcap;
+  t.Y = o; o += n * t.YT;
   t.lamb = o; o += t.iters * t.rcap;
   t.seps = o; o += (npos + 1) * t.rcap;
   t.words = al4i(o);
@@ -1117,27 +1119,20 @@ TapeLayout tape_layout(const TypePlan& tp, int npos, int nvel) {
 // Arena of one env in the adjoint kernel (offsets in words; see AdjLayout).
 AdjLayout adj_layout(const TypePlan& tp, int npos, int nvel) {
   const EnvTypeTable& T = tp.tab;
+  const TapeLayout tl = tape_layout(tp, npos, nvel);
   AdjLayout a{};
-  const int n = std::max(T.n_gen, 1), rc = tp.lay.rcap, cc = tp.lay.ccap, it = npos + nvel;
-  a.YS = rc | 1;
-  a.LS = n | 1;
+  const int n = std::max(T.n_gen, 1), rc = tp.lay.rcap;
+  a.YS = tl.YT;
+  a.LS = tl.LT;
   int o = 0;
-  a.Y = o; o += n * a.YS;
+  a.img = o; o += tl.words;
+  a.bar = o; o += 4;
   a.Yb = o; o += n * a.YS;
-  a.L = o; o += n * a.LS;
   a.Mb = o; o += n * a.LS;
-  o = al4i(o);
-  a.rowc = o; o += 4 * rc;
-  a.rowa = o; o += rc;
-  a.lam = o; o += rc;
   a.lamb = o; o += rc;
   a.db = o; o += rc;
   a.invAb = o; o += rc;
-  a.lam0 = o; o += rc;
   a.xb = o; o += 3 * rc;
-  a.lambef = o; o += it * rc;
-  a.seps = o; o += (npos + 1) * rc;
-  a.con = o; o += 5 * cc;
   a.vec = o; o += kAdjVecs * n;
   a.SD = o; o += 6 * n;
   a.FM = o; o += 6 * n;
@@ -1181,8 +1176,9 @@ int64_t tape_floats(const sim_s* h, int substeps, std::vector<int64_t>* offs) {
   return total;
 }
 
-// One taped step: the state buffers of `a` advance exactly as sim_step advances them (same kernel
-// code and arithmetic), and each env-substep's tape is written to `tape`.
+// One taped step: the per-type step kernels, given the tape pointer, advance the state buffers of
+// `a` exactly as sim_step's per-type launches do (the same kernels and arithmetic; the tape stores
+// are their only difference) and write each env-substep's tape to `tape`.
 int launch_taped(sim_s* h, StepArgs a, float* tape, cudaStream_t st) {
   std::vector<int64_t> offs;
   tape_floats(h, a.substeps, &offs);
@@ -1199,10 +1195,8 @@ int launch_taped(sim_s* h, StepArgs a, float* tape, cudaStream_t st) {
     fill_type(h, t, ta);
     ta.tape = tape + offs[t];
     ta.tl = tape_layout(tp, a.pos_iters, a.vel_iters);
-    CK(set_taped_step_kernel_smem_cap(tp.G, tp.lay.grows != 0, kMaxSmemPerCta));
-    const cudaError_t e = launch_taped_step_kernel(tp.G, tp.lay.grows != 0, a, ta, tp.groups_per_block,
-                                                   tp.smem_bytes, st);
-    if (e != cudaSuccess) return cuda_fail(e, "taped step_kernel launch");
+    const cudaError_t e = launch_type(tp, a, ta, st);  // the per-type step kernel, recording the tape
+    if (e != cudaSuccess) return cuda_fail(e, "step_kernel launch (taped)");
   }
   return SIM_OK;
 }

@@ -148,18 +148,19 @@ struct TapeLayout {
   int hdr;    // 4: n_con | n_lim | R | 0 (int bits)
   int st;     // 2 per link (q, qd), then 13 per actor root (p 3 | quat 4 | v 3 | w 3)
   int vec;    // 7 x n: qdd | v_free | z0 = L^T v_free | z final | dz final | v | dq
-  int L;      // n x n, row-major, lower triangle
+  int L;      // n x LT (LT = n | 1, odd), row-major, lower triangle
   int Linv;   // n: 1 / L_kk
   int con;    // 5 x ccap (SoA): x y z (relative to the actor origin) | link | shape
   int rowc;   // 4 x rcap: the row headers (16-byte aligned)
   int rowa;   // rcap
   int lam0;   // rcap: warm-start impulses
   int lamf;   // rcap: final impulses
-  int Y;      // n x rcap: Y = L^-1 J^T, column r = row r
+  int Y;      // n x YT (YT = rcap | 1, odd): Y = L^-1 J^T, column r = row r
   int lamb;   // (npos + nvel) x rcap: impulse of row r before its update in iteration it
   int seps;   // (npos + 1) x rcap: separation d_r + Y_r . dz used in iteration it (the last for
               // every velocity iteration)
   int rcap, ccap, n, npos, iters;
+  int YT, LT; // odd strides of Y and L (the reverse kernel reads its shared-memory image in place)
 };
 
 // Arguments of one env type (read once per group, at the start of its step).
@@ -174,21 +175,23 @@ struct TypeArgs {
   TapeLayout tl;
 };
 
-// Shared-memory arena of one env in the reverse (adjoint) kernel, offsets in words.
+// Shared-memory arena of one env in the reverse (adjoint) kernel, offsets in words. The arena
+// starts with an image of the substep's tape block (TapeLayout offsets, copied by one bulk
+// asynchronous copy per substep and read in place); the impulses of its final-impulse block are
+// rewound in place during the reverse solve.
 struct AdjLayout {
-  int Y, Yb, YS;    // n x YS each (YS odd): Y, then its adjoint (the Jacobian-row adjoint later)
-  int L, Mb, LS;    // n x LS each (LS odd): the factor L; P, then L^-T P, then the inertia adjoint
-  int rowc;         // float4 x rcap (16-byte aligned)
-  int rowa, lam, lamb, db, invAb, lam0;  // rcap each
+  int img;          // the tape block (TapeLayout::words, 16-byte aligned)
+  int bar;          // the bulk copy's mbarrier (8-byte aligned, 4 words reserved)
+  int Yb, YS;       // n x YS (YS = the tape's Y stride): Y's adjoint, then the Jacobian-row adjoint
+  int Mb, LS;       // n x LS (LS = the tape's L stride): P, then L^-T P, then the inertia adjoint
+  int lamb, db, invAb;  // rcap each
   int xb;           // 3 x rcap: adjoint of each row's contact point
-  int lambef, seps; // iters x rcap, (npos + 1) x rcap
-  int con;          // 5 x ccap
   int vec;          // kAdjVecs x n (see adjoint_kernel.cuh)
   int SD, FM, FMb, Sb;  // 6 x n each: motion subspace, composite-inertia force, its adjoint, S adjoint
   int link;         // kAdjLinkWords x L
   int total;        // words per env (multiple of 4)
 };
-constexpr int kAdjVecs = 14;
+constexpr int kAdjVecs = 6;
 constexpr int kAdjLinkWords = 56;
 
 // Arguments of the reverse pass of one recorded step.

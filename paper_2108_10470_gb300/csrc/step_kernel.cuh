@@ -482,7 +482,7 @@ static __device__ __noinline__ int ball_joint_block(float* sl, float* bl, const 
 // a group reduction, and z moves by Y_r dl; the separations d_r + Y_r . dz are formed once per
 // iteration into s_sep (R words; s_dz, n words, is scratch). Starts from z_free (z0 of the DOF
 // lane) plus the warm start; returns (z, dz) of the lane. The impulses are updated in s_lam.
-template <int G, bool TAPE = false>
+template <int G>
 __device__ __noinline__ float2 pgs_row_form(const float* s_Y, const int YS, const float4* s_rowc, float* s_lam,
                                             float* s_dz, float* s_sep, const int R, const int Rw_max, const int n,
                                             const bool isg, const int lane, const int npos, const int nvel,
@@ -507,6 +507,12 @@ __device__ __noinline__ float2 pgs_row_form(const float* s_Y, const int YS, cons
       }
       __syncwarp();
     }
+    if (t_lamb) {  // taped step: every row's impulse before this iteration and its separation
+        for (int r = lane; r < R; r += G) {
+          t_lamb[it * t_rcap + r] = s_lam[r];
+          if (it <= npos) t_seps[it * t_rcap + r] = (it == 0) ? s_rowc[r].x : s_sep[r];
+        }
+    }
     // one group reduction per row, then a branch-free update (selects: measured 7 % faster on the
     // Ant step than a branch around it)
     for (int r = 0; r < Rw_max; ++r) {
@@ -527,12 +533,6 @@ __device__ __noinline__ float2 pgs_row_form(const float* s_Y, const int YS, cons
       const float dl = valid ? lnew - lam : 0.f;
       z += y * dl;
       if (valid) s_lam[r] = lnew;  // every lane stores the same value
-      if constexpr (TAPE) {  // the impulse before the update and the separation the row used
-        if (t_lamb && lane == 0 && r < R) {  // null for the dead groups of a launch
-          t_lamb[it * t_rcap + r] = lam;
-          if (it <= npos) t_seps[it * t_rcap + r] = sep;
-        }
-      }
     }
     if (pos) dz += hit * z;
   }
@@ -547,7 +547,7 @@ __device__ __noinline__ float2 pgs_row_form(const float* s_Y, const int YS, cons
 // per substep; z and dz are rebuilt from the impulses at the end. Returns (z, dz) of the lane and
 // leaves the impulses in s_lam; s_dq is used as scratch. Out of line, like the row form, so the
 // loop gets its own register allocation.
-template <int G, bool TAPE = false>
+template <int G>
 __device__ __noinline__ float2 pgs_delassus_form(const float* s_Y, const int YS, float* s_W, const float4* s_rowc,
                                                  float* s_lam, float* s_dq, const int R, const int Rw_max,
                                                  const int n, const bool isg, const int lane, const int npos,
@@ -579,6 +579,12 @@ __device__ __noinline__ float2 pgs_delassus_form(const float* s_Y, const int YS,
   const float inv_hit = 1.f / hit, inv_h = 1.f / h;
   for (int it = 0; it < npos + nvel; ++it) {
     const bool pos = it < npos;
+    if (t_lamb) {  // taped step: lane s, its row's impulse before this iteration and its separation
+      if (lane < R) {
+        t_lamb[it * t_rcap + lane] = lv;
+        if (it <= npos) t_seps[it * t_rcap + lane] = s_rowc[lane].x + dv;
+      }
+    }
     for (int r = 0; r < Rw_max; ++r) {
       const bool inr = r < R;
       const float4 hc = s_rowc[r];
@@ -599,12 +605,6 @@ __device__ __noinline__ float2 pgs_delassus_form(const float* s_Y, const int YS,
       const float dl = valid ? lnew - lam : 0.f;
       wv += wc * dl;
       if (valid && lane == r) lv = lnew;
-      if constexpr (TAPE) {
-        if (t_lamb && lane == 0 && inr) {
-          t_lamb[it * t_rcap + r] = lam;
-          if (it <= npos) t_seps[it * t_rcap + r] = sep;
-        }
-      }
     }
     if (pos) {
       dv += hit * wv;
@@ -633,7 +633,7 @@ __device__ __noinline__ float2 pgs_delassus_form(const float* s_Y, const int YS,
 // (grp >= n_launch_envs: a dead group, which shadows the last env and never stores); sm is the
 // group's shared arena and rb the base of its contact and row blocks (sm itself, or a private
 // slot of global scratch in the GROWS variant).
-template <int G, bool GROWS, bool BALL = false, bool TAPE = false>
+template <int G, bool GROWS, bool BALL = false>
 __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA, const int grp, float* sm,
                                            float* rb) {
   const EnvTypeTable* __restrict__ T = TA.type;
@@ -642,6 +642,7 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
   const int gi = live ? grp : TA.n_launch_envs - 1;
   const int env = TA.env_ids ? TA.env_ids[gi] : TA.env_first + gi;
   const SmemLayout& Ly = TA.lay;
+  const bool tape_on = TA.tape != nullptr;  // sim_step_taped: record the reverse pass's tape
   int* smi = reinterpret_cast<int*>(sm);
   int* rbi = reinterpret_cast<int*>(rb);
 
@@ -813,10 +814,11 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
   };
 
   for (int sub = 0; sub < A.substeps; ++sub) {
-    // taped instantiation: this env-substep's block of the tape (written by live groups only)
+    // taped step (a tape given): this env-substep's block of the tape, written by live groups only
+    // (the same code and arithmetic as the plain step: the stores are its only difference)
     float* tp = nullptr;
     const TapeLayout& TL = TA.tl;
-    if constexpr (TAPE) {
+    if (tape_on) {
       tp = TA.tape + ((size_t)gi * A.substeps + sub) * TL.words;
       if (live) {
         if (has_dof) { tp[TL.st + 2 * l] = q; tp[TL.st + 2 * l + 1] = qd; }
@@ -1267,7 +1269,7 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
       for (int k = 0; k < 6; ++k) { s_qdd[gd + k] = acc[k] - cc[k]; s_v0[gd + k] = vs[k]; }
     }
     __syncwarp();
-    if constexpr (TAPE) {
+    if (tape_on) {
       if (live && isg) tp[TL.vec + lane] = s_qdd[lane];
     }
 
@@ -1428,7 +1430,7 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
       s_lam[r] = act ? gcache[__float_as_int(hc.w)] : 0.f;
     }
     __syncwarp();
-    if constexpr (TAPE) {  // contact and row lists, L, Y and the warm-start impulses
+    if (tape_on) {  // contact and row lists, L, Y and the warm-start impulses
       if (live) {
         if (lane == 0) {
           int* th = reinterpret_cast<int*>(tp + TL.hdr);
@@ -1445,10 +1447,10 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
           reinterpret_cast<float4*>(tp + TL.rowc)[r] = s_rowc[r];
           tp[TL.rowa + r] = __int_as_float(s_rowa[r]);
           tp[TL.lam0 + r] = s_lam[r];
-          for (int i = 0; i < n; ++i) tp[TL.Y + i * TL.rcap + r] = s_Y[i * YS + r];
+          for (int i = 0; i < n; ++i) tp[TL.Y + i * TL.YT + r] = s_Y[i * YS + r];
         }
         if (isg) {
-          for (int k = 0; k <= lane; ++k) tp[TL.L + lane * n + k] = s_M[lane * MS + k];
+          for (int k = 0; k <= lane; ++k) tp[TL.L + lane * TL.LT + k] = s_M[lane * MS + k];
           tp[TL.Linv + lane] = s_Linv[lane];
         }
       }
@@ -1462,14 +1464,12 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
     __syncwarp();
     if (isg)
       for (int k = lane; k < n; ++k) z0 += s_M[k * MS + lane] * s_vf[k];  // z = L^T v_free
-    if constexpr (TAPE) {
+    if (tape_on) {
       if (live && isg) { tp[TL.vec + n + lane] = s_vf[lane]; tp[TL.vec + 2 * n + lane] = z0; }
     }
     float* t_lamb = nullptr;
     float* t_seps = nullptr;
-    if constexpr (TAPE) {
-      if (live) { t_lamb = tp + TL.lamb; t_seps = tp + TL.seps; }
-    }
+    if (tape_on && live) { t_lamb = tp + TL.lamb; t_seps = tp + TL.seps; }
     const int Rw_max = __reduce_max_sync(kFull, R);
     float z = 0.f, dz = 0.f;
     // The Delassus form serves one env per warp (G = 32: five-level reductions, nothing to share
@@ -1482,14 +1482,14 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
     const int wcap = GROWS ? L * kLinkWords : Ly.ywords - n * YS;
     const bool delassus = G == 32 && !(A.flags & 64) && __all_sync(kFull, R <= G && R * R + R <= wcap);
     if (delassus) {
-      const float2 zd = pgs_delassus_form<G, TAPE>(s_Y, YS, s_W, s_rowc, s_lam, s_dq, R, Rw_max, n, isg, lane, npos,
+      const float2 zd = pgs_delassus_form<G>(s_Y, YS, s_W, s_rowc, s_lam, s_dq, R, Rw_max, n, isg, lane, npos,
                                                    nvel, h, hit, A.bias_coef, A.max_depen_vel, z0,
                                                    t_lamb, t_seps, TL.rcap);
       z = zd.x;
       dz = zd.y;
     } else {
       // s_dq and the row aux words (dead after the Jacobian rows) are the form's scratch
-      const float2 zd = pgs_row_form<G, TAPE>(s_Y, YS, s_rowc, s_lam, s_dq, reinterpret_cast<float*>(s_rowa), R,
+      const float2 zd = pgs_row_form<G>(s_Y, YS, s_rowc, s_lam, s_dq, reinterpret_cast<float*>(s_rowa), R,
                                               Rw_max, n, isg, lane, npos, nvel, h, hit, A.bias_coef,
                                               A.max_depen_vel, z0, t_lamb, t_seps, TL.rcap);
       z = zd.x;
@@ -1511,7 +1511,7 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
       if (isg) { s_vf[lane] = xz; s_dq[lane] = xd; }
     }
     __syncwarp();
-    if constexpr (TAPE) {  // the solve's result in both coordinates, and the final impulses
+    if (tape_on) {  // the solve's result in both coordinates, and the final impulses
       if (live) {
         if (isg) {
           tp[TL.vec + 3 * n + lane] = z;
@@ -1662,7 +1662,7 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
 // One launch per env type: blocks of 128 / G groups, one env per group. In the GROWS variant the
 // group's scratch slot is its index in the launch (the dead groups of the last block own the
 // slots past the launched envs).
-template <int G, bool GROWS, bool BALL = false, bool TAPE = false>
+template <int G, bool GROWS, bool BALL = false>
 __global__ void __launch_bounds__(128, 4) step_kernel(const __grid_constant__ StepArgs A,
                                                      const __grid_constant__ TypeArgs TA) {
   extern __shared__ __align__(16) float smem[];
@@ -1670,7 +1670,7 @@ __global__ void __launch_bounds__(128, 4) step_kernel(const __grid_constant__ St
   const int grp = blockIdx.x * (blockDim.x / G) + grp_blk;
   float* sm = smem + grp_blk * TA.lay.total;
   float* rb = GROWS ? TA.scratch + (size_t)grp * TA.lay.scratch_words : sm;
-  step_group<G, GROWS, BALL, TAPE>(A, TA, grp, sm, rb);
+  step_group<G, GROWS, BALL>(A, TA, grp, sm, rb);
 }
 
 }  // namespace artsim

@@ -405,12 +405,17 @@ class Sim:
     def tape_floats(self, substeps: Optional[int] = None) -> Optional[int]:
         """Floats of one recorded step's tape, or None if the reverse pass does not cover this
         handle (its env types or flags): the derivative then runs in forward mode (step_vjp)."""
-        out = ctypes.c_int64(0)
-        rc = load().sim_tape_size(self.h, int(self.w.substeps if substeps is None else substeps), ctypes.byref(out))
-        if rc in (-1, -4):
-            return None
-        check(rc, "sim_tape_size")
-        return int(out.value)
+        sub = int(self.w.substeps if substeps is None else substeps)
+        cache = self.__dict__.setdefault("_tape_floats", {})
+        if sub not in cache:
+            out = ctypes.c_int64(0)
+            rc = load().sim_tape_size(self.h, sub, ctypes.byref(out))
+            if rc in (-1, -4):
+                cache[sub] = None
+            else:
+                check(rc, "sim_tape_size")
+                cache[sub] = int(out.value)
+        return cache[sub]
 
     def step_taped(self, tape, dt: Optional[float] = None, substeps: Optional[int] = None):
         """sim_step on the handle's views that also records the step's tape (a float32 device
@@ -434,6 +439,44 @@ class Sim:
         b = sim_adjoint_buffers(*self._ptrs(ADJ_FIELDS, bufs))
         check(load().sim_step_adjoint(self.h, ctypes.c_void_p(p), ctypes.byref(b), float(self.w.dt if dt is None else dt),
                                       sub), "sim_step_adjoint")
+
+    def reverse_rollout(self, tapes, acts, grads, g_acts):
+        """The reverse pass of len(acts) steps from the handle's current state: each step re-run with
+        its tape recorded in tapes[k], then the adjoints in reverse order from the final-state
+        gradients grads = (root, dof, cache), the actuation gradients written into g_acts[k].
+        Returns the initial-state gradients. Every buffer is checked once here, then passed to the
+        library as plain addresses (the per-step calls run in a loop of a few microseconds)."""
+        torch = self._torch
+        f32 = (torch.float32,)
+        steps = int(acts.shape[0])
+        need = self.tape_floats()
+        if need is None:
+            raise ValueError("the reverse pass does not cover this handle")
+        tstride = int(tapes.stride(0)) if tapes.dim() > 1 else need
+        self._dev_ptr(tapes, "tapes", f32, need + tstride * (steps - 1))
+        self._dev_ptr(acts, "acts", f32, self.dof_actuation.numel() * steps)
+        self._dev_ptr(g_acts, "g_acts", f32, self.dof_actuation.numel() * steps)
+        views = ("root_state", "dof_state", "impulse_cache")
+        g = [self._mirror_ptr(x, f"grad {v}", v) for x, v in zip(grads, views)]
+        sets = [tuple(torch.empty_like(getattr(self, v)) for v in views) for _ in range(2)]
+        L = load()
+        dt, sub = float(self.w.dt), int(self.w.substeps)
+        t0, nd = tapes.data_ptr(), self.dof_actuation.numel()
+        for k in range(steps):
+            self.dof_actuation.copy_(acts[k])
+            check(L.sim_step_taped(self.h, ctypes.c_void_p(t0 + 4 * tstride * k), dt, sub), "sim_step_taped")
+        b = sim_adjoint_buffers()
+        out = grads
+        for k in range(steps - 1, -1, -1):
+            out = sets[k % 2]
+            b.grad_root_state, b.grad_dof_state, b.grad_impulse_cache = g
+            b.grad_root_state_in, b.grad_dof_state_in, b.grad_impulse_cache_in = [x.data_ptr() for x in out]
+            b.grad_dof_actuation = g_acts.data_ptr() + 4 * nd * k
+            b.status = None
+            check(L.sim_step_adjoint(self.h, ctypes.c_void_p(t0 + 4 * tstride * k), ctypes.byref(b), dt, sub),
+                  "sim_step_adjoint")
+            g = [x.data_ptr() for x in out]
+        return out
 
     def set_root_state_indexed(self, src, actor_idx):
         """src: (n, 13) float32 root states; actor_idx: n int32 actor indices (device tensors)."""
