@@ -85,7 +85,11 @@ __device__ __forceinline__ V3 sym_mv(const float* S, V3 x) {
             S[4] * x.x + S[5] * x.y + S[2] * x.z);
 }
 
-// Per-link record of the reverse arena (kAdjLinkWords words).
+// Stride of the per-DOF 6-vectors of the reverse arena (odd: the lanes of a group that each hold one
+// DOF's vector fall on distinct banks).
+constexpr int kSDS = 7;
+
+// Per-link record of the reverse arena (kAdjLinkWords words, odd for the same reason).
 enum : int {
   kRecVs = 0, kRecCc = 6, kRecIO = 12, kRecH = 18, kRecCw = 21, kRecIcw = 24, kRecM = 30, kRecS = 31,
   kRecIc = 37,   // composite inertia m | h 3 | I_O 6 (10 words)
@@ -140,11 +144,10 @@ __device__ __forceinline__ void lt_solve_lane(const float* L, const int LS, cons
     const float xk = y[0] * linv[k];
     base[k * stride] = xk;
     const float* Lk = L + k * LS;
+    // every register shifts down one place; the m <= k ones also take their L_k,k-m term (the
+    // others are past the solution's start: no branch, the load clamped inside row k)
 #pragma unroll
-    for (int m = 1; m < G; ++m) {
-      if (m > k) break;
-      y[m - 1] = y[m] - Lk[k - m] * xk;
-    }
+    for (int m = 1; m < G; ++m) y[m - 1] = y[m] - ((m <= k) ? Lk[m <= k ? k - m : 0] * xk : 0.f);
   }
 }
 
@@ -222,6 +225,7 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
   float* s_FMb = sm + al.FMb;
   float* s_Sb = sm + al.Sb;
   float* s_link = sm + al.link;
+  float* s_sink = sm + al.bar + 2;  // a scratch word after the mbarrier (the arena reserves 4 words there)
   auto V = [&](int k) -> float* {
     return k < 7 ? img + TL.vec + k * n : (k == kVLinv ? img + TL.Linv : s_vec + (k - kVVb) * n);
   };
@@ -416,13 +420,13 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
       // motion subspace per generalized DOF (unit columns for a floating root)
       if (has_dof) {
 #pragma unroll
-        for (int k = 0; k < 6; ++k) s_SD[6 * gd + k] = S[k];
+        for (int k = 0; k < 6; ++k) s_SD[kSDS * gd + k] = S[k];
       }
       if (free_root) {
 #pragma unroll
         for (int c = 0; c < 6; ++c)
 #pragma unroll
-          for (int k = 0; k < 6; ++k) s_SD[6 * (gd + c) + k] = (k == c) ? 1.f : 0.f;
+          for (int k = 0; k < 6; ++k) s_SD[kSDS * (gd + c) + k] = (k == c) ? 1.f : 0.f;
       }
     }
 
@@ -521,7 +525,7 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
           const float dbr = s_db[rr], iab = s_invAb[rr], ln_cur = s_lam[nrow], lbn = s_lamb[nrow];
           const float D = valid ? la - lbf : 0.f;
           const float y = (isg && inr) ? s_Y[lane * YS + rr] : 0.f;
-          const float ybar = (isg && inr) ? s_Yb[lane * YS + rr] : 0.f;
+          const float ybar = isg ? s_Yb[lane * YS + rr] : 0.f;  // (rr's own value: written back unchanged)
           const float zbef = z - y * D;
           // two group reductions in one pass: Y_r . z_bar and Y_r . z (before the update)
           float Db = y * zb, yz = y * zbef;
@@ -543,25 +547,23 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
           const bool cap = !(t1 < vmax);
           const float tgt = pos ? ((sep >= 0.f) ? -sep * inv_hit : (cap ? vmax : t1)) : ((sep > 0.f) ? -sep * inv_h : 0.f);
           const float dts = pos ? ((sep >= 0.f) ? -inv_hit : (cap ? 0.f : -beta * inv_hit)) : ((sep > 0.f) ? -inv_h : 0.f);
-          const float argb = clamped ? 0.f : ap;
+          const float argb = (clamped || !valid) ? 0.f : ap;
           const float nbar = hi ? hc.x * ap : (lo ? -hc.x * ap : 0.f);
           const float yzb = -argb * invA;
           const float iadd = argb * ((fric ? 0.f : tgt) - yz);
           const float sepb = fric ? 0.f : argb * invA * dts;
-          if (valid && isg) {
-            s_Yb[lane * YS + rr] = ybar + D * zb + yzb * zbef + sepb * dzs;
-            zb += yzb * y;
-            dzb += sepb * y;
-          }
-          if (valid) z = zbef;
+          // (an invalid row, y = 0 and argb = 0, leaves every value as it was: the stores below are
+          // unconditional, the friction store of a non-friction row goes to a sink word)
+          if (isg) s_Yb[lane * YS + rr] = valid ? ybar + D * zb + yzb * zbef + sepb * dzs : ybar;
+          zb += yzb * y;
+          dzb += sepb * y;
+          z = zbef;
           __syncwarp();  // every lane has read what the stores below overwrite
-          if (valid) {
-            s_lam[r] = lbf;
-            s_lamb[r] = argb - Db;
-            s_db[r] = dbr + sepb;
-            s_invAb[r] = iab + iadd;
-            if (fric) s_lamb[nrow] = lbn + nbar;
-          }
+          s_lam[rr] = valid ? lbf : la;
+          s_lamb[rr] = valid ? argb - Db : lbar;
+          s_db[rr] = dbr + sepb;
+          s_invAb[rr] = iab + iadd;
+          *((valid && fric) ? s_lamb + nrow : s_sink) = lbn + nbar;
           __syncwarp();
         }
       }
@@ -602,19 +604,14 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
       for (int r = 0; r < R; ++r) {
         const float yb = s_Yb[lane * YS + r];
 #pragma unroll
-        for (int j = 0; j < G; ++j)
-          if (j < n) p[j] -= yb * s_Y[j * YS + r];
+        for (int j = 0; j < G; ++j) p[j] -= yb * s_Y[(j < n ? j : 0) * YS + r];  // j >= n: unused
       }
       const float zf = V(kVZf)[lane], dzf = V(kVDzf)[lane], z0 = V(kVZ0)[lane];
 #pragma unroll
       for (int j = 0; j < G; ++j) {
-        if (j >= n) break;
-        float v = 0.f;
-        if (j <= lane) {
-          v = p[j] - zf * V(kVZb6)[j] - dzf * V(kVDzb6)[j] + z0 * V(kVZb0)[j];
-          if (j == lane) v *= 0.5f;
-        }
-        s_Mb[lane * LS + j] = v;
+        const int jj = j < n ? j : 0;
+        const float v = p[j] - zf * V(kVZb6)[jj] - dzf * V(kVDzb6)[jj] + z0 * V(kVZb0)[jj];
+        if (j < n) s_Mb[lane * LS + j] = (j < lane) ? v : ((j == lane) ? 0.5f * v : 0.f);
       }
     }
     __syncwarp();
@@ -661,25 +658,51 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
     __syncwarp();
     if (isg) {
       const float* ic = s_link + kAdjLinkWords * T->dof_link[lane] + kRecIc;
-      inertia_mul(ic[0], v3(ic[1], ic[2], ic[3]), ic + 4, s_SD + 6 * lane, s_FM + 6 * lane);
+      inertia_mul(ic[0], v3(ic[1], ic[2], ic[3]), ic + 4, s_SD + kSDS * lane, s_FM + kSDS * lane);
     }
     __syncwarp();
-    // ---- reverse of the composite-rigid-body algorithm and of the contact rows (DOF mode) ----
+    // ---- contact rows (row mode): the contact-point adjoint x_bar = sum_g J_bar_rg (k x a_g), + d_bar
+    // e_z for a normal row; and, for the gather below, the row's [x x k; k] and the mask of the
+    // generalized DOFs it acts on (0 for a row without response), in the dead impulse-history block ----
+    float* s_fr = s_lambef;  // 7 x RC words: [x x k; k] (6) | DOF mask; the history is read
+    for (int r = n_lim + lane; r < R; r += G) {
+      const float4 hc = s_rowc[r];
+      const int a = s_rowa[r];
+      const int c = a & 0xff, dir = (a >> 8) & 3;
+      const unsigned anc = (hc.y > 0.f) ? T->anc[s_coni[3 * TL.ccap + c]] : 0u;
+      const V3 k = dir == 0 ? v3(0.f, 0.f, 1.f) : (dir == 1 ? v3(1.f, 0.f, 0.f) : v3(0.f, 1.f, 0.f));
+      const V3 x = v3(s_con[c], s_con[TL.ccap + c], s_con[2 * TL.ccap + c]);
+      V3 sa = v3(0.f, 0.f, 0.f);
+      for (int gg = 0; gg < n; ++gg) {
+        const float jb = ((anc >> gg) & 1u) ? s_Yb[gg * YS + r] : 0.f;
+        sa = sa + v3(s_SD[kSDS * gg], s_SD[kSDS * gg + 1], s_SD[kSDS * gg + 2]) * jb;
+      }
+      V3 xb = cross(k, sa);
+      if (dir == 0 && hc.y > 0.f) xb.z += s_db[r];
+      s_xb[3 * r] = xb.x; s_xb[3 * r + 1] = xb.y; s_xb[3 * r + 2] = xb.z;
+      const V3 xk = cross(x, k);
+      s_fr[r] = xk.x; s_fr[RC + r] = xk.y; s_fr[2 * RC + r] = xk.z;
+      s_fr[3 * RC + r] = k.x; s_fr[4 * RC + r] = k.y; s_fr[5 * RC + r] = k.z;
+      s_fr[6 * RC + r] = __uint_as_float(anc);
+    }
+    __syncwarp();
+    // ---- reverse of the composite-rigid-body algorithm and the contact rows' S adjoints (DOF mode;
+    // uniform trip counts, masks instead of branches) ----
     if (isg) {
       const int i = lane;
       const unsigned anc_i = T->anc[T->dof_link[i]];
       float Fb[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, Sb[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      for (int j = 0; j <= i; ++j) {
-        if (!((anc_i >> j) & 1u)) continue;
-        const float w = (j == i) ? s_Mb[i * LS + i] : s_Mb[i * LS + j] + s_Mb[j * LS + i];
+      for (int j = 0; j < n; ++j) {
+        // F_bar_i = sum_{j <= i on i's path} w_ij S_j; S_bar_i = sum_{k >= i, i on k's path} w_ki F_k
+        const float mij = s_Mb[i * LS + j], mji = s_Mb[j * LS + i];
+        const float w = (j == i) ? mij : mij + mji;
+        const float wf = (j <= i && ((anc_i >> j) & 1u)) ? w : 0.f;
+        const float ws = (j >= i && ((T->anc[T->dof_link[j]] >> i) & 1u)) ? w : 0.f;
 #pragma unroll
-        for (int k = 0; k < 6; ++k) Fb[k] += w * s_SD[6 * j + k];
-      }
-      for (int kk = i; kk < n; ++kk) {
-        if (!((T->anc[T->dof_link[kk]] >> i) & 1u)) continue;
-        const float w = (kk == i) ? s_Mb[i * LS + i] : s_Mb[kk * LS + i] + s_Mb[i * LS + kk];
-#pragma unroll
-        for (int k = 0; k < 6; ++k) Sb[k] += w * s_FM[6 * kk + k];
+        for (int k = 0; k < 6; ++k) {
+          Fb[k] += wf * s_SD[kSDS * j + k];
+          Sb[k] += ws * s_FM[kSDS * j + k];
+        }
       }
       {
         const float* ic = s_link + kAdjLinkWords * T->dof_link[i] + kRecIc;
@@ -690,37 +713,13 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
       }
       // contact rows: J_ri = S_i . [x x k; k] on the contact link's path
       for (int r = n_lim; r < R; ++r) {
-        const float4 hc = s_rowc[r];
-        if (!(hc.y > 0.f)) continue;
-        const int a = s_rowa[r];
-        const int c = a & 0xff, dir = (a >> 8) & 3;
-        if (!((T->anc[s_coni[3 * TL.ccap + c]] >> i) & 1u)) continue;
-        const float jb = s_Yb[i * YS + r];
-        const V3 x = v3(s_con[c], s_con[TL.ccap + c], s_con[2 * TL.ccap + c]);
-        const V3 k = dir == 0 ? v3(0.f, 0.f, 1.f) : (dir == 1 ? v3(1.f, 0.f, 0.f) : v3(0.f, 1.f, 0.f));
-        const V3 xk = cross(x, k);
-        Sb[0] += jb * xk.x; Sb[1] += jb * xk.y; Sb[2] += jb * xk.z;
-        Sb[3] += jb * k.x; Sb[4] += jb * k.y; Sb[5] += jb * k.z;
+        const unsigned mask = __float_as_uint(s_fr[6 * RC + r]);
+        const float jb = ((mask >> i) & 1u) ? s_Yb[i * YS + r] : 0.f;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) Sb[k] += jb * s_fr[k * RC + r];
       }
 #pragma unroll
-      for (int k = 0; k < 6; ++k) { s_Sb[6 * i + k] = Sb[k]; s_FMb[6 * i + k] = Fb[k]; }
-    }
-    // contact-point adjoints per row (row mode): x_bar = sum_g J_bar_rg (k x a_g), + d_bar e_z
-    for (int r = n_lim + lane; r < R; r += G) {
-      const float4 hc = s_rowc[r];
-      V3 xb = v3(0.f, 0.f, 0.f);
-      if (hc.y > 0.f) {
-        const int a = s_rowa[r];
-        const int c = a & 0xff, dir = (a >> 8) & 3;
-        const unsigned anc = T->anc[s_coni[3 * TL.ccap + c]];
-        const V3 k = dir == 0 ? v3(0.f, 0.f, 1.f) : (dir == 1 ? v3(1.f, 0.f, 0.f) : v3(0.f, 1.f, 0.f));
-        V3 sa = v3(0.f, 0.f, 0.f);
-        for (int gg = 0; gg < n; ++gg)
-          if ((anc >> gg) & 1u) sa = sa + v3(s_SD[6 * gg], s_SD[6 * gg + 1], s_SD[6 * gg + 2]) * s_Yb[gg * YS + r];
-        xb = cross(k, sa);
-        if (dir == 0) xb.z += s_db[r];
-      }
-      s_xb[3 * r] = xb.x; s_xb[3 * r + 1] = xb.y; s_xb[3 * r + 2] = xb.z;
+      for (int k = 0; k < 6; ++k) { s_Sb[kSDS * i + k] = Sb[k]; s_FMb[kSDS * i + k] = Fb[k]; }
     }
     __syncwarp();
 
@@ -729,7 +728,7 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
     float wr[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // pose wrench of the link's attached quantities
     if (isl) {
       for (int gg = 0; gg < n; ++gg)
-        if (T->dof_link[gg] == l) inertia_outer(s_FMb + 6 * gg, s_SD + 6 * gg, IOb, hbar);
+        if (T->dof_link[gg] == l) inertia_outer(s_FMb + kSDS * gg, s_SD + kSDS * gg, IOb, hbar);
       for (int c = 0; c < n_con; ++c) {
         if (s_coni[3 * TL.ccap + c] != l) continue;
         const int rn = n_lim + c, rf = n_lim + n_con + 2 * c;
@@ -764,7 +763,7 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
     float Sbar[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (has_dof) {
 #pragma unroll
-      for (int k = 0; k < 6; ++k) Sbar[k] = s_Sb[6 * gd + k];
+      for (int k = 0; k < 6; ++k) Sbar[k] = s_Sb[kSDS * gd + k];
     }
     float vs[6], cc[6], io[6];
 #pragma unroll

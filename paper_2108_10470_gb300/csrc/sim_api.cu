@@ -1112,6 +1112,8 @@ TapeLayout tape_layout(const TypePlan& tp, int npos, int nvel) {
   t.Y = o; o += n * t.YT;
   t.lamb = o; o += t.iters * t.rcap;
   t.seps = o; o += (npos + 1) * t.rcap;
+  // the adjoint reuses these two blocks, once read, as 7 words per row: keep at least that many
+  o = std::max(o, t.lamb + 7 * t.rcap);
   t.words = al4i(o);
   return t;
 }
@@ -1134,10 +1136,10 @@ AdjLayout adj_layout(const TypePlan& tp, int npos, int nvel) {
   a.invAb = o; o += rc;
   a.xb = o; o += 3 * rc;
   a.vec = o; o += kAdjVecs * n;
-  a.SD = o; o += 6 * n;
-  a.FM = o; o += 6 * n;
-  a.FMb = o; o += 6 * n;
-  a.Sb = o; o += 6 * n;
+  a.SD = o; o += 7 * n;   // 6-vectors at an odd stride of 7
+  a.FM = o; o += 7 * n;
+  a.FMb = o; o += 7 * n;
+  a.Sb = o; o += 7 * n;
   a.link = o; o += kAdjLinkWords * T.n_links;
   a.total = al4i(o);
   return a;

@@ -187,12 +187,13 @@ struct AdjLayout {
   int lamb, db, invAb;  // rcap each
   int xb;           // 3 x rcap: adjoint of each row's contact point
   int vec;          // kAdjVecs x n (see adjoint_kernel.cuh)
-  int SD, FM, FMb, Sb;  // 6 x n each: motion subspace, composite-inertia force, its adjoint, S adjoint
+  int SD, FM, FMb, Sb;  // 7 x n each (6-vectors at an odd stride): motion subspace, composite-inertia
+                        // force, its adjoint, S adjoint
   int link;         // kAdjLinkWords x L
   int total;        // words per env (multiple of 4)
 };
 constexpr int kAdjVecs = 6;
-constexpr int kAdjLinkWords = 56;
+constexpr int kAdjLinkWords = 57;
 
 // Arguments of the reverse pass of one recorded step.
 struct AdjArgs {

@@ -41,7 +41,7 @@ STATE = ("root_state", "dof_state", "impulse_cache", "net_contact_force", "conta
                                          ("humanoid", 37, "row_solver"), ("mixed_no_hand", 48, "per_type")])
 def test_taped_step_is_the_step(name, n, plan):
     """Six steps of sim_step and of sim_step_taped from the same seeded state: every view equal bit
-    for bit (the taped instantiation only adds stores)."""
+    for bit (the same kernels, given a tape pointer: the tape stores are their only difference)."""
     import torch
     from paper_2108_10470_gb300 import sim
     if name == "mixed_no_hand":
@@ -234,3 +234,38 @@ def test_uncovered_handles_report_no_tape(name):
     s, _ = make_sim(name, w)
     assert s.tape_floats() is None
     s.destroy()
+
+
+def test_reverse_vjp_full_size_sampled_envs():
+    """The differentiation workload's size and launch (1024 Ant-like envs, the reverse pass's
+    per-type launch): one step's VJP over all envs, 16 of them (strided) checked against the oracle's
+    derivative in every input direction."""
+    w = W.ant_workload(1024)
+    r, d, c, a = warm(w, seed=12)
+    rng = np.random.default_rng(13)
+    gout = output_gradient(w, r, d, c, rng)
+    s, ctl = make_sim("ant", w)
+    g = gpu_vjp(s, r, d, c, a, gout)
+    s.destroy()
+    assert not g["status"].any()
+    idx = list(range(0, 1024, 64))
+    ws = w.subset(idx)
+    nj = 8
+    rows = lambda x, per: np.concatenate([x[e * per:(e + 1) * per] for e in idx])
+    rs, ds, cs, as_ = r[idx], rows(d, nj), c[idx], rows(a, nj)
+    gs = (gout[0][idx], rows(gout[1], nj), gout[2][idx])
+    g32 = tuple(x.astype(np.float32).astype(np.float64) for x in gs)
+    dirs = directions(ws, rs, cs)
+    ref = oracle_grad(ws, rs, ds, cs, as_, g32, dirs, None)
+    probes = [oracle_grad(ws, rs, ds, cs, as_, g32, dirs, None, single=True, nudge=x) for x in (None, 1)]
+    gsub = {"grad_root_state_in": g["grad_root_state_in"][idx], "grad_dof_state_in": rows(g["grad_dof_state_in"], nj),
+            "grad_dof_actuation": rows(g["grad_dof_actuation"], nj), "grad_impulse_cache_in": g["grad_impulse_cache_in"][idx]}
+    got = gpu_grad(ws, gsub, rs, dirs)
+    bad = []
+    for e in range(ws.n_envs):
+        scale = max(1.0, np.abs(ref[e]).max())
+        spread = max(np.abs(p[e] - ref[e]).max() for p in probes)
+        if np.abs(got[e] - ref[e]).max() > 1e-3 * scale + K_COND * spread:
+            bad.append(idx[e])
+    print(f"ant x1024 (16 sampled envs, {len(dirs)} directions each): {len(bad)} outside the bound {bad}")
+    assert len(bad) <= 1, bad
