@@ -28,8 +28,9 @@
 //    position and rotational inertia), and a joint's position adjoint is S . (wrenches summed over
 //    its subtree), the root rotation's the angular part over the whole actor.
 // Supported: floating and fixed roots, revolute, prismatic and fixed joints, ground contacts of
-// spheres, capsules and boxes, joint limits, damping, armature, joint drives. (Tendons, ball joints,
-// shape pairs and external body forces use the forward-mode derivative kernel.)
+// spheres, capsules and boxes, joint limits, damping, armature, joint drives, fixed tendons (springs
+// and length-limit rows) and external body forces (their values constants of the derivative). (Ball
+// joints and shape pairs use the forward-mode derivative kernel.)
 #pragma once
 #include "step_kernel.cuh"
 
@@ -88,6 +89,8 @@ __device__ __forceinline__ V3 sym_mv(const float* S, V3 x) {
 // Stride of the per-DOF 6-vectors of the reverse arena (odd: the lanes of a group that each hold one
 // DOF's vector fall on distinct banks).
 constexpr int kSDS = 7;
+
+constexpr int SIM_STEP_BODY_FORCES = 8;  // StepArgs::flags bit: external body forces every substep
 
 // Per-link record of the reverse arena (kAdjLinkWords words, odd for the same reason).
 enum : int {
@@ -617,7 +620,8 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
     __syncwarp();
     // ---- Jacobian-row adjoints J_bar_r = L^-T Y_bar_r, in place (row mode, contact rows) ----
     for (int r = lane; r < R; r += G) {
-      if (!(s_rowc[r].y > 0.f) || (__float_as_int(s_rowc[r].z) & 3) == kRowLimit) continue;
+      const int kind = __float_as_int(s_rowc[r].z) & 3;
+      if (!(s_rowc[r].y > 0.f) || kind == kRowLimit || kind == kRowTendon) continue;  // constant J
       lt_solve_lane<G>(s_L, LS, s_linv, n, s_Yb + r, YS);
     }
     // ---- M_bar' = L^-T P L^-1 (its symmetric part is the joint-space inertia's adjoint) ----
@@ -741,11 +745,32 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
         const V3 m = cross(xf, xb);
         wr[0] += m.x; wr[1] += m.y; wr[2] += m.z; wr[3] += xb.x; wr[4] += xb.y; wr[5] += xb.z;
       }
-      if (has_dof)
-        for (int r = 0; r < n_lim; ++r) {
+      if (has_dof) {
+        for (int r = 0; r < n_lim; ++r) {  // joint limits: d = q - lo or hi - q
           const int a = s_rowa[r];
-          if ((a & 0xff) == gd && s_rowc[r].y > 0.f) qb += ((a >> 8) & 1) ? -s_db[r] : s_db[r];
+          if ((__float_as_int(s_rowc[r].z) & 3) == kRowLimit && (a & 0xff) == gd && s_rowc[r].y > 0.f)
+            qb += ((a >> 8) & 1) ? -s_db[r] : s_db[r];
         }
+        // fixed tendons (length l = sum c q): the limit rows' d = l - lo or hi - l, and the spring
+        // -k (l - rest) - d l_dot acting on each of the tendon's joints with its coefficient
+        for (int t = 0; t < T->n_tendons; ++t) {
+          float mine = 0.f, fbar = 0.f;
+          for (int k = 0; k < T->ten_n[t]; ++k) {
+            const int lk = T->ten_link[t][k];
+            const float c = T->ten_coef[t][k];
+            if (lk == l) mine += c;
+            fbar += c * V(kVCb)[T->gdof[lk]];  // adjoint of the tendon force: sum of c tau_bar
+          }
+          if (mine == 0.f) continue;
+          qb -= T->ten_k[t] * mine * fbar;
+          qdb -= T->ten_d[t] * mine * fbar;
+          for (int r = 0; r < n_lim; ++r) {
+            const int a = s_rowa[r];
+            if ((__float_as_int(s_rowc[r].z) & 3) == kRowTendon && (a & 0xff) == t && s_rowc[r].y > 0.f)
+              qb += ((a >> 8) & 1) ? -mine * s_db[r] : mine * s_db[r];
+          }
+        }
+      }
       if (is_root)
         for (int c = 0; c < n_con; ++c)
           if (T->actor[s_coni[3 * TL.ccap + c]] == T->actor[l]) rpb[2] += s_db[n_lim + c];
@@ -782,12 +807,23 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
     float ag[6] = {acc[0], acc[1], acc[2], acc[3] - g.x, acc[4] - g.y, acc[5] - g.z};
     float u[6], Fc[6];
     inertia_mul(m_l, h_l, io, vs, u);
+    // external force and torque at the COM (world axes; constants of the derivative), as in the step
+    V3 fe = v3(0.f, 0.f, 0.f), te = fe;
+    const int bdy = isl ? T->body[l] : -1;
+    if ((A.flags & SIM_STEP_BODY_FORCES) && bdy >= 0) {
+      const float* bf = A.body_force + (size_t)(A.env_body_base[env] + bdy) * 6;
+      fe = v3(bf[0], bf[1], bf[2]);
+      te = v3(bf[3], bf[4], bf[5]);
+    }
     {
       float ia[6], vu[6];
       inertia_mul(m_l, h_l, io, ag, ia);
       crf6(vs, u, vu);
+      const V3 cwl = isl ? v3(rec[kRecCw], rec[kRecCw + 1], rec[kRecCw + 2]) : v3(0.f, 0.f, 0.f);
+      const V3 na = cross(cwl, fe) + te;
+      const float fx[6] = {na.x, na.y, na.z, fe.x, fe.y, fe.z};
 #pragma unroll
-      for (int k = 0; k < 6; ++k) Fc[k] = isl ? ia[k] + vu[k] : 0.f;
+      for (int k = 0; k < 6; ++k) Fc[k] = isl ? ia[k] + vu[k] - fx[k] : 0.f;
     }
     inward6(Fc);
     float fb[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -802,6 +838,8 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
     }
     outward(fb, 6);
     float accb[6], vsb[6];
+    // adjoint of the COM position from the external force's moment -(c x F): f_bar_ang x F
+    const V3 cwb_ext = cross(v3(fb[0], fb[1], fb[2]), fe);
     {
       float ub[6], t[6];
       crm6(vs, fb, ub);
@@ -861,7 +899,7 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
       const V3 cw = v3(rec[kRecCw], rec[kRecCw + 1], rec[kRecCw + 2]);
       const float* icw = rec + kRecIcw;
       const float tr = IOb[0] + IOb[1] + IOb[2];
-      const V3 gc = (cw * (2.f * tr) - sym_mv(IOb, cw) * 2.f) * m_l + v3(hbar[0], hbar[1], hbar[2]) * m_l;
+      const V3 gc = (cw * (2.f * tr) - sym_mv(IOb, cw) * 2.f) * m_l + v3(hbar[0], hbar[1], hbar[2]) * m_l + cwb_ext;
       // B = IOb Icw; vee(B - B^T) = 2 (B21 - B12, B02 - B20, B10 - B01)
       const float B01 = IOb[0] * icw[3] + IOb[3] * icw[1] + IOb[4] * icw[5];
       const float B02 = IOb[0] * icw[4] + IOb[3] * icw[5] + IOb[4] * icw[2];

@@ -1147,16 +1147,12 @@ AdjLayout adj_layout(const TypePlan& tp, int npos, int nvel) {
 
 constexpr int kAdjThreads = 64;
 
-// The reverse pass covers env types without tendons, ball joints and shape pairs, in steps
-// without external body forces, whose adjoint arena fits a CTA.
+// The reverse pass covers env types without ball joints and shape pairs whose adjoint arena fits a
+// CTA.
 int reverse_supported(const sim_s* h) {
-  if (h->params.flags & SIM_FLAG_BODY_FORCES) {
-    g_last_error = "reverse pass: steps with external body forces use the forward-mode derivative";
-    return SIM_ERR_INVALID_ARG;
-  }
   for (const TypePlan& tp : h->types) {
-    if (tp.tab.n_tendons > 0 || tp.tab.has_ball || tp.tab.n_pairs > 0) {
-      g_last_error = "reverse pass: env types with tendons, ball joints or shape pairs use the forward-mode derivative";
+    if (tp.tab.has_ball || tp.tab.n_pairs > 0) {
+      g_last_error = "reverse pass: env types with ball joints or shape pairs use the forward-mode derivative";
       return SIM_ERR_INVALID_ARG;
     }
     const AdjLayout al = adj_layout(tp, h->params.pos_iters, h->params.vel_iters);

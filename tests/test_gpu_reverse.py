@@ -11,7 +11,7 @@ which uses them where they cover the handle) against the FP64 oracle's forward-m
   An env whose FP32 evaluation takes a different branch (a clamp or target within rounding of its
   threshold) may deviate: at most one env per test.
 * The reverse and the forward-mode GPU evaluations agree (the second, independent kernel).
-* Handles the reverse pass does not cover report no tape size.
+* Handles the reverse pass does not cover (shape pairs, ball joints) report no tape size.
 """
 import numpy as np
 import pytest
@@ -170,7 +170,8 @@ def output_gradient(w, r, d, c, rng):
     return gout
 
 
-@pytest.mark.parametrize("name,n", [("ant", 40), ("humanoid", 16), ("cartpole", 32), ("driven_ant", 24)])
+@pytest.mark.parametrize("name,n", [("ant", 40), ("humanoid", 16), ("cartpole", 32), ("driven_ant", 24),
+                                    ("tendon_ant", 24), ("pushed_ant", 24)])
 def test_reverse_vjp_matches_oracle_derivative(name, n):
     w = WORKLOADS[name](n)
     r, d, c, a = warm(w, seed=5)
@@ -200,24 +201,29 @@ def test_reverse_vjp_matches_oracle_derivative(name, n):
     assert len(bad) <= 1, bad
 
 
-@pytest.mark.parametrize("name,n", [("ant", 40), ("humanoid", 16), ("driven_ant", 24)])
+@pytest.mark.parametrize("name,n", [("ant", 40), ("humanoid", 16), ("driven_ant", 24), ("tendon_ant", 24),
+                                    ("pushed_ant", 24)])
 def test_reverse_and_forward_mode_agree(name, n):
     """The reverse pass against the forward-mode kernel (SIM_FLAG_TANGENT_VJP) on the same inputs:
     two FP32 evaluations of the same derivative; the quaternion gradient compared along the sphere."""
+    import torch
     from paper_2108_10470_gb300 import sim
     w = WORKLOADS[name](n)
     r, d, c, a = warm(w, seed=7)
     rng = np.random.default_rng(8)
     gout = output_gradient(w, r, d, c, rng)
     s, ctl = make_sim(name, w)
+    assert s.tape_floats() is not None
     g_rev = gpu_vjp(s, r, d, c, a, gout)
     s.destroy()
-    w_f = WORKLOADS[name](n)
-    s = sim.Sim(w_f, flags=sim.SIM_FLAG_TANGENT_VJP)
-    if ctl:
-        import torch
-        s.dof_position_target.copy_(torch.from_numpy(ctl["pos_target"].astype(np.float32)))
-        s.dof_velocity_target.copy_(torch.from_numpy(ctl["vel_target"].astype(np.float32)))
+    flags = sim.SIM_FLAG_TANGENT_VJP | (sim.SIM_FLAG_BODY_FORCES if name == "pushed_ant" else 0)
+    s = sim.Sim(WORKLOADS[name](n), flags=flags)
+    t32 = lambda x: torch.from_numpy(x.astype(np.float32))
+    if ctl and "pos_target" in ctl:
+        s.dof_position_target.copy_(t32(ctl["pos_target"]))
+        s.dof_velocity_target.copy_(t32(ctl["vel_target"]))
+    if ctl and "body_force" in ctl:
+        s.rigid_body_force.copy_(t32(ctl["body_force"]))
     g_fwd = gpu_vjp(s, r, d, c, a, gout)
     s.destroy()
     dirs = directions(w, r, c)
@@ -227,9 +233,9 @@ def test_reverse_and_forward_mode_agree(name, n):
     assert (rel <= 1e-2).mean() >= 0.95 and np.median(rel) <= 1e-3
 
 
-@pytest.mark.parametrize("name", ["hand", "tendon_ant", "ball_ant", "pushed_ant"])
+@pytest.mark.parametrize("name", ["hand", "hand_tendon", "ball_ant"])
 def test_uncovered_handles_report_no_tape(name):
-    """Shape pairs, tendons, ball joints and external body forces are differentiated in forward mode."""
+    """Shape pairs and ball joints are differentiated in forward mode."""
     w = WORKLOADS[name](4)
     s, _ = make_sim(name, w)
     assert s.tape_floats() is None
