@@ -536,8 +536,11 @@ def configs_measure(dev, peak_tflops, warm=20, steps=100):
 def adjoint_measure(dev, n_envs=1024, steps=64, checkpoint=16, reps=2):
     """Adjoint throughput on the differentiable-rollout workload: 1024 Ant-like envs, 64 env-steps,
     loss = mean final root x-velocity, gradients w.r.t. every action and the initial DOF state
-    (autograd rollout with a checkpoint every 16 steps). value = env-steps differentiated per second
-    of the backward pass (which re-runs each segment forward, then applies the step adjoints)."""
+    (autograd rollout in segments of 16 steps). value = env-steps differentiated per second of the
+    backward pass under the rollout's default memory policy (the forward pass keeps every step's
+    tape when the rollout's tapes take at most a quarter of the free device memory: here 1.2 GB);
+    the checkpointing policy (each segment re-run with its tapes recorded in the backward pass) is
+    measured beside it."""
     import torch
 
     from paper_2108_10470_gb300 import autograd as AG, sim, workloads as W
@@ -550,30 +553,56 @@ def adjoint_measure(dev, n_envs=1024, steps=64, checkpoint=16, reps=2):
     d0 = torch.from_numpy(dof).to(dev).requires_grad_(True)
     c0 = torch.zeros((n_envs, s.cache_len), device=dev)
     A = torch.from_numpy(acts).to(dev).requires_grad_(True)
-    fwd, bwd = [], []
-    for rep in range(reps + 1):
-        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-        e[0].record()
-        rf, _, _ = AG.rollout(s, r0, d0, c0, A, checkpoint=checkpoint)
-        loss = rf[:, 7].mean()
-        e[1].record()
-        loss.backward()
-        e[2].record()
-        torch.cuda.synchronize()
-        if rep > 0:
-            fwd.append(e[0].elapsed_time(e[1]))
-            bwd.append(e[1].elapsed_time(e[2]))
-        d0.grad = None
-        A.grad = None
+
+    def timed(keep):
+        fwd, bwd = [], []
+        for rep in range(reps + 1):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record()
+            rf, _, _ = AG.rollout(s, r0, d0, c0, A, checkpoint=checkpoint, keep_tapes=keep)
+            loss = rf[:, 7].mean()
+            e[1].record()
+            loss.backward()
+            e[2].record()
+            torch.cuda.synchronize()
+            if rep > 0:
+                fwd.append(e[0].elapsed_time(e[1]))
+                bwd.append(e[1].elapsed_time(e[2]))
+            d0.grad = None
+            A.grad = None
+        return statistics.median(fwd), statistics.median(bwd)
+
+    kept = AG.keep_tapes_by_default(s, steps)
+    f_ms, b_ms = timed(None)
+    rf_ms, rb_ms = timed(False)
     s.destroy()
-    f_ms, b_ms = statistics.median(fwd), statistics.median(bwd)
     return {"value": n_envs * steps / (b_ms / 1e3), "unit": "adjoint env-steps/s",
             "workload": f"Ant-like, {n_envs} envs, {steps} env-steps, loss = mean final root x-velocity, gradients "
-                        f"w.r.t. actions and initial DOF state, checkpoint every {checkpoint} steps",
+                        f"w.r.t. actions and initial DOF state, segments of {checkpoint} steps",
+            "policy": "tapes kept from the forward pass" if kept else "segments recomputed (checkpointing)",
             "forward_ms": f_ms, "backward_ms": b_ms, "backward_over_forward": b_ms / f_ms,
-            "method": ("reverse pass: each segment re-run with its tapes recorded (sim_step_taped), then the "
-                       "steps' adjoints (sim_step_adjoint) in reverse order" if s_reverse else
+            "forward_plus_backward_ms": f_ms + b_ms,
+            "recompute": {"forward_ms": rf_ms, "backward_ms": rb_ms, "backward_over_forward": rb_ms / rf_ms,
+                          "forward_plus_backward_ms": rf_ms + rb_ms},
+            "method": ("reverse pass: sim_step_taped records each step's tape (in the forward pass when the tapes "
+                       "are kept, else in the backward pass's re-run of each segment), sim_step_adjoint applies "
+                       "the steps' adjoints in reverse order" if s_reverse else
                        "forward-mode dual kernel (one env per warp), vector-Jacobian product per env-step")}
+
+
+def run_adjoint_only(local_rank):
+    """The adjoint measurement alone (one GPU): the command the adjoint kernel's profiles are taken on."""
+    import torch
+
+    from paper_2108_10470_gb300 import build
+
+    build.build_library()
+    torch.cuda.set_device(local_rank)
+    adj = adjoint_measure(torch.device("cuda", local_rank))
+    line = {"metric": "adjoint env-steps/s (Ant-like, 1024 envs, 64-step rollout gradient)", "value": adj["value"],
+            "unit": adj["unit"], "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": adj["workload"]}, "adjoint": adj}
+    print(json.dumps(line), flush=True)
 
 
 def main():
@@ -590,6 +619,8 @@ def main():
     ap.add_argument("--autotune", action="store_true", help="autotune the launch knobs during warm-up")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint (differentiable rollout) measurement")
     ap.add_argument("--no-variants", action="store_true", help="skip the 8192 / 16384-env and CUDA-graph lines")
+    ap.add_argument("--adjoint-only", action="store_true",
+                    help="run only the adjoint (differentiable rollout) measurement and print its line")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per step-kernel launch from an ncu capture of the same kernel")
     args = ap.parse_args()
@@ -599,6 +630,9 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.adjoint_only:
+        run_adjoint_only(local_rank)
         return
     if world > 1:
         import torch

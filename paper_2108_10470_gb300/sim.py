@@ -440,14 +440,10 @@ class Sim:
         check(load().sim_step_adjoint(self.h, ctypes.c_void_p(p), ctypes.byref(b), float(self.w.dt if dt is None else dt),
                                       sub), "sim_step_adjoint")
 
-    def reverse_rollout(self, tapes, acts, grads, g_acts):
-        """The reverse pass of len(acts) steps from the handle's current state: each step re-run with
-        its tape recorded in tapes[k], then the adjoints in reverse order from the final-state
-        gradients grads = (root, dof, cache), the actuation gradients written into g_acts[k].
-        Returns the initial-state gradients. Every buffer is checked once here, then passed to the
-        library as plain addresses (the per-step calls run in a loop of a few microseconds)."""
-        torch = self._torch
-        f32 = (torch.float32,)
+    def _tape_rows(self, tapes, acts):
+        """Checks tapes (steps x >= tape_floats(), row-strided) and acts (steps x N_D) once; returns
+        (steps, address of tape 0, tape row stride in floats)."""
+        f32 = (self._torch.float32,)
         steps = int(acts.shape[0])
         need = self.tape_floats()
         if need is None:
@@ -455,16 +451,37 @@ class Sim:
         tstride = int(tapes.stride(0)) if tapes.dim() > 1 else need
         self._dev_ptr(tapes, "tapes", f32, need + tstride * (steps - 1))
         self._dev_ptr(acts, "acts", f32, self.dof_actuation.numel() * steps)
+        return steps, tapes.data_ptr(), tstride
+
+    def record_tapes(self, tapes, acts):
+        """len(acts) steps from the handle's current state, step k with actuation acts[k] and its
+        tape recorded in tapes[k] (sim_step_taped); the views end at the last step's state."""
+        steps, t0, tstride = self._tape_rows(tapes, acts)
+        L = load()
+        dt, sub = float(self.w.dt), int(self.w.substeps)
+        for k in range(steps):
+            self.dof_actuation.copy_(acts[k])
+            check(L.sim_step_taped(self.h, ctypes.c_void_p(t0 + 4 * tstride * k), dt, sub), "sim_step_taped")
+
+    def reverse_rollout(self, tapes, acts, grads, g_acts, recorded: bool = False):
+        """The reverse pass of len(acts) steps: unless `recorded` (tapes[k] already hold the steps,
+        from record_tapes), each step is first re-run from the handle's current state with its tape
+        recorded in tapes[k]; then the adjoints in reverse order from the final-state gradients
+        grads = (root, dof, cache), the actuation gradients written into g_acts[k]. Returns the
+        initial-state gradients. Every buffer is checked once here, then passed to the library as
+        plain addresses (the per-step calls run in a loop of a few microseconds)."""
+        torch = self._torch
+        f32 = (torch.float32,)
+        steps, t0, tstride = self._tape_rows(tapes, acts)
         self._dev_ptr(g_acts, "g_acts", f32, self.dof_actuation.numel() * steps)
         views = ("root_state", "dof_state", "impulse_cache")
         g = [self._mirror_ptr(x, f"grad {v}", v) for x, v in zip(grads, views)]
         sets = [tuple(torch.empty_like(getattr(self, v)) for v in views) for _ in range(2)]
         L = load()
         dt, sub = float(self.w.dt), int(self.w.substeps)
-        t0, nd = tapes.data_ptr(), self.dof_actuation.numel()
-        for k in range(steps):
-            self.dof_actuation.copy_(acts[k])
-            check(L.sim_step_taped(self.h, ctypes.c_void_p(t0 + 4 * tstride * k), dt, sub), "sim_step_taped")
+        nd = self.dof_actuation.numel()
+        if not recorded:
+            self.record_tapes(tapes, acts)
         b = sim_adjoint_buffers()
         out = grads
         for k in range(steps - 1, -1, -1):

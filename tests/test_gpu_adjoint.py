@@ -202,7 +202,7 @@ def test_vjp_is_the_transpose_of_the_jvp(name, n):
         assert abs(lhs - rhs) <= 1e-4 * max(1.0, scale), (e, lhs, rhs, scale)
 
 
-def loss_grad_gpu(w, root, dof, acts, checkpoint):
+def loss_grad_gpu(w, root, dof, acts, checkpoint, keep_tapes=None):
     import torch
     from paper_2108_10470_gb300 import autograd as AG, sim
     s = sim.Sim(w)
@@ -210,10 +210,11 @@ def loss_grad_gpu(w, root, dof, acts, checkpoint):
     d0 = torch.from_numpy(dof.astype(np.float32)).cuda().requires_grad_(True)
     c0 = torch.zeros((w.n_envs, s.cache_len), device="cuda")
     A = torch.from_numpy(acts.astype(np.float32)).cuda().requires_grad_(True)
-    rf, df, cf = AG.rollout(s, r0, d0, c0, A, checkpoint=checkpoint)
+    rf, df, cf = AG.rollout(s, r0, d0, c0, A, checkpoint=checkpoint, keep_tapes=keep_tapes)
     loss = rf[:, 7].mean()  # mean final root x-velocity
     loss.backward()
-    # the backward pass re-ran the segments on the handle: its views are back at the final state
+    # whether the backward pass re-ran the segments on the handle or used the tapes the forward
+    # pass kept, its views are at the final state
     assert torch.equal(s.root_state, rf.detach()) and torch.equal(s.dof_state, df.detach())
     assert torch.equal(s.impulse_cache, cf.detach())
     out = (float(loss), d0.grad.cpu().numpy().astype(np.float64), A.grad.cpu().numpy().astype(np.float64),
@@ -257,15 +258,17 @@ def test_rollout_gradient_matches_oracle_and_checkpointing_is_exact(name, steps,
     """8 envs (Ant over 12 steps; the hand holding its cube over 6), loss = mean final root
     x-velocity: gradients w.r.t. every action and the initial DOF state through the autograd rollout
     (checkpoints of 4 steps) against the oracle's forward-mode rollout; checkpoint lengths 1, 4 and
-    the whole rollout give bitwise equal gradients. max_bad envs may deviate by more than 1e-2: the
+    the whole rollout, with the tapes kept from the forward pass or recomputed, give bitwise equal
+    gradients (the hand runs in forward mode, where there is no tape to keep). max_bad envs may
+    deviate by more than 1e-2: the
     hand's contact-rich rollouts include an env whose derivative evaluated in single precision by the
     oracle itself lands 8e-2 from its FP64 value (a clamp within rounding of its threshold)."""
     w = W.ant_workload(8) if name == "ant" else W.hand_workload(8)
     root, dof, acts = W.seeded_inputs(w, 11, steps)
-    l4, gd4, ga4, _ = loss_grad_gpu(w, root, dof, acts, 4)
-    for ck in (1, steps):
-        l, gd, ga, _ = loss_grad_gpu(w, root, dof, acts, ck)
-        assert l == l4 and np.array_equal(gd, gd4) and np.array_equal(ga, ga4)
+    l4, gd4, ga4, _ = loss_grad_gpu(w, root, dof, acts, 4, keep_tapes=False)
+    for ck, keep in ((1, False), (steps, False), (4, True), (steps, True), (4, None)):
+        l, gd, ga, _ = loss_grad_gpu(w, root, dof, acts, ck, keep_tapes=keep)
+        assert l == l4 and np.array_equal(gd, gd4) and np.array_equal(ga, ga4), (ck, keep)
     od, oa = loss_grad_oracle(w, root, dof, acts)
     nj = w.n_dof // w.n_envs
     bad = []

@@ -134,6 +134,26 @@ def test_row_solver_form(name, n_envs, steps, rtol, atol):
     check_rollout(workload(name, n_envs), steps, rtol, atol, flags=1 | 64)
 
 
+def tray_arm_workload(n_envs):
+    """A fixed pivot and a hinged arm (one generalized DOF) carrying a flat box at ground height:
+    up to eight box-corner contacts, 24 rows, against one DOF, so the Gauss-Seidel solve works on a
+    rank-one Delassus matrix (every row's response lies along the same generalized direction)."""
+    b = W._Builder("tray_arm")
+    b.link(-1, W.JOINT_FIXED, mass=1.0, inertia=(1, 1, 1, 0, 0, 0))
+    m, inn = W.box_mass(0.2, 0.15, 0.05, 1.0)
+    arm = b.link(0, W.JOINT_REVOLUTE, axis=(0, 1, 0), mass=m, com=(0.3, 0.0, -0.25), inertia=inn, damping=0.1)
+    b.shape(arm, W.SHAPE_BOX, (0.2, 0.15, 0.05), pos=(0.3, 0.0, -0.25))
+    return W.homogeneous("tray_arm", b.build(root_pos=(0.0, 0.0, 0.3), dof_noise=0.05), n_envs)
+
+
+@pytest.mark.parametrize("steps,rtol,atol", [(1, 1e-4, 1e-5), (16, 1e-3, 1e-3)])
+def test_overconstrained_tray(steps, rtol, atol):
+    """Many contact rows on one generalized DOF (two to four box corners down): the impulses that
+    satisfy the contacts are not unique, and the Gauss-Seidel sweep picks one by its row order, as
+    the oracle's does; against the oracle at the usual bars."""
+    check_rollout(tray_arm_workload(48), steps, rtol, atol)
+
+
 @pytest.mark.parametrize("name,n_envs", [("ant", 4096), ("humanoid", 4096), ("hand", 4096), ("mixed", 16384)])
 def test_full_size_one_step(name, n_envs):
     """Full-size configurations (one launch per env type and step) against the oracle on all envs."""
