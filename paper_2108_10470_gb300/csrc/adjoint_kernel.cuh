@@ -33,6 +33,7 @@
 // joints and shape pairs use the forward-mode derivative kernel.)
 #pragma once
 #include "step_kernel.cuh"
+#include "tangent_step.cuh"
 
 namespace artsim {
 
@@ -186,10 +187,102 @@ __device__ __forceinline__ float back_subst(const float* sL, const int LS, const
 }
 
 // ---------------------------------------------------------------------------------------------
+// One kept capsule-box sample (pair p, slot) in forward mode over the step's pair geometry, with six
+// tangents seeded by `mode`: 0 the capsule link's twist about its actor origin (rotation [w]x R,
+// link origin w x P + v), 1 the box link's, 2 the two actor origins (the capsule's, then the box's).
+// out[j] = xb . dx/ds_j + nb . dn/ds_j + t1b . dt1/ds_j + t2b . dt2/ds_j + db dd/ds_j for the
+// sample's contact point x (relative to body a's actor origin), normal n (from b to a), its
+// friction directions and separation d. Out of line: it runs once per pair contact and pass.
+__device__ __noinline__ void pair_sample_adjoint(const EnvTypeTable* __restrict__ T, const int p, const int slot,
+                                                 const float* Rc, const float* Pc, const float* Oc, const float* Rx,
+                                                 const float* Px, const float* Ox, const int mode, const V3 xb,
+                                                 const V3 nb, const V3 t1b, const V3 t2b, const float db, float* out) {
+  constexpr int K = 6;
+  const int sa = T->pair_a[p], sb = T->pair_b[p];
+  const bool a_cap = T->shape_type[sa] == kCapsule;
+  const int sc = a_cap ? sa : sb, sx = a_cap ? sb : sa;
+  Dn<K> Rcd[9], Rxd[9];
+  DV3<K> Pcd, Pxd, Ocd, Oxd;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) { Rcd[k] = Dn<K>(Rc[k]); Rxd[k] = Dn<K>(Rx[k]); }
+  Pcd = dv3<K>(Dn<K>(Pc[0]), Dn<K>(Pc[1]), Dn<K>(Pc[2]));
+  Pxd = dv3<K>(Dn<K>(Px[0]), Dn<K>(Px[1]), Dn<K>(Px[2]));
+  Ocd = dv3<K>(Dn<K>(Oc[0]), Dn<K>(Oc[1]), Dn<K>(Oc[2]));
+  Oxd = dv3<K>(Dn<K>(Ox[0]), Dn<K>(Ox[1]), Dn<K>(Ox[2]));
+  if (mode < 2) {  // a twist of one link: d R = [e_j]x R (columns rotate), d P = e_j x P; d P = e_(j-3)
+    Dn<K>* R = mode == 0 ? Rcd : Rxd;
+    DV3<K>& P = mode == 0 ? Pcd : Pxd;
+    const float* Rv = mode == 0 ? Rc : Rx;
+    const float* Pv = mode == 0 ? Pc : Px;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const V3 e = v3(j == 0 ? 1.f : 0.f, j == 1 ? 1.f : 0.f, j == 2 ? 1.f : 0.f);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const V3 dc = cross(e, v3(Rv[k], Rv[3 + k], Rv[6 + k]));
+        R[k].d[j] = dc.x; R[3 + k].d[j] = dc.y; R[6 + k].d[j] = dc.z;
+      }
+      const V3 dp = cross(e, v3(Pv[0], Pv[1], Pv[2]));
+      P.x.d[j] = dp.x; P.y.d[j] = dp.y; P.z.d[j] = dp.z;
+    }
+    P.x.d[3] = 1.f; P.y.d[4] = 1.f; P.z.d[5] = 1.f;
+  } else {
+    Ocd.x.d[0] = 1.f; Ocd.y.d[1] = 1.f; Ocd.z.d[2] = 1.f;
+    Oxd.x.d[3] = 1.f; Oxd.y.d[4] = 1.f; Oxd.z.d[5] = 1.f;
+  }
+  // the geometry of the step's pair phase (relative to the box actor's origin)
+  Dn<K> Rsh[9], Rcs[9], Rb[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) Rsh[k] = Dn<K>(T->shape_rot[k][sc]);
+  dmm<K>(Rcd, Rsh, Rcs);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) Rsh[k] = Dn<K>(T->shape_rot[k][sx]);
+  dmm<K>(Rxd, Rsh, Rb);
+  const DV3<K> cc = Pcd + dmv<K>(Rcd, dv3<K>(Dn<K>(T->shape_pos[0][sc]), Dn<K>(T->shape_pos[1][sc]),
+                                             Dn<K>(T->shape_pos[2][sc]))) + (Ocd - Oxd);
+  const DV3<K> cb = Pxd + dmv<K>(Rxd, dv3<K>(Dn<K>(T->shape_pos[0][sx]), Dn<K>(T->shape_pos[1][sx]),
+                                             Dn<K>(T->shape_pos[2][sx])));
+  const float r = T->shape_size[0][sc], hl = T->shape_size[1][sc];
+  const float e[3] = {T->shape_size[0][sx], T->shape_size[1][sx], T->shape_size[2][sx]};
+  const DV3<K> ax = dv3<K>(Rcs[0], Rcs[3], Rcs[6]);
+  const DV3<K> b0 = dv3<K>(Rb[0], Rb[3], Rb[6]), b1 = dv3<K>(Rb[1], Rb[4], Rb[7]), b2 = dv3<K>(Rb[2], Rb[5], Rb[8]);
+  const DV3<K> w0 = cc - ax * Dn<K>(hl) - cb, w1 = cc + ax * Dn<K>(hl) - cb;
+  const DV3<K> p0 = dv3<K>(ddot(b0, w0), ddot(b1, w0), ddot(b2, w0));
+  const DV3<K> dv = dv3<K>(ddot(b0, w1), ddot(b1, w1), ddot(b2, w1)) - p0;
+  const Dn<K> tstar = dsegment_box_closest_t<K>(p0, dv, e);
+  Dn<K> ta, tb;
+  const bool clip = dface_clip<K>(p0, dv, e, r, tstar, ta, tb);
+  const Dn<K> t = slot == 0 ? Dn<K>(0.f) : (slot == 1 ? Dn<K>(1.f) : (slot == 2 ? ta : (slot == 3 ? tb : tstar)));
+  bool ok = true;  // the step kept this sample; its recomputation must find it valid too
+  if (slot >= 2) {
+    if (slot < 4 && !clip) ok = false;
+    if (slot == 3 && !(ta.v < tb.v)) ok = false;
+    if (!(t.v > 0.f && t.v < 1.f)) ok = false;
+  }
+#pragma unroll
+  for (int j = 0; j < K; ++j) out[j] = 0.f;
+  if (!ok) return;
+  DV3<K> pn, px;
+  Dn<K> pd;
+  dsphere_box<K>(p0 + dv * t, r, e, pn, pd, px);
+  DV3<K> nw = b0 * pn.x + b1 * pn.y + b2 * pn.z;  // box -> capsule
+  if (!a_cap) nw = dv3<K>(-nw.x, -nw.y, -nw.z);
+  const DV3<K> Oa = a_cap ? Ocd : Oxd;
+  const DV3<K> xw = cb + b0 * px.x + b1 * px.y + b2 * px.z + (Oxd - Oa);
+  DV3<K> t1, t2;
+  dtangent_basis<K>(nw, t1, t2);
+#pragma unroll
+  for (int j = 0; j < K; ++j)
+    out[j] = xb.x * xw.x.d[j] + xb.y * xw.y.d[j] + xb.z * xw.z.d[j] + nb.x * nw.x.d[j] + nb.y * nw.y.d[j] +
+             nb.z * nw.z.d[j] + t1b.x * t1.x.d[j] + t1b.y * t1.y.d[j] + t1b.z * t1.z.d[j] + t2b.x * t2.x.d[j] +
+             t2b.y * t2.y.d[j] + t2b.z * t2.z.d[j] + db * pd.d[j];
+}
+
+// ---------------------------------------------------------------------------------------------
 // The reverse pass of one env (group of G lanes): sm is the group's arena (AdjLayout), gi its index
 // in the launch (the tape block), live false for the dead groups of the last CTA (they shadow the
 // last env and store nothing).
-template <int G>
+template <int G, bool PAIRS>
 __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs& TA, const AdjArgs& J, const int grp,
                                               float* sm) {
   const EnvTypeTable* __restrict__ T = TA.type;
@@ -202,10 +295,11 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
   const int L = T->n_links, n = T->n_gen;
   const int maxdepth = T->max_depth;
   const int YS = al.YS, LS = al.LS, RC = TL.rcap;
-  // the substep's tape image (read in place; its final impulses are rewound during the solve)
+  // the substep's tape image (read in place; its final impulses are rewound during the solve); Y
+  // is the image's last block, or, when the arena has no room for it, read in place from the tape
   float* img = sm + al.img;
   void* bar = sm + al.bar;
-  float* s_Y = img + TL.Y;
+  const float* s_Y = img + TL.Y;
   float* s_L = img + TL.L;
   float4* s_rowc = reinterpret_cast<float4*>(img + TL.rowc);
   int* s_rowa = reinterpret_cast<int*>(img + TL.rowa);
@@ -216,12 +310,17 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
   float* s_con = img + TL.con;
   int* s_coni = reinterpret_cast<int*>(s_con);
   const float* s_linv = img + TL.Linv;
-  float* s_Yb = sm + al.Yb;
+  // Y's adjoint outside the arena: env types with shape pairs only (a global slot per group: the
+  // dead groups own one too); elsewhere both stay shared-memory pointers the compiler can see
+  float* s_Yb = (PAIRS && al.gY) ? J.ybg + (size_t)grp * (size_t)n * YS : sm + al.Yb;
   float* s_Mb = sm + al.Mb;
   float* s_lamb = sm + al.lamb;
   float* s_db = sm + al.db;
   float* s_invAb = sm + al.invAb;
   float* s_xb = sm + al.xb;
+  constexpr int XW = PAIRS ? 9 : 3;  // words per row of s_xb (AdjLayout::xbw)
+  constexpr bool pairs_t = PAIRS;    // the type has capsule-box shape pairs (TL.cw > 5)
+  float* s_pose = sm + al.pose;      // pairs: rotation 9 | origin 3 of each link
   float* s_vec = sm + al.vec;
   float* s_SD = sm + al.SD;
   float* s_FM = sm + al.FM;
@@ -308,10 +407,11 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
 
   for (int sub = A.substeps - 1; sub >= 0; --sub) {
     const float* tp = J.tape + ((size_t)gi * A.substeps + sub) * TL.words;
+    if (PAIRS && al.gY) s_Y = tp + TL.Y;
     // ---- the tape block into the arena: one bulk copy by the TMA engine ----
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // this lane's writes to the image first
     __syncwarp();
-    if (lane == 0) bulk_copy_g2s(img, tp, 4u * (unsigned)TL.words, bar);
+    if (lane == 0) bulk_copy_g2s(img, tp, 4u * (unsigned)al.imgw, bar);
     const bool arrived = mbar_wait(bar, parity);
     parity ^= 1u;
     if (__any_sync(kFull, !arrived)) {  // warp-uniform: both groups of the warp stop here
@@ -419,6 +519,11 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
         rec[kRecH] = m * cw.x; rec[kRecH + 1] = m * cw.y; rec[kRecH + 2] = m * cw.z;
         rec[kRecCw] = cw.x; rec[kRecCw + 1] = cw.y; rec[kRecCw + 2] = cw.z;
         rec[kRecM] = m;
+        if (pairs_t) {  // the link's pose, for the pair contacts' geometry
+#pragma unroll
+          for (int k = 0; k < 9; ++k) s_pose[12 * l + k] = Rw[k];
+          s_pose[12 * l + 9] = P.x; s_pose[12 * l + 10] = P.y; s_pose[12 * l + 11] = P.z;
+        }
       }
       // motion subspace per generalized DOF (unit columns for a floating root)
       if (has_dof) {
@@ -666,28 +771,65 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
     }
     __syncwarp();
     // ---- contact rows (row mode): the contact-point adjoint x_bar = sum_g J_bar_rg (k x a_g), + d_bar
-    // e_z for a normal row; and, for the gather below, the row's [x x k; k] and the mask of the
-    // generalized DOFs it acts on (0 for a row without response), in the dead impulse-history block ----
-    float* s_fr = s_lambef;  // 7 x RC words: [x x k; k] (6) | DOF mask; the history is read
+    // e_z for a ground normal row; and, for the gather below, the row's [x x k; k] and the mask of the
+    // generalized DOFs it acts on (0 for a row without response), in the dead impulse-history block.
+    // A pair row acts on two bodies, J_r = S . [x x k; k] on a's path and -S . [x_b x k; k] on b's
+    // (x_b = x - o_b, o_b b's actor origin relative to a's; k the pair normal or a friction direction
+    // of it): its adjoints of x, o_b and k go to the pair phase below ----
+    float* s_fr = s_lambef;  // 7 x RC words: [x x k; k] (6) | DOF mask; with shape pairs 7 more: b's
     for (int r = n_lim + lane; r < R; r += G) {
       const float4 hc = s_rowc[r];
       const int a = s_rowa[r];
       const int c = a & 0xff, dir = (a >> 8) & 3;
-      const unsigned anc = (hc.y > 0.f) ? T->anc[s_coni[3 * TL.ccap + c]] : 0u;
-      const V3 k = dir == 0 ? v3(0.f, 0.f, 1.f) : (dir == 1 ? v3(1.f, 0.f, 0.f) : v3(0.f, 1.f, 0.f));
+      const bool act = hc.y > 0.f;
+      const int lbk = pairs_t ? s_coni[5 * TL.ccap + c] : -1;  // body b of a pair contact
+      const unsigned anc = act ? T->anc[s_coni[3 * TL.ccap + c]] : 0u;
+      const unsigned ancb = (act && lbk >= 0) ? T->anc[lbk] : 0u;
       const V3 x = v3(s_con[c], s_con[TL.ccap + c], s_con[2 * TL.ccap + c]);
-      V3 sa = v3(0.f, 0.f, 0.f);
+      V3 k = dir == 0 ? v3(0.f, 0.f, 1.f) : (dir == 1 ? v3(1.f, 0.f, 0.f) : v3(0.f, 1.f, 0.f));
+      V3 dob = v3(0.f, 0.f, 0.f);
+      if (lbk >= 0) {
+        const V3 nrm = v3(s_con[7 * TL.ccap + c], s_con[8 * TL.ccap + c], s_con[9 * TL.ccap + c]);
+        dob = v3(s_con[10 * TL.ccap + c], s_con[11 * TL.ccap + c], s_con[12 * TL.ccap + c]);
+        k = nrm;
+        if (dir != 0) {
+          V3 t1, t2;
+          tangent_basis(nrm, t1, t2);
+          k = (dir == 1) ? t1 : t2;
+        }
+      }
+      V3 sa = v3(0.f, 0.f, 0.f), la = sa, sb = sa, lb = sa;  // sums of J_bar_rg S_g (angular, linear)
       for (int gg = 0; gg < n; ++gg) {
-        const float jb = ((anc >> gg) & 1u) ? s_Yb[gg * YS + r] : 0.f;
-        sa = sa + v3(s_SD[kSDS * gg], s_SD[kSDS * gg + 1], s_SD[kSDS * gg + 2]) * jb;
+        const float jr = s_Yb[gg * YS + r];
+        const float ja = ((anc >> gg) & 1u) ? jr : 0.f, jb = ((ancb >> gg) & 1u) ? jr : 0.f;
+        const V3 Sa = v3(s_SD[kSDS * gg], s_SD[kSDS * gg + 1], s_SD[kSDS * gg + 2]);
+        sa = sa + Sa * ja;
+        sb = sb + Sa * jb;
+        if (pairs_t) {
+          const V3 Sl = v3(s_SD[kSDS * gg + 3], s_SD[kSDS * gg + 4], s_SD[kSDS * gg + 5]);
+          la = la + Sl * ja;
+          lb = lb + Sl * jb;
+        }
       }
       V3 xb = cross(k, sa);
-      if (dir == 0 && hc.y > 0.f) xb.z += s_db[r];
-      s_xb[3 * r] = xb.x; s_xb[3 * r + 1] = xb.y; s_xb[3 * r + 2] = xb.z;
+      if (lbk < 0 && dir == 0 && act) xb.z += s_db[r];  // ground: d = O_z + x_z (a pair's d: below)
       const V3 xk = cross(x, k);
       s_fr[r] = xk.x; s_fr[RC + r] = xk.y; s_fr[2 * RC + r] = xk.z;
       s_fr[3 * RC + r] = k.x; s_fr[4 * RC + r] = k.y; s_fr[5 * RC + r] = k.z;
       s_fr[6 * RC + r] = __uint_as_float(anc);
+      if (pairs_t) {
+        const V3 xq = x - dob;                      // the point about b's actor origin
+        const V3 kxb = cross(k, sb);
+        xb = xb - kxb;                              // d/dx through x_b
+        const V3 kb = cross(sa, x) + la - cross(sb, xq) - lb;  // d/dk of both bodies' terms
+        s_xb[XW * r + 3] = kxb.x; s_xb[XW * r + 4] = kxb.y; s_xb[XW * r + 5] = kxb.z;  // d/do_b
+        s_xb[XW * r + 6] = kb.x; s_xb[XW * r + 7] = kb.y; s_xb[XW * r + 8] = kb.z;
+        const V3 xqk = cross(xq, k);
+        s_fr[7 * RC + r] = -xqk.x; s_fr[8 * RC + r] = -xqk.y; s_fr[9 * RC + r] = -xqk.z;
+        s_fr[10 * RC + r] = -k.x; s_fr[11 * RC + r] = -k.y; s_fr[12 * RC + r] = -k.z;
+        s_fr[13 * RC + r] = __uint_as_float(ancb);
+      }
+      s_xb[XW * r] = xb.x; s_xb[XW * r + 1] = xb.y; s_xb[XW * r + 2] = xb.z;
     }
     __syncwarp();
     // ---- reverse of the composite-rigid-body algorithm and the contact rows' S adjoints (DOF mode;
@@ -715,15 +857,67 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
 #pragma unroll
         for (int k = 0; k < 6; ++k) Sb[k] += t[k];
       }
-      // contact rows: J_ri = S_i . [x x k; k] on the contact link's path
+      // contact rows: J_ri = S_i . [x x k; k] on the contact link's path (and for a pair row
+      // -S_i . [x_b x k; k] on body b's)
       for (int r = n_lim; r < R; ++r) {
         const unsigned mask = __float_as_uint(s_fr[6 * RC + r]);
         const float jb = ((mask >> i) & 1u) ? s_Yb[i * YS + r] : 0.f;
 #pragma unroll
         for (int k = 0; k < 6; ++k) Sb[k] += jb * s_fr[k * RC + r];
+        if (pairs_t) {
+          const unsigned maskb = __float_as_uint(s_fr[13 * RC + r]);
+          const float jbb = ((maskb >> i) & 1u) ? s_Yb[i * YS + r] : 0.f;
+#pragma unroll
+          for (int k = 0; k < 6; ++k) Sb[k] += jbb * s_fr[(7 + k) * RC + r];
+        }
       }
 #pragma unroll
       for (int k = 0; k < 6; ++k) { s_Sb[kSDS * i + k] = Sb[k]; s_FMb[kSDS * i + k] = Fb[k]; }
+    }
+    __syncwarp();
+
+    // ---- capsule-box pair contacts (contact mode): the adjoints of each pair contact's point,
+    // normal, friction directions, b's actor offset and separation, carried to the poses of its two
+    // links and to the two actor origins by three forward-mode passes over the pair geometry (the
+    // capsule link's twist, the box link's, the origins), into 18 words per contact: wrench on link
+    // a (6) | on link b (6) | adjoint of a's actor origin (3) | of b's (3) ----
+    float* s_pw = s_lambef;  // (the row vectors of the gather above are dead)
+    if (pairs_t) {
+      for (int c = lane; c < n_con; c += G) {
+        const int lbk = s_coni[5 * TL.ccap + c];
+        if (lbk < 0) continue;
+        const int rn = n_lim + c, rf = n_lim + n_con + 2 * c;
+        V3 xa = v3(0.f, 0.f, 0.f), ob = xa;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const int r = q == 0 ? rn : rf + q - 1;
+          xa = xa + v3(s_xb[XW * r], s_xb[XW * r + 1], s_xb[XW * r + 2]);
+          ob = ob + v3(s_xb[XW * r + 3], s_xb[XW * r + 4], s_xb[XW * r + 5]);
+        }
+        const V3 nb = v3(s_xb[XW * rn + 6], s_xb[XW * rn + 7], s_xb[XW * rn + 8]);
+        const V3 t1b = v3(s_xb[XW * rf + 6], s_xb[XW * rf + 7], s_xb[XW * rf + 8]);
+        const V3 t2b = v3(s_xb[XW * (rf + 1) + 6], s_xb[XW * (rf + 1) + 7], s_xb[XW * (rf + 1) + 8]);
+        const float dbn = s_db[rn];
+        const int cand = s_coni[6 * TL.ccap + c] - T->n_ground_cand;
+        const int p = cand / kPairSlots, slot = cand - kPairSlots * p;
+        const bool a_cap = T->shape_type[T->pair_a[p]] == kCapsule;
+        const int la_ = s_coni[3 * TL.ccap + c];
+        const int lc = a_cap ? la_ : lbk, lx = a_cap ? lbk : la_;
+        const float* Oc = img + TL.st + 2 * L + 13 * T->actor[lc];
+        const float* Ox = img + TL.st + 2 * L + 13 * T->actor[lx];
+        float w[3][6];
+#pragma unroll 1
+        for (int mode = 0; mode < 3; ++mode)
+          pair_sample_adjoint(T, p, slot, s_pose + 12 * lc, s_pose + 12 * lc + 9, Oc, s_pose + 12 * lx,
+                              s_pose + 12 * lx + 9, Ox, mode, xa, nb, t1b, t2b, dbn, w[mode]);
+        float* o = s_pw + 18 * c;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) { o[k] = a_cap ? w[0][k] : w[1][k]; o[6 + k] = a_cap ? w[1][k] : w[0][k]; }
+        // origins: through the geometry, and o_b = O_b - O_a directly
+        const V3 oc = v3(w[2][0], w[2][1], w[2][2]), ox = v3(w[2][3], w[2][4], w[2][5]);
+        const V3 oa = (a_cap ? oc : ox) - ob, obb = (a_cap ? ox : oc) + ob;
+        o[12] = oa.x; o[13] = oa.y; o[14] = oa.z; o[15] = obb.x; o[16] = obb.y; o[17] = obb.z;
+      }
     }
     __syncwarp();
 
@@ -734,10 +928,23 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
       for (int gg = 0; gg < n; ++gg)
         if (T->dof_link[gg] == l) inertia_outer(s_FMb + kSDS * gg, s_SD + kSDS * gg, IOb, hbar);
       for (int c = 0; c < n_con; ++c) {
-        if (s_coni[3 * TL.ccap + c] != l) continue;
+        const int la_ = s_coni[3 * TL.ccap + c];
+        const int lbk = pairs_t ? s_coni[5 * TL.ccap + c] : -1;
+        if (lbk >= 0) {  // a pair contact: the wrenches of the pair phase
+          const float* o = s_pw + 18 * c;
+          if (la_ == l)
+#pragma unroll
+            for (int k = 0; k < 6; ++k) wr[k] += o[k];
+          if (lbk == l)
+#pragma unroll
+            for (int k = 0; k < 6; ++k) wr[k] += o[6 + k];
+          continue;
+        }
+        if (la_ != l) continue;
         const int rn = n_lim + c, rf = n_lim + n_con + 2 * c;
-        const V3 xb = v3(s_xb[3 * rn] + s_xb[3 * rf] + s_xb[3 * rf + 3], s_xb[3 * rn + 1] + s_xb[3 * rf + 1] + s_xb[3 * rf + 4],
-                         s_xb[3 * rn + 2] + s_xb[3 * rf + 2] + s_xb[3 * rf + 5]);
+        const V3 xb = v3(s_xb[XW * rn] + s_xb[XW * rf] + s_xb[XW * (rf + 1)],
+                         s_xb[XW * rn + 1] + s_xb[XW * rf + 1] + s_xb[XW * (rf + 1) + 1],
+                         s_xb[XW * rn + 2] + s_xb[XW * rf + 2] + s_xb[XW * (rf + 1) + 2]);
         const int sh = s_coni[4 * TL.ccap + c];
         const float rad = (T->shape_type[sh] == kBox) ? 0.f : T->shape_size[0][sh];
         // the body-fixed point: the contact point lies one radius straight below it
@@ -772,8 +979,21 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
         }
       }
       if (is_root)
-        for (int c = 0; c < n_con; ++c)
-          if (T->actor[s_coni[3 * TL.ccap + c]] == T->actor[l]) rpb[2] += s_db[n_lim + c];
+        for (int c = 0; c < n_con; ++c) {
+          const int la_ = s_coni[3 * TL.ccap + c];
+          const int lbk = pairs_t ? s_coni[5 * TL.ccap + c] : -1;
+          if (lbk >= 0) {  // the pair phase's origin adjoints
+            const float* o = s_pw + 18 * c;
+            if (T->actor[la_] == T->actor[l])
+#pragma unroll
+              for (int k = 0; k < 3; ++k) rpb[k] += o[12 + k];
+            if (T->actor[lbk] == T->actor[l])
+#pragma unroll
+              for (int k = 0; k < 3; ++k) rpb[k] += o[15 + k];
+          } else if (T->actor[la_] == T->actor[l]) {
+            rpb[2] += s_db[n_lim + c];
+          }
+        }
     }
     {  // composite-inertia adjoints reach every link of the subtree: outward prefix over ancestors
       float t9[9] = {IOb[0], IOb[1], IOb[2], IOb[3], IOb[4], IOb[5], hbar[0], hbar[1], hbar[2]};
@@ -987,14 +1207,14 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
 }
 
 // One launch per env type: blocks of blockDim / G groups, one env per group.
-template <int G>
+template <int G, bool PAIRS>
 __global__ void __launch_bounds__(64) adjoint_kernel(const __grid_constant__ StepArgs A,
                                                     const __grid_constant__ TypeArgs TA,
                                                     const __grid_constant__ AdjArgs J) {
   extern __shared__ __align__(16) float smem[];
   const int grp_blk = threadIdx.x / G;
   const int grp = blockIdx.x * (blockDim.x / G) + grp_blk;
-  adjoint_group<G>(A, TA, J, grp, smem + grp_blk * J.al.total);
+  adjoint_group<G, PAIRS>(A, TA, J, grp, smem + grp_blk * J.al.total);
 }
 
 }  // namespace artsim

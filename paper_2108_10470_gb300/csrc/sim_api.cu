@@ -36,6 +36,8 @@ struct TypePlan {
   size_t scratch_floats = 0;
   float* pscratch = nullptr;  // global rows, persistent launch: one slot per resident group
   size_t pscratch_floats = 0;
+  float* ybg = nullptr;       // reverse pass with Y outside the arena: Y's adjoint, one slot per env
+  size_t ybg_floats = 0;
   double env_cost = 0.0;      // relative cost of one env (persistent tile order)
 };
 
@@ -690,6 +692,7 @@ void free_all(sim_s* h) {
   for (auto& tp : h->types) {
     if (tp.scratch) cudaFree(tp.scratch);
     if (tp.pscratch) cudaFree(tp.pscratch);
+    if (tp.ybg) cudaFree(tp.ybg);
   }
   if (h->rv_state) cudaFree(h->rv_state);
   if (h->rv_tape) cudaFree(h->rv_tape);
@@ -1103,20 +1106,25 @@ TapeLayout tape_layout(const TypePlan& tp, int npos, int nvel) {
   t.vec = o; o += 7 * n;
   t.L = o; o += n * t.LT;
   t.Linv = o; o += n;
-  t.con = o; o += 5 * t.ccap;
+  t.cw = T.n_pairs > 0 ? kTapeConPairWords : 5;
+  t.con = o; o += t.cw * t.ccap;
   o = al4i(o);
   t.rowc = o; o += 4 * t.rcap;
   t.rowa = o; o += t.rcap;
   t.lam0 = o; o += t.rcap;
   t.lamf = o; o += t.rcap;
-  t.Y = o; o += n * t.YT;
   t.lamb = o; o += t.iters * t.rcap;
   t.seps = o; o += (npos + 1) * t.rcap;
-  // the adjoint reuses these two blocks, once read, as 7 words per row: keep at least that many
-  o = std::max(o, t.lamb + 7 * t.rcap);
+  // the adjoint reuses these two blocks, once read, as 7 words per row (14 with shape pairs: the
+  // rows act on two bodies), then as 18 words per pair contact: keep at least that many
+  o = std::max(o, t.lamb + (T.n_pairs > 0 ? 14 : 7) * t.rcap);
+  o = al4i(o);
+  t.Y = o; o += n * t.YT;
   t.words = al4i(o);
   return t;
 }
+
+constexpr int kAdjThreads = 64;  // threads per CTA of the adjoint kernel
 
 // Arena of one env in the adjoint kernel (offsets in words; see AdjLayout).
 AdjLayout adj_layout(const TypePlan& tp, int npos, int nvel) {
@@ -1126,33 +1134,40 @@ AdjLayout adj_layout(const TypePlan& tp, int npos, int nvel) {
   const int n = std::max(T.n_gen, 1), rc = tp.lay.rcap;
   a.YS = tl.YT;
   a.LS = tl.LT;
-  int o = 0;
-  a.img = o; o += tl.words;
-  a.bar = o; o += 4;
-  a.Yb = o; o += n * a.YS;
-  a.Mb = o; o += n * a.LS;
-  a.lamb = o; o += rc;
-  a.db = o; o += rc;
-  a.invAb = o; o += rc;
-  a.xb = o; o += 3 * rc;
-  a.vec = o; o += kAdjVecs * n;
-  a.SD = o; o += 7 * n;   // 6-vectors at an odd stride of 7
-  a.FM = o; o += 7 * n;
-  a.FMb = o; o += 7 * n;
-  a.Sb = o; o += 7 * n;
-  a.link = o; o += kAdjLinkWords * T.n_links;
-  a.total = al4i(o);
+  const bool pairs = T.n_pairs > 0;
+  for (int gY = 0; gY < 2; ++gY) {
+    int o = 0;
+    a.gY = gY;
+    a.imgw = gY ? tl.Y : tl.words;
+    a.img = o; o += a.imgw;
+    a.bar = o; o += 4;
+    a.Yb = o; o += gY ? 0 : n * a.YS;
+    a.Mb = o; o += n * a.LS;
+    a.lamb = o; o += rc;
+    a.db = o; o += rc;
+    a.invAb = o; o += rc;
+    a.xbw = pairs ? 9 : 3;
+    a.xb = o; o += a.xbw * rc;
+    a.vec = o; o += kAdjVecs * n;
+    a.SD = o; o += 7 * n;   // 6-vectors at an odd stride of 7
+    a.FM = o; o += 7 * n;
+    a.FMb = o; o += 7 * n;
+    a.Sb = o; o += 7 * n;
+    a.link = o; o += kAdjLinkWords * T.n_links;
+    a.pose = o; o += pairs ? 12 * T.n_links : 0;
+    a.total = al4i(o);
+    // Y and its adjoint in shared memory while the CTA's envs (64 threads / G) fit (the option of
+    // reading them from global memory is compiled into the kernels for env types with shape pairs)
+    if (!pairs || (size_t)(kAdjThreads / tp.G) * a.total * sizeof(float) <= kMaxSmemPerCta) break;
+  }
   return a;
 }
 
-constexpr int kAdjThreads = 64;
-
-// The reverse pass covers env types without ball joints and shape pairs whose adjoint arena fits a
-// CTA.
+// The reverse pass covers env types without ball joints whose adjoint arena fits a CTA.
 int reverse_supported(const sim_s* h) {
   for (const TypePlan& tp : h->types) {
-    if (tp.tab.has_ball || tp.tab.n_pairs > 0) {
-      g_last_error = "reverse pass: env types with ball joints or shape pairs use the forward-mode derivative";
+    if (tp.tab.has_ball) {
+      g_last_error = "reverse pass: env types with ball joints use the forward-mode derivative";
       return SIM_ERR_INVALID_ARG;
     }
     const AdjLayout al = adj_layout(tp, h->params.pos_iters, h->params.vel_iters);
@@ -1204,12 +1219,20 @@ int launch_adjoint(sim_s* h, const StepArgs& a, const float* tape, AdjArgs j, cu
   std::vector<int64_t> offs;
   tape_floats(h, a.substeps, &offs);
   for (size_t t = 0; t < h->types.size(); ++t) {
-    const TypePlan& tp = h->types[t];
+    TypePlan& tp = h->types[t];
     TypeArgs ta;
     fill_type(h, t, ta);
     ta.tl = tape_layout(tp, a.pos_iters, a.vel_iters);
     j.tape = tape + offs[t];
     j.al = adj_layout(tp, a.pos_iters, a.vel_iters);
+    j.ybg = nullptr;
+    if (j.al.gY) {  // one slot per group of the launch (the dead groups of the last CTA own theirs)
+      const size_t gpb = kAdjThreads / tp.G, groups = (tp.envs.size() + gpb - 1) / gpb * gpb;
+      const int rc = grow_buffer(&tp.ybg, &tp.ybg_floats, groups * (size_t)std::max(tp.tab.n_gen, 1) * j.al.YS,
+                                 "cudaMalloc (reverse-pass Y adjoint)");
+      if (rc != SIM_OK) return rc;
+      j.ybg = tp.ybg;
+    }
     CK(set_adjoint_kernel_smem_cap(tp.G, kMaxSmemPerCta));
     const cudaError_t e = launch_adjoint_kernel(tp.G, a, ta, j, st);
     if (e != cudaSuccess) return cuda_fail(e, "adjoint_kernel launch");

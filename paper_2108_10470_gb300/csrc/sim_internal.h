@@ -150,18 +150,23 @@ struct TapeLayout {
   int vec;    // 7 x n: qdd | v_free | z0 = L^T v_free | z final | dz final | v | dq
   int L;      // n x LT (LT = n | 1, odd), row-major, lower triangle
   int Linv;   // n: 1 / L_kk
-  int con;    // 5 x ccap (SoA): x y z (relative to the actor origin) | link | shape
+  int con;    // cw x ccap (SoA): x y z (relative to body a's actor origin) | link a | shape a, and for
+              // env types with shape pairs | link b (-1: the ground) | candidate | normal (3, from b
+              // to a) | b's actor origin minus a's (3)
+  int cw;     // 5, or kTapeConPairWords with shape pairs
   int rowc;   // 4 x rcap: the row headers (16-byte aligned)
   int rowa;   // rcap
   int lam0;   // rcap: warm-start impulses
   int lamf;   // rcap: final impulses
-  int Y;      // n x YT (YT = rcap | 1, odd): Y = L^-1 J^T, column r = row r
   int lamb;   // (npos + nvel) x rcap: impulse of row r before its update in iteration it
   int seps;   // (npos + 1) x rcap: separation d_r + Y_r . dz used in iteration it (the last for
               // every velocity iteration)
+  int Y;      // n x YT (YT = rcap | 1, odd): Y = L^-1 J^T, column r = row r; last, so that a
+              // reverse arena without room for it copies the block up to Y and reads Y in place
   int rcap, ccap, n, npos, iters;
-  int YT, LT; // odd strides of Y and L (the reverse kernel reads its shared-memory image in place)
+  int YT, LT; // odd strides of Y and L (the reverse kernel reads its image in place)
 };
+constexpr int kTapeConPairWords = 13;
 
 // Arguments of one env type (read once per group, at the start of its step).
 struct TypeArgs {
@@ -180,16 +185,22 @@ struct TypeArgs {
 // asynchronous copy per substep and read in place); the impulses of its final-impulse block are
 // rewound in place during the reverse solve.
 struct AdjLayout {
-  int img;          // the tape block (TapeLayout::words, 16-byte aligned)
+  int img;          // the tape block (16-byte aligned): imgw words of it
+  int imgw;         // TapeLayout::words, or TapeLayout::Y when gY
+  int gY;           // 1: Y is read in place from the tape and its adjoint lives in global scratch
+                    // (AdjArgs::ybg), for env types with shape pairs whose arena would not otherwise
+                    // fit a CTA's envs
   int bar;          // the bulk copy's mbarrier (8-byte aligned, 4 words reserved)
   int Yb, YS;       // n x YS (YS = the tape's Y stride): Y's adjoint, then the Jacobian-row adjoint
   int Mb, LS;       // n x LS (LS = the tape's L stride): P, then L^-T P, then the inertia adjoint
   int lamb, db, invAb;  // rcap each
-  int xb;           // 3 x rcap: adjoint of each row's contact point
+  int xb, xbw;      // xbw x rcap: per contact row the adjoint of its contact point (3), and with
+                    // shape pairs those of b's actor offset (3) and of its direction (3)
   int vec;          // kAdjVecs x n (see adjoint_kernel.cuh)
   int SD, FM, FMb, Sb;  // 7 x n each (6-vectors at an odd stride): motion subspace, composite-inertia
                         // force, its adjoint, S adjoint
   int link;         // kAdjLinkWords x L
+  int pose;         // 12 x L with shape pairs (rotation 9 | origin 3 of each link), else 0 words
   int total;        // words per env (multiple of 4)
 };
 constexpr int kAdjVecs = 6;
@@ -206,6 +217,7 @@ struct AdjArgs {
   float* gi_act;             // (N_D,) out
   float* gi_cache;           // (n_envs, cache_stride) out (also the working storage between substeps)
   int* status;               // (n_envs,) out or null
+  float* ybg;                // al.gY: n x YS floats per group of the launch (Y's adjoint), else null
   AdjLayout al;
 };
 

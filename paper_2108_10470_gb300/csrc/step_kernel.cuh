@@ -1442,6 +1442,15 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
           tp[TL.con + 2 * TL.ccap + c] = s_con[2 * CC + c];
           tp[TL.con + 3 * TL.ccap + c] = __int_as_float(s_coni[5 * CC + c]);
           tp[TL.con + 4 * TL.ccap + c] = __int_as_float(s_coni[7 * CC + c]);
+          if (has_pairs) {  // body b (-1: the ground), candidate, normal, b's actor offset
+            tp[TL.con + 5 * TL.ccap + c] = __int_as_float(s_coni[9 * CC + c]);
+            tp[TL.con + 6 * TL.ccap + c] = __int_as_float(s_coni[6 * CC + c]);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+              tp[TL.con + (7 + k) * TL.ccap + c] = s_con[(11 + k) * CC + c];
+              tp[TL.con + (10 + k) * TL.ccap + c] = s_con[(14 + k) * CC + c];
+            }
+          }
         }
         for (int r = lane; r < R; r += G) {
           reinterpret_cast<float4*>(tp + TL.rowc)[r] = s_rowc[r];

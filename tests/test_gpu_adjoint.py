@@ -259,10 +259,10 @@ def test_rollout_gradient_matches_oracle_and_checkpointing_is_exact(name, steps,
     x-velocity: gradients w.r.t. every action and the initial DOF state through the autograd rollout
     (checkpoints of 4 steps) against the oracle's forward-mode rollout; checkpoint lengths 1, 4 and
     the whole rollout, with the tapes kept from the forward pass or recomputed, give bitwise equal
-    gradients (the hand runs in forward mode, where there is no tape to keep). max_bad envs may
-    deviate by more than 1e-2: the
-    hand's contact-rich rollouts include an env whose derivative evaluated in single precision by the
-    oracle itself lands 8e-2 from its FP64 value (a clamp within rounding of its threshold)."""
+    gradients (both through the reverse pass, the hand's with its capsule-box pair contacts).
+    max_bad envs may deviate by more than 1e-2: the hand's contact-rich rollouts include an env
+    whose derivative evaluated in single precision by the oracle itself lands 8e-2 from its FP64
+    value (a clamp within rounding of its threshold)."""
     w = W.ant_workload(8) if name == "ant" else W.hand_workload(8)
     root, dof, acts = W.seeded_inputs(w, 11, steps)
     l4, gd4, ga4, _ = loss_grad_gpu(w, root, dof, acts, 4, keep_tapes=False)

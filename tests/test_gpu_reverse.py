@@ -11,7 +11,9 @@ which uses them where they cover the handle) against the FP64 oracle's forward-m
   An env whose FP32 evaluation takes a different branch (a clamp or target within rounding of its
   threshold) may deviate: at most one env per test.
 * The reverse and the forward-mode GPU evaluations agree (the second, independent kernel).
-* Handles the reverse pass does not cover (shape pairs, ball joints) report no tape size.
+* Capsule-box shape pairs (the hand holding its cube; a batch mixing Ant, Humanoid and hand envs)
+  go through the same checks.
+* Handles the reverse pass does not cover (ball joints) report no tape size.
 """
 import numpy as np
 import pytest
@@ -38,7 +40,8 @@ STATE = ("root_state", "dof_state", "impulse_cache", "net_contact_force", "conta
 
 @pytest.mark.parametrize("name,n,plan", [("ant", 67, "per_type"), ("humanoid", 37, "per_type"), ("cartpole", 64, "per_type"),
                                          ("driven_ant", 40, "per_type"), ("ant", 67, "persistent"),
-                                         ("humanoid", 37, "row_solver"), ("mixed_no_hand", 48, "per_type")])
+                                         ("humanoid", 37, "row_solver"), ("mixed_no_hand", 48, "per_type"),
+                                         ("hand", 37, "per_type"), ("mixed", 48, "per_type"), ("mixed", 48, "persistent")])
 def test_taped_step_is_the_step(name, n, plan):
     """Six steps of sim_step and of sim_step_taped from the same seeded state: every view equal bit
     for bit (the same kernels, given a tape pointer: the tape stores are their only difference)."""
@@ -47,6 +50,8 @@ def test_taped_step_is_the_step(name, n, plan):
     if name == "mixed_no_hand":
         ant, hum = W.ant(), W.humanoid()
         w = W.Workload("two_types", [ant, hum], np.array([i % 2 for i in range(n)], np.int32), 1, n, W.Params())
+    elif name == "mixed":
+        w = W.mixed_workload(n)
     else:
         w = WORKLOADS[name](n)
     flags = sim.SIM_FLAG_SIGNATURE | {"per_type": 0, "persistent": sim.SIM_FLAG_PERSISTENT,
@@ -102,19 +107,25 @@ def qtangent(q, k):
     return t
 
 
+def free_rows(w):
+    """Per root-state row (actor): whether its root is floating (its velocities are state)."""
+    return np.array([m.free_root for e in range(w.n_envs) for m in w.actor_models(e)])
+
+
 def directions(w, r, c):
-    """Input directions seeded in every env at once: (label, root, dof, act, cache) tangents."""
+    """Input directions seeded in every env at once: (label, root, dof, act, cache) tangents; the
+    root velocity directions on the floating roots only."""
     nj = w.n_dof // w.n_envs
-    free = w.models[0].free_root
+    free = free_rows(w)
     out = []
     for k in range(3):
         t = np.zeros_like(r); t[:, k] = 1.0
         out.append((f"p{k}", t, None, None, None))
         t = np.zeros_like(r); t[:, 3:7] = qtangent(r[:, 3:7], k)
         out.append((f"th{k}", t, None, None, None))
-        if free:
+        if free.any():
             for base, nm in ((7, "v"), (10, "w")):
-                t = np.zeros_like(r); t[:, base + k] = 1.0
+                t = np.zeros_like(r); t[free, base + k] = 1.0
                 out.append((f"{nm}{k}", t, None, None, None))
     for j in range(nj):
         for comp, nm in ((0, "q"), (1, "qd")):
@@ -165,13 +176,12 @@ def gpu_grad(w, g, r, dirs):
 
 def output_gradient(w, r, d, c, rng):
     gout = (rng.standard_normal(r.shape), rng.standard_normal(d.shape), rng.standard_normal(c.shape))
-    if not w.models[0].free_root:
-        gout[0][:, 7:] = 0.0  # a fixed root's velocity is not state
+    gout[0][~free_rows(w), 7:] = 0.0  # a fixed root's velocity is not state
     return gout
 
 
 @pytest.mark.parametrize("name,n", [("ant", 40), ("humanoid", 16), ("cartpole", 32), ("driven_ant", 24),
-                                    ("tendon_ant", 24), ("pushed_ant", 24)])
+                                    ("tendon_ant", 24), ("pushed_ant", 24), ("hand", 12), ("hand_tendon", 8)])
 def test_reverse_vjp_matches_oracle_derivative(name, n):
     w = WORKLOADS[name](n)
     r, d, c, a = warm(w, seed=5)
@@ -202,7 +212,7 @@ def test_reverse_vjp_matches_oracle_derivative(name, n):
 
 
 @pytest.mark.parametrize("name,n", [("ant", 40), ("humanoid", 16), ("driven_ant", 24), ("tendon_ant", 24),
-                                    ("pushed_ant", 24)])
+                                    ("pushed_ant", 24), ("hand", 12)])
 def test_reverse_and_forward_mode_agree(name, n):
     """The reverse pass against the forward-mode kernel (SIM_FLAG_TANGENT_VJP) on the same inputs:
     two FP32 evaluations of the same derivative; the quaternion gradient compared along the sphere."""
@@ -229,17 +239,79 @@ def test_reverse_and_forward_mode_agree(name, n):
     dirs = directions(w, r, c)
     A, B = gpu_grad(w, g_rev, r, dirs), gpu_grad(w, g_fwd, r, dirs)
     rel = np.abs(A - B).max(1) / np.maximum(1.0, np.abs(B).max(1))
-    print(f"{name} x{n}: reverse vs forward mode, relative deviation median {np.median(rel):.2e}, max {rel.max():.2e}")
-    assert (rel <= 1e-2).mean() >= 0.95 and np.median(rel) <= 1e-3
+    far = [(e, dirs[int(np.argmax(np.abs(A[e] - B[e])))][0]) for e in np.nonzero(rel > 1e-2)[0]]
+    print(f"{name} x{n}: reverse vs forward mode, relative deviation median {np.median(rel):.2e}, max {rel.max():.2e}, "
+          f"envs past 1e-2 (env, direction) {far}")
+    # two FP32 evaluations of the forward values too: an env whose contact or clamp decision lies
+    # within rounding of its threshold may take different branches in the two kernels
+    assert len(far) <= max(1, n // 20) and np.median(rel) <= 1e-3
 
 
-@pytest.mark.parametrize("name", ["hand", "hand_tendon", "ball_ant"])
-def test_uncovered_handles_report_no_tape(name):
-    """Shape pairs and ball joints are differentiated in forward mode."""
-    w = WORKLOADS[name](4)
-    s, _ = make_sim(name, w)
-    assert s.tape_floats() is None
+def test_uncovered_handles_report_no_tape():
+    """Ball joints are differentiated in forward mode; shape pairs have a tape."""
+    for name, taped in (("ball_ant", False), ("hand", True), ("hand_tendon", True)):
+        w = WORKLOADS[name](4)
+        s, _ = make_sim(name, w)
+        assert (s.tape_floats() is not None) == taped, name
+        s.destroy()
+
+
+def env_cache_len(w, e):
+    """Impulse-cache entries of env e: 3 per contact candidate (ground candidates of every shape,
+    five per capsule-box pair across actors), 2 per joint DOF, 2 per tendon."""
+    models = w.actor_models(e)
+    per = {W.SHAPE_SPHERE: 1, W.SHAPE_CAPSULE: 2, W.SHAPE_BOX: 8}
+    cand = sum(per[int(t)] for m in models for t in m.shape_type)
+    caps = [sum(int(t == W.SHAPE_CAPSULE) for t in m.shape_type) for m in models]
+    boxes = [sum(int(t == W.SHAPE_BOX) for t in m.shape_type) for m in models]
+    cand += 5 * sum(caps[i] * boxes[j] + boxes[i] * caps[j] for i in range(len(models)) for j in range(i + 1, len(models)))
+    return 3 * cand + 2 * w.env_jdof(e) + 2 * sum(len(m.tendons or []) for m in models)
+
+
+def test_reverse_and_forward_mode_agree_on_a_mixed_batch():
+    """Ant, Humanoid and hand envs in one handle (three env types, each with its own adjoint
+    launch; the hand's with the pair phase, Y read from the tape and its adjoint in global memory):
+    the reverse pass against the forward-mode kernel, per env over all of its input gradients."""
+    import torch
+    from paper_2108_10470_gb300 import sim
+    w = W.mixed_workload(24)
+    r, d, c, a = warm(w, seed=14)
+    rng = np.random.default_rng(15)
+    gout = output_gradient(w, r, d, c, rng)
+    s = sim.Sim(w)
+    assert s.tape_floats() is not None
+    g_rev = gpu_vjp(s, r, d, c, a, gout)
     s.destroy()
+    s = sim.Sim(w, flags=sim.SIM_FLAG_TANGENT_VJP)
+    g_fwd = gpu_vjp(s, r, d, c, a, gout)
+    s.destroy()
+    assert not g_rev["status"].any() and not g_fwd["status"].any()
+    ra = np.cumsum([0] + [w.env_actor_count(e) for e in range(w.n_envs)])
+    rd = np.cumsum([0] + [w.env_jdof(e) for e in range(w.n_envs)])
+    free = free_rows(w)
+    rel = []
+    for e in range(w.n_envs):
+        parts = []
+        for k in ("grad_root_state_in", "grad_dof_state_in", "grad_dof_actuation", "grad_impulse_cache_in"):
+            A, B = g_rev[k], g_fwd[k]
+            if k == "grad_root_state_in":  # the quaternion gradient along the sphere, velocities of free roots
+                rows = slice(ra[e], ra[e + 1])
+                qa, qb, q = A[rows, 3:7], B[rows, 3:7], r[rows, 3:7]
+                ta = np.stack([(qa * qtangent(q, k2)).sum(1) for k2 in range(3)], 1)
+                tb = np.stack([(qb * qtangent(q, k2)).sum(1) for k2 in range(3)], 1)
+                vel = free[rows][:, None]
+                parts.append((np.concatenate([A[rows, :3], ta, A[rows, 7:] * vel], 1).ravel(),
+                              np.concatenate([B[rows, :3], tb, B[rows, 7:] * vel], 1).ravel()))
+            elif k == "grad_impulse_cache_in":
+                parts.append((A[e, :env_cache_len(w, e)], B[e, :env_cache_len(w, e)]))
+            else:
+                parts.append((A[rd[e]:rd[e + 1]].ravel(), B[rd[e]:rd[e + 1]].ravel()))
+        x = np.concatenate([p[0] for p in parts])
+        y = np.concatenate([p[1] for p in parts])
+        rel.append(np.abs(x - y).max() / max(1.0, np.abs(y).max()))
+    rel = np.array(rel)
+    print(f"mixed x{w.n_envs}: reverse vs forward mode, relative deviation median {np.median(rel):.2e}, max {rel.max():.2e}")
+    assert (rel <= 1e-2).mean() >= 0.9 and np.median(rel) <= 1e-3
 
 
 def test_reverse_vjp_full_size_sampled_envs():
