@@ -633,7 +633,7 @@ __device__ __noinline__ float2 pgs_delassus_form(const float* s_Y, const int YS,
 // (grp >= n_launch_envs: a dead group, which shadows the last env and never stores); sm is the
 // group's shared arena and rb the base of its contact and row blocks (sm itself, or a private
 // slot of global scratch in the GROWS variant).
-template <int G, bool GROWS, bool BALL = false>
+template <int G, bool GROWS, bool BALL = false, bool TAPE = true>
 __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA, const int grp, float* sm,
                                            float* rb) {
   const EnvTypeTable* __restrict__ T = TA.type;
@@ -642,7 +642,9 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
   const int gi = live ? grp : TA.n_launch_envs - 1;
   const int env = TA.env_ids ? TA.env_ids[gi] : TA.env_first + gi;
   const SmemLayout& Ly = TA.lay;
-  const bool tape_on = TA.tape != nullptr;  // sim_step_taped: record the reverse pass's tape
+  // sim_step_taped: record the reverse pass's tape (TAPE false: a caller that never records one,
+  // the persistent kernel, compiles without the tape stores)
+  const bool tape_on = TAPE && TA.tape != nullptr;
   int* smi = reinterpret_cast<int*>(sm);
   int* rbi = reinterpret_cast<int*>(rb);
 

@@ -44,7 +44,10 @@ STATE = ("root_state", "dof_state", "impulse_cache", "net_contact_force", "conta
                                          ("hand", 37, "per_type"), ("mixed", 48, "per_type"), ("mixed", 48, "persistent")])
 def test_taped_step_is_the_step(name, n, plan):
     """Six steps of sim_step and of sim_step_taped from the same seeded state: every view equal bit
-    for bit (the same kernels, given a tape pointer: the tape stores are their only difference)."""
+    for bit (the same kernels, given a tape pointer: the tape stores are their only difference).
+    A persistent handle's taped step runs the per-type kernels, while its step runs the persistent
+    kernel, whose tile bodies are compiled without the tape stores (another register allocation):
+    there the float views agree to rounding and the integer views exactly."""
     import torch
     from paper_2108_10470_gb300 import sim
     if name == "mixed_no_hand":
@@ -77,7 +80,11 @@ def test_taped_step_is_the_step(name, n, plan):
         tap.step_taped(tape)
         torch.cuda.synchronize()
         for v in STATE:
-            assert torch.equal(getattr(ref, v), getattr(tap, v)), (v, k)
+            x, y = getattr(ref, v), getattr(tap, v)
+            if plan == "persistent" and x.dtype == torch.float32:
+                assert torch.allclose(x, y, rtol=1e-4, atol=1e-5), (v, k, (x - y).abs().max().item())
+            else:
+                assert torch.equal(x, y), (v, k)
     for s in handles:
         s.destroy()
 
