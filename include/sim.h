@@ -328,7 +328,8 @@ typedef struct {
  * memory owned by the caller, in the layouts of the views of the same names; the handle supplies
  * the model and its stream, its views are not touched (the reverse pass steps a library-owned copy
  * of the input state, allocated on first use). Asynchronous. Errors: HANDLE, INVALID_ARG (a
- * required pointer NULL, dt or substeps invalid), CAPACITY (unsupported env type), CUDA. */
+ * required pointer NULL: the DOF-state and actuation buffers may be NULL when the handle has no
+ * joint DOFs; dt or substeps invalid), CAPACITY (unsupported env type), CUDA. */
 int sim_step_vjp(sim_handle h, const sim_vjp_buffers* b, float dt, int32_t substeps);
 
 /* ---- reverse pass of a recorded step ------------------------------------------------------------
@@ -368,7 +369,8 @@ typedef struct {
  * the output gradients in, the input gradients out (device memory owned by the caller, in the
  * layouts of the views of the same names; outputs may alias nothing else). One launch per env
  * type, one env per group of lanes, substeps in reverse order; the step's constraint and active
- * sets are those recorded. Asynchronous. Errors: HANDLE, INVALID_ARG, CAPACITY, CUDA. */
+ * sets are those recorded (the DOF gradient buffers may be NULL when the handle has no joint
+ * DOFs). Asynchronous. Errors: HANDLE, INVALID_ARG, CAPACITY, CUDA. */
 int sim_step_adjoint(sim_handle h, const float* tape, const sim_adjoint_buffers* b, float dt, int32_t substeps);
 
 typedef struct {

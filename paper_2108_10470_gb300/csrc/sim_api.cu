@@ -1263,7 +1263,8 @@ int sim_step_taped(sim_handle h, float* tape, float dt, int32_t substeps) {
 
 int sim_step_adjoint(sim_handle h, const float* tape, const sim_adjoint_buffers* b, float dt, int32_t substeps) {
   if (!valid_handle(h)) return SIM_ERR_HANDLE;
-  if (!tape || !b || !b->grad_root_state_in || !b->grad_dof_state_in || !b->grad_dof_actuation ||
+  const bool jd = h->N_D > 0;  // the DOF buffers are required only when there are joint DOFs
+  if (!tape || !b || !b->grad_root_state_in || (jd && (!b->grad_dof_state_in || !b->grad_dof_actuation)) ||
       !b->grad_impulse_cache_in)
     return SIM_ERR_INVALID_ARG;
   if (!(dt > 0.f) || !finite(dt) || substeps < 1) return SIM_ERR_INVALID_ARG;
@@ -1281,8 +1282,10 @@ int sim_step_adjoint(sim_handle h, const float* tape, const sim_adjoint_buffers*
 
 int sim_step_vjp(sim_handle h, const sim_vjp_buffers* b, float dt, int32_t substeps) {
   if (!valid_handle(h)) return SIM_ERR_HANDLE;
-  if (!b || !b->root_state || !b->dof_state || !b->dof_actuation || !b->impulse_cache || !b->grad_root_state_in ||
-      !b->grad_dof_state_in || !b->grad_dof_actuation || !b->grad_impulse_cache_in)
+  const bool jd = h->N_D > 0;  // the DOF buffers are required only when there are joint DOFs
+  if (!b || !b->root_state || (jd && (!b->dof_state || !b->dof_actuation || !b->grad_dof_state_in ||
+                                      !b->grad_dof_actuation)) ||
+      !b->impulse_cache || !b->grad_root_state_in || !b->grad_impulse_cache_in)
     return SIM_ERR_INVALID_ARG;
   if (!(dt > 0.f) || !finite(dt) || substeps < 1) return SIM_ERR_INVALID_ARG;
   if (!(h->params.flags & SIM_FLAG_TANGENT_VJP) && reverse_supported(h) == SIM_OK) {
@@ -1349,10 +1352,11 @@ int sim_step_vjp(sim_handle h, const sim_vjp_buffers* b, float dt, int32_t subst
 
 int sim_step_jvp(sim_handle h, const sim_jvp_buffers* b, float dt, int32_t substeps) {
   if (!valid_handle(h)) return SIM_ERR_HANDLE;
-  if (!b || !b->root_state || !b->dof_state || !b->dof_actuation || !b->impulse_cache || !b->tan_root_state ||
-      !b->tan_dof_state || !b->tan_dof_actuation || !b->tan_impulse_cache || !b->root_state_out ||
-      !b->dof_state_out || !b->impulse_cache_out || !b->tan_root_state_out || !b->tan_dof_state_out ||
-      !b->tan_impulse_cache_out)
+  const bool jd = h->N_D > 0;  // the DOF buffers are required only when there are joint DOFs
+  if (!b || !b->root_state || !b->impulse_cache || !b->tan_root_state || !b->tan_impulse_cache ||
+      !b->root_state_out || !b->impulse_cache_out || !b->tan_root_state_out || !b->tan_impulse_cache_out ||
+      (jd && (!b->dof_state || !b->dof_actuation || !b->tan_dof_state || !b->tan_dof_actuation ||
+              !b->dof_state_out || !b->tan_dof_state_out)))
     return SIM_ERR_INVALID_ARG;
   if (!(dt > 0.f) || !finite(dt) || substeps < 1) return SIM_ERR_INVALID_ARG;
   int rc = tangent_supported(h);
