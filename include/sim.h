@@ -297,8 +297,8 @@ int sim_autotune(sim_handle h, float dt, int32_t substeps, int32_t reps, double*
  * DOF_VELOCITY_TARGET views as constants (no gradient with respect to the targets), and so do the
  * RIGID_BODY_FORCE view's forces under SIM_FLAG_BODY_FORCES; tendon springs and tendon-limit rows
  * are differentiated, and so are capsule-box pair contacts.
- * Two evaluations. The reverse pass (sim_step_taped + sim_step_adjoint below) covers env types
- * without ball joints (shape pairs, tendons, drives and SIM_FLAG_BODY_FORCES included); there the
+ * Two evaluations. The reverse pass (sim_step_taped + sim_step_adjoint below) covers every env
+ * type (shape pairs, ball joints, tendons, drives and SIM_FLAG_BODY_FORCES included); there the
  * gradient w.r.t. a root quaternion is its component tangent to the unit sphere (the step's
  * dependence on |q| is an artefact of the formulation: the output quaternion is normalised).
  * Otherwise (and under SIM_FLAG_TANGENT_VJP) forward-mode dual arithmetic, one env per warp, each
@@ -338,9 +338,9 @@ int sim_step_vjp(sim_handle h, const sim_vjp_buffers* b, float dt, int32_t subst
  * substep, the substep's input state, its contact and constraint-row lists, the joint-space
  * factor L and Y = L^-1 J^T, the generalized acceleration, the solve's vectors and each row
  * update's impulse and separation (and, for a capsule-box pair contact, its second body, normal
- * and the two actors' offset); everything else is recomputed by the adjoint. Covered: env types
- * without ball joints (other handles are refused with INVALID_ARG, or CAPACITY when an env type's
- * adjoint arena does not fit a CTA, and differentiate through sim_step_vjp's forward mode). */
+ * and the two actors' offset); everything else is recomputed by the adjoint. Covered: every env
+ * type whose adjoint arena fits a CTA (otherwise CAPACITY; sim_step_vjp then differentiates in
+ * forward mode). */
 
 /* Floats of one step's tape (caller-owned device memory: allocate this many floats per recorded
  * step; the size depends on the handle's env types, solver iterations and substeps). Errors:

@@ -187,6 +187,30 @@ __device__ __forceinline__ float back_subst(const float* sL, const int LS, const
 }
 
 // ---------------------------------------------------------------------------------------------
+// Adjoint of a ball joint's rotation update q' = log(exp(q) exp(dq)) (rotation vectors, dq in the
+// child frame; the step keeps the shorter rotation), in forward mode with six tangents (q, dq):
+// qb = (dq'/dq)^T ob, dqb = (dq'/d dq)^T ob. qb and dqb may alias the inputs.
+__device__ __noinline__ void ball_integration_adjoint(const float* q, const float* dq, const float* ob, float* qb,
+                                                      float* dqb) {
+  constexpr int K = 6;
+  Dn<K> a0(q[0]), a1(q[1]), a2(q[2]), b0(dq[0]), b1(dq[1]), b2(dq[2]);
+  a0.d[0] = 1.f; a1.d[1] = 1.f; a2.d[2] = 1.f; b0.d[3] = 1.f; b1.d[4] = 1.f; b2.d[5] = 1.f;
+  Dn<K> e1[4], e2[4], qn[4], r[3];
+  drotvec_quat<K>(a0, a1, a2, e1);
+  drotvec_quat<K>(b0, b1, b2, e2);
+  qn[0] = e1[3] * e2[0] + e1[0] * e2[3] + e1[1] * e2[2] - e1[2] * e2[1];
+  qn[1] = e1[3] * e2[1] - e1[0] * e2[2] + e1[1] * e2[3] + e1[2] * e2[0];
+  qn[2] = e1[3] * e2[2] + e1[0] * e2[1] - e1[1] * e2[0] + e1[2] * e2[3];
+  qn[3] = e1[3] * e2[3] - e1[0] * e2[0] - e1[1] * e2[1] - e1[2] * e2[2];
+  dquat_rotvec<K>(qn, r);
+  float o[K];
+#pragma unroll
+  for (int j = 0; j < K; ++j) o[j] = ob[0] * r[0].d[j] + ob[1] * r[1].d[j] + ob[2] * r[2].d[j];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) { qb[c] = o[c]; dqb[c] = o[3 + c]; }
+}
+
+// ---------------------------------------------------------------------------------------------
 // One kept capsule-box sample (pair p, slot) in forward mode over the step's pair geometry, with six
 // tangents seeded by `mode`: 0 the capsule link's twist about its actor origin (rotation [w]x R,
 // link origin w x P + v), 1 the box link's, 2 the two actor origins (the capsule's, then the box's).
@@ -282,7 +306,7 @@ __device__ __noinline__ void pair_sample_adjoint(const EnvTypeTable* __restrict_
 // The reverse pass of one env (group of G lanes): sm is the group's arena (AdjLayout), gi its index
 // in the launch (the tape block), live false for the dead groups of the last CTA (they shadow the
 // last env and store nothing).
-template <int G, bool PAIRS>
+template <int G, bool PAIRS, bool BALL>
 __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs& TA, const AdjArgs& J, const int grp,
                                               float* sm) {
   const EnvTypeTable* __restrict__ T = TA.type;
@@ -343,6 +367,9 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
   const bool is_root = isl && par < 0;
   const bool free_root = is_root && jt == kFree;
   const bool has_dof = isl && (jt == kRevolute || jt == kPrismatic);
+  // ball joint (three generalized DOFs from gd: rotation vector, angular velocity in the child
+  // frame), compiled into the BALL instantiation only
+  const bool is_ball = BALL && isl && jt == kSpherical;
   const bool isg = lane < n;
   float* rec = s_link + kAdjLinkWords * l;
   float* slot = rec + kRecSlot;
@@ -391,6 +418,14 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
     qb = J.g_dof[(size_t)(dof_base + jd) * 2];
     qdb = J.g_dof[(size_t)(dof_base + jd) * 2 + 1];
   }
+  float bqb[3] = {0.f, 0.f, 0.f}, bwb[3] = {0.f, 0.f, 0.f}, bab[3] = {0.f, 0.f, 0.f};  // ball: q, qd, act
+  if (is_ball && J.g_dof) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      bqb[c] = J.g_dof[(size_t)(dof_base + jd + c) * 2];
+      bwb[c] = J.g_dof[(size_t)(dof_base + jd + c) * 2 + 1];
+    }
+  }
   if (is_root && J.g_root) {
     const float* gr = J.g_root + (size_t)actor_row * 13;
 #pragma unroll
@@ -432,9 +467,14 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
     // the substep's input state
     float q = 0.f, qd = 0.f, rq[4] = {0.f, 0.f, 0.f, 1.f};
     V3 rp = v3(0.f, 0.f, 0.f), rw = rp, rv = rp;
-    if (has_dof) { q = img[TL.st + 2 * l]; qd = img[TL.st + 2 * l + 1]; }
+    if (has_dof) { q = img[TL.st + 2 * jd]; qd = img[TL.st + 2 * jd + 1]; }
+    float bq[3] = {0.f, 0.f, 0.f}, bw[3] = {0.f, 0.f, 0.f};  // ball: rotation vector, angular velocity
+    if (is_ball) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) { bq[c] = img[TL.st + 2 * (jd + c)]; bw[c] = img[TL.st + 2 * (jd + c) + 1]; }
+    }
     if (is_root) {
-      const float* r = img + TL.st + 2 * L + 13 * T->actor[l];
+      const float* r = img + TL.st + 2 * T->n_jdof + 13 * T->actor[l];
       rp = v3(r[0], r[1], r[2]);
       rq[0] = r[3]; rq[1] = r[4]; rq[2] = r[5]; rq[3] = r[6];
       rv = v3(r[7], r[8], r[9]);
@@ -483,6 +523,12 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
             for (int k = 0; k < 9; ++k) Rw[k] = RB[k];
             P = Pp + mv(Rp, pp + mv(Rpj, jaxis * q));
             S[3] = aw.x; S[4] = aw.y; S[5] = aw.z;
+          } else if (BALL && jt == kSpherical) {
+            float qj[4], RJ[9];
+            rotvec_quat(bq[0], bq[1], bq[2], qj);
+            quat_to_mat(qj, RJ);
+            mm(RB, RJ, Rw);
+            P = Pp + mv(Rp, pp);
           } else {
 #pragma unroll
             for (int k = 0; k < 9; ++k) Rw[k] = RB[k];
@@ -490,7 +536,17 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
           }
           float sq[6];
 #pragma unroll
-          for (int k = 0; k < 6; ++k) { sq[k] = S[k] * qd; vs[k] = vp[k] + sq[k]; }
+          for (int k = 0; k < 6; ++k) sq[k] = S[k] * qd;
+          if (BALL && jt == kSpherical) {  // the child's axes about the actor origin, one per DOF
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              const V3 ax = v3(Rw[c], Rw[3 + c], Rw[6 + c]), px = cross(P, ax);
+              sq[0] += ax.x * bw[c]; sq[1] += ax.y * bw[c]; sq[2] += ax.z * bw[c];
+              sq[3] += px.x * bw[c]; sq[4] += px.y * bw[c]; sq[5] += px.z * bw[c];
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < 6; ++k) vs[k] = vp[k] + sq[k];
           crm6(vs, sq, cc);
         }
       }
@@ -530,6 +586,14 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
 #pragma unroll
         for (int k = 0; k < 6; ++k) s_SD[kSDS * gd + k] = S[k];
       }
+      if (is_ball) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const V3 ax = v3(Rw[c], Rw[3 + c], Rw[6 + c]), px = cross(P, ax);
+          float* Sc = s_SD + kSDS * (gd + c);
+          Sc[0] = ax.x; Sc[1] = ax.y; Sc[2] = ax.z; Sc[3] = px.x; Sc[4] = px.y; Sc[5] = px.z;
+        }
+      }
       if (free_root) {
 #pragma unroll
         for (int c = 0; c < 6; ++c)
@@ -544,6 +608,19 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
       V(kVDqb)[gd] = qb;   // q' = q + dq (qb stays: the identity path)
       V(kVVb)[gd] = qdb;   // qd' = v
       qdb = 0.f;
+    }
+    if (is_ball) {  // q' = log(exp(q) exp(dq)) (the shorter rotation), qd' = v
+      float dqv[3], qin[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) dqv[c] = V(kVDq)[gd + c];
+      ball_integration_adjoint(bq, dqv, bqb, qin, dqv);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        V(kVDqb)[gd + c] = dqv[c];
+        V(kVVb)[gd + c] = bwb[c];
+        bqb[c] = qin[c];
+        bwb[c] = 0.f;
+      }
     }
     if (is_root) {
       // rotation adjoint of the output quaternion q' (its component along q' is dropped)
@@ -903,8 +980,8 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
         const bool a_cap = T->shape_type[T->pair_a[p]] == kCapsule;
         const int la_ = s_coni[3 * TL.ccap + c];
         const int lc = a_cap ? la_ : lbk, lx = a_cap ? lbk : la_;
-        const float* Oc = img + TL.st + 2 * L + 13 * T->actor[lc];
-        const float* Ox = img + TL.st + 2 * L + 13 * T->actor[lx];
+        const float* Oc = img + TL.st + 2 * T->n_jdof + 13 * T->actor[lc];
+        const float* Ox = img + TL.st + 2 * T->n_jdof + 13 * T->actor[lx];
         float w[3][6];
 #pragma unroll 1
         for (int mode = 0; mode < 3; ++mode)
@@ -1023,6 +1100,18 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
 #pragma unroll
       for (int k = 0; k < 6; ++k) acc[k] += V(kVQdd)[gd + k];
     }
+    float bSb[3][6];  // ball: the three columns' S adjoints
+    if (BALL) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) bSb[c][k] = is_ball ? s_Sb[kSDS * (gd + c) + k] : 0.f;
+      if (is_ball)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+          for (int k = 0; k < 6; ++k) acc[k] += s_SD[kSDS * (gd + c) + k] * V(kVQdd)[gd + c];
+    }
     outward(acc, 6);
     float ag[6] = {acc[0], acc[1], acc[2], acc[3] - g.x, acc[4] - g.y, acc[5] - g.z};
     float u[6], Fc[6];
@@ -1055,6 +1144,14 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
     if (free_root) {
 #pragma unroll
       for (int k = 0; k < 6; ++k) fb[k] = -V(kVCb)[gd + k];
+    }
+    if (is_ball) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float cb = V(kVCb)[gd + c];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) { fb[k] -= cb * s_SD[kSDS * (gd + c) + k]; bSb[c][k] -= cb * Fc[k]; }
+      }
     }
     outward(fb, 6);
     float accb[6], vsb[6];
@@ -1092,6 +1189,25 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
 #pragma unroll
       for (int k = 0; k < 6; ++k) { vsb[k] += t[k]; Sbar[k] -= sqb[k] * qd; qdb -= S[k] * sqb[k]; }
     }
+    if (is_ball) {
+      float sq[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, t[6], sqb[6];
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          const float Sck = s_SD[kSDS * (gd + c) + k];
+          sq[k] += Sck * bw[c];
+          bSb[c][k] += accb[k] * V(kVQdd)[gd + c];
+        }
+      crf6(sq, accb, t);
+      crf6(vs, accb, sqb);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) vsb[k] += t[k];
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) { bSb[c][k] -= sqb[k] * bw[c]; bwb[c] -= s_SD[kSDS * (gd + c) + k] * sqb[k]; }
+    }
     if (free_root) {  // c_root = [0; p_dot x omega]
       const V3 cb = v3(accb[3], accb[4], accb[5]);
       const V3 a = cross(rw, cb), b = cross(cb, rv);
@@ -1102,6 +1218,12 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
     if (has_dof) {
 #pragma unroll
       for (int k = 0; k < 6; ++k) { Sbar[k] += vsb[k] * qd; qdb += S[k] * vsb[k]; }
+    }
+    if (is_ball) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) { bSb[c][k] += vsb[k] * bw[c]; bwb[c] += s_SD[kSDS * (gd + c) + k] * vsb[k]; }
     }
     if (free_root) {
 #pragma unroll
@@ -1115,6 +1237,17 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
         crf6(S, Sbar, t);
 #pragma unroll
         for (int k = 0; k < 6; ++k) wr[k] += t[k];
+      }
+      if (is_ball) {  // the columns are the child's axes: they turn with the link
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          float t[6], Sc[6];
+#pragma unroll
+          for (int k = 0; k < 6; ++k) Sc[k] = s_SD[kSDS * (gd + c) + k];
+          crf6(Sc, bSb[c], t);
+#pragma unroll
+          for (int k = 0; k < 6; ++k) wr[k] += t[k];
+        }
       }
       const V3 cw = v3(rec[kRecCw], rec[kRecCw + 1], rec[kRecCw + 2]);
       const float* icw = rec + kRecIcw;
@@ -1134,6 +1267,33 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
     if (has_dof) {
 #pragma unroll
       for (int k = 0; k < 6; ++k) qb += S[k] * wr[k];
+    }
+    if (is_ball) {
+      // the subtree turns about the child's axes by J_r(q) dq (exp(q + dq) = exp(q) exp(J_r dq)):
+      // q_bar += J_r^T p, p_c = S_c . wr, J_r^T p = p + a q x p + b q x (q x p)
+      V3 pp = v3(0.f, 0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        pp.x += s_SD[kSDS * gd + k] * wr[k];
+        pp.y += s_SD[kSDS * (gd + 1) + k] * wr[k];
+        pp.z += s_SD[kSDS * (gd + 2) + k] * wr[k];
+      }
+      const V3 qv = v3(bq[0], bq[1], bq[2]);
+      const float a2 = dot(qv, qv);
+      float ca, cb;
+      if (a2 < 1e-8f) {
+        ca = 0.5f - a2 / 24.f;
+        cb = 1.f / 6.f - a2 / 120.f;
+      } else {
+        const float an = sqrtf(a2);
+        float sn, cs;
+        sincosf(an, &sn, &cs);
+        ca = (1.f - cs) / a2;
+        cb = (an - sn) / (a2 * an);
+      }
+      const V3 qp = cross(qv, pp);
+      const V3 jt3 = pp + qp * ca + cross(qv, qp) * cb;
+      bqb[0] += jt3.x; bqb[1] += jt3.y; bqb[2] += jt3.z;
     }
     if (is_root) { thb[0] += wr[0]; thb[1] += wr[1]; thb[2] += wr[2]; }
 
@@ -1155,6 +1315,15 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
     if (free_root) {
 #pragma unroll
       for (int k = 0; k < 3; ++k) { rwb[k] += V(kVVb)[gd + k]; rvb[k] += V(kVVb)[gd + 3 + k]; }
+    }
+    if (is_ball) {  // tau = actuation - damping qd per DOF
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float cb = V(kVCb)[gd + c];
+        bab[c] += cb;
+        bwb[c] -= T->damping[l] * cb;
+        bwb[c] += V(kVVb)[gd + c];
+      }
     }
     // ---- input impulse cache adjoint: the warm-start impulses' adjoints at their slots ----
     if (live)
@@ -1180,11 +1349,16 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
   if (failed) {  // no gradient for an env whose tape did not arrive
     qb = qdb = actb = 0.f;
 #pragma unroll
+    for (int c = 0; c < 3; ++c) { bqb[c] = 0.f; bwb[c] = 0.f; bab[c] = 0.f; }
+#pragma unroll
     for (int k = 0; k < 3; ++k) { rpb[k] = 0.f; rwb[k] = 0.f; rvb[k] = 0.f; }
 #pragma unroll
     for (int k = 0; k < 4; ++k) rqb[k] = 0.f;
   }
   if (has_dof && !(isfinite(qb) && isfinite(qdb) && isfinite(actb))) status = 2;
+  if (is_ball && !(isfinite(bqb[0] + bqb[1] + bqb[2]) && isfinite(bwb[0] + bwb[1] + bwb[2]) &&
+                   isfinite(bab[0] + bab[1] + bab[2])))
+    status = 2;
   if (is_root && !(isfinite(rpb[0] + rpb[1] + rpb[2]) && isfinite(rqb[0] + rqb[1] + rqb[2] + rqb[3]) &&
                    isfinite(rwb[0] + rwb[1] + rwb[2]) && isfinite(rvb[0] + rvb[1] + rvb[2])))
     status = 2;
@@ -1194,6 +1368,14 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
       J.gi_dof[(size_t)(dof_base + jd) * 2] = qb;
       J.gi_dof[(size_t)(dof_base + jd) * 2 + 1] = qdb;
       J.gi_act[dof_base + jd] = actb;
+    }
+    if (is_ball) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        J.gi_dof[(size_t)(dof_base + jd + c) * 2] = bqb[c];
+        J.gi_dof[(size_t)(dof_base + jd + c) * 2 + 1] = bwb[c];
+        J.gi_act[dof_base + jd + c] = bab[c];
+      }
     }
     if (is_root) {
       float* o = J.gi_root + (size_t)actor_row * 13;
@@ -1207,14 +1389,14 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
 }
 
 // One launch per env type: blocks of blockDim / G groups, one env per group.
-template <int G, bool PAIRS>
+template <int G, bool PAIRS, bool BALL>
 __global__ void __launch_bounds__(64) adjoint_kernel(const __grid_constant__ StepArgs A,
                                                     const __grid_constant__ TypeArgs TA,
                                                     const __grid_constant__ AdjArgs J) {
   extern __shared__ __align__(16) float smem[];
   const int grp_blk = threadIdx.x / G;
   const int grp = blockIdx.x * (blockDim.x / G) + grp_blk;
-  adjoint_group<G, PAIRS>(A, TA, J, grp, smem + grp_blk * J.al.total);
+  adjoint_group<G, PAIRS, BALL>(A, TA, J, grp, smem + grp_blk * J.al.total);
 }
 
 }  // namespace artsim

@@ -43,7 +43,8 @@ int tangent_lanes_per_dir(int n_dirs);
 // Reverse pass (kernels_tape.cu): the adjoint kernel (64-thread CTAs, 64 / G envs each, the
 // AdjLayout arena per env). The tape is written by the per-type step kernels when TypeArgs::tape
 // is set.
-cudaError_t launch_adjoint_kernel(int G, const StepArgs& a, const TypeArgs& ta, const AdjArgs& j, cudaStream_t st);
+cudaError_t launch_adjoint_kernel(int G, bool ball, const StepArgs& a, const TypeArgs& ta, const AdjArgs& j,
+                                  cudaStream_t st);
 cudaError_t set_adjoint_kernel_smem_cap(int G, size_t bytes);
 // Mass matrices (what = 0, n_envs x n_max x n_max) or link Jacobians (what = 1, n_envs x l_max x 6 x
 // n_max) of the envs of one type at the current state, one thread per env.

@@ -1099,7 +1099,7 @@ TapeLayout tape_layout(const TypePlan& tp, int npos, int nvel) {
   const int n = t.n;
   int o = 0;
   t.hdr = o; o += 4;
-  t.st = o; o += 2 * T.n_links + 13 * T.n_actors;
+  t.st = o; o += 2 * T.n_jdof + 13 * T.n_actors;
   o = al4i(o);
   t.LT = n | 1;
   t.YT = t.rcap | 1;
@@ -1163,13 +1163,9 @@ AdjLayout adj_layout(const TypePlan& tp, int npos, int nvel) {
   return a;
 }
 
-// The reverse pass covers env types without ball joints whose adjoint arena fits a CTA.
+// The reverse pass covers every env type whose adjoint arena fits a CTA.
 int reverse_supported(const sim_s* h) {
   for (const TypePlan& tp : h->types) {
-    if (tp.tab.has_ball) {
-      g_last_error = "reverse pass: env types with ball joints use the forward-mode derivative";
-      return SIM_ERR_INVALID_ARG;
-    }
     const AdjLayout al = adj_layout(tp, h->params.pos_iters, h->params.vel_iters);
     if ((size_t)(kAdjThreads / tp.G) * al.total * sizeof(float) > kMaxSmemPerCta) {
       g_last_error = "reverse pass: the env type's adjoint arena exceeds a CTA's shared memory";
@@ -1234,7 +1230,7 @@ int launch_adjoint(sim_s* h, const StepArgs& a, const float* tape, AdjArgs j, cu
       j.ybg = tp.ybg;
     }
     CK(set_adjoint_kernel_smem_cap(tp.G, kMaxSmemPerCta));
-    const cudaError_t e = launch_adjoint_kernel(tp.G, a, ta, j, st);
+    const cudaError_t e = launch_adjoint_kernel(tp.G, tp.tab.has_ball != 0, a, ta, j, st);
     if (e != cudaSuccess) return cuda_fail(e, "adjoint_kernel launch");
   }
   return SIM_OK;

@@ -146,7 +146,8 @@ struct StepArgs {
 struct TapeLayout {
   int words;  // per env and substep (multiple of 4)
   int hdr;    // 4: n_con | n_lim | R | 0 (int bits)
-  int st;     // 2 per link (q, qd), then 13 per actor root (p 3 | quat 4 | v 3 | w 3)
+  int st;     // 2 per joint DOF row (q, qd; a ball joint's three rows: rotation vector, angular
+              // velocity), then 13 per actor root (p 3 | quat 4 | v 3 | w 3)
   int vec;    // 7 x n: qdd | v_free | z0 = L^T v_free | z final | dz final | v | dq
   int L;      // n x LT (LT = n | 1, odd), row-major, lower triangle
   int Linv;   // n: 1 / L_kk

@@ -823,9 +823,13 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
     if (tape_on) {
       tp = TA.tape + ((size_t)gi * A.substeps + sub) * TL.words;
       if (live) {
-        if (has_dof) { tp[TL.st + 2 * l] = q; tp[TL.st + 2 * l + 1] = qd; }
+        if (has_dof) { tp[TL.st + 2 * jd] = q; tp[TL.st + 2 * jd + 1] = qd; }
+        if (is_ball) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) { tp[TL.st + 2 * (jd + c)] = bst[c]; tp[TL.st + 2 * (jd + c) + 1] = bst[3 + c]; }
+        }
         if (is_root) {
-          float* r = tp + TL.st + 2 * L + 13 * T->actor[l];
+          float* r = tp + TL.st + 2 * T->n_jdof + 13 * T->actor[l];
           r[0] = rp.x; r[1] = rp.y; r[2] = rp.z; r[3] = rq[0]; r[4] = rq[1]; r[5] = rq[2]; r[6] = rq[3];
           r[7] = rv.x; r[8] = rv.y; r[9] = rv.z; r[10] = rw.x; r[11] = rw.y; r[12] = rw.z;
         }

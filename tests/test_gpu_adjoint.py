@@ -106,7 +106,8 @@ WORKLOADS = {"ant": W.ant_workload, "humanoid": W.humanoid_workload, "cartpole":
              "ball_ant": lambda n: W.homogeneous("ball_ant", W.ant(ball_hips=True), n), "driven_ant": _driven_ant,
              "pushed_ant": W.ant_workload,
              "tendon_ant": lambda n: W.homogeneous("tendon_ant", W.ant(tendons=True), n),
-             "hand": W.hand_workload, "hand_tendon": W.hand_tendon_workload}
+             "hand": W.hand_workload, "hand_tendon": W.hand_tendon_workload,
+             "ball_humanoid": lambda n: W.homogeneous("ball_humanoid", W.humanoid(ball_joints=True), n)}
 
 
 def make_sim(name, w, seed=9):

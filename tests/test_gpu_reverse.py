@@ -12,8 +12,8 @@ which uses them where they cover the handle) against the FP64 oracle's forward-m
   threshold) may deviate: at most one env per test.
 * The reverse and the forward-mode GPU evaluations agree (the second, independent kernel).
 * Capsule-box shape pairs (the hand holding its cube; a batch mixing Ant, Humanoid and hand envs)
-  go through the same checks.
-* Handles the reverse pass does not cover (ball joints) report no tape size.
+  and ball joints (the Ant with ball hips, the Humanoid with ball abdomen and hips) go through the
+  same checks; every handle has a tape.
 """
 import numpy as np
 import pytest
@@ -41,7 +41,8 @@ STATE = ("root_state", "dof_state", "impulse_cache", "net_contact_force", "conta
 @pytest.mark.parametrize("name,n,plan", [("ant", 67, "per_type"), ("humanoid", 37, "per_type"), ("cartpole", 64, "per_type"),
                                          ("driven_ant", 40, "per_type"), ("ant", 67, "persistent"),
                                          ("humanoid", 37, "row_solver"), ("mixed_no_hand", 48, "per_type"),
-                                         ("hand", 37, "per_type"), ("mixed", 48, "per_type"), ("mixed", 48, "persistent")])
+                                         ("hand", 37, "per_type"), ("mixed", 48, "per_type"), ("mixed", 48, "persistent"),
+                                         ("ball_ant", 40, "per_type"), ("ball_humanoid", 16, "per_type")])
 def test_taped_step_is_the_step(name, n, plan):
     """Six steps of sim_step and of sim_step_taped from the same seeded state: every view equal bit
     for bit (the same kernels, given a tape pointer: the tape stores are their only difference).
@@ -188,7 +189,8 @@ def output_gradient(w, r, d, c, rng):
 
 
 @pytest.mark.parametrize("name,n", [("ant", 40), ("humanoid", 16), ("cartpole", 32), ("driven_ant", 24),
-                                    ("tendon_ant", 24), ("pushed_ant", 24), ("hand", 12), ("hand_tendon", 8)])
+                                    ("tendon_ant", 24), ("pushed_ant", 24), ("hand", 12), ("hand_tendon", 8),
+                                    ("ball_ant", 24), ("ball_humanoid", 12)])
 def test_reverse_vjp_matches_oracle_derivative(name, n):
     w = WORKLOADS[name](n)
     r, d, c, a = warm(w, seed=5)
@@ -278,7 +280,7 @@ def check_vjp_against_oracle(name, w, s, ctl, r, d, c, a, gout):
 
 
 @pytest.mark.parametrize("name,n", [("ant", 40), ("humanoid", 16), ("driven_ant", 24), ("tendon_ant", 24),
-                                    ("pushed_ant", 24), ("hand", 12)])
+                                    ("pushed_ant", 24), ("hand", 12), ("ball_ant", 24), ("ball_humanoid", 12)])
 def test_reverse_and_forward_mode_agree(name, n):
     """The reverse pass against the forward-mode kernel (SIM_FLAG_TANGENT_VJP) on the same inputs:
     two FP32 evaluations of the same derivative; the quaternion gradient compared along the sphere."""
@@ -313,12 +315,12 @@ def test_reverse_and_forward_mode_agree(name, n):
     assert len(far) <= max(1, n // 20) and np.median(rel) <= 1e-3
 
 
-def test_uncovered_handles_report_no_tape():
-    """Ball joints are differentiated in forward mode; shape pairs have a tape."""
-    for name, taped in (("ball_ant", False), ("hand", True), ("hand_tendon", True)):
+def test_every_handle_has_a_tape():
+    """Shape pairs, tendons and ball joints: the reverse pass covers them all."""
+    for name in ("ball_ant", "ball_humanoid", "hand", "hand_tendon"):
         w = WORKLOADS[name](4)
         s, _ = make_sim(name, w)
-        assert (s.tape_floats() is not None) == taped, name
+        assert s.tape_floats() is not None, name
         s.destroy()
 
 
