@@ -1,13 +1,15 @@
 // Reverse (adjoint) pass of the env-step for sm_103a: the vector-Jacobian product of one recorded
 // step, one environment per group of G lanes, substeps in reverse order. The forward step's
 // discrete choices (contact set, limit rows, every projection and target branch of the solve) are
-// held fixed, as in the forward-mode derivative; the step's taped instantiation records what the
+// held fixed, as in the forward-mode derivative; the step kernels, given a tape, record what the
 // reverse needs (TapeLayout in sim_internal.h), and everything else is recomputed.
 //
 // Formulation. The forward step computes qdd = M^-1 (tau - b) (articulated-body algorithm), a
 // Gauss-Seidel solve in z = L^T v with Y = L^-1 J^T, and integration. Its adjoint is taken in the
 // same coordinates:
-//  * integration: joints are additive; the root quaternion's adjoint is carried as the adjoint of
+//  * integration: hinge and slider joints are additive; a ball joint's rotation update
+//    log(exp(q) exp(dq)) is differentiated locally in forward mode; the root quaternion's adjoint
+//    is carried as the adjoint of
 //    a world-axis rotation th (q_bar = 2 [th_bar; 0] (x) q, the component along q is dropped: the
 //    step's output quaternion is normalised), through the exact exponential by the left Jacobian
 //    of SO(3);
@@ -26,11 +28,14 @@
 //    actor origin, contact points) is attached to a link; its adjoint becomes a wrench on that link
 //    (a motion subspace S: S x* S_bar; a point x: [x x x_bar; x_bar]; an inertia: from its COM
 //    position and rotational inertia), and a joint's position adjoint is S . (wrenches summed over
-//    its subtree), the root rotation's the angular part over the whole actor.
-// Supported: floating and fixed roots, revolute, prismatic and fixed joints, ground contacts of
-// spheres, capsules and boxes, joint limits, damping, armature, joint drives, fixed tendons (springs
-// and length-limit rows) and external body forces (their values constants of the derivative). (Ball
-// joints and shape pairs use the forward-mode derivative kernel.)
+//    its subtree) (for a ball joint through the right Jacobian of SO(3): J_r(q)^T S^T W), the root
+//    rotation's the angular part over the whole actor;
+//  * capsule-box pair contacts: two-body rows, and each contact's point, normal and separation
+//    differentiated locally in forward mode over the pair geometry (three passes of six tangents).
+// Supported: floating and fixed roots, revolute, prismatic, ball and fixed joints, ground contacts
+// of spheres, capsules and boxes, capsule-box pairs, joint limits, damping, armature, joint drives,
+// fixed tendons (springs and length-limit rows) and external body forces (their values constants of
+// the derivative). The pair and ball-joint paths are separate instantiations (template flags).
 #pragma once
 #include "step_kernel.cuh"
 #include "tangent_step.cuh"

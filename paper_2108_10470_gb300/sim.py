@@ -404,7 +404,8 @@ class Sim:
 
     def tape_floats(self, substeps: Optional[int] = None) -> Optional[int]:
         """Floats of one recorded step's tape, or None if the reverse pass does not cover this
-        handle (its env types or flags): the derivative then runs in forward mode (step_vjp)."""
+        handle (an env type whose adjoint arena does not fit a CTA): the derivative then runs in
+        forward mode (step_vjp)."""
         sub = int(self.w.substeps if substeps is None else substeps)
         cache = self.__dict__.setdefault("_tape_floats", {})
         if sub not in cache:
