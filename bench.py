@@ -576,6 +576,7 @@ def adjoint_measure(dev, n_envs=1024, steps=64, checkpoint=16, reps=2):
     f_ms, b_ms = timed(None)
     rf_ms, rb_ms = timed(False)
     s.destroy()
+    hand = hand_adjoint_measure(dev)
     return {"value": n_envs * steps / (b_ms / 1e3), "unit": "adjoint env-steps/s",
             "workload": f"Ant-like, {n_envs} envs, {steps} env-steps, loss = mean final root x-velocity, gradients "
                         f"w.r.t. actions and initial DOF state, segments of {checkpoint} steps",
@@ -584,10 +585,49 @@ def adjoint_measure(dev, n_envs=1024, steps=64, checkpoint=16, reps=2):
             "forward_plus_backward_ms": f_ms + b_ms,
             "recompute": {"forward_ms": rf_ms, "backward_ms": rb_ms, "backward_over_forward": rb_ms / rf_ms,
                           "forward_plus_backward_ms": rf_ms + rb_ms},
+            "hand": hand,
             "method": ("reverse pass: sim_step_taped records each step's tape (in the forward pass when the tapes "
                        "are kept, else in the backward pass's re-run of each segment), sim_step_adjoint applies "
                        "the steps' adjoints in reverse order" if s_reverse else
                        "forward-mode dual kernel (one env per warp), vector-Jacobian product per env-step")}
+
+
+def hand_adjoint_measure(dev, n_envs=1024, steps=16, reps=2):
+    """The same rollout gradient on the hand-with-cube workload (capsule-box pair contacts: the
+    reverse pass's pair instantiation): 1024 envs, 16 steps from the seeded state, tapes kept."""
+    import torch
+
+    from paper_2108_10470_gb300 import autograd as AG, sim, workloads as W
+
+    w = W.hand_workload(n_envs)
+    s = sim.Sim(w)
+    root, dof, acts = W.seeded_inputs(w, 0, steps)
+    r0 = torch.from_numpy(root).to(dev)
+    d0 = torch.from_numpy(dof).to(dev).requires_grad_(True)
+    c0 = torch.zeros((n_envs, s.cache_len), device=dev)
+    A = torch.from_numpy(acts).to(dev).requires_grad_(True)
+    fwd, bwd = [], []
+    for rep in range(reps + 1):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record()
+        rf, _, _ = AG.rollout(s, r0, d0, c0, A, checkpoint=steps)
+        loss = rf[:, 7].mean()
+        e[1].record()
+        loss.backward()
+        e[2].record()
+        torch.cuda.synchronize()
+        if rep > 0:
+            fwd.append(e[0].elapsed_time(e[1]))
+            bwd.append(e[1].elapsed_time(e[2]))
+        d0.grad = None
+        A.grad = None
+    kept = AG.keep_tapes_by_default(s, steps)
+    s.destroy()
+    f_ms, b_ms = statistics.median(fwd), statistics.median(bwd)
+    return {"value": n_envs * steps / (b_ms / 1e3), "unit": "adjoint env-steps/s",
+            "workload": f"hand with cube, {n_envs} envs, {steps} env-steps, loss = mean final root x-velocity",
+            "policy": "tapes kept from the forward pass" if kept else "segments recomputed (checkpointing)",
+            "forward_ms": f_ms, "backward_ms": b_ms, "backward_over_forward": b_ms / f_ms}
 
 
 def run_adjoint_only(local_rank):
