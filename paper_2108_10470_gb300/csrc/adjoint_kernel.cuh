@@ -334,8 +334,11 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
   int* s_rowa = reinterpret_cast<int*>(img + TL.rowa);
   float* s_lam = img + TL.lamf;
   float* s_lam0 = img + TL.lam0;
-  float* s_lambef = img + TL.lamb;
-  float* s_seps = img + TL.seps;
+  // the row history (read in the solve's reverse): in the image, or with gY in place in the tape
+  const float* s_lambef = img + TL.lamb;
+  const float* s_seps = img + TL.seps;
+  // row work blocks, once the history is dead: the image's history block, or a global slot
+  float* rws = (PAIRS && al.gY) ? J.rwg + (size_t)grp * al.rw : img + TL.lamb;
   float* s_con = img + TL.con;
   int* s_coni = reinterpret_cast<int*>(s_con);
   const float* s_linv = img + TL.Linv;
@@ -346,7 +349,7 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
   float* s_lamb = sm + al.lamb;
   float* s_db = sm + al.db;
   float* s_invAb = sm + al.invAb;
-  float* s_xb = sm + al.xb;
+  float* s_xb = (PAIRS && al.gY) ? rws + al.frw : sm + al.xb;
   constexpr int XW = PAIRS ? 9 : 3;  // words per row of s_xb (AdjLayout::xbw)
   constexpr bool pairs_t = PAIRS;    // the type has capsule-box shape pairs (TL.cw > 5)
   float* s_pose = sm + al.pose;      // pairs: rotation 9 | origin 3 of each link
@@ -447,7 +450,7 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
 
   for (int sub = A.substeps - 1; sub >= 0; --sub) {
     const float* tp = J.tape + ((size_t)gi * A.substeps + sub) * TL.words;
-    if (PAIRS && al.gY) s_Y = tp + TL.Y;
+    if (PAIRS && al.gY) { s_Y = tp + TL.Y; s_lambef = tp + TL.lamb; s_seps = tp + TL.seps; }
     // ---- the tape block into the arena: one bulk copy by the TMA engine ----
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // this lane's writes to the image first
     __syncwarp();
@@ -858,7 +861,7 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
     // A pair row acts on two bodies, J_r = S . [x x k; k] on a's path and -S . [x_b x k; k] on b's
     // (x_b = x - o_b, o_b b's actor origin relative to a's; k the pair normal or a friction direction
     // of it): its adjoints of x, o_b and k go to the pair phase below ----
-    float* s_fr = s_lambef;  // 7 x RC words: [x x k; k] (6) | DOF mask; with shape pairs 7 more: b's
+    float* s_fr = rws;  // 7 x RC words: [x x k; k] (6) | DOF mask; with shape pairs 7 more: b's
     for (int r = n_lim + lane; r < R; r += G) {
       const float4 hc = s_rowc[r];
       const int a = s_rowa[r];
@@ -963,7 +966,7 @@ __device__ __forceinline__ void adjoint_group(const StepArgs& A, const TypeArgs&
     // links and to the two actor origins by three forward-mode passes over the pair geometry (the
     // capsule link's twist, the box link's, the origins), into 18 words per contact: wrench on link
     // a (6) | on link b (6) | adjoint of a's actor origin (3) | of b's (3) ----
-    float* s_pw = s_lambef;  // (the row vectors of the gather above are dead)
+    float* s_pw = rws;  // (the row vectors of the gather above are dead)
     if (pairs_t) {
       for (int c = lane; c < n_con; c += G) {
         const int lbk = s_coni[5 * TL.ccap + c];

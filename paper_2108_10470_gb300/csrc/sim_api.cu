@@ -1113,6 +1113,7 @@ TapeLayout tape_layout(const TypePlan& tp, int npos, int nvel) {
   t.rowa = o; o += t.rcap;
   t.lam0 = o; o += t.rcap;
   t.lamf = o; o += t.rcap;
+  o = al4i(o);  // a reverse arena without room for the row history copies the block up to here
   t.lamb = o; o += t.iters * t.rcap;
   t.seps = o; o += (npos + 1) * t.rcap;
   // the adjoint reuses these two blocks, once read, as 7 words per row (14 with shape pairs: the
@@ -1138,7 +1139,9 @@ AdjLayout adj_layout(const TypePlan& tp, int npos, int nvel) {
   for (int gY = 0; gY < 2; ++gY) {
     int o = 0;
     a.gY = gY;
-    a.imgw = gY ? tl.Y : tl.words;
+    a.imgw = gY ? tl.lamb : tl.words;
+    a.frw = std::max(14 * rc, 18 * tl.ccap);
+    a.rw = gY ? a.frw + 9 * rc : 0;
     a.img = o; o += a.imgw;
     a.bar = o; o += 4;
     a.Yb = o; o += gY ? 0 : n * a.YS;
@@ -1147,7 +1150,7 @@ AdjLayout adj_layout(const TypePlan& tp, int npos, int nvel) {
     a.db = o; o += rc;
     a.invAb = o; o += rc;
     a.xbw = pairs ? 9 : 3;
-    a.xb = o; o += a.xbw * rc;
+    a.xb = o; o += gY ? 0 : a.xbw * rc;
     a.vec = o; o += kAdjVecs * n;
     a.SD = o; o += 7 * n;   // 6-vectors at an odd stride of 7
     a.FM = o; o += 7 * n;
@@ -1222,12 +1225,15 @@ int launch_adjoint(sim_s* h, const StepArgs& a, const float* tape, AdjArgs j, cu
     j.tape = tape + offs[t];
     j.al = adj_layout(tp, a.pos_iters, a.vel_iters);
     j.ybg = nullptr;
+    j.rwg = nullptr;
     if (j.al.gY) {  // one slot per group of the launch (the dead groups of the last CTA own theirs)
       const size_t gpb = kAdjThreads / tp.G, groups = (tp.envs.size() + gpb - 1) / gpb * gpb;
-      const int rc = grow_buffer(&tp.ybg, &tp.ybg_floats, groups * (size_t)std::max(tp.tab.n_gen, 1) * j.al.YS,
-                                 "cudaMalloc (reverse-pass Y adjoint)");
+      const size_t yb = groups * (size_t)std::max(tp.tab.n_gen, 1) * j.al.YS;
+      const int rc = grow_buffer(&tp.ybg, &tp.ybg_floats, yb + groups * (size_t)j.al.rw,
+                                 "cudaMalloc (reverse-pass Y adjoint and row work)");
       if (rc != SIM_OK) return rc;
       j.ybg = tp.ybg;
+      j.rwg = tp.ybg + yb;
     }
     CK(set_adjoint_kernel_smem_cap(tp.G, kMaxSmemPerCta));
     const cudaError_t e = launch_adjoint_kernel(tp.G, tp.tab.has_ball != 0, a, ta, j, st);

@@ -187,10 +187,12 @@ struct TypeArgs {
 // rewound in place during the reverse solve.
 struct AdjLayout {
   int img;          // the tape block (16-byte aligned): imgw words of it
-  int imgw;         // TapeLayout::words, or TapeLayout::Y when gY
-  int gY;           // 1: Y is read in place from the tape and its adjoint lives in global scratch
-                    // (AdjArgs::ybg), for env types with shape pairs whose arena would not otherwise
-                    // fit a CTA's envs
+  int imgw;         // TapeLayout::words, or TapeLayout::lamb when gY
+  int gY;           // 1 (env types with shape pairs whose arena would not otherwise fit a CTA's
+                    // envs): Y and the row history (lamb, seps) are read in place from the tape, and
+                    // Y's adjoint (AdjArgs::ybg) and the row work blocks (AdjArgs::rwg: frw words of
+                    // row vectors, then xbw x rcap of xb) live in global slots per group
+  int frw, rw;      // gY: words of the row-vector part and of a whole rwg slot
   int bar;          // the bulk copy's mbarrier (8-byte aligned, 4 words reserved)
   int Yb, YS;       // n x YS (YS = the tape's Y stride): Y's adjoint, then the Jacobian-row adjoint
   int Mb, LS;       // n x LS (LS = the tape's L stride): P, then L^-T P, then the inertia adjoint
@@ -219,6 +221,7 @@ struct AdjArgs {
   float* gi_cache;           // (n_envs, cache_stride) out (also the working storage between substeps)
   int* status;               // (n_envs,) out or null
   float* ybg;                // al.gY: n x YS floats per group of the launch (Y's adjoint), else null
+  float* rwg;                // al.gY: al.rw floats per group of the launch (row work blocks), else null
   AdjLayout al;
 };
 
