@@ -199,10 +199,13 @@ int sim_create(const sim_model_desc* models, int32_t n_models, const int32_t* en
  * INVALID_ARG (dt <= 0 or non-finite, substeps < 1), CUDA (launch failure). */
 int sim_step(sim_handle h, float dt, int32_t substeps);
 
-/* End-to-end step from host memory: copies host_actuation (N_D floats) into DOF_ACTUATION, runs
- * sim_step, copies ROOT_STATE (N_A*13 floats) and DOF_STATE (N_D*2 floats) back into the host
- * buffers (either output may be NULL) and synchronises the stream. Host buffers may be pageable
- * or pinned; pinned memory is faster. Errors as sim_step. */
+/* End-to-end step from host memory: host_actuation (N_D floats) into DOF_ACTUATION, sim_step,
+ * ROOT_STATE (N_A*13 floats) and DOF_STATE (N_D*2 floats) into the host buffers (either output may
+ * be NULL), then a stream synchronisation. Pinned buffers (CUDA-allocated or registered host
+ * memory, which the device addresses) are read and written by the step kernels themselves: no
+ * copy is launched; pageable buffers, and every buffer of a SIM_FLAG_GRAPH or SIM_FLAG_PERSISTENT
+ * handle, are copied.
+ * Either way the views end as after sim_step. Errors as sim_step. */
 int sim_step_host(sim_handle h, const float* host_actuation, float* host_root_out, float* host_dof_out,
                   float dt, int32_t substeps);
 

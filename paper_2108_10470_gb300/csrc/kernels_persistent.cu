@@ -19,7 +19,7 @@ __device__ __noinline__ void persistent_tile(const StepArgs& A, const TypeArgs& 
   const int grp = tile * (32 / G) + gw;
   float* sm = wsm + gw * TA.lay.total;
   float* rb = GROWS ? TA.scratch + (size_t)(gwarp * (32 / G) + gw) * TA.lay.scratch_words : sm;
-  step_group<G, GROWS, BALL, false>(A, TA, grp, sm, rb);  // taped steps use the per-type kernels
+  step_group<G, GROWS, BALL, false>(A, TA, grp, sm, rb);  // taped and direct-buffer steps: per-type kernels
 }
 
 template <bool BALL>

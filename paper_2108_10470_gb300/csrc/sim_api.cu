@@ -91,6 +91,10 @@ struct sim_s {
   int graph_substeps = 0;
   // sim_step_vjp by the reverse pass: a copy of the step's input state stepped by the taped step,
   // and the tape (allocated on first use)
+  // sim_step_host with pinned host buffers: their device addresses, for the duration of the call
+  const float* zc_act = nullptr;
+  float* zc_root = nullptr;
+  float* zc_dof = nullptr;
   float* rv_state = nullptr;
   size_t rv_state_floats = 0;
   float* rv_tape = nullptr;
@@ -573,6 +577,8 @@ void fill_common(const sim_s* h, float dt, int substeps, StepArgs& a) {
   a.env_dof_base = h->d_dof_base; a.env_body_base = h->d_body_base; a.env_actor_base = h->d_actor_base;
   a.pos_target = h->pos_target; a.vel_target = h->vel_target; a.body_force = h->body_force;
   a.dof_force = h->dof_force; a.body_state = h->body_state;
+  if (h->zc_act) { a.act = h->zc_act; a.act_copy = h->act; }
+  a.root_out = h->zc_root; a.dof_out = h->zc_dof;
   a.cache_stride = h->cache_stride; a.pair_stride = h->pair_stride;
   a.dt = dt; a.h = dt / (float)substeps; a.substeps = substeps;
   a.gx = p.gravity[0]; a.gy = p.gravity[1]; a.gz = p.gravity[2];
@@ -1067,16 +1073,41 @@ int sim_step_static_scratch(sim_handle h, const sim_state_buffers* io, float dt,
   return SIM_OK;
 }
 
+namespace {
+// Device address of a pinned host buffer (CUDA-allocated or registered), or null for pageable memory.
+void* device_view_of_host(const void* p) {
+  if (!p) return nullptr;
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();  // not an error of the step: the buffer is copied instead
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+}  // namespace
+
 int sim_step_host(sim_handle h, const float* host_actuation, float* host_root_out, float* host_dof_out, float dt,
                   int32_t substeps) {
   if (!valid_handle(h)) return SIM_ERR_HANDLE;
   if (!host_actuation && h->N_D > 0) return SIM_ERR_INVALID_ARG;
-  if (h->N_D > 0) CK(cudaMemcpyAsync(h->act, host_actuation, sizeof(float) * h->N_D, cudaMemcpyHostToDevice, h->stream));
+  if (!(dt > 0.f) || !finite(dt) || substeps < 1) return SIM_ERR_INVALID_ARG;
+  // Pinned buffers are read and written by the step kernels themselves (the actuation loads, the
+  // final state stores), with no copy launch; pageable buffers, graph handles (whose captured
+  // launches have fixed arguments) and persistent handles (whose kernel is compiled without these
+  // accesses) are copied.
+  const bool direct = !(h->params.flags & (SIM_FLAG_GRAPH | SIM_FLAG_PERSISTENT));
+  const float* za = (direct && h->N_D > 0) ? static_cast<const float*>(device_view_of_host(host_actuation)) : nullptr;
+  float* zr = direct ? static_cast<float*>(device_view_of_host(host_root_out)) : nullptr;
+  float* zd = (direct && h->N_D > 0) ? static_cast<float*>(device_view_of_host(host_dof_out)) : nullptr;
+  if (h->N_D > 0 && !za)
+    CK(cudaMemcpyAsync(h->act, host_actuation, sizeof(float) * h->N_D, cudaMemcpyHostToDevice, h->stream));
+  h->zc_act = za; h->zc_root = zr; h->zc_dof = zd;
   const int rc = sim_step(h, dt, substeps);
+  h->zc_act = nullptr; h->zc_root = nullptr; h->zc_dof = nullptr;
   if (rc != SIM_OK) return rc;
-  if (host_root_out)
+  if (host_root_out && !zr)
     CK(cudaMemcpyAsync(host_root_out, h->root, sizeof(float) * h->N_A * 13, cudaMemcpyDeviceToHost, h->stream));
-  if (host_dof_out && h->N_D > 0)
+  if (host_dof_out && h->N_D > 0 && !zd)
     CK(cudaMemcpyAsync(host_dof_out, h->dof, sizeof(float) * h->N_D * 2, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   return SIM_OK;

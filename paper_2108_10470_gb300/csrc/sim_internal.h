@@ -112,7 +112,10 @@ struct StepArgs {
   // global tensors
   float* root;               // (N_A, 13)
   float* dof;                // (N_D, 2)
-  const float* act;          // (N_D,)
+  const float* act;          // (N_D,) (device memory, or pinned host memory the device addresses)
+  float* act_copy;           // non-null: every actuation value read is also stored here (the view)
+  float* root_out;           // non-null: the step's final root rows are also stored here
+  float* dof_out;            // non-null: the step's final DOF rows are also stored here
   float* net_force;          // (N_B, 3)
   float* cache;              // (n_envs, cache_stride)
   int* pairs;                // (n_envs, pair_stride, 3)

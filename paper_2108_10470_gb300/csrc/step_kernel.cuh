@@ -633,7 +633,7 @@ __device__ __noinline__ float2 pgs_delassus_form(const float* s_Y, const int YS,
 // (grp >= n_launch_envs: a dead group, which shadows the last env and never stores); sm is the
 // group's shared arena and rb the base of its contact and row blocks (sm itself, or a private
 // slot of global scratch in the GROWS variant).
-template <int G, bool GROWS, bool BALL = false, bool TAPE = true>
+template <int G, bool GROWS, bool BALL = false, bool PER_TYPE = true>
 __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA, const int grp, float* sm,
                                            float* rb) {
   const EnvTypeTable* __restrict__ T = TA.type;
@@ -642,9 +642,11 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
   const int gi = live ? grp : TA.n_launch_envs - 1;
   const int env = TA.env_ids ? TA.env_ids[gi] : TA.env_first + gi;
   const SmemLayout& Ly = TA.lay;
-  // sim_step_taped: record the reverse pass's tape (TAPE false: a caller that never records one,
-  // the persistent kernel, compiles without the tape stores)
-  const bool tape_on = TAPE && TA.tape != nullptr;
+  // sim_step_taped: record the reverse pass's tape. PER_TYPE false (the persistent kernel's tile
+  // bodies: taped steps and sim_step_host's direct buffers always use the per-type kernels)
+  // compiles without the tape stores and the direct host-buffer loads and stores.
+  const bool tape_on = PER_TYPE && TA.tape != nullptr;
+  const bool direct_io = PER_TYPE;
   int* smi = reinterpret_cast<int*>(sm);
   int* rbi = reinterpret_cast<int*>(rb);
 
@@ -710,6 +712,7 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
     q = A.dof[(size_t)(dof_base + jd) * 2];
     qd = A.dof[(size_t)(dof_base + jd) * 2 + 1];
     tau = A.act[dof_base + jd];  // joint force of the step; damping is added per substep
+    if (direct_io && A.act_copy && live) A.act_copy[dof_base + jd] = tau;
   }
   // ball-joint links keep their state in a shared slot of kBallWords (not in registers, which the
   // rest of the global-rows variant needs): U (3 x 6) | D^-1 (sym 3 x 3) | u (3) | q (3) | qd (3) | tau (3)
@@ -721,6 +724,7 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
       bst[k] = A.dof[(size_t)(dof_base + jd + k) * 2];
       bst[3 + k] = A.dof[(size_t)(dof_base + jd + k) * 2 + 1];
       bst[6 + k] = A.act[dof_base + jd + k];
+      if (direct_io && A.act_copy && live) A.act_copy[dof_base + jd + k] = bst[6 + k];
     }
   }
   float q_t = 0.f, v_t = 0.f;  // drive targets
@@ -1641,16 +1645,31 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
       r[3] = rq[0]; r[4] = rq[1]; r[5] = rq[2]; r[6] = rq[3];
       r[7] = rv.x; r[8] = rv.y; r[9] = rv.z;
       r[10] = rw.x; r[11] = rw.y; r[12] = rw.z;
+      if (direct_io && A.root_out) {  // sim_step_host with a pinned output buffer: the row goes there too
+        float* o = A.root_out + (size_t)(A.env_actor_base[env] + T->actor[l]) * 13;
+        o[0] = rp.x; o[1] = rp.y; o[2] = rp.z;
+        o[3] = rq[0]; o[4] = rq[1]; o[5] = rq[2]; o[6] = rq[3];
+        o[7] = rv.x; o[8] = rv.y; o[9] = rv.z;
+        o[10] = rw.x; o[11] = rw.y; o[12] = rw.z;
+      }
     }
     if (has_dof) {
       A.dof[(size_t)(dof_base + jd) * 2] = q;
       A.dof[(size_t)(dof_base + jd) * 2 + 1] = qd;
+      if (direct_io && A.dof_out) {
+        A.dof_out[(size_t)(dof_base + jd) * 2] = q;
+        A.dof_out[(size_t)(dof_base + jd) * 2 + 1] = qd;
+      }
     }
     if (is_ball) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         A.dof[(size_t)(dof_base + jd + c) * 2] = bst[c];
         A.dof[(size_t)(dof_base + jd + c) * 2 + 1] = bst[3 + c];
+        if (direct_io && A.dof_out) {
+          A.dof_out[(size_t)(dof_base + jd + c) * 2] = bst[c];
+          A.dof_out[(size_t)(dof_base + jd + c) * 2 + 1] = bst[3 + c];
+        }
       }
     }
     const int bd = isl ? T->body[l] : -1;

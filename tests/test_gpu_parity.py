@@ -345,29 +345,41 @@ def test_status_reports_nonfinite_input():
     s.destroy()
 
 
-def test_step_host_matches_device_path():
+@pytest.mark.parametrize("pinned,plan", [(False, "per_type"), (True, "per_type"), (True, "persistent"),
+                                         (True, "graph")])
+def test_step_host_matches_device_path(pinned, plan):
+    """sim_step_host from pageable host buffers (copied) and from pinned ones (read and written by
+    the per-type step kernels themselves; copied for persistent and graph handles): the same outputs
+    as the device path of the same plan, bit for bit, and the views (root, DOF state, actuation) as
+    after sim_step."""
     import torch
     from paper_2108_10470_gb300 import sim
 
+    flags = {"per_type": 0, "persistent": sim.SIM_FLAG_PERSISTENT, "graph": sim.SIM_FLAG_GRAPH}[plan]
     w = W.ant_workload(32)
     root, dof, acts = W.seeded_inputs(w, 5, 2)
-    outs = []
+    host = (lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()) if pinned else np.ascontiguousarray
+    outs, views = [], []
     for use_host in (False, True):
-        s = sim.Sim(w)
+        s = sim.Sim(w, flags=flags)
         s.root_state.copy_(torch.from_numpy(root))
         s.dof_state.copy_(torch.from_numpy(dof))
-        r = np.zeros_like(root)
-        d = np.zeros_like(dof)
+        r = host(np.zeros_like(root))
+        d = host(np.zeros_like(dof))
         for k in range(2):
             if use_host:
-                s.step_host(np.ascontiguousarray(acts[k]), r, d)
+                s.step_host(host(acts[k]), r, d)
             else:
                 s.dof_actuation.copy_(torch.from_numpy(acts[k]))
                 s.step()
                 r, d = s.root_state.cpu().numpy(), s.dof_state.cpu().numpy()
         outs.append((r.copy(), d.copy()))
+        views.append([getattr(s, v).cpu().numpy() for v in ("root_state", "dof_state", "dof_actuation")])
         s.destroy()
     assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    for a, b in zip(*views):
+        assert np.array_equal(a, b)
+    assert np.array_equal(views[1][2], acts[1])
 
 
 def test_fp32_probe_reports_plausible_peak():
