@@ -18,8 +18,9 @@ __device__ __noinline__ void persistent_tile(const StepArgs& A, const TypeArgs& 
   const int gw = (threadIdx.x & 31) / G;  // group within the warp
   const int grp = tile * (32 / G) + gw;
   float* sm = wsm + gw * TA.lay.total;
-  float* rb = GROWS ? TA.scratch + (size_t)(gwarp * (32 / G) + gw) * TA.lay.scratch_words : sm;
-  step_group<G, GROWS, BALL, false>(A, TA, grp, sm, rb);  // taped and direct-buffer steps: per-type kernels
+  float* slot = TA.lay.scratch_words ? TA.scratch + (size_t)(gwarp * (32 / G) + gw) * TA.lay.scratch_words : nullptr;
+  float* rb = GROWS ? slot : sm;
+  step_group<G, GROWS, BALL, false>(A, TA, grp, sm, rb, GROWS ? nullptr : slot);  // taped and direct-buffer steps: per-type kernels
 }
 
 template <bool BALL>

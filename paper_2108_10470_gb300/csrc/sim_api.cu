@@ -394,9 +394,17 @@ constexpr int kSharedArenaLimit = 24 * 1024;
 // Per-CTA dynamic shared memory cap used by the planner.
 constexpr size_t kMaxSmemPerCta = 220 * 1024;
 
+// Residency of the step kernels: 128 registers x 128 threads (__launch_bounds__(128, 4)) leave 16
+// warps per SM; the SM's shared memory and the part of it reserved per CTA.
+constexpr int kStepWarpsPerSm = 16;
+constexpr int kSmemPerSm = 228 * 1024;
+constexpr int kSmemReservedPerCta = 1024;
+
 // Layout of one env's arena for G lanes per env; rows_global puts the contact and row blocks in a
-// per-env slot of global scratch instead of shared memory.
-SmemLayout make_layout(const EnvTypeTable& T, int G, bool rows_global) {
+// per-env slot of global scratch instead of shared memory. envs_per_cta > 0 lets a shared-rows
+// layout at G = 32 size its Y region below the type's row capacity (a global Y slot per group
+// then serves the substeps with more rows); 0 keeps the whole capacity in shared memory.
+SmemLayout make_layout(const EnvTypeTable& T, int G, bool rows_global, int envs_per_cta) {
   SmemLayout Ly{};
   const int n = std::max(T.n_gen, 1);
   const int L = T.n_links;
@@ -409,7 +417,22 @@ SmemLayout make_layout(const EnvTypeTable& T, int G, bool rows_global) {
   const int conw = T.n_pairs > 0 ? kConWords : 9;
   int o = 0;
   if (!rows_global) {
-    const int phase = std::max(L * kLinkWords, n * Ly.RS);
+    const int full = n * Ly.RS;
+    int phase = std::max(L * kLinkWords, full);
+    if (envs_per_cta > 0 && G == 32) {
+      // The Y region (Y of the substep's R rows at stride R | 1, then the Delassus block when it
+      // fits) is sized to what the shared memory of the register-limited residency leaves per env,
+      // not to the row capacity, which most substeps use a fraction of (the Humanoid: 96 rows of
+      // capacity, fewer than 42 in every substep of a 128-env, 140-step oracle rollout, 17.5 on
+      // average). Its arena: 18.1 -> 14.0 KB per env, four 4-env CTAs per SM instead of three; Y
+      // fits for up to 61 rows, W too for up to 29. It holds at least the link slots and Y of 32 rows.
+      const int rest = al4(al4(6 * n + n * Ly.MS + 5 * n + conw * Ly.ccap) + 6 * Ly.rcap + 3 * L);
+      const int ctas = std::max(1, kStepWarpsPerSm / (envs_per_cta * G / 32));
+      const int budget = (((kSmemPerSm / ctas - kSmemReservedPerCta) / 4) / envs_per_cta - rest) & ~3;
+      const int lo = al4(std::max(L * kLinkWords, n * 33));
+      if (lo < phase && budget < phase) phase = std::max(lo, budget);
+    }
+    if (phase < full) Ly.scratch_words = al4(full);  // the global Y slot of the substeps past it
     Ly.link = o;
     Ly.Y = o;
     Ly.ywords = phase;
@@ -455,7 +478,7 @@ SmemLayout make_layout(const EnvTypeTable& T, int G, bool rows_global) {
 // kSharedArenaLimit, and always for env types with shape pairs or ball joints (the pair phase and
 // the 3-DOF joint blocks are compiled into the global-rows variant only).
 bool default_rows_global(const EnvTypeTable& T, int G) {
-  return T.n_pairs > 0 || T.has_ball || make_layout(T, G, false).total * 4 > kSharedArenaLimit;
+  return T.n_pairs > 0 || T.has_ball || make_layout(T, G, false, 0).total * 4 > kSharedArenaLimit;
 }
 
 cudaError_t launch_type(const TypePlan& tp, const StepArgs& a, const TypeArgs& ta, cudaStream_t st) {
@@ -488,14 +511,14 @@ int configure_type(TypePlan& tp, int G, bool rows_global, int warps, bool per_ty
     g_last_error = "type config: env types with shape pairs or ball joints keep their rows in global memory";
     return SIM_ERR_INVALID_ARG;
   }
-  const SmemLayout Ly = make_layout(tp.tab, G, rows_global);
   const int gpb = warps * 32 / G;
+  const SmemLayout Ly = make_layout(tp.tab, G, rows_global, gpb);
   const size_t smem = (size_t)gpb * Ly.total * 4;
   if (smem > kMaxSmemPerCta) {
     g_last_error = "type config: the CTA's shared arena exceeds 220 KB";
     return SIM_ERR_CAPACITY;
   }
-  if (Ly.grows && per_type_scratch) {
+  if (Ly.scratch_words && per_type_scratch) {  // global rows, or a shared-rows layout's Y slots
     const size_t slots = (tp.envs.size() + gpb - 1) / gpb * gpb;
     const int rc = grow_buffer(&tp.scratch, &tp.scratch_floats, slots * (size_t)Ly.scratch_words,
                                "cudaMalloc (global rows scratch)");
@@ -542,7 +565,7 @@ int plan_persistent(sim_s* h) {
   h->p_smem = smem;
   h->p_warp_words = warp_words;
   for (TypePlan& tp : h->types)
-    if (tp.lay.grows) {
+    if (tp.lay.scratch_words) {
       const size_t need = (size_t)h->p_warps * (32 / tp.G) * tp.lay.scratch_words;
       const int rc = grow_buffer(&tp.pscratch, &tp.pscratch_floats, need, "cudaMalloc (persistent rows scratch)");
       if (rc != SIM_OK) return rc;
@@ -608,7 +631,7 @@ int launch_step(sim_s* h, cudaStream_t st, float dt, int substeps) {
       const int k = h->p_order[s];
       const TypePlan& tp = h->types[k];
       fill_type(h, (size_t)k, P.types[k]);
-      P.types[k].scratch = tp.lay.grows ? tp.pscratch : nullptr;
+      P.types[k].scratch = tp.lay.scratch_words ? tp.pscratch : nullptr;
       P.variant[k] = variant_of(tp);
       P.order[s] = k;
       const int per = 32 / tp.G;  // envs per warp tile
@@ -1067,7 +1090,20 @@ int sim_step_static_scratch(sim_handle h, const sim_state_buffers* io, float dt,
     TypeArgs ta;
     fill_type(h, t, ta);
     ta.scratch = tp.lay.grows ? scratch : nullptr;
-    const cudaError_t e = launch_type(tp, a, ta, h->stream);
+    size_t smem = tp.smem_bytes;
+    if (!tp.lay.grows && tp.lay.scratch_words) {
+      // a shared-rows type whose Y region is sized below its row capacity: step it with the whole
+      // capacity in shared memory (no global Y slots), so the array serves only global-rows types
+      ta.lay = make_layout(tp.tab, tp.G, false, 0);
+      smem = (size_t)tp.groups_per_block * ta.lay.total * 4;
+      if (smem > kMaxSmemPerCta) {
+        g_last_error = "sim_step_static_scratch: an env type's shared arena without global Y slots exceeds 220 KB "
+                       "(use fewer warps per CTA for it)";
+        return SIM_ERR_CAPACITY;
+      }
+    }
+    const cudaError_t e = launch_step_kernel(tp.G, tp.lay.grows != 0, tp.tab.has_ball != 0, a, ta,
+                                             tp.groups_per_block, smem, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "step_kernel launch (static scratch)");
   }
   return SIM_OK;
@@ -1227,7 +1263,7 @@ int launch_taped(sim_s* h, StepArgs a, float* tape, cudaStream_t st) {
   tape_floats(h, a.substeps, &offs);
   for (size_t t = 0; t < h->types.size(); ++t) {
     TypePlan& tp = h->types[t];
-    if (tp.lay.grows && !tp.scratch) {  // a persistent handle steps without per-type scratch
+    if (tp.lay.scratch_words) {  // a persistent handle steps without per-type scratch (no-op when it fits)
       const size_t gpb = (size_t)tp.groups_per_block;
       const int rc = grow_buffer(&tp.scratch, &tp.scratch_floats,
                                  (tp.envs.size() + gpb - 1) / gpb * gpb * (size_t)tp.lay.scratch_words,

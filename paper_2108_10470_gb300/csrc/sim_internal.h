@@ -81,7 +81,8 @@ struct EnvTypeTable {
 // the link slots get a shared-memory region of their own.
 struct SmemLayout {
   int grows;  // 1: contact and row blocks in global scratch
-  int scratch_words;  // words per env slot of global scratch (0 if grows == 0)
+  int scratch_words;  // words per group slot of global scratch: the contact and row blocks (grows), or
+                      // Y for the substeps whose rows exceed ywords (a compact shared-rows layout); 0: none
   int link;   // kLinkWords per link: IA 21 | pA 6 | Ic 10
   int Y;      // n_gen x RS: Y = L^-1 J^T, one column per constraint row
   int RS;     // row stride of Y (odd)
@@ -178,7 +179,7 @@ struct TypeArgs {
   const int* env_ids;        // env ids of the type (nullptr: env_first + index)
   int env_first;
   int n_launch_envs;
-  float* scratch;            // global rows: one slot per group (see the launch wrappers)
+  float* scratch;            // lay.scratch_words per group (see the launch wrappers), or null
   SmemLayout lay;
   float* tape;               // taped instantiation only: the type's tape, env-major then substep
   TapeLayout tl;

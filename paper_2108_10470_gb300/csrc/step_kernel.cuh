@@ -632,10 +632,12 @@ __device__ __noinline__ float2 pgs_delassus_form(const float* s_Y, const int YS,
 // One substep loop of one environment by one group of G lanes. grp indexes the launch's env list
 // (grp >= n_launch_envs: a dead group, which shadows the last env and never stores); sm is the
 // group's shared arena and rb the base of its contact and row blocks (sm itself, or a private
-// slot of global scratch in the GROWS variant).
+// slot of global scratch in the GROWS variant). yg (shared-rows layouts whose Y region is sized
+// below the type's row capacity, else null) is the group's global slot for Y in the substeps whose
+// rows do not fit that region.
 template <int G, bool GROWS, bool BALL = false, bool PER_TYPE = true>
 __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA, const int grp, float* sm,
-                                           float* rb) {
+                                           float* rb, float* yg) {
   const EnvTypeTable* __restrict__ T = TA.type;
   const int lane = threadIdx.x & (G - 1);
   const bool live = grp < TA.n_launch_envs;
@@ -654,7 +656,7 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
   const int maxdepth = T->max_depth;
   const int MS = Ly.MS, CC = Ly.ccap;
   float* s_link = sm + Ly.link;  // phase 1: per-link hand-off slots of the inward sweep
-  float* s_Y = rb + Ly.Y;        // phase 2 (aliases phase 1 in shared memory): Y = L^-1 J^T, n x (R | 1)
+  float* const s_Yr = rb + Ly.Y;  // phase 2 (aliases phase 1 in shared memory): Y = L^-1 J^T, n x (R | 1)
   float* s_SD = sm + Ly.SD;      // motion subspace column of every generalized DOF
   float* s_M = sm + Ly.M;        // Cholesky factor L (lower), n x MS
   float* s_qdd = sm + Ly.vec;
@@ -1348,6 +1350,10 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
     // Y is n x YS with the odd stride YS = R | 1 of this substep's rows, so that the rest of the
     // region can hold the Delassus block of the solve below
     const int YS = R | 1;
+    // A shared-rows layout at G = 32 may size the Y region for the rows a substep usually has (the
+    // Delassus form's 32 rows and more; the Humanoid's substeps rarely pass 40 of its 114) rather
+    // than the type's row capacity; a substep with more rows puts Y in the group's global slot.
+    float* const s_Y = (!GROWS && G == 32 && n * YS > Ly.ywords) ? yg : s_Yr;
     for (int r = lane; r < R; r += G) {
       const float4 hc = s_rowc[r];
       const int a = s_rowa[r];
@@ -1695,7 +1701,7 @@ __device__ __forceinline__ void step_group(const StepArgs& A, const TypeArgs& TA
 
 // One launch per env type: blocks of 128 / G groups, one env per group. In the GROWS variant the
 // group's scratch slot is its index in the launch (the dead groups of the last block own the
-// slots past the launched envs).
+// slots past the launched envs); so is a shared-rows layout's Y overflow slot.
 template <int G, bool GROWS, bool BALL = false>
 __global__ void __launch_bounds__(128, 4) step_kernel(const __grid_constant__ StepArgs A,
                                                      const __grid_constant__ TypeArgs TA) {
@@ -1704,6 +1710,7 @@ __global__ void __launch_bounds__(128, 4) step_kernel(const __grid_constant__ St
   const int grp = blockIdx.x * (blockDim.x / G) + grp_blk;
   float* sm = smem + grp_blk * TA.lay.total;
   float* rb = GROWS ? TA.scratch + (size_t)grp * TA.lay.scratch_words : sm;
+  float* yg = (!GROWS && TA.lay.scratch_words) ? TA.scratch + (size_t)grp * TA.lay.scratch_words : nullptr;
   // The type's model table (9.5 KB) is read by every phase, each phase first touching lines of its
   // own; after a cold L2 each first touch is a DRAM round trip on some env's dependent chain. One
   // warp of the first CTA requests all of its lines into L2 at the start (measured with L2 flushed
@@ -1714,7 +1721,7 @@ __global__ void __launch_bounds__(128, 4) step_kernel(const __grid_constant__ St
     for (int o = threadIdx.x * 128; o < (int)sizeof(EnvTypeTable); o += 32 * 128)
       asm volatile("prefetch.global.L2 [%0];" ::"l"(__cvta_generic_to_global(tb + o)));
   }
-  step_group<G, GROWS, BALL>(A, TA, grp, sm, rb);
+  step_group<G, GROWS, BALL>(A, TA, grp, sm, rb, yg);
 }
 
 }  // namespace artsim

@@ -1,11 +1,14 @@
 """GPU parity at the kernel's capacity limits and across lane widths: random articulated trees (mixed
 revolute / prismatic joints, random frames, axes and inertias) with 32 links and 31 joint DOFs on
-a fixed base, 27 links and 32 generalized DOFs on a floating base, and a batch mixing tree sizes
-that map to 8, 16 and 32 lanes per env."""
+a fixed base, 27 links and 32 generalized DOFs on a floating base, a batch mixing tree sizes
+that map to 8, 16 and 32 lanes per env, and substeps with more constraint rows than the shared Y
+region of a 32-lane env holds (Y in the group's global slot: bit for bit the same steps as with the
+whole row capacity in shared memory)."""
 import numpy as np
 import pytest
 
 from paper_2108_10470_gb300 import workloads as W
+from scenes import capsule_chain
 from test_gpu_parity import check_rollout
 
 pytestmark = pytest.mark.gpu
@@ -41,3 +44,92 @@ def test_mixed_lane_widths():
     eam = np.array([i % 3 for i in range(60)], np.int32)
     w = W.Workload("trees", models, eam, 1, 60, W.Params())
     check_rollout(w, 4, 1e-3, 1e-3, min_same=1.0)
+
+
+def staggered(w):
+    """Lift env e's chain by 4 mm x (e mod 10): one launch then steps envs without contacts, with a
+    few and with up to 34 (102 rows and more)."""
+    def start(root, dof):
+        root[:, 2] += 0.004 * (np.arange(w.n_envs) % 10)
+    return start
+
+
+def shared_rows(s):
+    s.set_type_config(0, 32, 0, 4)
+    assert s.type_config(0)["rows_global"] == 0
+
+
+def test_persistent_global_y_slots_match_per_type_launch():
+    """The persistent launch gives every resident warp its own global Y slot (the per-type launch
+    one per env): 4 steps of the capsule chain, whose substeps put Y past 33 rows in those slots,
+    agree with the per-type launch's to rounding (1e-4 relative, 1e-5 absolute) and in every
+    integer output."""
+    import torch
+    from paper_2108_10470_gb300 import sim
+
+    w = W.homogeneous("capsule_chain", capsule_chain(), 37)
+    root, dof, acts = W.seeded_inputs(w, 2, 4)
+    staggered(w)(root, dof)
+    a = sim.Sim(w, flags=sim.SIM_FLAG_SIGNATURE)
+    b = sim.Sim(w, flags=sim.SIM_FLAG_SIGNATURE | sim.SIM_FLAG_PERSISTENT)
+    most = 0
+    for s in (a, b):
+        shared_rows(s)
+        s.root_state.copy_(torch.from_numpy(root))
+        s.dof_state.copy_(torch.from_numpy(dof))
+    for k in range(4):
+        for s in (a, b):
+            s.dof_actuation.copy_(torch.from_numpy(acts[k]))
+            s.step()
+        for name in a.STATE_NAMES:
+            x, y = getattr(a, name), getattr(b, name)
+            if x.dtype == torch.float32:
+                assert torch.allclose(x, y, rtol=1e-4, atol=1e-5), (name, k, (x - y).abs().max().item())
+            else:
+                assert np.array_equal(x.cpu().numpy(), y.cpu().numpy()), (name, k)
+        most = max(most, int(a.contact_count.max()))
+    assert most >= 12 and not a.status.any() and not b.status.any()
+    a.destroy()
+    b.destroy()
+
+
+def test_global_y_slot_is_bitwise_the_shared_region():
+    """Where Y lives does not change the arithmetic: with the row form of the solve forced (so
+    that the Delassus form's fit, which depends on the region's size, plays no part), 16 steps of
+    the capsule chain with Y past 33 rows in global slots equal, bit for bit, the same steps with
+    the whole row capacity in shared memory (sim_step_static_scratch lays such a type out that
+    way)."""
+    import torch
+    from paper_2108_10470_gb300 import sim
+
+    w = W.homogeneous("capsule_chain", capsule_chain(), 37)
+    root, dof, acts = W.seeded_inputs(w, 1, 16)
+    staggered(w)(root, dof)
+    flags = sim.SIM_FLAG_SIGNATURE | sim.SIM_FLAG_ROW_SOLVER
+    a, b = sim.Sim(w, flags=flags), sim.Sim(w, flags=flags)
+    shared_rows(a)
+    shared_rows(b)
+    a.root_state.copy_(torch.from_numpy(root))
+    a.dof_state.copy_(torch.from_numpy(dof))
+    def raw(t):  # the bits of a float32 / int32 / uint32 tensor
+        return t.cpu().numpy().view(np.uint32)
+
+    bufs = {}
+    for name in b.STATE_NAMES:
+        v = getattr(b, name)
+        dtype = v.dtype if v.dtype in (torch.float32, torch.int32) else torch.int32  # u32 as raw bits
+        bufs[name] = torch.zeros(tuple(v.shape), dtype=dtype, device=v.device)
+    bufs["root_state"].copy_(torch.from_numpy(root))
+    bufs["dof_state"].copy_(torch.from_numpy(dof))
+    most = 0
+    for k in range(16):
+        a.dof_actuation.copy_(torch.from_numpy(acts[k]))
+        a.step()
+        bufs["dof_actuation"].copy_(torch.from_numpy(acts[k]))
+        b.step_static_scratch(bufs)
+        for name in b.STATE_NAMES:
+            assert np.array_equal(raw(getattr(a, name)), raw(bufs[name])), f"{name} after step {k + 1}"
+        most = max(most, int(a.contact_count.max()))
+    assert most >= 12 and not a.status.any()
+    a.destroy()
+    b.destroy()
