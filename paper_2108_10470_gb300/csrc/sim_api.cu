@@ -386,9 +386,9 @@ int build_type(const sim_model_desc* models, const std::vector<int>& actor_model
   return SIM_OK;
 }
 
-// Largest per-env shared arena; bigger worst cases, and every env type with shape pairs, keep
-// their contact / row blocks in global scratch (the Humanoid's 18 KB stays in shared memory, the
-// hand-with-cube's ~60 KB does not).
+// Largest per-env shared arena sized to the row capacity; bigger worst cases, and every env type
+// with shape pairs, keep their contact / row blocks in global scratch (the Humanoid's 18 KB stays
+// in shared memory, the hand-with-cube's ~60 KB does not).
 constexpr int kSharedArenaLimit = 24 * 1024;
 
 // Per-CTA dynamic shared memory cap used by the planner.
