@@ -312,8 +312,7 @@ def run_ours(args, rank, world, local_rank):
     act_dev = torch.from_numpy(acts).to(dev)  # every step's actions resident in HBM
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     for k in range(Wm):
-        s.dof_actuation.copy_(act_dev[k])
-        s.step()
+        actuated_step(s, act_dev[k])
         if args.autotune and k == Wm // 2:  # tune on a mid-warm-up state; the state is left unchanged
             s.autotune(reps=5)
     torch.cuda.synchronize()
@@ -322,6 +321,7 @@ def run_ours(args, rank, world, local_rank):
             "types": [{k: c[k] for k in ("lanes_per_env", "rows_global", "warps_per_cta", "n_envs")}
                       for c in (s.type_config(t) for t in range(s.n_types))]}
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    in_place = reads_actions_in_place(s)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -330,10 +330,14 @@ def run_ours(args, rank, world, local_rank):
             flush.zero_()  # L2 flush, outside the step's events
             e0, e1, e2 = ev[k]
             e0.record(stream)
-            s.dof_actuation.copy_(act_dev[Wm + k])
+            if not in_place:  # graph and persistent handles: the actions copied into the view
+                s.dof_actuation.copy_(act_dev[Wm + k])
             e1.record(stream)
             torch.cuda.nvtx.range_push("timed_step")  # lets ncu --nvtx-include pick timed launches
-            s.step()
+            if in_place:  # the step kernels read the step's actions from act_dev themselves
+                s.step_actuated(act_dev[Wm + k])
+            else:
+                s.step()
             torch.cuda.nvtx.range_pop()
             e2.record(stream)
         torch.cuda.synchronize()
@@ -413,21 +417,39 @@ def probe_peak_flops() -> float:
     return statistics.median(sim.probe_fp32_peak(20000) for _ in range(3))
 
 
+def reads_actions_in_place(s) -> bool:
+    """Whether sim_step_actuated serves the handle by its step kernel reading a step's actions from
+    the caller's tensor (one env type, per-type launch, no captured graph); other handles get the
+    actions copied into the actuation view first."""
+    from paper_2108_10470_gb300 import sim
+    return s.n_types == 1 and not (s.flags & (sim.SIM_FLAG_GRAPH | sim.SIM_FLAG_PERSISTENT))
+
+
+def actuated_step(s, act):
+    """One control step with this step's actions (a device tensor): sim_step_actuated where the
+    step kernel reads the actions in place (paper: applying the actuation force tensor, then
+    simulating); elsewhere the copy into the actuation view and sim_step (what sim_step_actuated
+    enqueues for those handles), so that the events can time the step kernels alone."""
+    if reads_actions_in_place(s):
+        s.step_actuated(act)
+    else:
+        s.dof_actuation.copy_(act)
+        s.step()
+
+
 def timed_steps(s, act_dev, warm, steps, flush):
-    """Mean device time of `steps` sim_steps (actions copied in, L2 flushed before each, outside
-    the step's events) after `warm` untimed steps."""
+    """Mean device time of `steps` control steps (each: the step's actions applied and sim_step;
+    L2 flushed before each, outside the step's events) after `warm` untimed steps."""
     import torch
     for k in range(warm):
-        s.dof_actuation.copy_(act_dev[k % act_dev.shape[0]])
-        s.step()
+        actuated_step(s, act_dev[k % act_dev.shape[0]])
     torch.cuda.synchronize()
     ev = []
     for k in range(steps):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        s.dof_actuation.copy_(act_dev[(warm + k) % act_dev.shape[0]])
-        s.step()
+        actuated_step(s, act_dev[(warm + k) % act_dev.shape[0]])
         e1.record()
         ev.append((e0, e1))
     torch.cuda.synchronize()
@@ -474,8 +496,7 @@ def config_line(w, dev, flush, warm, steps, flags=0, autotune=False, peak_tflops
     act_dev = torch.from_numpy(acts).to(dev)
     if autotune:
         for k in range(warm // 2):
-            s.dof_actuation.copy_(act_dev[k])
-            s.step()
+            actuated_step(s, act_dev[k])
         s.autotune(reps=5)
         s.root_state.copy_(torch.from_numpy(root))
         s.dof_state.copy_(torch.from_numpy(dof))
@@ -490,7 +511,8 @@ def config_line(w, dev, flush, warm, steps, flags=0, autotune=False, peak_tflops
         out["roofline"] = {"bound": "alu", "flops_per_env_step": f, "flops_window": window,
                            "achieved": f * w.n_envs / (ms / 1e3) / 1e12, "peak": peak_tflops, "unit": "TFLOP/s",
                            "frac": f * w.n_envs / (ms / 1e3) / 1e12 / peak_tflops,
-                           "note": "step time includes the action copy (one launch per env type)"}
+                           "note": "step time includes applying the step's actions (read in place by the "
+                                   "step kernel of a one-type handle, else copied into the actuation view)"}
     return out
 
 

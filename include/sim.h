@@ -199,6 +199,19 @@ int sim_create(const sim_model_desc* models, int32_t n_models, const int32_t* en
  * INVALID_ARG (dt <= 0 or non-finite, substeps < 1), CUDA (launch failure). */
 int sim_step(sim_handle h, float dt, int32_t substeps);
 
+/* The step with this step's DOF actuation forces given by the caller (paper: applying an actuation
+ * force tensor, set_dof_actuation_force_tensor, then simulate): `actuation` holds N_D floats in the
+ * DOF_ACTUATION layout, in memory the device can read (device memory of the handle's device,
+ * managed memory, pinned host memory) or any other host memory. On a handle of one env type the
+ * step kernel loads the forces straight from a buffer the device can address and stores them into
+ * DOF_ACTUATION, so no copy is launched; other buffers, and every buffer of a handle with several
+ * env types or with SIM_FLAG_GRAPH or SIM_FLAG_PERSISTENT, are copied into DOF_ACTUATION on the
+ * handle's stream first. Either way the views end exactly as after
+ * writing DOF_ACTUATION and calling sim_step. The buffer is read asynchronously on the handle's
+ * stream and must not change until the step has run; the caller keeps its ownership. Errors as
+ * sim_step; INVALID_ARG for a NULL buffer when the handle has DOFs. */
+int sim_step_actuated(sim_handle h, const float* actuation, float dt, int32_t substeps);
+
 /* End-to-end step from host memory: host_actuation (N_D floats) into DOF_ACTUATION, sim_step,
  * ROOT_STATE (N_A*13 floats) and DOF_STATE (N_D*2 floats) into the host buffers (either output may
  * be NULL), then a stream synchronisation. Pinned buffers (CUDA-allocated or registered host
@@ -285,7 +298,9 @@ int sim_set_type_config(sim_handle h, int32_t type, int32_t lanes_per_env, int32
  * SIM_FLAG_PERSISTENT each type is tuned on its own launch over every valid (lanes, rows, warps);
  * with it, (lanes, rows) of each type in turn are tried on the whole persistent step (two passes
  * of coordinate descent). Each candidate is timed with CUDA events over `reps` steps (1..1000)
- * after one warm-up step, each step starting from a snapshot of every state tensor; the snapshot
+ * after one warm-up step, each step starting from a snapshot of every state tensor, and replaces
+ * the knobs held so far (first the handle's current ones) only when its median step is at least
+ * 3 % faster; the snapshot
  * is restored at the end, so the visible state is unchanged. *ms_per_step receives the chosen
  * plan's median step time. Synchronises the stream; allocates the snapshot for the call's
  * duration. Errors: HANDLE, INVALID_ARG, CUDA. */

@@ -31,7 +31,7 @@ SIM_FLAG_TANGENT_VJP = 128
  SIM_VIEW_CONTACT_PAIRS, SIM_VIEW_CONTACT_COUNT, SIM_VIEW_SIGNATURE, SIM_VIEW_STATUS,
  SIM_VIEW_IMPULSE_CACHE, SIM_VIEW_DOF_POSITION_TARGET, SIM_VIEW_DOF_VELOCITY_TARGET, SIM_VIEW_DOF_FORCE,
  SIM_VIEW_RIGID_BODY_STATE, SIM_VIEW_RIGID_BODY_FORCE) = range(14)
-EXPORTED = ("sim_create", "sim_step", "sim_step_host", "sim_get_view", "sim_set_root_state_indexed",
+EXPORTED = ("sim_create", "sim_step", "sim_step_actuated", "sim_step_host", "sim_get_view", "sim_set_root_state_indexed",
             "sim_set_dof_state_indexed", "sim_set_stream", "sim_sync_status", "sim_get_sizes", "sim_destroy",
             "sim_error_string", "sim_last_error_message", "sim_probe_fp32_peak", "sim_step_static_scratch",
             "sim_get_type_config", "sim_set_type_config", "sim_autotune", "sim_step_vjp", "sim_step_jvp",
@@ -125,6 +125,7 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     L.sim_create.argtypes = [ctypes.POINTER(sim_model_desc), ctypes.c_int32, I32, ctypes.c_int32, ctypes.c_int32,
                              ctypes.POINTER(sim_params), ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
     L.sim_step.argtypes = [ctypes.c_void_p, ctypes.c_float, ctypes.c_int32]
+    L.sim_step_actuated.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float, ctypes.c_int32]
     L.sim_step_host.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float,
                                 ctypes.c_int32]
     L.sim_get_view.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(sim_view)]
@@ -258,6 +259,7 @@ class Sim:
 
         L = load()
         self.w = w
+        self.flags = int(flags)
         self._torch = torch
         self._stream = stream if stream is not None else torch.cuda.current_stream()
         arr, keep = model_structs(w.models)
@@ -287,6 +289,23 @@ class Sim:
     def step(self, dt: Optional[float] = None, substeps: Optional[int] = None):
         check(load().sim_step(self.h, float(self.w.dt if dt is None else dt),
                               int(self.w.substeps if substeps is None else substeps)), "sim_step")
+
+    def step_actuated(self, act, dt: Optional[float] = None, substeps: Optional[int] = None):
+        """The step with this step's DOF actuation forces taken from `act` (paper: applying the
+        actuation force tensor, then simulating): a float32, contiguous torch tensor of at least N_D
+        elements, on the handle's device (or in pinned host memory), which the step kernels read
+        in place; the actuation view ends holding the forces, as after writing it and calling step.
+        Other tensors are refused with ValueError before anything is launched."""
+        torch = self._torch
+        need = self.dof_actuation.numel()
+        if isinstance(act, torch.Tensor) and act.device.type == "cpu" and act.is_pinned():
+            if act.dtype != torch.float32 or not act.is_contiguous() or act.numel() < need:
+                raise ValueError("act: a pinned host tensor must be float32, contiguous, with at least N_D elements")
+            ptr = act.data_ptr()
+        else:
+            ptr = self._dev_ptr(act, "act", (torch.float32,), need)
+        check(load().sim_step_actuated(self.h, ptr, float(self.w.dt if dt is None else dt),
+                                       int(self.w.substeps if substeps is None else substeps)), "sim_step_actuated")
 
     def step_host(self, act: np.ndarray, root_out: Optional[np.ndarray], dof_out: Optional[np.ndarray],
                   dt: Optional[float] = None, substeps: Optional[int] = None):

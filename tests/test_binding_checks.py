@@ -85,3 +85,23 @@ def test_indexed_setters_check_index_dtype_and_source_size():
         s.set_root_state_indexed(torch.zeros((1, 13)), torch.tensor([0, 1], dtype=torch.int32))
     with pytest.raises(ValueError):
         s.set_dof_state_indexed(torch.zeros((2, 15)), torch.tensor([0, 1], dtype=torch.int32))
+
+
+@pytest.mark.parametrize("bad", ["dtype", "size", "contiguity", "device", "type"])
+def test_step_actuated_buffer_is_checked(bad):
+    """The actuation tensor of step_actuated: float32, contiguous, on the handle's device (or pinned
+    host memory), with at least N_D elements; anything else raises before the library is called."""
+    s = fake_sim()
+    act = torch.zeros(s.dof_actuation.shape)
+    if bad == "dtype":
+        act = act.double()
+    elif bad == "size":
+        act = act[:-1]
+    elif bad == "contiguity":
+        act = torch.zeros((2, act.shape[0]))[:, 0]
+    elif bad == "device":
+        act = torch.zeros(act.shape, device="meta")
+    else:
+        act = np.zeros(act.shape, np.float32)
+    with pytest.raises(ValueError):
+        s.step_actuated(act)

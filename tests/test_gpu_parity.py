@@ -382,6 +382,43 @@ def test_step_host_matches_device_path(pinned, plan):
     assert np.array_equal(views[1][2], acts[1])
 
 
+@pytest.mark.parametrize("source,plan", [("device", "per_type"), ("pinned", "per_type"), ("pageable", "per_type"),
+                                         ("device", "mixed"), ("device", "persistent"), ("device", "graph")])
+def test_step_actuated_equals_writing_the_view(source, plan):
+    """sim_step_actuated with this step's forces in a caller buffer (read in place by the step
+    kernel of a one-type handle from device or pinned host memory; copied into the view from
+    pageable memory and for mixed, persistent and graph handles): every view bit for bit as after
+    writing DOF_ACTUATION and calling sim_step, over three steps, the actuation view holding the
+    last step's forces."""
+    import torch
+    from paper_2108_10470_gb300 import sim
+
+    flags = sim.SIM_FLAG_SIGNATURE | {"per_type": 0, "mixed": 0, "persistent": sim.SIM_FLAG_PERSISTENT,
+                                      "graph": sim.SIM_FLAG_GRAPH}[plan]
+    w = W.mixed_workload(48) if plan == "mixed" else W.ant_workload(40)
+    root, dof, acts = W.seeded_inputs(w, 7, 3)
+    a, b = sim.Sim(w, flags=flags), sim.Sim(w, flags=flags)
+    for s in (a, b):
+        s.root_state.copy_(torch.from_numpy(root))
+        s.dof_state.copy_(torch.from_numpy(dof))
+    for k in range(3):
+        a.dof_actuation.copy_(torch.from_numpy(acts[k]))
+        a.step()
+        f = torch.from_numpy(np.ascontiguousarray(acts[k]))
+        f = {"device": lambda t: t.cuda(), "pinned": lambda t: t.pin_memory(), "pageable": lambda t: t}[source](f)
+        if source == "pageable":  # the binding passes only device or pinned tensors: call the C ABI directly
+            sim.check(sim.load().sim_step_actuated(b.h, f.data_ptr(), float(w.dt), int(w.substeps)), "step")
+        else:
+            b.step_actuated(f)
+        torch.cuda.synchronize()
+        for name in b.STATE_NAMES:
+            x, y = getattr(a, name).cpu().numpy(), getattr(b, name).cpu().numpy()
+            assert np.array_equal(x.view(np.uint32), y.view(np.uint32)), (name, k)
+    assert np.array_equal(b.dof_actuation.cpu().numpy(), acts[2])
+    a.destroy()
+    b.destroy()
+
+
 def test_fp32_probe_reports_plausible_peak():
     from paper_2108_10470_gb300 import sim
     f = sim.probe_fp32_peak(2000)
