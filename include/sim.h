@@ -256,7 +256,10 @@ typedef struct {
  * Limit: each such env type needs its env count, rounded up to a whole CTA (128 / G envs, G the
  * lanes per env), times its per-env scratch within 64 MiB (a hand-with-cube env uses about 62 KB,
  * so about 1050 of them fit); a larger type fails with CAPACITY and a message giving the sizes,
- * before anything is launched. Env types that fit in shared memory have no limit.
+ * before anything is launched. Env types that fit in shared memory have no limit: they step with
+ * their whole row capacity in shared memory (sim_step may hold part of it in global slots of the
+ * handle), which fails with CAPACITY only for a type whose knobs were set so that its CTA's arena
+ * exceeds 220 KB.
  * Address: each call outside a stream capture looks up the array's device address on the
  * handle's device (with that device made current, the caller's device restored), so a device
  * reset between calls is followed; a call during a capture reuses the address of the last call on
