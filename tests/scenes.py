@@ -21,7 +21,7 @@ def two_actor_env(cap_pos, cap_quat, box_pos, params=None):
 
 
 
-def capsule_chain(n_links=17, radius=0.03, half_len=0.08, pitch=0.2, density=1000.0, gear=1.0, spheres=False):
+def capsule_chain(n_links=17, radius=0.03, half_len=0.08, pitch=0.2, density=1000.0, gear=1.0):
     """A floating chain of n_links capsules along x joined end to end by hinges about their y axis
     (limits +-45 deg), lying on the ground: 17 links (32 lanes per env), 22 generalized DOFs, two
     contacts per capsule lying flat, so a substep can have more constraint rows (3 per contact,
@@ -30,13 +30,12 @@ def capsule_chain(n_links=17, radius=0.03, half_len=0.08, pitch=0.2, density=100
     m, inertia = W.capsule_mass_x(radius, half_len, density)
     bld = W._Builder("capsule_chain")
     prev = bld.link(-1, W.JOINT_FREE, mass=m, com=(pitch / 2, 0.0, 0.0), inertia=inertia)
-    shape = (W.SHAPE_SPHERE, (radius,)) if spheres else (W.SHAPE_CAPSULE, (radius, half_len))
-    bld.shape(prev, *shape, pos=(pitch / 2, 0.0, 0.0))
+    bld.shape(prev, W.SHAPE_CAPSULE, (radius, half_len), pos=(pitch / 2, 0.0, 0.0))
     for _ in range(n_links - 1):
         prev = bld.link(prev, W.JOINT_REVOLUTE, axis=(0.0, 1.0, 0.0), ppos=(pitch, 0.0, 0.0), mass=m,
                         com=(pitch / 2, 0.0, 0.0), inertia=inertia, armature=0.05, damping=0.2,
                         limit=(-np.pi / 4, np.pi / 4), gear=gear)
-        bld.shape(prev, *shape, pos=(pitch / 2, 0.0, 0.0))
+        bld.shape(prev, W.SHAPE_CAPSULE, (radius, half_len), pos=(pitch / 2, 0.0, 0.0))
     # the chain straight, 5 mm above the ground at q = 0; hinge noise lifts parts of it
     return bld.build(root_pos=(0.0, 0.0, radius + 0.005), dof_noise=0.05)
 
