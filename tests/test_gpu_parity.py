@@ -419,6 +419,30 @@ def test_step_actuated_equals_writing_the_view(source, plan):
     b.destroy()
 
 
+def test_step_actuated_without_dofs():
+    """A batch with no joint DOFs (free boxes dropped on the ground): sim_step_actuated takes an
+    empty tensor (a null buffer at the C ABI) and steps exactly as sim_step."""
+    import torch
+    from paper_2108_10470_gb300 import sim
+
+    w = W.homogeneous("boxes", W.free_box(0.2, 0.1, 0.1, mass=2.0, z=0.12), 24)
+    root, dof, _ = W.seeded_inputs(w, 3, 1)
+    root[:, 2] += 0.01 * np.arange(24)
+    a, b = sim.Sim(w, flags=sim.SIM_FLAG_SIGNATURE), sim.Sim(w, flags=sim.SIM_FLAG_SIGNATURE)
+    assert a.N_D == 0
+    for s in (a, b):
+        s.root_state.copy_(torch.from_numpy(root))
+    for k in range(4):
+        a.step()
+        b.step_actuated(torch.empty(0, device="cuda"))
+    torch.cuda.synchronize()
+    for name in ("root_state", "net_contact_force", "impulse_cache", "contact_count"):
+        assert np.array_equal(getattr(a, name).cpu().numpy(), getattr(b, name).cpu().numpy()), name
+    assert int(a.contact_count.cpu().numpy().sum()) > 0
+    a.destroy()
+    b.destroy()
+
+
 def test_fp32_probe_reports_plausible_peak():
     from paper_2108_10470_gb300 import sim
     f = sim.probe_fp32_peak(2000)
