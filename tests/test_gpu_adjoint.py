@@ -283,6 +283,78 @@ def test_rollout_gradient_matches_oracle_and_checkpointing_is_exact(name, steps,
     assert len(bad) <= max_bad, bad
 
 
+def test_rollout_gradient_matches_central_differences():
+    """The differentiable-rollout workload's check: the GPU gradient of loss = mean final root
+    x-velocity of a 12-step, 8-env Ant rollout (through the autograd rollout and the reverse pass)
+    against central finite differences with h = 1e-4 of the FP64 oracle's rollout, w.r.t. the
+    actions of steps 0, 5 and 11 and the initial DOF positions and velocities. A difference counts
+    where the rollout is smooth over +-h: every step's constraint set is that of the unperturbed
+    rollout under both perturbations, and the difference agrees with the one at h / 4 to 1e-3 of
+    the env's gradient scale (the derivative holds the solver's clamps at the forward pass's
+    choices, which the constraint set does not record: within 1e-4 of some initial joint positions
+    a friction or impulse clamp switches over the 12 steps). Envs are independent, so each
+    direction perturbs the same component in every env at once."""
+    w = W.ant_workload(8)
+    steps, h = 12, 1e-4
+    root, dof, acts = W.seeded_inputs(w, 11, steps)
+    _, gd, ga, _ = loss_grad_gpu(w, root, dof, acts, 4)
+    nj = w.n_dof // w.n_envs
+
+    def rollout(d_act=None, d_dof=None):
+        O = oracle.Oracle(w)
+        r, d = root.astype(np.float64), dof.astype(np.float64)
+        if d_dof is not None:
+            d += d_dof
+        sigs = []
+        for k in range(steps):
+            a = acts[k].astype(np.float64) + (d_act[k] if d_act is not None else 0.0)
+            sigs.append(O.step(r, d, a)["signature"].copy())
+        return r[:, 7].copy(), np.array(sigs)  # per env (one actor each): final v_x; signatures
+
+    _, base_sig = rollout()
+
+    def central(make):  # d loss / d(component), per env, at h and h / 4; constraint sets kept at +-h
+        (vp, sp), (vm, sm) = rollout(**make(h)), rollout(**make(-h))
+        (vq, _), (vn, _) = rollout(**make(h / 4)), rollout(**make(-h / 4))
+        same = (sp == base_sig).all(0) & (sm == base_sig).all(0)
+        return (vp - vm) / (2 * h * w.n_envs), (vq - vn) / (h / 2 * w.n_envs), same
+
+    fd, fd4, same, gpu = [], [], [], []
+    for k in (0, 5, 11):
+        for j in range(nj):
+            def act(x, k=k, j=j):
+                da = np.zeros((steps, w.n_dof))
+                da[k, j::nj] = x
+                return {"d_act": da}
+            a, b, c = central(act)
+            fd.append(a), fd4.append(b), same.append(c), gpu.append(ga[k, j::nj])
+    for j in range(nj):
+        for comp in range(2):
+            def ini(x, j=j, comp=comp):
+                dd = np.zeros((w.n_dof, 2))
+                dd[j::nj, comp] = x
+                return {"d_dof": dd}
+            a, b, c = central(ini)
+            fd.append(a), fd4.append(b), same.append(c), gpu.append(gd[j::nj, comp])
+    fd, fd4, same, gpu = (np.array(x) for x in (fd, fd4, same, gpu))  # (directions, envs)
+    bad, checked = [], 0
+    for e in range(w.n_envs):
+        scale = max(np.abs(fd4[:, e]).max(), 1e-12)
+        m = same[:, e] & (np.abs(fd[:, e] - fd4[:, e]) <= 1e-3 * scale)
+        if m.any():  # the scale of the smooth directions alone, and the mask again with it
+            scale = max(np.abs(fd4[m, e]).max(), 1e-12)
+            m = same[:, e] & (np.abs(fd[:, e] - fd4[:, e]) <= 1e-3 * scale)
+        if m.sum() < len(m) // 2:
+            continue  # no smooth neighbourhood in most directions
+        checked += 1
+        rel = np.abs(gpu[m, e] - fd[m, e]).max() / scale
+        print(f"env {e}: {int(m.sum())} of {len(m)} directions smooth over +-h, gradient scale {scale:.3e}, "
+              f"relative deviation from central differences {rel:.2e}")
+        if rel > 1e-2:
+            bad.append(e)
+    assert checked >= w.n_envs // 2 and len(bad) <= 1, (checked, bad)
+
+
 def many_boxes(n_boxes=19):
     """A free body carrying n_boxes box shapes (8 ground candidates each) and a hinged child: 19
     boxes give an impulse cache of 3 * 152 + 2 = 458 entries, past the derivative's 448."""
